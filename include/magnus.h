@@ -1,0 +1,183 @@
+/*
+ * magnus.h -- C ABI of the GB300 first-order Magnus time-evolution library.
+ *
+ * The library evolves a driven Hamiltonian
+ *
+ *     H(t) = H0 + sum_k u^(k)(t) H_k                      (Eq. magnus-generic-ham)
+ *
+ * over N uniform Magnus intervals t_n = t0 + n dt.  For every interval it forms
+ * the first-order Magnus term
+ *
+ *     Hbar_n = dt H0 + sum_k c_{k,n} H_k,                 (Eq. magnus-first-order-term)
+ *     c_{k,n} = int_{t_n}^{t_n + dt} u^(k)(t) dt,         (Eq. magnus-first-order-coeff)
+ *
+ * exponentiates it to U_n = exp(-i Hbar_n) (hbar = 1), and carries a state or
+ * the full propagator through the product U_{N-1} ... U_0 (later intervals on
+ * the left).  This follows the paper's statement of the problem in Sec. "Time
+ * Coarse-Graining Hamiltonians" and the package interface of App. A.5
+ * (`magnus(tlist, drift_ham, control_sigs, control_hams)`,
+ * `update_control_sigs()`, `evolve()`).
+ *
+ * Conventions
+ *   - Complex matrices are d x d, row-major, interleaved (re, im) doubles:
+ *     element (i, j) is at doubles [2(i d + j), 2(i d + j) + 1].  Vectors are d
+ *     interleaved complex doubles.
+ *   - Pointers are DEVICE pointers unless a call says otherwise or the
+ *     MG_FLAG_HOST_PTRS flag is given.  The caller owns every buffer it passes;
+ *     the library copies what it keeps (operators) into its own device memory.
+ *   - Every call returns MG_OK (0) or a negative MG_E* code; mg_strerror()
+ *     turns a code into text and mg_last_error_message() gives the detail of
+ *     the most recent failure on the calling thread.  No C++ exception crosses
+ *     this interface.
+ *   - Work is queued on the context's CUDA stream.  Outputs are valid once that
+ *     stream has been synchronised; calls that fill an mg_report synchronise
+ *     the stream before returning.
+ *   - The library requires a GPU of compute capability 10.3 (sm_103a).  There is
+ *     no CPU fallback: without such a device mg_ctx_create fails with MG_ECUDA.
+ */
+#ifndef MAGNUS_H_
+#define MAGNUS_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes --------------------------------------------------------- */
+#define MG_OK            0
+#define MG_EINVAL       -1   /* bad argument (size, null pointer, mode)            */
+#define MG_ENOMEM       -2   /* device allocation failed                           */
+#define MG_ECUDA        -3   /* a CUDA runtime/driver call failed                  */
+#define MG_ENONFINITE   -4   /* NaN/Inf in a norm (bad samples or operators)       */
+#define MG_ENOTHERM     -5   /* operator not Hermitian (MG_FLAG_CHECK_HERMITIAN)   */
+#define MG_ETIMEOUT     -6   /* a bounded device-side wait gave up                 */
+#define MG_EAGAIN       -7   /* not admissible now (serving: memory budget)        */
+#define MG_EUNSUPPORTED -8   /* size or mode outside what this build supports     */
+
+/* ---- precision modes ------------------------------------------------------ */
+/* MG_PREC_FP64: every matrix product in native FP64 arithmetic.
+ * MG_PREC_SPLIT: matrix products on the tcgen05 tensor cores.  Each FP64
+ *   operand row (column) is scaled by a power of two and cut into `slices`
+ *   signed BF16 digits of `beta` bits; digit products are accumulated in FP32
+ *   TMEM accumulators that stay exact for the leading digits, and combined in
+ *   FP64.  More slices give more accuracy (about beta*slices bits).  All other
+ *   steps (quadrature, Hbar_n, norms, phases, re-orthonormalisation) run in FP64. */
+#define MG_PREC_FP64   0
+#define MG_PREC_SPLIT  1
+
+/* ---- outputs --------------------------------------------------------------- */
+#define MG_OUT_STATE       0  /* psi(T) = U_{N-1} ... U_0 psi0            */
+#define MG_OUT_PROPAGATOR  1  /* U(T)   = U_{N-1} ... U_0                 */
+
+/* ---- flags ----------------------------------------------------------------- */
+#define MG_FLAG_HOST_PTRS        1  /* the call's data pointers are host memory */
+#define MG_FLAG_CHECK_HERMITIAN  2  /* plan: reject operators with |H - H^dag| > 1e-12 |H| */
+#define MG_FLAG_NO_TRACE_SHIFT   4  /* plan: exponentiate Hbar_n itself, not Hbar_n - tr/d I */
+
+typedef struct mg_ctx mg_ctx;
+typedef struct mg_plan mg_plan;
+
+/* Per-call report (FP64 diagnostics).  Filled by mg_evolve when non-NULL. */
+typedef struct mg_report {
+  int32_t intervals;          /* Magnus intervals processed                     */
+  int32_t taylor_degree;      /* Taylor degree m used by the exponential        */
+  int32_t max_squarings;      /* largest squaring count s_n over the intervals  */
+  int32_t min_squarings;      /* smallest s_n                                   */
+  double  max_norm1;          /* largest ||Hbar_n - tau_n I||_1                 */
+  double  unitarity_defect;   /* max|U^dag U - I| (propagator) or |‖psi‖ - 1|  */
+  double  ms_total;           /* wall time of the call on the device stream     */
+  int64_t matrix_products;    /* complex d x d products issued                  */
+} mg_report;
+
+/* ---- context ---------------------------------------------------------------- */
+/* Create a context bound to CUDA device `device` and the CUDA stream `stream`
+ * (a cudaStream_t cast to void*, NULL for the legacy default stream).  The
+ * context owns the scratch workspace of later calls.  Fails with MG_ECUDA when
+ * the device is absent or is not compute capability 10.3. */
+int mg_ctx_create(mg_ctx** out, int device, void* stream);
+int mg_ctx_destroy(mg_ctx* ctx);
+/* Upper bound (bytes) on the scratch workspace the context may hold; default
+ * 16 GiB.  Larger jobs are processed in interval chunks that fit. */
+int mg_ctx_set_workspace_limit(mg_ctx* ctx, size_t bytes);
+
+/* ---- quadrature ------------------------------------------------------------- */
+/* Gauss-Legendre nodes x[p] and weights w[p] (p < P) on [-1, 1], HOST arrays.
+ * The drive samples a plan consumes are u^(k) evaluated at
+ *     t_{n,p} = t0 + n dt + (1 + x[p]) dt / 2,
+ * so that c_{k,n} = (dt/2) sum_p w[p] u^(k)(t_{n,p}) integrates
+ * Eq. magnus-first-order-coeff exactly for polynomial u of degree <= 2P - 1.
+ * 1 <= P <= 64. */
+int mg_quadrature_nodes(int P, double* x, double* w);
+
+/* ---- plan: resident operators -------------------------------------------- */
+/* Copy H0 (d x d) and H_k (K x d x d, consecutive) into device memory owned by
+ * the plan.  `precision` is MG_PREC_FP64 or MG_PREC_SPLIT; `slices` (2..8) is
+ * the number of BF16 digits per operand in MG_PREC_SPLIT (ignored for FP64).
+ * Flags: MG_FLAG_HOST_PTRS (H0/Hk are host memory), MG_FLAG_CHECK_HERMITIAN,
+ * MG_FLAG_NO_TRACE_SHIFT.  1 <= d <= 4096, 0 <= K <= 64. */
+int mg_plan_create(mg_ctx* ctx, mg_plan** out, int d, int K, const double* H0,
+                   const double* Hk, int precision, int slices, int flags);
+int mg_plan_destroy(mg_plan* plan);
+
+/* Replace the control signals (the `update_control_sigs()` step of App. A.5).
+ * samples: N x P x K doubles, u^(k)(t_{n,p}) at the nodes documented at
+ * mg_quadrature_nodes; w: the P quadrature weights (HOST array).  The samples
+ * are copied into the plan.  flags: MG_FLAG_HOST_PTRS when `samples` is host
+ * memory.  Any N >= 1 and 1 <= P <= 64. */
+int mg_set_controls(mg_plan* plan, int N, int P, double t0, double dt, const double* w,
+                    const double* samples, int flags);
+
+/* Evolve through all N intervals of the current controls (`evolve()` of App. A.5).
+ *   output = MG_OUT_STATE:      in = psi0 (d complex), out = psi(T) (d complex)
+ *   output = MG_OUT_PROPAGATOR: in = NULL (identity start) or U0 (d x d),
+ *                               out = U(T) U0 (d x d)
+ * reorth_every = R > 0 re-orthonormalises the running product every R
+ * intervals in FP64 (propagator: one Newton-Schulz polar step
+ * U <- U (3I - U^dag U)/2; state: psi <- psi/|psi|); 0 disables it.
+ * flags: MG_FLAG_HOST_PTRS when in/out are host memory (the copies are then
+ * part of the call).  rep may be NULL. */
+int mg_evolve(mg_plan* plan, int output, const double* in, double* out, int reorth_every,
+              int flags, mg_report* rep);
+
+/* ---- steps of the path (device pointers) --------------------------------- */
+/* c[n][k] = (dt/2) sum_p w[p] samples[n][p][k]   (Eq. magnus-first-order-coeff).
+ * samples N x P x K, w P doubles (device), c N x K. */
+int mg_coefficients(mg_ctx* ctx, int N, int P, int K, double dt, const double* w,
+                    const double* samples, double* c);
+
+/* Hbar[n] = dt H0 + sum_k c[n][k] H_k   (Eq. magnus-first-order-term), N x d x d
+ * complex output; also tau[n] = Re tr(Hbar_n)/d and norm1[n] =
+ * ||Hbar_n - tau_n I||_1 (largest absolute column sum), both N doubles (device,
+ * may be NULL). */
+int mg_build_omega(mg_ctx* ctx, int N, int d, int K, double dt, const double* H0,
+                   const double* Hk, const double* c, double* Hbar, double* tau, double* norm1);
+
+/* U[b] = exp(-i A[b]) for a batch of Hermitian d x d matrices A (trace shift,
+ * scaling and squaring of a Taylor polynomial).  precision/slices as for plans.
+ * The squaring count of every matrix is chosen from its own FP64 1-norm;
+ * squarings (device int[batch], may be NULL) receives it. */
+int mg_expm(mg_ctx* ctx, int batch, int d, const double* A, double* U, int precision,
+            int slices, int* squarings);
+
+/* C[b] = A[b] B[b] for a batch of complex d x d matrices (the matrix product
+ * every exponential and propagation step is built from). */
+int mg_cgemm(mg_ctx* ctx, int batch, int d, const double* A, const double* B, double* C,
+             int precision, int slices);
+
+/* Carry a state or a propagator through given interval propagators U (N x d x d):
+ * the propagation step of mg_evolve on its own.  Arguments as for mg_evolve. */
+int mg_propagate(mg_ctx* ctx, int N, int d, const double* U, int output, const double* in,
+                 double* out, int reorth_every, int precision, int slices);
+
+/* ---- diagnostics ----------------------------------------------------------- */
+const char* mg_strerror(int code);
+const char* mg_last_error_message(void);
+/* Number of kernels this process has launched through the library. */
+int64_t mg_kernel_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MAGNUS_H_ */

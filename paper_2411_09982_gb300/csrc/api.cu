@@ -1,0 +1,911 @@
+// C ABI of the Magnus library and the host-side orchestration of the hot path:
+//
+//   samples --(quadrature)--> c_{k,n} --(first-order term)--> Hbar_n - tau_n I
+//     --(FP64 1-norm, (m, s) choice)--> X_n = -i 2^{-s} (Hbar_n - tau_n I)
+//     --(Taylor polynomial, Paterson-Stockmeyer)--> T_m(X_n)
+//     --(s squarings)--> e^{-i tau_n} T_m(X_n)^{2^s} = U_n
+//     --(propagation)--> psi(T) or U(T) = U_{N-1} ... U_0
+//
+// (Sec. "Magnus Expansion": Eqs. magnus-first-order-term and
+// magnus-first-order-coeff, exponentiated per interval; App. A.5 for the
+// interface.)  Intervals are processed in chunks that fit the context's
+// workspace; within a chunk every step is one batched launch over all of the
+// chunk's intervals.
+#include "common.cuh"
+
+#include <cmath>
+#include <cstdarg>
+#include <cstring>
+#include <algorithm>
+#include <atomic>
+#include <mutex>
+#include <string>
+#include <vector>
+
+// ---------------------------------------------------------------------------
+// error reporting
+// ---------------------------------------------------------------------------
+namespace mg {
+static thread_local char g_msg[512] = "";
+static std::atomic<long long> g_launches{0};
+
+void set_last_message(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_msg, sizeof(g_msg), fmt, ap);
+  va_end(ap);
+}
+void set_last_cuda_error(cudaError_t e, const char* what, const char* file, int line) {
+  set_last_message("%s failed: %s (%s:%d)", what, cudaGetErrorString(e), file, line);
+}
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+int check_launch(const char* name) {
+  count_launch();
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    set_last_message("launch of %s failed: %s", name, cudaGetErrorString(e));
+    return MG_ECUDA;
+  }
+  return MG_OK;
+}
+}  // namespace mg
+
+using namespace mg;
+
+// ---------------------------------------------------------------------------
+// context and plan
+// ---------------------------------------------------------------------------
+struct mg_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  size_t ws_limit = (size_t)16 << 30;
+  std::vector<void*> slot_ptr;
+  std::vector<size_t> slot_size;
+  int* status = nullptr;      // device status word of bounded waits
+  double* small = nullptr;    // small device scratch (norm bits, reductions)
+  size_t small_n = 0;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+};
+
+struct mg_plan {
+  mg_ctx* ctx = nullptr;
+  int d = 0, K = 0, precision = MG_PREC_FP64, L = 6, flags = 0;
+  double* H0 = nullptr;
+  double* Hk = nullptr;
+  int N = 0, P = 0;
+  double t0 = 0.0, dt = 0.0;
+  double* w = nullptr;
+  double* samples = nullptr;
+  double* c = nullptr;
+  size_t samples_cap = 0, c_cap = 0;
+};
+
+namespace {
+
+enum Slot {
+  WS_W = 0,       // Hbar_n - tau_n I, then X_n
+  WS_P2, WS_P3, WS_Y, WS_R0, WS_R1,
+  WS_ABUF, WS_BBUF0, WS_BBUF1,
+  WS_TAU, WS_NORM, WS_ACC, WS_ACC2, WS_NS_G, WS_NS_H, WS_VEC,
+  WS_TREE0, WS_TREE1, WS_UBUF,
+  WS_COUNT
+};
+
+int ws_get(mg_ctx* ctx, int slot, size_t bytes, void** out) {
+  if ((int)ctx->slot_ptr.size() < WS_COUNT) {
+    ctx->slot_ptr.resize(WS_COUNT, nullptr);
+    ctx->slot_size.resize(WS_COUNT, 0);
+  }
+  if (bytes == 0) bytes = 256;
+  if (ctx->slot_size[slot] < bytes) {
+    if (ctx->slot_ptr[slot]) {
+      MG_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+      MG_CUDA_TRY(cudaFree(ctx->slot_ptr[slot]));
+      ctx->slot_ptr[slot] = nullptr;
+      ctx->slot_size[slot] = 0;
+    }
+    void* p = nullptr;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      set_last_message("device allocation of %zu bytes failed", bytes);
+      return MG_ENOMEM;
+    }
+    ctx->slot_ptr[slot] = p;
+    ctx->slot_size[slot] = bytes;
+  }
+  *out = ctx->slot_ptr[slot];
+  return MG_OK;
+}
+
+template <typename T>
+int ws(mg_ctx* ctx, int slot, size_t count, T** out) {
+  void* p = nullptr;
+  MG_TRY(ws_get(ctx, slot, count * sizeof(T), &p));
+  *out = reinterpret_cast<T*>(p);
+  return MG_OK;
+}
+
+int small_scratch(mg_ctx* ctx, size_t n, double** out) {
+  if (ctx->small_n < n) {
+    if (ctx->small) {
+      MG_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+      cudaFree(ctx->small);
+      ctx->small = nullptr;
+    }
+    size_t m = std::max<size_t>(n, 4096);
+    if (cudaMalloc(&ctx->small, m * sizeof(double)) != cudaSuccess) {
+      cudaGetLastError();
+      set_last_message("device allocation of %zu doubles failed", m);
+      return MG_ENOMEM;
+    }
+    ctx->small_n = m;
+  }
+  *out = ctx->small;
+  return MG_OK;
+}
+
+int check_status(mg_ctx* ctx) {
+  int st = 0;
+  MG_CUDA_TRY(cudaMemcpyAsync(&st, ctx->status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  MG_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  if (st == MG_DEV_TIMEOUT) {
+    set_last_message("a bounded device-side wait gave up (tensor-core product)");
+    int z = 0;
+    cudaMemcpy(ctx->status, &z, sizeof(int), cudaMemcpyHostToDevice);
+    return MG_ETIMEOUT;
+  }
+  return MG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Taylor degree / squaring selection
+// ---------------------------------------------------------------------------
+struct TaylorChoice {
+  int m, p, products, s;
+  double theta;
+};
+
+// Largest theta with  sum_{j>m} theta^j / j!  <=  u * theta: the truncated
+// series then errs by at most u relative to ||X|| <= theta, and the 2^s
+// squarings keep that relative bound for 2^s X (the error of the squared
+// result grows like 2^s * u * theta = u * ||A||).
+double taylor_theta(int m, double u) {
+  auto tail_ratio = [&](double th) {
+    double term = 1.0;
+    for (int j = 1; j <= m; ++j) term *= th / j;
+    double sum = 0.0;
+    for (int j = m + 1; j <= m + 80; ++j) {
+      term *= th / j;
+      sum += term;
+      if (term < 1e-40 * sum) break;
+    }
+    return sum / th;
+  };
+  double lo = 0.0, hi = 40.0;
+  for (int it = 0; it < 200; ++it) {
+    double mid = 0.5 * (lo + hi);
+    if (tail_ratio(mid) <= u) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+double unit_roundoff(int precision, int L, int d) {
+  double u64 = std::ldexp(1.0, -53);
+  if (precision == MG_PREC_FP64) return u64;
+  int beta = split_beta_for(d);
+  return std::max(u64, std::ldexp(1.0, -beta * L));
+}
+
+TaylorChoice choose_taylor(double norm1, double u) {
+  static const int ms[] = {2, 4, 6, 9, 12, 16};
+  static const int ps[] = {2, 2, 3, 3, 4, 4};
+  static const int cost[] = {1, 2, 3, 4, 5, 6};
+  TaylorChoice best{16, 4, 6, 0, 0.0};
+  int best_total = 1 << 30;
+  for (int i = 0; i < 6; ++i) {
+    double th = taylor_theta(ms[i], u);
+    int s = 0;
+    if (norm1 > th) s = (int)std::ceil(std::log2(norm1 / th));
+    while (s > 0 && norm1 * std::ldexp(1.0, -(s - 1)) <= th) --s;
+    while (norm1 * std::ldexp(1.0, -s) > th) ++s;
+    int total = cost[i] + s;
+    if (total < best_total || (total == best_total && s < best.s)) {
+      best_total = total;
+      best = TaylorChoice{ms[i], ps[i], cost[i], s, th};
+    }
+  }
+  return best;
+}
+
+// ---------------------------------------------------------------------------
+// matrix-product engine: FP64 or split precision, same call pattern
+// ---------------------------------------------------------------------------
+struct Engine {
+  mg_ctx* ctx;
+  int d, prec, L;
+  void* abuf = nullptr;
+  void* bbuf[2] = {nullptr, nullptr};
+  long long products = 0;
+
+  int reserve(int batch) {
+    if (prec != MG_PREC_SPLIT) return MG_OK;
+    MG_TRY(ws_get(ctx, WS_ABUF, split_a_bytes(d, L, batch), &abuf));
+    MG_TRY(ws_get(ctx, WS_BBUF0, split_b_bytes(d, L, batch), &bbuf[0]));
+    MG_TRY(ws_get(ctx, WS_BBUF1, split_b_bytes(d, L, batch), &bbuf[1]));
+    return MG_OK;
+  }
+  int prepA(int batch, const double* A, long long sA) {
+    if (prec != MG_PREC_SPLIT) return MG_OK;
+    return split_slice_a(d, L, batch, A, sA, abuf, ctx->stream);
+  }
+  int prepB(int slot, int batch, const double* B, long long sB) {
+    if (prec != MG_PREC_SPLIT) return MG_OK;
+    return split_slice_b(d, L, batch, B, sB, bbuf[slot], ctx->stream);
+  }
+  // C = A B (+ addends); split mode uses the digits prepared by prepA / prepB(slot).
+  int mul(int batch, const double* A, long long sA, int slot, const double* B, long long sB, double* C,
+          long long sC, const AddTerms& add) {
+    products += batch;
+    if (prec == MG_PREC_SPLIT) return split_gemm(d, L, batch, abuf, bbuf[slot], C, sC, add, ctx->status, ctx->stream);
+    return launch_cgemm_f64(batch, d, A, sA, 0, B, sB, C, sC, add, ctx->stream);
+  }
+};
+
+long long mat_doubles(int d) { return 2LL * d * d; }
+
+// ---------------------------------------------------------------------------
+// batched exponential of a chunk:  U_b = e^{-i tau_b} exp(-i W_b)
+// W (shifted, Hermitian) is overwritten by X.  norm1 and tau are device arrays.
+// ---------------------------------------------------------------------------
+struct ExpmStats {
+  int m = 0, s_applied = 0, s_min = 1 << 30, s_max = 0;
+  double max_norm = 0.0;
+};
+
+int expm_chunk(mg_ctx* ctx, Engine& eng, int batch, double* W, const double* tau, const double* norm1_dev,
+               double* U, long long sU, ExpmStats* st) {
+  const int d = eng.d;
+  const long long md = mat_doubles(d);
+  cudaStream_t s = ctx->stream;
+
+  // FP64 norms -> host: squaring count per interval and for the batch
+  std::vector<double> nrm(batch);
+  MG_CUDA_TRY(cudaMemcpyAsync(nrm.data(), norm1_dev, sizeof(double) * batch, cudaMemcpyDeviceToHost, s));
+  MG_CUDA_TRY(cudaStreamSynchronize(s));
+  double nmax = 0.0;
+  for (int b = 0; b < batch; ++b) {
+    if (!std::isfinite(nrm[b])) {
+      set_last_message("non-finite norm of the Magnus exponent in item %d of the batch", b);
+      return MG_ENONFINITE;
+    }
+    nmax = std::max(nmax, nrm[b]);
+  }
+  const double u = unit_roundoff(eng.prec, eng.L, d);
+  TaylorChoice tc = choose_taylor(nmax, u);
+  if (st) {
+    st->m = tc.m;
+    st->s_applied = tc.s;
+    st->max_norm = std::max(st->max_norm, nmax);
+    for (int b = 0; b < batch; ++b) {
+      int sb = 0;
+      while (nrm[b] * std::ldexp(1.0, -sb) > tc.theta) ++sb;
+      st->s_min = std::min(st->s_min, sb);
+      st->s_max = std::max(st->s_max, sb);
+    }
+  }
+
+  double *P2, *P3, *Y, *R0, *R1;
+  MG_TRY(ws(ctx, WS_P2, md * batch, &P2));
+  MG_TRY(ws(ctx, WS_P3, md * batch, &P3));
+  MG_TRY(ws(ctx, WS_Y, md * batch, &Y));
+  MG_TRY(ws(ctx, WS_R0, md * batch, &R0));
+  MG_TRY(ws(ctx, WS_R1, md * batch, &R1));
+  MG_TRY(eng.reserve(batch));
+
+  // X = -i 2^{-s} W   (in place)
+  MG_TRY(launch_scale_minus_i(batch, d, W, W, nullptr, tc.s, s));
+  const double* X = W;
+
+  // coefficients 1/j!
+  double a[17];
+  a[0] = 1.0;
+  for (int j = 1; j <= 16; ++j) a[j] = a[j - 1] / j;
+  auto coef = [&](int j) { return j <= tc.m ? a[j] : 0.0; };
+
+  // powers P_1 = X, ..., P_p = Y
+  const int p = tc.p, m = tc.m;
+  const double* P[5] = {nullptr, X, nullptr, nullptr, nullptr};
+  double* pow_buf[5] = {nullptr, nullptr, P2, P3, nullptr};
+  pow_buf[p] = Y;
+  MG_TRY(eng.prepB(0, batch, X, md));
+  for (int j = 2; j <= p; ++j) {
+    MG_TRY(eng.prepA(batch, P[j - 1], md));
+    AddTerms none;
+    MG_TRY(eng.mul(batch, P[j - 1], md, 0, X, md, pow_buf[j], md, none));
+    P[j] = pow_buf[j];
+  }
+  // Horner in Y = X^p over blocks B_i = sum_{j<p} a_{ip+j} X^j
+  const int q = m / p, r = m - q * p;
+  double* R = R0;
+  double* Rn = R1;
+  int i_next;
+  {
+    const double* src[4];
+    double cf[4];
+    int ns = 0;
+    int top = (r == 0) ? q - 1 : q;
+    for (int j = 1; j < p; ++j) { src[ns] = P[j]; cf[ns] = coef(top * p + j); ++ns; }
+    double diag = coef(top * p);
+    if (r == 0) { src[ns] = P[p]; cf[ns] = coef(m); ++ns; }
+    MG_TRY(launch_lincomb(batch, d, R, ns, src, cf, diag, s));
+    i_next = top - 1;
+  }
+  if (i_next >= 0) MG_TRY(eng.prepB(1, batch, P[p], md));
+  for (int i = i_next; i >= 0; --i) {
+    AddTerms add;
+    add.n = 0;
+    for (int j = 1; j < p; ++j) { add.src[add.n] = P[j]; add.coef[add.n] = coef(i * p + j); ++add.n; }
+    add.stride = md;
+    add.diag = coef(i * p);
+    MG_TRY(eng.prepA(batch, R, md));
+    MG_TRY(eng.mul(batch, R, md, 1, P[p], md, Rn, md, add));
+    std::swap(R, Rn);
+  }
+  // squarings
+  for (int k = 0; k < tc.s; ++k) {
+    MG_TRY(eng.prepA(batch, R, md));
+    MG_TRY(eng.prepB(0, batch, R, md));
+    AddTerms none;
+    MG_TRY(eng.mul(batch, R, md, 0, R, md, Rn, md, none));
+    std::swap(R, Rn);
+  }
+  // exact trace phase e^{-i tau_b}
+  if (sU != md) return MG_EINVAL;
+  if (tau) return launch_apply_phase(batch, d, (long long)d * d, tau, R, U, s);
+  return launch_copy_strided(batch, md, R, md, U, sU, s);
+}
+
+// One Newton-Schulz polar step in FP64 on a batch: Z <- Z (3I - Z^dag Z)/2.
+int reorth_batch(mg_ctx* ctx, int batch, int d, double* Z, long long sZ) {
+  const long long md = mat_doubles(d);
+  double *G, *H;
+  MG_TRY(ws(ctx, WS_NS_G, md * batch, &G));
+  MG_TRY(ws(ctx, WS_NS_H, md * batch, &H));
+  AddTerms none;
+  MG_TRY(launch_cgemm_f64(batch, d, Z, sZ, 1, Z, sZ, G, md, none, ctx->stream));
+  const double* src[1] = {G};
+  double cf[1] = {-0.5};
+  MG_TRY(launch_lincomb(batch, d, H, 1, src, cf, 1.5, ctx->stream));
+  MG_TRY(launch_cgemm_f64(batch, d, Z, sZ, 0, H, md, G, md, none, ctx->stream));
+  return launch_copy_strided(batch, md, G, md, Z, sZ, ctx->stream);
+}
+
+// Tree product of a batch of propagators (earliest first): *out receives a
+// pointer (inside the workspace) to U_{n-1} ... U_1 U_0.  Level k multiplies
+// neighbouring pairs, later item on the left; an odd item is carried up.  Nodes
+// spanning `reorth_span` intervals (a power of two; 0 = never) are
+// re-orthonormalised in FP64.
+int tree_product(mg_ctx* ctx, Engine& eng, int n, const double* U, double** out, int reorth_span) {
+  const int d = eng.d;
+  const long long md = mat_doubles(d);
+  double *b0, *b1;
+  MG_TRY(ws(ctx, WS_TREE0, md * std::max(1, (n + 1) / 2), &b0));
+  MG_TRY(ws(ctx, WS_TREE1, md * std::max(1, (n + 3) / 4), &b1));
+  if (n == 1) {
+    MG_TRY(launch_copy_strided(1, md, U, md, b0, md, ctx->stream));
+    *out = b0;
+    return MG_OK;
+  }
+  const double* cur = U;
+  int cnt = n, span = 1, level = 0;
+  while (cnt > 1) {
+    double* dst = (level % 2 == 0) ? b0 : b1;   // level 0 -> ceil(n/2) items, level 1 -> ceil(n/4), ...
+    const int pairs = cnt / 2;
+    MG_TRY(eng.reserve(pairs));
+    MG_TRY(eng.prepA(pairs, cur + md, 2 * md));
+    MG_TRY(eng.prepB(0, pairs, cur, 2 * md));
+    AddTerms none;
+    MG_TRY(eng.mul(pairs, cur + md, 2 * md, 0, cur, 2 * md, dst, md, none));
+    if (cnt & 1)
+      MG_TRY(launch_copy_strided(1, md, cur + (long long)(cnt - 1) * md, md, dst + (long long)pairs * md, md,
+                                 ctx->stream));
+    span *= 2;
+    cnt = pairs + (cnt & 1);
+    if (reorth_span > 0 && span == reorth_span) MG_TRY(reorth_batch(ctx, cnt, d, dst, md));
+    cur = dst;
+    ++level;
+  }
+  *out = const_cast<double*>(cur);
+  return MG_OK;
+}
+
+// Device bytes one interval of a chunk needs: Hbar/X, X^2, X^3, Y, two Horner
+// buffers, the chunk's U_n, tree and re-orthonormalisation scratch (about
+// 9 matrices), plus the BF16 digits of one A and two B operands.
+size_t per_interval_bytes(int d, int prec, int L) {
+  size_t md = (size_t)mat_doubles(d) * sizeof(double);
+  size_t b = 9 * md;
+  if (prec == MG_PREC_SPLIT) b += split_a_bytes(d, L, 1) + 2 * split_b_bytes(d, L, 1);
+  return b;
+}
+
+int chunk_size(mg_ctx* ctx, int d, int prec, int L, int N, int align) {
+  const size_t per = per_interval_bytes(d, prec, L);
+  long long c = (long long)(ctx->ws_limit / per);
+  if (c < 1) c = 1;
+  if (c > 4096) c = 4096;
+  if (c > N) c = N;
+  if (align > 1 && c > align) c = (c / align) * align;
+  return (int)c;
+}
+
+int validate_prec(int precision, int L) {
+  if (precision != MG_PREC_FP64 && precision != MG_PREC_SPLIT) return MG_EINVAL;
+  if (precision == MG_PREC_SPLIT && (L < 2 || L > 8)) return MG_EINVAL;
+  return MG_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+const char* mg_strerror(int code) {
+  switch (code) {
+    case MG_OK: return "ok";
+    case MG_EINVAL: return "invalid argument";
+    case MG_ENOMEM: return "out of device memory";
+    case MG_ECUDA: return "CUDA error";
+    case MG_ENONFINITE: return "non-finite value";
+    case MG_ENOTHERM: return "operator is not Hermitian";
+    case MG_ETIMEOUT: return "device-side wait timed out";
+    case MG_EAGAIN: return "not admissible now";
+    case MG_EUNSUPPORTED: return "unsupported size or mode";
+  }
+  return "unknown error";
+}
+
+const char* mg_last_error_message(void) { return g_msg; }
+
+int64_t mg_kernel_launch_count(void) { return (int64_t)g_launches.load(); }
+
+int mg_ctx_create(mg_ctx** out, int device, void* stream) {
+  if (!out) return MG_EINVAL;
+  *out = nullptr;
+  int n = 0;
+  MG_CUDA_TRY(cudaGetDeviceCount(&n));
+  if (device < 0 || device >= n) {
+    set_last_message("device %d not present (%d devices)", device, n);
+    return MG_EINVAL;
+  }
+  cudaDeviceProp prop;
+  MG_CUDA_TRY(cudaGetDeviceProperties(&prop, device));
+  if (prop.major != 10 || prop.minor != 3) {
+    set_last_message("device %d is sm_%d%d; this library is built for sm_103a only", device, prop.major,
+                     prop.minor);
+    return MG_ECUDA;
+  }
+  MG_CUDA_TRY(cudaSetDevice(device));
+  mg_ctx* c = new mg_ctx();
+  c->device = device;
+  c->stream = reinterpret_cast<cudaStream_t>(stream);
+  if (cudaMalloc(&c->status, sizeof(int)) != cudaSuccess) {
+    delete c;
+    return MG_ENOMEM;
+  }
+  cudaMemset(c->status, 0, sizeof(int));
+  cudaEventCreate(&c->ev0);
+  cudaEventCreate(&c->ev1);
+  *out = c;
+  return MG_OK;
+}
+
+int mg_ctx_destroy(mg_ctx* ctx) {
+  if (!ctx) return MG_EINVAL;
+  cudaSetDevice(ctx->device);
+  cudaStreamSynchronize(ctx->stream);
+  for (void* p : ctx->slot_ptr)
+    if (p) cudaFree(p);
+  if (ctx->small) cudaFree(ctx->small);
+  if (ctx->status) cudaFree(ctx->status);
+  if (ctx->ev0) cudaEventDestroy(ctx->ev0);
+  if (ctx->ev1) cudaEventDestroy(ctx->ev1);
+  delete ctx;
+  return MG_OK;
+}
+
+int mg_ctx_set_workspace_limit(mg_ctx* ctx, size_t bytes) {
+  if (!ctx || bytes < ((size_t)1 << 20)) return MG_EINVAL;
+  ctx->ws_limit = bytes;
+  return MG_OK;
+}
+
+// Gauss-Legendre nodes by Newton iteration on P_n(x) with the three-term
+// recurrence; weights 2 / ((1 - x^2) P_n'(x)^2).
+int mg_quadrature_nodes(int P, double* x, double* w) {
+  if (P < 1 || P > 64 || !x || !w) return MG_EINVAL;
+  const double pi = 3.14159265358979323846;
+  for (int i = 0; i < (P + 1) / 2; ++i) {
+    double z = std::cos(pi * (i + 0.75) / (P + 0.5));
+    double dp = 0.0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = z;
+      for (int k = 2; k <= P; ++k) {
+        double pk = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+        p0 = p1;
+        p1 = pk;
+      }
+      if (P == 1) { p1 = z; p0 = 1.0; }
+      dp = P * (z * p1 - p0) / (z * z - 1.0);
+      double dz = p1 / dp;
+      z -= dz;
+      if (std::fabs(dz) < 1e-16) {
+        // one more update of the derivative at the converged node
+        p0 = 1.0; p1 = z;
+        for (int k = 2; k <= P; ++k) {
+          double pk = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+          p0 = p1;
+          p1 = pk;
+        }
+        dp = P * (z * p1 - p0) / (z * z - 1.0);
+        break;
+      }
+    }
+    double wi = 2.0 / ((1.0 - z * z) * dp * dp);
+    x[i] = -z;
+    x[P - 1 - i] = z;
+    w[i] = wi;
+    w[P - 1 - i] = wi;
+  }
+  if (P % 2 == 1) x[P / 2] = 0.0;
+  return MG_OK;
+}
+
+int mg_plan_create(mg_ctx* ctx, mg_plan** out, int d, int K, const double* H0, const double* Hk, int precision,
+                   int slices, int flags) {
+  if (!ctx || !out || !H0 || d < 1 || d > 4096 || K < 0 || K > 64 || (K > 0 && !Hk)) return MG_EINVAL;
+  MG_TRY(validate_prec(precision, slices));
+  *out = nullptr;
+  MG_CUDA_TRY(cudaSetDevice(ctx->device));
+  mg_plan* p = new mg_plan();
+  p->ctx = ctx;
+  p->d = d;
+  p->K = K;
+  p->precision = precision;
+  p->L = slices;
+  p->flags = flags;
+  const size_t mb = sizeof(double) * mat_doubles(d);
+  if (cudaMalloc(&p->H0, mb) != cudaSuccess || (K > 0 && cudaMalloc(&p->Hk, mb * K) != cudaSuccess)) {
+    cudaGetLastError();
+    mg_plan_destroy(p);
+    return MG_ENOMEM;
+  }
+  const cudaMemcpyKind kind = (flags & MG_FLAG_HOST_PTRS) ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+  cudaError_t e = cudaMemcpyAsync(p->H0, H0, mb, kind, ctx->stream);
+  if (e == cudaSuccess && K > 0) e = cudaMemcpyAsync(p->Hk, Hk, mb * K, kind, ctx->stream);
+  if (e != cudaSuccess) {
+    set_last_cuda_error(e, "operator copy", __FILE__, __LINE__);
+    mg_plan_destroy(p);
+    return MG_ECUDA;
+  }
+  if (flags & MG_FLAG_CHECK_HERMITIAN) {
+    double* sc;
+    int r = small_scratch(ctx, 4, &sc);
+    unsigned long long hb[2];
+    for (int k = 0; r == MG_OK && k <= K; ++k) {
+      const double* H = k == 0 ? p->H0 : p->Hk + (k - 1) * mat_doubles(d);
+      r = launch_hermitian_defect(d, 1, H, reinterpret_cast<unsigned long long*>(sc), ctx->stream);
+      if (r == MG_OK && cudaMemcpy(hb, sc, sizeof(hb), cudaMemcpyDeviceToHost) != cudaSuccess) r = MG_ECUDA;
+      if (r == MG_OK) {
+        double dm, hm;
+        memcpy(&dm, &hb[0], 8);
+        memcpy(&hm, &hb[1], 8);
+        if (!(dm <= 1e-12 * hm)) {
+          set_last_message("operator %d is not Hermitian: max|H - H^dag| = %g, max|H| = %g", k, dm, hm);
+          r = MG_ENOTHERM;
+        }
+      }
+    }
+    if (r != MG_OK) {
+      mg_plan_destroy(p);
+      return r;
+    }
+  }
+  *out = p;
+  return MG_OK;
+}
+
+int mg_plan_destroy(mg_plan* p) {
+  if (!p) return MG_EINVAL;
+  if (p->ctx) cudaStreamSynchronize(p->ctx->stream);
+  cudaFree(p->H0);
+  cudaFree(p->Hk);
+  cudaFree(p->w);
+  cudaFree(p->samples);
+  cudaFree(p->c);
+  delete p;
+  return MG_OK;
+}
+
+int mg_set_controls(mg_plan* p, int N, int P, double t0, double dt, const double* w, const double* samples,
+                    int flags) {
+  if (!p || N < 1 || P < 1 || P > 64 || !w || !(dt > 0.0) || !std::isfinite(t0)) return MG_EINVAL;
+  if (p->K > 0 && !samples) return MG_EINVAL;
+  mg_ctx* ctx = p->ctx;
+  MG_CUDA_TRY(cudaSetDevice(ctx->device));
+  cudaStream_t s = ctx->stream;
+  const size_t ns = (size_t)N * P * p->K;
+  if (p->samples_cap < ns) {
+    cudaFree(p->samples);
+    p->samples = nullptr;
+    if (cudaMalloc(&p->samples, std::max<size_t>(ns, 1) * sizeof(double)) != cudaSuccess) { cudaGetLastError(); return MG_ENOMEM; }
+    p->samples_cap = ns;
+  }
+  const size_t nc = (size_t)N * p->K;
+  if (p->c_cap < nc) {
+    cudaFree(p->c);
+    p->c = nullptr;
+    if (cudaMalloc(&p->c, std::max<size_t>(nc, 1) * sizeof(double)) != cudaSuccess) { cudaGetLastError(); return MG_ENOMEM; }
+    p->c_cap = nc;
+  }
+  if (!p->w && cudaMalloc(&p->w, 64 * sizeof(double)) != cudaSuccess) { cudaGetLastError(); return MG_ENOMEM; }
+  MG_CUDA_TRY(cudaMemcpyAsync(p->w, w, P * sizeof(double), cudaMemcpyHostToDevice, s));
+  if (ns > 0) {
+    const cudaMemcpyKind kind = (flags & MG_FLAG_HOST_PTRS) ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    MG_CUDA_TRY(cudaMemcpyAsync(p->samples, samples, ns * sizeof(double), kind, s));
+  }
+  p->N = N;
+  p->P = P;
+  p->t0 = t0;
+  p->dt = dt;
+  MG_TRY(launch_coefficients(N, P, p->K, dt, p->w, p->samples, p->c, s));
+  // stage the weights before the host array may go away
+  MG_CUDA_TRY(cudaStreamSynchronize(s));
+  return MG_OK;
+}
+
+int mg_coefficients(mg_ctx* ctx, int N, int P, int K, double dt, const double* w, const double* samples,
+                    double* c) {
+  if (!ctx || N < 1 || P < 1 || K < 0 || !w || (K > 0 && (!samples || !c))) return MG_EINVAL;
+  MG_CUDA_TRY(cudaSetDevice(ctx->device));
+  return launch_coefficients(N, P, K, dt, w, samples, c, ctx->stream);
+}
+
+int mg_build_omega(mg_ctx* ctx, int N, int d, int K, double dt, const double* H0, const double* Hk,
+                   const double* c, double* Hbar, double* tau, double* norm1) {
+  if (!ctx || N < 1 || d < 1 || K < 0 || !H0 || !Hbar || (K > 0 && (!Hk || !c))) return MG_EINVAL;
+  MG_CUDA_TRY(cudaSetDevice(ctx->device));
+  double* sc;
+  MG_TRY(small_scratch(ctx, (size_t)K + 1 + N, &sc));
+  return launch_build_omega(N, d, K, dt, H0, Hk, c, Hbar, tau, norm1, /*shift=*/1, /*write_shifted=*/0, sc,
+                            ctx->stream);
+}
+
+int mg_cgemm(mg_ctx* ctx, int batch, int d, const double* A, const double* B, double* C, int precision,
+             int slices) {
+  if (!ctx || batch < 1 || d < 1 || d > 4096 || !A || !B || !C) return MG_EINVAL;
+  MG_TRY(validate_prec(precision, slices));
+  MG_CUDA_TRY(cudaSetDevice(ctx->device));
+  Engine eng{ctx, d, precision, slices};
+  const long long md = mat_doubles(d);
+  const int chunk = std::min(batch, 65535);
+  for (int b0 = 0; b0 < batch; b0 += chunk) {
+    int nb = std::min(chunk, batch - b0);
+    MG_TRY(eng.reserve(nb));
+    MG_TRY(eng.prepA(nb, A + b0 * md, md));
+    MG_TRY(eng.prepB(0, nb, B + b0 * md, md));
+    AddTerms none;
+    MG_TRY(eng.mul(nb, A + b0 * md, md, 0, B + b0 * md, md, C + b0 * md, md, none));
+  }
+  if (precision == MG_PREC_SPLIT) return check_status(ctx);
+  return MG_OK;
+}
+
+int mg_expm(mg_ctx* ctx, int batch, int d, const double* A, double* U, int precision, int slices, int* squarings) {
+  if (!ctx || batch < 1 || d < 1 || d > 4096 || !A || !U) return MG_EINVAL;
+  MG_TRY(validate_prec(precision, slices));
+  MG_CUDA_TRY(cudaSetDevice(ctx->device));
+  Engine eng{ctx, d, precision, slices};
+  const long long md = mat_doubles(d);
+  const int chunk = chunk_size(ctx, d, precision, slices, batch, 1);
+  for (int b0 = 0; b0 < batch; b0 += chunk) {
+    const int nb = std::min(chunk, batch - b0);
+    double *W, *tau, *nrm, *sc;
+    MG_TRY(ws(ctx, WS_W, md * nb, &W));
+    MG_TRY(ws(ctx, WS_TAU, nb, &tau));
+    MG_TRY(ws(ctx, WS_NORM, nb, &nrm));
+    MG_TRY(small_scratch(ctx, nb, &sc));
+    MG_TRY(launch_shift_norm(nb, d, A + b0 * md, W, tau, nrm, reinterpret_cast<unsigned long long*>(sc), 1,
+                             ctx->stream));
+    ExpmStats st;
+    MG_TRY(expm_chunk(ctx, eng, nb, W, tau, nrm, U + b0 * md, md, &st));
+    if (squarings) {
+      std::vector<int> sq(nb, st.s_applied);
+      MG_CUDA_TRY(cudaMemcpyAsync(squarings + b0, sq.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, ctx->stream));
+      MG_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    }
+  }
+  if (precision == MG_PREC_SPLIT) return check_status(ctx);
+  return MG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// propagation driver shared by mg_evolve and mg_propagate
+// ---------------------------------------------------------------------------
+namespace {
+
+struct PropState {
+  int output;
+  int d;
+  double* psi = nullptr;     // state mode (device, workspace)
+  double* acc = nullptr;     // propagator mode: running product (device, workspace)
+  bool acc_init = false;
+  int done = 0;
+};
+
+// Fold the chunk's propagators U (n of them, stride md) into the running state.
+int fold_chunk(mg_ctx* ctx, Engine& eng, PropState& ps, int n, const double* U, int reorth) {
+  const int d = ps.d;
+  const long long md = mat_doubles(d);
+  if (ps.output == MG_OUT_STATE) {
+    double* tmp;
+    MG_TRY(ws(ctx, WS_VEC, 2 * d + 2, &tmp));
+    MG_TRY(launch_state_chain(n, d, U, md, ps.psi, tmp + 2, reorth, ps.done, ctx->stream));
+    ps.done += n;
+    return MG_OK;
+  }
+  int span = 0;
+  if (reorth > 0) {
+    span = 1;
+    while (span * 2 <= reorth) span *= 2;
+    if (span < 2) span = 0;
+  }
+  double* chunk_prod = nullptr;
+  MG_TRY(tree_product(ctx, eng, n, U, &chunk_prod, span));
+  if (!ps.acc_init) {
+    MG_TRY(launch_copy_strided(1, md, chunk_prod, md, ps.acc, md, ctx->stream));
+    ps.acc_init = true;
+  } else {
+    double* acc2;
+    MG_TRY(ws(ctx, WS_ACC2, md, &acc2));
+    MG_TRY(eng.reserve(1));
+    MG_TRY(eng.prepA(1, chunk_prod, md));
+    MG_TRY(eng.prepB(0, 1, ps.acc, md));
+    AddTerms none;
+    MG_TRY(eng.mul(1, chunk_prod, md, 0, ps.acc, md, acc2, md, none));
+    MG_TRY(launch_copy_strided(1, md, acc2, md, ps.acc, md, ctx->stream));
+  }
+  ps.done += n;
+  if (reorth > 0 && (ps.done / reorth) != ((ps.done - n) / reorth)) MG_TRY(reorth_batch(ctx, 1, d, ps.acc, md));
+  return MG_OK;
+}
+
+int begin_prop(mg_ctx* ctx, PropState& ps, const double* in, int flags) {
+  const int d = ps.d;
+  const long long md = mat_doubles(d);
+  const cudaMemcpyKind kind = (flags & MG_FLAG_HOST_PTRS) ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+  if (ps.output == MG_OUT_STATE) {
+    if (!in) return MG_EINVAL;
+    MG_TRY(ws(ctx, WS_ACC, 2 * d, &ps.psi));
+    MG_CUDA_TRY(cudaMemcpyAsync(ps.psi, in, sizeof(double) * 2 * d, kind, ctx->stream));
+  } else {
+    MG_TRY(ws(ctx, WS_ACC, md, &ps.acc));
+    if (in) {
+      MG_CUDA_TRY(cudaMemcpyAsync(ps.acc, in, sizeof(double) * md, kind, ctx->stream));
+      ps.acc_init = true;
+    }
+  }
+  return MG_OK;
+}
+
+int finish_prop(mg_ctx* ctx, Engine& eng, PropState& ps, double* out, int flags, mg_report* rep) {
+  const int d = ps.d;
+  const long long md = mat_doubles(d);
+  const cudaMemcpyKind kind = (flags & MG_FLAG_HOST_PTRS) ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+  if (ps.output == MG_OUT_STATE) {
+    MG_CUDA_TRY(cudaMemcpyAsync(out, ps.psi, sizeof(double) * 2 * d, kind, ctx->stream));
+  } else {
+    if (!ps.acc_init) MG_TRY(launch_identity(1, d, ps.acc, ctx->stream));
+    MG_CUDA_TRY(cudaMemcpyAsync(out, ps.acc, sizeof(double) * md, kind, ctx->stream));
+  }
+  (void)eng;
+  if (rep) {
+    double* sc;
+    MG_TRY(small_scratch(ctx, 2, &sc));
+    if (ps.output == MG_OUT_STATE) {
+      MG_TRY(launch_norm_defect(d, ps.psi, sc, ctx->stream));
+    } else {
+      double* G;
+      MG_TRY(ws(ctx, WS_NS_G, md, &G));
+      AddTerms none;
+      MG_TRY(launch_cgemm_f64(1, d, ps.acc, md, 1, ps.acc, md, G, md, none, ctx->stream));
+      MG_TRY(launch_max_identity_defect(1, d, G, sc, ctx->stream));
+    }
+    MG_CUDA_TRY(cudaMemcpyAsync(&rep->unitarity_defect, sc, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  }
+  return MG_OK;
+}
+
+}  // namespace
+
+int mg_evolve(mg_plan* p, int output, const double* in, double* out, int reorth_every, int flags, mg_report* rep) {
+  if (!p || !out || p->N < 1 || (output != MG_OUT_STATE && output != MG_OUT_PROPAGATOR) || reorth_every < 0)
+    return MG_EINVAL;
+  mg_ctx* ctx = p->ctx;
+  MG_CUDA_TRY(cudaSetDevice(ctx->device));
+  cudaStream_t s = ctx->stream;
+  const int d = p->d;
+  const long long md = mat_doubles(d);
+  if (rep) {
+    memset(rep, 0, sizeof(*rep));
+    MG_CUDA_TRY(cudaEventRecord(ctx->ev0, s));
+  }
+  Engine eng{ctx, d, p->precision, p->L};
+  PropState ps;
+  ps.output = output;
+  ps.d = d;
+  MG_TRY(begin_prop(ctx, ps, in, flags));
+  int align = 1;
+  if (output == MG_OUT_PROPAGATOR && reorth_every > 1) align = reorth_every;
+  const int chunk = chunk_size(ctx, d, p->precision, p->L, p->N, align);
+  ExpmStats st;
+  const int shift = (p->flags & MG_FLAG_NO_TRACE_SHIFT) ? 0 : 1;
+  for (int n0 = 0; n0 < p->N; n0 += chunk) {
+    const int nb = std::min(chunk, p->N - n0);
+    double *W, *tau, *nrm, *sc;
+    MG_TRY(ws(ctx, WS_W, md * nb, &W));
+    MG_TRY(ws(ctx, WS_TAU, nb, &tau));
+    MG_TRY(ws(ctx, WS_NORM, nb, &nrm));
+    MG_TRY(small_scratch(ctx, (size_t)p->K + 1 + nb, &sc));
+    MG_TRY(launch_build_omega(nb, d, p->K, p->dt, p->H0, p->Hk, p->c + (long long)n0 * p->K, W, tau, nrm, shift,
+                              /*write_shifted=*/1, sc, s));
+    double* Ubuf;
+    MG_TRY(ws(ctx, WS_UBUF, md * nb, &Ubuf));
+    MG_TRY(expm_chunk(ctx, eng, nb, W, tau, nrm, Ubuf, md, &st));
+    MG_TRY(fold_chunk(ctx, eng, ps, nb, Ubuf, reorth_every));
+  }
+  MG_TRY(finish_prop(ctx, eng, ps, out, flags, rep));
+  if (rep) {
+    MG_CUDA_TRY(cudaEventRecord(ctx->ev1, s));
+    MG_CUDA_TRY(cudaEventSynchronize(ctx->ev1));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
+    rep->ms_total = ms;
+    rep->intervals = p->N;
+    rep->taylor_degree = st.m;
+    rep->max_squarings = st.s_max;
+    rep->min_squarings = st.s_min == (1 << 30) ? 0 : st.s_min;
+    rep->max_norm1 = st.max_norm;
+    rep->matrix_products = eng.products;
+  }
+  if (p->precision == MG_PREC_SPLIT) return check_status(ctx);
+  if (flags & MG_FLAG_HOST_PTRS) MG_CUDA_TRY(cudaStreamSynchronize(s));
+  return MG_OK;
+}
+
+int mg_propagate(mg_ctx* ctx, int N, int d, const double* U, int output, const double* in, double* out,
+                 int reorth_every, int precision, int slices) {
+  if (!ctx || N < 1 || d < 1 || d > 4096 || !U || !out || reorth_every < 0) return MG_EINVAL;
+  if (output != MG_OUT_STATE && output != MG_OUT_PROPAGATOR) return MG_EINVAL;
+  MG_TRY(validate_prec(precision, slices));
+  MG_CUDA_TRY(cudaSetDevice(ctx->device));
+  Engine eng{ctx, d, precision, slices};
+  PropState ps;
+  ps.output = output;
+  ps.d = d;
+  MG_TRY(begin_prop(ctx, ps, in, 0));
+  const long long md = mat_doubles(d);
+  int align = (output == MG_OUT_PROPAGATOR && reorth_every > 1) ? reorth_every : 1;
+  const int chunk = chunk_size(ctx, d, precision, slices, N, align);
+  for (int n0 = 0; n0 < N; n0 += chunk) {
+    const int nb = std::min(chunk, N - n0);
+    MG_TRY(fold_chunk(ctx, eng, ps, nb, U + (long long)n0 * md, reorth_every));
+  }
+  MG_TRY(finish_prop(ctx, eng, ps, out, 0, nullptr));
+  if (precision == MG_PREC_SPLIT) return check_status(ctx);
+  return MG_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,131 @@
+// Shared definitions of the Magnus library's CUDA translation units.
+//
+// Complex matrices are stored row-major with interleaved (re, im) FP64 pairs:
+// element (i, j) of a d x d matrix lives at doubles [2 (i d + j), 2 (i d + j) + 1].
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstdio>
+
+#include "../../include/magnus.h"
+
+namespace mg {
+
+// ---------------------------------------------------------------------------
+// error plumbing (no C++ exception crosses the C ABI)
+// ---------------------------------------------------------------------------
+#define MG_CUDA_TRY(expr)                                                       \
+  do {                                                                          \
+    cudaError_t _e = (expr);                                                    \
+    if (_e != cudaSuccess) {                                                    \
+      mg::set_last_cuda_error(_e, #expr, __FILE__, __LINE__);                   \
+      return MG_ECUDA;                                                          \
+    }                                                                           \
+  } while (0)
+
+#define MG_TRY(expr)                                                            \
+  do {                                                                          \
+    int _r = (expr);                                                            \
+    if (_r != MG_OK) return _r;                                                 \
+  } while (0)
+
+void set_last_cuda_error(cudaError_t e, const char* what, const char* file, int line);
+void set_last_message(const char* fmt, ...);
+
+// Device-side status word.  Kernels that wait on an mbarrier give up after a
+// bounded number of polls, record MG_DEV_TIMEOUT here and return; the host maps
+// it to MG_ETIMEOUT.  Non-finite norms set MG_DEV_NONFINITE.
+enum : int { MG_DEV_OK = 0, MG_DEV_TIMEOUT = 1, MG_DEV_NONFINITE = 2 };
+
+// ---------------------------------------------------------------------------
+// small device helpers
+// ---------------------------------------------------------------------------
+struct cplx {
+  double re, im;
+};
+
+__host__ __device__ __forceinline__ cplx cmul(cplx a, cplx b) {
+  return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
+}
+__host__ __device__ __forceinline__ cplx cadd(cplx a, cplx b) { return {a.re + b.re, a.im + b.im}; }
+
+inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
+
+// Every kernel launch goes through check_launch(): it counts the launch and
+// converts a launch error into MG_ECUDA with a message.
+int check_launch(const char* name);
+void count_launch();
+
+// ---------------------------------------------------------------------------
+// kernels shared between translation units (launch wrappers)
+// ---------------------------------------------------------------------------
+// c[n][k] = (dt/2) sum_p w[p] samples[n][p][k]
+int launch_coefficients(int N, int P, int K, double dt, const double* w_dev,
+                        const double* samples, double* c, cudaStream_t s);
+
+// omega[n] = dt H0 + sum_k c[n][k] H_k (minus tau_n I when write_shifted), with
+// tau[n] = Re tr/d (0 unless shift) and norm1[n] = ||omega_n - tau_n I||_1.
+// scratch: K + 1 + N doubles of device memory.
+int launch_build_omega(int N, int d, int K, double dt, const double* H0, const double* Hk,
+                       const double* c, double* omega, double* tau, double* norm1, int shift,
+                       int write_shifted, double* scratch, cudaStream_t s);
+
+// tau_b = Re tr(A_b)/d (0 unless shift), dst_b = A_b - tau_b I, norm1_b = ||dst_b||_1
+int launch_shift_norm(int batch, int d, const double* A, double* dst, double* tau, double* norm1,
+                      unsigned long long* bits, int shift, cudaStream_t s);
+
+// out[0] = max|H - H^dag|, out[1] = max|H| over `count` stacked d x d operators (as double bits)
+int launch_hermitian_defect(int d, int count, const double* H, unsigned long long* out, cudaStream_t s);
+
+// X_b = (-i) 2^{-sq_b} src_b, sq from a device int array (sq_dev) or the constant sq
+int launch_scale_minus_i(int batch, int d, const double* src, double* dst, const int* sq_dev,
+                         int sq, cudaStream_t s);
+
+// dst = sum_m coef[m] src_m + diag I over a batch (nsrc <= 4; sources may alias dst)
+int launch_lincomb(int batch, int d, double* dst, int nsrc, const double* const* src,
+                   const double* coef, double diag, cudaStream_t s);
+
+// dst_b = exp(-i phase_b) src_b  (phase from device array)
+int launch_apply_phase(int batch, int d, long long count_per_item, const double* phase,
+                       const double* src, double* dst, cudaStream_t s);
+
+int launch_identity(int batch, int d, double* dst, cudaStream_t s);
+
+// copy a strided batch: dst[b] = src[b * src_stride] (strides in doubles)
+int launch_copy_strided(int batch, long long elems, const double* src, long long src_stride,
+                        double* dst, long long dst_stride, cudaStream_t s);
+
+// FP64 batched complex GEMM: C[b] = scale * opA(A[b]) B[b] + sum_m coef[m] P_m[b] + diag I.
+// opA: 0 = A, 1 = A^dagger.  Batch strides in doubles.
+struct AddTerms {
+  int n = 0;
+  const double* src[3] = {nullptr, nullptr, nullptr};
+  double coef[3] = {0, 0, 0};
+  long long stride = 0;   // batch stride of the addend matrices (doubles)
+  double diag = 0.0;
+  double scale = 1.0;
+};
+int launch_cgemm_f64(int batch, int d, const double* A, long long strideA, int opA,
+                     const double* B, long long strideB, double* C, long long strideC,
+                     const AddTerms& add, cudaStream_t s);
+
+// max-abs reductions used for reports: out = max_b max_ij |U_b^dag U_b - I| computed
+// from G_b = U_b^dag U_b (already formed), or |‖psi‖ - 1|.
+int launch_max_identity_defect(int batch, int d, const double* G, double* out_dev, cudaStream_t s);
+
+// Split-precision (BF16-digit, tcgen05) products; see split_gemm.cu.
+int split_beta_for(int d);
+size_t split_a_bytes(int d, int L, int batch);
+size_t split_b_bytes(int d, int L, int batch);
+int split_slice_a(int d, int L, int batch, const double* A, long long sA, void* buf, cudaStream_t s);
+int split_slice_b(int d, int L, int batch, const double* B, long long sB, void* buf, cudaStream_t s);
+int split_gemm(int d, int L, int batch, const void* abuf, const void* bbuf, double* C, long long sC,
+               const AddTerms& add, int* status, cudaStream_t s);
+
+// State propagation; see propagate.cu.
+int launch_state_chain(int n_steps, int d, const double* U, long long sU, double* psi, double* tmp,
+                       int reorth_every, int step_offset, cudaStream_t s);
+int launch_norm_defect(int d, const double* psi, double* out, cudaStream_t s);
+
+}  // namespace mg

@@ -1,0 +1,151 @@
+// Elementwise and reduction kernels of the exponential and propagation steps
+// (FP64, HBM-bound): scaling X = -i 2^{-s} Hbar, linear combinations of matrix
+// powers for the Taylor polynomial, the exact trace-shift phase e^{-i tau},
+// identities and strided copies, and the FP64 unitarity/norm diagnostics.
+#include "common.cuh"
+
+namespace mg {
+
+// ---------------------------------------------------------------------------
+__global__ void scale_minus_i_kernel(long long per_item, int batch, const double* __restrict__ src,
+                                     double* __restrict__ dst, const int* __restrict__ sq_dev, int sq) {
+  long long total = per_item * batch;  // complex elements
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    int b = (int)(e / per_item);
+    int s = sq_dev ? sq_dev[b] : sq;
+    double f = ldexp(1.0, -s);
+    double2 v = reinterpret_cast<const double2*>(src)[e];
+    // (-i)(a + i b) = b - i a
+    reinterpret_cast<double2*>(dst)[e] = make_double2(f * v.y, -f * v.x);
+  }
+}
+
+static int grid_for(long long n, int threads = 256) {
+  long long g = (n + threads - 1) / threads;
+  if (g > 152 * 32) g = 152 * 32;
+  if (g < 1) g = 1;
+  return (int)g;
+}
+
+int launch_scale_minus_i(int batch, int d, const double* src, double* dst, const int* sq_dev, int sq,
+                         cudaStream_t s) {
+  long long per = (long long)d * d;
+  scale_minus_i_kernel<<<grid_for(per * batch), 256, 0, s>>>(per, batch, src, dst, sq_dev, sq);
+  return check_launch("scale_minus_i_kernel");
+}
+
+// ---------------------------------------------------------------------------
+struct LincombArgs {
+  const double* src[4];
+  double coef[4];
+};
+
+__global__ void lincomb_kernel(int d, int batch, int nsrc, LincombArgs a, double diag,
+                               double* __restrict__ dst) {
+  const long long per = (long long)d * d;
+  const long long total = per * batch;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    double re = 0.0, im = 0.0;
+    for (int m = 0; m < nsrc; ++m) {
+      double2 v = reinterpret_cast<const double2*>(a.src[m])[e];
+      re = fma(a.coef[m], v.x, re);
+      im = fma(a.coef[m], v.y, im);
+    }
+    long long r = e % per;
+    if (r / d == r % d) re += diag;
+    reinterpret_cast<double2*>(dst)[e] = make_double2(re, im);
+  }
+}
+
+int launch_lincomb(int batch, int d, double* dst, int nsrc, const double* const* src, const double* coef,
+                   double diag, cudaStream_t s) {
+  if (nsrc < 0 || nsrc > 4) return MG_EINVAL;
+  LincombArgs a{};
+  for (int m = 0; m < nsrc; ++m) { a.src[m] = src[m]; a.coef[m] = coef[m]; }
+  lincomb_kernel<<<grid_for((long long)d * d * batch), 256, 0, s>>>(d, batch, nsrc, a, diag, dst);
+  return check_launch("lincomb_kernel");
+}
+
+// ---------------------------------------------------------------------------
+__global__ void apply_phase_kernel(long long per_item, int batch, const double* __restrict__ phase,
+                                   const double* __restrict__ src, double* __restrict__ dst) {
+  const long long total = per_item * batch;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    int b = (int)(e / per_item);
+    double sn, cs;
+    sincos(phase[b], &sn, &cs);
+    // e^{-i p} (x + i y) = (c - i s)(x + i y)
+    double2 v = reinterpret_cast<const double2*>(src)[e];
+    reinterpret_cast<double2*>(dst)[e] = make_double2(cs * v.x + sn * v.y, cs * v.y - sn * v.x);
+  }
+}
+
+int launch_apply_phase(int batch, int d, long long count_per_item, const double* phase, const double* src,
+                       double* dst, cudaStream_t s) {
+  (void)d;
+  apply_phase_kernel<<<grid_for(count_per_item * batch), 256, 0, s>>>(count_per_item, batch, phase, src, dst);
+  return check_launch("apply_phase_kernel");
+}
+
+// ---------------------------------------------------------------------------
+__global__ void identity_kernel(int d, int batch, double* __restrict__ dst) {
+  const long long per = (long long)d * d;
+  const long long total = per * batch;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    long long r = e % per;
+    reinterpret_cast<double2*>(dst)[e] = make_double2((r / d == r % d) ? 1.0 : 0.0, 0.0);
+  }
+}
+
+int launch_identity(int batch, int d, double* dst, cudaStream_t s) {
+  identity_kernel<<<grid_for((long long)d * d * batch), 256, 0, s>>>(d, batch, dst);
+  return check_launch("identity_kernel");
+}
+
+__global__ void copy_strided_kernel(int batch, long long elems, const double* __restrict__ src,
+                                    long long ss, double* __restrict__ dst, long long ds) {
+  const long long total = elems * batch;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    long long b = e / elems, r = e % elems;
+    dst[b * ds + r] = src[b * ss + r];
+  }
+}
+
+int launch_copy_strided(int batch, long long elems, const double* src, long long src_stride, double* dst,
+                        long long dst_stride, cudaStream_t s) {
+  copy_strided_kernel<<<grid_for(elems * batch), 256, 0, s>>>(batch, elems, src, src_stride, dst, dst_stride);
+  return check_launch("copy_strided_kernel");
+}
+
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void atomic_max_nonneg(double* addr, double v) {
+  atomicMax(reinterpret_cast<unsigned long long*>(addr), (unsigned long long)__double_as_longlong(v));
+}
+
+__global__ void identity_defect_kernel(int d, int batch, const double* __restrict__ G, double* out) {
+  const long long per = (long long)d * d;
+  const long long total = per * batch;
+  double m = 0.0;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    long long r = e % per;
+    double2 v = reinterpret_cast<const double2*>(G)[e];
+    if (r / d == r % d) v.x -= 1.0;
+    m = fmax(m, hypot(v.x, v.y));
+  }
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomic_max_nonneg(out, m);
+}
+
+int launch_max_identity_defect(int batch, int d, const double* G, double* out_dev, cudaStream_t s) {
+  MG_CUDA_TRY(cudaMemsetAsync(out_dev, 0, sizeof(double), s));
+  identity_defect_kernel<<<grid_for((long long)d * d * batch), 256, 0, s>>>(d, batch, G, out_dev);
+  return check_launch("identity_defect_kernel");
+}
+
+}  // namespace mg

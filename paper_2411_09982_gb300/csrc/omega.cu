@@ -1,0 +1,279 @@
+// Quadrature coefficients and the first-order Magnus term of every interval.
+//
+//   c_{k,n}  = (dt/2) sum_p w_p u^(k)(t_{n,p})        (Eq. magnus-first-order-coeff)
+//   Hbar_n   = dt H0 + sum_k c_{k,n} H_k              (Eq. magnus-first-order-term)
+//
+// The Hbar builder is HBM-bound: it streams the operators once per block of
+// NB intervals (register blocking over intervals) and writes every Hbar_n once.
+// In the same pass it forms the exact trace shift tau_n = Re tr(Hbar_n)/d (from
+// the precomputed operator traces) and the FP64 1-norm ||Hbar_n - tau_n I||_1
+// that selects the squaring count of the exponential.
+#include "common.cuh"
+
+namespace mg {
+
+// ---------------------------------------------------------------------------
+__global__ void coefficients_kernel(int N, int P, int K, double half_dt, const double* __restrict__ w,
+                                    const double* __restrict__ samples, double* __restrict__ c) {
+  long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (idx >= (long long)N * K) return;
+  int n = (int)(idx / K), k = (int)(idx % K);
+  const double* s = samples + (long long)n * P * K + k;
+  double acc = 0.0;
+  for (int p = 0; p < P; ++p) acc = fma(w[p], s[(long long)p * K], acc);
+  c[idx] = half_dt * acc;
+}
+
+int launch_coefficients(int N, int P, int K, double dt, const double* w_dev, const double* samples,
+                        double* c, cudaStream_t s) {
+  if (N <= 0 || K <= 0) return MG_OK;
+  long long total = (long long)N * K;
+  int threads = 256;
+  coefficients_kernel<<<ceil_div(total, threads), threads, 0, s>>>(N, P, K, 0.5 * dt, w_dev, samples, c);
+  return check_launch("coefficients_kernel");
+}
+
+// ---------------------------------------------------------------------------
+// traces: tr[0] = Re tr H0, tr[1 + k] = Re tr H_k
+__global__ void operator_traces_kernel(int d, int K, const double* __restrict__ H0,
+                                       const double* __restrict__ Hk, double* __restrict__ tr) {
+  int k = blockIdx.x;  // 0..K
+  const double* H = (k == 0) ? H0 : Hk + (long long)(k - 1) * d * d * 2;
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < d; i += blockDim.x) acc += H[2 * ((long long)i * d + i)];
+  __shared__ double red[256];
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+    if (threadIdx.x < st) red[threadIdx.x] += red[threadIdx.x + st];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) tr[k] = red[0];
+}
+
+// Ordered encoding of a non-negative double so that unsigned max = double max.
+__device__ __forceinline__ unsigned long long nonneg_bits(double x) {
+  return (unsigned long long)__double_as_longlong(x);
+}
+
+constexpr int OMEGA_NB = 8;      // intervals per CTA (register blocking)
+constexpr int OMEGA_COLS = 32;   // columns per CTA (one per lane)
+constexpr int OMEGA_WARPS = 8;   // row phases per CTA
+
+// grid: (ceil(d/32), ceil(N/NB)); block 256 = 8 warps x 32 lanes.
+// lane -> column j, warp -> rows i = warp, warp + 8, ...
+__global__ void __launch_bounds__(256)
+build_omega_kernel(int N, int d, int K, double dt, const double* __restrict__ H0,
+                   const double* __restrict__ Hk, const double* __restrict__ c,
+                   const double* __restrict__ tr, double* __restrict__ omega,
+                   double* __restrict__ tau_out, unsigned long long* __restrict__ norm_bits,
+                   int shift, int write_shifted) {
+  extern __shared__ double sm[];
+  double* cs = sm;                              // [NB][K]
+  double* taus = cs + OMEGA_NB * (K > 0 ? K : 1);   // [NB]
+  double* colpart = taus + OMEGA_NB;            // [WARPS][NB][32]
+
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int j = blockIdx.x * OMEGA_COLS + lane;
+  const int n0 = blockIdx.y * OMEGA_NB;
+  const int nb = min(OMEGA_NB, N - n0);
+
+  for (int t = threadIdx.x; t < OMEGA_NB * K; t += blockDim.x) {
+    int b = t / K, k = t % K;
+    cs[t] = (b < nb) ? c[(long long)(n0 + b) * K + k] : 0.0;
+  }
+  __syncthreads();
+  if (threadIdx.x < OMEGA_NB) {
+    int b = threadIdx.x;
+    double t = 0.0;
+    if (shift && b < nb) {
+      t = dt * tr[0];
+      for (int k = 0; k < K; ++k) t += cs[b * K + k] * tr[1 + k];
+      t /= d;
+    }
+    taus[b] = t;
+    if (b < nb && blockIdx.x == 0 && tau_out) tau_out[n0 + b] = t;
+  }
+  __syncthreads();
+
+  double colsum[OMEGA_NB];
+#pragma unroll
+  for (int b = 0; b < OMEGA_NB; ++b) colsum[b] = 0.0;
+
+  if (j < d) {
+    const long long dd2 = (long long)d * d * 2;
+    for (int i = warp; i < d; i += OMEGA_WARPS) {
+      const long long off = 2 * ((long long)i * d + j);
+      const double2 h0 = *reinterpret_cast<const double2*>(H0 + off);
+      double re[OMEGA_NB], im[OMEGA_NB];
+#pragma unroll
+      for (int b = 0; b < OMEGA_NB; ++b) { re[b] = dt * h0.x; im[b] = dt * h0.y; }
+      for (int k = 0; k < K; ++k) {
+        const double2 hk = *reinterpret_cast<const double2*>(Hk + k * dd2 + off);
+#pragma unroll
+        for (int b = 0; b < OMEGA_NB; ++b) {
+          const double ck = cs[b * K + k];
+          re[b] = fma(ck, hk.x, re[b]);
+          im[b] = fma(ck, hk.y, im[b]);
+        }
+      }
+#pragma unroll
+      for (int b = 0; b < OMEGA_NB; ++b) {
+        if (b < nb) {
+          double r = re[b];
+          if (i == j) r -= taus[b];
+          colsum[b] += hypot(r, im[b]);
+          double2 o;
+          o.x = write_shifted ? r : re[b];
+          o.y = im[b];
+          *reinterpret_cast<double2*>(omega + (long long)(n0 + b) * dd2 + off) = o;
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int b = 0; b < OMEGA_NB; ++b) colpart[(warp * OMEGA_NB + b) * 32 + lane] = colsum[b];
+  __syncthreads();
+  // reduce over warps (rows) then max over lanes (columns)
+  if (warp < OMEGA_NB && warp < nb) {
+    const int b = warp;
+    double s = 0.0;
+    for (int w = 0; w < OMEGA_WARPS; ++w) s += colpart[(w * OMEGA_NB + b) * 32 + lane];
+    if (j >= d) s = 0.0;
+    for (int o = 16; o > 0; o >>= 1) s = fmax(s, __shfl_xor_sync(0xffffffffu, s, o));
+    if (lane == 0) {
+      if (!(s <= 1.0e300)) s = __longlong_as_double(0x7ff0000000000000LL);  // NaN/Inf -> +Inf
+      atomicMax(norm_bits + n0 + b, nonneg_bits(s));
+    }
+  }
+}
+
+__global__ void bits_to_double_kernel(int n, const unsigned long long* bits, double* out) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = __longlong_as_double((long long)bits[i]);
+}
+
+int launch_build_omega(int N, int d, int K, double dt, const double* H0, const double* Hk,
+                       const double* c, double* omega, double* tau, double* norm1, int shift,
+                       int write_shifted, double* scratch, cudaStream_t s) {
+  // scratch: (K+1) traces + N norm words
+  if (N <= 0) return MG_OK;
+  double* tr = scratch;
+  unsigned long long* bits = reinterpret_cast<unsigned long long*>(scratch + (K + 1));
+  operator_traces_kernel<<<K + 1, 256, 0, s>>>(d, K, H0, Hk, tr);
+  MG_TRY(check_launch("operator_traces_kernel"));
+  MG_CUDA_TRY(cudaMemsetAsync(bits, 0, sizeof(unsigned long long) * N, s));
+  dim3 grid(ceil_div(d, OMEGA_COLS), ceil_div(N, OMEGA_NB));
+  size_t smem = sizeof(double) * (OMEGA_NB * (K > 0 ? K : 1) + OMEGA_NB + OMEGA_WARPS * OMEGA_NB * 32);
+  if (smem > 48 * 1024) {
+    MG_CUDA_TRY(cudaFuncSetAttribute(build_omega_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem));
+  }
+  build_omega_kernel<<<grid, 256, smem, s>>>(N, d, K, dt, H0, Hk, c, tr, omega, tau, bits, shift,
+                                            write_shifted);
+  MG_TRY(check_launch("build_omega_kernel"));
+  if (norm1) {
+    bits_to_double_kernel<<<ceil_div(N, 256), 256, 0, s>>>(N, bits, norm1);
+    MG_TRY(check_launch("bits_to_double_kernel"));
+  }
+  return MG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// General Hermitian input (mg_expm): tau_b = Re tr(A_b)/d, dst = A_b - tau_b I,
+// norm1_b = ||dst||_1.  grid (ceil(d/32), batch), block 256.
+__global__ void __launch_bounds__(256)
+shift_norm_kernel(int d, const double* __restrict__ A, double* __restrict__ dst,
+                  const double* __restrict__ tau, unsigned long long* __restrict__ norm_bits) {
+  __shared__ double part[8][32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int j = blockIdx.x * 32 + lane;
+  const long long base = (long long)blockIdx.y * d * d * 2;
+  const double t = tau[blockIdx.y];
+  double s = 0.0;
+  if (j < d) {
+    for (int i = warp; i < d; i += 8) {
+      long long off = base + 2 * ((long long)i * d + j);
+      double2 v = *reinterpret_cast<const double2*>(A + off);
+      if (i == j) v.x -= t;
+      s += hypot(v.x, v.y);
+      *reinterpret_cast<double2*>(dst + off) = v;
+    }
+  }
+  part[warp][lane] = s;
+  __syncthreads();
+  if (warp == 0) {
+    double v = 0.0;
+    for (int w = 0; w < 8; ++w) v += part[w][lane];
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if (lane == 0) {
+      if (!(v <= 1.0e300)) v = __longlong_as_double(0x7ff0000000000000LL);
+      atomicMax(norm_bits + blockIdx.y, nonneg_bits(v));
+    }
+  }
+}
+
+__global__ void batch_trace_kernel(int d, const double* __restrict__ A, double* __restrict__ tau) {
+  const long long base = (long long)blockIdx.x * d * d * 2;
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < d; i += blockDim.x) acc += A[base + 2 * ((long long)i * d + i)];
+  __shared__ double red[256];
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+    if (threadIdx.x < st) red[threadIdx.x] += red[threadIdx.x + st];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) tau[blockIdx.x] = red[0] / d;
+}
+
+int launch_shift_norm(int batch, int d, const double* A, double* dst, double* tau, double* norm1,
+                      unsigned long long* bits, int shift, cudaStream_t s) {
+  if (shift) {
+    batch_trace_kernel<<<batch, 256, 0, s>>>(d, A, tau);
+    MG_TRY(check_launch("batch_trace_kernel"));
+  } else {
+    MG_CUDA_TRY(cudaMemsetAsync(tau, 0, sizeof(double) * batch, s));
+  }
+  MG_CUDA_TRY(cudaMemsetAsync(bits, 0, sizeof(unsigned long long) * batch, s));
+  shift_norm_kernel<<<dim3(ceil_div(d, 32), batch), 256, 0, s>>>(d, A, dst, tau, bits);
+  MG_TRY(check_launch("shift_norm_kernel"));
+  bits_to_double_kernel<<<ceil_div(batch, 256), 256, 0, s>>>(batch, bits, norm1);
+  return check_launch("bits_to_double_kernel");
+}
+
+// ---------------------------------------------------------------------------
+// Hermiticity check of a stack of operators: out[0] = max |H - H^dag|, out[1] = max |H|
+__global__ void hermitian_defect_kernel(int d, int count, const double* __restrict__ H,
+                                        unsigned long long* __restrict__ out) {
+  long long total = (long long)count * d * d;
+  double dmax = 0.0, hmax = 0.0;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    long long m = e / ((long long)d * d);
+    long long r = e % ((long long)d * d);
+    int i = (int)(r / d), j = (int)(r % d);
+    const double* M = H + m * d * d * 2;
+    double ar = M[2 * ((long long)i * d + j)], ai = M[2 * ((long long)i * d + j) + 1];
+    double br = M[2 * ((long long)j * d + i)], bi = -M[2 * ((long long)j * d + i) + 1];
+    dmax = fmax(dmax, hypot(ar - br, ai - bi));
+    hmax = fmax(hmax, hypot(ar, ai));
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+    hmax = fmax(hmax, __shfl_xor_sync(0xffffffffu, hmax, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicMax(out, nonneg_bits(dmax));
+    atomicMax(out + 1, nonneg_bits(hmax));
+  }
+}
+
+int launch_hermitian_defect(int d, int count, const double* H, unsigned long long* out, cudaStream_t s) {
+  MG_CUDA_TRY(cudaMemsetAsync(out, 0, 2 * sizeof(unsigned long long), s));
+  if (count <= 0) return MG_OK;
+  hermitian_defect_kernel<<<304, 256, 0, s>>>(d, count, H, out);
+  return check_launch("hermitian_defect_kernel");
+}
+
+}  // namespace mg

@@ -1,0 +1,643 @@
+// Split-precision complex matrix product on the tcgen05 tensor cores.
+//
+// Every matrix product of the exponential (Taylor powers, Horner steps,
+// squarings) and of the propagator product is a complex d x d GEMM
+// C = A B.  In MG_PREC_SPLIT mode it runs as a real GEMM on BF16 digits:
+//
+//   * complex -> real:   [Cr | Ci] = [Ar | Ai] * [[Br, Bi], [-Bi, Br]]
+//     (M = d, N = 2d, K = 2d; 8 d^3 real flops, the "4M" form).
+//   * digits:  each FP64 row i of [Ar | Ai] is scaled by 2^{-(E_i+1)} so that
+//     it lies in (-1/2, 1/2) and cut into `L` signed digits of `beta` bits,
+//     a = 2^{E_i+1-beta} sum_s v_s with v_s = q_s 2^{-beta s}, |q_s| <= 2^{beta-1};
+//     every v_s is exact in BF16.  Columns of B are cut the same way.
+//   * products: digit products v_s^A v_t^B with s + t <= L - 1 are accumulated
+//     in three FP32 TMEM accumulators by level s + t = 0, 1, >= 2.  beta is
+//     chosen so that 2^{2 beta - 1} * 2d <= 2^24: the level-0 and level-1 sums are
+//     then integers (in units of 1 and 2^-beta) below 2^24 and accumulate
+//     exactly; only the small level->=2 part is rounded.
+//   * epilogue: C_ij = 2^{(E_i+1-beta)+(F_j+1-beta)} (g0 + g1 + g2) in FP64, plus
+//     optional FP64 addends (Taylor/Horner terms) and a diagonal.
+//
+// The error of one product is about 2^{-beta L} relative to max|A| max|B|, so
+// L = 5..6 gives a far smaller per-product error than FP32 arithmetic and
+// L = 7..8 approaches FP64.  This is the tensor-core replacement of the FP64
+// products of the exponential; everything else of the path stays FP64.
+//
+// Kernel structure (one 128 x 64-complex output tile per CTA, 192 threads):
+//   warp 0      TMA producer: per K-step of 16 one 4-D box of all L A-digit
+//               tiles (128 x 16 BF16 each) and one of all L B-digit tiles,
+//               SWIZZLE_32B, into a STAGES-deep ring of shared-memory stages.
+//   warp 1      TMEM owner and MMA issuer: tcgen05.mma kind::f16 (BF16 in,
+//               FP32 accumulate), M = 128, N = 128 (64 real + 64 imaginary
+//               output columns), K = 16, one instruction per digit pair.
+//   warps 2..5  epilogue: tcgen05.ld of the three accumulators, FP64 combine.
+// Every mbarrier wait is bounded by a wall-clock deadline; a wait that gives up
+// records MG_DEV_TIMEOUT in the status word and the CTA winds down.
+#include "common.cuh"
+
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+
+#include <mutex>
+
+namespace mg {
+
+// ---------------------------------------------------------------------------
+// host-side geometry
+// ---------------------------------------------------------------------------
+constexpr int SG_BM = 128;      // output rows per tile
+constexpr int SG_BNC = 64;      // complex output columns per tile (N = 128 real)
+constexpr int SG_BK = 16;       // K per stage (32 bytes of BF16: one SW32 atom)
+constexpr int SG_TILE_BYTES = SG_BM * SG_BK * 2;   // 4096 bytes per digit tile
+
+struct SplitGeom {
+  int d, L, beta;
+  int Kp;      // padded 2d (multiple of 16)
+  int Mp;      // padded d rows (multiple of 128)
+  int Np;      // padded B rows: 128 per 64 complex columns
+  long long a_item_elems() const { return (long long)L * Mp * Kp; }   // BF16 elements
+  long long b_item_elems() const { return (long long)L * Np * Kp; }
+};
+
+int split_beta_for(int d) {
+  // largest beta <= 8 with 2^{2 beta - 1} * 2d <= 2^24
+  for (int beta = 8; beta >= 2; --beta) {
+    double lhs = std::ldexp(1.0, 2 * beta - 1) * 2.0 * d;
+    if (lhs <= 16777216.0) return beta;
+  }
+  return 2;
+}
+
+SplitGeom split_geom(int d, int L) {
+  SplitGeom g;
+  g.d = d;
+  g.L = L;
+  g.beta = split_beta_for(d);
+  g.Kp = ceil_div(2 * d, SG_BK) * SG_BK;
+  g.Mp = ceil_div(d, SG_BM) * SG_BM;
+  g.Np = ceil_div(d, SG_BNC) * 2 * SG_BNC;
+  return g;
+}
+
+// ---------------------------------------------------------------------------
+// digit extraction (shared by the A and B slicers)
+// ---------------------------------------------------------------------------
+// x in (-1/2, 1/2): x = sum_{s<L} q_s 2^{-beta (s+1)} + r; writes v_s = q_s 2^{-beta s}.
+template <int L>
+__device__ __forceinline__ void make_digits(double x, int beta, __nv_bfloat16 (&v)[L]) {
+  const double up = ldexp(1.0, beta);
+#pragma unroll
+  for (int s = 0; s < L; ++s) {
+    double y = x * up;
+    double q = rint(y);
+    x = y - q;
+    v[s] = __float2bfloat16_rn((float)ldexp(q, -beta * s));
+  }
+}
+
+__device__ __forceinline__ int row_exponent(double m) {
+  // smallest E with m < 2^E (m > 0); 0 for m == 0
+  if (!(m > 0.0)) return 0;
+  int e;
+  frexp(m, &e);
+  return e;
+}
+
+// A digits: rows of [Re A | Im A].  grid (ceil(Mp/8), batch), block 256 (one warp per row).
+template <int L>
+__global__ void __launch_bounds__(256)
+slice_a_kernel(int d, int Kp, int Mp, int beta, const double* __restrict__ A, long long sA,
+               __nv_bfloat16* __restrict__ out, int* __restrict__ ea) {
+  const int lane = threadIdx.x & 31;
+  const int row = blockIdx.x * 8 + (threadIdx.x >> 5);
+  const int b = blockIdx.y;
+  if (row >= Mp) return;
+  const long long slice_stride = (long long)Mp * Kp;
+  __nv_bfloat16* o = out + (long long)b * L * slice_stride + (long long)row * Kp;
+  const __nv_bfloat16 zero = __float2bfloat16_rn(0.0f);
+  if (row >= d) {
+    for (int k = lane; k < Kp; k += 32)
+#pragma unroll
+      for (int s = 0; s < L; ++s) o[s * slice_stride + k] = zero;
+    return;
+  }
+  const double2* a = reinterpret_cast<const double2*>(A + b * sA) + (long long)row * d;
+  double m = 0.0;
+  for (int k = lane; k < d; k += 32) {
+    double2 v = a[k];
+    m = fmax(m, fmax(fabs(v.x), fabs(v.y)));
+  }
+  for (int o2 = 16; o2 > 0; o2 >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o2));
+  const int E = row_exponent(m);
+  if (lane == 0) ea[(long long)b * Mp + row] = E;
+  const double sc = ldexp(1.0, -(E + 1));
+  for (int k = lane; k < d; k += 32) {
+    double2 v = a[k];
+    __nv_bfloat16 dr[L], di[L];
+    make_digits<L>(v.x * sc, beta, dr);
+    make_digits<L>(v.y * sc, beta, di);
+#pragma unroll
+    for (int s = 0; s < L; ++s) {
+      o[s * slice_stride + k] = dr[s];
+      o[s * slice_stride + d + k] = di[s];
+    }
+  }
+  for (int k = 2 * d + lane; k < Kp; k += 32)
+#pragma unroll
+    for (int s = 0; s < L; ++s) o[s * slice_stride + k] = zero;
+}
+
+// B digits: K-major rows of [[Br, Bi], [-Bi, Br]]^T, tile-interleaved: for the
+// 64 complex columns of tile t, rows 128t + r hold [Re B[:, j] | -Im B[:, j]] and
+// rows 128t + 64 + r hold [Im B[:, j] | Re B[:, j]] (j = 64t + r).
+// grid (ceil(d/64), batch), block 256.
+constexpr int SB_KCHUNK = 32;
+template <int L>
+__global__ void __launch_bounds__(256)
+slice_b_kernel(int d, int Kp, int Np, int beta, const double* __restrict__ B, long long sB,
+               __nv_bfloat16* __restrict__ out, int* __restrict__ eb) {
+  __shared__ double2 tile[SB_KCHUNK][SG_BNC + 1];
+  __shared__ double red[4][SG_BNC];
+  __shared__ double scale[SG_BNC];
+  const int t = blockIdx.x, b = blockIdx.y;
+  const int j0 = t * SG_BNC;
+  const int tid = threadIdx.x;
+  const double2* Bb = reinterpret_cast<const double2*>(B + b * sB);
+  const long long slice_stride = (long long)Np * Kp;
+  __nv_bfloat16* ob = out + (long long)b * L * slice_stride;
+
+  // pass 1: column maxima
+  {
+    const int c = tid & 63, g = tid >> 6;
+    double m = 0.0;
+    if (j0 + c < d)
+      for (int k = g; k < d; k += 4) {
+        double2 v = Bb[(long long)k * d + j0 + c];
+        m = fmax(m, fmax(fabs(v.x), fabs(v.y)));
+      }
+    red[g][c] = m;
+    __syncthreads();
+    if (tid < SG_BNC) {
+      double mm = fmax(fmax(red[0][tid], red[1][tid]), fmax(red[2][tid], red[3][tid]));
+      int E = row_exponent(mm);
+      scale[tid] = ldexp(1.0, -(E + 1));
+      if (j0 + tid < d) eb[(long long)b * (Np / 2) + j0 + tid] = E;
+    }
+    __syncthreads();
+  }
+  const __nv_bfloat16 zero = __float2bfloat16_rn(0.0f);
+  // pass 2: digits, K-chunks staged through shared memory
+  for (int k0 = 0; k0 < d; k0 += SB_KCHUNK) {
+    for (int e = tid; e < SB_KCHUNK * SG_BNC; e += 256) {
+      int kk = e / SG_BNC, c = e % SG_BNC;
+      double2 v = make_double2(0.0, 0.0);
+      if (k0 + kk < d && j0 + c < d) v = Bb[(long long)(k0 + kk) * d + j0 + c];
+      tile[kk][c] = v;
+    }
+    __syncthreads();
+    for (int e = tid; e < SB_KCHUNK * SG_BNC; e += 256) {
+      int kk = e % SB_KCHUNK, r = e / SB_KCHUNK;
+      int k = k0 + kk;
+      if (k >= d) continue;
+      double2 v = tile[kk][r];
+      __nv_bfloat16 dr[L], di[L];
+      make_digits<L>(v.x * scale[r], beta, dr);
+      make_digits<L>(v.y * scale[r], beta, di);
+      __nv_bfloat16* row_re = ob + (long long)(t * 2 * SG_BNC + r) * Kp;          // [Re | -Im]
+      __nv_bfloat16* row_im = ob + (long long)(t * 2 * SG_BNC + SG_BNC + r) * Kp; // [Im | Re]
+#pragma unroll
+      for (int s = 0; s < L; ++s) {
+        long long so = s * slice_stride;
+        row_re[so + k] = dr[s];
+        row_re[so + d + k] = __hneg(di[s]);
+        row_im[so + k] = di[s];
+        row_im[so + d + k] = dr[s];
+      }
+    }
+    __syncthreads();
+  }
+  // zero the K tail of every row of this tile (and whole rows beyond d)
+  for (int e = tid; e < 2 * SG_BNC * (Kp - 2 * d); e += 256) {
+    int rr = e / (Kp - 2 * d), k = 2 * d + e % (Kp - 2 * d);
+#pragma unroll
+    for (int s = 0; s < L; ++s) ob[s * slice_stride + (long long)(t * 2 * SG_BNC + rr) * Kp + k] = zero;
+  }
+  const int live = min(SG_BNC, d - j0);
+  if (live < SG_BNC) {
+    for (int e = tid; e < (SG_BNC - live) * 2 * d; e += 256) {
+      int rr = live + e / (2 * d), k = e % (2 * d);
+#pragma unroll
+      for (int s = 0; s < L; ++s) {
+        ob[s * slice_stride + (long long)(t * 2 * SG_BNC + rr) * Kp + k] = zero;
+        ob[s * slice_stride + (long long)(t * 2 * SG_BNC + SG_BNC + rr) * Kp + k] = zero;
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// PTX wrappers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Poll until the phase of `parity` completes or the deadline passes.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint64_t deadline) {
+  while (!mbar_try_wait(bar, parity)) {
+    if (global_ns() > deadline) return false;
+  }
+  return true;
+}
+__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, uint64_t* bar, int c0, int c1,
+                                            int c2, int c3) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                            uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+__device__ __forceinline__ void tc_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// Shared-memory matrix descriptor: K-major operand tile, 32-byte swizzle,
+// 8-row core groups 256 bytes apart (rows are 32 bytes), descriptor version 1.
+__device__ __forceinline__ uint64_t sw32_kmajor_desc(uint32_t saddr) {
+  uint64_t desc = 0;
+  desc |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  desc |= (uint64_t)1 << 16;            // leading-dimension offset (unused with swizzle)
+  desc |= (uint64_t)(256 >> 4) << 32;   // stride-dimension offset
+  desc |= (uint64_t)1 << 46;            // descriptor version
+  desc |= (uint64_t)6 << 61;            // SWIZZLE_32B
+  return desc;
+}
+
+// Instruction descriptor: kind::f16, A = B = BF16, D = F32, both K-major, M = 128, N = 128.
+constexpr uint32_t kIdescBf16 = (1u << 4) | (1u << 7) | (1u << 10) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
+
+constexpr int SG_THREADS = 192;
+constexpr uint64_t SG_WAIT_NS = 4000000000ull;   // 4 s: far beyond any legitimate wait
+
+struct SplitEpi {
+  const double* add_src[3];
+  double add_coef[3];
+  long long add_stride;
+  int add_n;
+  double diag;
+  double scale;
+};
+
+template <int L, int STAGES>
+__global__ void __launch_bounds__(SG_THREADS, 1)
+split_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                  int d, int Kp, int Mp, int Np, int beta, const int* __restrict__ ea,
+                  const int* __restrict__ eb, double* __restrict__ C, long long sC, SplitEpi epi,
+                  int* __restrict__ status) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* smem = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  constexpr int STAGE_BYTES = 2 * L * SG_TILE_BYTES;
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
+  uint64_t* empty = full + STAGES;
+  uint64_t* accfull = empty + STAGES;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accfull + 1);
+  int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nt = blockIdx.x, mt = blockIdx.y, b = blockIdx.z;
+  const int num_k = Kp / SG_BK;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(accfull, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(512)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const uint64_t deadline = global_ns() + SG_WAIT_NS;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---------------- TMA producer ----------------
+      int issued = 0;
+      for (int kb = 0; kb < num_k; ++kb) {
+        const int s = kb % STAGES;
+        const uint32_t ph = (kb / STAGES) & 1;
+        if (!mbar_wait(&empty[s], ph ^ 1, deadline)) {
+          atomicExch(status, MG_DEV_TIMEOUT);
+          *(volatile int*)abort_flag = 1;
+          break;
+        }
+        unsigned char* st = smem + s * STAGE_BYTES;
+        mbar_expect_tx(&full[s], STAGE_BYTES);
+        tma_load_4d(st, &tmA, &full[s], kb * SG_BK, mt * SG_BM, 0, b);
+        tma_load_4d(st + L * SG_TILE_BYTES, &tmB, &full[s], kb * SG_BK, nt * 2 * SG_BNC, 0, b);
+        issued = kb + 1;
+      }
+      // never leave the CTA with a bulk copy still in flight into its shared memory
+      const uint64_t drain_deadline = global_ns() + SG_WAIT_NS;
+      for (int kb = issued > STAGES ? issued - STAGES : 0; kb < issued; ++kb)
+        mbar_wait(&full[kb % STAGES], (kb / STAGES) & 1, drain_deadline);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ---------------- MMA issuer ----------------
+      bool ok = true;
+      for (int kb = 0; kb < num_k && ok; ++kb) {
+        const int s = kb % STAGES;
+        const uint32_t ph = (kb / STAGES) & 1;
+        if (!mbar_wait(&full[s], ph, deadline)) {
+          atomicExch(status, MG_DEV_TIMEOUT);
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t a0 = smem_u32(smem + s * STAGE_BYTES);
+        const uint32_t b0 = a0 + L * SG_TILE_BYTES;
+        bool first[3] = {kb == 0, kb == 0, kb == 0};
+#pragma unroll
+        for (int sa = 0; sa < L; ++sa) {
+#pragma unroll
+          for (int sb = 0; sb < L - sa; ++sb) {
+            const int g = (sa + sb) < 2 ? (sa + sb) : 2;
+            const uint32_t acc = first[g] ? 0u : 1u;
+            first[g] = false;
+            tc_mma_bf16(tmem + g * 128, sw32_kmajor_desc(a0 + sa * SG_TILE_BYTES),
+                        sw32_kmajor_desc(b0 + sb * SG_TILE_BYTES), kIdescBf16, acc);
+          }
+        }
+        tc_commit(&empty[s]);
+      }
+      tc_commit(accfull);   // fires once every issued MMA has completed
+      if (!ok) *(volatile int*)abort_flag = 1;
+    }
+  } else {
+    // ---------------- epilogue (warps 2..5) ----------------
+    const int q = warp & 3;                   // TMEM lane quarter this warp may access
+    // one lane polls, the warp follows its verdict (tcgen05.ld is warp-collective)
+    int got_i = 0;
+    if (lane == 0) got_i = mbar_wait(accfull, 0, deadline) ? 1 : 0;
+    const bool got = __shfl_sync(0xffffffffu, got_i, 0) != 0;
+    tc_fence_after();
+    if (!got) {
+      if (lane == 0) atomicExch(status, MG_DEV_TIMEOUT);
+    } else if (*(volatile int*)abort_flag == 0) {
+      const int row = mt * SG_BM + q * 32 + lane;
+      const bool row_ok = row < d;
+      const int Ea = row_ok ? ea[(long long)b * Mp + row] : 0;
+      const double* addp[3];
+#pragma unroll
+      for (int m = 0; m < 3; ++m) addp[m] = epi.add_src[m] ? epi.add_src[m] + b * epi.add_stride : nullptr;
+      double2* Cb = reinterpret_cast<double2*>(C + b * sC);
+      const uint32_t lane_base = tmem + ((uint32_t)(q * 32) << 16);
+      for (int jc = 0; jc < SG_BNC; jc += 16) {
+        uint32_t r0[16], r1[16], r2[16], i0[16], i1[16], i2[16];
+        tmem_ld16(lane_base + 0 * 128 + jc, r0);
+        tmem_ld16(lane_base + 1 * 128 + jc, r1);
+        tmem_ld16(lane_base + 2 * 128 + jc, r2);
+        tmem_ld16(lane_base + 0 * 128 + SG_BNC + jc, i0);
+        tmem_ld16(lane_base + 1 * 128 + SG_BNC + jc, i1);
+        tmem_ld16(lane_base + 2 * 128 + SG_BNC + jc, i2);
+        tmem_wait_ld();
+        if (row_ok) {
+#pragma unroll
+          for (int jj = 0; jj < 16; ++jj) {
+            const int j = nt * SG_BNC + jc + jj;
+            if (j < d) {
+              const int Eb = eb[(long long)b * (Np / 2) + j];
+              const double f = ldexp(1.0, Ea + Eb + 2 - 2 * beta);
+              double re = ((double)__uint_as_float(r0[jj]) + (double)__uint_as_float(r1[jj])) +
+                          (double)__uint_as_float(r2[jj]);
+              double im = ((double)__uint_as_float(i0[jj]) + (double)__uint_as_float(i1[jj])) +
+                          (double)__uint_as_float(i2[jj]);
+              re *= f * epi.scale;
+              im *= f * epi.scale;
+              const long long off = (long long)row * d + j;
+              for (int m = 0; m < epi.add_n; ++m) {
+                double2 p = reinterpret_cast<const double2*>(addp[m])[off];
+                re = fma(epi.add_coef[m], p.x, re);
+                im = fma(epi.add_coef[m], p.y, im);
+              }
+              if (row == j) re += epi.diag;
+              Cb[off] = make_double2(re, im);
+            }
+          }
+        }
+      }
+    }
+    tc_fence_before();
+  }
+  __syncthreads();
+  if (warp == 1) {
+    __syncwarp();
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512) : "memory");
+  }
+}
+
+// ---------------------------------------------------------------------------
+// host side: tensor maps, launches, workspace
+// ---------------------------------------------------------------------------
+static PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+static std::once_flag g_encode_once;
+
+static int get_encoder() {
+  std::call_once(g_encode_once, [] {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  });
+  if (!g_encode) {
+    set_last_message("cuTensorMapEncodeTiled is not available from the CUDA driver");
+    return MG_ECUDA;
+  }
+  return MG_OK;
+}
+
+// 4-D map over digit tiles: (k, row, slice, batch), box (16, 128, L, 1), SWIZZLE_32B.
+static int make_digit_map(CUtensorMap* map, const void* base, int Kp, int rows, int L, int batch) {
+  MG_TRY(get_encoder());
+  cuuint64_t dims[4] = {(cuuint64_t)Kp, (cuuint64_t)rows, (cuuint64_t)L, (cuuint64_t)batch};
+  cuuint64_t strides[3] = {(cuuint64_t)Kp * 2, (cuuint64_t)rows * Kp * 2, (cuuint64_t)L * rows * Kp * 2};
+  cuuint32_t box[4] = {(cuuint32_t)SG_BK, (cuuint32_t)SG_BM, (cuuint32_t)L, 1};
+  cuuint32_t estr[4] = {1, 1, 1, 1};
+  CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(base), dims, strides, box,
+                        estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    set_last_message("cuTensorMapEncodeTiled failed (%d): Kp=%d rows=%d L=%d batch=%d", (int)r, Kp, rows, L,
+                     batch);
+    return MG_ECUDA;
+  }
+  return MG_OK;
+}
+
+template <int L>
+static constexpr int stages_for() {
+  return (196608 / (2 * L * SG_TILE_BYTES)) > 8 ? 8 : (196608 / (2 * L * SG_TILE_BYTES));
+}
+
+template <int L>
+static int launch_split_gemm_L(const SplitGeom& g, int batch, const __nv_bfloat16* Ad, const int* ea,
+                               const __nv_bfloat16* Bd, const int* eb, double* C, long long sC,
+                               const SplitEpi& epi, int* status, cudaStream_t s) {
+  constexpr int STAGES = stages_for<L>();
+  CUtensorMap ma, mb;
+  MG_TRY(make_digit_map(&ma, Ad, g.Kp, g.Mp, L, batch));
+  MG_TRY(make_digit_map(&mb, Bd, g.Kp, g.Np, L, batch));
+  const size_t smem = (size_t)STAGES * 2 * L * SG_TILE_BYTES + 1024 /*barriers*/ + 1024 /*align*/;
+  auto kern = split_gemm_kernel<L, STAGES>;
+  MG_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  dim3 grid(ceil_div(g.d, SG_BNC), g.Mp / SG_BM, batch);
+  kern<<<grid, SG_THREADS, smem, s>>>(ma, mb, g.d, g.Kp, g.Mp, g.Np, g.beta, ea, eb, C, sC, epi, status);
+  return check_launch("split_gemm_kernel");
+}
+
+template <int L>
+static int launch_slicers_L(const SplitGeom& g, int batch, const double* A, long long sA, __nv_bfloat16* Ad,
+                            int* ea, const double* B, long long sB, __nv_bfloat16* Bd, int* eb,
+                            cudaStream_t s) {
+  if (A) {
+    slice_a_kernel<L><<<dim3(g.Mp / 8, batch), 256, 0, s>>>(g.d, g.Kp, g.Mp, g.beta, A, sA, Ad, ea);
+    MG_TRY(check_launch("slice_a_kernel"));
+  }
+  if (B) {
+    slice_b_kernel<L><<<dim3(ceil_div(g.d, SG_BNC), batch), 256, 0, s>>>(g.d, g.Kp, g.Np, g.beta, B, sB, Bd, eb);
+    MG_TRY(check_launch("slice_b_kernel"));
+  }
+  return MG_OK;
+}
+
+// Public-to-the-library entry points ------------------------------------------
+
+size_t split_a_bytes(int d, int L, int batch) {
+  SplitGeom g = split_geom(d, L);
+  return (size_t)g.a_item_elems() * 2 * batch + (size_t)g.Mp * 4 * batch;
+}
+size_t split_b_bytes(int d, int L, int batch) {
+  SplitGeom g = split_geom(d, L);
+  return (size_t)g.b_item_elems() * 2 * batch + (size_t)(g.Np / 2) * 4 * batch;
+}
+
+// A-side digits of a batch: layout [digits | exponents] in one buffer.
+int split_slice_a(int d, int L, int batch, const double* A, long long sA, void* buf, cudaStream_t s) {
+  SplitGeom g = split_geom(d, L);
+  __nv_bfloat16* Ad = reinterpret_cast<__nv_bfloat16*>(buf);
+  int* ea = reinterpret_cast<int*>(Ad + g.a_item_elems() * batch);
+  switch (L) {
+    case 2: return launch_slicers_L<2>(g, batch, A, sA, Ad, ea, nullptr, 0, nullptr, nullptr, s);
+    case 3: return launch_slicers_L<3>(g, batch, A, sA, Ad, ea, nullptr, 0, nullptr, nullptr, s);
+    case 4: return launch_slicers_L<4>(g, batch, A, sA, Ad, ea, nullptr, 0, nullptr, nullptr, s);
+    case 5: return launch_slicers_L<5>(g, batch, A, sA, Ad, ea, nullptr, 0, nullptr, nullptr, s);
+    case 6: return launch_slicers_L<6>(g, batch, A, sA, Ad, ea, nullptr, 0, nullptr, nullptr, s);
+    case 7: return launch_slicers_L<7>(g, batch, A, sA, Ad, ea, nullptr, 0, nullptr, nullptr, s);
+    case 8: return launch_slicers_L<8>(g, batch, A, sA, Ad, ea, nullptr, 0, nullptr, nullptr, s);
+  }
+  return MG_EINVAL;
+}
+
+int split_slice_b(int d, int L, int batch, const double* B, long long sB, void* buf, cudaStream_t s) {
+  SplitGeom g = split_geom(d, L);
+  __nv_bfloat16* Bd = reinterpret_cast<__nv_bfloat16*>(buf);
+  int* eb = reinterpret_cast<int*>(Bd + g.b_item_elems() * batch);
+  switch (L) {
+    case 2: return launch_slicers_L<2>(g, batch, nullptr, 0, nullptr, nullptr, B, sB, Bd, eb, s);
+    case 3: return launch_slicers_L<3>(g, batch, nullptr, 0, nullptr, nullptr, B, sB, Bd, eb, s);
+    case 4: return launch_slicers_L<4>(g, batch, nullptr, 0, nullptr, nullptr, B, sB, Bd, eb, s);
+    case 5: return launch_slicers_L<5>(g, batch, nullptr, 0, nullptr, nullptr, B, sB, Bd, eb, s);
+    case 6: return launch_slicers_L<6>(g, batch, nullptr, 0, nullptr, nullptr, B, sB, Bd, eb, s);
+    case 7: return launch_slicers_L<7>(g, batch, nullptr, 0, nullptr, nullptr, B, sB, Bd, eb, s);
+    case 8: return launch_slicers_L<8>(g, batch, nullptr, 0, nullptr, nullptr, B, sB, Bd, eb, s);
+  }
+  return MG_EINVAL;
+}
+
+// C[b] = scale * A[b] B[b] + addends, from digit buffers made by split_slice_a/b.
+int split_gemm(int d, int L, int batch, const void* abuf, const void* bbuf, double* C, long long sC,
+               const AddTerms& add, int* status, cudaStream_t s) {
+  if (batch <= 0) return MG_OK;
+  if (batch > 65535) return MG_EUNSUPPORTED;
+  SplitGeom g = split_geom(d, L);
+  const __nv_bfloat16* Ad = reinterpret_cast<const __nv_bfloat16*>(abuf);
+  const int* ea = reinterpret_cast<const int*>(Ad + g.a_item_elems() * batch);
+  const __nv_bfloat16* Bd = reinterpret_cast<const __nv_bfloat16*>(bbuf);
+  const int* eb = reinterpret_cast<const int*>(Bd + g.b_item_elems() * batch);
+  SplitEpi e{};
+  e.add_n = add.n;
+  for (int m = 0; m < 3; ++m) { e.add_src[m] = add.src[m]; e.add_coef[m] = add.coef[m]; }
+  e.add_stride = add.stride;
+  e.diag = add.diag;
+  e.scale = add.scale;
+  switch (L) {
+    case 2: return launch_split_gemm_L<2>(g, batch, Ad, ea, Bd, eb, C, sC, e, status, s);
+    case 3: return launch_split_gemm_L<3>(g, batch, Ad, ea, Bd, eb, C, sC, e, status, s);
+    case 4: return launch_split_gemm_L<4>(g, batch, Ad, ea, Bd, eb, C, sC, e, status, s);
+    case 5: return launch_split_gemm_L<5>(g, batch, Ad, ea, Bd, eb, C, sC, e, status, s);
+    case 6: return launch_split_gemm_L<6>(g, batch, Ad, ea, Bd, eb, C, sC, e, status, s);
+    case 7: return launch_split_gemm_L<7>(g, batch, Ad, ea, Bd, eb, C, sC, e, status, s);
+    case 8: return launch_split_gemm_L<8>(g, batch, Ad, ea, Bd, eb, C, sC, e, status, s);
+  }
+  return MG_EINVAL;
+}
+
+}  // namespace mg

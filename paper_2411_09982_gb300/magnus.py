@@ -1,0 +1,266 @@
+"""Thin ctypes binding of libmagnus.so (the C ABI declared in include/magnus.h).
+
+Argument marshalling only: every step of the path runs in the library's CUDA
+kernels.  Functions keep the C names; tensors are passed as device pointers
+(`torch.Tensor.data_ptr()`), complex matrices as complex128 tensors (the
+interleaved (re, im) FP64 layout of the ABI).  There is no CPU fallback: if
+the library cannot be loaded or no sm_103a device is present, calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_lib", "libmagnus.so")
+
+MG_OK = 0
+MG_EINVAL = -1
+MG_ENOMEM = -2
+MG_ECUDA = -3
+MG_ENONFINITE = -4
+MG_ENOTHERM = -5
+MG_ETIMEOUT = -6
+MG_EAGAIN = -7
+MG_EUNSUPPORTED = -8
+
+MG_PREC_FP64 = 0
+MG_PREC_SPLIT = 1
+MG_OUT_STATE = 0
+MG_OUT_PROPAGATOR = 1
+MG_FLAG_HOST_PTRS = 1
+MG_FLAG_CHECK_HERMITIAN = 2
+MG_FLAG_NO_TRACE_SHIFT = 4
+
+
+class MagnusError(RuntimeError):
+    def __init__(self, code, where, detail=""):
+        self.code = code
+        super().__init__(f"{where}: {code} ({detail})")
+
+
+class mg_report(ctypes.Structure):
+    _fields_ = [
+        ("intervals", ctypes.c_int32),
+        ("taylor_degree", ctypes.c_int32),
+        ("max_squarings", ctypes.c_int32),
+        ("min_squarings", ctypes.c_int32),
+        ("max_norm1", ctypes.c_double),
+        ("unitarity_defect", ctypes.c_double),
+        ("ms_total", ctypes.c_double),
+        ("matrix_products", ctypes.c_int64),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_D = ctypes.c_double
+
+# name -> (restype, argtypes); mirrors include/magnus.h
+SIGNATURES = {
+    "mg_ctx_create": (_I, [ctypes.POINTER(_P), _I, _P]),
+    "mg_ctx_destroy": (_I, [_P]),
+    "mg_ctx_set_workspace_limit": (_I, [_P, ctypes.c_size_t]),
+    "mg_quadrature_nodes": (_I, [_I, _P, _P]),
+    "mg_plan_create": (_I, [_P, ctypes.POINTER(_P), _I, _I, _P, _P, _I, _I, _I]),
+    "mg_plan_destroy": (_I, [_P]),
+    "mg_set_controls": (_I, [_P, _I, _I, _D, _D, _P, _P, _I]),
+    "mg_evolve": (_I, [_P, _I, _P, _P, _I, _I, ctypes.POINTER(mg_report)]),
+    "mg_coefficients": (_I, [_P, _I, _I, _I, _D, _P, _P, _P]),
+    "mg_build_omega": (_I, [_P, _I, _I, _I, _D, _P, _P, _P, _P, _P, _P]),
+    "mg_expm": (_I, [_P, _I, _I, _P, _P, _I, _I, _P]),
+    "mg_cgemm": (_I, [_P, _I, _I, _P, _P, _P, _I, _I]),
+    "mg_propagate": (_I, [_P, _I, _I, _P, _I, _P, _P, _I, _I, _I]),
+    "mg_strerror": (ctypes.c_char_p, [_I]),
+    "mg_last_error_message": (ctypes.c_char_p, []),
+    "mg_kernel_launch_count": (ctypes.c_int64, []),
+}
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libmagnus.so (building it first if it is missing)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        from . import build as _build
+        _build.build()
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(code, where):
+    if code != MG_OK:
+        lib = load()
+        raise MagnusError(code, where, (lib.mg_strerror(code) or b"").decode() + "; " +
+                          (lib.mg_last_error_message() or b"").decode())
+    return code
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    return ctypes.c_void_p(int(stream.cuda_stream))
+
+
+# ----------------------------------------------------------------------------
+# object wrappers
+# ----------------------------------------------------------------------------
+class Context:
+    """An mg_ctx bound to one device and one CUDA stream (torch stream or None)."""
+
+    def __init__(self, device: int = 0, stream=None, workspace_limit: int | None = None):
+        lib = load()
+        h = ctypes.c_void_p()
+        _check(lib.mg_ctx_create(ctypes.byref(h), device, _stream_ptr(stream)), "mg_ctx_create")
+        self.h = h
+        self.device = device
+        self.stream = stream
+        if workspace_limit is not None:
+            _check(lib.mg_ctx_set_workspace_limit(self.h, int(workspace_limit)), "mg_ctx_set_workspace_limit")
+
+    def close(self):
+        if self.h:
+            load().mg_ctx_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Plan:
+    """An mg_plan: resident H0 / H_k on the device, a precision mode and controls."""
+
+    def __init__(self, ctx: Context, H0, Hk, precision=MG_PREC_FP64, slices=6, flags=0):
+        import torch
+        lib = load()
+        self.ctx = ctx
+        self.d = int(H0.shape[0])
+        self.K = int(Hk.shape[0]) if Hk is not None else 0
+        H0 = torch.as_tensor(H0, dtype=torch.complex128).contiguous()
+        Hk_t = torch.as_tensor(Hk, dtype=torch.complex128).contiguous() if self.K else None
+        host = not H0.is_cuda
+        h = ctypes.c_void_p()
+        _check(lib.mg_plan_create(ctx.h, ctypes.byref(h), self.d, self.K, _ptr(H0), _ptr(Hk_t), precision,
+                                  slices, flags | (MG_FLAG_HOST_PTRS if host else 0)), "mg_plan_create")
+        self.h = h
+
+    def set_controls(self, N, P, t0, dt, w, samples):
+        import torch
+        lib = load()
+        w = torch.as_tensor(w, dtype=torch.float64).contiguous().cpu()
+        samples = torch.as_tensor(samples, dtype=torch.float64).contiguous()
+        host = not samples.is_cuda
+        self._w = w
+        self._samples = samples
+        _check(lib.mg_set_controls(self.h, N, P, float(t0), float(dt), _ptr(w), _ptr(samples),
+                                   MG_FLAG_HOST_PTRS if host else 0), "mg_set_controls")
+
+    def evolve(self, output, inp, out, reorth_every=0, host=False, report=True):
+        lib = load()
+        rep = mg_report()
+        _check(lib.mg_evolve(self.h, output, _ptr(inp), _ptr(out), reorth_every,
+                             MG_FLAG_HOST_PTRS if host else 0, ctypes.byref(rep) if report else None),
+               "mg_evolve")
+        return rep.as_dict() if report else None
+
+    def close(self):
+        if self.h:
+            load().mg_plan_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ----------------------------------------------------------------------------
+# functional entry points (same names as the C ABI)
+# ----------------------------------------------------------------------------
+def mg_quadrature_nodes(P: int):
+    import numpy as np
+    lib = load()
+    x = np.zeros(P)
+    w = np.zeros(P)
+    _check(lib.mg_quadrature_nodes(P, x.ctypes.data_as(ctypes.c_void_p), w.ctypes.data_as(ctypes.c_void_p)),
+           "mg_quadrature_nodes")
+    return x, w
+
+
+def mg_coefficients(ctx, N, P, K, dt, w_dev, samples, c):
+    _check(load().mg_coefficients(ctx.h, N, P, K, float(dt), _ptr(w_dev), _ptr(samples), _ptr(c)),
+           "mg_coefficients")
+
+
+def mg_build_omega(ctx, N, d, K, dt, H0, Hk, c, Hbar, tau=None, norm1=None):
+    _check(load().mg_build_omega(ctx.h, N, d, K, float(dt), _ptr(H0), _ptr(Hk), _ptr(c), _ptr(Hbar), _ptr(tau),
+                                 _ptr(norm1)), "mg_build_omega")
+
+
+def mg_expm(ctx, batch, d, A, U, precision=MG_PREC_FP64, slices=6, squarings=None):
+    _check(load().mg_expm(ctx.h, batch, d, _ptr(A), _ptr(U), precision, slices, _ptr(squarings)), "mg_expm")
+
+
+def mg_cgemm(ctx, batch, d, A, B, C, precision=MG_PREC_FP64, slices=6):
+    _check(load().mg_cgemm(ctx.h, batch, d, _ptr(A), _ptr(B), _ptr(C), precision, slices), "mg_cgemm")
+
+
+def mg_propagate(ctx, N, d, U, output, inp, out, reorth_every=0, precision=MG_PREC_FP64, slices=6):
+    _check(load().mg_propagate(ctx.h, N, d, _ptr(U), output, _ptr(inp), _ptr(out), reorth_every, precision,
+                               slices), "mg_propagate")
+
+
+def mg_kernel_launch_count() -> int:
+    return int(load().mg_kernel_launch_count())
+
+
+# ----------------------------------------------------------------------------
+# convenience: a whole workload through the ABI
+# ----------------------------------------------------------------------------
+def node_samples(wl, N=None):
+    """Drive samples at the library's quadrature nodes t0 + n dt + (1 + x_p) dt / 2."""
+    import numpy as np
+    N = wl.N if N is None else N
+    x, w = mg_quadrature_nodes(wl.P)
+    t = wl.t0 + wl.dt * np.arange(N)[:, None] + (1.0 + x[None, :]) * (0.5 * wl.dt)
+    return np.ascontiguousarray(wl.drive(t)), w
+
+
+def evolve_workload(ctx, wl, precision=MG_PREC_FP64, slices=6, N=None, reorth_every=0, device="cuda"):
+    """Run a workloads.Workload through mg_plan_create / mg_set_controls / mg_evolve."""
+    import torch
+    N = wl.N if N is None else N
+    samples, w = node_samples(wl, N)
+    plan = Plan(ctx, torch.from_numpy(wl.H0).to(device), torch.from_numpy(wl.Hk).to(device), precision, slices)
+    plan.set_controls(N, wl.P, wl.t0, wl.dt, w, torch.from_numpy(samples).to(device))
+    if wl.psi0 is None:
+        out = torch.empty((wl.d, wl.d), dtype=torch.complex128, device=device)
+        rep = plan.evolve(MG_OUT_PROPAGATOR, None, out, reorth_every)
+    else:
+        psi0 = torch.from_numpy(wl.psi0).to(device)
+        out = torch.empty(wl.d, dtype=torch.complex128, device=device)
+        rep = plan.evolve(MG_OUT_STATE, psi0, out, reorth_every)
+    torch.cuda.synchronize()
+    plan.close()
+    return out, rep

@@ -1,0 +1,255 @@
+"""GPU parity of every step of the path against the CPU FP64 oracle (through the C ABI).
+
+Tolerances (written per test):
+  * FP64 mode: the oracle's own rounding level, ~1e-13 relative per product,
+    and the stated max-abs bound 1e-11 on whole evolutions.
+  * split mode: a product with L digits of beta bits errs by about
+    (L + 2) * 2d * 2^{-beta L} * max|A| * max|B| in the worst case; whole
+    evolutions must meet the stated max-abs bound 1e-6.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_2411_09982_gb300 import magnus as M  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    M.load()
+    c = M.Context(0)
+    yield c
+    c.close()
+
+
+def cuda(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to("cuda")
+
+
+def rand_c(rng, shape, scale=1.0):
+    return scale * (rng.normal(size=shape) + 1j * rng.normal(size=shape))
+
+
+def rand_herm(rng, d, scale=1.0):
+    a = rand_c(rng, (d, d))
+    return scale * 0.5 * (a + a.conj().T)
+
+
+def split_beta(d):
+    for beta in range(8, 1, -1):
+        if 2.0 ** (2 * beta - 1) * 2 * d <= 2.0 ** 24:
+            return beta
+    return 2
+
+
+# ----------------------------------------------------------------------------
+# quadrature and the first-order term
+# ----------------------------------------------------------------------------
+@pytest.mark.parametrize("P", [1, 2, 5, 8, 16, 33, 64])
+def test_quadrature_nodes_match_leggauss(P):
+    x, w = M.mg_quadrature_nodes(P)
+    xr, wr = oracle.gauss_legendre(P)
+    np.testing.assert_allclose(x, xr, atol=2e-15, rtol=0)
+    np.testing.assert_allclose(w, wr, atol=2e-15, rtol=0)
+
+
+def test_coefficients_match_oracle(ctx):
+    wl = W.config(1, N=300)
+    samples, w = M.node_samples(wl, 300)
+    c = torch.empty((300, wl.K), dtype=torch.float64, device="cuda")
+    M.mg_coefficients(ctx, 300, wl.P, wl.K, wl.dt, cuda(w), cuda(samples), c)
+    torch.cuda.synchronize()
+    ref = oracle.drive_coefficients(samples, oracle.gauss_legendre(wl.P)[1], wl.dt)
+    np.testing.assert_allclose(c.cpu().numpy(), ref, atol=1e-16, rtol=1e-13)
+
+
+@pytest.mark.parametrize("d,K,N", [(1, 0, 3), (30, 1, 19), (45, 3, 8), (129, 2, 9)])
+def test_build_omega_matches_oracle(ctx, d, K, N):
+    rng = np.random.default_rng(d + K)
+    H0 = rand_herm(rng, d, 3.0)
+    Hk = np.stack([rand_herm(rng, d) for _ in range(K)]) if K else np.zeros((0, d, d), complex)
+    c = rng.normal(size=(N, K)) * 0.1
+    dt = 0.05
+    Hbar = torch.empty((N, d, d), dtype=torch.complex128, device="cuda")
+    tau = torch.empty(N, dtype=torch.float64, device="cuda")
+    nrm = torch.empty(N, dtype=torch.float64, device="cuda")
+    M.mg_build_omega(ctx, N, d, K, dt, cuda(H0), cuda(Hk) if K else None, cuda(c) if K else None, Hbar, tau, nrm)
+    torch.cuda.synchronize()
+    for n in range(N):
+        ref = oracle.first_order_term(H0, Hk, c[n], dt)
+        np.testing.assert_allclose(Hbar[n].cpu().numpy(), ref, atol=1e-14, rtol=0)
+        t = np.trace(ref).real / d
+        assert abs(tau[n].item() - t) < 1e-14
+        assert abs(nrm[n].item() - np.linalg.norm(ref - t * np.eye(d), 1)) < 1e-12
+
+
+# ----------------------------------------------------------------------------
+# matrix products
+# ----------------------------------------------------------------------------
+@pytest.mark.parametrize("d,batch", [(1, 3), (7, 2), (30, 5), (64, 2), (65, 3), (129, 2), (200, 1)])
+def test_cgemm_fp64(ctx, d, batch):
+    rng = np.random.default_rng(d)
+    A, B = rand_c(rng, (batch, d, d)), rand_c(rng, (batch, d, d))
+    C = torch.empty((batch, d, d), dtype=torch.complex128, device="cuda")
+    M.mg_cgemm(ctx, batch, d, cuda(A), cuda(B), C, M.MG_PREC_FP64)
+    torch.cuda.synchronize()
+    np.testing.assert_allclose(C.cpu().numpy(), A @ B, atol=1e-13 * d, rtol=0)
+
+
+@pytest.mark.parametrize("d", [1, 5, 16, 30])
+def test_cgemm_split_exact_on_small_integers(ctx, d):
+    """Integer entries |a| <= 3 are one exact digit: the split product must equal the exact one bit for bit."""
+    rng = np.random.default_rng(100 + d)
+    A = rng.integers(-3, 4, (2, d, d)) + 1j * rng.integers(-3, 4, (2, d, d))
+    B = rng.integers(-3, 4, (2, d, d)) + 1j * rng.integers(-3, 4, (2, d, d))
+    C = torch.empty((2, d, d), dtype=torch.complex128, device="cuda")
+    M.mg_cgemm(ctx, 2, d, cuda(A), cuda(B), C, M.MG_PREC_SPLIT, 2)
+    torch.cuda.synchronize()
+    assert np.array_equal(C.cpu().numpy(), A @ B)
+
+
+@pytest.mark.parametrize("d,L", [(30, 2), (30, 4), (30, 6), (64, 6), (129, 3), (129, 6), (200, 8), (300, 5),
+                                 (729, 6)])
+def test_cgemm_split_within_digit_bound(ctx, d, L):
+    rng = np.random.default_rng(7 * d + L)
+    batch = 2
+    A, B = rand_c(rng, (batch, d, d)), rand_c(rng, (batch, d, d))
+    C = torch.empty((batch, d, d), dtype=torch.complex128, device="cuda")
+    M.mg_cgemm(ctx, batch, d, cuda(A), cuda(B), C, M.MG_PREC_SPLIT, L)
+    torch.cuda.synchronize()
+    got = C.cpu().numpy()
+    ref = A @ B
+    beta = split_beta(d)
+    ma = np.abs(np.stack([A.real, A.imag])).max()
+    mb = np.abs(np.stack([B.real, B.imag])).max()
+    bound = (L + 2) * 2 * d * 2.0 ** (-beta * L) * (2 * ma) * (2 * mb) + 1e-13 * d * ma * mb
+    err = np.abs(got - ref).max()
+    assert err <= bound, (err, bound)
+    # and it is a real approximation: the error falls with every digit
+    if L >= 4:
+        assert err <= 1e-5 * np.abs(ref).max()
+
+
+# ----------------------------------------------------------------------------
+# exponential
+# ----------------------------------------------------------------------------
+@pytest.mark.parametrize("d,scale", [(1, 3.0), (2, 1.0), (30, 0.5), (30, 8.0), (100, 2.0), (129, 0.05)])
+def test_expm_fp64_matches_oracle(ctx, d, scale):
+    rng = np.random.default_rng(d)
+    A = np.stack([rand_herm(rng, d, scale) for _ in range(3)])
+    U = torch.empty_like(cuda(A))
+    sq = torch.zeros(3, dtype=torch.int32, device="cuda")
+    M.mg_expm(ctx, 3, d, cuda(A), U, M.MG_PREC_FP64, 6, sq)
+    torch.cuda.synchronize()
+    for b in range(3):
+        ref = oracle.expm_minus_i(A[b])
+        nrm = np.linalg.norm(A[b] - np.trace(A[b]).real / d * np.eye(d), 1)
+        np.testing.assert_allclose(U[b].cpu().numpy(), ref, atol=5e-15 * d * max(1.0, nrm), rtol=0)
+
+
+@pytest.mark.parametrize("d,L", [(30, 6), (100, 5), (129, 7), (256, 6)])
+def test_expm_split_matches_oracle(ctx, d, L):
+    rng = np.random.default_rng(d + L)
+    A = np.stack([rand_herm(rng, d, 0.3) for _ in range(2)])
+    U = torch.empty_like(cuda(A))
+    M.mg_expm(ctx, 2, d, cuda(A), U, M.MG_PREC_SPLIT, L)
+    torch.cuda.synchronize()
+    beta = split_beta(d)
+    for b in range(2):
+        ref = oracle.expm_minus_i(A[b])
+        err = np.abs(U[b].cpu().numpy() - ref).max()
+        assert err < 200 * d * 2.0 ** (-beta * L) + 1e-13, err
+
+
+def test_expm_diagonal_is_exact_phase(ctx):
+    lam = np.linspace(-20, 20, 33)
+    A = np.diag(lam).astype(np.complex128)[None]
+    U = torch.empty_like(cuda(A))
+    M.mg_expm(ctx, 1, 33, cuda(A), U, M.MG_PREC_FP64, 6)
+    torch.cuda.synchronize()
+    np.testing.assert_allclose(np.diag(U[0].cpu().numpy()), np.exp(-1j * lam), atol=1e-13, rtol=0)
+    off = U[0].cpu().numpy() - np.diag(np.diag(U[0].cpu().numpy()))
+    assert np.abs(off).max() == 0.0
+
+
+# ----------------------------------------------------------------------------
+# propagation
+# ----------------------------------------------------------------------------
+@pytest.mark.parametrize("N,d,prec", [(1, 5, 0), (2, 5, 0), (37, 12, 0), (37, 12, 1), (64, 40, 1)])
+def test_propagate_tree_matches_sequential_product(ctx, N, d, prec):
+    rng = np.random.default_rng(N * d)
+    Us = np.stack([oracle.expm_minus_i(rand_herm(rng, d, 0.7)) for _ in range(N)])
+    out = torch.empty((d, d), dtype=torch.complex128, device="cuda")
+    M.mg_propagate(ctx, N, d, cuda(Us), M.MG_OUT_PROPAGATOR, None, out, 0, prec, 6)
+    torch.cuda.synchronize()
+    ref = oracle.propagate_unitary(Us)
+    tol = 1e-12 if prec == 0 else 1e-9
+    np.testing.assert_allclose(out.cpu().numpy(), ref, atol=tol, rtol=0)
+    psi = torch.empty(d, dtype=torch.complex128, device="cuda")
+    psi0 = W.basis_state(d, 1)
+    M.mg_propagate(ctx, N, d, cuda(Us), M.MG_OUT_STATE, cuda(psi0), psi, 0, prec, 6)
+    torch.cuda.synchronize()
+    np.testing.assert_allclose(psi.cpu().numpy(), oracle.propagate_state(Us, psi0), atol=1e-12, rtol=0)
+
+
+# ----------------------------------------------------------------------------
+# whole evolutions
+# ----------------------------------------------------------------------------
+def test_evolve_transmon_resonator_d30_fp64(ctx):
+    """The d = 30 workload (1000 intervals, 16 points, psi0 = |0,0>) within 1e-11 of the oracle."""
+    wl = W.config(0)
+    psi, rep = M.evolve_workload(ctx, wl, M.MG_PREC_FP64)
+    ref = oracle.evolve_workload(wl)
+    err = np.abs(psi.cpu().numpy() - ref).max()
+    assert err <= 1e-11, err
+    assert rep["unitarity_defect"] < 1e-12
+
+
+@pytest.mark.parametrize("L", [5, 6])
+def test_evolve_transmon_resonator_d30_split(ctx, L):
+    wl = W.config(0)
+    psi, rep = M.evolve_workload(ctx, wl, M.MG_PREC_SPLIT, L)
+    ref = oracle.evolve_workload(wl)
+    err = np.abs(psi.cpu().numpy() - ref).max()
+    assert err <= 1e-6, err
+
+
+@pytest.mark.parametrize("prec,L,tol", [(0, 6, 1e-11), (1, 6, 1e-6), (1, 7, 1e-6)])
+def test_evolve_chain_d729_prefix(ctx, prec, L, tol):
+    """The d = 729 chain (full propagator) on its first 24 intervals."""
+    wl = W.config(1)
+    n = 24
+    U, rep = M.evolve_workload(ctx, wl, prec, L, N=n)
+    ref = oracle.evolve_workload(wl, n_intervals=n)
+    err = np.abs(U.cpu().numpy() - ref).max()
+    assert err <= tol, err
+
+
+def test_evolve_constant_hamiltonian_exact(ctx):
+    """Time-independent H: U(T) = exp(-i H T) for any number of intervals (ragged tree of 13)."""
+    rng = np.random.default_rng(3)
+    d = 21
+    H0 = rand_herm(rng, d, 2.0)
+    wl = W.Workload("const", H0, np.zeros((1, d, d), complex) + rand_herm(rng, d)[None], W.ConstantDrive(np.array([0.3])),
+                    0.0, 1.7, 13, 4, None)
+    U, _ = M.evolve_workload(ctx, wl, M.MG_PREC_FP64)
+    ref = oracle.expm_minus_i(wl.T * (wl.H0 + 0.3 * wl.Hk[0]))
+    np.testing.assert_allclose(U.cpu().numpy(), ref, atol=1e-12, rtol=0)
+
+
+def test_evolve_host_pointers_match_device(ctx):
+    wl = W.config(0, N=50)
+    samples, w = M.node_samples(wl)
+    plan = M.Plan(ctx, wl.H0, wl.Hk)  # host operators
+    plan.set_controls(wl.N, wl.P, wl.t0, wl.dt, w, torch.from_numpy(samples))
+    out_h = torch.empty(wl.d, dtype=torch.complex128).pin_memory()
+    plan.evolve(M.MG_OUT_STATE, torch.from_numpy(wl.psi0), out_h, host=True)
+    ref = oracle.evolve_workload(wl)
+    assert np.abs(out_h.numpy() - ref).max() <= 1e-11
