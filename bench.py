@@ -1,0 +1,324 @@
+#!/usr/bin/env python
+"""Benchmark: first-order Magnus intervals per second on the d = 729 transmon chain.
+
+Workload: chain of 6 three-level transmons (d = 729), 6 Gaussian-cosine drives,
+2000 Magnus intervals of 16 Gauss-Legendre points over T = 50 ns, full
+propagator U(T) = U_1999 ... U_0.  One step = one pass of the whole path on one
+GPU: quadrature coefficients, Hbar_n, FP64 norms, exponentials (Taylor +
+squaring on the tcgen05 split-precision products), tree product.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line.  `value` is device-timed throughput with inputs resident
+in HBM; `e2e` repeats the step through the same C ABI with host buffers
+(samples host->device, U device->host inside the timed region).  The CPU oracle
+(`--impl reference`, and the `cpu_baseline` sample) runs on the host cores.
+Under torchrun each rank evolves its own independent replica (weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Magnus intervals/sec at dim 729 vs FP64 err; p50/p99 latency, mixed stream"
+UNIT = "intervals/s"
+WORKLOAD = "transmon_chain_d729_N2000_P16_K6_propagator"
+SAMPLE_INTERVALS = 128          # oracle sample (cpu_baseline) and accuracy prefix
+REFERENCE_STEP_INTERVALS = 16   # oracle intervals per step of --impl reference
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", choices=["split", "fp64"], default="split")
+    ap.add_argument("--slices", type=int, default=6)
+    ap.add_argument("--intervals", type=int, default=2000)
+    ap.add_argument("--e2e-steps", type=int, default=None)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_info():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "hbm_gbs": 6800.0}, "fallback"
+
+
+# ----------------------------------------------------------------------------
+# clocks during the timed region
+# ----------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            import tempfile
+            fd, self.path = tempfile.mkstemp(prefix="clocks_", suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        smax = [num(r[2]) for r in rows if num(r[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows),
+                "power_w_max": max([num(r[3]) for r in rows if num(r[3]) is not None] or [0.0])}
+
+
+# ----------------------------------------------------------------------------
+# our arm
+# ----------------------------------------------------------------------------
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import workloads as W
+    from paper_2411_09982_gb300 import build as B
+    from paper_2411_09982_gb300 import magnus as M
+
+    ws, rank, local = dist_info()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    B.build()
+    M.load()
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(device=dev)
+    ctx = M.Context(local, stream)
+    prec = M.MG_PREC_SPLIT if args.precision == "split" else M.MG_PREC_FP64
+    N = args.intervals
+
+    wl = W.config(1, seed=1 + rank)
+    samples_np, w = M.node_samples(wl, N)
+    H0 = torch.from_numpy(wl.H0).to(dev)
+    Hk = torch.from_numpy(wl.Hk).to(dev)
+    samples = torch.from_numpy(samples_np).to(dev)
+    samples_host = torch.from_numpy(samples_np).pin_memory()
+    out = torch.empty((wl.d, wl.d), dtype=torch.complex128, device=dev)
+    out_host = torch.empty((wl.d, wl.d), dtype=torch.complex128).pin_memory()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # 256 MiB > L2
+    plan = M.Plan(ctx, H0, Hk, prec, args.slices)
+
+    def step():
+        plan.set_controls(N, wl.P, wl.t0, wl.dt, w, samples)
+        plan.evolve(M.MG_OUT_PROPAGATOR, None, out, 0, report=False)
+
+    with torch.cuda.stream(stream):
+        for _ in range(max(3, args.warmup)):
+            step()
+        stream.synchronize()
+
+        # ---- timed region: K steps, L2 flushed before each, CUDA events on the library's stream
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        clocks = ClockSampler(local)
+        clocks.start()
+        launches0 = M.mg_kernel_launch_count()
+        ctx.gemm_stats(reset=True)
+        ctx.enable_gemm_timing(True)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        for i in range(args.steps):
+            flush.zero_()
+            ev[i][0].record(stream)
+            step()
+            ev[i][1].record(stream)
+        stream.synchronize()
+        ctx.enable_gemm_timing(False)
+        gstats = ctx.gemm_stats(reset=True)
+        launches = M.mg_kernel_launch_count() - launches0
+        torch.cuda.synchronize()
+        clk = clocks.stop()
+        step_ms = [a.elapsed_time(b) for a, b in ev]
+        total_ms = sum(step_ms)
+        if ws > 1:
+            t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            total_ms = float(t.item())
+            torch.distributed.barrier()
+
+        # ---- end to end through the C ABI with host buffers
+        e2e_steps = args.e2e_steps or args.steps
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            plan.set_controls(N, wl.P, wl.t0, wl.dt, w, samples_host)
+            plan.evolve(M.MG_OUT_PROPAGATOR, None, out_host, 0, host=True, report=False)
+        stream.synchronize()
+        e2e_s = time.perf_counter() - t0
+        if ws > 1:
+            t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            e2e_s = float(t.item())
+
+    value = ws * N * args.steps / (total_ms / 1000.0)
+    e2e_value = ws * N * e2e_steps / e2e_s
+
+    result = None
+    if rank == 0:
+        peaks, peak_src = measured_peaks()
+        # dominant kernel: the matrix-product launches (split GEMM or FP64 GEMM)
+        per_launch_ms = gstats["ms"] / max(1, gstats["launches"])
+        per_launch_flops = gstats["flops"] / max(1, gstats["launches"])
+        achieved = per_launch_flops / (per_launch_ms * 1e-3) / 1e12
+        if prec == M.MG_PREC_SPLIT:
+            peak = float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops")))
+            pairs = args.slices * (args.slices + 1) // 2
+            roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                    "frac": achieved / peak, "traffic": None,
+                    "kernel": "split_gemm_kernel (with its operand slicers)",
+                    "peak_source": f"bf16 dense sustained, {peak_src}",
+                    "tensor_pipe_frac": achieved * pairs / peak,
+                    "note": f"achieved counts 8 d^3 flops per complex product; the tensor pipe issues "
+                            f"{pairs} BF16 digit-pair products per such flop"}
+        else:
+            fp64_peak = 1.25   # TFLOP/s, nominal GB300 FP64 rate (no measured FP64 peak on this machine)
+            roof = {"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
+                    "frac": achieved / fp64_peak, "traffic": None, "kernel": "cgemm_f64_kernel",
+                    "peak_source": "nominal GB300 FP64 rate"}
+        result = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": max(3, args.warmup), "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": (f"bf16 digits x{args.slices} (fp32 accumulate) + f64" if prec == M.MG_PREC_SPLIT else "f64"),
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "d": wl.d, "intervals": N, "quadrature_points": wl.P,
+                       "controls": wl.K, "output": "full propagator", "precision": args.precision,
+                       "slices": args.slices if prec == M.MG_PREC_SPLIT else None,
+                       "l2": "256 MiB buffer written before every timed step",
+                       "parallelism": "independent replica per GPU"},
+            "roofline": roof,
+            "e2e": {"value": e2e_value, "unit": UNIT,
+                    "h2d_bytes_per_step": int(samples_host.numel() * 8),
+                    "d2h_bytes_per_step": int(out_host.numel() * 16)},
+            "clocks": clk,
+            "gpu_launches": int(launches),
+            "gemm_launches_timed": int(gstats["launches"]),
+        }
+        # accuracy vs the FP64 oracle and the CPU baseline on the same prefix
+        if not args.no_cpu_baseline:
+            import oracle
+            n_s = min(SAMPLE_INTERVALS, N)
+            cores = len(os.sched_getaffinity(0))
+            t0 = time.perf_counter()
+            ref = oracle.evolve_workload(wl, n_intervals=n_s)
+            cpu_s = time.perf_counter() - t0
+            with torch.cuda.stream(stream):
+                pre = M.Plan(ctx, H0, Hk, prec, args.slices)
+                pre.set_controls(n_s, wl.P, wl.t0, wl.dt, w, samples[:n_s].contiguous())
+                pre.evolve(M.MG_OUT_PROPAGATOR, None, out, 0, report=False)
+                stream.synchronize()
+                err = float(np.abs(out.cpu().numpy() - ref).max())
+                pre.close()
+            result["cpu_baseline"] = {"value": n_s / cpu_s, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                      "sample": f"first {n_s} of the {N} intervals of the same workload "
+                                                f"(numpy eigh exponentials, sequential products)"}
+            result["accuracy"] = {"max_abs_err_vs_fp64_oracle": err, "intervals_compared": n_s,
+                                  "tolerance": 1e-6 if prec == M.MG_PREC_SPLIT else 1e-11}
+    plan.close()
+    ctx.close()
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    if result is not None:
+        print(json.dumps(result), flush=True)
+
+
+# ----------------------------------------------------------------------------
+# reference arm: the CPU FP64 oracle, timed on the host cores (rank 0 only)
+# ----------------------------------------------------------------------------
+def run_reference(args):
+    ws, rank, _ = dist_info()
+    if rank != 0:
+        return
+    import oracle
+    import workloads as W
+    wl = W.config(1, seed=1)
+    n = REFERENCE_STEP_INTERVALS
+    cores = len(os.sched_getaffinity(0))
+    for _ in range(max(3, args.warmup) if args.warmup else 0):
+        oracle.evolve_workload(wl, n_intervals=2)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.evolve_workload(wl, n_intervals=n)
+        times.append(time.perf_counter() - t0)
+    total = sum(times)
+    value = n * args.steps / total
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1000.0 * total / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "d": wl.d, "intervals": args.intervals, "quadrature_points": wl.P,
+                   "controls": wl.K, "output": "full propagator"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{n} intervals of the workload per step"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+if __name__ == "__main__":
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)

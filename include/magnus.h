@@ -172,6 +172,15 @@ int mg_propagate(mg_ctx* ctx, int N, int d, const double* U, int output, const d
                  double* out, int reorth_every, int precision, int slices);
 
 /* ---- diagnostics ----------------------------------------------------------- */
+/* Per-launch timing of the matrix-product kernels (the dominant kernels of the
+ * path).  While enabled, the context records a CUDA event pair around every
+ * product launch on its stream; mg_ctx_gemm_stats synchronises the stream and
+ * returns the number of launches, their summed device time (ms) and their
+ * summed algorithmic work (8 d^3 real flops per complex d x d product, the
+ * 4-real-multiplication form), then optionally resets the counters. */
+int mg_ctx_enable_gemm_timing(mg_ctx* ctx, int enable);
+int mg_ctx_gemm_stats(mg_ctx* ctx, int64_t* launches, double* ms, double* flops, int reset);
+
 const char* mg_strerror(int code);
 const char* mg_last_error_message(void);
 /* Number of kernels this process has launched through the library. */

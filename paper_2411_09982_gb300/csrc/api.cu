@@ -65,6 +65,13 @@ struct mg_ctx {
   double* small = nullptr;    // small device scratch (norm bits, reductions)
   size_t small_n = 0;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  // optional per-launch timing of matrix-product kernels
+  bool timing = false;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<std::pair<int, int>> ev_pending;   // indices into ev_pool
+  size_t ev_next = 0;
+  long long t_launches = 0;
+  double t_flops = 0.0, t_ms = 0.0;
 };
 
 struct mg_plan {
@@ -246,8 +253,31 @@ struct Engine {
   int mul(int batch, const double* A, long long sA, int slot, const double* B, long long sB, double* C,
           long long sC, const AddTerms& add) {
     products += batch;
-    if (prec == MG_PREC_SPLIT) return split_gemm(d, L, batch, abuf, bbuf[slot], C, sC, add, ctx->status, ctx->stream);
-    return launch_cgemm_f64(batch, d, A, sA, 0, B, sB, C, sC, add, ctx->stream);
+    int e0 = -1, e1 = -1;
+    if (ctx->timing) MG_TRY(timing_begin(&e0));
+    int r;
+    if (prec == MG_PREC_SPLIT)
+      r = split_gemm(d, L, batch, abuf, bbuf[slot], C, sC, add, ctx->status, ctx->stream);
+    else
+      r = launch_cgemm_f64(batch, d, A, sA, 0, B, sB, C, sC, add, ctx->stream);
+    if (r != MG_OK) return r;
+    if (ctx->timing) {
+      MG_TRY(timing_begin(&e1));
+      ctx->ev_pending.emplace_back(e0, e1);
+      ctx->t_launches += 1;
+      ctx->t_flops += 8.0 * (double)d * d * d * batch;
+    }
+    return MG_OK;
+  }
+  int timing_begin(int* idx) {
+    if (ctx->ev_next >= ctx->ev_pool.size()) {
+      cudaEvent_t e;
+      MG_CUDA_TRY(cudaEventCreate(&e));
+      ctx->ev_pool.push_back(e);
+    }
+    *idx = (int)ctx->ev_next++;
+    MG_CUDA_TRY(cudaEventRecord(ctx->ev_pool[*idx], ctx->stream));
+    return MG_OK;
   }
 };
 
@@ -512,7 +542,35 @@ int mg_ctx_destroy(mg_ctx* ctx) {
   if (ctx->status) cudaFree(ctx->status);
   if (ctx->ev0) cudaEventDestroy(ctx->ev0);
   if (ctx->ev1) cudaEventDestroy(ctx->ev1);
+  for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
   delete ctx;
+  return MG_OK;
+}
+
+int mg_ctx_enable_gemm_timing(mg_ctx* ctx, int enable) {
+  if (!ctx) return MG_EINVAL;
+  ctx->timing = enable != 0;
+  return MG_OK;
+}
+
+int mg_ctx_gemm_stats(mg_ctx* ctx, int64_t* launches, double* ms, double* flops, int reset) {
+  if (!ctx) return MG_EINVAL;
+  MG_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  for (auto& pr : ctx->ev_pending) {
+    float t = 0.f;
+    MG_CUDA_TRY(cudaEventElapsedTime(&t, ctx->ev_pool[pr.first], ctx->ev_pool[pr.second]));
+    ctx->t_ms += t;
+  }
+  ctx->ev_pending.clear();
+  ctx->ev_next = 0;
+  if (launches) *launches = ctx->t_launches;
+  if (ms) *ms = ctx->t_ms;
+  if (flops) *flops = ctx->t_flops;
+  if (reset) {
+    ctx->t_launches = 0;
+    ctx->t_ms = 0.0;
+    ctx->t_flops = 0.0;
+  }
   return MG_OK;
 }
 

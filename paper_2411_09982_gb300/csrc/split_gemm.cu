@@ -11,11 +11,12 @@
 //     a = 2^{E_i+1-beta} sum_s v_s with v_s = q_s 2^{-beta s}, |q_s| <= 2^{beta-1};
 //     every v_s is exact in BF16.  Columns of B are cut the same way.
 //   * products: digit products v_s^A v_t^B with s + t <= L - 1 are accumulated
-//     in three FP32 TMEM accumulators by level s + t = 0, 1, >= 2.  beta is
+//     in four FP32 TMEM accumulators by level s + t = 0, 1, 2, >= 3.  beta is
 //     chosen so that 2^{2 beta - 1} * 2d <= 2^24: the level-0 and level-1 sums are
 //     then integers (in units of 1 and 2^-beta) below 2^24 and accumulate
-//     exactly; only the small level->=2 part is rounded.
-//   * epilogue: C_ij = 2^{(E_i+1-beta)+(F_j+1-beta)} (g0 + g1 + g2) in FP64, plus
+//     exactly; level 2 is exact for all but adversarial inputs, and only the
+//     level->=3 part, 2^{-3 beta} below the leading one, is rounded.
+//   * epilogue: C_ij = 2^{(E_i+1-beta)+(F_j+1-beta)} (g0 + g1 + g2 + g3) in FP64, plus
 //     optional FP64 addends (Taylor/Horner terms) and a diagonal.
 //
 // The error of one product is about 2^{-beta L} relative to max|A| max|B|, so
@@ -30,7 +31,7 @@
 //   warp 1      TMEM owner and MMA issuer: tcgen05.mma kind::f16 (BF16 in,
 //               FP32 accumulate), M = 128, N = 128 (64 real + 64 imaginary
 //               output columns), K = 16, one instruction per digit pair.
-//   warps 2..5  epilogue: tcgen05.ld of the three accumulators, FP64 combine.
+//   warps 2..5  epilogue: tcgen05.ld of the four accumulators, FP64 combine.
 // Every mbarrier wait is bounded by a wall-clock deadline; a wait that gives up
 // records MG_DEV_TIMEOUT in the status word and the CTA winds down.
 #include "common.cuh"
@@ -295,12 +296,10 @@ __device__ __forceinline__ void tc_commit(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
                : "memory");
 }
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
   asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
-      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
       : "r"(taddr));
 }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
@@ -321,6 +320,8 @@ __device__ __forceinline__ uint64_t sw32_kmajor_desc(uint32_t saddr) {
 constexpr uint32_t kIdescBf16 = (1u << 4) | (1u << 7) | (1u << 10) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
 
 constexpr int SG_THREADS = 192;
+// TMEM accumulators: digit-pair levels 0, 1, 2 and >= 3, 128 columns each (all 512).
+constexpr int SG_GROUPS = 4;
 constexpr uint64_t SG_WAIT_NS = 4000000000ull;   // 4 s: far beyond any legitimate wait
 
 struct SplitEpi {
@@ -411,12 +412,12 @@ split_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
         tc_fence_after();
         const uint32_t a0 = smem_u32(smem + s * STAGE_BYTES);
         const uint32_t b0 = a0 + L * SG_TILE_BYTES;
-        bool first[3] = {kb == 0, kb == 0, kb == 0};
+        bool first[SG_GROUPS] = {kb == 0, kb == 0, kb == 0, kb == 0};
 #pragma unroll
         for (int sa = 0; sa < L; ++sa) {
 #pragma unroll
           for (int sb = 0; sb < L - sa; ++sb) {
-            const int g = (sa + sb) < 2 ? (sa + sb) : 2;
+            const int g = (sa + sb) < SG_GROUPS - 1 ? (sa + sb) : SG_GROUPS - 1;
             const uint32_t acc = first[g] ? 0u : 1u;
             first[g] = false;
             tc_mma_bf16(tmem + g * 128, sw32_kmajor_desc(a0 + sa * SG_TILE_BYTES),
@@ -447,26 +448,28 @@ split_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
       for (int m = 0; m < 3; ++m) addp[m] = epi.add_src[m] ? epi.add_src[m] + b * epi.add_stride : nullptr;
       double2* Cb = reinterpret_cast<double2*>(C + b * sC);
       const uint32_t lane_base = tmem + ((uint32_t)(q * 32) << 16);
-      for (int jc = 0; jc < SG_BNC; jc += 16) {
-        uint32_t r0[16], r1[16], r2[16], i0[16], i1[16], i2[16];
-        tmem_ld16(lane_base + 0 * 128 + jc, r0);
-        tmem_ld16(lane_base + 1 * 128 + jc, r1);
-        tmem_ld16(lane_base + 2 * 128 + jc, r2);
-        tmem_ld16(lane_base + 0 * 128 + SG_BNC + jc, i0);
-        tmem_ld16(lane_base + 1 * 128 + SG_BNC + jc, i1);
-        tmem_ld16(lane_base + 2 * 128 + SG_BNC + jc, i2);
+      for (int jc = 0; jc < SG_BNC; jc += 8) {
+        uint32_t re_acc[SG_GROUPS][8], im_acc[SG_GROUPS][8];
+#pragma unroll
+        for (int g = 0; g < SG_GROUPS; ++g) {
+          tmem_ld8(lane_base + g * 128 + jc, re_acc[g]);
+          tmem_ld8(lane_base + g * 128 + SG_BNC + jc, im_acc[g]);
+        }
         tmem_wait_ld();
         if (row_ok) {
 #pragma unroll
-          for (int jj = 0; jj < 16; ++jj) {
+          for (int jj = 0; jj < 8; ++jj) {
             const int j = nt * SG_BNC + jc + jj;
             if (j < d) {
               const int Eb = eb[(long long)b * (Np / 2) + j];
               const double f = ldexp(1.0, Ea + Eb + 2 - 2 * beta);
-              double re = ((double)__uint_as_float(r0[jj]) + (double)__uint_as_float(r1[jj])) +
-                          (double)__uint_as_float(r2[jj]);
-              double im = ((double)__uint_as_float(i0[jj]) + (double)__uint_as_float(i1[jj])) +
-                          (double)__uint_as_float(i2[jj]);
+              // smallest group first: g3 and g2 are tiny next to g0
+              double re = 0.0, im = 0.0;
+#pragma unroll
+              for (int g = SG_GROUPS - 1; g >= 0; --g) {
+                re += (double)__uint_as_float(re_acc[g][jj]);
+                im += (double)__uint_as_float(im_acc[g][jj]);
+              }
               re *= f * epi.scale;
               im *= f * epi.scale;
               const long long off = (long long)row * d + j;

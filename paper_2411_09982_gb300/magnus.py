@@ -74,6 +74,8 @@ SIGNATURES = {
     "mg_expm": (_I, [_P, _I, _I, _P, _P, _I, _I, _P]),
     "mg_cgemm": (_I, [_P, _I, _I, _P, _P, _P, _I, _I]),
     "mg_propagate": (_I, [_P, _I, _I, _P, _I, _P, _P, _I, _I, _I]),
+    "mg_ctx_enable_gemm_timing": (_I, [_P, _I]),
+    "mg_ctx_gemm_stats": (_I, [_P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(_D), ctypes.POINTER(_D), _I]),
     "mg_strerror": (ctypes.c_char_p, [_I]),
     "mg_last_error_message": (ctypes.c_char_p, []),
     "mg_kernel_launch_count": (ctypes.c_int64, []),
@@ -134,6 +136,17 @@ class Context:
         self.stream = stream
         if workspace_limit is not None:
             _check(lib.mg_ctx_set_workspace_limit(self.h, int(workspace_limit)), "mg_ctx_set_workspace_limit")
+
+    def enable_gemm_timing(self, on=True):
+        _check(load().mg_ctx_enable_gemm_timing(self.h, 1 if on else 0), "mg_ctx_enable_gemm_timing")
+
+    def gemm_stats(self, reset=True):
+        n = ctypes.c_int64()
+        ms = ctypes.c_double()
+        fl = ctypes.c_double()
+        _check(load().mg_ctx_gemm_stats(self.h, ctypes.byref(n), ctypes.byref(ms), ctypes.byref(fl),
+                                        1 if reset else 0), "mg_ctx_gemm_stats")
+        return dict(launches=n.value, ms=ms.value, flops=fl.value)
 
     def close(self):
         if self.h:
