@@ -69,24 +69,31 @@ int launch_lincomb(int batch, int d, double* dst, int nsrc, const double* const*
 }
 
 // ---------------------------------------------------------------------------
-__global__ void apply_phase_kernel(long long per_item, int batch, const double* __restrict__ phase,
+// grid (chunks, batch): the phase factor is formed once per block, not per element.
+__global__ void apply_phase_kernel(long long per_item, const double* __restrict__ phase,
                                    const double* __restrict__ src, double* __restrict__ dst) {
-  const long long total = per_item * batch;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+  __shared__ double cs_sn[2];
+  const int b = blockIdx.y;
+  if (threadIdx.x == 0) sincos(phase[b], &cs_sn[1], &cs_sn[0]);
+  __syncthreads();
+  const double cs = cs_sn[0], sn = cs_sn[1];
+  const double2* sb = reinterpret_cast<const double2*>(src) + (long long)b * per_item;
+  double2* db = reinterpret_cast<double2*>(dst) + (long long)b * per_item;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < per_item;
        e += (long long)gridDim.x * blockDim.x) {
-    int b = (int)(e / per_item);
-    double sn, cs;
-    sincos(phase[b], &sn, &cs);
     // e^{-i p} (x + i y) = (c - i s)(x + i y)
-    double2 v = reinterpret_cast<const double2*>(src)[e];
-    reinterpret_cast<double2*>(dst)[e] = make_double2(cs * v.x + sn * v.y, cs * v.y - sn * v.x);
+    const double2 v = sb[e];
+    db[e] = make_double2(cs * v.x + sn * v.y, cs * v.y - sn * v.x);
   }
 }
 
 int launch_apply_phase(int batch, int d, long long count_per_item, const double* phase, const double* src,
                        double* dst, cudaStream_t s) {
   (void)d;
-  apply_phase_kernel<<<grid_for(count_per_item * batch), 256, 0, s>>>(count_per_item, batch, phase, src, dst);
+  if (batch > 65535) return MG_EUNSUPPORTED;
+  long long bx = (count_per_item + 1023) / 1024;
+  if (bx > 64) bx = 64;
+  apply_phase_kernel<<<dim3((unsigned)bx, batch), 256, 0, s>>>(count_per_item, phase, src, dst);
   return check_launch("apply_phase_kernel");
 }
 

@@ -6,10 +6,10 @@
 //
 //   * complex -> real:   [Cr | Ci] = [Ar | Ai] * [[Br, Bi], [-Bi, Br]]
 //     (M = d, N = 2d, K = 2d; 8 d^3 real flops, the "4M" form).
-//   * digits:  each FP64 row i of [Ar | Ai] is scaled by 2^{-(E_i+1)} so that
-//     it lies in (-1/2, 1/2) and cut into `L` signed digits of `beta` bits,
-//     a = 2^{E_i+1-beta} sum_s v_s with v_s = q_s 2^{-beta s}, |q_s| <= 2^{beta-1};
-//     every v_s is exact in BF16.  Columns of B are cut the same way.
+//   * digits:  each FP64 row i of [Ar | Ai] (all entries below 2^{E_i}) is cut
+//     into `L` signed digits of `beta` bits, a = 2^{E_i+1-beta} sum_s v_s with
+//     v_s = q_s 2^{-beta s}, |q_s| <= 2^{beta-1}; every v_s is exact in BF16.
+//     Columns of B are cut the same way.
 //   * products: digit products v_s^A v_t^B with s + t <= L - 1 are accumulated
 //     in four FP32 TMEM accumulators by level s + t = 0, 1, 2, >= 3.  beta is
 //     chosen so that 2^{2 beta - 1} * 2d <= 2^24: the level-0 and level-1 sums are
@@ -84,25 +84,53 @@ SplitGeom split_geom(int d, int L) {
 // ---------------------------------------------------------------------------
 // digit extraction (shared by the A and B slicers)
 // ---------------------------------------------------------------------------
-// x in (-1/2, 1/2): x = sum_{s<L} q_s 2^{-beta (s+1)} + r; writes v_s = q_s 2^{-beta s}.
-template <int L>
-__device__ __forceinline__ void make_digits(double x, int beta, __nv_bfloat16 (&v)[L]) {
-  const double up = ldexp(1.0, beta);
-#pragma unroll
-  for (int s = 0; s < L; ++s) {
-    double y = x * up;
-    double q = rint(y);
-    x = y - q;
-    v[s] = __float2bfloat16_rn((float)ldexp(q, -beta * s));
-  }
+// GB300's FP64 pipe is narrow, so digits are cut with integer arithmetic on the
+// IEEE-754 bits: a value a of a row whose largest magnitude is below 2^E becomes
+// the fixed-point integer X = round(a 2^{beta L - E - 1}), |X| < 2^{beta L - 1},
+// which is written in balanced base 2^beta:
+//     X = sum_{s<L} q_s 2^{beta (L-1-s)},  q_1..q_{L-1} in [-2^{beta-1}, 2^{beta-1}),
+// and the leading q_0 in [-2^{beta-1}, 2^{beta-1}].  Then
+//     a ~= 2^{E+1-beta} sum_s v_s,   v_s = q_s 2^{-beta s}  (exact in BF16),
+// with an error below 2^{E - beta L} (the rounding of X).
+
+// exponent E of |a| with |a| < 2^E (biased exponent - 1022); zero and subnormals -> INT_MIN/2
+__device__ __forceinline__ int exp_bound(double a) {
+  const long long bits = __double_as_longlong(a);
+  const int bexp = (int)((bits >> 52) & 0x7FF);
+  return bexp == 0 ? -(1 << 29) : bexp - 1022;
 }
 
-__device__ __forceinline__ int row_exponent(double m) {
-  // smallest E with m < 2^E (m > 0); 0 for m == 0
-  if (!(m > 0.0)) return 0;
-  int e;
-  frexp(m, &e);
-  return e;
+// round(a * 2^sh) as a signed 64-bit integer (sh chosen so that the result fits)
+__device__ __forceinline__ long long fixed_point(double a, int sh) {
+  const long long bits = __double_as_longlong(a);
+  const int bexp = (int)((bits >> 52) & 0x7FF);
+  if (bexp == 0) return 0;
+  const long long mant = (bits & 0xFFFFFFFFFFFFFLL) | 0x10000000000000LL;   // a = mant 2^{bexp-1075}
+  const int shift = bexp - 1075 + sh;
+  long long X;
+  if (shift >= 0) X = mant << shift;
+  else if (shift > -62) X = (mant + (1LL << (-shift - 1))) >> (-shift);
+  else X = 0;
+  return bits < 0 ? -X : X;
+}
+
+template <int L>
+__device__ __forceinline__ void make_digits(double a, int sh, int beta, __nv_bfloat16 (&v)[L]) {
+  long long X = fixed_point(a, sh);
+  const long long half = 1LL << (beta - 1), mask = (1LL << beta) - 1;
+  int q[L];
+#pragma unroll
+  for (int s = L - 1; s >= 1; --s) {
+    const long long r = ((X + half) & mask) - half;
+    q[s] = (int)r;
+    X = (X - r) >> beta;
+  }
+  q[0] = (int)X;
+#pragma unroll
+  for (int s = 0; s < L; ++s) {
+    const float pw = __int_as_float((127 - beta * s) << 23);   // 2^{-beta s}, exact
+    v[s] = __float2bfloat16_rn(__int2float_rn(q[s]) * pw);
+  }
 }
 
 // A digits: rows of [Re A | Im A].  grid (ceil(Mp/8), batch), block 256 (one warp per row).
@@ -124,20 +152,20 @@ slice_a_kernel(int d, int Kp, int Mp, int beta, const double* __restrict__ A, lo
     return;
   }
   const double2* a = reinterpret_cast<const double2*>(A + b * sA) + (long long)row * d;
-  double m = 0.0;
+  int E = -(1 << 29);
   for (int k = lane; k < d; k += 32) {
-    double2 v = a[k];
-    m = fmax(m, fmax(fabs(v.x), fabs(v.y)));
+    const double2 v = a[k];
+    E = max(E, max(exp_bound(v.x), exp_bound(v.y)));
   }
-  for (int o2 = 16; o2 > 0; o2 >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o2));
-  const int E = row_exponent(m);
+  for (int o2 = 16; o2 > 0; o2 >>= 1) E = max(E, __shfl_xor_sync(0xffffffffu, E, o2));
+  if (E < -(1 << 28)) E = 0;   // all-zero row
   if (lane == 0) ea[(long long)b * Mp + row] = E;
-  const double sc = ldexp(1.0, -(E + 1));
+  const int sh = beta * L - E - 1;
   for (int k = lane; k < d; k += 32) {
-    double2 v = a[k];
+    const double2 v = a[k];
     __nv_bfloat16 dr[L], di[L];
-    make_digits<L>(v.x * sc, beta, dr);
-    make_digits<L>(v.y * sc, beta, di);
+    make_digits<L>(v.x, sh, beta, dr);
+    make_digits<L>(v.y, sh, beta, di);
 #pragma unroll
     for (int s = 0; s < L; ++s) {
       o[s * slice_stride + k] = dr[s];
@@ -159,8 +187,8 @@ __global__ void __launch_bounds__(256)
 slice_b_kernel(int d, int Kp, int Np, int beta, const double* __restrict__ B, long long sB,
                __nv_bfloat16* __restrict__ out, int* __restrict__ eb) {
   __shared__ double2 tile[SB_KCHUNK][SG_BNC + 1];
-  __shared__ double red[4][SG_BNC];
-  __shared__ double scale[SG_BNC];
+  __shared__ int red[4][SG_BNC];
+  __shared__ int shift[SG_BNC];
   const int t = blockIdx.x, b = blockIdx.y;
   const int j0 = t * SG_BNC;
   const int tid = threadIdx.x;
@@ -168,22 +196,22 @@ slice_b_kernel(int d, int Kp, int Np, int beta, const double* __restrict__ B, lo
   const long long slice_stride = (long long)Np * Kp;
   __nv_bfloat16* ob = out + (long long)b * L * slice_stride;
 
-  // pass 1: column maxima
+  // pass 1: column exponent bounds
   {
     const int c = tid & 63, g = tid >> 6;
-    double m = 0.0;
+    int E = -(1 << 29);
     if (j0 + c < d)
       for (int k = g; k < d; k += 4) {
-        double2 v = Bb[(long long)k * d + j0 + c];
-        m = fmax(m, fmax(fabs(v.x), fabs(v.y)));
+        const double2 v = Bb[(long long)k * d + j0 + c];
+        E = max(E, max(exp_bound(v.x), exp_bound(v.y)));
       }
-    red[g][c] = m;
+    red[g][c] = E;
     __syncthreads();
     if (tid < SG_BNC) {
-      double mm = fmax(fmax(red[0][tid], red[1][tid]), fmax(red[2][tid], red[3][tid]));
-      int E = row_exponent(mm);
-      scale[tid] = ldexp(1.0, -(E + 1));
-      if (j0 + tid < d) eb[(long long)b * (Np / 2) + j0 + tid] = E;
+      int EE = max(max(red[0][tid], red[1][tid]), max(red[2][tid], red[3][tid]));
+      if (EE < -(1 << 28)) EE = 0;
+      shift[tid] = beta * L - EE - 1;
+      if (j0 + tid < d) eb[(long long)b * (Np / 2) + j0 + tid] = EE;
     }
     __syncthreads();
   }
@@ -201,10 +229,10 @@ slice_b_kernel(int d, int Kp, int Np, int beta, const double* __restrict__ B, lo
       int kk = e % SB_KCHUNK, r = e / SB_KCHUNK;
       int k = k0 + kk;
       if (k >= d) continue;
-      double2 v = tile[kk][r];
+      const double2 v = tile[kk][r];
       __nv_bfloat16 dr[L], di[L];
-      make_digits<L>(v.x * scale[r], beta, dr);
-      make_digits<L>(v.y * scale[r], beta, di);
+      make_digits<L>(v.x, shift[r], beta, dr);
+      make_digits<L>(v.y, shift[r], beta, di);
       __nv_bfloat16* row_re = ob + (long long)(t * 2 * SG_BNC + r) * Kp;          // [Re | -Im]
       __nv_bfloat16* row_im = ob + (long long)(t * 2 * SG_BNC + SG_BNC + r) * Kp; // [Im | Re]
 #pragma unroll
@@ -323,6 +351,34 @@ constexpr int SG_THREADS = 192;
 // TMEM accumulators: digit-pair levels 0, 1, 2 and >= 3, 128 columns each (all 512).
 constexpr int SG_GROUPS = 4;
 constexpr uint64_t SG_WAIT_NS = 4000000000ull;   // 4 s: far beyond any legitimate wait
+
+// The four level accumulators hold (in units of the leading digit product)
+//   g0: integers, g1: multiples of 2^-beta, g2: multiples of 2^-2beta (all exact),
+//   g3: the rounded remainder.
+// They are combined exactly in 64-bit fixed point with `fx` extra fraction bits
+// below 2^-3beta, converted to FP64 once and scaled by 2^e_total through the
+// exponent field: integer work instead of GB300's narrow FP64 pipe.
+__device__ __forceinline__ float pow2f(int k) { return __int_as_float((127 + k) << 23); }
+
+__device__ __forceinline__ double scale_pow2(double x, int e) {
+  const long long bits = __double_as_longlong(x);
+  const int bexp = (int)((bits >> 52) & 0x7FF);
+  if (bexp == 0) return x;   // zero (G is an integer: no subnormal inputs)
+  const int ne = bexp + e;
+  if (ne > 0 && ne < 2047) return __longlong_as_double(bits + ((long long)e << 52));
+  return ldexp(x, e);
+}
+
+__device__ __forceinline__ double combine_levels(uint32_t u0, uint32_t u1, uint32_t u2, uint32_t u3, int beta,
+                                                 int fx, int e_total) {
+  const long long i0 = __float2ll_rn(__uint_as_float(u0));
+  const long long i1 = __float2ll_rn(__uint_as_float(u1) * pow2f(beta));
+  const long long i2 = __float2ll_rn(__uint_as_float(u2) * pow2f(2 * beta));
+  const long long i3 = __float2ll_rn(__uint_as_float(u3) * pow2f(3 * beta + fx));
+  const long long G = i0 * (1LL << (3 * beta + fx)) + i1 * (1LL << (2 * beta + fx)) +
+                      i2 * (1LL << (beta + fx)) + i3;
+  return scale_pow2(__ll2double_rn(G), e_total);
+}
 
 struct SplitEpi {
   const double* add_src[3];
@@ -443,6 +499,7 @@ split_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
       const int row = mt * SG_BM + q * 32 + lane;
       const bool row_ok = row < d;
       const int Ea = row_ok ? ea[(long long)b * Mp + row] : 0;
+      const int fx_bits = 37 - 3 * beta;   // fraction bits kept below the level-3 unit
       const double* addp[3];
 #pragma unroll
       for (int m = 0; m < 3; ++m) addp[m] = epi.add_src[m] ? epi.add_src[m] + b * epi.add_stride : nullptr;
@@ -461,17 +518,15 @@ split_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
           for (int jj = 0; jj < 8; ++jj) {
             const int j = nt * SG_BNC + jc + jj;
             if (j < d) {
-              const int Eb = eb[(long long)b * (Np / 2) + j];
-              const double f = ldexp(1.0, Ea + Eb + 2 - 2 * beta);
-              // smallest group first: g3 and g2 are tiny next to g0
-              double re = 0.0, im = 0.0;
-#pragma unroll
-              for (int g = SG_GROUPS - 1; g >= 0; --g) {
-                re += (double)__uint_as_float(re_acc[g][jj]);
-                im += (double)__uint_as_float(im_acc[g][jj]);
+              const int e_total = Ea + eb[(long long)b * (Np / 2) + j] + 2 - 5 * beta - fx_bits;
+              double re = combine_levels(re_acc[0][jj], re_acc[1][jj], re_acc[2][jj], re_acc[3][jj], beta,
+                                         fx_bits, e_total);
+              double im = combine_levels(im_acc[0][jj], im_acc[1][jj], im_acc[2][jj], im_acc[3][jj], beta,
+                                         fx_bits, e_total);
+              if (epi.scale != 1.0) {
+                re *= epi.scale;
+                im *= epi.scale;
               }
-              re *= f * epi.scale;
-              im *= f * epi.scale;
               const long long off = (long long)row * d + j;
               for (int m = 0; m < epi.add_n; ++m) {
                 double2 p = reinterpret_cast<const double2*>(addp[m])[off];
