@@ -14,7 +14,7 @@ __global__ void scale_minus_i_kernel(long long per_item, int batch, const double
        e += (long long)gridDim.x * blockDim.x) {
     int b = (int)(e / per_item);
     int s = sq_dev ? sq_dev[b] : sq;
-    double f = ldexp(1.0, -s);
+    const double f = __longlong_as_double((long long)(1023 - s) << 52);   // 2^{-s}, 0 <= s < 1023
     double2 v = reinterpret_cast<const double2*>(src)[e];
     // (-i)(a + i b) = b - i a
     reinterpret_cast<double2*>(dst)[e] = make_double2(f * v.y, -f * v.x);
