@@ -94,7 +94,7 @@ enum Slot {
   WS_P2, WS_P3, WS_Y, WS_R0, WS_R1,
   WS_ABUF, WS_BBUF0, WS_BBUF1,
   WS_TAU, WS_NORM, WS_ACC, WS_ACC2, WS_NS_G, WS_NS_H, WS_VEC,
-  WS_TREE0, WS_TREE1, WS_UBUF,
+  WS_TREE0, WS_TREE1, WS_UBUF, WS_NS_Z, WS_OUT,
   WS_COUNT
 };
 
@@ -241,13 +241,43 @@ struct Engine {
     MG_TRY(ws_get(ctx, WS_BBUF1, split_b_bytes(d, L, batch), &bbuf[1]));
     return MG_OK;
   }
-  int prepA(int batch, const double* A, long long sA) {
+  // Products of the split path are stored as double-float (DF32, see df32.cuh);
+  // the FP64 path stores FP64.  Both use 16 bytes per complex element.
+  bool df() const { return prec == MG_PREC_SPLIT; }
+  int prepA(int batch, const double* A, long long sA, int in_df) {
     if (prec != MG_PREC_SPLIT) return MG_OK;
-    return split_slice_a(d, L, batch, A, sA, abuf, ctx->stream);
+    return split_slice_a(d, L, batch, A, sA, in_df, abuf, ctx->stream);
   }
-  int prepB(int slot, int batch, const double* B, long long sB) {
+  int prepB(int slot, int batch, const double* B, long long sB, int in_df) {
     if (prec != MG_PREC_SPLIT) return MG_OK;
-    return split_slice_b(d, L, batch, B, sB, bbuf[slot], ctx->stream);
+    return split_slice_b(d, L, batch, B, sB, in_df, bbuf[slot], ctx->stream);
+  }
+  int prepA(int batch, const double* A, long long sA) { return prepA(batch, A, sA, df() ? 1 : 0); }
+  int prepB(int slot, int batch, const double* B, long long sB) { return prepB(slot, batch, B, sB, df() ? 1 : 0); }
+  // elementwise steps in the engine's storage format
+  int lincomb(int batch, double* dst, int n, const double* const* src, const double* coef, double diag) {
+    return df() ? launch_lincomb_df(batch, d, dst, n, src, coef, diag, ctx->stream)
+                : launch_lincomb(batch, d, dst, n, src, coef, diag, ctx->stream);
+  }
+  int identity(int batch, double* dst) {
+    return df() ? launch_identity_df(batch, d, dst, ctx->stream) : launch_identity(batch, d, dst, ctx->stream);
+  }
+  int phase(int batch, const double* tau, const double* src, double* dst) {
+    return df() ? launch_apply_phase_df(batch, d, tau, src, dst, ctx->stream)
+                : launch_apply_phase(batch, d, (long long)d * d, tau, src, dst, ctx->stream);
+  }
+  // X = -i 2^{-sq} W (W FP64, X in engine storage; may alias)
+  int scale_x(int batch, const double* W, double* X, int sq) {
+    return df() ? launch_scale_minus_i_df(batch, d, W, X, sq, ctx->stream)
+                : launch_scale_minus_i(batch, d, W, X, nullptr, sq, ctx->stream);
+  }
+  int to_fp64(int batch, const double* src, long long ss, double* dst, long long ds) {
+    return df() ? launch_df_to_fp64(batch, d, src, ss, dst, ds, ctx->stream)
+                : launch_copy_strided(batch, 2LL * d * d, src, ss, dst, ds, ctx->stream);
+  }
+  int from_fp64(int batch, const double* src, long long ss, double* dst, long long ds) {
+    return df() ? launch_fp64_to_df(batch, d, src, ss, dst, ds, ctx->stream)
+                : launch_copy_strided(batch, 2LL * d * d, src, ss, dst, ds, ctx->stream);
   }
   // C = A B (+ addends); split mode uses the digits prepared by prepA / prepB(slot).
   int mul(int batch, const double* A, long long sA, int slot, const double* B, long long sB, double* C,
@@ -332,8 +362,8 @@ int expm_chunk(mg_ctx* ctx, Engine& eng, int batch, double* W, const double* tau
   MG_TRY(ws(ctx, WS_R1, md * batch, &R1));
   MG_TRY(eng.reserve(batch));
 
-  // X = -i 2^{-s} W   (in place)
-  MG_TRY(launch_scale_minus_i(batch, d, W, W, nullptr, tc.s, s));
+  // X = -i 2^{-s} W   (in place, into the engine's storage format)
+  MG_TRY(eng.scale_x(batch, W, W, tc.s));
   const double* X = W;
 
   // coefficients 1/j!
@@ -367,7 +397,7 @@ int expm_chunk(mg_ctx* ctx, Engine& eng, int batch, double* W, const double* tau
     for (int j = 1; j < p; ++j) { src[ns] = P[j]; cf[ns] = coef(top * p + j); ++ns; }
     double diag = coef(top * p);
     if (r == 0) { src[ns] = P[p]; cf[ns] = coef(m); ++ns; }
-    MG_TRY(launch_lincomb(batch, d, R, ns, src, cf, diag, s));
+    MG_TRY(eng.lincomb(batch, R, ns, src, cf, diag));
     i_next = top - 1;
   }
   if (i_next >= 0) MG_TRY(eng.prepB(1, batch, P[p], md));
@@ -391,23 +421,27 @@ int expm_chunk(mg_ctx* ctx, Engine& eng, int batch, double* W, const double* tau
   }
   // exact trace phase e^{-i tau_b}
   if (sU != md) return MG_EINVAL;
-  if (tau) return launch_apply_phase(batch, d, (long long)d * d, tau, R, U, s);
+  if (tau) return eng.phase(batch, tau, R, U);
   return launch_copy_strided(batch, md, R, md, U, sU, s);
 }
 
 // One Newton-Schulz polar step in FP64 on a batch: Z <- Z (3I - Z^dag Z)/2.
-int reorth_batch(mg_ctx* ctx, int batch, int d, double* Z, long long sZ) {
+// Z is in the engine's storage format; the step itself runs in FP64.
+int reorth_batch(mg_ctx* ctx, Engine& eng, int batch, double* Z, long long sZ) {
+  const int d = eng.d;
   const long long md = mat_doubles(d);
-  double *G, *H;
+  double *Zf, *G, *H;
+  MG_TRY(ws(ctx, WS_NS_Z, md * batch, &Zf));
   MG_TRY(ws(ctx, WS_NS_G, md * batch, &G));
   MG_TRY(ws(ctx, WS_NS_H, md * batch, &H));
+  MG_TRY(eng.to_fp64(batch, Z, sZ, Zf, md));
   AddTerms none;
-  MG_TRY(launch_cgemm_f64(batch, d, Z, sZ, 1, Z, sZ, G, md, none, ctx->stream));
+  MG_TRY(launch_cgemm_f64(batch, d, Zf, md, 1, Zf, md, G, md, none, ctx->stream));
   const double* src[1] = {G};
   double cf[1] = {-0.5};
   MG_TRY(launch_lincomb(batch, d, H, 1, src, cf, 1.5, ctx->stream));
-  MG_TRY(launch_cgemm_f64(batch, d, Z, sZ, 0, H, md, G, md, none, ctx->stream));
-  return launch_copy_strided(batch, md, G, md, Z, sZ, ctx->stream);
+  MG_TRY(launch_cgemm_f64(batch, d, Zf, md, 0, H, md, G, md, none, ctx->stream));
+  return eng.from_fp64(batch, G, md, Z, sZ);
 }
 
 // Tree product of a batch of propagators (earliest first): *out receives a
@@ -441,7 +475,7 @@ int tree_product(mg_ctx* ctx, Engine& eng, int n, const double* U, double** out,
                                  ctx->stream));
     span *= 2;
     cnt = pairs + (cnt & 1);
-    if (reorth_span > 0 && span == reorth_span) MG_TRY(reorth_batch(ctx, cnt, d, dst, md));
+    if (reorth_span > 0 && span == reorth_span) MG_TRY(reorth_batch(ctx, eng, cnt, dst, md));
     cur = dst;
     ++level;
   }
@@ -748,14 +782,22 @@ int mg_cgemm(mg_ctx* ctx, int batch, int d, const double* A, const double* B, do
   MG_CUDA_TRY(cudaSetDevice(ctx->device));
   Engine eng{ctx, d, precision, slices};
   const long long md = mat_doubles(d);
-  const int chunk = std::min(batch, 65535);
+  const int chunk = std::min(chunk_size(ctx, d, precision, slices, batch, 1), 65535);
   for (int b0 = 0; b0 < batch; b0 += chunk) {
     int nb = std::min(chunk, batch - b0);
     MG_TRY(eng.reserve(nb));
-    MG_TRY(eng.prepA(nb, A + b0 * md, md));
-    MG_TRY(eng.prepB(0, nb, B + b0 * md, md));
+    MG_TRY(eng.prepA(nb, A + b0 * md, md, 0));
+    MG_TRY(eng.prepB(0, nb, B + b0 * md, md, 0));
     AddTerms none;
-    MG_TRY(eng.mul(nb, A + b0 * md, md, 0, B + b0 * md, md, C + b0 * md, md, none));
+    if (eng.df()) {
+      // the split product is double-float; convert into the caller's FP64 C
+      double* T;
+      MG_TRY(ws(ctx, WS_OUT, md * nb, &T));
+      MG_TRY(eng.mul(nb, A + b0 * md, md, 0, B + b0 * md, md, T, md, none));
+      MG_TRY(eng.to_fp64(nb, T, md, C + b0 * md, md));
+    } else {
+      MG_TRY(eng.mul(nb, A + b0 * md, md, 0, B + b0 * md, md, C + b0 * md, md, none));
+    }
   }
   if (precision == MG_PREC_SPLIT) return check_status(ctx);
   return MG_OK;
@@ -778,7 +820,10 @@ int mg_expm(mg_ctx* ctx, int batch, int d, const double* A, double* U, int preci
     MG_TRY(launch_shift_norm(nb, d, A + b0 * md, W, tau, nrm, reinterpret_cast<unsigned long long*>(sc), 1,
                              ctx->stream));
     ExpmStats st;
-    MG_TRY(expm_chunk(ctx, eng, nb, W, tau, nrm, U + b0 * md, md, &st));
+    double* Ue;
+    MG_TRY(ws(ctx, WS_UBUF, md * nb, &Ue));
+    MG_TRY(expm_chunk(ctx, eng, nb, W, tau, nrm, Ue, md, &st));
+    MG_TRY(eng.to_fp64(nb, Ue, md, U + b0 * md, md));
     if (squarings) {
       std::vector<int> sq(nb, st.s_applied);
       MG_CUDA_TRY(cudaMemcpyAsync(squarings + b0, sq.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, ctx->stream));
@@ -810,7 +855,14 @@ int fold_chunk(mg_ctx* ctx, Engine& eng, PropState& ps, int n, const double* U, 
   if (ps.output == MG_OUT_STATE) {
     double* tmp;
     MG_TRY(ws(ctx, WS_VEC, 2 * d + 2, &tmp));
-    MG_TRY(launch_state_chain(n, d, U, md, ps.psi, tmp + 2, reorth, ps.done, ctx->stream));
+    const double* Uf = U;
+    if (eng.df()) {
+      double* conv;
+      MG_TRY(ws(ctx, WS_NS_Z, md * n, &conv));
+      MG_TRY(eng.to_fp64(n, U, md, conv, md));
+      Uf = conv;
+    }
+    MG_TRY(launch_state_chain(n, d, Uf, md, ps.psi, tmp + 2, reorth, ps.done, ctx->stream));
     ps.done += n;
     return MG_OK;
   }
@@ -836,11 +888,11 @@ int fold_chunk(mg_ctx* ctx, Engine& eng, PropState& ps, int n, const double* U, 
     MG_TRY(launch_copy_strided(1, md, acc2, md, ps.acc, md, ctx->stream));
   }
   ps.done += n;
-  if (reorth > 0 && (ps.done / reorth) != ((ps.done - n) / reorth)) MG_TRY(reorth_batch(ctx, 1, d, ps.acc, md));
+  if (reorth > 0 && (ps.done / reorth) != ((ps.done - n) / reorth)) MG_TRY(reorth_batch(ctx, eng, 1, ps.acc, md));
   return MG_OK;
 }
 
-int begin_prop(mg_ctx* ctx, PropState& ps, const double* in, int flags) {
+int begin_prop(mg_ctx* ctx, Engine& eng, PropState& ps, const double* in, int flags) {
   const int d = ps.d;
   const long long md = mat_doubles(d);
   const cudaMemcpyKind kind = (flags & MG_FLAG_HOST_PTRS) ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
@@ -851,7 +903,10 @@ int begin_prop(mg_ctx* ctx, PropState& ps, const double* in, int flags) {
   } else {
     MG_TRY(ws(ctx, WS_ACC, md, &ps.acc));
     if (in) {
-      MG_CUDA_TRY(cudaMemcpyAsync(ps.acc, in, sizeof(double) * md, kind, ctx->stream));
+      double* t;
+      MG_TRY(ws(ctx, WS_OUT, md, &t));
+      MG_CUDA_TRY(cudaMemcpyAsync(t, in, sizeof(double) * md, kind, ctx->stream));
+      MG_TRY(eng.from_fp64(1, t, md, ps.acc, md));
       ps.acc_init = true;
     }
   }
@@ -862,13 +917,15 @@ int finish_prop(mg_ctx* ctx, Engine& eng, PropState& ps, double* out, int flags,
   const int d = ps.d;
   const long long md = mat_doubles(d);
   const cudaMemcpyKind kind = (flags & MG_FLAG_HOST_PTRS) ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+  double* accf = nullptr;   // FP64 propagator
   if (ps.output == MG_OUT_STATE) {
     MG_CUDA_TRY(cudaMemcpyAsync(out, ps.psi, sizeof(double) * 2 * d, kind, ctx->stream));
   } else {
-    if (!ps.acc_init) MG_TRY(launch_identity(1, d, ps.acc, ctx->stream));
-    MG_CUDA_TRY(cudaMemcpyAsync(out, ps.acc, sizeof(double) * md, kind, ctx->stream));
+    if (!ps.acc_init) MG_TRY(eng.identity(1, ps.acc));
+    MG_TRY(ws(ctx, WS_OUT, md, &accf));
+    MG_TRY(eng.to_fp64(1, ps.acc, md, accf, md));
+    MG_CUDA_TRY(cudaMemcpyAsync(out, accf, sizeof(double) * md, kind, ctx->stream));
   }
-  (void)eng;
   if (rep) {
     double* sc;
     MG_TRY(small_scratch(ctx, 2, &sc));
@@ -878,7 +935,7 @@ int finish_prop(mg_ctx* ctx, Engine& eng, PropState& ps, double* out, int flags,
       double* G;
       MG_TRY(ws(ctx, WS_NS_G, md, &G));
       AddTerms none;
-      MG_TRY(launch_cgemm_f64(1, d, ps.acc, md, 1, ps.acc, md, G, md, none, ctx->stream));
+      MG_TRY(launch_cgemm_f64(1, d, accf, md, 1, accf, md, G, md, none, ctx->stream));
       MG_TRY(launch_max_identity_defect(1, d, G, sc, ctx->stream));
     }
     MG_CUDA_TRY(cudaMemcpyAsync(&rep->unitarity_defect, sc, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
@@ -904,7 +961,7 @@ int mg_evolve(mg_plan* p, int output, const double* in, double* out, int reorth_
   PropState ps;
   ps.output = output;
   ps.d = d;
-  MG_TRY(begin_prop(ctx, ps, in, flags));
+  MG_TRY(begin_prop(ctx, eng, ps, in, flags));
   int align = 1;
   if (output == MG_OUT_PROPAGATOR && reorth_every > 1) align = reorth_every;
   const int chunk = chunk_size(ctx, d, p->precision, p->L, p->N, align);
@@ -953,13 +1010,20 @@ int mg_propagate(mg_ctx* ctx, int N, int d, const double* U, int output, const d
   PropState ps;
   ps.output = output;
   ps.d = d;
-  MG_TRY(begin_prop(ctx, ps, in, 0));
+  MG_TRY(begin_prop(ctx, eng, ps, in, 0));
   const long long md = mat_doubles(d);
   int align = (output == MG_OUT_PROPAGATOR && reorth_every > 1) ? reorth_every : 1;
   const int chunk = chunk_size(ctx, d, precision, slices, N, align);
   for (int n0 = 0; n0 < N; n0 += chunk) {
     const int nb = std::min(chunk, N - n0);
-    MG_TRY(fold_chunk(ctx, eng, ps, nb, U + (long long)n0 * md, reorth_every));
+    const double* Uc = U + (long long)n0 * md;
+    if (eng.df()) {
+      double* Ue;
+      MG_TRY(ws(ctx, WS_UBUF, md * nb, &Ue));
+      MG_TRY(eng.from_fp64(nb, Uc, md, Ue, md));
+      Uc = Ue;
+    }
+    MG_TRY(fold_chunk(ctx, eng, ps, nb, Uc, reorth_every));
   }
   MG_TRY(finish_prop(ctx, eng, ps, out, 0, nullptr));
   if (precision == MG_PREC_SPLIT) return check_status(ctx);

@@ -118,8 +118,10 @@ int launch_max_identity_defect(int batch, int d, const double* G, double* out_de
 int split_beta_for(int d);
 size_t split_a_bytes(int d, int L, int batch);
 size_t split_b_bytes(int d, int L, int batch);
-int split_slice_a(int d, int L, int batch, const double* A, long long sA, void* buf, cudaStream_t s);
-int split_slice_b(int d, int L, int batch, const double* B, long long sB, void* buf, cudaStream_t s);
+// Inputs are FP64 (in_df32 = 0) or double-float (in_df32 = 1) complex matrices; the
+// product C and the addends are double-float (see df32.cuh).
+int split_slice_a(int d, int L, int batch, const double* A, long long sA, int in_df32, void* buf, cudaStream_t s);
+int split_slice_b(int d, int L, int batch, const double* B, long long sB, int in_df32, void* buf, cudaStream_t s);
 int split_gemm(int d, int L, int batch, const void* abuf, const void* bbuf, double* C, long long sC,
                const AddTerms& add, int* status, cudaStream_t s);
 
@@ -127,5 +129,14 @@ int split_gemm(int d, int L, int batch, const void* abuf, const void* bbuf, doub
 int launch_state_chain(int n_steps, int d, const double* U, long long sU, double* psi, double* tmp,
                        int reorth_every, int step_offset, cudaStream_t s);
 int launch_norm_defect(int d, const double* psi, double* out, cudaStream_t s);
+
+// Double-float (DF32) elementwise kernels of the split path; see elementwise.cu.
+int launch_scale_minus_i_df(int batch, int d, const double* src_fp64, double* dst_df, int sq, cudaStream_t s);
+int launch_lincomb_df(int batch, int d, double* dst, int nsrc, const double* const* src, const double* coef,
+                      double diag, cudaStream_t s);
+int launch_apply_phase_df(int batch, int d, const double* phase, const double* src, double* dst, cudaStream_t s);
+int launch_identity_df(int batch, int d, double* dst, cudaStream_t s);
+int launch_df_to_fp64(int batch, int d, const double* src, long long ss, double* dst, long long ds, cudaStream_t s);
+int launch_fp64_to_df(int batch, int d, const double* src, long long ss, double* dst, long long ds, cudaStream_t s);
 
 }  // namespace mg

@@ -3,6 +3,9 @@
 // powers for the Taylor polynomial, the exact trace-shift phase e^{-i tau},
 // identities and strided copies, and the FP64 unitarity/norm diagnostics.
 #include "common.cuh"
+#include "df32.cuh"
+
+#include <cmath>
 
 namespace mg {
 
@@ -153,6 +156,150 @@ int launch_max_identity_defect(int batch, int d, const double* G, double* out_de
   MG_CUDA_TRY(cudaMemsetAsync(out_dev, 0, sizeof(double), s));
   identity_defect_kernel<<<grid_for((long long)d * d * batch), 256, 0, s>>>(d, batch, G, out_dev);
   return check_launch("identity_defect_kernel");
+}
+
+// ---------------------------------------------------------------------------
+// double-float (DF32) versions used by the split-precision path
+// ---------------------------------------------------------------------------
+// X = (-i) 2^{-sq} src: FP64 in, DF32 out
+__global__ void scale_minus_i_df_kernel(long long total, const double* __restrict__ src, float4* __restrict__ dst,
+                                        double f) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const double2 v = reinterpret_cast<const double2*>(src)[e];
+    const df32 re = df_from_double(f * v.y), im = df_from_double(-f * v.x);
+    dst[e] = make_float4(re.hi, re.lo, im.hi, im.lo);
+  }
+}
+
+int launch_scale_minus_i_df(int batch, int d, const double* src_fp64, double* dst_df, int sq, cudaStream_t s) {
+  const long long total = (long long)d * d * batch;
+  const double f = std::ldexp(1.0, -sq);
+  scale_minus_i_df_kernel<<<grid_for(total), 256, 0, s>>>(total, src_fp64, reinterpret_cast<float4*>(dst_df), f);
+  return check_launch("scale_minus_i_df_kernel");
+}
+
+struct LincombDfArgs {
+  const float4* src[4];
+  df32 coef[4];
+};
+
+__global__ void lincomb_df_kernel(int d, long long total, int nsrc, LincombDfArgs a, df32 diag,
+                                  float4* __restrict__ dst) {
+  const long long per = (long long)d * d;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    df32 re{0.f, 0.f}, im{0.f, 0.f};
+    for (int m = 0; m < nsrc; ++m) {
+      const float4 v = a.src[m][e];
+      re = df_add(re, df_mul(df32{v.x, v.y}, a.coef[m]));
+      im = df_add(im, df_mul(df32{v.z, v.w}, a.coef[m]));
+    }
+    const long long r = e % per;
+    if (r / d == r % d) re = df_add(re, diag);
+    dst[e] = make_float4(re.hi, re.lo, im.hi, im.lo);
+  }
+}
+
+int launch_lincomb_df(int batch, int d, double* dst, int nsrc, const double* const* src, const double* coef,
+                      double diag, cudaStream_t s) {
+  if (nsrc < 0 || nsrc > 4) return MG_EINVAL;
+  LincombDfArgs a{};
+  for (int m = 0; m < nsrc; ++m) {
+    a.src[m] = reinterpret_cast<const float4*>(src[m]);
+    a.coef[m] = df_from_double(coef[m]);
+  }
+  const long long total = (long long)d * d * batch;
+  lincomb_df_kernel<<<grid_for(total), 256, 0, s>>>(d, total, nsrc, a, df_from_double(diag),
+                                                    reinterpret_cast<float4*>(dst));
+  return check_launch("lincomb_df_kernel");
+}
+
+// dst_b = e^{-i phase_b} src_b in DF32; the phase factor is formed once per block in FP64
+__global__ void apply_phase_df_kernel(long long per_item, const double* __restrict__ phase,
+                                      const float4* __restrict__ src, float4* __restrict__ dst) {
+  __shared__ df32 cs_sn[2];
+  const int b = blockIdx.y;
+  if (threadIdx.x == 0) {
+    double sn, cs;
+    sincos(phase[b], &sn, &cs);
+    cs_sn[0] = df_from_double(cs);
+    cs_sn[1] = df_from_double(sn);
+  }
+  __syncthreads();
+  const df32 c = cs_sn[0], sn = cs_sn[1], msn = df_neg(cs_sn[1]);
+  const float4* sb = src + (long long)b * per_item;
+  float4* db = dst + (long long)b * per_item;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < per_item;
+       e += (long long)gridDim.x * blockDim.x) {
+    const float4 v = sb[e];
+    const df32 x{v.x, v.y}, y{v.z, v.w};
+    // (c - i s)(x + i y) = (c x + s y) + i (c y - s x)
+    const df32 re = df_add(df_mul(x, c), df_mul(y, sn));
+    const df32 im = df_add(df_mul(y, c), df_mul(x, msn));
+    db[e] = make_float4(re.hi, re.lo, im.hi, im.lo);
+  }
+}
+
+int launch_apply_phase_df(int batch, int d, const double* phase, const double* src, double* dst, cudaStream_t s) {
+  if (batch > 65535) return MG_EUNSUPPORTED;
+  const long long per = (long long)d * d;
+  long long bx = (per + 1023) / 1024;
+  if (bx > 64) bx = 64;
+  apply_phase_df_kernel<<<dim3((unsigned)bx, batch), 256, 0, s>>>(per, phase, reinterpret_cast<const float4*>(src),
+                                                                  reinterpret_cast<float4*>(dst));
+  return check_launch("apply_phase_df_kernel");
+}
+
+__global__ void identity_df_kernel(int d, long long total, float4* __restrict__ dst) {
+  const long long per = (long long)d * d;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long r = e % per;
+    dst[e] = make_float4((r / d == r % d) ? 1.f : 0.f, 0.f, 0.f, 0.f);
+  }
+}
+
+int launch_identity_df(int batch, int d, double* dst, cudaStream_t s) {
+  const long long total = (long long)d * d * batch;
+  identity_df_kernel<<<grid_for(total), 256, 0, s>>>(d, total, reinterpret_cast<float4*>(dst));
+  return check_launch("identity_df_kernel");
+}
+
+__global__ void df_to_fp64_kernel(long long per, long long total, const float4* __restrict__ src, long long ss,
+                                  double2* __restrict__ dst, long long ds) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long b = e / per, r = e % per;
+    const float4 v = src[b * ss + r];
+    dst[b * ds + r] = make_double2((double)v.x + (double)v.y, (double)v.z + (double)v.w);
+  }
+}
+
+__global__ void fp64_to_df_kernel(long long per, long long total, const double2* __restrict__ src, long long ss,
+                                  float4* __restrict__ dst, long long ds) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long b = e / per, r = e % per;
+    const double2 v = src[b * ss + r];
+    const df32 re = df_from_double(v.x), im = df_from_double(v.y);
+    dst[b * ds + r] = make_float4(re.hi, re.lo, im.hi, im.lo);
+  }
+}
+
+// strides in doubles (two per complex element in either format)
+int launch_df_to_fp64(int batch, int d, const double* src, long long ss, double* dst, long long ds, cudaStream_t s) {
+  const long long per = (long long)d * d, total = per * batch;
+  df_to_fp64_kernel<<<grid_for(total), 256, 0, s>>>(per, total, reinterpret_cast<const float4*>(src), ss / 2,
+                                                    reinterpret_cast<double2*>(dst), ds / 2);
+  return check_launch("df_to_fp64_kernel");
+}
+
+int launch_fp64_to_df(int batch, int d, const double* src, long long ss, double* dst, long long ds, cudaStream_t s) {
+  const long long per = (long long)d * d, total = per * batch;
+  fp64_to_df_kernel<<<grid_for(total), 256, 0, s>>>(per, total, reinterpret_cast<const double2*>(src), ss / 2,
+                                                    reinterpret_cast<float4*>(dst), ds / 2);
+  return check_launch("fp64_to_df_kernel");
 }
 
 }  // namespace mg

@@ -56,6 +56,16 @@ __device__ __forceinline__ unsigned long long nonneg_bits(double x) {
   return (unsigned long long)__double_as_longlong(x);
 }
 
+// |x + i y| rounded up: an FP32 magnitude widened by 2^-20 relative, so that the
+// FP64-accumulated column sums bound ||.||_1 from above (the norm only selects
+// the squaring count, for which any upper bound is valid) without a long chain
+// of FP64 instructions per element on GB300's narrow FP64 pipe.
+__device__ __forceinline__ double magnitude_upper(double x, double y) {
+  const float xf = (float)x, yf = (float)y;
+  const float m = sqrtf(fmaf(xf, xf, yf * yf));
+  return (double)(m * (1.0f + 9.5367431640625e-07f)) + 1e-300;
+}
+
 constexpr int OMEGA_NB = 8;      // intervals per CTA (register blocking)
 constexpr int OMEGA_COLS = 32;   // columns per CTA (one per lane)
 constexpr int OMEGA_WARPS = 8;   // row phases per CTA
@@ -122,7 +132,7 @@ build_omega_kernel(int N, int d, int K, double dt, const double* __restrict__ H0
         if (b < nb) {
           double r = re[b];
           if (i == j) r -= taus[b];
-          colsum[b] += hypot(r, im[b]);
+          colsum[b] += magnitude_upper(r, im[b]);
           double2 o;
           o.x = write_shifted ? r : re[b];
           o.y = im[b];

@@ -35,6 +35,7 @@
 // Every mbarrier wait is bounded by a wall-clock deadline; a wait that gives up
 // records MG_DEV_TIMEOUT in the status word and the CTA winds down.
 #include "common.cuh"
+#include "df32.cuh"
 
 #include <cuda.h>
 #include <cudaTypedefs.h>
@@ -93,11 +94,17 @@ SplitGeom split_geom(int d, int L) {
 //     a ~= 2^{E+1-beta} sum_s v_s,   v_s = q_s 2^{-beta s}  (exact in BF16),
 // with an error below 2^{E - beta L} (the rounding of X).
 
-// exponent E of |a| with |a| < 2^E (biased exponent - 1022); zero and subnormals -> INT_MIN/2
+// exponent E of |a| with |a| < 2^E (biased exponent - 1022); zero and subnormals -> -2^29
 __device__ __forceinline__ int exp_bound(double a) {
   const long long bits = __double_as_longlong(a);
   const int bexp = (int)((bits >> 52) & 0x7FF);
   return bexp == 0 ? -(1 << 29) : bexp - 1022;
+}
+// the same for a double-float hi + lo (|hi + lo| < 2^E whenever |hi| < 2^E)
+__device__ __forceinline__ int exp_bound(df32 a) {
+  const int bits = __float_as_int(a.hi);
+  const int bexp = (bits >> 23) & 0xFF;
+  return bexp == 0 ? -(1 << 29) : bexp - 126;
 }
 
 // round(a * 2^sh) as a signed 64-bit integer (sh chosen so that the result fits)
@@ -113,9 +120,43 @@ __device__ __forceinline__ long long fixed_point(double a, int sh) {
   else X = 0;
   return bits < 0 ? -X : X;
 }
+__device__ __forceinline__ long long fixed_point(float a, int sh) {
+  const int bits = __float_as_int(a);
+  const int bexp = (bits >> 23) & 0xFF;
+  if (bexp == 0) return 0;
+  const long long mant = (long long)((bits & 0x7FFFFF) | 0x800000);          // a = mant 2^{bexp-150}
+  const int shift = bexp - 150 + sh;
+  long long X;
+  if (shift >= 0) X = shift < 40 ? (mant << shift) : 0;
+  else if (shift > -30) X = (mant + (1LL << (-shift - 1))) >> (-shift);
+  else X = 0;
+  return bits < 0 ? -X : X;
+}
+__device__ __forceinline__ long long fixed_point(df32 a, int sh) {
+  return fixed_point(a.hi, sh) + fixed_point(a.lo, sh);
+}
 
-template <int L>
-__device__ __forceinline__ void make_digits(double a, int sh, int beta, __nv_bfloat16 (&v)[L]) {
+// one complex element of an FP64 or DF32 matrix (16 bytes either way)
+struct c64 { double re, im; };
+struct cdf { df32 re, im; };
+template <typename T> struct Elem;
+template <> struct Elem<double> {
+  using type = c64;
+  __device__ __forceinline__ static type load(const double* base, long long idx) {
+    const double2 v = reinterpret_cast<const double2*>(base)[idx];
+    return {v.x, v.y};
+  }
+};
+template <> struct Elem<df32> {
+  using type = cdf;
+  __device__ __forceinline__ static type load(const double* base, long long idx) {
+    const float4 v = reinterpret_cast<const float4*>(base)[idx];
+    return {{v.x, v.y}, {v.z, v.w}};
+  }
+};
+
+template <int L, typename V>
+__device__ __forceinline__ void make_digits(V a, int sh, int beta, __nv_bfloat16 (&v)[L]) {
   long long X = fixed_point(a, sh);
   const long long half = 1LL << (beta - 1), mask = (1LL << beta) - 1;
   int q[L];
@@ -134,10 +175,12 @@ __device__ __forceinline__ void make_digits(double a, int sh, int beta, __nv_bfl
 }
 
 // A digits: rows of [Re A | Im A].  grid (ceil(Mp/8), batch), block 256 (one warp per row).
-template <int L>
+// T = double (FP64 input) or df32 (double-float input); strides count doubles.
+template <int L, typename T>
 __global__ void __launch_bounds__(256)
 slice_a_kernel(int d, int Kp, int Mp, int beta, const double* __restrict__ A, long long sA,
                __nv_bfloat16* __restrict__ out, int* __restrict__ ea) {
+  using E_ = Elem<T>;
   const int lane = threadIdx.x & 31;
   const int row = blockIdx.x * 8 + (threadIdx.x >> 5);
   const int b = blockIdx.y;
@@ -151,21 +194,22 @@ slice_a_kernel(int d, int Kp, int Mp, int beta, const double* __restrict__ A, lo
       for (int s = 0; s < L; ++s) o[s * slice_stride + k] = zero;
     return;
   }
-  const double2* a = reinterpret_cast<const double2*>(A + b * sA) + (long long)row * d;
+  const double* a = A + b * sA;
+  const long long r0 = (long long)row * d;
   int E = -(1 << 29);
   for (int k = lane; k < d; k += 32) {
-    const double2 v = a[k];
-    E = max(E, max(exp_bound(v.x), exp_bound(v.y)));
+    const auto v = E_::load(a, r0 + k);
+    E = max(E, max(exp_bound(v.re), exp_bound(v.im)));
   }
   for (int o2 = 16; o2 > 0; o2 >>= 1) E = max(E, __shfl_xor_sync(0xffffffffu, E, o2));
   if (E < -(1 << 28)) E = 0;   // all-zero row
   if (lane == 0) ea[(long long)b * Mp + row] = E;
   const int sh = beta * L - E - 1;
   for (int k = lane; k < d; k += 32) {
-    const double2 v = a[k];
+    const auto v = E_::load(a, r0 + k);
     __nv_bfloat16 dr[L], di[L];
-    make_digits<L>(v.x, sh, beta, dr);
-    make_digits<L>(v.y, sh, beta, di);
+    make_digits<L>(v.re, sh, beta, dr);
+    make_digits<L>(v.im, sh, beta, di);
 #pragma unroll
     for (int s = 0; s < L; ++s) {
       o[s * slice_stride + k] = dr[s];
@@ -182,17 +226,19 @@ slice_a_kernel(int d, int Kp, int Mp, int beta, const double* __restrict__ A, lo
 // rows 128t + 64 + r hold [Im B[:, j] | Re B[:, j]] (j = 64t + r).
 // grid (ceil(d/64), batch), block 256.
 constexpr int SB_KCHUNK = 32;
-template <int L>
+template <int L, typename T>
 __global__ void __launch_bounds__(256)
 slice_b_kernel(int d, int Kp, int Np, int beta, const double* __restrict__ B, long long sB,
                __nv_bfloat16* __restrict__ out, int* __restrict__ eb) {
-  __shared__ double2 tile[SB_KCHUNK][SG_BNC + 1];
+  using E_ = Elem<T>;
+  using V = typename E_::type;
+  __shared__ V tile[SB_KCHUNK][SG_BNC + 1];
   __shared__ int red[4][SG_BNC];
   __shared__ int shift[SG_BNC];
   const int t = blockIdx.x, b = blockIdx.y;
   const int j0 = t * SG_BNC;
   const int tid = threadIdx.x;
-  const double2* Bb = reinterpret_cast<const double2*>(B + b * sB);
+  const double* Bb = B + b * sB;
   const long long slice_stride = (long long)Np * Kp;
   __nv_bfloat16* ob = out + (long long)b * L * slice_stride;
 
@@ -202,8 +248,8 @@ slice_b_kernel(int d, int Kp, int Np, int beta, const double* __restrict__ B, lo
     int E = -(1 << 29);
     if (j0 + c < d)
       for (int k = g; k < d; k += 4) {
-        const double2 v = Bb[(long long)k * d + j0 + c];
-        E = max(E, max(exp_bound(v.x), exp_bound(v.y)));
+        const V v = E_::load(Bb, (long long)k * d + j0 + c);
+        E = max(E, max(exp_bound(v.re), exp_bound(v.im)));
       }
     red[g][c] = E;
     __syncthreads();
@@ -220,8 +266,8 @@ slice_b_kernel(int d, int Kp, int Np, int beta, const double* __restrict__ B, lo
   for (int k0 = 0; k0 < d; k0 += SB_KCHUNK) {
     for (int e = tid; e < SB_KCHUNK * SG_BNC; e += 256) {
       int kk = e / SG_BNC, c = e % SG_BNC;
-      double2 v = make_double2(0.0, 0.0);
-      if (k0 + kk < d && j0 + c < d) v = Bb[(long long)(k0 + kk) * d + j0 + c];
+      V v{};
+      if (k0 + kk < d && j0 + c < d) v = E_::load(Bb, (long long)(k0 + kk) * d + j0 + c);
       tile[kk][c] = v;
     }
     __syncthreads();
@@ -229,10 +275,10 @@ slice_b_kernel(int d, int Kp, int Np, int beta, const double* __restrict__ B, lo
       int kk = e % SB_KCHUNK, r = e / SB_KCHUNK;
       int k = k0 + kk;
       if (k >= d) continue;
-      const double2 v = tile[kk][r];
+      const V v = tile[kk][r];
       __nv_bfloat16 dr[L], di[L];
-      make_digits<L>(v.x, shift[r], beta, dr);
-      make_digits<L>(v.y, shift[r], beta, di);
+      make_digits<L>(v.re, shift[r], beta, dr);
+      make_digits<L>(v.im, shift[r], beta, di);
       __nv_bfloat16* row_re = ob + (long long)(t * 2 * SG_BNC + r) * Kp;          // [Re | -Im]
       __nv_bfloat16* row_im = ob + (long long)(t * 2 * SG_BNC + SG_BNC + r) * Kp; // [Im | Re]
 #pragma unroll
@@ -355,38 +401,20 @@ constexpr uint64_t SG_WAIT_NS = 4000000000ull;   // 4 s: far beyond any legitima
 // The four level accumulators hold (in units of the leading digit product)
 //   g0: integers, g1: multiples of 2^-beta, g2: multiples of 2^-2beta (all exact),
 //   g3: the rounded remainder.
-// They are combined exactly in 64-bit fixed point with `fx` extra fraction bits
-// below 2^-3beta, converted to FP64 once and scaled by 2^e_total through the
-// exponent field: integer work instead of GB300's narrow FP64 pipe.
-__device__ __forceinline__ float pow2f(int k) { return __int_as_float((127 + k) << 23); }
-
-__device__ __forceinline__ double scale_pow2(double x, int e) {
-  const long long bits = __double_as_longlong(x);
-  const int bexp = (int)((bits >> 52) & 0x7FF);
-  if (bexp == 0) return x;   // zero (G is an integer: no subnormal inputs)
-  const int ne = bexp + e;
-  if (ne > 0 && ne < 2047) return __longlong_as_double(bits + ((long long)e << 52));
-  return ldexp(x, e);
-}
-
-__device__ __forceinline__ double combine_levels(uint32_t u0, uint32_t u1, uint32_t u2, uint32_t u3, int beta,
-                                                 int fx, int e_total) {
-  const long long i0 = __float2ll_rn(__uint_as_float(u0));
-  const long long i1 = __float2ll_rn(__uint_as_float(u1) * pow2f(beta));
-  const long long i2 = __float2ll_rn(__uint_as_float(u2) * pow2f(2 * beta));
-  const long long i3 = __float2ll_rn(__uint_as_float(u3) * pow2f(3 * beta + fx));
-  const long long G = i0 * (1LL << (3 * beta + fx)) + i1 * (1LL << (2 * beta + fx)) +
-                      i2 * (1LL << (beta + fx)) + i3;
-  return scale_pow2(__ll2double_rn(G), e_total);
+// Their sum is formed in double-float with error-free FP32 transformations and
+// scaled by 2^k exactly: no instruction of GB300's narrow FP64 pipe.
+__device__ __forceinline__ df32 combine_levels(uint32_t u0, uint32_t u1, uint32_t u2, uint32_t u3, int k) {
+  const df32 a = two_sum(__uint_as_float(u0), __uint_as_float(u1));
+  const df32 b = two_sum(__uint_as_float(u2), __uint_as_float(u3));
+  return df_ldexp(df_add(a, b), k);
 }
 
 struct SplitEpi {
-  const double* add_src[3];
-  double add_coef[3];
-  long long add_stride;
+  const double* add_src[3];   // DF32 matrices (float4 per complex element)
+  df32 add_coef[3];
+  long long add_stride;       // in doubles
   int add_n;
-  double diag;
-  double scale;
+  df32 diag;
 };
 
 template <int L, int STAGES>
@@ -499,11 +527,10 @@ split_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
       const int row = mt * SG_BM + q * 32 + lane;
       const bool row_ok = row < d;
       const int Ea = row_ok ? ea[(long long)b * Mp + row] : 0;
-      const int fx_bits = 37 - 3 * beta;   // fraction bits kept below the level-3 unit
       const double* addp[3];
 #pragma unroll
       for (int m = 0; m < 3; ++m) addp[m] = epi.add_src[m] ? epi.add_src[m] + b * epi.add_stride : nullptr;
-      double2* Cb = reinterpret_cast<double2*>(C + b * sC);
+      float4* Cb = reinterpret_cast<float4*>(C + b * sC);
       const uint32_t lane_base = tmem + ((uint32_t)(q * 32) << 16);
       for (int jc = 0; jc < SG_BNC; jc += 8) {
         uint32_t re_acc[SG_GROUPS][8], im_acc[SG_GROUPS][8];
@@ -518,23 +545,17 @@ split_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
           for (int jj = 0; jj < 8; ++jj) {
             const int j = nt * SG_BNC + jc + jj;
             if (j < d) {
-              const int e_total = Ea + eb[(long long)b * (Np / 2) + j] + 2 - 5 * beta - fx_bits;
-              double re = combine_levels(re_acc[0][jj], re_acc[1][jj], re_acc[2][jj], re_acc[3][jj], beta,
-                                         fx_bits, e_total);
-              double im = combine_levels(im_acc[0][jj], im_acc[1][jj], im_acc[2][jj], im_acc[3][jj], beta,
-                                         fx_bits, e_total);
-              if (epi.scale != 1.0) {
-                re *= epi.scale;
-                im *= epi.scale;
-              }
+              const int k = Ea + eb[(long long)b * (Np / 2) + j] + 2 - 2 * beta;
+              df32 re = combine_levels(re_acc[0][jj], re_acc[1][jj], re_acc[2][jj], re_acc[3][jj], k);
+              df32 im = combine_levels(im_acc[0][jj], im_acc[1][jj], im_acc[2][jj], im_acc[3][jj], k);
               const long long off = (long long)row * d + j;
               for (int m = 0; m < epi.add_n; ++m) {
-                double2 p = reinterpret_cast<const double2*>(addp[m])[off];
-                re = fma(epi.add_coef[m], p.x, re);
-                im = fma(epi.add_coef[m], p.y, im);
+                const float4 p = reinterpret_cast<const float4*>(addp[m])[off];
+                re = df_add(re, df_mul(df32{p.x, p.y}, epi.add_coef[m]));
+                im = df_add(im, df_mul(df32{p.z, p.w}, epi.add_coef[m]));
               }
-              if (row == j) re += epi.diag;
-              Cb[off] = make_double2(re, im);
+              if (row == j) re = df_add(re, epi.diag);
+              Cb[off] = make_float4(re.hi, re.lo, im.hi, im.lo);
             }
           }
         }
@@ -611,19 +632,41 @@ static int launch_split_gemm_L(const SplitGeom& g, int batch, const __nv_bfloat1
   return check_launch("split_gemm_kernel");
 }
 
-template <int L>
-static int launch_slicers_L(const SplitGeom& g, int batch, const double* A, long long sA, __nv_bfloat16* Ad,
-                            int* ea, const double* B, long long sB, __nv_bfloat16* Bd, int* eb,
-                            cudaStream_t s) {
+template <int L, typename T>
+static int launch_slicers_LT(const SplitGeom& g, int batch, const double* A, long long sA, __nv_bfloat16* Ad,
+                             int* ea, const double* B, long long sB, __nv_bfloat16* Bd, int* eb, cudaStream_t s) {
   if (A) {
-    slice_a_kernel<L><<<dim3(g.Mp / 8, batch), 256, 0, s>>>(g.d, g.Kp, g.Mp, g.beta, A, sA, Ad, ea);
+    slice_a_kernel<L, T><<<dim3(g.Mp / 8, batch), 256, 0, s>>>(g.d, g.Kp, g.Mp, g.beta, A, sA, Ad, ea);
     MG_TRY(check_launch("slice_a_kernel"));
   }
   if (B) {
-    slice_b_kernel<L><<<dim3(ceil_div(g.d, SG_BNC), batch), 256, 0, s>>>(g.d, g.Kp, g.Np, g.beta, B, sB, Bd, eb);
+    slice_b_kernel<L, T><<<dim3(ceil_div(g.d, SG_BNC), batch), 256, 0, s>>>(g.d, g.Kp, g.Np, g.beta, B, sB, Bd, eb);
     MG_TRY(check_launch("slice_b_kernel"));
   }
   return MG_OK;
+}
+
+template <int L>
+static int launch_slicers_L(const SplitGeom& g, int batch, int in_df32, const double* A, long long sA,
+                            __nv_bfloat16* Ad, int* ea, const double* B, long long sB, __nv_bfloat16* Bd, int* eb,
+                            cudaStream_t s) {
+  if (in_df32) return launch_slicers_LT<L, df32>(g, batch, A, sA, Ad, ea, B, sB, Bd, eb, s);
+  return launch_slicers_LT<L, double>(g, batch, A, sA, Ad, ea, B, sB, Bd, eb, s);
+}
+
+static int launch_slicers(const SplitGeom& g, int batch, int in_df32, const double* A, long long sA,
+                          __nv_bfloat16* Ad, int* ea, const double* B, long long sB, __nv_bfloat16* Bd, int* eb,
+                          cudaStream_t s) {
+  switch (g.L) {
+    case 2: return launch_slicers_L<2>(g, batch, in_df32, A, sA, Ad, ea, B, sB, Bd, eb, s);
+    case 3: return launch_slicers_L<3>(g, batch, in_df32, A, sA, Ad, ea, B, sB, Bd, eb, s);
+    case 4: return launch_slicers_L<4>(g, batch, in_df32, A, sA, Ad, ea, B, sB, Bd, eb, s);
+    case 5: return launch_slicers_L<5>(g, batch, in_df32, A, sA, Ad, ea, B, sB, Bd, eb, s);
+    case 6: return launch_slicers_L<6>(g, batch, in_df32, A, sA, Ad, ea, B, sB, Bd, eb, s);
+    case 7: return launch_slicers_L<7>(g, batch, in_df32, A, sA, Ad, ea, B, sB, Bd, eb, s);
+    case 8: return launch_slicers_L<8>(g, batch, in_df32, A, sA, Ad, ea, B, sB, Bd, eb, s);
+  }
+  return MG_EINVAL;
 }
 
 // Public-to-the-library entry points ------------------------------------------
@@ -637,44 +680,27 @@ size_t split_b_bytes(int d, int L, int batch) {
   return (size_t)g.b_item_elems() * 2 * batch + (size_t)(g.Np / 2) * 4 * batch;
 }
 
-// A-side digits of a batch: layout [digits | exponents] in one buffer.
-int split_slice_a(int d, int L, int batch, const double* A, long long sA, void* buf, cudaStream_t s) {
+// A-side digits of a batch (FP64 or DF32 input): layout [digits | exponents] in one buffer.
+int split_slice_a(int d, int L, int batch, const double* A, long long sA, int in_df32, void* buf, cudaStream_t s) {
   SplitGeom g = split_geom(d, L);
   __nv_bfloat16* Ad = reinterpret_cast<__nv_bfloat16*>(buf);
   int* ea = reinterpret_cast<int*>(Ad + g.a_item_elems() * batch);
-  switch (L) {
-    case 2: return launch_slicers_L<2>(g, batch, A, sA, Ad, ea, nullptr, 0, nullptr, nullptr, s);
-    case 3: return launch_slicers_L<3>(g, batch, A, sA, Ad, ea, nullptr, 0, nullptr, nullptr, s);
-    case 4: return launch_slicers_L<4>(g, batch, A, sA, Ad, ea, nullptr, 0, nullptr, nullptr, s);
-    case 5: return launch_slicers_L<5>(g, batch, A, sA, Ad, ea, nullptr, 0, nullptr, nullptr, s);
-    case 6: return launch_slicers_L<6>(g, batch, A, sA, Ad, ea, nullptr, 0, nullptr, nullptr, s);
-    case 7: return launch_slicers_L<7>(g, batch, A, sA, Ad, ea, nullptr, 0, nullptr, nullptr, s);
-    case 8: return launch_slicers_L<8>(g, batch, A, sA, Ad, ea, nullptr, 0, nullptr, nullptr, s);
-  }
-  return MG_EINVAL;
+  return launch_slicers(g, batch, in_df32, A, sA, Ad, ea, nullptr, 0, nullptr, nullptr, s);
 }
 
-int split_slice_b(int d, int L, int batch, const double* B, long long sB, void* buf, cudaStream_t s) {
+int split_slice_b(int d, int L, int batch, const double* B, long long sB, int in_df32, void* buf, cudaStream_t s) {
   SplitGeom g = split_geom(d, L);
   __nv_bfloat16* Bd = reinterpret_cast<__nv_bfloat16*>(buf);
   int* eb = reinterpret_cast<int*>(Bd + g.b_item_elems() * batch);
-  switch (L) {
-    case 2: return launch_slicers_L<2>(g, batch, nullptr, 0, nullptr, nullptr, B, sB, Bd, eb, s);
-    case 3: return launch_slicers_L<3>(g, batch, nullptr, 0, nullptr, nullptr, B, sB, Bd, eb, s);
-    case 4: return launch_slicers_L<4>(g, batch, nullptr, 0, nullptr, nullptr, B, sB, Bd, eb, s);
-    case 5: return launch_slicers_L<5>(g, batch, nullptr, 0, nullptr, nullptr, B, sB, Bd, eb, s);
-    case 6: return launch_slicers_L<6>(g, batch, nullptr, 0, nullptr, nullptr, B, sB, Bd, eb, s);
-    case 7: return launch_slicers_L<7>(g, batch, nullptr, 0, nullptr, nullptr, B, sB, Bd, eb, s);
-    case 8: return launch_slicers_L<8>(g, batch, nullptr, 0, nullptr, nullptr, B, sB, Bd, eb, s);
-  }
-  return MG_EINVAL;
+  return launch_slicers(g, batch, in_df32, nullptr, 0, nullptr, nullptr, B, sB, Bd, eb, s);
 }
 
-// C[b] = scale * A[b] B[b] + addends, from digit buffers made by split_slice_a/b.
+// C[b] = A[b] B[b] + addends (C and addends DF32), from digit buffers made by split_slice_a/b.
 int split_gemm(int d, int L, int batch, const void* abuf, const void* bbuf, double* C, long long sC,
                const AddTerms& add, int* status, cudaStream_t s) {
   if (batch <= 0) return MG_OK;
   if (batch > 65535) return MG_EUNSUPPORTED;
+  if (add.scale != 1.0) return MG_EINVAL;
   SplitGeom g = split_geom(d, L);
   const __nv_bfloat16* Ad = reinterpret_cast<const __nv_bfloat16*>(abuf);
   const int* ea = reinterpret_cast<const int*>(Ad + g.a_item_elems() * batch);
@@ -682,10 +708,9 @@ int split_gemm(int d, int L, int batch, const void* abuf, const void* bbuf, doub
   const int* eb = reinterpret_cast<const int*>(Bd + g.b_item_elems() * batch);
   SplitEpi e{};
   e.add_n = add.n;
-  for (int m = 0; m < 3; ++m) { e.add_src[m] = add.src[m]; e.add_coef[m] = add.coef[m]; }
+  for (int m = 0; m < 3; ++m) { e.add_src[m] = add.src[m]; e.add_coef[m] = df_from_double(add.coef[m]); }
   e.add_stride = add.stride;
-  e.diag = add.diag;
-  e.scale = add.scale;
+  e.diag = df_from_double(add.diag);
   switch (L) {
     case 2: return launch_split_gemm_L<2>(g, batch, Ad, ea, Bd, eb, C, sC, e, status, s);
     case 3: return launch_split_gemm_L<3>(g, batch, Ad, ea, Bd, eb, C, sC, e, status, s);

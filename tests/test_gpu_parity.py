@@ -87,7 +87,10 @@ def test_build_omega_matches_oracle(ctx, d, K, N):
         np.testing.assert_allclose(Hbar[n].cpu().numpy(), ref, atol=1e-14, rtol=0)
         t = np.trace(ref).real / d
         assert abs(tau[n].item() - t) < 1e-14
-        assert abs(nrm[n].item() - np.linalg.norm(ref - t * np.eye(d), 1)) < 1e-12
+        # the 1-norm only selects the squaring count: the kernel returns an upper bound
+        # within 2^-19 relative (FP32 magnitudes widened by 2^-20, summed in FP64)
+        exact = np.linalg.norm(ref - t * np.eye(d), 1)
+        assert exact * (1 - 1e-12) <= nrm[n].item() <= exact * (1 + 2.0 ** -19) + 1e-300
 
 
 # ----------------------------------------------------------------------------
