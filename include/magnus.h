@@ -171,6 +171,31 @@ int mg_cgemm(mg_ctx* ctx, int batch, int d, const double* A, const double* B, do
 int mg_propagate(mg_ctx* ctx, int N, int d, const double* U, int output, const double* in,
                  double* out, int reorth_every, int precision, int slices);
 
+/* ---- allocation-free product ---------------------------------------------- */
+/* C[b] = A[b] B[b] for a batch of complex d x d matrices (device pointers, the
+ * layout of mg_cgemm), computed exactly like mg_cgemm in MG_PREC_SPLIT mode with
+ * `slices` digits, but without allocating any device memory and without a
+ * context.  It is meant for callers that cannot call cudaMalloc: code whose
+ * device memory is owned by another allocator or pool, which must not take the
+ * implicit device-wide synchronisation of cudaMalloc/cudaFree, and fixed-latency
+ * loops (pulse optimisation, control feedback) that must not allocate once
+ * running.  The paper has no counterpart: it is an interface convenience.
+ *
+ * Scratch comes from one static device array of MG_STATIC_SCRATCH_BYTES that
+ * every GPU which loads the library holds until the process exits.  A call
+ * whose digit operands and product do not fit returns MG_EUNSUPPORTED (about
+ * batch * d^2 * (16 + 12 slices) bytes plus tile padding are needed; one d = 729
+ * product with 6 digits fits).  The first call on a device resolves the array's device address;
+ * make that first call before any stream capture.  Every call reuses the same
+ * array, so calls whose work overlaps on the GPU (other streams, other host
+ * threads) race and must be serialised by the caller.  Work runs on `stream`
+ * (a cudaStream_t, NULL for the legacy stream) of CUDA device `device`; the
+ * call synchronises that stream before returning and restores the caller's
+ * current device. */
+#define MG_STATIC_SCRATCH_BYTES (64u << 20)
+int mg_cgemm_split_static(int device, void* stream, int batch, int d, const double* A, const double* B,
+                          double* C, int slices);
+
 /* ---- diagnostics ----------------------------------------------------------- */
 /* Per-launch timing of the matrix-product kernels (the dominant kernels of the
  * path).  While enabled, the context records a CUDA event pair around every

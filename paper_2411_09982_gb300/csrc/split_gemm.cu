@@ -42,6 +42,7 @@
 #include <cuda_bf16.h>
 
 #include <mutex>
+#include <cstring>
 
 namespace mg {
 
@@ -723,4 +724,94 @@ int split_gemm(int d, int L, int batch, const void* abuf, const void* bbuf, doub
   return MG_EINVAL;
 }
 
+// ---------------------------------------------------------------------------
+// Allocation-free variant of the split-precision product
+// ---------------------------------------------------------------------------
+// Its scratch (digit operands, the double-float product and the status word of
+// the bounded waits) lives in one file-scope device array instead of memory
+// from cudaMalloc.  The array exists on every device that loads this library,
+// for the life of the process.  Host code must not pass the symbol itself to a
+// kernel (on the host it only names a stand-in object): the device address is
+// resolved once per device with cudaGetSymbolAddress, that device current.
+constexpr size_t kStaticScratchBytes = (size_t)64 << 20;   // 64 MiB
+__device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+
+static std::mutex g_static_mu;
+static void* g_static_addr[128];
+
+static int static_scratch_address(int device, void** out) {
+  std::lock_guard<std::mutex> lock(g_static_mu);
+  if (device < 0 || device >= 128) return MG_EINVAL;
+  if (!g_static_addr[device]) {
+    int prev = 0;
+    MG_CUDA_TRY(cudaGetDevice(&prev));
+    MG_CUDA_TRY(cudaSetDevice(device));
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+    cudaSetDevice(prev);
+    if (e != cudaSuccess) {
+      set_last_cuda_error(e, "cudaGetSymbolAddress(g_static_scratch)", __FILE__, __LINE__);
+      return MG_ECUDA;
+    }
+    g_static_addr[device] = p;
+  }
+  *out = g_static_addr[device];
+  return MG_OK;
+}
+
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+size_t static_scratch_bytes_needed(int d, int L, int batch) {
+  return 256 + align256(split_a_bytes(d, L, batch)) + align256(split_b_bytes(d, L, batch)) +
+         align256((size_t)16 * d * d * batch);
+}
+
 }  // namespace mg
+
+extern "C" int mg_cgemm_split_static(int device, void* stream, int batch, int d, const double* A, const double* B,
+                                     double* C, int slices) {
+  using namespace mg;
+  if (batch < 1 || batch > 65535 || d < 1 || d > 4096 || !A || !B || !C || slices < 2 || slices > 8) {
+    set_last_message("mg_cgemm_split_static: invalid argument");
+    return MG_EINVAL;
+  }
+  const size_t need = static_scratch_bytes_needed(d, slices, batch);
+  if (need > kStaticScratchBytes) {
+    set_last_message("mg_cgemm_split_static: batch %d of d = %d with %d digits needs %zu bytes of scratch; "
+                     "the static scratch holds %zu",
+                     batch, d, slices, need, kStaticScratchBytes);
+    return MG_EUNSUPPORTED;
+  }
+  int prev = 0;
+  MG_CUDA_TRY(cudaGetDevice(&prev));
+  void* base = nullptr;
+  int r = static_scratch_address(device, &base);
+  if (r != MG_OK) return r;
+  MG_CUDA_TRY(cudaSetDevice(device));
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  unsigned char* p = reinterpret_cast<unsigned char*>(base);
+  int* status = reinterpret_cast<int*>(p);
+  void* abuf = p + 256;
+  void* bbuf = p + 256 + align256(split_a_bytes(d, slices, batch));
+  double* prod = reinterpret_cast<double*>(reinterpret_cast<unsigned char*>(bbuf) +
+                                           align256(split_b_bytes(d, slices, batch)));
+  const long long md = 2LL * d * d;
+  AddTerms none;
+  int st = 0;
+  // the status word is the only scratch that must start at zero; the digit
+  // buffers (padding included) and the product are fully rewritten
+  if (cudaMemsetAsync(status, 0, sizeof(int), s) != cudaSuccess) r = MG_ECUDA;
+  if (r == MG_OK) r = split_slice_a(d, slices, batch, A, md, 0, abuf, s);
+  if (r == MG_OK) r = split_slice_b(d, slices, batch, B, md, 0, bbuf, s);
+  if (r == MG_OK) r = split_gemm(d, slices, batch, abuf, bbuf, prod, md, none, status, s);
+  if (r == MG_OK) r = launch_df_to_fp64(batch, d, prod, md, C, md, s);
+  if (r == MG_OK && cudaMemcpyAsync(&st, status, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess) r = MG_ECUDA;
+  if (r == MG_OK && cudaStreamSynchronize(s) != cudaSuccess) r = MG_ECUDA;
+  if (r == MG_OK && st == MG_DEV_TIMEOUT) {
+    set_last_message("mg_cgemm_split_static: a bounded device-side wait gave up");
+    r = MG_ETIMEOUT;
+  }
+  cudaSetDevice(prev);
+  return r;
+}
+

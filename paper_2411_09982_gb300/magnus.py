@@ -76,6 +76,7 @@ SIGNATURES = {
     "mg_propagate": (_I, [_P, _I, _I, _P, _I, _P, _P, _I, _I, _I]),
     "mg_ctx_enable_gemm_timing": (_I, [_P, _I]),
     "mg_ctx_gemm_stats": (_I, [_P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(_D), ctypes.POINTER(_D), _I]),
+    "mg_cgemm_split_static": (_I, [_I, _P, _I, _I, _P, _P, _P, _I]),
     "mg_strerror": (ctypes.c_char_p, [_I]),
     "mg_last_error_message": (ctypes.c_char_p, []),
     "mg_kernel_launch_count": (ctypes.c_int64, []),
@@ -237,6 +238,12 @@ def mg_expm(ctx, batch, d, A, U, precision=MG_PREC_FP64, slices=6, squarings=Non
 
 def mg_cgemm(ctx, batch, d, A, B, C, precision=MG_PREC_FP64, slices=6):
     _check(load().mg_cgemm(ctx.h, batch, d, _ptr(A), _ptr(B), _ptr(C), precision, slices), "mg_cgemm")
+
+
+def mg_cgemm_split_static(device, stream, batch, d, A, B, C, slices=6):
+    """Split-precision product with the library's static scratch (no device allocation)."""
+    _check(load().mg_cgemm_split_static(device, _stream_ptr(stream), batch, d, _ptr(A), _ptr(B), _ptr(C), slices),
+           "mg_cgemm_split_static")
 
 
 def mg_propagate(ctx, N, d, U, output, inp, out, reorth_every=0, precision=MG_PREC_FP64, slices=6):
