@@ -24,14 +24,15 @@
 // L = 7..8 approaches FP64.  This is the tensor-core replacement of the FP64
 // products of the exponential; everything else of the path stays FP64.
 //
-// Kernel structure (one 128 x 64-complex output tile per CTA, 192 threads):
+// Kernel structure (one 128 x 64-complex output tile per CTA, 320 threads):
 //   warp 0      TMA producer: per K-step of 16 one 4-D box of all L A-digit
 //               tiles (128 x 16 BF16 each) and one of all L B-digit tiles,
 //               SWIZZLE_32B, into a STAGES-deep ring of shared-memory stages.
 //   warp 1      TMEM owner and MMA issuer: tcgen05.mma kind::f16 (BF16 in,
 //               FP32 accumulate), M = 128, N = 128 (64 real + 64 imaginary
 //               output columns), K = 16, one instruction per digit pair.
-//   warps 2..5  epilogue: tcgen05.ld of the four accumulators, FP64 combine.
+//   warps 2..9  epilogue: tcgen05.ld of the four accumulators (two warps per TMEM
+//               lane quarter, 32 complex columns each), double-float combine.
 // Every mbarrier wait is bounded by a wall-clock deadline; a wait that gives up
 // records MG_DEV_TIMEOUT in the status word and the CTA winds down.
 #include "common.cuh"
@@ -225,84 +226,95 @@ slice_a_kernel(int d, int Kp, int Mp, int beta, const double* __restrict__ A, lo
 // B digits: K-major rows of [[Br, Bi], [-Bi, Br]]^T, tile-interleaved: for the
 // 64 complex columns of tile t, rows 128t + r hold [Re B[:, j] | -Im B[:, j]] and
 // rows 128t + 64 + r hold [Im B[:, j] | Re B[:, j]] (j = 64t + r).
-// grid (ceil(d/64), batch), block 256.
+// Two launches with many CTAs each (a column-exponent pass, then the digits of
+// 32 x 64 blocks), so that the HBM-bound work has enough warps in flight.
+
+// Column exponent bounds: grid (ceil(d/64), ceil(d/64), batch), block 256.
+// eb must be preset below -2^28 (byte 0x80); blocks combine with atomicMax.
+template <typename T>
+__global__ void __launch_bounds__(256)
+col_exponent_kernel(int d, int Np, const double* __restrict__ B, long long sB, int* __restrict__ eb) {
+  using E_ = Elem<T>;
+  __shared__ int red[4][SG_BNC];
+  const int j0 = blockIdx.x * SG_BNC, k0 = blockIdx.y * 64, b = blockIdx.z;
+  const int c = threadIdx.x & 63, g = threadIdx.x >> 6;
+  const double* Bb = B + b * sB;
+  int E = -(1 << 29);
+  if (j0 + c < d) {
+    const int kend = min(d, k0 + 64);
+    for (int k = k0 + g; k < kend; k += 4) {
+      const auto v = E_::load(Bb, (long long)k * d + j0 + c);
+      E = max(E, max(exp_bound(v.re), exp_bound(v.im)));
+    }
+  }
+  red[g][c] = E;
+  __syncthreads();
+  if (g == 0 && j0 + c < d) {
+    const int EE = max(max(red[0][c], red[1][c]), max(red[2][c], red[3][c]));
+    atomicMax(eb + (long long)b * (Np / 2) + j0 + c, EE);
+  }
+}
+
 constexpr int SB_KCHUNK = 32;
+// Digits of one 32 (k) x 64 (j) block: grid (ceil(d/64), ceil(d/32), batch), block 256.
+// The blocks with blockIdx.y == 0 also zero the K tail and the rows beyond d.
 template <int L, typename T>
 __global__ void __launch_bounds__(256)
 slice_b_kernel(int d, int Kp, int Np, int beta, const double* __restrict__ B, long long sB,
-               __nv_bfloat16* __restrict__ out, int* __restrict__ eb) {
+               __nv_bfloat16* __restrict__ out, const int* __restrict__ eb) {
   using E_ = Elem<T>;
   using V = typename E_::type;
   __shared__ V tile[SB_KCHUNK][SG_BNC + 1];
-  __shared__ int red[4][SG_BNC];
   __shared__ int shift[SG_BNC];
-  const int t = blockIdx.x, b = blockIdx.y;
-  const int j0 = t * SG_BNC;
+  const int t = blockIdx.x, b = blockIdx.z;
+  const int j0 = t * SG_BNC, k0 = blockIdx.y * SB_KCHUNK;
   const int tid = threadIdx.x;
   const double* Bb = B + b * sB;
   const long long slice_stride = (long long)Np * Kp;
   __nv_bfloat16* ob = out + (long long)b * L * slice_stride;
-
-  // pass 1: column exponent bounds
-  {
-    const int c = tid & 63, g = tid >> 6;
-    int E = -(1 << 29);
-    if (j0 + c < d)
-      for (int k = g; k < d; k += 4) {
-        const V v = E_::load(Bb, (long long)k * d + j0 + c);
-        E = max(E, max(exp_bound(v.re), exp_bound(v.im)));
-      }
-    red[g][c] = E;
-    __syncthreads();
-    if (tid < SG_BNC) {
-      int EE = max(max(red[0][tid], red[1][tid]), max(red[2][tid], red[3][tid]));
-      if (EE < -(1 << 28)) EE = 0;
-      shift[tid] = beta * L - EE - 1;
-      if (j0 + tid < d) eb[(long long)b * (Np / 2) + j0 + tid] = EE;
-    }
-    __syncthreads();
+  if (tid < SG_BNC) {
+    int E = j0 + tid < d ? eb[(long long)b * (Np / 2) + j0 + tid] : 0;
+    if (E < -(1 << 28)) E = 0;   // all-zero column
+    shift[tid] = beta * L - E - 1;
   }
-  const __nv_bfloat16 zero = __float2bfloat16_rn(0.0f);
-  // pass 2: digits, K-chunks staged through shared memory
-  for (int k0 = 0; k0 < d; k0 += SB_KCHUNK) {
-    for (int e = tid; e < SB_KCHUNK * SG_BNC; e += 256) {
-      int kk = e / SG_BNC, c = e % SG_BNC;
-      V v{};
-      if (k0 + kk < d && j0 + c < d) v = E_::load(Bb, (long long)(k0 + kk) * d + j0 + c);
-      tile[kk][c] = v;
-    }
-    __syncthreads();
-    for (int e = tid; e < SB_KCHUNK * SG_BNC; e += 256) {
-      int kk = e % SB_KCHUNK, r = e / SB_KCHUNK;
-      int k = k0 + kk;
-      if (k >= d) continue;
-      const V v = tile[kk][r];
-      __nv_bfloat16 dr[L], di[L];
-      make_digits<L>(v.re, shift[r], beta, dr);
-      make_digits<L>(v.im, shift[r], beta, di);
-      __nv_bfloat16* row_re = ob + (long long)(t * 2 * SG_BNC + r) * Kp;          // [Re | -Im]
-      __nv_bfloat16* row_im = ob + (long long)(t * 2 * SG_BNC + SG_BNC + r) * Kp; // [Im | Re]
+  for (int e = tid; e < SB_KCHUNK * SG_BNC; e += 256) {
+    const int kk = e / SG_BNC, c = e % SG_BNC;
+    V v{};
+    if (k0 + kk < d && j0 + c < d) v = E_::load(Bb, (long long)(k0 + kk) * d + j0 + c);
+    tile[kk][c] = v;
+  }
+  __syncthreads();
+  for (int e = tid; e < SB_KCHUNK * SG_BNC; e += 256) {
+    const int kk = e % SB_KCHUNK, r = e / SB_KCHUNK;
+    const int k = k0 + kk;
+    if (k >= d || j0 + r >= d) continue;
+    const V v = tile[kk][r];
+    __nv_bfloat16 dr[L], di[L];
+    make_digits<L>(v.re, shift[r], beta, dr);
+    make_digits<L>(v.im, shift[r], beta, di);
+    __nv_bfloat16* row_re = ob + (long long)(t * 2 * SG_BNC + r) * Kp;          // [Re | -Im]
+    __nv_bfloat16* row_im = ob + (long long)(t * 2 * SG_BNC + SG_BNC + r) * Kp; // [Im | Re]
 #pragma unroll
-      for (int s = 0; s < L; ++s) {
-        long long so = s * slice_stride;
-        row_re[so + k] = dr[s];
-        row_re[so + d + k] = __hneg(di[s]);
-        row_im[so + k] = di[s];
-        row_im[so + d + k] = dr[s];
-      }
+    for (int s = 0; s < L; ++s) {
+      const long long so = s * slice_stride;
+      row_re[so + k] = dr[s];
+      row_re[so + d + k] = __hneg(di[s]);
+      row_im[so + k] = di[s];
+      row_im[so + d + k] = dr[s];
     }
-    __syncthreads();
   }
-  // zero the K tail of every row of this tile (and whole rows beyond d)
-  for (int e = tid; e < 2 * SG_BNC * (Kp - 2 * d); e += 256) {
-    int rr = e / (Kp - 2 * d), k = 2 * d + e % (Kp - 2 * d);
+  if (blockIdx.y != 0) return;
+  const __nv_bfloat16 zero = __float2bfloat16_rn(0.0f);
+  const int tail = Kp - 2 * d;
+  for (int e = tid; e < 2 * SG_BNC * tail; e += 256) {
+    const int rr = e / tail, k = 2 * d + e % tail;
 #pragma unroll
     for (int s = 0; s < L; ++s) ob[s * slice_stride + (long long)(t * 2 * SG_BNC + rr) * Kp + k] = zero;
   }
   const int live = min(SG_BNC, d - j0);
   if (live < SG_BNC) {
     for (int e = tid; e < (SG_BNC - live) * 2 * d; e += 256) {
-      int rr = live + e / (2 * d), k = e % (2 * d);
+      const int rr = live + e / (2 * d), k = e % (2 * d);
 #pragma unroll
       for (int s = 0; s < L; ++s) {
         ob[s * slice_stride + (long long)(t * 2 * SG_BNC + rr) * Kp + k] = zero;
@@ -377,6 +389,11 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
       : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
       : "r"(taddr));
 }
+__device__ __forceinline__ void tmem_ld4(uint32_t taddr, uint32_t (&r)[4]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(taddr));
+}
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 // Shared-memory matrix descriptor: K-major operand tile, 32-byte swizzle,
@@ -394,7 +411,8 @@ __device__ __forceinline__ uint64_t sw32_kmajor_desc(uint32_t saddr) {
 // Instruction descriptor: kind::f16, A = B = BF16, D = F32, both K-major, M = 128, N = 128.
 constexpr uint32_t kIdescBf16 = (1u << 4) | (1u << 7) | (1u << 10) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
 
-constexpr int SG_THREADS = 192;
+constexpr int SG_THREADS = 320;   // producer warp, MMA warp, 8 epilogue warps
+constexpr int SG_EPI_WARPS = 8;
 // TMEM accumulators: digit-pair levels 0, 1, 2 and >= 3, 128 columns each (all 512).
 constexpr int SG_GROUPS = 4;
 constexpr uint64_t SG_WAIT_NS = 4000000000ull;   // 4 s: far beyond any legitimate wait
@@ -432,6 +450,7 @@ split_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
   uint64_t* accfull = empty + STAGES;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accfull + 1);
   int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
+  int* eb_s = abort_flag + 1;   // column exponents of this tile's 64 columns
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nt = blockIdx.x, mt = blockIdx.y, b = blockIdx.z;
@@ -446,6 +465,10 @@ split_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 2 || warp == 3) {
+    const int c = (warp - 2) * 32 + lane, j = nt * SG_BNC + c;
+    eb_s[c] = j < d ? eb[(long long)b * (Np / 2) + j] : 0;
   }
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
@@ -515,8 +538,9 @@ split_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
       if (!ok) *(volatile int*)abort_flag = 1;
     }
   } else {
-    // ---------------- epilogue (warps 2..5) ----------------
+    // ---------------- epilogue (warps 2..9) ----------------
     const int q = warp & 3;                   // TMEM lane quarter this warp may access
+    const int c0 = ((warp - 2) >> 2) * (SG_BNC / 2);   // first of this warp's 32 complex columns
     // one lane polls, the warp follows its verdict (tcgen05.ld is warp-collective)
     int got_i = 0;
     if (lane == 0) got_i = mbar_wait(accfull, 0, deadline) ? 1 : 0;
@@ -528,35 +552,48 @@ split_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
       const int row = mt * SG_BM + q * 32 + lane;
       const bool row_ok = row < d;
       const int Ea = row_ok ? ea[(long long)b * Mp + row] : 0;
-      const double* addp[3];
+      const float4* addp[3];
 #pragma unroll
-      for (int m = 0; m < 3; ++m) addp[m] = epi.add_src[m] ? epi.add_src[m] + b * epi.add_stride : nullptr;
+      for (int m = 0; m < 3; ++m)
+        addp[m] = epi.add_src[m] ? reinterpret_cast<const float4*>(epi.add_src[m] + b * epi.add_stride) : nullptr;
       float4* Cb = reinterpret_cast<float4*>(C + b * sC);
       const uint32_t lane_base = tmem + ((uint32_t)(q * 32) << 16);
-      for (int jc = 0; jc < SG_BNC; jc += 8) {
-        uint32_t re_acc[SG_GROUPS][8], im_acc[SG_GROUPS][8];
+      const long long row_off = (long long)row * d;
+      constexpr int CW = 4;   // complex columns per step
+      for (int jc = c0; jc < c0 + SG_BNC / 2; jc += CW) {
+        uint32_t re_acc[SG_GROUPS][CW], im_acc[SG_GROUPS][CW];
 #pragma unroll
         for (int g = 0; g < SG_GROUPS; ++g) {
-          tmem_ld8(lane_base + g * 128 + jc, re_acc[g]);
-          tmem_ld8(lane_base + g * 128 + SG_BNC + jc, im_acc[g]);
+          tmem_ld4(lane_base + g * 128 + jc, re_acc[g]);
+          tmem_ld4(lane_base + g * 128 + SG_BNC + jc, im_acc[g]);
         }
+        // issue every addend load of these columns before the arithmetic
+        float4 ad[3][CW];
+#pragma unroll
+        for (int m = 0; m < 3; ++m)
+#pragma unroll
+          for (int jj = 0; jj < CW; ++jj) {
+            const int j = nt * SG_BNC + jc + jj;
+            ad[m][jj] = (m < epi.add_n && row_ok && j < d) ? addp[m][row_off + j] : make_float4(0.f, 0.f, 0.f, 0.f);
+          }
         tmem_wait_ld();
         if (row_ok) {
 #pragma unroll
-          for (int jj = 0; jj < 8; ++jj) {
+          for (int jj = 0; jj < CW; ++jj) {
             const int j = nt * SG_BNC + jc + jj;
             if (j < d) {
-              const int k = Ea + eb[(long long)b * (Np / 2) + j] + 2 - 2 * beta;
+              const int k = Ea + eb_s[jc + jj] + 2 - 2 * beta;
               df32 re = combine_levels(re_acc[0][jj], re_acc[1][jj], re_acc[2][jj], re_acc[3][jj], k);
               df32 im = combine_levels(im_acc[0][jj], im_acc[1][jj], im_acc[2][jj], im_acc[3][jj], k);
-              const long long off = (long long)row * d + j;
-              for (int m = 0; m < epi.add_n; ++m) {
-                const float4 p = reinterpret_cast<const float4*>(addp[m])[off];
-                re = df_add(re, df_mul(df32{p.x, p.y}, epi.add_coef[m]));
-                im = df_add(im, df_mul(df32{p.z, p.w}, epi.add_coef[m]));
+#pragma unroll
+              for (int m = 0; m < 3; ++m) {
+                if (m < epi.add_n) {
+                  re = df_add(re, df_mul(df32{ad[m][jj].x, ad[m][jj].y}, epi.add_coef[m]));
+                  im = df_add(im, df_mul(df32{ad[m][jj].z, ad[m][jj].w}, epi.add_coef[m]));
+                }
               }
               if (row == j) re = df_add(re, epi.diag);
-              Cb[off] = make_float4(re.hi, re.lo, im.hi, im.lo);
+              Cb[row_off + j] = make_float4(re.hi, re.lo, im.hi, im.lo);
             }
           }
         }
@@ -625,7 +662,7 @@ static int launch_split_gemm_L(const SplitGeom& g, int batch, const __nv_bfloat1
   CUtensorMap ma, mb;
   MG_TRY(make_digit_map(&ma, Ad, g.Kp, g.Mp, L, batch));
   MG_TRY(make_digit_map(&mb, Bd, g.Kp, g.Np, L, batch));
-  const size_t smem = (size_t)STAGES * 2 * L * SG_TILE_BYTES + 1024 /*barriers*/ + 1024 /*align*/;
+  const size_t smem = (size_t)STAGES * 2 * L * SG_TILE_BYTES + 1024 /*barriers, exponents*/ + 1024 /*align*/;
   auto kern = split_gemm_kernel<L, STAGES>;
   MG_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   dim3 grid(ceil_div(g.d, SG_BNC), g.Mp / SG_BM, batch);
@@ -641,7 +678,11 @@ static int launch_slicers_LT(const SplitGeom& g, int batch, const double* A, lon
     MG_TRY(check_launch("slice_a_kernel"));
   }
   if (B) {
-    slice_b_kernel<L, T><<<dim3(ceil_div(g.d, SG_BNC), batch), 256, 0, s>>>(g.d, g.Kp, g.Np, g.beta, B, sB, Bd, eb);
+    MG_CUDA_TRY(cudaMemsetAsync(eb, 0x80, sizeof(int) * (size_t)(g.Np / 2) * batch, s));
+    col_exponent_kernel<T><<<dim3(ceil_div(g.d, SG_BNC), ceil_div(g.d, 64), batch), 256, 0, s>>>(g.d, g.Np, B, sB, eb);
+    MG_TRY(check_launch("col_exponent_kernel"));
+    slice_b_kernel<L, T><<<dim3(ceil_div(g.d, SG_BNC), ceil_div(g.d, SB_KCHUNK), batch), 256, 0, s>>>(
+        g.d, g.Kp, g.Np, g.beta, B, sB, Bd, eb);
     MG_TRY(check_launch("slice_b_kernel"));
   }
   return MG_OK;
