@@ -141,6 +141,20 @@ int mg_set_controls(mg_plan* plan, int N, int P, double t0, double dt, const dou
 int mg_evolve(mg_plan* plan, int output, const double* in, double* out, int reorth_every,
               int flags, mg_report* rep);
 
+/* Evolve n independent jobs (plans with their controls set) of uneven
+ * dimension and length together: jobs are grouped by precision mode and by
+ * dimension rounded up to a multiple of 16 (zero padding is exact: the padded
+ * block of exp(-i Hbar) is the identity), and within a group all intervals of
+ * all jobs share one batched launch per step of the exponential; states of all
+ * jobs of a chunk advance in one multi-job launch.  outputs[i], in[i], out[i]
+ * are as for mg_evolve (in[i] may be NULL for propagators; in may be NULL when
+ * no job needs an input).  State jobs need d <= 256.  job_status (HOST, may be
+ * NULL) receives MG_OK or MG_ENONFINITE per job: a job whose Magnus exponent
+ * has a NaN/Inf norm fails alone, the others complete.  flags:
+ * MG_FLAG_HOST_PTRS when every in[i]/out[i] is host memory. */
+int mg_evolve_batch(mg_ctx* ctx, int n, mg_plan* const* plans, const int* outputs, const double* const* in,
+                    double* const* out, int reorth_every, int flags, int* job_status);
+
 /* ---- steps of the path (device pointers) --------------------------------- */
 /* c[n][k] = (dt/2) sum_p w[p] samples[n][p][k]   (Eq. magnus-first-order-coeff).
  * samples N x P x K, w P doubles (device), c N x K. */

@@ -323,15 +323,19 @@ struct ExpmStats {
 };
 
 int expm_chunk(mg_ctx* ctx, Engine& eng, int batch, double* W, const double* tau, const double* norm1_dev,
-               double* U, long long sU, ExpmStats* st) {
+               double* U, long long sU, ExpmStats* st, const std::vector<double>* host_norms = nullptr) {
   const int d = eng.d;
   const long long md = mat_doubles(d);
   cudaStream_t s = ctx->stream;
 
   // FP64 norms -> host: squaring count per interval and for the batch
   std::vector<double> nrm(batch);
-  MG_CUDA_TRY(cudaMemcpyAsync(nrm.data(), norm1_dev, sizeof(double) * batch, cudaMemcpyDeviceToHost, s));
-  MG_CUDA_TRY(cudaStreamSynchronize(s));
+  if (host_norms) {
+    nrm = *host_norms;
+  } else {
+    MG_CUDA_TRY(cudaMemcpyAsync(nrm.data(), norm1_dev, sizeof(double) * batch, cudaMemcpyDeviceToHost, s));
+    MG_CUDA_TRY(cudaStreamSynchronize(s));
+  }
   double nmax = 0.0;
   for (int b = 0; b < batch; ++b) {
     if (!std::isfinite(nrm[b])) {
@@ -1028,6 +1032,261 @@ int mg_propagate(mg_ctx* ctx, int N, int d, const double* U, int output, const d
   MG_TRY(finish_prop(ctx, eng, ps, out, 0, nullptr));
   if (precision == MG_PREC_SPLIT) return check_status(ctx);
   return MG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// many independent jobs of uneven size in shared batched launches
+// ---------------------------------------------------------------------------
+namespace {
+
+struct BatchJob {
+  int idx;          // position in the caller's arrays
+  mg_plan* p;
+  int output;
+  const double* H0;  // padded operators (device)
+  const double* Hk;
+  double* state;     // padded psi (d_pad) or running product (d_pad x d_pad, engine storage)
+  bool init = false;
+  bool failed = false;
+  int done = 0;
+};
+
+int round_dim(int d) { return ((d + 15) / 16) * 16; }
+
+// Run all jobs of one (precision, digits, padded dimension) group.
+int run_group(mg_ctx* ctx, std::vector<BatchJob>& jobs, int dp, int prec, int L, const double* const* in,
+              double* const* out, int reorth_every, int flags, int* job_status) {
+  cudaStream_t s = ctx->stream;
+  Engine eng{ctx, dp, prec, L};
+  const long long md = mat_doubles(dp);
+  const cudaMemcpyKind h2d = (flags & MG_FLAG_HOST_PTRS) ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+  const cudaMemcpyKind d2h = (flags & MG_FLAG_HOST_PTRS) ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+  std::vector<void*> owned;
+  auto dmalloc = [&](size_t bytes, void** ptr) -> int {
+    if (cudaMalloc(ptr, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      set_last_message("device allocation of %zu bytes failed (batched jobs)", bytes);
+      return MG_ENOMEM;
+    }
+    owned.push_back(*ptr);
+    return MG_OK;
+  };
+  int rc = MG_OK;
+  long long total = 0;
+  int nstate = 0;
+  for (auto& j : jobs) total += j.p->N;
+  // padded operators and per-job state
+  for (auto& j : jobs) {
+    const int d = j.p->d, K = j.p->K;
+    if (d == dp) {
+      j.H0 = j.p->H0;
+      j.Hk = j.p->Hk;
+    } else {
+      void* buf;
+      if ((rc = dmalloc(sizeof(double) * md * (1 + K), &buf)) != MG_OK) goto done;
+      double* H = reinterpret_cast<double*>(buf);
+      if ((rc = launch_pad_copy(1, d, dp, j.p->H0, H, s)) != MG_OK) goto done;
+      if (K > 0 && (rc = launch_pad_copy(K, d, dp, j.p->Hk, H + md, s)) != MG_OK) goto done;
+      j.H0 = H;
+      j.Hk = H + md;
+    }
+    void* st;
+    const size_t sb = j.output == MG_OUT_STATE ? sizeof(double) * 2 * dp : sizeof(double) * md;
+    if ((rc = dmalloc(sb, &st)) != MG_OK) goto done;
+    j.state = reinterpret_cast<double*>(st);
+    if (j.output == MG_OUT_STATE) {
+      ++nstate;
+      if (!in || !in[j.idx]) { rc = MG_EINVAL; goto done; }
+      if (cudaMemsetAsync(j.state, 0, sb, s) != cudaSuccess ||
+          cudaMemcpyAsync(j.state, in[j.idx], sizeof(double) * 2 * d, h2d, s) != cudaSuccess) {
+        rc = MG_ECUDA;
+        goto done;
+      }
+      j.init = true;
+    } else if (in && in[j.idx]) {
+      double *t, *tp;
+      if ((rc = ws(ctx, WS_OUT, mat_doubles(d), &t)) != MG_OK) goto done;
+      if ((rc = ws(ctx, WS_NS_Z, md, &tp)) != MG_OK) goto done;
+      if (cudaMemcpyAsync(t, in[j.idx], sizeof(double) * mat_doubles(d), h2d, s) != cudaSuccess) { rc = MG_ECUDA; goto done; }
+      if ((rc = launch_pad_copy(1, d, dp, t, tp, s)) != MG_OK) goto done;
+      // identity on the padded block keeps the padding exact
+      for (int q = d; q < dp; ++q) {
+        const double one = 1.0;
+        if (cudaMemcpyAsync(tp + 2 * ((long long)q * dp + q), &one, sizeof(double), cudaMemcpyHostToDevice, s) !=
+            cudaSuccess) { rc = MG_ECUDA; goto done; }
+        if (cudaStreamSynchronize(s) != cudaSuccess) { rc = MG_ECUDA; goto done; }
+      }
+      if ((rc = eng.from_fp64(1, tp, md, j.state, md)) != MG_OK) goto done;
+      j.init = true;
+    }
+  }
+  {
+    // device array of state pointers for the multi-job chain kernel
+    void* pbuf;
+    if ((rc = dmalloc(sizeof(double*) * std::max<size_t>(1, jobs.size()), &pbuf)) != MG_OK) goto done;
+    double** psi_dev = reinterpret_cast<double**>(pbuf);
+    std::vector<double*> ptrs;
+    for (auto& j : jobs) ptrs.push_back(j.state);
+    if (cudaMemcpyAsync(psi_dev, ptrs.data(), sizeof(double*) * ptrs.size(), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) { rc = MG_ECUDA; goto done; }
+    void* sbuf;
+    if ((rc = dmalloc(sizeof(ChainSeg) * std::max<size_t>(1, jobs.size()), &sbuf)) != MG_OK) goto done;
+    ChainSeg* segs_dev = reinterpret_cast<ChainSeg*>(sbuf);
+
+    const int chunk = chunk_size(ctx, dp, prec, L, (int)std::min<long long>(total, 1 << 30), 1);
+    size_t jcur = 0;
+    int jlocal = 0;
+    ExpmStats st;
+    while (jcur < jobs.size()) {
+      // gather the chunk's segments
+      struct Seg { size_t job; int a, n, off; };
+      std::vector<Seg> segs;
+      int fill = 0;
+      while (jcur < jobs.size() && fill < chunk) {
+        BatchJob& j = jobs[jcur];
+        const int take = std::min(chunk - fill, j.p->N - jlocal);
+        segs.push_back({jcur, jlocal, take, fill});
+        fill += take;
+        jlocal += take;
+        if (jlocal == j.p->N) { ++jcur; jlocal = 0; }
+      }
+      double *W, *tau, *nrm, *Ub, *sc;
+      if ((rc = ws(ctx, WS_W, md * fill, &W)) != MG_OK) goto done;
+      if ((rc = ws(ctx, WS_TAU, fill, &tau)) != MG_OK) goto done;
+      if ((rc = ws(ctx, WS_NORM, fill, &nrm)) != MG_OK) goto done;
+      if ((rc = ws(ctx, WS_UBUF, md * fill, &Ub)) != MG_OK) goto done;
+      for (const Seg& g : segs) {
+        BatchJob& j = jobs[g.job];
+        if ((rc = small_scratch(ctx, (size_t)j.p->K + 1 + g.n, &sc)) != MG_OK) goto done;
+        rc = launch_build_omega(g.n, dp, j.p->K, j.p->dt, j.H0, j.Hk, j.p->c + (long long)g.a * j.p->K,
+                                W + g.off * md, tau + g.off, nrm + g.off, 1, 1, sc, s);
+        if (rc != MG_OK) goto done;
+      }
+      // FP64 norms: a non-finite norm fails its job only (its exponents are zeroed)
+      std::vector<double> hn(fill);
+      if (cudaMemcpyAsync(hn.data(), nrm, sizeof(double) * fill, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+          cudaStreamSynchronize(s) != cudaSuccess) { rc = MG_ECUDA; goto done; }
+      for (const Seg& g : segs) {
+        bool bad = false;
+        for (int q = 0; q < g.n; ++q) bad |= !std::isfinite(hn[g.off + q]);
+        if (bad) {
+          jobs[g.job].failed = true;
+          for (int q = 0; q < g.n; ++q) hn[g.off + q] = 0.0;
+          if (cudaMemsetAsync(W + g.off * md, 0, sizeof(double) * md * g.n, s) != cudaSuccess ||
+              cudaMemsetAsync(tau + g.off, 0, sizeof(double) * g.n, s) != cudaSuccess) { rc = MG_ECUDA; goto done; }
+        }
+      }
+      if ((rc = expm_chunk(ctx, eng, fill, W, tau, nrm, Ub, md, &st, &hn)) != MG_OK) goto done;
+      // fold each job's segment into its state
+      std::vector<ChainSeg> cs;
+      for (const Seg& g : segs) {
+        BatchJob& j = jobs[g.job];
+        if (j.output == MG_OUT_STATE) {
+          cs.push_back(ChainSeg{(int)g.job, g.off, g.n, j.done});
+        } else {
+          int span = 0;
+          if (reorth_every > 1) { span = 1; while (span * 2 <= reorth_every) span *= 2; if (span < 2) span = 0; }
+          double* prod;
+          if ((rc = tree_product(ctx, eng, g.n, Ub + g.off * md, &prod, span)) != MG_OK) goto done;
+          if (!j.init) {
+            if ((rc = launch_copy_strided(1, md, prod, md, j.state, md, s)) != MG_OK) goto done;
+            j.init = true;
+          } else {
+            double* acc2;
+            if ((rc = ws(ctx, WS_ACC2, md, &acc2)) != MG_OK) goto done;
+            if ((rc = eng.reserve(1)) != MG_OK) goto done;
+            if ((rc = eng.prepA(1, prod, md)) != MG_OK) goto done;
+            if ((rc = eng.prepB(0, 1, j.state, md)) != MG_OK) goto done;
+            AddTerms none;
+            if ((rc = eng.mul(1, prod, md, 0, j.state, md, acc2, md, none)) != MG_OK) goto done;
+            if ((rc = launch_copy_strided(1, md, acc2, md, j.state, md, s)) != MG_OK) goto done;
+          }
+          if (reorth_every > 0 && (j.done + g.n) / reorth_every != j.done / reorth_every)
+            if ((rc = reorth_batch(ctx, eng, 1, j.state, md)) != MG_OK) goto done;
+        }
+        j.done += g.n;
+      }
+      if (!cs.empty()) {
+        const double* Uf = Ub;
+        if (eng.df()) {
+          double* conv;
+          if ((rc = ws(ctx, WS_NS_Z, md * fill, &conv)) != MG_OK) goto done;
+          if ((rc = eng.to_fp64(fill, Ub, md, conv, md)) != MG_OK) goto done;
+          Uf = conv;
+        }
+        if (cudaMemcpyAsync(segs_dev, cs.data(), sizeof(ChainSeg) * cs.size(), cudaMemcpyHostToDevice, s) !=
+            cudaSuccess) { rc = MG_ECUDA; goto done; }
+        if ((rc = launch_multi_chain((int)cs.size(), dp, segs_dev, Uf, md, psi_dev, reorth_every, s)) != MG_OK)
+          goto done;
+        // the segment table is host memory reused next chunk
+        if (cudaStreamSynchronize(s) != cudaSuccess) { rc = MG_ECUDA; goto done; }
+      }
+    }
+    // results
+    for (auto& j : jobs) {
+      const int d = j.p->d;
+      if (j.output == MG_OUT_STATE) {
+        if (cudaMemcpyAsync(out[j.idx], j.state, sizeof(double) * 2 * d, d2h, s) != cudaSuccess) { rc = MG_ECUDA; goto done; }
+      } else {
+        double *f, *t;
+        if ((rc = ws(ctx, WS_NS_G, md, &f)) != MG_OK) goto done;
+        if ((rc = ws(ctx, WS_OUT, mat_doubles(d), &t)) != MG_OK) goto done;
+        if (!j.init) { if ((rc = eng.identity(1, j.state)) != MG_OK) goto done; }
+        if ((rc = eng.to_fp64(1, j.state, md, f, md)) != MG_OK) goto done;
+        if ((rc = launch_unpad_copy(d, dp, f, t, s)) != MG_OK) goto done;
+        if (cudaMemcpyAsync(out[j.idx], t, sizeof(double) * mat_doubles(d), d2h, s) != cudaSuccess) { rc = MG_ECUDA; goto done; }
+        if (cudaStreamSynchronize(s) != cudaSuccess) { rc = MG_ECUDA; goto done; }
+      }
+      if (job_status) job_status[j.idx] = j.failed ? MG_ENONFINITE : MG_OK;
+    }
+    if (cudaStreamSynchronize(s) != cudaSuccess) rc = MG_ECUDA;
+  }
+done:
+  cudaStreamSynchronize(s);
+  for (void* q : owned) cudaFree(q);
+  if (rc == MG_OK && prec == MG_PREC_SPLIT) rc = check_status(ctx);
+  return rc;
+}
+
+}  // namespace
+
+int mg_evolve_batch(mg_ctx* ctx, int n, mg_plan* const* plans, const int* outputs, const double* const* in,
+                    double* const* out, int reorth_every, int flags, int* job_status) {
+  if (!ctx || n < 1 || !plans || !outputs || !out || reorth_every < 0) return MG_EINVAL;
+  MG_CUDA_TRY(cudaSetDevice(ctx->device));
+  // group by (precision, digits, padded dimension); one group at a time
+  struct Key { int prec, L, dp; bool operator<(const Key& o) const {
+      return prec != o.prec ? prec < o.prec : (L != o.L ? L < o.L : dp < o.dp); } };
+  std::vector<std::pair<Key, BatchJob>> all;
+  for (int i = 0; i < n; ++i) {
+    mg_plan* p = plans[i];
+    if (!p || p->ctx != ctx || p->N < 1 || !out[i] ||
+        (outputs[i] != MG_OUT_STATE && outputs[i] != MG_OUT_PROPAGATOR)) return MG_EINVAL;
+    if (outputs[i] == MG_OUT_STATE && p->d > 256 && round_dim(p->d) > 256) {
+      set_last_message("mg_evolve_batch: state jobs need d <= 256 (job %d has d = %d)", i, p->d);
+      return MG_EUNSUPPORTED;
+    }
+    BatchJob j;
+    j.idx = i;
+    j.p = p;
+    j.output = outputs[i];
+    const int L = p->precision == MG_PREC_SPLIT ? p->L : 0;
+    all.push_back({Key{p->precision, L, round_dim(p->d)}, j});
+  }
+  std::stable_sort(all.begin(), all.end(), [](const auto& a, const auto& b) { return a.first < b.first; });
+  int rc = MG_OK;
+  for (size_t g0 = 0; g0 < all.size() && rc == MG_OK;) {
+    size_t g1 = g0;
+    std::vector<BatchJob> jobs;
+    while (g1 < all.size() && !(all[g0].first < all[g1].first) && !(all[g1].first < all[g0].first)) {
+      jobs.push_back(all[g1].second);
+      ++g1;
+    }
+    const Key k = all[g0].first;
+    rc = run_group(ctx, jobs, k.dp, k.prec, k.L == 0 ? 6 : k.L, in, out, reorth_every, flags, job_status);
+    g0 = g1;
+  }
+  return rc;
 }
 
 }  // extern "C"

@@ -129,6 +129,19 @@ int split_gemm(int d, int L, int batch, const void* abuf, const void* bbuf, doub
 int launch_state_chain(int n_steps, int d, const double* U, long long sU, double* psi, double* tmp,
                        int reorth_every, int step_offset, cudaStream_t s);
 int launch_norm_defect(int d, const double* psi, double* out, cudaStream_t s);
+// A job's stretch of intervals inside a chunk of the batched path.
+struct ChainSeg {
+  int job;          // index into the per-job state arrays
+  int first;        // first interval of the segment within the chunk
+  int count;        // intervals in the segment
+  int done_before;  // intervals of this job already applied (for the re-normalisation period)
+};
+int launch_multi_chain(int nseg, int d, const ChainSeg* segs_dev, const double* U, long long sU,
+                       double* const* psi_dev, int reorth_every, cudaStream_t s);
+// dst (dp x dp, zero padded) <- src (d x d), for `count` stacked matrices
+int launch_pad_copy(int count, int d, int dp, const double* src, double* dst, cudaStream_t s);
+// dst (d x d) <- top-left block of src (dp x dp)
+int launch_unpad_copy(int d, int dp, const double* src, double* dst, cudaStream_t s);
 
 // Double-float (DF32) elementwise kernels of the split path; see elementwise.cu.
 int launch_scale_minus_i_df(int batch, int d, const double* src_fp64, double* dst_df, int sq, cudaStream_t s);

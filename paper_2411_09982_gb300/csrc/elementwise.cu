@@ -302,4 +302,41 @@ int launch_fp64_to_df(int batch, int d, const double* src, long long ss, double*
   return check_launch("fp64_to_df_kernel");
 }
 
+// ---------------------------------------------------------------------------
+// zero padding of operators to a bucket dimension (exact: exp of a block-diagonal
+// matrix with a zero block is the identity on that block)
+__global__ void pad_copy_kernel(long long total, int d, int dp, const double2* __restrict__ src,
+                                double2* __restrict__ dst) {
+  const long long per = (long long)dp * dp;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long m = e / per, r = e % per;
+    const int i = (int)(r / dp), j = (int)(r % dp);
+    dst[e] = (i < d && j < d) ? src[m * (long long)d * d + (long long)i * d + j] : make_double2(0.0, 0.0);
+  }
+}
+
+int launch_pad_copy(int count, int d, int dp, const double* src, double* dst, cudaStream_t s) {
+  const long long total = (long long)count * dp * dp;
+  if (total == 0) return MG_OK;
+  pad_copy_kernel<<<grid_for(total), 256, 0, s>>>(total, d, dp, reinterpret_cast<const double2*>(src),
+                                                 reinterpret_cast<double2*>(dst));
+  return check_launch("pad_copy_kernel");
+}
+
+__global__ void unpad_copy_kernel(int d, int dp, const double2* __restrict__ src, double2* __restrict__ dst) {
+  const long long total = (long long)d * d;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(e / d), j = (int)(e % d);
+    dst[e] = src[(long long)i * dp + j];
+  }
+}
+
+int launch_unpad_copy(int d, int dp, const double* src, double* dst, cudaStream_t s) {
+  unpad_copy_kernel<<<grid_for((long long)d * d), 256, 0, s>>>(d, dp, reinterpret_cast<const double2*>(src),
+                                                                reinterpret_cast<double2*>(dst));
+  return check_launch("unpad_copy_kernel");
+}
+
 }  // namespace mg

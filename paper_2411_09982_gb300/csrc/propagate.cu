@@ -13,13 +13,12 @@ namespace mg {
 
 constexpr int CHAIN_THREADS = 1024;
 
-__global__ void __launch_bounds__(CHAIN_THREADS)
-state_chain_kernel(int n_steps, int d, const double* __restrict__ U, long long sU,
-                   double* __restrict__ psi, int reorth_every, int step_offset) {
-  extern __shared__ double2 sh[];
+// One CTA carries psi (d complex, global) through n_steps propagators.
+__device__ void chain_body(int n_steps, int d, const double* __restrict__ U, long long sU,
+                           double* __restrict__ psi, int reorth_every, int step_offset, double2* sh,
+                           double* red) {
   double2* cur = sh;
   double2* nxt = sh + d;
-  __shared__ double red[CHAIN_THREADS / 32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int i = threadIdx.x; i < d; i += blockDim.x) cur[i] = reinterpret_cast<double2*>(psi)[i];
   __syncthreads();
@@ -62,6 +61,24 @@ state_chain_kernel(int n_steps, int d, const double* __restrict__ U, long long s
     }
   }
   for (int i = threadIdx.x; i < d; i += blockDim.x) reinterpret_cast<double2*>(psi)[i] = cur[i];
+}
+
+__global__ void __launch_bounds__(CHAIN_THREADS)
+state_chain_kernel(int n_steps, int d, const double* __restrict__ U, long long sU,
+                   double* __restrict__ psi, int reorth_every, int step_offset) {
+  extern __shared__ double2 sh[];
+  __shared__ double red[CHAIN_THREADS / 32];
+  chain_body(n_steps, d, U, sU, psi, reorth_every, step_offset, sh, red);
+}
+
+// Many jobs at once: CTA b carries job segs[b].job through its segment of the chunk.
+__global__ void __launch_bounds__(CHAIN_THREADS)
+multi_chain_kernel(int d, const ChainSeg* __restrict__ segs, const double* __restrict__ U, long long sU,
+                   double* const* __restrict__ psi, int reorth_every) {
+  extern __shared__ double2 sh[];
+  __shared__ double red[CHAIN_THREADS / 32];
+  const ChainSeg g = segs[blockIdx.x];
+  chain_body(g.count, d, U + g.first * sU, sU, psi[g.job], reorth_every, g.done_before, sh, red);
 }
 
 // out = U psi (one interval), rows split over CTAs: 8 warps per CTA, one row per warp.
@@ -144,6 +161,15 @@ int launch_state_chain(int n_steps, int d, const double* U, long long sU, double
   }
   if (a != psi) MG_CUDA_TRY(cudaMemcpyAsync(psi, a, sizeof(double) * 2 * d, cudaMemcpyDeviceToDevice, s));
   return MG_OK;
+}
+
+int launch_multi_chain(int nseg, int d, const ChainSeg* segs_dev, const double* U, long long sU,
+                       double* const* psi_dev, int reorth_every, cudaStream_t s) {
+  if (nseg <= 0) return MG_OK;
+  if (d > 256) return MG_EUNSUPPORTED;
+  const int threads = d <= 32 ? 256 : CHAIN_THREADS;
+  multi_chain_kernel<<<nseg, threads, sizeof(double2) * 2 * d, s>>>(d, segs_dev, U, sU, psi_dev, reorth_every);
+  return check_launch("multi_chain_kernel");
 }
 
 int launch_norm_defect(int d, const double* psi, double* out, cudaStream_t s) {

@@ -69,6 +69,7 @@ SIGNATURES = {
     "mg_plan_destroy": (_I, [_P]),
     "mg_set_controls": (_I, [_P, _I, _I, _D, _D, _P, _P, _I]),
     "mg_evolve": (_I, [_P, _I, _P, _P, _I, _I, ctypes.POINTER(mg_report)]),
+    "mg_evolve_batch": (_I, [_P, _I, _P, _P, _P, _P, _I, _I, _P]),
     "mg_coefficients": (_I, [_P, _I, _I, _I, _D, _P, _P, _P]),
     "mg_build_omega": (_I, [_P, _I, _I, _I, _D, _P, _P, _P, _P, _P, _P]),
     "mg_expm": (_I, [_P, _I, _I, _P, _P, _I, _I, _P]),
@@ -212,6 +213,23 @@ class Plan:
 # ----------------------------------------------------------------------------
 # functional entry points (same names as the C ABI)
 # ----------------------------------------------------------------------------
+def mg_evolve_batch(ctx, plans, outputs, inputs, outs, reorth_every=0, host=False):
+    """Evolve many plans together; returns the per-job status list."""
+    n = len(plans)
+    PA = ctypes.c_void_p * n
+    IA = ctypes.c_int * n
+    hp = PA(*[p.h.value for p in plans])
+    oa = IA(*outputs)
+    ia = PA(*[(t.data_ptr() if t is not None else None) for t in inputs])
+    oa2 = PA(*[t.data_ptr() for t in outs])
+    st = IA(*([0] * n))
+    _check(load().mg_evolve_batch(ctx.h, n, ctypes.cast(hp, ctypes.c_void_p), ctypes.cast(oa, ctypes.c_void_p),
+                                  ctypes.cast(ia, ctypes.c_void_p), ctypes.cast(oa2, ctypes.c_void_p), reorth_every,
+                                  MG_FLAG_HOST_PTRS if host else 0, ctypes.cast(st, ctypes.c_void_p)),
+           "mg_evolve_batch")
+    return list(st)
+
+
 def mg_quadrature_nodes(P: int):
     import numpy as np
     lib = load()

@@ -260,3 +260,118 @@ def test_evolve_host_pointers_match_device(ctx):
     plan.evolve(M.MG_OUT_STATE, torch.from_numpy(wl.psi0), out_h, host=True)
     ref = oracle.evolve_workload(wl)
     assert np.abs(out_h.numpy() - ref).max() <= 1e-11
+
+
+# ----------------------------------------------------------------------------
+# many uneven jobs in shared launches (mg_evolve_batch)
+# ----------------------------------------------------------------------------
+def _small_jobs(seed=21, n=10):
+    rng = np.random.default_rng(seed)
+    jobs = []
+    for i in range(n):
+        wl = W.random_instance(rng, name=f"job{i}", N_range=(5, 40), d_range=(16, 110))
+        if i % 3 == 2:
+            wl.psi0 = None   # full propagator
+        jobs.append(wl)
+    # a few fixed odd sizes
+    jobs.append(W.transmon_resonator(nt=3, nr=7, N=17, name="d21"))
+    jobs.append(W.transmon_resonator(nt=2, nr=3, N=9, name="d6", unitary=True))
+    return jobs
+
+
+@pytest.mark.parametrize("prec,L,tol", [(0, 6, 1e-11), (1, 6, 1e-6)])
+def test_evolve_batch_matches_oracle_per_job(ctx, prec, L, tol):
+    jobs = _small_jobs()
+    plans, outs, ins, kinds = [], [], [], []
+    for wl in jobs:
+        samples, w = M.node_samples(wl)
+        p = M.Plan(ctx, cuda(wl.H0), cuda(wl.Hk), prec, L)
+        p.set_controls(wl.N, wl.P, wl.t0, wl.dt, w, cuda(samples))
+        plans.append(p)
+        if wl.psi0 is None:
+            kinds.append(M.MG_OUT_PROPAGATOR)
+            ins.append(None)
+            outs.append(torch.empty((wl.d, wl.d), dtype=torch.complex128, device="cuda"))
+        else:
+            kinds.append(M.MG_OUT_STATE)
+            ins.append(cuda(wl.psi0))
+            outs.append(torch.empty(wl.d, dtype=torch.complex128, device="cuda"))
+    status = M.mg_evolve_batch(ctx, plans, kinds, ins, outs)
+    torch.cuda.synchronize()
+    assert status == [0] * len(jobs)
+    for wl, o in zip(jobs, outs):
+        ref = oracle.evolve_workload(wl)
+        err = np.abs(o.cpu().numpy() - ref).max()
+        assert err <= tol, (wl.name, wl.d, wl.N, err)
+    for p in plans:
+        p.close()
+
+
+def test_evolve_batch_result_same_alone_and_in_mix(ctx):
+    """A job's result does not depend on the other jobs of the batch (within the split tolerance)."""
+    jobs = _small_jobs(seed=5, n=8)
+    target = W.transmon_resonator(nt=4, nr=9, N=33, name="target")
+    alone, _ = M.evolve_workload(ctx, target, M.MG_PREC_SPLIT, 6)
+    plans, outs, ins, kinds = [], [], [], []
+    for wl in jobs[:4] + [target] + jobs[4:]:
+        samples, w = M.node_samples(wl)
+        p = M.Plan(ctx, cuda(wl.H0), cuda(wl.Hk), M.MG_PREC_SPLIT, 6)
+        p.set_controls(wl.N, wl.P, wl.t0, wl.dt, w, cuda(samples))
+        plans.append(p)
+        state = wl.psi0 is not None
+        kinds.append(M.MG_OUT_STATE if state else M.MG_OUT_PROPAGATOR)
+        ins.append(cuda(wl.psi0) if state else None)
+        outs.append(torch.empty(wl.d if state else (wl.d, wl.d), dtype=torch.complex128, device="cuda"))
+    M.mg_evolve_batch(ctx, plans, kinds, ins, outs)
+    torch.cuda.synchronize()
+    assert np.abs(outs[4].cpu().numpy() - alone.cpu().numpy()).max() <= 1e-6
+    for p in plans:
+        p.close()
+
+
+def test_evolve_batch_nonfinite_job_fails_alone(ctx):
+    jobs = _small_jobs(seed=9, n=4)
+    plans, outs, ins, kinds = [], [], [], []
+    for i, wl in enumerate(jobs):
+        samples, w = M.node_samples(wl)
+        if i == 1:
+            samples = samples.copy()
+            samples[2, 3, 0] = np.nan
+        p = M.Plan(ctx, cuda(wl.H0), cuda(wl.Hk), M.MG_PREC_FP64)
+        p.set_controls(wl.N, wl.P, wl.t0, wl.dt, w, cuda(samples))
+        plans.append(p)
+        state = wl.psi0 is not None
+        kinds.append(M.MG_OUT_STATE if state else M.MG_OUT_PROPAGATOR)
+        ins.append(cuda(wl.psi0) if state else None)
+        outs.append(torch.empty(wl.d if state else (wl.d, wl.d), dtype=torch.complex128, device="cuda"))
+    status = M.mg_evolve_batch(ctx, plans, kinds, ins, outs)
+    torch.cuda.synchronize()
+    assert status[1] == M.MG_ENONFINITE
+    for i, (wl, o) in enumerate(zip(jobs, outs)):
+        if i == 1:
+            continue
+        assert status[i] == 0
+        assert np.abs(o.cpu().numpy() - oracle.evolve_workload(wl)).max() <= 1e-11
+    for p in plans:
+        p.close()
+
+
+def test_evolve_nonfinite_samples_rejected(ctx):
+    wl = W.config(0, N=20)
+    samples, w = M.node_samples(wl)
+    samples[3, 0, 0] = np.inf
+    p = M.Plan(ctx, cuda(wl.H0), cuda(wl.Hk))
+    p.set_controls(wl.N, wl.P, wl.t0, wl.dt, w, cuda(samples))
+    out = torch.empty(wl.d, dtype=torch.complex128, device="cuda")
+    with pytest.raises(M.MagnusError) as e:
+        p.evolve(M.MG_OUT_STATE, cuda(wl.psi0), out)
+    assert e.value.code == M.MG_ENONFINITE
+    p.close()
+
+
+def test_plan_rejects_non_hermitian_operator(ctx):
+    rng = np.random.default_rng(0)
+    H0 = rand_c(rng, (5, 5))
+    with pytest.raises(M.MagnusError) as e:
+        M.Plan(ctx, cuda(H0), cuda(rand_herm(rng, 5)[None]), flags=M.MG_FLAG_CHECK_HERMITIAN)
+    assert e.value.code == M.MG_ENOTHERM
