@@ -119,6 +119,8 @@ int mg_quadrature_nodes(int P, double* x, double* w);
  * MG_FLAG_NO_TRACE_SHIFT.  1 <= d <= 4096, 0 <= K <= 64. */
 int mg_plan_create(mg_ctx* ctx, mg_plan** out, int d, int K, const double* H0,
                    const double* Hk, int precision, int slices, int flags);
+/* Free the plan's device memory.  Does not use the plan's context, so plans may
+ * be destroyed before or after their context. */
 int mg_plan_destroy(mg_plan* plan);
 
 /* Replace the control signals (the `update_control_sigs()` step of App. A.5).

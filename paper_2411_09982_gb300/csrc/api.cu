@@ -713,9 +713,10 @@ int mg_plan_create(mg_ctx* ctx, mg_plan** out, int d, int K, const double* H0, c
   return MG_OK;
 }
 
+// A plan owns only its device buffers: destroying it never touches its context
+// (which the caller may already have destroyed).  cudaFree waits for the device.
 int mg_plan_destroy(mg_plan* p) {
   if (!p) return MG_EINVAL;
-  if (p->ctx) cudaStreamSynchronize(p->ctx->stream);
   cudaFree(p->H0);
   cudaFree(p->Hk);
   cudaFree(p->w);

@@ -296,15 +296,20 @@ def test_evolve_batch_matches_oracle_per_job(ctx, prec, L, tol):
             kinds.append(M.MG_OUT_STATE)
             ins.append(cuda(wl.psi0))
             outs.append(torch.empty(wl.d, dtype=torch.complex128, device="cuda"))
-    status = M.mg_evolve_batch(ctx, plans, kinds, ins, outs)
-    torch.cuda.synchronize()
-    assert status == [0] * len(jobs)
-    for wl, o in zip(jobs, outs):
-        ref = oracle.evolve_workload(wl)
-        err = np.abs(o.cpu().numpy() - ref).max()
-        assert err <= tol, (wl.name, wl.d, wl.N, err)
-    for p in plans:
-        p.close()
+    try:
+        status = M.mg_evolve_batch(ctx, plans, kinds, ins, outs)
+        torch.cuda.synchronize()
+        assert status == [0] * len(jobs)
+        for wl, o in zip(jobs, outs):
+            ref, parts = oracle.evolve_workload(wl, return_parts=True)
+            # rounding grows with the phase of the exponent: these random jobs have
+            # |Hbar_n| up to ~1e4 rad (few long intervals), the named workloads ~20
+            hmax = max(np.abs(h).sum(axis=0).max() for h in parts["Hbar"])
+            err = np.abs(o.cpu().numpy() - ref).max()
+            assert err <= tol * max(1.0, hmax / 25.0), (wl.name, wl.d, wl.N, hmax, err)
+    finally:
+        for p in plans:
+            p.close()
 
 
 def test_evolve_batch_result_same_alone_and_in_mix(ctx):
