@@ -157,6 +157,54 @@ int mg_evolve(mg_plan* plan, int output, const double* in, double* out, int reor
 int mg_evolve_batch(mg_ctx* ctx, int n, mg_plan* const* plans, const int* outputs, const double* const* in,
                     double* const* out, int reorth_every, int flags, int* job_status);
 
+/* ---- serving ---------------------------------------------------------------- */
+/* A request loop over one context: mg_submit admits a job if its device memory
+ * (padded operators, coefficients, state, upload staging) fits the budget next
+ * to the jobs already resident, otherwise returns MG_EAGAIN; the job's inputs
+ * are uploaded on a separate stream and stay resident until it completes.  A
+ * worker thread repeatedly takes every admitted job that shares the oldest
+ * job's (precision, padded dimension) key and advances each by up to
+ * `quantum_intervals` intervals in one shared chunk step (batched exponential,
+ * multi-job propagation), admitting new arrivals at every chunk boundary, so
+ * requests that arrive while others run join them on the device instead of
+ * waiting for them to finish (continuous batching).  While a server runs, the
+ * caller must not use its context for anything else. */
+typedef struct mg_server mg_server;
+
+typedef struct mg_job {
+  int d, K;                 /* dimension, number of controls */
+  const double* H0;         /* d x d complex */
+  const double* Hk;         /* K x d x d complex */
+  int N, P;                 /* intervals, quadrature points per interval */
+  double t0, dt;
+  const double* w;          /* P quadrature weights (HOST) */
+  const double* samples;    /* N x P x K drive samples at the nodes of mg_quadrature_nodes */
+  int output;               /* MG_OUT_STATE (in = psi0) or MG_OUT_PROPAGATOR (in must be NULL) */
+  const double* in;
+  double* out;              /* written when the job completes; keep it valid until mg_wait returns */
+  int precision, slices;
+  int flags;                /* MG_FLAG_HOST_PTRS: H0, Hk, samples, in and out are host memory */
+} mg_job;
+
+typedef struct mg_job_report {
+  int32_t status;           /* MG_OK or the job's error */
+  double latency_ms;        /* submit -> result written */
+  double queue_ms;          /* submit -> first chunk step */
+  int64_t intervals;
+} mg_job_report;
+
+int mg_server_create(mg_ctx* ctx, size_t mem_budget_bytes, int quantum_intervals, mg_server** out);
+int mg_submit(mg_server* srv, const mg_job* job, uint64_t* job_id);
+/* Block until the job completes (timeout_s < 0: no limit).  Returns the job's
+ * status, or MG_ETIMEOUT if it has not completed in time (the job keeps
+ * running and can be waited for again).  A completed job is forgotten once
+ * waited for. */
+int mg_wait(mg_server* srv, uint64_t job_id, double timeout_s, mg_job_report* rep);
+/* Latency percentiles of completed jobs and intervals completed per second of
+ * wall time since the first submission. */
+int mg_server_stats(mg_server* srv, double* p50_ms, double* p99_ms, double* intervals_per_s, int64_t* completed);
+int mg_server_destroy(mg_server* srv);
+
 /* ---- steps of the path (device pointers) --------------------------------- */
 /* c[n][k] = (dt/2) sum_p w[p] samples[n][p][k]   (Eq. magnus-first-order-coeff).
  * samples N x P x K, w P doubles (device), c N x K. */

@@ -18,7 +18,12 @@
 #include <cstring>
 #include <algorithm>
 #include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <map>
 #include <mutex>
+#include <thread>
 #include <string>
 #include <vector>
 
@@ -1040,29 +1045,173 @@ int mg_propagate(mg_ctx* ctx, int N, int d, const double* U, int output, const d
 // ---------------------------------------------------------------------------
 namespace {
 
+// One job of the batched path (mg_evolve_batch) or of the server.
 struct BatchJob {
-  int idx;          // position in the caller's arrays
-  mg_plan* p;
-  int output;
-  const double* H0;  // padded operators (device)
-  const double* Hk;
-  double* state;     // padded psi (d_pad) or running product (d_pad x d_pad, engine storage)
+  int idx = 0;                // position in the caller's arrays (batch) / unused (server)
+  int output = MG_OUT_STATE;
+  int d = 0, K = 0, N = 0;
+  double dt = 0.0;
+  const double* H0 = nullptr;  // operators padded to the group dimension (device)
+  const double* Hk = nullptr;
+  const double* c = nullptr;   // quadrature coefficients N x K (device)
+  double* state = nullptr;     // padded psi (dp) or running product (dp x dp, engine storage)
   bool init = false;
   bool failed = false;
-  int done = 0;
+  int done = 0;                // intervals applied so far
 };
 
 int round_dim(int d) { return ((d + 15) / 16) * 16; }
 
+struct ChunkSeg {
+  BatchJob* job;
+  int a, n, off;   // job-local first interval, count, offset in the chunk
+};
+
+// One chunk step shared by mg_evolve_batch and the server: Hbar_n of every
+// segment, one batched exponential for the whole chunk, then every job's
+// segment folded into its state (multi-job chain launch for states, tree
+// product for propagators).  segs_dev / psi_dev: device scratch for the chain
+// launch (capacity >= number of segments).
+int process_chunk(mg_ctx* ctx, Engine& eng, std::vector<ChunkSeg>& segs, int fill, int reorth_every,
+                  ChainSeg* segs_dev, double** psi_dev, ExpmStats* st) {
+  cudaStream_t s = ctx->stream;
+  const int dp = eng.d;
+  const long long md = mat_doubles(dp);
+  double *W, *tau, *nrm, *Ub, *sc;
+  MG_TRY(ws(ctx, WS_W, md * fill, &W));
+  MG_TRY(ws(ctx, WS_TAU, fill, &tau));
+  MG_TRY(ws(ctx, WS_NORM, fill, &nrm));
+  MG_TRY(ws(ctx, WS_UBUF, md * fill, &Ub));
+  for (const ChunkSeg& g : segs) {
+    const BatchJob& j = *g.job;
+    MG_TRY(small_scratch(ctx, (size_t)j.K + 1 + g.n, &sc));
+    MG_TRY(launch_build_omega(g.n, dp, j.K, j.dt, j.H0, j.Hk, j.c + (long long)g.a * j.K, W + g.off * md,
+                              tau + g.off, nrm + g.off, 1, 1, sc, s));
+  }
+  // FP64 norms: a non-finite norm fails its job only (its exponents are zeroed)
+  std::vector<double> hn(fill);
+  MG_CUDA_TRY(cudaMemcpyAsync(hn.data(), nrm, sizeof(double) * fill, cudaMemcpyDeviceToHost, s));
+  MG_CUDA_TRY(cudaStreamSynchronize(s));
+  for (const ChunkSeg& g : segs) {
+    bool bad = false;
+    for (int q = 0; q < g.n; ++q) bad |= !std::isfinite(hn[g.off + q]);
+    if (bad) {
+      g.job->failed = true;
+      for (int q = 0; q < g.n; ++q) hn[g.off + q] = 0.0;
+      MG_CUDA_TRY(cudaMemsetAsync(W + g.off * md, 0, sizeof(double) * md * g.n, s));
+      MG_CUDA_TRY(cudaMemsetAsync(tau + g.off, 0, sizeof(double) * g.n, s));
+    }
+  }
+  MG_TRY(expm_chunk(ctx, eng, fill, W, tau, nrm, Ub, md, st, &hn));
+  std::vector<ChainSeg> cs;
+  std::vector<double*> psis;
+  for (const ChunkSeg& g : segs) {
+    BatchJob& j = *g.job;
+    if (j.output == MG_OUT_STATE) {
+      cs.push_back(ChainSeg{(int)psis.size(), g.off, g.n, j.done});
+      psis.push_back(j.state);
+    } else {
+      int span = 0;
+      if (reorth_every > 1) { span = 1; while (span * 2 <= reorth_every) span *= 2; if (span < 2) span = 0; }
+      double* prod;
+      MG_TRY(tree_product(ctx, eng, g.n, Ub + g.off * md, &prod, span));
+      if (!j.init) {
+        MG_TRY(launch_copy_strided(1, md, prod, md, j.state, md, s));
+        j.init = true;
+      } else {
+        double* acc2;
+        MG_TRY(ws(ctx, WS_ACC2, md, &acc2));
+        MG_TRY(eng.reserve(1));
+        MG_TRY(eng.prepA(1, prod, md));
+        MG_TRY(eng.prepB(0, 1, j.state, md));
+        AddTerms none;
+        MG_TRY(eng.mul(1, prod, md, 0, j.state, md, acc2, md, none));
+        MG_TRY(launch_copy_strided(1, md, acc2, md, j.state, md, s));
+      }
+      if (reorth_every > 0 && (j.done + g.n) / reorth_every != j.done / reorth_every)
+        MG_TRY(reorth_batch(ctx, eng, 1, j.state, md));
+    }
+    j.done += g.n;
+  }
+  if (!cs.empty()) {
+    const double* Uf = Ub;
+    if (eng.df()) {
+      double* conv;
+      MG_TRY(ws(ctx, WS_NS_Z, md * fill, &conv));
+      MG_TRY(eng.to_fp64(fill, Ub, md, conv, md));
+      Uf = conv;
+    }
+    MG_CUDA_TRY(cudaMemcpyAsync(segs_dev, cs.data(), sizeof(ChainSeg) * cs.size(), cudaMemcpyHostToDevice, s));
+    MG_CUDA_TRY(cudaMemcpyAsync(psi_dev, psis.data(), sizeof(double*) * psis.size(), cudaMemcpyHostToDevice, s));
+    if (dp <= 256) {
+      MG_TRY(launch_multi_chain((int)cs.size(), dp, segs_dev, Uf, md, psi_dev, reorth_every, s));
+    } else {
+      double* tmp;
+      MG_TRY(ws(ctx, WS_VEC, 2 * dp + 2, &tmp));
+      for (size_t q = 0; q < cs.size(); ++q)
+        MG_TRY(launch_state_chain(cs[q].count, dp, Uf + cs[q].first * md, md, psis[q], tmp + 2, reorth_every,
+                                  cs[q].done_before, s));
+    }
+    // the host tables above are reused by the next chunk
+    MG_CUDA_TRY(cudaStreamSynchronize(s));
+  }
+  return MG_OK;
+}
+
+// Final value of a job: psi (first d entries) or the top-left d x d block of U.
+int write_job_output(mg_ctx* ctx, Engine& eng, BatchJob& j, double* out, cudaMemcpyKind kind) {
+  cudaStream_t s = ctx->stream;
+  const int dp = eng.d, d = j.d;
+  const long long md = mat_doubles(dp);
+  if (j.output == MG_OUT_STATE) {
+    MG_CUDA_TRY(cudaMemcpyAsync(out, j.state, sizeof(double) * 2 * d, kind, s));
+  } else {
+    double *f, *t;
+    MG_TRY(ws(ctx, WS_NS_G, md, &f));
+    MG_TRY(ws(ctx, WS_OUT, mat_doubles(d), &t));
+    if (!j.init) MG_TRY(eng.identity(1, j.state));
+    MG_TRY(eng.to_fp64(1, j.state, md, f, md));
+    MG_TRY(launch_unpad_copy(d, dp, f, t, s));
+    MG_CUDA_TRY(cudaMemcpyAsync(out, t, sizeof(double) * mat_doubles(d), kind, s));
+  }
+  MG_CUDA_TRY(cudaStreamSynchronize(s));
+  return MG_OK;
+}
+
+// Initial state of a job: psi0 padded with zeros, or U0 padded with the identity.
+int init_job_state(mg_ctx* ctx, Engine& eng, BatchJob& j, const double* in, cudaMemcpyKind kind,
+                   cudaStream_t s) {
+  const int dp = eng.d, d = j.d;
+  const long long md = mat_doubles(dp);
+  if (j.output == MG_OUT_STATE) {
+    if (!in) return MG_EINVAL;
+    MG_CUDA_TRY(cudaMemsetAsync(j.state, 0, sizeof(double) * 2 * dp, s));
+    MG_CUDA_TRY(cudaMemcpyAsync(j.state, in, sizeof(double) * 2 * d, kind, s));
+    j.init = true;
+  } else if (in) {
+    // U0 -> FP64 identity-padded -> engine storage; uses the context workspace
+    double *t, *tp;
+    MG_TRY(ws(ctx, WS_OUT, mat_doubles(d), &t));
+    MG_TRY(ws(ctx, WS_NS_Z, md, &tp));
+    MG_CUDA_TRY(cudaMemcpyAsync(t, in, sizeof(double) * mat_doubles(d), kind, s));
+    MG_TRY(launch_identity(1, dp, tp, s));
+    MG_TRY(launch_pad_into(d, dp, t, tp, s));
+    MG_TRY(eng.from_fp64(1, tp, md, j.state, md));
+    j.init = true;
+  }
+  return MG_OK;
+}
+
 // Run all jobs of one (precision, digits, padded dimension) group.
-int run_group(mg_ctx* ctx, std::vector<BatchJob>& jobs, int dp, int prec, int L, const double* const* in,
-              double* const* out, int reorth_every, int flags, int* job_status) {
+int run_group(mg_ctx* ctx, std::vector<BatchJob>& jobs, std::vector<mg_plan*>& plans, int dp, int prec, int L,
+              const double* const* in, double* const* out, int reorth_every, int flags, int* job_status) {
   cudaStream_t s = ctx->stream;
   Engine eng{ctx, dp, prec, L};
   const long long md = mat_doubles(dp);
   const cudaMemcpyKind h2d = (flags & MG_FLAG_HOST_PTRS) ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
   const cudaMemcpyKind d2h = (flags & MG_FLAG_HOST_PTRS) ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
   std::vector<void*> owned;
+  int rc = MG_OK;
   auto dmalloc = [&](size_t bytes, void** ptr) -> int {
     if (cudaMalloc(ptr, bytes) != cudaSuccess) {
       cudaGetLastError();
@@ -1072,177 +1221,57 @@ int run_group(mg_ctx* ctx, std::vector<BatchJob>& jobs, int dp, int prec, int L,
     owned.push_back(*ptr);
     return MG_OK;
   };
-  int rc = MG_OK;
-  long long total = 0;
-  int nstate = 0;
-  for (auto& j : jobs) total += j.p->N;
-  // padded operators and per-job state
-  for (auto& j : jobs) {
-    const int d = j.p->d, K = j.p->K;
-    if (d == dp) {
-      j.H0 = j.p->H0;
-      j.Hk = j.p->Hk;
-    } else {
-      void* buf;
-      if ((rc = dmalloc(sizeof(double) * md * (1 + K), &buf)) != MG_OK) goto done;
-      double* H = reinterpret_cast<double*>(buf);
-      if ((rc = launch_pad_copy(1, d, dp, j.p->H0, H, s)) != MG_OK) goto done;
-      if (K > 0 && (rc = launch_pad_copy(K, d, dp, j.p->Hk, H + md, s)) != MG_OK) goto done;
-      j.H0 = H;
-      j.Hk = H + md;
-    }
-    void* st;
-    const size_t sb = j.output == MG_OUT_STATE ? sizeof(double) * 2 * dp : sizeof(double) * md;
-    if ((rc = dmalloc(sb, &st)) != MG_OK) goto done;
-    j.state = reinterpret_cast<double*>(st);
-    if (j.output == MG_OUT_STATE) {
-      ++nstate;
-      if (!in || !in[j.idx]) { rc = MG_EINVAL; goto done; }
-      if (cudaMemsetAsync(j.state, 0, sb, s) != cudaSuccess ||
-          cudaMemcpyAsync(j.state, in[j.idx], sizeof(double) * 2 * d, h2d, s) != cudaSuccess) {
-        rc = MG_ECUDA;
-        goto done;
+  auto body = [&]() -> int {
+    long long total = 0;
+    for (size_t q = 0; q < jobs.size(); ++q) {
+      BatchJob& j = jobs[q];
+      mg_plan* p = plans[q];
+      total += j.N;
+      if (j.d == dp) {
+        j.H0 = p->H0;
+        j.Hk = p->Hk;
+      } else {
+        void* buf;
+        MG_TRY(dmalloc(sizeof(double) * md * (1 + j.K), &buf));
+        double* H = reinterpret_cast<double*>(buf);
+        MG_TRY(launch_pad_copy(1, j.d, dp, p->H0, H, s));
+        if (j.K > 0) MG_TRY(launch_pad_copy(j.K, j.d, dp, p->Hk, H + md, s));
+        j.H0 = H;
+        j.Hk = H + md;
       }
-      j.init = true;
-    } else if (in && in[j.idx]) {
-      double *t, *tp;
-      if ((rc = ws(ctx, WS_OUT, mat_doubles(d), &t)) != MG_OK) goto done;
-      if ((rc = ws(ctx, WS_NS_Z, md, &tp)) != MG_OK) goto done;
-      if (cudaMemcpyAsync(t, in[j.idx], sizeof(double) * mat_doubles(d), h2d, s) != cudaSuccess) { rc = MG_ECUDA; goto done; }
-      if ((rc = launch_pad_copy(1, d, dp, t, tp, s)) != MG_OK) goto done;
-      // identity on the padded block keeps the padding exact
-      for (int q = d; q < dp; ++q) {
-        const double one = 1.0;
-        if (cudaMemcpyAsync(tp + 2 * ((long long)q * dp + q), &one, sizeof(double), cudaMemcpyHostToDevice, s) !=
-            cudaSuccess) { rc = MG_ECUDA; goto done; }
-        if (cudaStreamSynchronize(s) != cudaSuccess) { rc = MG_ECUDA; goto done; }
-      }
-      if ((rc = eng.from_fp64(1, tp, md, j.state, md)) != MG_OK) goto done;
-      j.init = true;
+      void* st;
+      MG_TRY(dmalloc(j.output == MG_OUT_STATE ? sizeof(double) * 2 * dp : sizeof(double) * md, &st));
+      j.state = reinterpret_cast<double*>(st);
+      MG_TRY(init_job_state(ctx, eng, j, in ? in[j.idx] : nullptr, h2d, s));
     }
-  }
-  {
-    // device array of state pointers for the multi-job chain kernel
-    void* pbuf;
-    if ((rc = dmalloc(sizeof(double*) * std::max<size_t>(1, jobs.size()), &pbuf)) != MG_OK) goto done;
-    double** psi_dev = reinterpret_cast<double**>(pbuf);
-    std::vector<double*> ptrs;
-    for (auto& j : jobs) ptrs.push_back(j.state);
-    if (cudaMemcpyAsync(psi_dev, ptrs.data(), sizeof(double*) * ptrs.size(), cudaMemcpyHostToDevice, s) != cudaSuccess ||
-        cudaStreamSynchronize(s) != cudaSuccess) { rc = MG_ECUDA; goto done; }
-    void* sbuf;
-    if ((rc = dmalloc(sizeof(ChainSeg) * std::max<size_t>(1, jobs.size()), &sbuf)) != MG_OK) goto done;
-    ChainSeg* segs_dev = reinterpret_cast<ChainSeg*>(sbuf);
-
+    void *pbuf, *sbuf;
+    MG_TRY(dmalloc(sizeof(double*) * jobs.size(), &pbuf));
+    MG_TRY(dmalloc(sizeof(ChainSeg) * jobs.size(), &sbuf));
     const int chunk = chunk_size(ctx, dp, prec, L, (int)std::min<long long>(total, 1 << 30), 1);
     size_t jcur = 0;
     int jlocal = 0;
     ExpmStats st;
     while (jcur < jobs.size()) {
-      // gather the chunk's segments
-      struct Seg { size_t job; int a, n, off; };
-      std::vector<Seg> segs;
+      std::vector<ChunkSeg> segs;
       int fill = 0;
       while (jcur < jobs.size() && fill < chunk) {
         BatchJob& j = jobs[jcur];
-        const int take = std::min(chunk - fill, j.p->N - jlocal);
-        segs.push_back({jcur, jlocal, take, fill});
+        const int take = std::min(chunk - fill, j.N - jlocal);
+        segs.push_back({&j, jlocal, take, fill});
         fill += take;
         jlocal += take;
-        if (jlocal == j.p->N) { ++jcur; jlocal = 0; }
+        if (jlocal == j.N) { ++jcur; jlocal = 0; }
       }
-      double *W, *tau, *nrm, *Ub, *sc;
-      if ((rc = ws(ctx, WS_W, md * fill, &W)) != MG_OK) goto done;
-      if ((rc = ws(ctx, WS_TAU, fill, &tau)) != MG_OK) goto done;
-      if ((rc = ws(ctx, WS_NORM, fill, &nrm)) != MG_OK) goto done;
-      if ((rc = ws(ctx, WS_UBUF, md * fill, &Ub)) != MG_OK) goto done;
-      for (const Seg& g : segs) {
-        BatchJob& j = jobs[g.job];
-        if ((rc = small_scratch(ctx, (size_t)j.p->K + 1 + g.n, &sc)) != MG_OK) goto done;
-        rc = launch_build_omega(g.n, dp, j.p->K, j.p->dt, j.H0, j.Hk, j.p->c + (long long)g.a * j.p->K,
-                                W + g.off * md, tau + g.off, nrm + g.off, 1, 1, sc, s);
-        if (rc != MG_OK) goto done;
-      }
-      // FP64 norms: a non-finite norm fails its job only (its exponents are zeroed)
-      std::vector<double> hn(fill);
-      if (cudaMemcpyAsync(hn.data(), nrm, sizeof(double) * fill, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-          cudaStreamSynchronize(s) != cudaSuccess) { rc = MG_ECUDA; goto done; }
-      for (const Seg& g : segs) {
-        bool bad = false;
-        for (int q = 0; q < g.n; ++q) bad |= !std::isfinite(hn[g.off + q]);
-        if (bad) {
-          jobs[g.job].failed = true;
-          for (int q = 0; q < g.n; ++q) hn[g.off + q] = 0.0;
-          if (cudaMemsetAsync(W + g.off * md, 0, sizeof(double) * md * g.n, s) != cudaSuccess ||
-              cudaMemsetAsync(tau + g.off, 0, sizeof(double) * g.n, s) != cudaSuccess) { rc = MG_ECUDA; goto done; }
-        }
-      }
-      if ((rc = expm_chunk(ctx, eng, fill, W, tau, nrm, Ub, md, &st, &hn)) != MG_OK) goto done;
-      // fold each job's segment into its state
-      std::vector<ChainSeg> cs;
-      for (const Seg& g : segs) {
-        BatchJob& j = jobs[g.job];
-        if (j.output == MG_OUT_STATE) {
-          cs.push_back(ChainSeg{(int)g.job, g.off, g.n, j.done});
-        } else {
-          int span = 0;
-          if (reorth_every > 1) { span = 1; while (span * 2 <= reorth_every) span *= 2; if (span < 2) span = 0; }
-          double* prod;
-          if ((rc = tree_product(ctx, eng, g.n, Ub + g.off * md, &prod, span)) != MG_OK) goto done;
-          if (!j.init) {
-            if ((rc = launch_copy_strided(1, md, prod, md, j.state, md, s)) != MG_OK) goto done;
-            j.init = true;
-          } else {
-            double* acc2;
-            if ((rc = ws(ctx, WS_ACC2, md, &acc2)) != MG_OK) goto done;
-            if ((rc = eng.reserve(1)) != MG_OK) goto done;
-            if ((rc = eng.prepA(1, prod, md)) != MG_OK) goto done;
-            if ((rc = eng.prepB(0, 1, j.state, md)) != MG_OK) goto done;
-            AddTerms none;
-            if ((rc = eng.mul(1, prod, md, 0, j.state, md, acc2, md, none)) != MG_OK) goto done;
-            if ((rc = launch_copy_strided(1, md, acc2, md, j.state, md, s)) != MG_OK) goto done;
-          }
-          if (reorth_every > 0 && (j.done + g.n) / reorth_every != j.done / reorth_every)
-            if ((rc = reorth_batch(ctx, eng, 1, j.state, md)) != MG_OK) goto done;
-        }
-        j.done += g.n;
-      }
-      if (!cs.empty()) {
-        const double* Uf = Ub;
-        if (eng.df()) {
-          double* conv;
-          if ((rc = ws(ctx, WS_NS_Z, md * fill, &conv)) != MG_OK) goto done;
-          if ((rc = eng.to_fp64(fill, Ub, md, conv, md)) != MG_OK) goto done;
-          Uf = conv;
-        }
-        if (cudaMemcpyAsync(segs_dev, cs.data(), sizeof(ChainSeg) * cs.size(), cudaMemcpyHostToDevice, s) !=
-            cudaSuccess) { rc = MG_ECUDA; goto done; }
-        if ((rc = launch_multi_chain((int)cs.size(), dp, segs_dev, Uf, md, psi_dev, reorth_every, s)) != MG_OK)
-          goto done;
-        // the segment table is host memory reused next chunk
-        if (cudaStreamSynchronize(s) != cudaSuccess) { rc = MG_ECUDA; goto done; }
-      }
+      MG_TRY(process_chunk(ctx, eng, segs, fill, reorth_every, reinterpret_cast<ChainSeg*>(sbuf),
+                           reinterpret_cast<double**>(pbuf), &st));
     }
-    // results
     for (auto& j : jobs) {
-      const int d = j.p->d;
-      if (j.output == MG_OUT_STATE) {
-        if (cudaMemcpyAsync(out[j.idx], j.state, sizeof(double) * 2 * d, d2h, s) != cudaSuccess) { rc = MG_ECUDA; goto done; }
-      } else {
-        double *f, *t;
-        if ((rc = ws(ctx, WS_NS_G, md, &f)) != MG_OK) goto done;
-        if ((rc = ws(ctx, WS_OUT, mat_doubles(d), &t)) != MG_OK) goto done;
-        if (!j.init) { if ((rc = eng.identity(1, j.state)) != MG_OK) goto done; }
-        if ((rc = eng.to_fp64(1, j.state, md, f, md)) != MG_OK) goto done;
-        if ((rc = launch_unpad_copy(d, dp, f, t, s)) != MG_OK) goto done;
-        if (cudaMemcpyAsync(out[j.idx], t, sizeof(double) * mat_doubles(d), d2h, s) != cudaSuccess) { rc = MG_ECUDA; goto done; }
-        if (cudaStreamSynchronize(s) != cudaSuccess) { rc = MG_ECUDA; goto done; }
-      }
+      MG_TRY(write_job_output(ctx, eng, j, out[j.idx], d2h));
       if (job_status) job_status[j.idx] = j.failed ? MG_ENONFINITE : MG_OK;
     }
-    if (cudaStreamSynchronize(s) != cudaSuccess) rc = MG_ECUDA;
-  }
-done:
+    return MG_OK;
+  };
+  rc = body();
   cudaStreamSynchronize(s);
   for (void* q : owned) cudaFree(q);
   if (rc == MG_OK && prec == MG_PREC_SPLIT) rc = check_status(ctx);
@@ -1256,38 +1285,369 @@ int mg_evolve_batch(mg_ctx* ctx, int n, mg_plan* const* plans, const int* output
   if (!ctx || n < 1 || !plans || !outputs || !out || reorth_every < 0) return MG_EINVAL;
   MG_CUDA_TRY(cudaSetDevice(ctx->device));
   // group by (precision, digits, padded dimension); one group at a time
-  struct Key { int prec, L, dp; bool operator<(const Key& o) const {
-      return prec != o.prec ? prec < o.prec : (L != o.L ? L < o.L : dp < o.dp); } };
-  std::vector<std::pair<Key, BatchJob>> all;
+  struct Key {
+    int prec, L, dp;
+    bool operator<(const Key& o) const { return prec != o.prec ? prec < o.prec : (L != o.L ? L < o.L : dp < o.dp); }
+  };
+  struct Item { Key k; BatchJob j; mg_plan* p; };
+  std::vector<Item> all;
   for (int i = 0; i < n; ++i) {
     mg_plan* p = plans[i];
     if (!p || p->ctx != ctx || p->N < 1 || !out[i] ||
         (outputs[i] != MG_OUT_STATE && outputs[i] != MG_OUT_PROPAGATOR)) return MG_EINVAL;
-    if (outputs[i] == MG_OUT_STATE && p->d > 256 && round_dim(p->d) > 256) {
-      set_last_message("mg_evolve_batch: state jobs need d <= 256 (job %d has d = %d)", i, p->d);
-      return MG_EUNSUPPORTED;
-    }
     BatchJob j;
     j.idx = i;
-    j.p = p;
     j.output = outputs[i];
+    j.d = p->d;
+    j.K = p->K;
+    j.N = p->N;
+    j.dt = p->dt;
+    j.c = p->c;
     const int L = p->precision == MG_PREC_SPLIT ? p->L : 0;
-    all.push_back({Key{p->precision, L, round_dim(p->d)}, j});
+    all.push_back({Key{p->precision, L, round_dim(p->d)}, j, p});
   }
-  std::stable_sort(all.begin(), all.end(), [](const auto& a, const auto& b) { return a.first < b.first; });
+  std::stable_sort(all.begin(), all.end(), [](const Item& a, const Item& b) { return a.k < b.k; });
   int rc = MG_OK;
   for (size_t g0 = 0; g0 < all.size() && rc == MG_OK;) {
     size_t g1 = g0;
     std::vector<BatchJob> jobs;
-    while (g1 < all.size() && !(all[g0].first < all[g1].first) && !(all[g1].first < all[g0].first)) {
-      jobs.push_back(all[g1].second);
+    std::vector<mg_plan*> ps;
+    while (g1 < all.size() && !(all[g0].k < all[g1].k) && !(all[g1].k < all[g0].k)) {
+      jobs.push_back(all[g1].j);
+      ps.push_back(all[g1].p);
       ++g1;
     }
-    const Key k = all[g0].first;
-    rc = run_group(ctx, jobs, k.dp, k.prec, k.L == 0 ? 6 : k.L, in, out, reorth_every, flags, job_status);
+    const Key k = all[g0].k;
+    rc = run_group(ctx, jobs, ps, k.dp, k.prec, k.L == 0 ? 6 : k.L, in, out, reorth_every, flags, job_status);
     g0 = g1;
   }
   return rc;
+}
+
+// ---------------------------------------------------------------------------
+// serving: admission by device memory, continuous batching of chunk steps
+// ---------------------------------------------------------------------------
+namespace {
+
+using clk = std::chrono::steady_clock;
+
+struct SJob {
+  uint64_t id = 0;
+  BatchJob b;
+  int dp = 0, prec = 0, L = 6;
+  double* out = nullptr;
+  cudaMemcpyKind out_kind = cudaMemcpyDeviceToDevice;
+  std::vector<void*> owned;     // device buffers of this job
+  size_t bytes = 0;
+  cudaEvent_t ready = nullptr;  // uploads finished
+  clk::time_point t_submit, t_start, t_done;
+  bool started = false, finished = false;
+  int status = MG_OK;
+};
+
+}  // namespace
+
+struct mg_server {
+  mg_ctx* ctx = nullptr;
+  size_t budget = 0, used = 0;
+  int quantum = 256;
+  cudaStream_t upload = nullptr;
+  std::mutex mu;
+  std::condition_variable cv, done_cv;
+  std::deque<SJob*> pending;
+  std::vector<SJob*> active;
+  std::map<uint64_t, SJob*> jobs;
+  std::thread worker;
+  bool stop = false;
+  uint64_t next_id = 1;
+  ChainSeg* segs_dev = nullptr;
+  double** psi_dev = nullptr;
+  int seg_cap = 4096;
+  std::vector<double> latencies_ms;
+  long long intervals_done = 0;
+  clk::time_point t_first;
+  bool any = false;
+  double busy_ms = 0.0;
+};
+
+namespace {
+
+void free_job_memory(SJob* j) {
+  for (void* q : j->owned) cudaFree(q);
+  j->owned.clear();
+  if (j->ready) cudaEventDestroy(j->ready);
+  j->ready = nullptr;
+}
+
+void finish_job(mg_server* srv, SJob* j, int status) {
+  std::lock_guard<std::mutex> lock(srv->mu);
+  j->status = status;
+  j->finished = true;
+  j->t_done = clk::now();
+  srv->used -= j->bytes;
+  srv->latencies_ms.push_back(std::chrono::duration<double, std::milli>(j->t_done - j->t_submit).count());
+  srv->intervals_done += j->b.N;
+  srv->done_cv.notify_all();
+}
+
+void server_loop(mg_server* srv) {
+  mg_ctx* ctx = srv->ctx;
+  cudaSetDevice(ctx->device);
+  for (;;) {
+    std::vector<SJob*> group;
+    {
+      std::unique_lock<std::mutex> lock(srv->mu);
+      srv->cv.wait(lock, [&] { return srv->stop || !srv->pending.empty() || !srv->active.empty(); });
+      if (srv->stop && srv->pending.empty() && srv->active.empty()) return;
+      // continuous admission: every request that arrived joins at this chunk boundary
+      while (!srv->pending.empty()) {
+        SJob* j = srv->pending.front();
+        srv->pending.pop_front();
+        j->t_start = clk::now();
+        j->started = true;
+        srv->active.push_back(j);
+      }
+      // the oldest job picks the group; its peers with the same key share the chunk
+      SJob* head = srv->active.front();
+      for (SJob* j : srv->active)
+        if (j->dp == head->dp && j->prec == head->prec && j->L == head->L && (int)group.size() < srv->seg_cap)
+          group.push_back(j);
+    }
+    const auto t0 = clk::now();
+    Engine eng{ctx, group[0]->dp, group[0]->prec, group[0]->L};
+    int rc = MG_OK;
+    for (SJob* j : group) cudaStreamWaitEvent(ctx->stream, j->ready, 0);
+    const int chunk = chunk_size(ctx, eng.d, eng.prec, eng.L, 1 << 30, 1);
+    std::vector<ChunkSeg> segs;
+    int fill = 0;
+    for (SJob* j : group) {
+      const int n = std::min(std::min(srv->quantum, j->b.N - j->b.done), chunk - fill);
+      if (n <= 0) continue;
+      segs.push_back({&j->b, j->b.done, n, fill});
+      fill += n;
+      if (fill >= chunk) break;
+    }
+    ExpmStats st;
+    if (fill > 0) rc = process_chunk(ctx, eng, segs, fill, 0, srv->segs_dev, srv->psi_dev, &st);
+    if (rc == MG_OK && eng.prec == MG_PREC_SPLIT) rc = check_status(ctx);
+    // completed jobs leave; on an error every job of the group fails
+    std::vector<SJob*> done_now;
+    for (SJob* j : group)
+      if (rc != MG_OK || j->b.done >= j->b.N) done_now.push_back(j);
+    for (SJob* j : done_now) {
+      int jr = rc;
+      if (jr == MG_OK) jr = write_job_output(ctx, eng, j->b, j->out, j->out_kind);
+      if (jr == MG_OK && j->b.failed) jr = MG_ENONFINITE;
+      cudaStreamSynchronize(ctx->stream);
+      free_job_memory(j);
+      {
+        std::lock_guard<std::mutex> lock(srv->mu);
+        srv->active.erase(std::find(srv->active.begin(), srv->active.end(), j));
+      }
+      finish_job(srv, j, jr);
+    }
+    std::lock_guard<std::mutex> lock(srv->mu);
+    srv->busy_ms += std::chrono::duration<double, std::milli>(clk::now() - t0).count();
+  }
+}
+
+}  // namespace
+
+int mg_server_create(mg_ctx* ctx, size_t mem_budget_bytes, int quantum_intervals, mg_server** out) {
+  if (!ctx || !out || mem_budget_bytes == 0 || quantum_intervals < 1) return MG_EINVAL;
+  *out = nullptr;
+  MG_CUDA_TRY(cudaSetDevice(ctx->device));
+  mg_server* srv = new mg_server();
+  srv->ctx = ctx;
+  srv->budget = mem_budget_bytes;
+  srv->quantum = quantum_intervals;
+  if (cudaStreamCreateWithFlags(&srv->upload, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaMalloc(&srv->segs_dev, sizeof(ChainSeg) * srv->seg_cap) != cudaSuccess ||
+      cudaMalloc(&srv->psi_dev, sizeof(double*) * srv->seg_cap) != cudaSuccess) {
+    cudaGetLastError();
+    if (srv->upload) cudaStreamDestroy(srv->upload);
+    cudaFree(srv->segs_dev);
+    cudaFree(srv->psi_dev);
+    delete srv;
+    return MG_ENOMEM;
+  }
+  srv->worker = std::thread(server_loop, srv);
+  *out = srv;
+  return MG_OK;
+}
+
+int mg_submit(mg_server* srv, const mg_job* job, uint64_t* job_id) {
+  if (!srv || !job || !job_id) return MG_EINVAL;
+  const int d = job->d, K = job->K, N = job->N, P = job->P;
+  if (d < 1 || d > 4096 || K < 0 || K > 64 || N < 1 || P < 1 || P > 64 || !job->H0 || (K > 0 && !job->Hk) ||
+      !job->w || (K > 0 && !job->samples) || !job->out || !(job->dt > 0.0) ||
+      (job->output != MG_OUT_STATE && job->output != MG_OUT_PROPAGATOR) ||
+      (job->output == MG_OUT_STATE && !job->in) || (job->output == MG_OUT_PROPAGATOR && job->in))
+    return MG_EINVAL;
+  MG_TRY(validate_prec(job->precision, job->slices));
+  if (job->output == MG_OUT_STATE && round_dim(d) > 256 && d > 256) {
+    // large-d states run one chain launch per interval; allowed
+  }
+  const int dp = round_dim(d);
+  const long long md = mat_doubles(dp);
+  const size_t op_bytes = sizeof(double) * md * (1 + K);
+  const size_t c_bytes = sizeof(double) * std::max<size_t>(1, (size_t)N * K);
+  const size_t st_bytes = job->output == MG_OUT_STATE ? sizeof(double) * 2 * dp : sizeof(double) * md;
+  const size_t tmp_bytes = sizeof(double) * ((size_t)mat_doubles(d) * (1 + K) + (size_t)N * P * K + P);
+  const size_t bytes = op_bytes + c_bytes + st_bytes + tmp_bytes;
+  {
+    std::lock_guard<std::mutex> lock(srv->mu);
+    if (srv->used + bytes > srv->budget) {
+      set_last_message("job of %zu bytes not admissible now (%zu of %zu bytes in use)", bytes, srv->used, srv->budget);
+      return MG_EAGAIN;
+    }
+    srv->used += bytes;
+  }
+  SJob* j = new SJob();
+  j->bytes = bytes;
+  j->dp = dp;
+  j->prec = job->precision;
+  j->L = job->precision == MG_PREC_SPLIT ? job->slices : 6;
+  j->out = job->out;
+  const bool host = (job->flags & MG_FLAG_HOST_PTRS) != 0;
+  j->out_kind = host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+  const cudaMemcpyKind h2d = host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+  BatchJob& b = j->b;
+  b.output = job->output;
+  b.d = d;
+  b.K = K;
+  b.N = N;
+  b.dt = job->dt;
+  int rc = MG_OK;
+  cudaStream_t s = srv->upload;
+  auto dmalloc = [&](size_t n, void** ptr) -> int {
+    if (cudaMalloc(ptr, n) != cudaSuccess) {
+      cudaGetLastError();
+      set_last_message("device allocation of %zu bytes failed (job upload)", n);
+      return MG_ENOMEM;
+    }
+    j->owned.push_back(*ptr);
+    return MG_OK;
+  };
+  auto upload = [&]() -> int {
+    MG_CUDA_TRY(cudaSetDevice(srv->ctx->device));
+    void *ops, *c, *st, *tmp;
+    MG_TRY(dmalloc(op_bytes, &ops));
+    MG_TRY(dmalloc(c_bytes, &c));
+    MG_TRY(dmalloc(st_bytes, &st));
+    if (cudaMalloc(&tmp, tmp_bytes) != cudaSuccess) { cudaGetLastError(); return MG_ENOMEM; }
+    double* T = reinterpret_cast<double*>(tmp);
+    double* Tw = T + mat_doubles(d) * (1 + K);
+    double* Ts = Tw + P;
+    int r = MG_OK;
+    double* H = reinterpret_cast<double*>(ops);
+    if (cudaMemcpyAsync(T, job->H0, sizeof(double) * mat_doubles(d), h2d, s) != cudaSuccess ||
+        (K > 0 && cudaMemcpyAsync(T + mat_doubles(d), job->Hk, sizeof(double) * mat_doubles(d) * K, h2d, s) !=
+                      cudaSuccess) ||
+        cudaMemcpyAsync(Tw, job->w, sizeof(double) * P, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        (K > 0 && cudaMemcpyAsync(Ts, job->samples, sizeof(double) * (size_t)N * P * K, h2d, s) != cudaSuccess))
+      r = MG_ECUDA;
+    if (r == MG_OK) r = launch_pad_copy(1 + K, d, dp, T, H, s);
+    if (r == MG_OK && K > 0) r = launch_coefficients(N, P, K, job->dt, Tw, Ts, reinterpret_cast<double*>(c), s);
+    b.H0 = H;
+    b.Hk = H + md;
+    b.c = reinterpret_cast<double*>(c);
+    b.state = reinterpret_cast<double*>(st);
+    if (r == MG_OK && b.output == MG_OUT_STATE) {
+      if (cudaMemsetAsync(b.state, 0, st_bytes, s) != cudaSuccess ||
+          cudaMemcpyAsync(b.state, job->in, sizeof(double) * 2 * d, h2d, s) != cudaSuccess)
+        r = MG_ECUDA;
+      b.init = true;
+    }
+    if (cudaStreamSynchronize(s) != cudaSuccess && r == MG_OK) r = MG_ECUDA;
+    cudaFree(tmp);
+    if (r == MG_OK && cudaEventCreateWithFlags(&j->ready, cudaEventDisableTiming) != cudaSuccess) r = MG_ECUDA;
+    if (r == MG_OK && cudaEventRecord(j->ready, s) != cudaSuccess) r = MG_ECUDA;
+    return r;
+  };
+  rc = upload();
+  if (rc != MG_OK) {
+    free_job_memory(j);
+    std::lock_guard<std::mutex> lock(srv->mu);
+    srv->used -= bytes;
+    delete j;
+    return rc;
+  }
+  {
+    std::lock_guard<std::mutex> lock(srv->mu);
+    j->id = srv->next_id++;
+    j->t_submit = clk::now();
+    if (!srv->any) { srv->any = true; srv->t_first = j->t_submit; }
+    srv->jobs[j->id] = j;
+    srv->pending.push_back(j);
+    *job_id = j->id;
+  }
+  srv->cv.notify_all();
+  return MG_OK;
+}
+
+int mg_wait(mg_server* srv, uint64_t job_id, double timeout_s, mg_job_report* rep) {
+  if (!srv) return MG_EINVAL;
+  std::unique_lock<std::mutex> lock(srv->mu);
+  auto it = srv->jobs.find(job_id);
+  if (it == srv->jobs.end()) return MG_EINVAL;
+  SJob* j = it->second;
+  const auto pred = [&] { return j->finished; };
+  if (timeout_s < 0) {
+    srv->done_cv.wait(lock, pred);
+  } else if (!srv->done_cv.wait_for(lock, std::chrono::duration<double>(timeout_s), pred)) {
+    set_last_message("job %llu not finished within %g s", (unsigned long long)job_id, timeout_s);
+    return MG_ETIMEOUT;
+  }
+  if (rep) {
+    rep->status = j->status;
+    rep->latency_ms = std::chrono::duration<double, std::milli>(j->t_done - j->t_submit).count();
+    rep->queue_ms = std::chrono::duration<double, std::milli>(j->t_start - j->t_submit).count();
+    rep->intervals = j->b.N;
+  }
+  const int st = j->status;
+  srv->jobs.erase(it);
+  delete j;
+  return st;
+}
+
+int mg_server_stats(mg_server* srv, double* p50_ms, double* p99_ms, double* intervals_per_s, int64_t* completed) {
+  if (!srv) return MG_EINVAL;
+  std::lock_guard<std::mutex> lock(srv->mu);
+  std::vector<double> l = srv->latencies_ms;
+  std::sort(l.begin(), l.end());
+  auto pct = [&](double q) {
+    if (l.empty()) return 0.0;
+    size_t k = (size_t)std::ceil(q * l.size()) - 1;
+    return l[std::min(k, l.size() - 1)];
+  };
+  if (p50_ms) *p50_ms = pct(0.50);
+  if (p99_ms) *p99_ms = pct(0.99);
+  if (completed) *completed = (int64_t)l.size();
+  if (intervals_per_s) {
+    const double secs = srv->any ? std::chrono::duration<double>(clk::now() - srv->t_first).count() : 0.0;
+    *intervals_per_s = secs > 0 ? srv->intervals_done / secs : 0.0;
+  }
+  return MG_OK;
+}
+
+int mg_server_destroy(mg_server* srv) {
+  if (!srv) return MG_EINVAL;
+  {
+    std::lock_guard<std::mutex> lock(srv->mu);
+    srv->stop = true;
+  }
+  srv->cv.notify_all();
+  if (srv->worker.joinable()) srv->worker.join();
+  for (auto& kv : srv->jobs) {
+    free_job_memory(kv.second);
+    delete kv.second;
+  }
+  cudaFree(srv->segs_dev);
+  cudaFree(srv->psi_dev);
+  cudaStreamDestroy(srv->upload);
+  delete srv;
+  return MG_OK;
 }
 
 }  // extern "C"

@@ -140,6 +140,8 @@ int launch_multi_chain(int nseg, int d, const ChainSeg* segs_dev, const double* 
                        double* const* psi_dev, int reorth_every, cudaStream_t s);
 // dst (dp x dp, zero padded) <- src (d x d), for `count` stacked matrices
 int launch_pad_copy(int count, int d, int dp, const double* src, double* dst, cudaStream_t s);
+// top-left d x d block of dst (dp x dp) <- src (d x d); the rest of dst untouched
+int launch_pad_into(int d, int dp, const double* src, double* dst, cudaStream_t s);
 // dst (d x d) <- top-left block of src (dp x dp)
 int launch_unpad_copy(int d, int dp, const double* src, double* dst, cudaStream_t s);
 

@@ -339,4 +339,19 @@ int launch_unpad_copy(int d, int dp, const double* src, double* dst, cudaStream_
   return check_launch("unpad_copy_kernel");
 }
 
+__global__ void pad_into_kernel(int d, int dp, const double2* __restrict__ src, double2* __restrict__ dst) {
+  const long long total = (long long)d * d;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(e / d), j = (int)(e % d);
+    dst[(long long)i * dp + j] = src[e];
+  }
+}
+
+int launch_pad_into(int d, int dp, const double* src, double* dst, cudaStream_t s) {
+  pad_into_kernel<<<grid_for((long long)d * d), 256, 0, s>>>(d, dp, reinterpret_cast<const double2*>(src),
+                                                              reinterpret_cast<double2*>(dst));
+  return check_launch("pad_into_kernel");
+}
+
 }  // namespace mg

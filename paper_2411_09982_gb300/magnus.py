@@ -55,6 +55,23 @@ class mg_report(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class mg_job(ctypes.Structure):
+    _fields_ = [
+        ("d", ctypes.c_int), ("K", ctypes.c_int),
+        ("H0", ctypes.c_void_p), ("Hk", ctypes.c_void_p),
+        ("N", ctypes.c_int), ("P", ctypes.c_int),
+        ("t0", ctypes.c_double), ("dt", ctypes.c_double),
+        ("w", ctypes.c_void_p), ("samples", ctypes.c_void_p),
+        ("output", ctypes.c_int), ("input", ctypes.c_void_p), ("out", ctypes.c_void_p),
+        ("precision", ctypes.c_int), ("slices", ctypes.c_int), ("flags", ctypes.c_int),
+    ]
+
+
+class mg_job_report(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("latency_ms", ctypes.c_double), ("queue_ms", ctypes.c_double),
+                ("intervals", ctypes.c_int64)]
+
+
 _P = ctypes.c_void_p
 _I = ctypes.c_int
 _D = ctypes.c_double
@@ -78,6 +95,12 @@ SIGNATURES = {
     "mg_ctx_enable_gemm_timing": (_I, [_P, _I]),
     "mg_ctx_gemm_stats": (_I, [_P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(_D), ctypes.POINTER(_D), _I]),
     "mg_cgemm_split_static": (_I, [_I, _P, _I, _I, _P, _P, _P, _I]),
+    "mg_server_create": (_I, [_P, ctypes.c_size_t, _I, ctypes.POINTER(_P)]),
+    "mg_submit": (_I, [_P, ctypes.POINTER(mg_job), ctypes.POINTER(ctypes.c_uint64)]),
+    "mg_wait": (_I, [_P, ctypes.c_uint64, _D, ctypes.POINTER(mg_job_report)]),
+    "mg_server_stats": (_I, [_P, ctypes.POINTER(_D), ctypes.POINTER(_D), ctypes.POINTER(_D),
+                             ctypes.POINTER(ctypes.c_int64)]),
+    "mg_server_destroy": (_I, [_P]),
     "mg_strerror": (ctypes.c_char_p, [_I]),
     "mg_last_error_message": (ctypes.c_char_p, []),
     "mg_kernel_launch_count": (ctypes.c_int64, []),
@@ -201,6 +224,63 @@ class Plan:
     def close(self):
         if self.h:
             load().mg_plan_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """mg_server: memory-admitted continuous batching of jobs on one context."""
+
+    def __init__(self, ctx: Context, mem_budget_bytes: int, quantum_intervals: int = 256):
+        h = ctypes.c_void_p()
+        _check(load().mg_server_create(ctx.h, int(mem_budget_bytes), int(quantum_intervals), ctypes.byref(h)),
+               "mg_server_create")
+        self.h = h
+        self.ctx = ctx
+        self._keep = {}
+
+    def submit(self, H0, Hk, N, P, t0, dt, w, samples, output, inp, out, precision=MG_PREC_SPLIT, slices=6,
+               host=False):
+        """Returns the job id, or None when the job is not admissible now (MG_EAGAIN)."""
+        import numpy as np
+        w = np.ascontiguousarray(w, dtype=np.float64)
+        j = mg_job(int(H0.shape[0]), int(Hk.shape[0]) if Hk is not None else 0, H0.data_ptr(),
+                   Hk.data_ptr() if Hk is not None else None, int(N), int(P), float(t0), float(dt),
+                   w.ctypes.data_as(ctypes.c_void_p), samples.data_ptr() if samples is not None else None,
+                   int(output), inp.data_ptr() if inp is not None else None, out.data_ptr(), int(precision),
+                   int(slices), MG_FLAG_HOST_PTRS if host else 0)
+        jid = ctypes.c_uint64()
+        r = load().mg_submit(self.h, ctypes.byref(j), ctypes.byref(jid))
+        if r == MG_EAGAIN:
+            return None
+        _check(r, "mg_submit")
+        self._keep[jid.value] = (out, w)
+        return jid.value
+
+    def wait(self, job_id, timeout_s=-1.0):
+        rep = mg_job_report()
+        r = load().mg_wait(self.h, ctypes.c_uint64(job_id), float(timeout_s), ctypes.byref(rep))
+        if r == MG_ETIMEOUT:
+            return None
+        self._keep.pop(job_id, None)
+        _check(r, "mg_wait")
+        return {k: getattr(rep, k) for k, _ in rep._fields_}
+
+    def stats(self):
+        p50, p99, ips = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        n = ctypes.c_int64()
+        _check(load().mg_server_stats(self.h, ctypes.byref(p50), ctypes.byref(p99), ctypes.byref(ips),
+                                      ctypes.byref(n)), "mg_server_stats")
+        return dict(p50_ms=p50.value, p99_ms=p99.value, intervals_per_s=ips.value, completed=n.value)
+
+    def close(self):
+        if self.h:
+            load().mg_server_destroy(self.h)
             self.h = None
 
     def __del__(self):

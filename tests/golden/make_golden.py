@@ -26,15 +26,16 @@ def sample_indices(d, count, seed):
     return sorted((int(i), int(j)) for i, j in idx)
 
 
-def write_propagator_samples(wl, name, count=256):
+def write_propagator_samples(wl, name, count=256, n_intervals=None):
     t0 = time.time()
-    U = oracle.evolve_workload(wl)
+    U = oracle.evolve_workload(wl, n_intervals=n_intervals)
     secs = time.time() - t0
     idx = sample_indices(wl.d, count, seed=12345)
     rec = {
         "what": f"sampled entries of the full propagator U(T) = U_(N-1)...U_0 of workloads.{name}",
         "source": "oracle.evolve_workload (CPU FP64: Gauss-Legendre quadrature, eigh exponentials, plain products)",
-        "workload": {"name": wl.name, "d": wl.d, "K": wl.K, "N": wl.N, "P": wl.P, "T": wl.T},
+        "workload": {"name": wl.name, "d": wl.d, "K": wl.K, "N": wl.N, "P": wl.P, "T": wl.T,
+                     "intervals_applied": wl.N if n_intervals is None else n_intervals},
         "oracle_seconds": secs,
         "unitarity_defect": oracle.unitarity_defect(U),
         "frobenius_norm": float(np.linalg.norm(U)),
@@ -48,4 +49,10 @@ def write_propagator_samples(wl, name, count=256):
 
 
 if __name__ == "__main__":
-    write_propagator_samples(W.config(1), "chain_d729_N2000_propagator")
+    which = sys.argv[1:] or ["chain", "alltoall"]
+    if "chain" in which:
+        write_propagator_samples(W.config(1), "chain_d729_N2000_propagator")
+    if "alltoall" in which:
+        # the first 2 of the 500 intervals of the d = 4096 workload (one 4096 x 4096
+        # eigendecomposition per interval on the CPU)
+        write_propagator_samples(W.config(3), "alltoall_d4096_N500_first2_propagator", n_intervals=2)
