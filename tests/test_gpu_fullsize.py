@@ -53,3 +53,18 @@ def test_chain_d729_full_fp64(ctx, golden):
     wl = W.config(1)
     U, rep = M.evolve_workload(ctx, wl, M.MG_PREC_FP64)
     check(U.cpu().numpy(), golden, 1e-11)
+
+
+GOLDEN_4096 = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
+                           "alltoall_d4096_N500_first2_propagator.json")
+
+
+@pytest.mark.parametrize("prec,L,tol", [(M.MG_PREC_SPLIT, 6, 1e-6), (M.MG_PREC_FP64, 6, 1e-11)])
+def test_alltoall_d4096_first_intervals(ctx, prec, L, tol):
+    """d = 4096 (4 transmons x 8 levels, all-to-all, two-tone drives): the first 2 of its 500
+    intervals against the oracle's sampled entries (one 4096 x 4096 eigendecomposition each)."""
+    with open(GOLDEN_4096) as f:
+        g = json.load(f)
+    wl = W.config(3)
+    U, rep = M.evolve_workload(ctx, wl, prec, L, N=g["workload"]["intervals_applied"])
+    check(U.cpu().numpy(), g, tol)
