@@ -583,8 +583,12 @@ split_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
             const int j = nt * SG_BNC + jc + jj;
             if (j < d) {
               const int k = Ea + eb_s[jc + jj] + 2 - 2 * beta;
-              df32 re = combine_levels(re_acc[0][jj], re_acc[1][jj], re_acc[2][jj], re_acc[3][jj], k);
-              df32 im = combine_levels(im_acc[0][jj], im_acc[1][jj], im_acc[2][jj], im_acc[3][jj], k);
+              // levels that no digit pair reaches (L < 4) were never written: they hold
+              // whatever an earlier kernel left in TMEM and must not be read as data
+              df32 re = combine_levels(re_acc[0][jj], L > 1 ? re_acc[1][jj] : 0u, L > 2 ? re_acc[2][jj] : 0u,
+                                       L > 3 ? re_acc[3][jj] : 0u, k);
+              df32 im = combine_levels(im_acc[0][jj], L > 1 ? im_acc[1][jj] : 0u, L > 2 ? im_acc[2][jj] : 0u,
+                                       L > 3 ? im_acc[3][jj] : 0u, k);
 #pragma unroll
               for (int m = 0; m < 3; ++m) {
                 if (m < epi.add_n) {

@@ -108,8 +108,11 @@ def test_cgemm_fp64(ctx, d, batch):
 
 @pytest.mark.parametrize("d", [1, 5, 16, 30])
 def test_cgemm_split_exact_on_small_integers(ctx, d):
-    """Integer entries |a| <= 3 are one exact digit: the split product must equal the exact one bit for bit."""
+    """Integer entries |a| <= 3 are one exact digit: the split product must equal the exact one bit for bit,
+    also right after a product with more digits has left nonzero accumulators behind in TMEM."""
     rng = np.random.default_rng(100 + d)
+    X = cuda(rand_c(rng, (4, 200, 200)))
+    M.mg_cgemm(ctx, 4, 200, X, X, torch.empty_like(X), M.MG_PREC_SPLIT, 8)
     A = rng.integers(-3, 4, (2, d, d)) + 1j * rng.integers(-3, 4, (2, d, d))
     B = rng.integers(-3, 4, (2, d, d)) + 1j * rng.integers(-3, 4, (2, d, d))
     C = torch.empty((2, d, d), dtype=torch.complex128, device="cuda")
