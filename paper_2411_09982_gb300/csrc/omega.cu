@@ -150,11 +150,10 @@ build_omega_kernel(int N, int d, int K, double dt, const double* __restrict__ H0
     double s = 0.0;
     for (int w = 0; w < OMEGA_WARPS; ++w) s += colpart[(w * OMEGA_NB + b) * 32 + lane];
     if (j >= d) s = 0.0;
+    // NaN/Inf -> +Inf before the max (fmax would drop a NaN)
+    if (!(s <= 1.0e300)) s = __longlong_as_double(0x7ff0000000000000LL);
     for (int o = 16; o > 0; o >>= 1) s = fmax(s, __shfl_xor_sync(0xffffffffu, s, o));
-    if (lane == 0) {
-      if (!(s <= 1.0e300)) s = __longlong_as_double(0x7ff0000000000000LL);  // NaN/Inf -> +Inf
-      atomicMax(norm_bits + n0 + b, nonneg_bits(s));
-    }
+    if (lane == 0) atomicMax(norm_bits + n0 + b, nonneg_bits(s));
   }
 }
 
@@ -215,11 +214,9 @@ shift_norm_kernel(int d, const double* __restrict__ A, double* __restrict__ dst,
   if (warp == 0) {
     double v = 0.0;
     for (int w = 0; w < 8; ++w) v += part[w][lane];
+    if (!(v <= 1.0e300)) v = __longlong_as_double(0x7ff0000000000000LL);   // before fmax drops a NaN
     for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-    if (lane == 0) {
-      if (!(v <= 1.0e300)) v = __longlong_as_double(0x7ff0000000000000LL);
-      atomicMax(norm_bits + blockIdx.y, nonneg_bits(v));
-    }
+    if (lane == 0) atomicMax(norm_bits + blockIdx.y, nonneg_bits(v));
   }
 }
 
