@@ -1,0 +1,75 @@
+"""World-size-2 gloo tests (CPU) of the multi-process path: interval-range sharding of one job
+with a single all-gather of partial products, and the max-over-ranks timing reduction."""
+import os
+import socket
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+from paper_2411_09982_gb300 import shard
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    return port
+
+
+def _worker(rank, world, port, q):
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        wl = W.transmon_resonator(nt=3, nr=4, N=37, T=3.0, sigma=0.7, omega0=0.4, unitary=True)
+        x, w = oracle.gauss_legendre(wl.P)
+
+        def local_partial(start, count):
+            t = oracle.node_times(wl.t0 + start * wl.dt, wl.dt, count, x)
+            U, _, _ = oracle.interval_propagators(wl.H0, wl.Hk, wl.drive(t), w, wl.dt)
+            return oracle.propagate_unitary(U)
+
+        U = shard.sharded_propagator(local_partial, wl.N, wl.d)
+        slowest = shard.max_over_ranks(1.0 + rank)
+        q.put((rank, U, slowest))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_interval_ranges_cover_in_order():
+    for N in (1, 2, 7, 100):
+        for world in (1, 2, 3, 8):
+            r = shard.interval_ranges(N, world)
+            assert sum(c for _, c in r) == N
+            assert all(r[i][0] + r[i][1] == r[i + 1][0] for i in range(len(r) - 1))
+            assert max(c for _, c in r) - min(c for _, c in r) <= 1
+
+
+def test_combine_partials_orders_later_on_the_left():
+    rng = np.random.default_rng(0)
+    P = [rng.normal(size=(3, 3)) for _ in range(3)]
+    np.testing.assert_allclose(shard.combine_partials(P), P[2] @ P[1] @ P[0])
+
+
+@pytest.mark.timeout(180)
+def test_two_rank_sharded_propagator_matches_single_process():
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    results = [q.get(timeout=150) for _ in range(2)]
+    for p in procs:
+        p.join(timeout=30)
+        assert p.exitcode == 0
+    wl = W.transmon_resonator(nt=3, nr=4, N=37, T=3.0, sigma=0.7, omega0=0.4, unitary=True)
+    ref = oracle.evolve_workload(wl)
+    for rank, U, slowest in results:
+        np.testing.assert_allclose(U, ref, atol=1e-12, rtol=0)
+        assert slowest == 2.0
