@@ -123,6 +123,17 @@ int mg_plan_create(mg_ctx* ctx, mg_plan** out, int d, int K, const double* H0,
  * be destroyed before or after their context. */
 int mg_plan_destroy(mg_plan* plan);
 
+/* Magnus order of the plan's exponents: 1 (the default, the paper's method) or 2,
+ * which adds the second-order term of Eq. magnus-avg,
+ *   Hbar^(2)_n = -(i/2) int int_{t_n <= t2 <= t1 <= t_n + dt} [H(t1), H(t2)],
+ * as sum_k alpha_{k,n} (-i/2)[H0, H_k] + sum_{k<l} beta_{kl,n} (-i/2)[H_k, H_l]:
+ * the K + K(K-1)/2 commutators are formed once here (FP64 products) and the
+ * scalar double integrals alpha, beta come from the interpolating polynomial of
+ * the P samples of each interval (exact for drives polynomial in t of degree
+ * < P).  Takes effect with the next mg_set_controls (controls must be set again).
+ * mg_evolve and mg_evolve_batch honour it; the server uses order 1. */
+int mg_plan_set_magnus_order(mg_plan* plan, int order);
+
 /* Replace the control signals (the `update_control_sigs()` step of App. A.5).
  * samples: N x P x K doubles, u^(k)(t_{n,p}) at the nodes documented at
  * mg_quadrature_nodes; w: the P quadrature weights (HOST array).  The samples

@@ -172,6 +172,37 @@ def evolve_workload(wl, n_intervals=None, return_parts=False):
     return out
 
 
+def interval_propagators_second_order(H0, Hk, drive, t0, dt, N, P):
+    """U_n = exp(-i (Hbar^(1)_n + Hbar^(2)_n)) with both Magnus terms of Eq. magnus-avg over
+    every interval: Hbar^(1) by P-point Gauss-Legendre quadrature of the drive, Hbar^(2) by
+    nested P-point quadrature of [H(t1), H(t2)] (`second_order_term`).  `drive(t)` -> (..., K)."""
+    x, w = gauss_legendre(P)
+    d = H0.shape[0]
+    U = np.empty((N, d, d), dtype=np.complex128)
+
+    def Hfun(t):
+        u = drive(np.array([t]))[0]
+        out = np.asarray(H0, dtype=np.complex128).copy()
+        for k in range(Hk.shape[0]):
+            out = out + u[k] * Hk[k]
+        return out
+
+    c = drive_coefficients(drive(node_times(t0, dt, N, x)), w, dt)
+    for n in range(N):
+        a = t0 + n * dt
+        H1 = first_order_term(H0, Hk, c[n], dt)
+        H2 = second_order_term(Hfun, a, a + dt, P)
+        U[n] = expm_minus_i(H1 + 0.5 * (H2 + H2.conj().T))
+    return U
+
+
+def evolve_workload_second_order(wl, n_intervals=None):
+    """Second-order Magnus evolution of a `workloads.Workload`."""
+    N = wl.N if n_intervals is None else int(n_intervals)
+    U = interval_propagators_second_order(wl.H0, wl.Hk, wl.drive, wl.t0, wl.dt, N, wl.P)
+    return propagate_unitary(U) if wl.psi0 is None else propagate_state(U, wl.psi0)
+
+
 # ----------------------------------------------------------------------------
 # invariants reported next to a result
 # ----------------------------------------------------------------------------

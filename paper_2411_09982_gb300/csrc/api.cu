@@ -90,6 +90,10 @@ struct mg_plan {
   double* samples = nullptr;
   double* c = nullptr;
   size_t samples_cap = 0, c_cap = 0;
+  // Magnus order: 1, or 2 with the commutator operators appended to Hk
+  int order = 1;
+  int Kx = 0;               // operators entering Hbar_n: K (order 1) or 2K + K(K-1)/2 (order 2)
+  double* mrc = nullptr;    // second-order quadrature matrix on the device
 };
 
 namespace {
@@ -228,6 +232,16 @@ TaylorChoice choose_taylor(double norm1, double u) {
   }
   return best;
 }
+
+// ---------------------------------------------------------------------------
+// second-order quadrature matrix
+// ---------------------------------------------------------------------------
+// M_pq = int_0^1 l_p(s1) int_0^s1 l_q(s2) ds2 ds1 for the Lagrange basis l on the
+// Gauss-Legendre nodes s_r = (1 + x_r)/2 of [0, 1].  l_p L_q has degree 2P - 1, so
+// P-point Gauss-Legendre integrates the outer integral exactly: M_pq = (w_p/2) L_q(s_p),
+// and L_q(s_p) = int_0^{s_p} l_q is again an exact P-point rule on [0, s_p].
+// Output: M (row-major), then column sums, then row sums.
+int lagrange_triangle(int P, std::vector<double>& mrc);
 
 // ---------------------------------------------------------------------------
 // matrix-product engine: FP64 or split precision, same call pattern
@@ -520,6 +534,33 @@ int validate_prec(int precision, int L) {
 
 }  // namespace
 
+namespace {
+int lagrange_triangle(int P, std::vector<double>& mrc) {
+  std::vector<double> x(P), wl(P), sn(P);
+  MG_TRY(mg_quadrature_nodes(P, x.data(), wl.data()));
+  for (int r = 0; r < P; ++r) sn[r] = 0.5 * (1.0 + x[r]);
+  auto ell = [&](int q, double t) {
+    double v = 1.0;
+    for (int r = 0; r < P; ++r)
+      if (r != q) v *= (t - sn[r]) / (sn[q] - sn[r]);
+    return v;
+  };
+  mrc.assign((size_t)P * P + 2 * P, 0.0);
+  for (int p = 0; p < P; ++p)
+    for (int q = 0; q < P; ++q) {
+      double Lq = 0.0;
+      for (int r = 0; r < P; ++r) Lq += 0.5 * sn[p] * wl[r] * ell(q, 0.5 * sn[p] * (1.0 + x[r]));
+      mrc[(size_t)p * P + q] = 0.5 * wl[p] * Lq;
+    }
+  for (int p = 0; p < P; ++p)
+    for (int q = 0; q < P; ++q) {
+      mrc[(size_t)P * P + q] += mrc[(size_t)p * P + q];       // column sums C_q
+      mrc[(size_t)P * P + P + p] += mrc[(size_t)p * P + q];   // row sums R_p
+    }
+  return MG_OK;
+}
+}  // namespace
+
 // ---------------------------------------------------------------------------
 // C ABI
 // ---------------------------------------------------------------------------
@@ -677,6 +718,7 @@ int mg_plan_create(mg_ctx* ctx, mg_plan** out, int d, int K, const double* H0, c
   p->precision = precision;
   p->L = slices;
   p->flags = flags;
+  p->Kx = K;
   const size_t mb = sizeof(double) * mat_doubles(d);
   if (cudaMalloc(&p->H0, mb) != cudaSuccess || (K > 0 && cudaMalloc(&p->Hk, mb * K) != cudaSuccess)) {
     cudaGetLastError();
@@ -727,6 +769,7 @@ int mg_plan_destroy(mg_plan* p) {
   cudaFree(p->w);
   cudaFree(p->samples);
   cudaFree(p->c);
+  cudaFree(p->mrc);
   delete p;
   return MG_OK;
 }
@@ -745,7 +788,7 @@ int mg_set_controls(mg_plan* p, int N, int P, double t0, double dt, const double
     if (cudaMalloc(&p->samples, std::max<size_t>(ns, 1) * sizeof(double)) != cudaSuccess) { cudaGetLastError(); return MG_ENOMEM; }
     p->samples_cap = ns;
   }
-  const size_t nc = (size_t)N * p->K;
+  const size_t nc = (size_t)N * p->Kx;
   if (p->c_cap < nc) {
     cudaFree(p->c);
     p->c = nullptr;
@@ -762,7 +805,17 @@ int mg_set_controls(mg_plan* p, int N, int P, double t0, double dt, const double
   p->P = P;
   p->t0 = t0;
   p->dt = dt;
-  MG_TRY(launch_coefficients(N, P, p->K, dt, p->w, p->samples, p->c, s));
+  if (p->order == 2 && p->K > 0) {
+    std::vector<double> mrc;
+    MG_TRY(lagrange_triangle(P, mrc));
+    cudaFree(p->mrc);
+    p->mrc = nullptr;
+    if (cudaMalloc(&p->mrc, mrc.size() * sizeof(double)) != cudaSuccess) { cudaGetLastError(); return MG_ENOMEM; }
+    MG_CUDA_TRY(cudaMemcpyAsync(p->mrc, mrc.data(), mrc.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+    MG_TRY(launch_second_order_coefficients(N, P, p->K, dt, p->w, p->mrc, p->samples, p->c, s));
+  } else {
+    MG_TRY(launch_coefficients(N, P, p->K, dt, p->w, p->samples, p->c, s));
+  }
   // stage the weights before the host array may go away
   MG_CUDA_TRY(cudaStreamSynchronize(s));
   return MG_OK;
@@ -983,8 +1036,8 @@ int mg_evolve(mg_plan* p, int output, const double* in, double* out, int reorth_
     MG_TRY(ws(ctx, WS_W, md * nb, &W));
     MG_TRY(ws(ctx, WS_TAU, nb, &tau));
     MG_TRY(ws(ctx, WS_NORM, nb, &nrm));
-    MG_TRY(small_scratch(ctx, (size_t)p->K + 1 + nb, &sc));
-    MG_TRY(launch_build_omega(nb, d, p->K, p->dt, p->H0, p->Hk, p->c + (long long)n0 * p->K, W, tau, nrm, shift,
+    MG_TRY(small_scratch(ctx, (size_t)p->Kx + 1 + nb, &sc));
+    MG_TRY(launch_build_omega(nb, d, p->Kx, p->dt, p->H0, p->Hk, p->c + (long long)n0 * p->Kx, W, tau, nrm, shift,
                               /*write_shifted=*/1, sc, s));
     double* Ubuf;
     MG_TRY(ws(ctx, WS_UBUF, md * nb, &Ubuf));
@@ -1299,7 +1352,7 @@ int mg_evolve_batch(mg_ctx* ctx, int n, mg_plan* const* plans, const int* output
     j.idx = i;
     j.output = outputs[i];
     j.d = p->d;
-    j.K = p->K;
+    j.K = p->Kx;
     j.N = p->N;
     j.dt = p->dt;
     j.c = p->c;
@@ -1647,6 +1700,64 @@ int mg_server_destroy(mg_server* srv) {
   cudaFree(srv->psi_dev);
   cudaStreamDestroy(srv->upload);
   delete srv;
+  return MG_OK;
+}
+
+int mg_plan_set_magnus_order(mg_plan* p, int order) {
+  if (!p || (order != 1 && order != 2)) return MG_EINVAL;
+  mg_ctx* ctx = p->ctx;
+  MG_CUDA_TRY(cudaSetDevice(ctx->device));
+  const int K = p->K, d = p->d;
+  if (order == 1 || K == 0) {
+    p->order = order;
+    p->Kx = K;
+    p->N = 0;   // controls must be set again
+    return MG_OK;
+  }
+  const int Kx = 2 * K + K * (K - 1) / 2;
+  const long long md = mat_doubles(d);
+  double *Hx = nullptr, *T1 = nullptr, *T2 = nullptr;
+  if (cudaMalloc(&Hx, sizeof(double) * md * Kx) != cudaSuccess || cudaMalloc(&T1, sizeof(double) * md) != cudaSuccess ||
+      cudaMalloc(&T2, sizeof(double) * md) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(Hx); cudaFree(T1); cudaFree(T2);
+    return MG_ENOMEM;
+  }
+  cudaStream_t s = ctx->stream;
+  int rc = MG_OK;
+  if (cudaMemcpyAsync(Hx, p->Hk, sizeof(double) * md * K, cudaMemcpyDeviceToDevice, s) != cudaSuccess) rc = MG_ECUDA;
+  // C = -(i/2) [A, B]: T1 = A B, T2 = A B - B A, C = (-i) 2^-1 T2   (FP64 products, once per plan)
+  auto comm = [&](const double* A, const double* B, double* C) -> int {
+    AddTerms none;
+    MG_TRY(launch_cgemm_f64(1, d, A, md, 0, B, md, T1, md, none, s));
+    AddTerms sub;
+    sub.n = 1;
+    sub.src[0] = T1;
+    sub.coef[0] = 1.0;
+    sub.stride = md;
+    sub.scale = -1.0;
+    MG_TRY(launch_cgemm_f64(1, d, B, md, 0, A, md, T2, md, sub, s));
+    return launch_scale_minus_i(1, d, T2, C, nullptr, 1, s);
+  };
+  for (int k = 0; rc == MG_OK && k < K; ++k) rc = comm(p->H0, p->Hk + k * md, Hx + (K + k) * md);
+  int m = 2 * K;
+  for (int k = 0; rc == MG_OK && k < K; ++k)
+    for (int l = k + 1; rc == MG_OK && l < K; ++l, ++m) rc = comm(p->Hk + k * md, p->Hk + l * md, Hx + m * md);
+  if (cudaStreamSynchronize(s) != cudaSuccess && rc == MG_OK) rc = MG_ECUDA;
+  cudaFree(T1);
+  cudaFree(T2);
+  if (rc != MG_OK) {
+    cudaFree(Hx);
+    return rc;
+  }
+  cudaFree(p->Hk);
+  p->Hk = Hx;
+  p->order = 2;
+  p->Kx = Kx;
+  p->N = 0;   // controls must be set again
+  p->c_cap = 0;
+  cudaFree(p->c);
+  p->c = nullptr;
   return MG_OK;
 }
 

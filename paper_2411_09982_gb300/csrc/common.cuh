@@ -64,6 +64,11 @@ void count_launch();
 int launch_coefficients(int N, int P, int K, double dt, const double* w_dev,
                         const double* samples, double* c, cudaStream_t s);
 
+// first-order c_k, alpha_k and beta_kl of the second-order Magnus term per interval
+// (row length 2K + K(K-1)/2); mrc = [M (P x P) | column sums | row sums] on the device
+int launch_second_order_coefficients(int N, int P, int K, double dt, const double* w_dev, const double* mrc_dev,
+                                     const double* samples, double* c, cudaStream_t s);
+
 // omega[n] = dt H0 + sum_k c[n][k] H_k (minus tau_n I when write_shifted), with
 // tau[n] = Re tr/d (0 unless shift) and norm1[n] = ||omega_n - tau_n I||_1.
 // scratch: K + 1 + N doubles of device memory.

@@ -34,6 +34,66 @@ int launch_coefficients(int N, int P, int K, double dt, const double* w_dev, con
 }
 
 // ---------------------------------------------------------------------------
+// Second-order Magnus coefficients (Eq. magnus-avg, second line).  With
+// H(t) = H0 + sum_k u_k(t) H_k the commutator splits as
+//   [H(t1), H(t2)] = sum_k (u_k(t2) - u_k(t1)) [H0, H_k]
+//                  + sum_{k<l} (u_k(t1) u_l(t2) - u_l(t1) u_k(t2)) [H_k, H_l],
+// so Hbar^(2)_n = sum_k alpha_k (-i/2)[H0, H_k] + sum_{k<l} beta_kl (-i/2)[H_k, H_l]
+// with scalar double integrals over t_n <= t2 <= t1 <= t_n + dt.  The drive is
+// represented by its interpolating polynomial through the P samples, for which
+//   int int f(t2) g(t1) = dt^2 sum_{p,q} g_p f_q M_pq
+// with M_pq = int_0^1 l_p(s1) int_0^s1 l_q(s2) (Lagrange basis on the nodes).
+// mrc holds M (P x P, row p = t1 node), then its column sums C_q and row sums R_p.
+// Output row n of c (length K + K + K(K-1)/2): first-order c_k, then alpha_k, then
+// beta_kl in the order (0,1), (0,2), ..., (K-2,K-1).
+__global__ void second_order_coefficients_kernel(int N, int P, int K, double dt, const double* __restrict__ w,
+                                                 const double* __restrict__ mrc,
+                                                 const double* __restrict__ samples, double* __restrict__ c) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  const int Kx = 2 * K + K * (K - 1) / 2;
+  const double* u = samples + (long long)n * P * K;   // u[p*K + k]
+  double* out = c + (long long)n * Kx;
+  const double* Mm = mrc;
+  const double* Cq = mrc + P * P;
+  const double* Rp = Cq + P;
+  const double dt2 = dt * dt;
+  for (int k = 0; k < K; ++k) {
+    double first = 0.0, a = 0.0;
+    for (int p = 0; p < P; ++p) {
+      const double v = u[p * K + k];
+      first = fma(w[p], v, first);
+      a = fma(Cq[p] - Rp[p], v, a);
+    }
+    out[k] = 0.5 * dt * first;
+    out[K + k] = dt2 * a;
+  }
+  int m = 2 * K;
+  for (int k = 0; k < K; ++k)
+    for (int l = k + 1; l < K; ++l, ++m) {
+      double b = 0.0;
+      for (int p = 0; p < P; ++p) {
+        double inner_kl = 0.0, inner_lk = 0.0;
+        for (int q = 0; q < P; ++q) {
+          const double mpq = Mm[p * P + q];
+          inner_kl = fma(mpq, u[q * K + l], inner_kl);
+          inner_lk = fma(mpq, u[q * K + k], inner_lk);
+        }
+        b = fma(u[p * K + k], inner_kl, b);
+        b = fma(-u[p * K + l], inner_lk, b);
+      }
+      out[m] = dt2 * b;
+    }
+}
+
+int launch_second_order_coefficients(int N, int P, int K, double dt, const double* w_dev, const double* mrc_dev,
+                                     const double* samples, double* c, cudaStream_t s) {
+  if (N <= 0 || K <= 0) return MG_OK;
+  second_order_coefficients_kernel<<<ceil_div(N, 128), 128, 0, s>>>(N, P, K, dt, w_dev, mrc_dev, samples, c);
+  return check_launch("second_order_coefficients_kernel");
+}
+
+// ---------------------------------------------------------------------------
 // traces: tr[0] = Re tr H0, tr[1 + k] = Re tr H_k
 __global__ void operator_traces_kernel(int d, int K, const double* __restrict__ H0,
                                        const double* __restrict__ Hk, double* __restrict__ tr) {

@@ -84,6 +84,7 @@ SIGNATURES = {
     "mg_quadrature_nodes": (_I, [_I, _P, _P]),
     "mg_plan_create": (_I, [_P, ctypes.POINTER(_P), _I, _I, _P, _P, _I, _I, _I]),
     "mg_plan_destroy": (_I, [_P]),
+    "mg_plan_set_magnus_order": (_I, [_P, _I]),
     "mg_set_controls": (_I, [_P, _I, _I, _D, _D, _P, _P, _I]),
     "mg_evolve": (_I, [_P, _I, _P, _P, _I, _I, ctypes.POINTER(mg_report)]),
     "mg_evolve_batch": (_I, [_P, _I, _P, _P, _P, _P, _I, _I, _P]),
@@ -201,6 +202,9 @@ class Plan:
         _check(lib.mg_plan_create(ctx.h, ctypes.byref(h), self.d, self.K, _ptr(H0), _ptr(Hk_t), precision,
                                   slices, flags | (MG_FLAG_HOST_PTRS if host else 0)), "mg_plan_create")
         self.h = h
+
+    def set_magnus_order(self, order):
+        _check(load().mg_plan_set_magnus_order(self.h, int(order)), "mg_plan_set_magnus_order")
 
     def set_controls(self, N, P, t0, dt, w, samples):
         import torch
@@ -365,12 +369,14 @@ def node_samples(wl, N=None):
     return np.ascontiguousarray(wl.drive(t)), w
 
 
-def evolve_workload(ctx, wl, precision=MG_PREC_FP64, slices=6, N=None, reorth_every=0, device="cuda"):
+def evolve_workload(ctx, wl, precision=MG_PREC_FP64, slices=6, N=None, reorth_every=0, device="cuda", order=1):
     """Run a workloads.Workload through mg_plan_create / mg_set_controls / mg_evolve."""
     import torch
     N = wl.N if N is None else N
     samples, w = node_samples(wl, N)
     plan = Plan(ctx, torch.from_numpy(wl.H0).to(device), torch.from_numpy(wl.Hk).to(device), precision, slices)
+    if order != 1:
+        plan.set_magnus_order(order)
     plan.set_controls(N, wl.P, wl.t0, wl.dt, w, torch.from_numpy(samples).to(device))
     if wl.psi0 is None:
         out = torch.empty((wl.d, wl.d), dtype=torch.complex128, device=device)

@@ -389,3 +389,26 @@ def test_plan_rejects_non_hermitian_operator(ctx):
     with pytest.raises(M.MagnusError) as e:
         M.Plan(ctx, cuda(H0), cuda(rand_herm(rng, 5)[None]), flags=M.MG_FLAG_CHECK_HERMITIAN)
     assert e.value.code == M.MG_ENOTHERM
+
+
+# ----------------------------------------------------------------------------
+# second-order Magnus term (Eq. magnus-avg, commutator line)
+# ----------------------------------------------------------------------------
+def _second_order_cases():
+    return [
+        W.transmon_resonator(nt=3, nr=2, T=2.0, sigma=0.5, omega0=0.4, N=20, P=16, name="tr6"),
+        W.transmon_chain(n_sites=3, levels=2, J=0.05, seed=7, omega0_max=0.3, T=4.0, sigma=1.0, N=12, P=16,
+                         unitary=True, name="chain8_K3"),
+    ]
+
+
+@pytest.mark.parametrize("prec,L,tol", [(0, 6, 1e-11), (1, 6, 1e-8)])
+def test_second_order_magnus_matches_oracle(ctx, prec, L, tol):
+    for wl in _second_order_cases():
+        out, rep = M.evolve_workload(ctx, wl, prec, L, order=2)
+        ref2 = oracle.evolve_workload_second_order(wl)
+        ref1 = oracle.evolve_workload(wl)
+        got = out.cpu().numpy()
+        assert np.abs(got - ref2).max() <= tol, (wl.name, np.abs(got - ref2).max())
+        # the commutator term matters for these drives: order 1 is far away
+        assert np.abs(ref2 - ref1).max() > 1e3 * tol

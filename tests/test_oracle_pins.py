@@ -325,3 +325,22 @@ def test_second_order_term_linear_drive_closed_form():
     expect = 1j * tau ** 3 / 12 * (H0 @ H1 - H1 @ H0)
     np.testing.assert_allclose(got, expect, atol=1e-14, rtol=0)
     np.testing.assert_allclose(got, got.conj().T, atol=1e-14, rtol=0)
+
+
+@pytest.mark.slow
+def test_second_order_magnus_converges_at_fourth_order():
+    """Hbar^(1) + Hbar^(2) (Eq. magnus-avg) is the fourth-order Magnus integrator: its global error
+    against a fine-step RK4 solution falls as dt^4 (first order alone: dt^2)."""
+    wl = W.transmon_resonator(nt=3, nr=2, T=2.0, sigma=0.5, omega0=0.3, N=50, P=8)
+
+    def Hfun(t):
+        return wl.H0 + wl.drive(np.array([t]))[0, 0] * wl.Hk[0]
+
+    ref = rk4_state(Hfun, wl.psi0, wl.T, 40000)
+    errs = []
+    Ns = [40, 80, 160]
+    for N in Ns:
+        U = oracle.interval_propagators_second_order(wl.H0, wl.Hk, wl.drive, 0.0, wl.T / N, N, wl.P)
+        errs.append(np.linalg.norm(oracle.propagate_state(U, wl.psi0) - ref))
+    slopes = np.diff(np.log(errs)) / np.diff(np.log(Ns))
+    assert np.all(slopes < -3.6) and np.all(slopes > -4.5), (errs, slopes)
