@@ -50,6 +50,11 @@ def parse():
     ap.add_argument("--intervals", type=int, default=2000)
     ap.add_argument("--e2e-steps", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--config", type=int, default=1,
+                    help="1: d = 729 chain (headline); 0: d = 30 transmon-resonator state, FP64; "
+                         "2: 512 uneven instances batched; 3: d = 4096 all-to-all, tree product; "
+                         "4: served request stream (p50/p99)")
+    ap.add_argument("--requests", type=int, default=48, help="config 4: requests taken from the stream")
     return ap.parse_args()
 
 
@@ -292,6 +297,190 @@ def run_ours(args):
 
 
 # ----------------------------------------------------------------------------
+# the other workloads (one GPU; not the driver's default line)
+# ----------------------------------------------------------------------------
+def run_config(args):
+    import numpy as np
+    import torch
+
+    import oracle
+    import workloads as W
+    from paper_2411_09982_gb300 import build as B
+    from paper_2411_09982_gb300 import magnus as M
+
+    B.build()
+    M.load()
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(device=dev)
+    ctx = M.Context(0, stream)
+    cores = len(os.sched_getaffinity(0))
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    warm = max(3, args.warmup)
+    out_line = {"metric": None, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": warm,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "data": "synthetic"}
+
+    def timed(step, steps):
+        with torch.cuda.stream(stream):
+            for _ in range(warm):
+                step()
+            stream.synchronize()
+            clocks = ClockSampler(0)
+            clocks.start()
+            l0 = M.mg_kernel_launch_count()
+            ctx.gemm_stats(reset=True)
+            ctx.enable_gemm_timing(True)
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+            for i in range(steps):
+                flush.zero_()
+                ev[i][0].record(stream)
+                step()
+                ev[i][1].record(stream)
+            stream.synchronize()
+            ctx.enable_gemm_timing(False)
+            g = ctx.gemm_stats(reset=True)
+            clk = clocks.stop()
+        return sum(a.elapsed_time(b) for a, b in ev), g, clk, M.mg_kernel_launch_count() - l0
+
+    def gemm_roof(g, pairs):
+        if not g["launches"]:
+            return None
+        ach = g["flops"] / (g["ms"] * 1e-3) / 1e12
+        peaks, src = measured_peaks()
+        peak = float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops")))
+        return {"bound": "tensor" if pairs else "alu", "achieved": ach, "peak": peak if pairs else 1.25,
+                "unit": "TFLOP/s", "frac": ach / (peak if pairs else 1.25), "traffic": None,
+                "tensor_pipe_frac": ach * pairs / peak if pairs else None,
+                "peak_source": f"bf16 dense sustained, {src}" if pairs else "nominal GB300 FP64 rate"}
+
+    if args.config in (0, 3):
+        wl = W.config(args.config)
+        prec = M.MG_PREC_FP64 if args.config == 0 else M.MG_PREC_SPLIT
+        reorth = 64 if args.config == 3 else 0
+        samples_np, w = M.node_samples(wl)
+        samples = torch.from_numpy(samples_np).to(dev)
+        plan = M.Plan(ctx, torch.from_numpy(wl.H0).to(dev), torch.from_numpy(wl.Hk).to(dev), prec, args.slices)
+        state = wl.psi0 is not None
+        inp = torch.from_numpy(wl.psi0).to(dev) if state else None
+        out = torch.empty(wl.d if state else (wl.d, wl.d), dtype=torch.complex128, device=dev)
+
+        def step():
+            plan.set_controls(wl.N, wl.P, wl.t0, wl.dt, w, samples)
+            plan.evolve(M.MG_OUT_STATE if state else M.MG_OUT_PROPAGATOR, inp, out, reorth, report=False)
+
+        ms, g, clk, launches = timed(step, args.steps)
+        out_line.update(metric=f"Magnus intervals/sec, {wl.name}", value=wl.N * args.steps / (ms / 1e3),
+                        ms_per_step=ms / args.steps, dtype="f64" if prec == M.MG_PREC_FP64 else
+                        f"bf16 digits x{args.slices} (fp32 accumulate) + f64",
+                        config={"workload": wl.name, "d": wl.d, "intervals": wl.N, "quadrature_points": wl.P,
+                                "controls": wl.K, "output": "state" if state else "full propagator",
+                                "reorth_every": reorth, "l2": "256 MiB buffer written before every timed step"},
+                        roofline=gemm_roof(g, 0 if prec == M.MG_PREC_FP64 else args.slices * (args.slices + 1) // 2),
+                        clocks=clk, gpu_launches=int(launches))
+        if not args.no_cpu_baseline:
+            n_s = 128 if args.config == 0 else 1
+            t0 = time.perf_counter()
+            ref = oracle.evolve_workload(wl, n_intervals=n_s)
+            cpu_s = time.perf_counter() - t0
+            out_line["cpu_baseline"] = {"value": n_s / cpu_s, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                        "sample": f"first {n_s} intervals of the workload"}
+            if args.config == 0:
+                full = oracle.evolve_workload(wl)
+                with torch.cuda.stream(stream):
+                    step()
+                    stream.synchronize()
+                out_line["accuracy"] = {"max_abs_err_vs_fp64_oracle": float(np.abs(out.cpu().numpy() - full).max()),
+                                        "intervals_compared": wl.N, "tolerance": 1e-11}
+        plan.close()
+    elif args.config == 2:
+        jobs = W.uneven_batch()
+        plans, kinds, ins, outs, samp = [], [], [], [], []
+        for wl in jobs:
+            sn, w = M.node_samples(wl)
+            st = torch.from_numpy(sn).to(dev)
+            p = M.Plan(ctx, torch.from_numpy(wl.H0).to(dev), torch.from_numpy(wl.Hk).to(dev), M.MG_PREC_SPLIT,
+                       args.slices)
+            plans.append(p)
+            samp.append((st, w))
+            kinds.append(M.MG_OUT_STATE)
+            ins.append(torch.from_numpy(wl.psi0).to(dev))
+            outs.append(torch.empty(wl.d, dtype=torch.complex128, device=dev))
+        total = sum(wl.N for wl in jobs)
+
+        def step():
+            for p, wl, (st, w) in zip(plans, jobs, samp):
+                p.set_controls(wl.N, wl.P, wl.t0, wl.dt, w, st)
+            M.mg_evolve_batch(ctx, plans, kinds, ins, outs)
+
+        ms, g, clk, launches = timed(step, args.steps)
+        ds = sorted(wl.d for wl in jobs)
+        out_line.update(metric="Magnus intervals/sec, 512 uneven transmon-resonator instances (batched)",
+                        value=total * args.steps / (ms / 1e3), ms_per_step=ms / args.steps,
+                        dtype=f"bf16 digits x{args.slices} (fp32 accumulate) + f64",
+                        config={"workload": "uneven_batch_512", "jobs": len(jobs), "intervals_total": total,
+                                "d_min": ds[0], "d_median": ds[len(ds) // 2], "d_max": ds[-1],
+                                "output": "state", "l2": "256 MiB buffer written before every timed step"},
+                        roofline=gemm_roof(g, args.slices * (args.slices + 1) // 2), clocks=clk,
+                        gpu_launches=int(launches))
+        if not args.no_cpu_baseline:
+            sample = jobs[:3]
+            t0 = time.perf_counter()
+            refs = [oracle.evolve_workload(wl) for wl in sample]
+            cpu_s = time.perf_counter() - t0
+            out_line["cpu_baseline"] = {"value": sum(wl.N for wl in sample) / cpu_s, "unit": UNIT, "cores": cores,
+                                        "kind": "oracle", "sample": "the first 3 instances of the batch"}
+            err = max(float(np.abs(o.cpu().numpy() - r).max()) for o, r in zip(outs[:3], refs))
+            out_line["accuracy"] = {"max_abs_err_vs_fp64_oracle": err, "jobs_compared": 3, "tolerance": 1e-6}
+        for p in plans:
+            p.close()
+    elif args.config == 4:
+        stream_spec = W.serving_stream()[: args.requests]
+        srv = M.Server(ctx, mem_budget_bytes=64 << 30, quantum_intervals=256)
+        built = [W.serving_job(sp) for _, sp in stream_spec]
+        inputs = []
+        for wl in built:
+            sn, w = M.node_samples(wl)
+            inputs.append((torch.from_numpy(wl.H0).to(dev), torch.from_numpy(wl.Hk).to(dev),
+                           torch.from_numpy(sn).to(dev), w,
+                           torch.from_numpy(wl.psi0).to(dev) if wl.psi0 is not None else None,
+                           torch.empty(wl.d if wl.psi0 is not None else (wl.d, wl.d), dtype=torch.complex128,
+                                       device=dev)))
+        torch.cuda.synchronize()
+        clocks = ClockSampler(0)
+        clocks.start()
+        t_start = time.perf_counter()
+        ids, rejected = [], 0
+        for (arr, sp), wl, (H0, Hk, S, w, inp, o) in zip(stream_spec, built, inputs):
+            now = time.perf_counter() - t_start
+            if arr > now:
+                time.sleep(arr - now)
+            kind = M.MG_OUT_STATE if inp is not None else M.MG_OUT_PROPAGATOR
+            while True:
+                jid = srv.submit(H0, Hk, wl.N, wl.P, wl.t0, wl.dt, w, S, kind, inp, o, M.MG_PREC_SPLIT, args.slices)
+                if jid is not None:
+                    break
+                rejected += 1
+                time.sleep(0.01)
+            ids.append(jid)
+        reps = [srv.wait(j, 3600.0) for j in ids]
+        wall = time.perf_counter() - t_start
+        clk = clocks.stop()
+        st = srv.stats()
+        lat = sorted(r["latency_ms"] for r in reps)
+        intervals = sum(wl.N for wl in built)
+        out_line.update(metric="served Magnus stream: intervals/sec with p50/p99 request latency",
+                        value=intervals / wall, ms_per_step=None, steps=1, warmup=0,
+                        dtype=f"bf16 digits x{args.slices} (fp32 accumulate) + f64",
+                        config={"workload": "poisson_200_per_s_mixed_d32_2048", "requests": len(ids),
+                                "arrival_span_s": stream_spec[-1][0], "d_max": max(wl.d for wl in built),
+                                "intervals_total": intervals, "quantum_intervals": 256},
+                        latency_ms={"p50": st["p50_ms"], "p99": st["p99_ms"], "max": lat[-1]},
+                        admission_retries=rejected, clocks=clk)
+        srv.close()
+    ctx.close()
+    print(json.dumps(out_line), flush=True)
+
+
+# ----------------------------------------------------------------------------
 # reference arm: the CPU FP64 oracle, timed on the host cores (rank 0 only)
 # ----------------------------------------------------------------------------
 def run_reference(args):
@@ -328,5 +517,7 @@ if __name__ == "__main__":
     a = parse()
     if a.impl == "reference":
         run_reference(a)
+    elif a.config != 1:
+        run_config(a)
     else:
         run_ours(a)

@@ -381,3 +381,24 @@ def serving_stream(rate_hz=200.0, duration_s=60.0, seed=4, d_min=32, d_max=2048)
                             output="unitary" if rng.uniform() < 0.5 else "state",
                             seed=int(rng.integers(0, 2**31 - 1)))))
     return out
+
+
+def serving_job(spec: dict) -> Workload:
+    """The Workload of one request of `serving_stream`: a 3-level transmon chain of
+    log3(d) sites or a transmon-resonator with nt x nr = d, N intervals of dt, one
+    drive per transmon, parameters drawn from the request's seed."""
+    rng = np.random.default_rng(spec["seed"])
+    N, dt = spec["N"], spec["dt"]
+    T = N * dt
+    state = spec["output"] == "state"
+    if spec["family"] == "chain3":
+        n = int(round(math.log(spec["d"]) / math.log(3)))
+        return transmon_chain(n_sites=n, levels=3, J=0.01, seed=int(rng.integers(0, 2**31 - 1)), T=T,
+                              sigma=T / 5, N=N, P=16, unitary=not state, name=f"chain3_d{spec['d']}")
+    d = spec["d"]
+    nt = next(k for k in range(8, 1, -1) if d % k == 0) if d > 1 else 1
+    nr = d // nt
+    return transmon_resonator(nt=nt, nr=nr, wq=rng.uniform(4.8, 5.2), alpha=rng.uniform(-0.3, -0.2),
+                              wr=rng.uniform(6.5, 7.5), g=rng.uniform(0.05, 0.15),
+                              omega0=0.05 * (1.0 - rng.uniform()), T=T, sigma=T / 5, N=N, P=16,
+                              phase=rng.uniform(0, TWO_PI), name=f"tr_d{d}", unitary=not state)
