@@ -43,6 +43,7 @@
 #include <cuda_bf16.h>
 
 #include <mutex>
+#include <algorithm>
 #include <cstring>
 
 namespace mg {
@@ -413,6 +414,9 @@ constexpr uint32_t kIdescBf16 = (1u << 4) | (1u << 7) | (1u << 10) | ((128u >> 3
 
 constexpr int SG_THREADS = 320;   // producer warp, MMA warp, 8 epilogue warps
 constexpr int SG_EPI_WARPS = 8;
+// epilogue staging tile: 128 rows x 64 complex (float4) with one float4 of padding per row
+constexpr int SG_EPI_PITCH = SG_BNC + 1;
+constexpr int SG_EPI_BYTES = SG_BM * SG_EPI_PITCH * 16;
 // TMEM accumulators: digit-pair levels 0, 1, 2 and >= 3, 128 columns each (all 512).
 constexpr int SG_GROUPS = 4;
 constexpr uint64_t SG_WAIT_NS = 4000000000ull;   // 4 s: far beyond any legitimate wait
@@ -445,12 +449,14 @@ split_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   constexpr int STAGE_BYTES = 2 * L * SG_TILE_BYTES;
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
+  constexpr int RING_BYTES = STAGES * STAGE_BYTES > SG_EPI_BYTES ? STAGES * STAGE_BYTES : SG_EPI_BYTES;
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + RING_BYTES);
   uint64_t* empty = full + STAGES;
   uint64_t* accfull = empty + STAGES;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accfull + 1);
   int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
   int* eb_s = abort_flag + 1;   // column exponents of this tile's 64 columns
+  int* epi_flag = eb_s + SG_BNC;  // epilogue verdict (accumulators ready and no abort)
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nt = blockIdx.x, mt = blockIdx.y, b = blockIdx.z;
@@ -541,24 +547,23 @@ split_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
     // ---------------- epilogue (warps 2..9) ----------------
     const int q = warp & 3;                   // TMEM lane quarter this warp may access
     const int c0 = ((warp - 2) >> 2) * (SG_BNC / 2);   // first of this warp's 32 complex columns
-    // one lane polls, the warp follows its verdict (tcgen05.ld is warp-collective)
-    int got_i = 0;
-    if (lane == 0) got_i = mbar_wait(accfull, 0, deadline) ? 1 : 0;
-    const bool got = __shfl_sync(0xffffffffu, got_i, 0) != 0;
+    // one thread polls; all eight epilogue warps follow its verdict, so that they
+    // either all reach both named barriers below or none does
+    if (warp == 2 && lane == 0) {
+      const bool got = mbar_wait(accfull, 0, deadline);
+      if (!got) atomicExch(status, MG_DEV_TIMEOUT);
+      *epi_flag = (got && *(volatile int*)abort_flag == 0) ? 1 : 0;
+    }
+    asm volatile("bar.sync 1, %0;" ::"n"(SG_EPI_WARPS * 32) : "memory");
     tc_fence_after();
-    if (!got) {
-      if (lane == 0) atomicExch(status, MG_DEV_TIMEOUT);
-    } else if (*(volatile int*)abort_flag == 0) {
-      const int row = mt * SG_BM + q * 32 + lane;
-      const bool row_ok = row < d;
-      const int Ea = row_ok ? ea[(long long)b * Mp + row] : 0;
-      const float4* addp[3];
-#pragma unroll
-      for (int m = 0; m < 3; ++m)
-        addp[m] = epi.add_src[m] ? reinterpret_cast<const float4*>(epi.add_src[m] + b * epi.add_stride) : nullptr;
-      float4* Cb = reinterpret_cast<float4*>(C + b * sC);
+    if (*(volatile int*)epi_flag != 0) {
+      // phase 1 (thread = row): TMEM -> level combine -> double-float tile in shared memory
+      // (the stage ring is idle once every MMA has completed)
+      float4* stile = reinterpret_cast<float4*>(smem);
+      const int r = q * 32 + lane;                 // tile-local row
+      const int row = mt * SG_BM + r;
+      const int Ea = row < d ? ea[(long long)b * Mp + row] : 0;
       const uint32_t lane_base = tmem + ((uint32_t)(q * 32) << 16);
-      const long long row_off = (long long)row * d;
       constexpr int CW = 4;   // complex columns per step
       for (int jc = c0; jc < c0 + SG_BNC / 2; jc += CW) {
         uint32_t re_acc[SG_GROUPS][CW], im_acc[SG_GROUPS][CW];
@@ -567,39 +572,51 @@ split_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
           tmem_ld4(lane_base + g * 128 + jc, re_acc[g]);
           tmem_ld4(lane_base + g * 128 + SG_BNC + jc, im_acc[g]);
         }
-        // issue every addend load of these columns before the arithmetic
-        float4 ad[3][CW];
-#pragma unroll
-        for (int m = 0; m < 3; ++m)
-#pragma unroll
-          for (int jj = 0; jj < CW; ++jj) {
-            const int j = nt * SG_BNC + jc + jj;
-            ad[m][jj] = (m < epi.add_n && row_ok && j < d) ? addp[m][row_off + j] : make_float4(0.f, 0.f, 0.f, 0.f);
-          }
         tmem_wait_ld();
-        if (row_ok) {
 #pragma unroll
-          for (int jj = 0; jj < CW; ++jj) {
-            const int j = nt * SG_BNC + jc + jj;
-            if (j < d) {
-              const int k = Ea + eb_s[jc + jj] + 2 - 2 * beta;
-              // levels that no digit pair reaches (L < 4) were never written: they hold
-              // whatever an earlier kernel left in TMEM and must not be read as data
-              df32 re = combine_levels(re_acc[0][jj], L > 1 ? re_acc[1][jj] : 0u, L > 2 ? re_acc[2][jj] : 0u,
-                                       L > 3 ? re_acc[3][jj] : 0u, k);
-              df32 im = combine_levels(im_acc[0][jj], L > 1 ? im_acc[1][jj] : 0u, L > 2 ? im_acc[2][jj] : 0u,
-                                       L > 3 ? im_acc[3][jj] : 0u, k);
+        for (int jj = 0; jj < CW; ++jj) {
+          const int k = Ea + eb_s[jc + jj] + 2 - 2 * beta;
+          // levels that no digit pair reaches (L < 4) were never written: they hold
+          // whatever an earlier kernel left in TMEM and must not be read as data
+          const df32 re = combine_levels(re_acc[0][jj], L > 1 ? re_acc[1][jj] : 0u, L > 2 ? re_acc[2][jj] : 0u,
+                                         L > 3 ? re_acc[3][jj] : 0u, k);
+          const df32 im = combine_levels(im_acc[0][jj], L > 1 ? im_acc[1][jj] : 0u, L > 2 ? im_acc[2][jj] : 0u,
+                                         L > 3 ? im_acc[3][jj] : 0u, k);
+          stile[r * SG_EPI_PITCH + jc + jj] = make_float4(re.hi, re.lo, im.hi, im.lo);
+        }
+      }
+      tc_fence_before();
+      asm volatile("bar.sync 1, %0;" ::"n"(SG_EPI_WARPS * 32) : "memory");
+      // phase 2 (warp = row, lane = column): addends and coalesced row stores
+      const float4* addp[3];
 #pragma unroll
-              for (int m = 0; m < 3; ++m) {
-                if (m < epi.add_n) {
-                  re = df_add(re, df_mul(df32{ad[m][jj].x, ad[m][jj].y}, epi.add_coef[m]));
-                  im = df_add(im, df_mul(df32{ad[m][jj].z, ad[m][jj].w}, epi.add_coef[m]));
-                }
-              }
-              if (row == j) re = df_add(re, epi.diag);
-              Cb[row_off + j] = make_float4(re.hi, re.lo, im.hi, im.lo);
+      for (int m = 0; m < 3; ++m)
+        addp[m] = epi.add_src[m] ? reinterpret_cast<const float4*>(epi.add_src[m] + b * epi.add_stride) : nullptr;
+      float4* Cb = reinterpret_cast<float4*>(C + b * sC);
+      const int ew = warp - 2;
+      for (int rr = ew; rr < SG_BM; rr += SG_EPI_WARPS) {
+        const int grow = mt * SG_BM + rr;
+        if (grow >= d) break;
+#pragma unroll
+        for (int h = 0; h < SG_BNC / 32; ++h) {
+          const int c = h * 32 + lane;
+          const int j = nt * SG_BNC + c;
+          if (j >= d) continue;
+          const long long off = (long long)grow * d + j;
+          float4 ad[3];
+#pragma unroll
+          for (int m = 0; m < 3; ++m) ad[m] = m < epi.add_n ? addp[m][off] : make_float4(0.f, 0.f, 0.f, 0.f);
+          const float4 v = stile[rr * SG_EPI_PITCH + c];
+          df32 re{v.x, v.y}, im{v.z, v.w};
+#pragma unroll
+          for (int m = 0; m < 3; ++m) {
+            if (m < epi.add_n) {
+              re = df_add(re, df_mul(df32{ad[m].x, ad[m].y}, epi.add_coef[m]));
+              im = df_add(im, df_mul(df32{ad[m].z, ad[m].w}, epi.add_coef[m]));
             }
           }
+          if (grow == j) re = df_add(re, epi.diag);
+          Cb[off] = make_float4(re.hi, re.lo, im.hi, im.lo);
         }
       }
     }
@@ -666,7 +683,8 @@ static int launch_split_gemm_L(const SplitGeom& g, int batch, const __nv_bfloat1
   CUtensorMap ma, mb;
   MG_TRY(make_digit_map(&ma, Ad, g.Kp, g.Mp, L, batch));
   MG_TRY(make_digit_map(&mb, Bd, g.Kp, g.Np, L, batch));
-  const size_t smem = (size_t)STAGES * 2 * L * SG_TILE_BYTES + 1024 /*barriers, exponents*/ + 1024 /*align*/;
+  const size_t ring = std::max<size_t>((size_t)STAGES * 2 * L * SG_TILE_BYTES, (size_t)SG_EPI_BYTES);
+  const size_t smem = ring + 1024 /*barriers, exponents*/ + 1024 /*align*/;
   auto kern = split_gemm_kernel<L, STAGES>;
   MG_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   dim3 grid(ceil_div(g.d, SG_BNC), g.Mp / SG_BM, batch);
