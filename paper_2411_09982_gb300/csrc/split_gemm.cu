@@ -27,10 +27,13 @@
 // Kernel structure (one 128 x 64-complex output tile per CTA, 320 threads):
 //   warp 0      TMA producer: per K-step of 16 one 4-D box of all L A-digit
 //               tiles (128 x 16 BF16 each) and one of all L B-digit tiles,
-//               SWIZZLE_32B, into a STAGES-deep ring of shared-memory stages.
+//               SWIZZLE_64B (64-byte rows: half the TMA row requests of 32-byte
+//               rows, which capped operand delivery at ~58 GB/s per SM), into a
+//               STAGES-deep ring of shared-memory stages.
 //   warp 1      TMEM owner and MMA issuer: tcgen05.mma kind::f16 (BF16 in,
 //               FP32 accumulate), M = 128, N = 128 (64 real + 64 imaginary
-//               output columns), K = 16, one instruction per digit pair.
+//               output columns), K = 16, two instructions per digit pair and
+//               stage (the second starts 32 bytes into the swizzle atom).
 //   warps 2..9  epilogue: tcgen05.ld of the four accumulators (two warps per TMEM
 //               lane quarter, 32 complex columns each), double-float combine.
 // Every mbarrier wait is bounded by a wall-clock deadline; a wait that gives up
@@ -53,8 +56,9 @@ namespace mg {
 // ---------------------------------------------------------------------------
 constexpr int SG_BM = 128;      // output rows per tile
 constexpr int SG_BNC = 64;      // complex output columns per tile (N = 128 real)
-constexpr int SG_BK = 16;       // K per stage (32 bytes of BF16: one SW32 atom)
-constexpr int SG_TILE_BYTES = SG_BM * SG_BK * 2;   // 4096 bytes per digit tile
+constexpr int SG_BK = 32;       // K per stage (64 bytes of BF16: one SW64 atom row, two MMA K-steps)
+constexpr int SG_MMA_K = 16;    // K of one tcgen05.mma kind::f16
+constexpr int SG_TILE_BYTES = SG_BM * SG_BK * 2;   // 8192 bytes per digit tile
 
 struct SplitGeom {
   int d, L, beta;
@@ -397,15 +401,18 @@ __device__ __forceinline__ void tmem_ld4(uint32_t taddr, uint32_t (&r)[4]) {
 }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
-// Shared-memory matrix descriptor: K-major operand tile, 32-byte swizzle,
-// 8-row core groups 256 bytes apart (rows are 32 bytes), descriptor version 1.
-__device__ __forceinline__ uint64_t sw32_kmajor_desc(uint32_t saddr) {
+// Shared-memory matrix descriptor: K-major operand tile, 64-byte swizzle,
+// 8-row core groups 512 bytes apart (rows are 64 bytes), descriptor version 1.
+// The second K = 16 step of a 64-byte row starts 32 bytes further: the swizzle
+// is applied to the final address bits, so advancing the start address inside
+// the atom selects the next 16 elements of every row.
+__device__ __forceinline__ uint64_t sw64_kmajor_desc(uint32_t saddr) {
   uint64_t desc = 0;
   desc |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
   desc |= (uint64_t)1 << 16;            // leading-dimension offset (unused with swizzle)
-  desc |= (uint64_t)(256 >> 4) << 32;   // stride-dimension offset
+  desc |= (uint64_t)(512 >> 4) << 32;   // stride-dimension offset
   desc |= (uint64_t)1 << 46;            // descriptor version
-  desc |= (uint64_t)6 << 61;            // SWIZZLE_32B
+  desc |= (uint64_t)4 << 61;            // SWIZZLE_64B
   return desc;
 }
 
@@ -528,14 +535,17 @@ split_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
         const uint32_t b0 = a0 + L * SG_TILE_BYTES;
         bool first[SG_GROUPS] = {kb == 0, kb == 0, kb == 0, kb == 0};
 #pragma unroll
-        for (int sa = 0; sa < L; ++sa) {
+        for (int kk = 0; kk < SG_BK / SG_MMA_K; ++kk) {
 #pragma unroll
-          for (int sb = 0; sb < L - sa; ++sb) {
-            const int g = (sa + sb) < SG_GROUPS - 1 ? (sa + sb) : SG_GROUPS - 1;
-            const uint32_t acc = first[g] ? 0u : 1u;
-            first[g] = false;
-            tc_mma_bf16(tmem + g * 128, sw32_kmajor_desc(a0 + sa * SG_TILE_BYTES),
-                        sw32_kmajor_desc(b0 + sb * SG_TILE_BYTES), kIdescBf16, acc);
+          for (int sa = 0; sa < L; ++sa) {
+#pragma unroll
+            for (int sb = 0; sb < L - sa; ++sb) {
+              const int g = (sa + sb) < SG_GROUPS - 1 ? (sa + sb) : SG_GROUPS - 1;
+              const uint32_t acc = first[g] ? 0u : 1u;
+              first[g] = false;
+              tc_mma_bf16(tmem + g * 128, sw64_kmajor_desc(a0 + sa * SG_TILE_BYTES + kk * SG_MMA_K * 2),
+                          sw64_kmajor_desc(b0 + sb * SG_TILE_BYTES + kk * SG_MMA_K * 2), kIdescBf16, acc);
+            }
           }
         }
         tc_commit(&empty[s]);
@@ -652,7 +662,7 @@ static int get_encoder() {
   return MG_OK;
 }
 
-// 4-D map over digit tiles: (k, row, slice, batch), box (16, 128, L, 1), SWIZZLE_32B.
+// 4-D map over digit tiles: (k, row, slice, batch), box (32, 128, L, 1), SWIZZLE_64B.
 static int make_digit_map(CUtensorMap* map, const void* base, int Kp, int rows, int L, int batch) {
   MG_TRY(get_encoder());
   cuuint64_t dims[4] = {(cuuint64_t)Kp, (cuuint64_t)rows, (cuuint64_t)L, (cuuint64_t)batch};
@@ -660,7 +670,7 @@ static int make_digit_map(CUtensorMap* map, const void* base, int Kp, int rows, 
   cuuint32_t box[4] = {(cuuint32_t)SG_BK, (cuuint32_t)SG_BM, (cuuint32_t)L, 1};
   cuuint32_t estr[4] = {1, 1, 1, 1};
   CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(base), dims, strides, box,
-                        estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B,
+                        estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
                         CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) {
     set_last_message("cuTensorMapEncodeTiled failed (%d): Kp=%d rows=%d L=%d batch=%d", (int)r, Kp, rows, L,
@@ -672,7 +682,9 @@ static int make_digit_map(CUtensorMap* map, const void* base, int Kp, int rows, 
 
 template <int L>
 static constexpr int stages_for() {
-  return (196608 / (2 * L * SG_TILE_BYTES)) > 8 ? 8 : (196608 / (2 * L * SG_TILE_BYTES));
+  // ring budget 224 KiB (the opt-in limit is 227 KiB per block; 2 KiB go to barriers and alignment)
+  return (229376 / (2 * L * SG_TILE_BYTES)) > 8 ? 8
+         : ((229376 / (2 * L * SG_TILE_BYTES)) < 1 ? 1 : (229376 / (2 * L * SG_TILE_BYTES)));
 }
 
 template <int L>
