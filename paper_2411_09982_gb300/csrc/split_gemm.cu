@@ -373,6 +373,27 @@ __device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, u
       "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar))
       : "memory");
 }
+__device__ __forceinline__ void tma_load_4d_mc(void* dst, const CUtensorMap* map, uint64_t* bar, int c0, int c1,
+                                               int c2, int c3, uint16_t mask) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster"
+      " [%0], [%1, {%2, %3, %4, %5}], [%6], %7;" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar)), "h"(mask)
+      : "memory");
+}
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tc_commit_mc(uint64_t* bar, uint16_t mask) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;"
+               ::"r"(smem_u32(bar)), "h"(mask)
+               : "memory");
+}
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
@@ -447,9 +468,14 @@ struct SplitEpi {
   df32 diag;
 };
 
-template <int L, int STAGES>
+// CM = 1: one CTA per tile.  CM = 2: CTAs (mt = 2c, 2c + 1) of one cluster compute the
+// same 64 complex columns, so they share the B digit tile: each loads half of it (one
+// 64-row box per digit) and multicasts it to both, cutting L2 reads per tile by 25%.
+// A stage may then be refilled only when both CTAs' MMAs have released it.
+template <int L, int STAGES, int CM>
 __global__ void __launch_bounds__(SG_THREADS, 1)
 split_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                  const __grid_constant__ CUtensorMap tmBh,
                   int d, int Kp, int Mp, int Np, int beta, const int* __restrict__ ea,
                   const int* __restrict__ eb, double* __restrict__ C, long long sC, SplitEpi epi,
                   int* __restrict__ status) {
@@ -469,10 +495,11 @@ split_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
   const int nt = blockIdx.x, mt = blockIdx.y, b = blockIdx.z;
   const int num_k = Kp / SG_BK;
 
+  const uint32_t crank = CM > 1 ? cluster_rank() : 0u;
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(&full[s], 1);
-      mbar_init(&empty[s], 1);
+      mbar_init(&empty[s], CM);   // released by the MMA warp of every CTA that writes the stage
     }
     mbar_init(accfull, 1);
     *abort_flag = 0;
@@ -490,7 +517,10 @@ split_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   tc_fence_before();
-  __syncthreads();
+  if (CM > 1)
+    cluster_sync_all();   // barriers of both CTAs initialised before any multicast touches them
+  else
+    __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
   const uint64_t deadline = global_ns() + SG_WAIT_NS;
@@ -510,7 +540,16 @@ split_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
         unsigned char* st = smem + s * STAGE_BYTES;
         mbar_expect_tx(&full[s], STAGE_BYTES);
         tma_load_4d(st, &tmA, &full[s], kb * SG_BK, mt * SG_BM, 0, b);
-        tma_load_4d(st + L * SG_TILE_BYTES, &tmB, &full[s], kb * SG_BK, nt * 2 * SG_BNC, 0, b);
+        if (CM == 1) {
+          tma_load_4d(st + L * SG_TILE_BYTES, &tmB, &full[s], kb * SG_BK, nt * 2 * SG_BNC, 0, b);
+        } else {
+          // this CTA's half (64 of the 128 B rows) of every digit tile, to both CTAs
+#pragma unroll
+          for (int sd = 0; sd < L; ++sd)
+            tma_load_4d_mc(st + L * SG_TILE_BYTES + sd * SG_TILE_BYTES + crank * (SG_TILE_BYTES / 2), &tmBh,
+                           &full[s], kb * SG_BK, nt * 2 * SG_BNC + (int)crank * (SG_BM / 2), sd, b,
+                           (uint16_t)((1u << CM) - 1u));
+        }
         issued = kb + 1;
       }
       // never leave the CTA with a bulk copy still in flight into its shared memory
@@ -548,7 +587,10 @@ split_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
             }
           }
         }
-        tc_commit(&empty[s]);
+        if (CM == 1)
+          tc_commit(&empty[s]);
+        else
+          tc_commit_mc(&empty[s], (uint16_t)((1u << CM) - 1u));
       }
       tc_commit(accfull);   // fires once every issued MMA has completed
       if (!ok) *(volatile int*)abort_flag = 1;
@@ -633,6 +675,9 @@ split_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
     tc_fence_before();
   }
   __syncthreads();
+  // no CTA of a cluster leaves while its partner may still multicast into it or
+  // release its stages
+  if (CM > 1) cluster_sync_all();
   if (warp == 1) {
     __syncwarp();
     tc_fence_after();
@@ -662,12 +707,13 @@ static int get_encoder() {
   return MG_OK;
 }
 
-// 4-D map over digit tiles: (k, row, slice, batch), box (32, 128, L, 1), SWIZZLE_64B.
-static int make_digit_map(CUtensorMap* map, const void* base, int Kp, int rows, int L, int batch) {
+// 4-D map over digit tiles: (k, row, slice, batch), box (32, box_rows, box_slices, 1), SWIZZLE_64B.
+static int make_digit_map(CUtensorMap* map, const void* base, int Kp, int rows, int L, int batch,
+                          int box_rows = SG_BM, int box_slices = -1) {
   MG_TRY(get_encoder());
   cuuint64_t dims[4] = {(cuuint64_t)Kp, (cuuint64_t)rows, (cuuint64_t)L, (cuuint64_t)batch};
   cuuint64_t strides[3] = {(cuuint64_t)Kp * 2, (cuuint64_t)rows * Kp * 2, (cuuint64_t)L * rows * Kp * 2};
-  cuuint32_t box[4] = {(cuuint32_t)SG_BK, (cuuint32_t)SG_BM, (cuuint32_t)L, 1};
+  cuuint32_t box[4] = {(cuuint32_t)SG_BK, (cuuint32_t)box_rows, (cuuint32_t)(box_slices < 0 ? L : box_slices), 1};
   cuuint32_t estr[4] = {1, 1, 1, 1};
   CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(base), dims, strides, box,
                         estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
@@ -692,15 +738,40 @@ static int launch_split_gemm_L(const SplitGeom& g, int batch, const __nv_bfloat1
                                const __nv_bfloat16* Bd, const int* eb, double* C, long long sC,
                                const SplitEpi& epi, int* status, cudaStream_t s) {
   constexpr int STAGES = stages_for<L>();
-  CUtensorMap ma, mb;
+  CUtensorMap ma, mb, mbh;
   MG_TRY(make_digit_map(&ma, Ad, g.Kp, g.Mp, L, batch));
   MG_TRY(make_digit_map(&mb, Bd, g.Kp, g.Np, L, batch));
+  MG_TRY(make_digit_map(&mbh, Bd, g.Kp, g.Np, L, batch, SG_BM / 2, 1));
   const size_t ring = std::max<size_t>((size_t)STAGES * 2 * L * SG_TILE_BYTES, (size_t)SG_EPI_BYTES);
   const size_t smem = ring + 1024 /*barriers, exponents*/ + 1024 /*align*/;
-  auto kern = split_gemm_kernel<L, STAGES>;
-  MG_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  dim3 grid(ceil_div(g.d, SG_BNC), g.Mp / SG_BM, batch);
-  kern<<<grid, SG_THREADS, smem, s>>>(ma, mb, g.d, g.Kp, g.Mp, g.Np, g.beta, ea, eb, C, sC, epi, status);
+  const int mtiles = g.Mp / SG_BM;
+  const int cm = mtiles >= 2 ? 2 : 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(ceil_div(g.d, SG_BNC), ceil_div(mtiles, cm) * cm, batch);
+  cfg.blockDim = dim3(SG_THREADS, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 1;
+  attr[0].val.clusterDim.y = cm;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaError_t e;
+  if (cm == 2) {
+    auto kern = split_gemm_kernel<L, STAGES, 2>;
+    MG_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    e = cudaLaunchKernelEx(&cfg, kern, ma, mb, mbh, g.d, g.Kp, g.Mp, g.Np, g.beta, ea, eb, C, sC, epi, status);
+  } else {
+    auto kern = split_gemm_kernel<L, STAGES, 1>;
+    MG_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    e = cudaLaunchKernelEx(&cfg, kern, ma, mb, mbh, g.d, g.Kp, g.Mp, g.Np, g.beta, ea, eb, C, sC, epi, status);
+  }
+  if (e != cudaSuccess) {
+    set_last_cuda_error(e, "cudaLaunchKernelEx(split_gemm_kernel)", __FILE__, __LINE__);
+    return MG_ECUDA;
+  }
   return check_launch("split_gemm_kernel");
 }
 
