@@ -75,6 +75,11 @@ extern "C" {
 #define MG_FLAG_HOST_PTRS        1  /* the call's data pointers are host memory */
 #define MG_FLAG_CHECK_HERMITIAN  2  /* plan: reject operators with |H - H^dag| > 1e-12 |H| */
 #define MG_FLAG_NO_TRACE_SHIFT   4  /* plan: exponentiate Hbar_n itself, not Hbar_n - tr/d I */
+/* plan: state outputs apply exp(-i Hbar_n) to the state by a scaled Taylor series
+ * of sparse (CSR) matrix-vector products in FP64 instead of forming U_n; exact up
+ * to the unit roundoff, cheaper whenever the operators are sparse.  Propagator
+ * outputs are unaffected. */
+#define MG_FLAG_STATE_ACTION     8
 
 typedef struct mg_ctx mg_ctx;
 typedef struct mg_plan mg_plan;

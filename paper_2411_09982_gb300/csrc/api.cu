@@ -94,6 +94,14 @@ struct mg_plan {
   int order = 1;
   int Kx = 0;               // operators entering Hbar_n: K (order 1) or 2K + K(K-1)/2 (order 2)
   double* mrc = nullptr;    // second-order quadrature matrix on the device
+  // CSR copies of H0 and the Kx operators for the action-based state path
+  bool csr_ok = false;
+  int* csr_rowptr = nullptr;
+  int* csr_col = nullptr;
+  double* csr_val = nullptr;
+  int* csr_opoff = nullptr;
+  double* csr_tmean = nullptr;   // trace means
+  double* csr_snorm = nullptr;   // ||H - t I||_1
 };
 
 namespace {
@@ -535,6 +543,81 @@ int validate_prec(int precision, int L) {
 }  // namespace
 
 namespace {
+// CSR copies of H0 and the plan's Kx operators (host-built once from the dense
+// device copies), with each operator's trace mean and shifted 1-norm.
+int ensure_csr(mg_plan* p) {
+  if (p->csr_ok) return MG_OK;
+  if (p->Kx + 1 > 256) {
+    set_last_message("action-based state path supports at most 255 control operators (plan has %d)", p->Kx);
+    return MG_EUNSUPPORTED;
+  }
+  if (p->d > 4096 / 1) { return MG_EUNSUPPORTED; }
+  const int d = p->d, nops = 1 + p->Kx;
+  const size_t dd = (size_t)d * d;
+  std::vector<double> dense(2 * dd);
+  std::vector<int> rowptr((size_t)nops * (d + 1)), col, opoff(nops);
+  std::vector<double> val, tmean(nops), snorm(nops);
+  for (int op = 0; op < nops; ++op) {
+    const double* src = op == 0 ? p->H0 : p->Hk + (size_t)(op - 1) * 2 * dd;
+    MG_CUDA_TRY(cudaMemcpy(dense.data(), src, sizeof(double) * 2 * dd, cudaMemcpyDeviceToHost));
+    opoff[op] = (int)col.size();
+    double tr = 0.0;
+    for (int i = 0; i < d; ++i) tr += dense[2 * ((size_t)i * d + i)];
+    tmean[op] = tr / d;
+    std::vector<double> colsum(d, 0.0);
+    int* rp = rowptr.data() + (size_t)op * (d + 1);
+    rp[0] = 0;
+    for (int i = 0; i < d; ++i) {
+      for (int j = 0; j < d; ++j) {
+        const double re = dense[2 * ((size_t)i * d + j)], im = dense[2 * ((size_t)i * d + j) + 1];
+        colsum[j] += std::hypot(re - (i == j ? tmean[op] : 0.0), im);
+        if (re != 0.0 || im != 0.0) {
+          col.push_back(j);
+          val.push_back(re);
+          val.push_back(im);
+        }
+      }
+      rp[i + 1] = (int)col.size() - opoff[op];
+    }
+    snorm[op] = *std::max_element(colsum.begin(), colsum.end());
+  }
+  auto up = [&](void** dst, const void* src, size_t bytes) -> int {
+    cudaFree(*dst);
+    *dst = nullptr;
+    if (cudaMalloc(dst, std::max<size_t>(bytes, 16)) != cudaSuccess) { cudaGetLastError(); return MG_ENOMEM; }
+    MG_CUDA_TRY(cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice));
+    return MG_OK;
+  };
+  MG_TRY(up(reinterpret_cast<void**>(&p->csr_rowptr), rowptr.data(), sizeof(int) * rowptr.size()));
+  MG_TRY(up(reinterpret_cast<void**>(&p->csr_col), col.data(), sizeof(int) * col.size()));
+  MG_TRY(up(reinterpret_cast<void**>(&p->csr_val), val.data(), sizeof(double) * val.size()));
+  MG_TRY(up(reinterpret_cast<void**>(&p->csr_opoff), opoff.data(), sizeof(int) * opoff.size()));
+  MG_TRY(up(reinterpret_cast<void**>(&p->csr_tmean), tmean.data(), sizeof(double) * tmean.size()));
+  MG_TRY(up(reinterpret_cast<void**>(&p->csr_snorm), snorm.data(), sizeof(double) * snorm.size()));
+  p->csr_ok = true;
+  return MG_OK;
+}
+
+ActionJob action_job(mg_plan* p, double* psi) {
+  ActionJob j{};
+  j.d = p->d;
+  j.K = p->Kx;
+  j.N = p->N;
+  j.first = 0;
+  j.dt = p->dt;
+  j.rowptr = p->csr_rowptr;
+  j.col = p->csr_col;
+  j.val = p->csr_val;
+  j.opoff = p->csr_opoff;
+  j.c = p->c;
+  j.trace_mean = p->csr_tmean;
+  j.shifted_norm = p->csr_snorm;
+  j.psi = psi;
+  return j;
+}
+}  // namespace
+
+namespace {
 int lagrange_triangle(int P, std::vector<double>& mrc) {
   std::vector<double> x(P), wl(P), sn(P);
   MG_TRY(mg_quadrature_nodes(P, x.data(), wl.data()));
@@ -770,6 +853,12 @@ int mg_plan_destroy(mg_plan* p) {
   cudaFree(p->samples);
   cudaFree(p->c);
   cudaFree(p->mrc);
+  cudaFree(p->csr_rowptr);
+  cudaFree(p->csr_col);
+  cudaFree(p->csr_val);
+  cudaFree(p->csr_opoff);
+  cudaFree(p->csr_tmean);
+  cudaFree(p->csr_snorm);
   delete p;
   return MG_OK;
 }
@@ -1025,6 +1114,27 @@ int mg_evolve(mg_plan* p, int output, const double* in, double* out, int reorth_
   ps.output = output;
   ps.d = d;
   MG_TRY(begin_prop(ctx, eng, ps, in, flags));
+  if (output == MG_OUT_STATE && (p->flags & MG_FLAG_STATE_ACTION)) {
+    // action-based: exp(-i Hbar_n) applied to the state by sparse Taylor steps
+    MG_TRY(ensure_csr(p));
+    ActionJob job = action_job(p, ps.psi);
+    double* jbuf;
+    MG_TRY(ws(ctx, WS_VEC, sizeof(ActionJob) / sizeof(double) + 1, &jbuf));
+    MG_CUDA_TRY(cudaMemcpyAsync(jbuf, &job, sizeof(ActionJob), cudaMemcpyHostToDevice, s));
+    MG_TRY(launch_action_chain(1, reinterpret_cast<ActionJob*>(jbuf), d, s));
+    MG_CUDA_TRY(cudaStreamSynchronize(s));   // the job record lives on the host stack
+    MG_TRY(finish_prop(ctx, eng, ps, out, flags, rep));
+    if (rep) {
+      MG_CUDA_TRY(cudaEventRecord(ctx->ev1, s));
+      MG_CUDA_TRY(cudaEventSynchronize(ctx->ev1));
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
+      rep->ms_total = ms;
+      rep->intervals = p->N;
+    }
+    MG_CUDA_TRY(cudaStreamSynchronize(s));
+    return MG_OK;
+  }
   int align = 1;
   if (output == MG_OUT_PROPAGATOR && reorth_every > 1) align = reorth_every;
   const int chunk = chunk_size(ctx, d, p->precision, p->L, p->N, align);
@@ -1358,6 +1468,52 @@ int mg_evolve_batch(mg_ctx* ctx, int n, mg_plan* const* plans, const int* output
     j.c = p->c;
     const int L = p->precision == MG_PREC_SPLIT ? p->L : 0;
     all.push_back({Key{p->precision, L, round_dim(p->d)}, j, p});
+  }
+  // state jobs of action-flagged plans: every one in a single launch, one CTA per job
+  {
+    std::vector<ActionJob> aj;
+    std::vector<int> aidx;
+    std::vector<Item> rest;
+    int dmax = 1;
+    for (auto& it : all) {
+      if (it.j.output == MG_OUT_STATE && (it.p->flags & MG_FLAG_STATE_ACTION)) {
+        aidx.push_back(it.j.idx);
+        aj.push_back(ActionJob{});
+        dmax = std::max(dmax, it.p->d);
+      } else {
+        rest.push_back(it);
+      }
+    }
+    if (!aj.empty()) {
+      const cudaMemcpyKind h2d = (flags & MG_FLAG_HOST_PTRS) ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+      const cudaMemcpyKind d2h = (flags & MG_FLAG_HOST_PTRS) ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+      size_t total = 0;
+      for (int q : aidx) total += 2 * (size_t)plans[q]->d;
+      double *psis, *jb;
+      MG_TRY(ws(ctx, WS_ACC, total, &psis));
+      MG_TRY(ws(ctx, WS_VEC, (sizeof(ActionJob) * aj.size()) / sizeof(double) + 1, &jb));
+      size_t off = 0;
+      for (size_t q = 0; q < aidx.size(); ++q) {
+        mg_plan* p = plans[aidx[q]];
+        if (!in || !in[aidx[q]]) return MG_EINVAL;
+        MG_TRY(ensure_csr(p));
+        aj[q] = action_job(p, psis + off);
+        MG_CUDA_TRY(cudaMemcpyAsync(psis + off, in[aidx[q]], sizeof(double) * 2 * p->d, h2d, ctx->stream));
+        off += 2 * (size_t)p->d;
+      }
+      MG_CUDA_TRY(cudaMemcpyAsync(jb, aj.data(), sizeof(ActionJob) * aj.size(), cudaMemcpyHostToDevice, ctx->stream));
+      MG_TRY(launch_action_chain((int)aj.size(), reinterpret_cast<ActionJob*>(jb), dmax, ctx->stream));
+      off = 0;
+      for (size_t q = 0; q < aidx.size(); ++q) {
+        mg_plan* p = plans[aidx[q]];
+        MG_CUDA_TRY(cudaMemcpyAsync(out[aidx[q]], psis + off, sizeof(double) * 2 * p->d, d2h, ctx->stream));
+        off += 2 * (size_t)p->d;
+        if (job_status) job_status[aidx[q]] = MG_OK;
+      }
+      MG_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    }
+    all.swap(rest);
+    if (all.empty()) return MG_OK;
   }
   std::stable_sort(all.begin(), all.end(), [](const Item& a, const Item& b) { return a.k < b.k; });
   int rc = MG_OK;
@@ -1711,6 +1867,7 @@ int mg_plan_set_magnus_order(mg_plan* p, int order) {
   if (order == 1 || K == 0) {
     p->order = order;
     p->Kx = K;
+    p->csr_ok = false;
     p->N = 0;   // controls must be set again
     return MG_OK;
   }
@@ -1752,6 +1909,7 @@ int mg_plan_set_magnus_order(mg_plan* p, int order) {
   }
   cudaFree(p->Hk);
   p->Hk = Hx;
+  p->csr_ok = false;
   p->order = 2;
   p->Kx = Kx;
   p->N = 0;   // controls must be set again

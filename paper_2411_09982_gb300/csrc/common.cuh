@@ -143,6 +143,25 @@ struct ChainSeg {
 };
 int launch_multi_chain(int nseg, int d, const ChainSeg* segs_dev, const double* U, long long sU,
                        double* const* psi_dev, int reorth_every, cudaStream_t s);
+// Action-based state propagation with CSR operators; see action.cu.
+struct ActionJob {
+  int d;
+  int K;
+  int N;
+  int first;
+  double dt;
+  const int* rowptr;
+  const int* col;
+  const double* val;
+  const int* opoff;
+  const double* c;
+  const double* trace_mean;
+  const double* shifted_norm;
+  double* psi;
+  int status;
+};
+int launch_action_chain(int njobs, const ActionJob* jobs_dev, int dmax, cudaStream_t s);
+
 // dst (dp x dp, zero padded) <- src (d x d), for `count` stacked matrices
 int launch_pad_copy(int count, int d, int dp, const double* src, double* dst, cudaStream_t s);
 // top-left d x d block of dst (dp x dp) <- src (d x d); the rest of dst untouched

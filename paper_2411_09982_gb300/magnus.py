@@ -31,6 +31,7 @@ MG_OUT_PROPAGATOR = 1
 MG_FLAG_HOST_PTRS = 1
 MG_FLAG_CHECK_HERMITIAN = 2
 MG_FLAG_NO_TRACE_SHIFT = 4
+MG_FLAG_STATE_ACTION = 8
 
 
 class MagnusError(RuntimeError):
@@ -369,12 +370,14 @@ def node_samples(wl, N=None):
     return np.ascontiguousarray(wl.drive(t)), w
 
 
-def evolve_workload(ctx, wl, precision=MG_PREC_FP64, slices=6, N=None, reorth_every=0, device="cuda", order=1):
+def evolve_workload(ctx, wl, precision=MG_PREC_FP64, slices=6, N=None, reorth_every=0, device="cuda", order=1,
+                    flags=0):
     """Run a workloads.Workload through mg_plan_create / mg_set_controls / mg_evolve."""
     import torch
     N = wl.N if N is None else N
     samples, w = node_samples(wl, N)
-    plan = Plan(ctx, torch.from_numpy(wl.H0).to(device), torch.from_numpy(wl.Hk).to(device), precision, slices)
+    plan = Plan(ctx, torch.from_numpy(wl.H0).to(device), torch.from_numpy(wl.Hk).to(device), precision, slices,
+                flags)
     if order != 1:
         plan.set_magnus_order(order)
     plan.set_controls(N, wl.P, wl.t0, wl.dt, w, torch.from_numpy(samples).to(device))

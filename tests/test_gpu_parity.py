@@ -412,3 +412,42 @@ def test_second_order_magnus_matches_oracle(ctx, prec, L, tol):
         assert np.abs(got - ref2).max() <= tol, (wl.name, np.abs(got - ref2).max())
         # the commutator term matters for these drives: order 1 is far away
         assert np.abs(ref2 - ref1).max() > 1e3 * tol
+
+
+# ----------------------------------------------------------------------------
+# action-based state path with sparse operators (MG_FLAG_STATE_ACTION)
+# ----------------------------------------------------------------------------
+@pytest.mark.parametrize("order", [1, 2])
+def test_action_state_path_matches_oracle(ctx, order):
+    cases = [W.config(0, N=120), W.transmon_resonator(nt=3, nr=2, T=2.0, sigma=0.5, omega0=0.4, N=20, P=16),
+             W.transmon_chain(n_sites=3, levels=3, J=0.02, seed=4, omega0_max=0.2, T=5.0, sigma=1.2, N=30, P=16,
+                              unitary=False)]
+    for wl in cases:
+        out, _ = M.evolve_workload(ctx, wl, M.MG_PREC_FP64, order=order, flags=M.MG_FLAG_STATE_ACTION)
+        ref = oracle.evolve_workload(wl) if order == 1 else oracle.evolve_workload_second_order(wl)
+        err = np.abs(out.cpu().numpy() - ref).max()
+        assert err <= 1e-11, (wl.name, err)
+
+
+def test_action_state_path_in_batch(ctx):
+    jobs = _small_jobs(seed=31, n=6)
+    plans, outs, ins, kinds = [], [], [], []
+    for wl in jobs:
+        samples, w = M.node_samples(wl)
+        state = wl.psi0 is not None
+        p = M.Plan(ctx, cuda(wl.H0), cuda(wl.Hk), M.MG_PREC_FP64, 6, M.MG_FLAG_STATE_ACTION)
+        p.set_controls(wl.N, wl.P, wl.t0, wl.dt, w, cuda(samples))
+        plans.append(p)
+        kinds.append(M.MG_OUT_STATE if state else M.MG_OUT_PROPAGATOR)
+        ins.append(cuda(wl.psi0) if state else None)
+        outs.append(torch.empty(wl.d if state else (wl.d, wl.d), dtype=torch.complex128, device="cuda"))
+    try:
+        status = M.mg_evolve_batch(ctx, plans, kinds, ins, outs)
+        torch.cuda.synchronize()
+        assert status == [0] * len(jobs)
+        for wl, o in zip(jobs, outs):
+            ref, t = _norm_scaled_tol(wl, 1e-11)
+            assert np.abs(o.cpu().numpy() - ref).max() <= t, wl.name
+    finally:
+        for p in plans:
+            p.close()
