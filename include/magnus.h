@@ -76,9 +76,16 @@ extern "C" {
 #define MG_FLAG_CHECK_HERMITIAN  2  /* plan: reject operators with |H - H^dag| > 1e-12 |H| */
 #define MG_FLAG_NO_TRACE_SHIFT   4  /* plan: exponentiate Hbar_n itself, not Hbar_n - tr/d I */
 /* plan: state outputs apply exp(-i Hbar_n) to the state by a scaled Taylor series
- * of sparse (CSR) matrix-vector products in FP64 instead of forming U_n; exact up
- * to the unit roundoff, cheaper whenever the operators are sparse.  Propagator
- * outputs are unaffected. */
+ * of sparse (CSR) matrix-vector products in FP64 instead of forming U_n
+ * (Eq. magnus-first-order-term and the ordered product of the interval
+ * propagators, evaluated by their action on psi); exact up to the unit
+ * roundoff, cheaper whenever the operators are sparse.  One thread block per
+ * job, so it suits batches of jobs or large sparse d.  Limits: d <= 4800,
+ * at most 255 operators (after the commutators of order 2), and at most
+ * 16384 sub-steps of norm 2 per interval (||Hbar_n - tau_n I||_1 bound <= 32768);
+ * beyond the last the call (or the job's batch status) returns MG_EUNSUPPORTED,
+ * a non-finite bound MG_ENONFINITE.  The CSR copy of the operators is built on
+ * the host at the first such call.  Propagator outputs are unaffected. */
 #define MG_FLAG_STATE_ACTION     8
 
 typedef struct mg_ctx mg_ctx;
@@ -94,6 +101,8 @@ typedef struct mg_report {
   double  unitarity_defect;   /* max|U^dag U - I| (propagator) or |‖psi‖ - 1|  */
   double  ms_total;           /* wall time of the call on the device stream     */
   int64_t matrix_products;    /* complex d x d products issued                  */
+  int64_t sparse_matvecs;     /* operator applications (MG_FLAG_STATE_ACTION)   */
+  int64_t sparse_nnz;         /* stored nonzeros of H0 and the H_k (same path)  */
 } mg_report;
 
 /* ---- context ---------------------------------------------------------------- */
@@ -282,7 +291,9 @@ int mg_cgemm_split_static(int device, void* stream, int batch, int d, const doub
  * product launch on its stream; mg_ctx_gemm_stats synchronises the stream and
  * returns the number of launches, their summed device time (ms) and their
  * summed algorithmic work (8 d^3 real flops per complex d x d product, the
- * 4-real-multiplication form), then optionally resets the counters. */
+ * 4-real-multiplication form), then optionally resets the counters.  The
+ * action kernel of MG_FLAG_STATE_ACTION counts as one launch with 8 flops per
+ * stored operator nonzero per operator application. */
 int mg_ctx_enable_gemm_timing(mg_ctx* ctx, int enable);
 int mg_ctx_gemm_stats(mg_ctx* ctx, int64_t* launches, double* ms, double* flops, int reset);
 

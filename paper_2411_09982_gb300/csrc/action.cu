@@ -7,7 +7,7 @@
 //   (Hbar_n - tau_n I) v = dt (H0 - t0 I) v + sum_k c_{k,n} (H_k - t_k I) v,
 //
 // (t0, t_k the operators' trace means, tau_n = dt t0 + sum_k c_{k,n} t_k), with
-// a scaled Taylor series: s_n = ceil(nu_n / 6) sub-steps of at most 60 terms,
+// a scaled Taylor series: s_n = ceil(nu_n / 2) sub-steps of at most 40 terms,
 //   v <- sum_{j<=m} (-i A / s_n)^j v / j!,
 // stopped early once two consecutive terms fall below the FP64 unit roundoff
 // relative to the partial sum.  The operators are held in CSR (they are
@@ -23,11 +23,15 @@
 namespace mg {
 
 constexpr int ACTION_THREADS = 256;
-// theta = 6 with up to 60 terms: the terms needed per unit of norm fall as the
-// series lengthens (6^60/60! is far below the FP64 unit roundoff)
-constexpr int ACTION_MAX_TERMS = 60;
-constexpr double ACTION_THETA = 6.0;
+// Sub-step norm theta = 2: the rounding of one sub-step grows like e^theta
+// (the sum of the terms' magnitudes) while the sub-step count falls like
+// 1/theta; theta = 2 keeps the summed rounding of a long run within a few
+// times that of theta = 1 at 65% of its matvecs.  2^40/40! is far below the
+// FP64 unit roundoff, so 40 terms always suffice.
+constexpr int ACTION_MAX_TERMS = 40;
+constexpr double ACTION_THETA = 2.0;
 constexpr int ACTION_MAX_OPS = 256;
+constexpr int ACTION_MAX_SUBSTEPS = 1 << 14;
 
 __device__ __forceinline__ double2 cmul_i(double2 a, double s) {  // (-i s) a
   return make_double2(s * a.y, -s * a.x);
@@ -73,7 +77,7 @@ __device__ double block_max(double v, double* red) {
 }
 
 __global__ void __launch_bounds__(ACTION_THREADS)
-action_chain_kernel(const ActionJob* __restrict__ jobs, double theta) {
+action_chain_kernel(ActionJob* __restrict__ jobs, double theta) {
   extern __shared__ double2 vec[];
   __shared__ double red[ACTION_THREADS / 32];
   __shared__ double cn[ACTION_MAX_OPS];
@@ -83,6 +87,9 @@ action_chain_kernel(const ActionJob* __restrict__ jobs, double theta) {
   double2* term = vec + d;
   double2* nxt = vec + 2 * d;
   for (int i = threadIdx.x; i < d; i += blockDim.x) psi[i] = reinterpret_cast<double2*>(J.psi)[i];
+  long long matvecs = 0;
+  int max_sub = 0, min_sub = 1 << 30, max_terms = 0;
+  double max_nu = 0.0;
   __syncthreads();
   for (int n = 0; n < J.N; ++n) {
     const double* crow = J.c + (long long)(J.first + n) * J.K;
@@ -94,7 +101,16 @@ action_chain_kernel(const ActionJob* __restrict__ jobs, double theta) {
       tau = fma(cn[k], J.trace_mean[1 + k], tau);
       nu = fma(fabs(cn[k]), J.shifted_norm[1 + k], nu);
     }
+    // bounded work: a non-finite bound or more than ACTION_MAX_SUBSTEPS sub-steps
+    // ends the job with an error status instead of an arbitrarily long loop
+    if (!(nu <= theta * ACTION_MAX_SUBSTEPS)) {
+      if (threadIdx.x == 0) jobs[blockIdx.x].status = isfinite(nu) ? MG_EUNSUPPORTED : MG_ENONFINITE;
+      return;
+    }
     const int s = nu > theta ? (int)ceil(nu / theta) : 1;
+    max_sub = max(max_sub, s);
+    min_sub = min(min_sub, s);
+    max_nu = fmax(max_nu, nu);
     const double inv_s = 1.0 / s;
     for (int sub = 0; sub < s; ++sub) {
       // term = psi; acc (psi) accumulates terms
@@ -103,6 +119,8 @@ action_chain_kernel(const ActionJob* __restrict__ jobs, double theta) {
       double prev = 1e300;
       for (int j = 1; j <= ACTION_MAX_TERMS; ++j) {
         apply_shifted(J, cn, tau, term, nxt);
+        ++matvecs;
+        max_terms = max(max_terms, j);
         __syncthreads();
         const double f = inv_s / j;
         double tmax = 0.0, amax = 0.0;
@@ -133,14 +151,24 @@ action_chain_kernel(const ActionJob* __restrict__ jobs, double theta) {
     __syncthreads();
   }
   for (int i = threadIdx.x; i < d; i += blockDim.x) reinterpret_cast<double2*>(J.psi)[i] = psi[i];
+  if (threadIdx.x == 0) {
+    ActionJob& R = jobs[blockIdx.x];
+    R.matvecs = matvecs;
+    R.max_sub = max_sub;
+    R.min_sub = J.N > 0 ? min_sub : 0;
+    R.max_terms = max_terms;
+    R.max_nu = max_nu;
+  }
 }
 
-int launch_action_chain(int njobs, const ActionJob* jobs_dev, int dmax, cudaStream_t s) {
+int launch_action_chain(int njobs, ActionJob* jobs_dev, int dmax, cudaStream_t s) {
   if (njobs <= 0) return MG_OK;
   const size_t smem = sizeof(double2) * 3 * dmax;
   if (smem > 48 * 1024)
     MG_CUDA_TRY(cudaFuncSetAttribute(action_chain_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  action_chain_kernel<<<njobs, ACTION_THREADS, smem, s>>>(jobs_dev, ACTION_THETA);
+  // one thread per row up to ACTION_THREADS; small jobs take fewer warps
+  const int threads = std::min(ACTION_THREADS, (dmax + 31) / 32 * 32);
+  action_chain_kernel<<<njobs, threads, smem, s>>>(jobs_dev, ACTION_THETA);
   return check_launch("action_chain_kernel");
 }
 

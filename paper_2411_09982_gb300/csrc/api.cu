@@ -102,6 +102,7 @@ struct mg_plan {
   int* csr_opoff = nullptr;
   double* csr_tmean = nullptr;   // trace means
   double* csr_snorm = nullptr;   // ||H - t I||_1
+  long long csr_nnz = 0;
 };
 
 namespace {
@@ -254,6 +255,18 @@ int lagrange_triangle(int P, std::vector<double>& mrc);
 // ---------------------------------------------------------------------------
 // matrix-product engine: FP64 or split precision, same call pattern
 // ---------------------------------------------------------------------------
+// records one event of the per-launch timing pool on the context's stream
+int timing_mark(mg_ctx* ctx, int* idx) {
+  if (ctx->ev_next >= ctx->ev_pool.size()) {
+    cudaEvent_t e;
+    MG_CUDA_TRY(cudaEventCreate(&e));
+    ctx->ev_pool.push_back(e);
+  }
+  *idx = (int)ctx->ev_next++;
+  MG_CUDA_TRY(cudaEventRecord(ctx->ev_pool[*idx], ctx->stream));
+  return MG_OK;
+}
+
 struct Engine {
   mg_ctx* ctx;
   int d, prec, L;
@@ -326,16 +339,7 @@ struct Engine {
     }
     return MG_OK;
   }
-  int timing_begin(int* idx) {
-    if (ctx->ev_next >= ctx->ev_pool.size()) {
-      cudaEvent_t e;
-      MG_CUDA_TRY(cudaEventCreate(&e));
-      ctx->ev_pool.push_back(e);
-    }
-    *idx = (int)ctx->ev_next++;
-    MG_CUDA_TRY(cudaEventRecord(ctx->ev_pool[*idx], ctx->stream));
-    return MG_OK;
-  }
+  int timing_begin(int* idx) { return timing_mark(ctx, idx); }
 };
 
 long long mat_doubles(int d) { return 2LL * d * d; }
@@ -551,7 +555,10 @@ int ensure_csr(mg_plan* p) {
     set_last_message("action-based state path supports at most 255 control operators (plan has %d)", p->Kx);
     return MG_EUNSUPPORTED;
   }
-  if (p->d > 4096 / 1) { return MG_EUNSUPPORTED; }
+  if (48LL * p->d > 225LL * 1024) {   // three complex FP64 vectors of length d in shared memory
+    set_last_message("action-based state path supports d <= %d (plan has d = %d)", 225 * 1024 / 48, p->d);
+    return MG_EUNSUPPORTED;
+  }
   const int d = p->d, nops = 1 + p->Kx;
   const size_t dd = (size_t)d * d;
   std::vector<double> dense(2 * dd);
@@ -594,6 +601,7 @@ int ensure_csr(mg_plan* p) {
   MG_TRY(up(reinterpret_cast<void**>(&p->csr_opoff), opoff.data(), sizeof(int) * opoff.size()));
   MG_TRY(up(reinterpret_cast<void**>(&p->csr_tmean), tmean.data(), sizeof(double) * tmean.size()));
   MG_TRY(up(reinterpret_cast<void**>(&p->csr_snorm), snorm.data(), sizeof(double) * snorm.size()));
+  p->csr_nnz = (long long)col.size();
   p->csr_ok = true;
   return MG_OK;
 }
@@ -614,6 +622,27 @@ ActionJob action_job(mg_plan* p, double* psi) {
   j.shifted_norm = p->csr_snorm;
   j.psi = psi;
   return j;
+}
+// Uploads the job records to `jbuf` (device), launches the action kernel on the
+// context's stream, reads the records back and waits.  With per-launch timing
+// on, the launch is timed and its work (8 flops per stored nonzero of every
+// operator per operator application) is added to the context's counters.
+int run_action(mg_ctx* ctx, std::vector<ActionJob>& jobs, const std::vector<long long>& nnz, void* jbuf, int dmax) {
+  ActionJob* dev = reinterpret_cast<ActionJob*>(jbuf);
+  MG_CUDA_TRY(cudaMemcpyAsync(dev, jobs.data(), sizeof(ActionJob) * jobs.size(), cudaMemcpyHostToDevice, ctx->stream));
+  int e0 = -1, e1 = -1;
+  if (ctx->timing) MG_TRY(timing_mark(ctx, &e0));
+  MG_TRY(launch_action_chain((int)jobs.size(), dev, dmax, ctx->stream));
+  if (ctx->timing) {
+    MG_TRY(timing_mark(ctx, &e1));
+    ctx->ev_pending.emplace_back(e0, e1);
+    ctx->t_launches += 1;
+  }
+  MG_CUDA_TRY(cudaMemcpyAsync(jobs.data(), dev, sizeof(ActionJob) * jobs.size(), cudaMemcpyDeviceToHost, ctx->stream));
+  MG_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  if (ctx->timing)
+    for (size_t q = 0; q < jobs.size(); ++q) ctx->t_flops += 8.0 * (double)nnz[q] * (double)jobs[q].matvecs;
+  return MG_OK;
 }
 }  // namespace
 
@@ -1117,12 +1146,16 @@ int mg_evolve(mg_plan* p, int output, const double* in, double* out, int reorth_
   if (output == MG_OUT_STATE && (p->flags & MG_FLAG_STATE_ACTION)) {
     // action-based: exp(-i Hbar_n) applied to the state by sparse Taylor steps
     MG_TRY(ensure_csr(p));
-    ActionJob job = action_job(p, ps.psi);
+    std::vector<ActionJob> jv{action_job(p, ps.psi)};
     double* jbuf;
     MG_TRY(ws(ctx, WS_VEC, sizeof(ActionJob) / sizeof(double) + 1, &jbuf));
-    MG_CUDA_TRY(cudaMemcpyAsync(jbuf, &job, sizeof(ActionJob), cudaMemcpyHostToDevice, s));
-    MG_TRY(launch_action_chain(1, reinterpret_cast<ActionJob*>(jbuf), d, s));
-    MG_CUDA_TRY(cudaStreamSynchronize(s));   // the job record lives on the host stack
+    MG_TRY(run_action(ctx, jv, {p->csr_nnz}, jbuf, d));
+    const ActionJob& job = jv[0];
+    if (job.status != MG_OK) {
+      set_last_message("action-based state path stopped: %s", job.status == MG_ENONFINITE
+                       ? "non-finite norm bound" : "norm bound needs more than 16384 sub-steps per interval");
+      return job.status;
+    }
     MG_TRY(finish_prop(ctx, eng, ps, out, flags, rep));
     if (rep) {
       MG_CUDA_TRY(cudaEventRecord(ctx->ev1, s));
@@ -1131,6 +1164,12 @@ int mg_evolve(mg_plan* p, int output, const double* in, double* out, int reorth_
       cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
       rep->ms_total = ms;
       rep->intervals = p->N;
+      rep->taylor_degree = job.max_terms;
+      rep->max_squarings = job.max_sub;     // sub-steps s_n of the scaled series
+      rep->min_squarings = job.min_sub;
+      rep->max_norm1 = job.max_nu;
+      rep->sparse_matvecs = job.matvecs;
+      rep->sparse_nnz = p->csr_nnz;
     }
     MG_CUDA_TRY(cudaStreamSynchronize(s));
     return MG_OK;
@@ -1493,24 +1532,26 @@ int mg_evolve_batch(mg_ctx* ctx, int n, mg_plan* const* plans, const int* output
       MG_TRY(ws(ctx, WS_ACC, total, &psis));
       MG_TRY(ws(ctx, WS_VEC, (sizeof(ActionJob) * aj.size()) / sizeof(double) + 1, &jb));
       size_t off = 0;
+      std::vector<long long> nnz(aidx.size());
       for (size_t q = 0; q < aidx.size(); ++q) {
         mg_plan* p = plans[aidx[q]];
         if (!in || !in[aidx[q]]) return MG_EINVAL;
         MG_TRY(ensure_csr(p));
         aj[q] = action_job(p, psis + off);
+        nnz[q] = p->csr_nnz;
         MG_CUDA_TRY(cudaMemcpyAsync(psis + off, in[aidx[q]], sizeof(double) * 2 * p->d, h2d, ctx->stream));
         off += 2 * (size_t)p->d;
       }
-      MG_CUDA_TRY(cudaMemcpyAsync(jb, aj.data(), sizeof(ActionJob) * aj.size(), cudaMemcpyHostToDevice, ctx->stream));
-      MG_TRY(launch_action_chain((int)aj.size(), reinterpret_cast<ActionJob*>(jb), dmax, ctx->stream));
+      MG_TRY(run_action(ctx, aj, nnz, jb, dmax));
       off = 0;
       for (size_t q = 0; q < aidx.size(); ++q) {
         mg_plan* p = plans[aidx[q]];
         MG_CUDA_TRY(cudaMemcpyAsync(out[aidx[q]], psis + off, sizeof(double) * 2 * p->d, d2h, ctx->stream));
         off += 2 * (size_t)p->d;
-        if (job_status) job_status[aidx[q]] = MG_OK;
       }
       MG_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+      for (size_t q = 0; q < aidx.size(); ++q)
+        if (job_status) job_status[aidx[q]] = aj[q].status;
     }
     all.swap(rest);
     if (all.empty()) return MG_OK;

@@ -158,9 +158,13 @@ struct ActionJob {
   const double* trace_mean;
   const double* shifted_norm;
   double* psi;
-  int status;
+  int status;   // MG_OK, or set by the kernel when the job stopped early
+  // written by the kernel: operator applications, sub-step counts, series length, norm bound
+  long long matvecs;
+  int max_sub, min_sub, max_terms;
+  double max_nu;
 };
-int launch_action_chain(int njobs, const ActionJob* jobs_dev, int dmax, cudaStream_t s);
+int launch_action_chain(int njobs, ActionJob* jobs_dev, int dmax, cudaStream_t s);
 
 // dst (dp x dp, zero padded) <- src (d x d), for `count` stacked matrices
 int launch_pad_copy(int count, int d, int dp, const double* src, double* dst, cudaStream_t s);

@@ -50,6 +50,8 @@ class mg_report(ctypes.Structure):
         ("unitarity_defect", ctypes.c_double),
         ("ms_total", ctypes.c_double),
         ("matrix_products", ctypes.c_int64),
+        ("sparse_matvecs", ctypes.c_int64),
+        ("sparse_nnz", ctypes.c_int64),
     ]
 
     def as_dict(self):

@@ -451,3 +451,12 @@ def test_action_state_path_in_batch(ctx):
     finally:
         for p in plans:
             p.close()
+
+
+def test_action_state_path_rejects_unbounded_work(ctx):
+    # a norm bound that would need more than 16384 sub-steps in one interval ends the
+    # job with MG_EUNSUPPORTED from inside the kernel instead of running on
+    wl = W.config(0, N=2)
+    wl.H0 = wl.H0 * 100.0
+    with pytest.raises(RuntimeError, match="sub-steps"):
+        M.evolve_workload(ctx, wl, M.MG_PREC_FP64, flags=M.MG_FLAG_STATE_ACTION)
