@@ -75,17 +75,20 @@ extern "C" {
 #define MG_FLAG_HOST_PTRS        1  /* the call's data pointers are host memory */
 #define MG_FLAG_CHECK_HERMITIAN  2  /* plan: reject operators with |H - H^dag| > 1e-12 |H| */
 #define MG_FLAG_NO_TRACE_SHIFT   4  /* plan: exponentiate Hbar_n itself, not Hbar_n - tr/d I */
-/* plan: state outputs apply exp(-i Hbar_n) to the state by a scaled Taylor series
- * of sparse (CSR) matrix-vector products in FP64 instead of forming U_n
- * (Eq. magnus-first-order-term and the ordered product of the interval
- * propagators, evaluated by their action on psi); exact up to the unit
- * roundoff, cheaper whenever the operators are sparse.  One thread block per
- * job, so it suits batches of jobs or large sparse d.  Limits: d <= 4800,
- * at most 255 operators (after the commutators of order 2), and at most
- * 16384 sub-steps of norm 2 per interval (||Hbar_n - tau_n I||_1 bound <= 32768);
- * beyond the last the call (or the job's batch status) returns MG_EUNSUPPORTED,
- * a non-finite bound MG_ENONFINITE.  The CSR copy of the operators is built on
- * the host at the first such call.  Propagator outputs are unaffected. */
+/* plan: state outputs apply exp(-i Hbar_n) to the state instead of forming
+ * U_n (Eq. magnus-first-order-term and the ordered product of the interval
+ * propagators, evaluated by their action on psi): a Chebyshev expansion
+ * (Tal-Ezer and Kosloff 1984) over the Gershgorin interval of Hbar_n, with
+ * sparse (CSR) matrix-vector products in FP64; exact up to the unit roundoff,
+ * cheaper whenever the operators are sparse.  One thread block per job, so it
+ * suits batches of jobs or large sparse d.  Limits: d <= 4800, at most 255
+ * operators (after the commutators of order 2), and a Gershgorin half-width of
+ * Hbar_n of at most 327680 (16384 sub-steps of 20); beyond it the call (or the
+ * job's batch status) returns MG_EUNSUPPORTED, a non-finite bound
+ * MG_ENONFINITE.  The CSR copy of the operators is built on the host at the
+ * first such call.  Propagator outputs are unaffected.  In the report,
+ * taylor_degree is the largest Chebyshev degree, max/min_squarings the sub-step
+ * counts and max_norm1 the largest half-width. */
 #define MG_FLAG_STATE_ACTION     8
 
 typedef struct mg_ctx mg_ctx;

@@ -1,174 +1,307 @@
 // Action-based state propagation with sparse operators.
 //
 // For state outputs the product U_{N-1} ... U_0 psi0 never needs the matrices
-// U_n = exp(-i Hbar_n): each interval applies the exponential to the state,
+// U_n = exp(-i Hbar_n), Hbar_n = dt H0 + sum_k c_{k,n} H_k (Eq.
+// magnus-first-order-term): each interval applies the exponential to the state.
 //
-//   psi <- e^{-i tau_n} exp(-i (Hbar_n - tau_n I)) psi,
-//   (Hbar_n - tau_n I) v = dt (H0 - t0 I) v + sum_k c_{k,n} (H_k - t_k I) v,
+// Spectral interval.  Gershgorin's discs of Hbar_n put its (real) spectrum in
+// [c_n - rho_n, c_n + rho_n].  With X = (Hbar_n - c_n I) / rho_n, whose
+// spectrum lies in [-1, 1], and s_n sub-steps of z = rho_n / s_n <= 20,
 //
-// (t0, t_k the operators' trace means, tau_n = dt t0 + sum_k c_{k,n} t_k), with
-// a scaled Taylor series: s_n = ceil(nu_n / 2) sub-steps of at most 40 terms,
-//   v <- sum_{j<=m} (-i A / s_n)^j v / j!,
-// stopped early once two consecutive terms fall below the FP64 unit roundoff
-// relative to the partial sum.  The operators are held in CSR (they are
-// sparse in the circuit-QED models: b + b^dag, n, a^dag a), so an interval
-// costs about (terms) x (nonzeros) complex multiply-adds instead of the d^3
-// products that forming U_n takes.  s_n comes from an FP64 upper bound of
-// ||Hbar_n - tau_n I||_1 built from the operators' shifted 1-norms.
+//   exp(-i Hbar_n) = e^{-i c_n} [ J_0(z) I + 2 sum_{k>=1} (-i)^k J_k(z) T_k(X) ]^{s_n}
 //
-// One CTA carries one job's state through a range of intervals (grid = jobs),
-// vectors in shared memory, one thread per row.
+// (the Jacobi-Anger expansion of e^{-i z x} in Chebyshev polynomials: the
+// Chebyshev propagator of Tal-Ezer and Kosloff, J. Chem. Phys. 81, 3967
+// (1984)), with T_k(X) v from the three-term recurrence
+// T_{k+1}(X) v = 2 X T_k(X) v - T_{k-1}(X) v.  The phase e^{-i c_n} is applied
+// exactly in FP64.  The Bessel values J_k(z) come from Miller's downward
+// recurrence J_{k-1} = (2k/z) J_k - J_{k+1}, normalised by
+// J_0 + 2 sum_{k>=1} J_{2k} = 1; the series stops at the first degree k_t past
+// which the bound |J_k(z)| <= (z/2)^k / k! leaves a tail below 2^-56.
+//
+// Sparse operators.  H0 and the H_k are held in one CSR pattern (the union of
+// their nonzeros plus the diagonal) with one value array per operator, so an
+// interval first forms X's values (sum over operators, shift, scale) and then
+// runs plain CSR products.  In the circuit-QED models (b + b^dag, n, a^dag a)
+// an interval costs about (degree) x (nonzeros) complex multiply-adds instead
+// of the d^3 products that forming U_n takes.
+//
+// Two kernels: a bounds kernel (one warp per interval, all intervals of all
+// jobs in parallel) computes c_n, rho_n, s_n, k_t and the J_k(z); the chain
+// kernel (one CTA per job) carries the state through the intervals with one
+// thread per row and one barrier per operator application, the vectors and,
+// where they fit, the interval matrix and its pattern in shared memory.
 #include "common.cuh"
+
+#include <algorithm>
 
 namespace mg {
 
 constexpr int ACTION_THREADS = 256;
-// Sub-step norm theta = 2: the rounding of one sub-step grows like e^theta
-// (the sum of the terms' magnitudes) while the sub-step count falls like
-// 1/theta; theta = 2 keeps the summed rounding of a long run within a few
-// times that of theta = 1 at 65% of its matvecs.  2^40/40! is far below the
-// FP64 unit roundoff, so 40 terms always suffice.
-constexpr int ACTION_MAX_TERMS = 40;
-constexpr double ACTION_THETA = 2.0;
 constexpr int ACTION_MAX_OPS = 256;
-constexpr int ACTION_MAX_SUBSTEPS = 1 << 14;
+constexpr double ACTION_ZMAX = 20.0;          // largest z = rho / s of one sub-step
+constexpr int ACTION_MAX_SUBSTEPS = 1 << 14;  // per interval
+// z <= 20 needs degrees below 64: 2 (10^{k+1} / (k+1)!) <= 2^-56 from k = 53
+constexpr int ACTION_KMAX = 64;
+static_assert(5 + ACTION_KMAX + 1 <= ACTION_REC, "interval record too small");
 
-__device__ __forceinline__ double2 cmul_i(double2 a, double s) {  // (-i s) a
-  return make_double2(s * a.y, -s * a.x);
+__device__ __forceinline__ double2 cfma(double2 a, double2 b, double2 acc) {   // acc + a b
+  acc.x = fma(a.x, b.x, acc.x);
+  acc.x = fma(-a.y, b.y, acc.x);
+  acc.y = fma(a.x, b.y, acc.y);
+  acc.y = fma(a.y, b.x, acc.y);
+  return acc;
 }
 
-// y = (Hbar - tau I) x for one interval (x, y in shared memory)
-__device__ void apply_shifted(const ActionJob& J, const double* cn, double tau, const double2* x, double2* y) {
-  for (int i = threadIdx.x; i < J.d; i += blockDim.x) {
-    double re = 0.0, im = 0.0;
-    for (int op = 0; op <= J.K; ++op) {
-      const double coef = op == 0 ? J.dt : cn[op - 1];
-      if (coef == 0.0) continue;
-      const int* rp = J.rowptr + op * (J.d + 1);
-      const int base = J.opoff[op];
-      double sr = 0.0, si = 0.0;
-      for (int e = rp[i]; e < rp[i + 1]; ++e) {
-        const int j = J.col[base + e];
-        const double2 h = reinterpret_cast<const double2*>(J.val)[base + e];
-        const double2 v = x[j];
-        sr = fma(h.x, v.x, sr);
-        sr = fma(-h.y, v.y, sr);
-        si = fma(h.x, v.y, si);
-        si = fma(h.y, v.x, si);
-      }
-      re = fma(coef, sr, re);
-      im = fma(coef, si, im);
-    }
-    re -= tau * x[i].x;
-    im -= tau * x[i].y;
-    y[i] = make_double2(re, im);
+// J_k(z), k = 0..k_t, into J; returns k_t (see the file comment).  0 <= z <= 20.
+__device__ int bessel_series(double z, double* J) {
+  if (!(z > 1e-100)) {   // J_0 = 1 and J_1 ~ z/2 below any rounding of the state
+    J[0] = 1.0;
+    return 0;
   }
+  // degree: smallest k >= z - 2 with 2 (z/2)^{k+1} / (k+1)! <= 2^-56; past it
+  // the bound's ratio (z/2)/(k+2) is at most 1/2, so the tail is at most twice that
+  const double h = 0.5 * z;
+  double b = 1.0;   // (z/2)^k / k!
+  int kt = ACTION_KMAX;
+  for (int k = 0; k < ACTION_KMAX; ++k) {
+    const double next = b * h / (k + 1);
+    if (k + 2 >= z && 2.0 * next <= 0x1p-56) {
+      kt = k;
+      break;
+    }
+    b = next;
+  }
+  // Miller: downward from m0 well past k_t, rescaling to stay in range
+  const int m0 = kt + 32;
+  const double two_over_z = 2.0 / z;
+  double jp1 = 0.0, j = 0x1p-200, norm = 0.0;
+  for (int k = m0; k >= 1; --k) {
+    if (k <= kt) J[k] = j;
+    if ((k & 1) == 0) norm += 2.0 * j;
+    const double jm1 = fma(k * two_over_z, j, -jp1);
+    jp1 = j;
+    j = jm1;
+    if (fabs(j) > 0x1p+600) {   // rescale everything held so far
+      j *= 0x1p-600;
+      jp1 *= 0x1p-600;
+      norm *= 0x1p-600;
+      for (int q = k; q <= kt; ++q) J[q] *= 0x1p-600;
+    }
+  }
+  norm += j;   // J_0
+  J[0] = j;
+  const double inv = 1.0 / norm;
+  for (int q = 0; q <= kt; ++q) J[q] *= inv;
+  return kt;
 }
 
-__device__ double block_max(double v, double* red) {
-  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  __syncthreads();
-  if (lane == 0) red[w] = v;
-  __syncthreads();
-  double m = 0.0;
-  for (int k = 0; k < (int)(blockDim.x >> 5); ++k) m = fmax(m, red[k]);
-  return m;
+// One warp per (job, interval): Gershgorin bounds of Hbar_n, the sub-step
+// count and the Chebyshev coefficients.  Record layout (ACTION_REC doubles):
+// [c_n, 1/rho_n, s_n, k_t, rho_n, J_0 .. J_{k_t}]; s_n = -1 marks a
+// non-finite bound, -2 one that needs more than ACTION_MAX_SUBSTEPS sub-steps.
+__global__ void __launch_bounds__(256) action_bounds_kernel(const ActionJob* __restrict__ jobs) {
+  const ActionJob& J = jobs[blockIdx.y];
+  const int lane = threadIdx.x & 31;
+  const int n = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (n >= J.N) return;   // whole warps leave together
+  const double* crow = J.c + (long long)(J.first + n) * J.K;
+  double lo = 1e300, hi = -1e300;
+  bool bad = false;
+  for (int i = lane; i < J.d; i += 32) {
+    double dv = 0.0, r = 0.0;
+    const int di = J.diag[i];
+    for (int e = J.rowptr[i]; e < J.rowptr[i + 1]; ++e) {
+      double ar = 0.0, ai = 0.0;
+      for (int op = 0; op <= J.K; ++op) {
+        const double coef = op == 0 ? J.dt : crow[op - 1];
+        const double2 v = reinterpret_cast<const double2*>(J.val)[(long long)op * J.nnz + e];
+        ar = fma(coef, v.x, ar);
+        ai = fma(coef, v.y, ai);
+      }
+      if (e == di) {
+        dv = ar;
+        r += fabs(ai);   // zero for Hermitian input; kept so the disc stays an upper bound
+      } else {
+        r += hypot(ar, ai);
+      }
+    }
+    if (!isfinite(dv) || !isfinite(r)) bad = true;
+    lo = fmin(lo, dv - r);
+    hi = fmax(hi, dv + r);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+    hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+  }
+  bad = __any_sync(0xffffffffu, bad);
+  if (lane != 0) return;
+  double* rec = J.cheb + (long long)n * ACTION_REC;
+  const double center = 0.5 * (lo + hi);
+  // half-width, widened by 2^-40 of the largest endpoint to cover the rounding of the disc sums
+  const double rho = 0.5 * (hi - lo) + 0x1p-40 * fmax(fabs(lo), fabs(hi));
+  if (bad || !isfinite(center) || !isfinite(rho)) {
+    rec[2] = -1.0;
+    return;
+  }
+  if (rho > ACTION_ZMAX * ACTION_MAX_SUBSTEPS) {
+    rec[2] = -2.0;
+    return;
+  }
+  const int s = rho > ACTION_ZMAX ? (int)ceil(rho / ACTION_ZMAX) : 1;
+  const double z = rho / s;
+  const int kt = bessel_series(z, rec + 5);
+  rec[0] = center;
+  rec[1] = rho > 0.0 ? 1.0 / rho : 0.0;
+  rec[2] = (double)s;
+  rec[3] = (double)kt;
+  rec[4] = rho;
+}
+
+// acc + 2 (-i)^k J_k v, with twoJ = 2 J_k
+__device__ __forceinline__ double2 add_term(double2 acc, double2 v, double twoJ, int k) {
+  switch (k & 3) {
+    case 0: acc.x = fma(twoJ, v.x, acc.x); acc.y = fma(twoJ, v.y, acc.y); break;
+    case 1: acc.x = fma(twoJ, v.y, acc.x); acc.y = fma(-twoJ, v.x, acc.y); break;
+    case 2: acc.x = fma(-twoJ, v.x, acc.x); acc.y = fma(-twoJ, v.y, acc.y); break;
+    default: acc.x = fma(-twoJ, v.y, acc.x); acc.y = fma(twoJ, v.x, acc.y); break;
+  }
+  return acc;
 }
 
 __global__ void __launch_bounds__(ACTION_THREADS)
-action_chain_kernel(ActionJob* __restrict__ jobs, double theta) {
-  extern __shared__ double2 vec[];
-  __shared__ double red[ACTION_THREADS / 32];
+action_chain_kernel(ActionJob* __restrict__ jobs, int dmax, int nnz_cap) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double cn[ACTION_MAX_OPS];
-  const ActionJob J = jobs[blockIdx.x];
+  __shared__ double Jk[ACTION_KMAX + 1];
+  ActionJob& R = jobs[blockIdx.x];
+  const ActionJob J = R;
   const int d = J.d;
-  double2* psi = vec;
-  double2* term = vec + d;
-  double2* nxt = vec + 2 * d;
-  for (int i = threadIdx.x; i < d; i += blockDim.x) psi[i] = reinterpret_cast<double2*>(J.psi)[i];
+  double2* acc = reinterpret_cast<double2*>(smem_raw);   // the state
+  double2* vx = acc + dmax;
+  double2* vy = acc + 2 * dmax;
+  const bool in_smem = J.nnz <= nnz_cap;
+  double2* A = in_smem ? acc + 3 * dmax : reinterpret_cast<double2*>(J.abuf);
+  int* col_s = reinterpret_cast<int*>(acc + 3 * dmax + nnz_cap);
+  int* rp_s = col_s + nnz_cap;
+  const int* col = in_smem ? col_s : J.col;
+  const int* rp = in_smem ? rp_s : J.rowptr;
+  if (in_smem) {
+    for (int e = threadIdx.x; e < J.nnz; e += blockDim.x) col_s[e] = J.col[e];
+    for (int i = threadIdx.x; i <= d; i += blockDim.x) rp_s[i] = J.rowptr[i];
+  }
+  for (int i = threadIdx.x; i < d; i += blockDim.x) acc[i] = reinterpret_cast<const double2*>(J.psi)[i];
   long long matvecs = 0;
-  int max_sub = 0, min_sub = 1 << 30, max_terms = 0;
-  double max_nu = 0.0;
+  int max_sub = 0, min_sub = 1 << 30, max_deg = 0;
+  double max_rho = 0.0;
   __syncthreads();
   for (int n = 0; n < J.N; ++n) {
-    const double* crow = J.c + (long long)(J.first + n) * J.K;
-    for (int k = threadIdx.x; k < J.K; k += blockDim.x) cn[k] = crow[k];
-    __syncthreads();
-    double tau = J.dt * J.trace_mean[0];
-    double nu = J.dt * J.shifted_norm[0];
-    for (int k = 0; k < J.K; ++k) {
-      tau = fma(cn[k], J.trace_mean[1 + k], tau);
-      nu = fma(fabs(cn[k]), J.shifted_norm[1 + k], nu);
-    }
-    // bounded work: a non-finite bound or more than ACTION_MAX_SUBSTEPS sub-steps
-    // ends the job with an error status instead of an arbitrarily long loop
-    if (!(nu <= theta * ACTION_MAX_SUBSTEPS)) {
-      if (threadIdx.x == 0) jobs[blockIdx.x].status = isfinite(nu) ? MG_EUNSUPPORTED : MG_ENONFINITE;
+    const double* rec = J.cheb + (long long)n * ACTION_REC;
+    const int s = (int)rec[2];
+    if (s <= 0) {   // uniform: every thread reads the same record
+      if (threadIdx.x == 0) R.status = s == -1 ? MG_ENONFINITE : MG_EUNSUPPORTED;
       return;
     }
-    const int s = nu > theta ? (int)ceil(nu / theta) : 1;
+    const double center = rec[0], inv_rho = rec[1];
+    const int kt = (int)rec[3];
     max_sub = max(max_sub, s);
     min_sub = min(min_sub, s);
-    max_nu = fmax(max_nu, nu);
-    const double inv_s = 1.0 / s;
-    for (int sub = 0; sub < s; ++sub) {
-      // term = psi; acc (psi) accumulates terms
-      for (int i = threadIdx.x; i < d; i += blockDim.x) term[i] = psi[i];
-      __syncthreads();
-      double prev = 1e300;
-      for (int j = 1; j <= ACTION_MAX_TERMS; ++j) {
-        apply_shifted(J, cn, tau, term, nxt);
-        ++matvecs;
-        max_terms = max(max_terms, j);
-        __syncthreads();
-        const double f = inv_s / j;
-        double tmax = 0.0, amax = 0.0;
-        for (int i = threadIdx.x; i < d; i += blockDim.x) {
-          const double2 t = cmul_i(nxt[i], f);
-          term[i] = t;
-          double2 a = psi[i];
-          a.x += t.x;
-          a.y += t.y;
-          psi[i] = a;
-          tmax = fmax(tmax, fmax(fabs(t.x), fabs(t.y)));
-          amax = fmax(amax, fmax(fabs(a.x), fabs(a.y)));
+    max_deg = max(max_deg, kt);
+    max_rho = fmax(max_rho, rec[4]);
+    const double* crow = J.c + (long long)(J.first + n) * J.K;
+    for (int k = threadIdx.x; k < J.K; k += blockDim.x) cn[k] = crow[k];
+    for (int k = threadIdx.x; k <= kt; k += blockDim.x) Jk[k] = rec[5 + k];
+    __syncthreads();
+    // X = (Hbar_n - c_n I) / rho_n on the union pattern, own rows
+    for (int i = threadIdx.x; i < d; i += blockDim.x) {
+      const int di = J.diag[i];
+      for (int e = rp[i]; e < rp[i + 1]; ++e) {
+        double ar = 0.0, ai = 0.0;
+        for (int op = 0; op <= J.K; ++op) {
+          const double coef = op == 0 ? J.dt : cn[op - 1];
+          const double2 v = reinterpret_cast<const double2*>(J.val)[(long long)op * J.nnz + e];
+          ar = fma(coef, v.x, ar);
+          ai = fma(coef, v.y, ai);
         }
-        tmax = block_max(tmax, red);
-        amax = block_max(amax, red);
-        if (tmax + prev <= 1.1102230246251565e-16 * amax) break;   // two negligible terms in a row
-        prev = tmax;
+        if (e == di) ar -= center;
+        A[e] = make_double2(ar * inv_rho, ai * inv_rho);
+      }
+    }
+    __syncthreads();
+    for (int sub = 0; sub < s; ++sub) {
+      // T_0 v = v (in vx); acc = J_0 v
+      for (int i = threadIdx.x; i < d; i += blockDim.x) {
+        const double2 v = acc[i];
+        vx[i] = v;
+        acc[i] = make_double2(Jk[0] * v.x, Jk[0] * v.y);
       }
       __syncthreads();
+      for (int k = 1; k <= kt; ++k) {
+        // k odd: vy <- 2 X vx - vy (k = 1: X vx); k even: vx <- 2 X vy - vx
+        const double2* cur = (k & 1) ? vx : vy;
+        double2* old = (k & 1) ? vy : vx;
+        const double two = k == 1 ? 1.0 : 2.0;
+        const double twoJ = 2.0 * Jk[k];
+        for (int i = threadIdx.x; i < d; i += blockDim.x) {
+          double2 y0 = make_double2(0.0, 0.0), y1 = make_double2(0.0, 0.0);
+          const int e1 = rp[i + 1];
+          int e = rp[i];
+          for (; e + 1 < e1; e += 2) {   // two independent accumulators
+            y0 = cfma(A[e], cur[col[e]], y0);
+            y1 = cfma(A[e + 1], cur[col[e + 1]], y1);
+          }
+          if (e < e1) y0 = cfma(A[e], cur[col[e]], y0);
+          double2 t = make_double2(two * (y0.x + y1.x), two * (y0.y + y1.y));
+          if (k > 1) {
+            const double2 o = old[i];
+            t.x -= o.x;
+            t.y -= o.y;
+          }
+          old[i] = t;
+          acc[i] = add_term(acc[i], t, twoJ, k);
+        }
+        __syncthreads();
+      }
+      matvecs += kt;
     }
-    // exact phase of the trace shift
+    // exact phase of the spectral centre
     double sn, cs;
-    sincos(tau, &sn, &cs);
+    sincos(center, &sn, &cs);
     for (int i = threadIdx.x; i < d; i += blockDim.x) {
-      const double2 v = psi[i];
-      psi[i] = make_double2(cs * v.x + sn * v.y, cs * v.y - sn * v.x);
+      const double2 v = acc[i];
+      acc[i] = make_double2(cs * v.x + sn * v.y, cs * v.y - sn * v.x);
     }
     __syncthreads();
   }
-  for (int i = threadIdx.x; i < d; i += blockDim.x) reinterpret_cast<double2*>(J.psi)[i] = psi[i];
+  for (int i = threadIdx.x; i < d; i += blockDim.x) reinterpret_cast<double2*>(J.psi)[i] = acc[i];
   if (threadIdx.x == 0) {
-    ActionJob& R = jobs[blockIdx.x];
     R.matvecs = matvecs;
     R.max_sub = max_sub;
     R.min_sub = J.N > 0 ? min_sub : 0;
-    R.max_terms = max_terms;
-    R.max_nu = max_nu;
+    R.max_terms = max_deg;
+    R.max_nu = max_rho;
   }
 }
 
-int launch_action_chain(int njobs, ActionJob* jobs_dev, int dmax, cudaStream_t s) {
+size_t action_smem_bytes(int dmax, int nnz_cap) {
+  size_t b = sizeof(double2) * 3 * (size_t)dmax;
+  if (nnz_cap > 0) b += (sizeof(double2) + sizeof(int)) * (size_t)nnz_cap + sizeof(int) * ((size_t)dmax + 1);
+  return b;
+}
+
+int launch_action_chain(int njobs, ActionJob* jobs_dev, int dmax, int nmax, int nnz_cap, cudaStream_t s) {
   if (njobs <= 0) return MG_OK;
-  const size_t smem = sizeof(double2) * 3 * dmax;
+  if (nmax > 0) {
+    dim3 grid((nmax + 7) / 8, njobs);
+    action_bounds_kernel<<<grid, 256, 0, s>>>(jobs_dev);
+    MG_TRY(check_launch("action_bounds_kernel"));
+  }
+  const size_t smem = action_smem_bytes(dmax, nnz_cap);
   if (smem > 48 * 1024)
     MG_CUDA_TRY(cudaFuncSetAttribute(action_chain_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   // one thread per row up to ACTION_THREADS; small jobs take fewer warps
   const int threads = std::min(ACTION_THREADS, (dmax + 31) / 32 * 32);
-  action_chain_kernel<<<njobs, threads, smem, s>>>(jobs_dev, ACTION_THETA);
+  action_chain_kernel<<<njobs, threads, smem, s>>>(jobs_dev, dmax, nnz_cap);
   return check_launch("action_chain_kernel");
 }
 

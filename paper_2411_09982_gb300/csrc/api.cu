@@ -96,12 +96,10 @@ struct mg_plan {
   double* mrc = nullptr;    // second-order quadrature matrix on the device
   // CSR copies of H0 and the Kx operators for the action-based state path
   bool csr_ok = false;
-  int* csr_rowptr = nullptr;
+  int* csr_rowptr = nullptr;     // union pattern of H0, H_1..H_K and the diagonal
   int* csr_col = nullptr;
-  double* csr_val = nullptr;
-  int* csr_opoff = nullptr;
-  double* csr_tmean = nullptr;   // trace means
-  double* csr_snorm = nullptr;   // ||H - t I||_1
+  int* csr_diag = nullptr;       // position of each row's diagonal entry
+  double* csr_val = nullptr;     // (1 + K) x nnz complex, operator-major
   long long csr_nnz = 0;
 };
 
@@ -113,6 +111,7 @@ enum Slot {
   WS_ABUF, WS_BBUF0, WS_BBUF1,
   WS_TAU, WS_NORM, WS_ACC, WS_ACC2, WS_NS_G, WS_NS_H, WS_VEC,
   WS_TREE0, WS_TREE1, WS_UBUF, WS_NS_Z, WS_OUT,
+  WS_ACT_REC, WS_ACT_MAT,   // action path: interval records, interval matrices off chip
   WS_COUNT
 };
 
@@ -555,39 +554,43 @@ int ensure_csr(mg_plan* p) {
     set_last_message("action-based state path supports at most 255 control operators (plan has %d)", p->Kx);
     return MG_EUNSUPPORTED;
   }
-  if (48LL * p->d > 225LL * 1024) {   // three complex FP64 vectors of length d in shared memory
+  if (action_smem_bytes(p->d, 0) > 225 * 1024) {   // three complex FP64 vectors in shared memory
     set_last_message("action-based state path supports d <= %d (plan has d = %d)", 225 * 1024 / 48, p->d);
     return MG_EUNSUPPORTED;
   }
   const int d = p->d, nops = 1 + p->Kx;
   const size_t dd = (size_t)d * d;
-  std::vector<double> dense(2 * dd);
-  std::vector<int> rowptr((size_t)nops * (d + 1)), col, opoff(nops);
-  std::vector<double> val, tmean(nops), snorm(nops);
+  std::vector<double> dense((size_t)nops * 2 * dd);
   for (int op = 0; op < nops; ++op) {
     const double* src = op == 0 ? p->H0 : p->Hk + (size_t)(op - 1) * 2 * dd;
-    MG_CUDA_TRY(cudaMemcpy(dense.data(), src, sizeof(double) * 2 * dd, cudaMemcpyDeviceToHost));
-    opoff[op] = (int)col.size();
-    double tr = 0.0;
-    for (int i = 0; i < d; ++i) tr += dense[2 * ((size_t)i * d + i)];
-    tmean[op] = tr / d;
-    std::vector<double> colsum(d, 0.0);
-    int* rp = rowptr.data() + (size_t)op * (d + 1);
-    rp[0] = 0;
-    for (int i = 0; i < d; ++i) {
-      for (int j = 0; j < d; ++j) {
-        const double re = dense[2 * ((size_t)i * d + j)], im = dense[2 * ((size_t)i * d + j) + 1];
-        colsum[j] += std::hypot(re - (i == j ? tmean[op] : 0.0), im);
-        if (re != 0.0 || im != 0.0) {
-          col.push_back(j);
-          val.push_back(re);
-          val.push_back(im);
-        }
-      }
-      rp[i + 1] = (int)col.size() - opoff[op];
-    }
-    snorm[op] = *std::max_element(colsum.begin(), colsum.end());
+    MG_CUDA_TRY(cudaMemcpy(dense.data() + (size_t)op * 2 * dd, src, sizeof(double) * 2 * dd,
+                           cudaMemcpyDeviceToHost));
   }
+  std::vector<int> rowptr(d + 1), col, diag(d);
+  rowptr[0] = 0;
+  for (int i = 0; i < d; ++i) {
+    for (int j = 0; j < d; ++j) {
+      bool nz = i == j;
+      for (int op = 0; op < nops && !nz; ++op) {
+        const double* v = dense.data() + (size_t)op * 2 * dd + 2 * ((size_t)i * d + j);
+        nz = v[0] != 0.0 || v[1] != 0.0;
+      }
+      if (nz) {
+        if (i == j) diag[i] = (int)col.size();
+        col.push_back(j);
+      }
+    }
+    rowptr[i + 1] = (int)col.size();
+  }
+  const size_t nnz = col.size();
+  std::vector<double> val((size_t)nops * nnz * 2);
+  for (int op = 0; op < nops; ++op)
+    for (int i = 0; i < d; ++i)
+      for (int e = rowptr[i]; e < rowptr[i + 1]; ++e) {
+        const double* v = dense.data() + (size_t)op * 2 * dd + 2 * ((size_t)i * d + col[e]);
+        val[2 * ((size_t)op * nnz + e)] = v[0];
+        val[2 * ((size_t)op * nnz + e) + 1] = v[1];
+      }
   auto up = [&](void** dst, const void* src, size_t bytes) -> int {
     cudaFree(*dst);
     *dst = nullptr;
@@ -597,51 +600,90 @@ int ensure_csr(mg_plan* p) {
   };
   MG_TRY(up(reinterpret_cast<void**>(&p->csr_rowptr), rowptr.data(), sizeof(int) * rowptr.size()));
   MG_TRY(up(reinterpret_cast<void**>(&p->csr_col), col.data(), sizeof(int) * col.size()));
+  MG_TRY(up(reinterpret_cast<void**>(&p->csr_diag), diag.data(), sizeof(int) * diag.size()));
   MG_TRY(up(reinterpret_cast<void**>(&p->csr_val), val.data(), sizeof(double) * val.size()));
-  MG_TRY(up(reinterpret_cast<void**>(&p->csr_opoff), opoff.data(), sizeof(int) * opoff.size()));
-  MG_TRY(up(reinterpret_cast<void**>(&p->csr_tmean), tmean.data(), sizeof(double) * tmean.size()));
-  MG_TRY(up(reinterpret_cast<void**>(&p->csr_snorm), snorm.data(), sizeof(double) * snorm.size()));
-  p->csr_nnz = (long long)col.size();
+  p->csr_nnz = (long long)nnz;
   p->csr_ok = true;
   return MG_OK;
 }
-
 ActionJob action_job(mg_plan* p, double* psi) {
   ActionJob j{};
   j.d = p->d;
   j.K = p->Kx;
   j.N = p->N;
   j.first = 0;
+  j.nnz = (int)p->csr_nnz;
   j.dt = p->dt;
   j.rowptr = p->csr_rowptr;
   j.col = p->csr_col;
+  j.diag = p->csr_diag;
   j.val = p->csr_val;
-  j.opoff = p->csr_opoff;
   j.c = p->c;
-  j.trace_mean = p->csr_tmean;
-  j.shifted_norm = p->csr_snorm;
   j.psi = psi;
   return j;
 }
-// Uploads the job records to `jbuf` (device), launches the action kernel on the
-// context's stream, reads the records back and waits.  With per-launch timing
-// on, the launch is timed and its work (8 flops per stored nonzero of every
-// operator per operator application) is added to the context's counters.
-int run_action(mg_ctx* ctx, std::vector<ActionJob>& jobs, const std::vector<long long>& nnz, void* jbuf, int dmax) {
+// Runs the action path for `jobs` (records with the operator, coefficient and
+// state pointers set): places the interval records and any off-chip interval
+// matrices in workspace, uploads the records to `jbuf` (device), launches the
+// bounds and chain kernels on the context's stream, reads the records back and
+// waits.  Jobs are launched heaviest first.  With per-launch timing on, the
+// chain kernel is timed and its work (8 flops per pattern nonzero per operator
+// application) is added to the context's counters.
+int run_action(mg_ctx* ctx, std::vector<ActionJob>& jobs, void* jbuf) {
+  const size_t nj = jobs.size();
+  std::vector<size_t> order(nj);
+  for (size_t q = 0; q < nj; ++q) order[q] = q;
+  std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) {
+    return (double)jobs[a].N * jobs[a].nnz > (double)jobs[b].N * jobs[b].nnz;
+  });
+  int dmax = 1, nmax = 0;
+  for (auto& j : jobs) {
+    dmax = std::max(dmax, j.d);
+    nmax = std::max(nmax, j.N);
+  }
+  // nonzeros held on chip: all of a lone job's if they fit in 200 KiB; in a
+  // batch the largest count that keeps a CTA within 72 KiB (three per SM)
+  const size_t budget = nj <= 152 ? 200 * 1024 : 72 * 1024;
+  int cap = 0;
+  for (auto& j : jobs)
+    if (j.nnz > cap && action_smem_bytes(dmax, j.nnz) <= budget) cap = j.nnz;
+  size_t rec_total = 0, mat_total = 0;
+  for (auto& j : jobs) {
+    rec_total += (size_t)j.N * ACTION_REC;
+    if (j.nnz > cap) mat_total += 2 * (size_t)j.nnz;
+  }
+  double *rec, *mat;
+  MG_TRY(ws(ctx, WS_ACT_REC, rec_total, &rec));
+  MG_TRY(ws(ctx, WS_ACT_MAT, std::max<size_t>(mat_total, 2), &mat));
+  std::vector<ActionJob> launch(nj);
+  size_t ro = 0, mo = 0;
+  for (size_t q = 0; q < nj; ++q) {
+    ActionJob j = jobs[order[q]];
+    j.cheb = rec + ro;
+    ro += (size_t)j.N * ACTION_REC;
+    j.abuf = nullptr;
+    if (j.nnz > cap) {
+      j.abuf = mat + mo;
+      mo += 2 * (size_t)j.nnz;
+    }
+    launch[q] = j;
+  }
   ActionJob* dev = reinterpret_cast<ActionJob*>(jbuf);
-  MG_CUDA_TRY(cudaMemcpyAsync(dev, jobs.data(), sizeof(ActionJob) * jobs.size(), cudaMemcpyHostToDevice, ctx->stream));
+  MG_CUDA_TRY(cudaMemcpyAsync(dev, launch.data(), sizeof(ActionJob) * nj, cudaMemcpyHostToDevice, ctx->stream));
   int e0 = -1, e1 = -1;
   if (ctx->timing) MG_TRY(timing_mark(ctx, &e0));
-  MG_TRY(launch_action_chain((int)jobs.size(), dev, dmax, ctx->stream));
+  MG_TRY(launch_action_chain((int)nj, dev, dmax, nmax, cap, ctx->stream));
   if (ctx->timing) {
     MG_TRY(timing_mark(ctx, &e1));
     ctx->ev_pending.emplace_back(e0, e1);
     ctx->t_launches += 1;
   }
-  MG_CUDA_TRY(cudaMemcpyAsync(jobs.data(), dev, sizeof(ActionJob) * jobs.size(), cudaMemcpyDeviceToHost, ctx->stream));
+  MG_CUDA_TRY(cudaMemcpyAsync(launch.data(), dev, sizeof(ActionJob) * nj, cudaMemcpyDeviceToHost, ctx->stream));
   MG_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
-  if (ctx->timing)
-    for (size_t q = 0; q < jobs.size(); ++q) ctx->t_flops += 8.0 * (double)nnz[q] * (double)jobs[q].matvecs;
+  for (size_t q = 0; q < nj; ++q) {
+    jobs[order[q]] = launch[q];
+    if (ctx->timing) ctx->t_flops += 8.0 * (double)launch[q].nnz * (double)launch[q].matvecs;
+  }
   return MG_OK;
 }
 }  // namespace
@@ -885,9 +927,7 @@ int mg_plan_destroy(mg_plan* p) {
   cudaFree(p->csr_rowptr);
   cudaFree(p->csr_col);
   cudaFree(p->csr_val);
-  cudaFree(p->csr_opoff);
-  cudaFree(p->csr_tmean);
-  cudaFree(p->csr_snorm);
+  cudaFree(p->csr_diag);
   delete p;
   return MG_OK;
 }
@@ -1149,11 +1189,11 @@ int mg_evolve(mg_plan* p, int output, const double* in, double* out, int reorth_
     std::vector<ActionJob> jv{action_job(p, ps.psi)};
     double* jbuf;
     MG_TRY(ws(ctx, WS_VEC, sizeof(ActionJob) / sizeof(double) + 1, &jbuf));
-    MG_TRY(run_action(ctx, jv, {p->csr_nnz}, jbuf, d));
+    MG_TRY(run_action(ctx, jv, jbuf));
     const ActionJob& job = jv[0];
     if (job.status != MG_OK) {
       set_last_message("action-based state path stopped: %s", job.status == MG_ENONFINITE
-                       ? "non-finite norm bound" : "norm bound needs more than 16384 sub-steps per interval");
+                       ? "non-finite spectral bound" : "spectral half-width needs more than 16384 sub-steps per interval");
       return job.status;
     }
     MG_TRY(finish_prop(ctx, eng, ps, out, flags, rep));
@@ -1513,12 +1553,10 @@ int mg_evolve_batch(mg_ctx* ctx, int n, mg_plan* const* plans, const int* output
     std::vector<ActionJob> aj;
     std::vector<int> aidx;
     std::vector<Item> rest;
-    int dmax = 1;
     for (auto& it : all) {
       if (it.j.output == MG_OUT_STATE && (it.p->flags & MG_FLAG_STATE_ACTION)) {
         aidx.push_back(it.j.idx);
         aj.push_back(ActionJob{});
-        dmax = std::max(dmax, it.p->d);
       } else {
         rest.push_back(it);
       }
@@ -1532,17 +1570,15 @@ int mg_evolve_batch(mg_ctx* ctx, int n, mg_plan* const* plans, const int* output
       MG_TRY(ws(ctx, WS_ACC, total, &psis));
       MG_TRY(ws(ctx, WS_VEC, (sizeof(ActionJob) * aj.size()) / sizeof(double) + 1, &jb));
       size_t off = 0;
-      std::vector<long long> nnz(aidx.size());
       for (size_t q = 0; q < aidx.size(); ++q) {
         mg_plan* p = plans[aidx[q]];
         if (!in || !in[aidx[q]]) return MG_EINVAL;
         MG_TRY(ensure_csr(p));
         aj[q] = action_job(p, psis + off);
-        nnz[q] = p->csr_nnz;
         MG_CUDA_TRY(cudaMemcpyAsync(psis + off, in[aidx[q]], sizeof(double) * 2 * p->d, h2d, ctx->stream));
         off += 2 * (size_t)p->d;
       }
-      MG_TRY(run_action(ctx, aj, nnz, jb, dmax));
+      MG_TRY(run_action(ctx, aj, jb));
       off = 0;
       for (size_t q = 0; q < aidx.size(); ++q) {
         mg_plan* p = plans[aidx[q]];

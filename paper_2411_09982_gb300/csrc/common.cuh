@@ -143,28 +143,35 @@ struct ChainSeg {
 };
 int launch_multi_chain(int nseg, int d, const ChainSeg* segs_dev, const double* U, long long sU,
                        double* const* psi_dev, int reorth_every, cudaStream_t s);
-// Action-based state propagation with CSR operators; see action.cu.
+// One state job of the action-based path (action.cu).  The operators are one
+// CSR pattern (union of the nonzeros of H0, H_1.. H_K plus the diagonal) with
+// one complex value array per operator, operator-major: val[(op * nnz + e)].
+constexpr int ACTION_REC = 72;   // doubles per interval record
 struct ActionJob {
   int d;
   int K;
   int N;
-  int first;
+  int first;            // first interval's row in c
+  int nnz;
   double dt;
-  const int* rowptr;
-  const int* col;
-  const double* val;
-  const int* opoff;
-  const double* c;
-  const double* trace_mean;
-  const double* shifted_norm;
-  double* psi;
-  int status;   // MG_OK, or set by the kernel when the job stopped early
-  // written by the kernel: operator applications, sub-step counts, series length, norm bound
+  const int* rowptr;    // d + 1
+  const int* col;       // nnz
+  const int* diag;      // d: position of the diagonal entry of each row
+  const double* val;    // (1 + K) x nnz complex
+  const double* c;      // coefficients c_{k,n}, row-major N x K
+  double* cheb;         // N x ACTION_REC interval records (written by the bounds kernel)
+  double* abuf;         // nnz complex: the interval matrix when it does not fit in shared memory
+  double* psi;          // d complex, in and out
+  int status;           // MG_OK, or set by the kernel when the job stopped early
+  // written by the kernel: operator applications, sub-step counts, degree, half-width
   long long matvecs;
   int max_sub, min_sub, max_terms;
   double max_nu;
 };
-int launch_action_chain(int njobs, ActionJob* jobs_dev, int dmax, cudaStream_t s);
+// shared memory of the chain kernel for the largest d and the largest nonzero
+// count held on chip (0: every interval matrix in global memory)
+size_t action_smem_bytes(int dmax, int nnz_cap);
+int launch_action_chain(int njobs, ActionJob* jobs_dev, int dmax, int nmax, int nnz_cap, cudaStream_t s);
 
 // dst (dp x dp, zero padded) <- src (d x d), for `count` stacked matrices
 int launch_pad_copy(int count, int d, int dp, const double* src, double* dst, cudaStream_t s);

@@ -419,9 +419,12 @@ def test_second_order_magnus_matches_oracle(ctx, prec, L, tol):
 # ----------------------------------------------------------------------------
 @pytest.mark.parametrize("order", [1, 2])
 def test_action_state_path_matches_oracle(ctx, order):
+    diag = W.config(0, N=50)   # commuting diagonal operators: Gershgorin's interval is the spectrum
+    diag.H0 = np.diag(np.diag(diag.H0))
+    diag.Hk = np.diag(np.arange(diag.d, dtype=np.complex128))[None]
     cases = [W.config(0, N=120), W.transmon_resonator(nt=3, nr=2, T=2.0, sigma=0.5, omega0=0.4, N=20, P=16),
              W.transmon_chain(n_sites=3, levels=3, J=0.02, seed=4, omega0_max=0.2, T=5.0, sigma=1.2, N=30, P=16,
-                              unitary=False)]
+                              unitary=False), diag]
     for wl in cases:
         out, _ = M.evolve_workload(ctx, wl, M.MG_PREC_FP64, order=order, flags=M.MG_FLAG_STATE_ACTION)
         ref = oracle.evolve_workload(wl) if order == 1 else oracle.evolve_workload_second_order(wl)
