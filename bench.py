@@ -32,10 +32,11 @@ METRIC = "Magnus intervals/sec at dim 729 vs FP64 err; p50/p99 latency, mixed st
 UNIT = "intervals/s"
 WORKLOAD = "transmon_chain_d729_N2000_P16_K6_propagator"
 SAMPLE_INTERVALS = 128          # oracle sample (cpu_baseline) and accuracy prefix
-# DRAM bytes (read + write) per complex d = 729 product of split_gemm_kernel<6,4>, from the ncu
-# capture summarised in profiles/split_gemm_d729_batch32_L6.md (1.918 GB for 32 products);
-# scaled to a launch by the products it computes.  Valid for that kernel build only.
-GEMM_DRAM_BYTES_PER_PRODUCT = {(729, 6): 1.918174e9 / 32}
+# DRAM bytes (read + write) per complex d = 729 product of split_gemm_kernel<6,2,2> (64-byte
+# swizzled K = 32 stages, 2-CTA clusters sharing B by multicast), from the ncu capture summarised
+# in profiles/split_gemm_d729_batch32_L6.md (1.885 GB for 32 products); scaled to a launch by the
+# products it computes.  Valid for that kernel build only.
+GEMM_DRAM_BYTES_PER_PRODUCT = {(729, 6): 1.885035e9 / 32}
 REFERENCE_STEP_INTERVALS = 16   # oracle intervals per step of --impl reference
 
 
@@ -242,7 +243,7 @@ def run_ours(args):
                     "frac": achieved / peak,
                     "traffic": per_prod * products_per_launch if per_prod else None,
                     "traffic_note": "bytes per average launch, scaled by products from one ncu capture",
-                    "kernel": "split_gemm_kernel (with its operand slicers)",
+                    "kernel": "split_gemm_kernel",
                     "peak_source": f"bf16 dense sustained, {peak_src}",
                     "tensor_pipe_frac": achieved * pairs / peak,
                     "note": f"achieved counts 8 d^3 flops per complex product; the tensor pipe issues "
