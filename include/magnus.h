@@ -106,6 +106,7 @@ typedef struct mg_report {
   int64_t matrix_products;    /* complex d x d products issued                  */
   int64_t sparse_matvecs;     /* operator applications (MG_FLAG_STATE_ACTION)   */
   int64_t sparse_nnz;         /* stored nonzeros of H0 and the H_k (same path)  */
+  int64_t action_ctas;        /* CTAs per job of the action chain (1 or a cluster size) */
 } mg_report;
 
 /* ---- context ---------------------------------------------------------------- */

@@ -26,12 +26,20 @@
 // an interval costs about (degree) x (nonzeros) complex multiply-adds instead
 // of the d^3 products that forming U_n takes.
 //
-// Two kernels: a bounds kernel (one warp per interval, all intervals of all
-// jobs in parallel) computes c_n, rho_n, s_n, k_t and the J_k(z); the chain
-// kernel (one CTA per job) carries the state through the intervals with one
-// thread per row and one barrier per operator application, the vectors and,
-// where they fit, the interval matrix and its pattern in shared memory.
+// Kernels: a bounds kernel (one warp per interval, all intervals of all jobs
+// in parallel) computes c_n, rho_n, s_n, k_t and the J_k(z); a chain kernel
+// carries each job's state through its intervals with one thread per row and
+// one barrier per operator application, the vectors and, where they fit, the
+// interval matrix and its pattern in shared memory.  The chain runs either as
+// one CTA per job (batches: every SM busy with its own jobs) or as one thread
+// block cluster of up to 16 CTAs per job (a few large jobs): each CTA owns a
+// contiguous block of rows and keeps full copies of the two recurrence vectors,
+// writes its new rows into every CTA of the cluster through distributed shared
+// memory after each operator application, and the cluster barrier that follows
+// orders them before the next application reads.
 #include "common.cuh"
+
+#include <cooperative_groups.h>
 
 #include <algorithm>
 
@@ -283,19 +291,214 @@ action_chain_kernel(ActionJob* __restrict__ jobs, int dmax, int nnz_cap) {
   }
 }
 
+// One cluster of C CTAs per job (blockIdx.x / C); CTA r of the cluster owns
+// rows [r * ceil(d / C), ...).  Shared memory: full copies of the two
+// recurrence vectors (dmax each), the state of the own rows (rows_max), then,
+// where cap_loc > 0 and the job's own-row nonzeros fit, the own rows' interval
+// matrix and column indices; the own rows' local row offsets always.
+__global__ void __launch_bounds__(ACTION_THREADS)
+action_chain_cluster_kernel(ActionJob* __restrict__ jobs, int dmax, int cap_loc) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cl = cg::this_cluster();
+  const int C = (int)cl.num_blocks();
+  const int rank = (int)cl.block_rank();
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double cn[ACTION_MAX_OPS];
+  __shared__ double Jk[ACTION_KMAX + 1];
+  const int job = blockIdx.x / C;
+  ActionJob& R = jobs[job];
+  const ActionJob J = R;
+  const int d = J.d;
+  const int rows_max = (dmax + C - 1) / C;
+  const int rows_per = (d + C - 1) / C;
+  const int r0 = min(d, rank * rows_per), r1 = min(d, r0 + rows_per);
+  const int nr = r1 - r0;
+  double2* vx = reinterpret_cast<double2*>(smem_raw);
+  double2* vy = vx + dmax;
+  double2* acc = vy + dmax;   // own rows
+  const int e_base = J.rowptr[r0];
+  const int nnz_loc = J.rowptr[r1] - e_base;
+  const bool in_smem = nnz_loc <= cap_loc;
+  double2* A_s = acc + rows_max;
+  int* col_s = reinterpret_cast<int*>(A_s + cap_loc);
+  int* rp = col_s + cap_loc;   // rows_max + 1 local offsets
+  double2* A = in_smem ? A_s : reinterpret_cast<double2*>(J.abuf) + e_base;
+  const int* col = in_smem ? col_s : J.col + e_base;
+  for (int li = threadIdx.x; li <= nr; li += blockDim.x) rp[li] = J.rowptr[r0 + li] - e_base;
+  if (in_smem)
+    for (int e = threadIdx.x; e < nnz_loc; e += blockDim.x) col_s[e] = J.col[e_base + e];
+  for (int li = threadIdx.x; li < nr; li += blockDim.x)
+    acc[li] = reinterpret_cast<const double2*>(J.psi)[r0 + li];
+  long long matvecs = 0;
+  int max_sub = 0, min_sub = 1 << 30, max_deg = 0;
+  double max_rho = 0.0;
+  cl.sync();   // every CTA of the cluster runs before any remote write
+  for (int n = 0; n < J.N; ++n) {
+    const double* rec = J.cheb + (long long)n * ACTION_REC;
+    const int s = (int)rec[2];
+    if (s <= 0) {   // uniform over the cluster: every CTA reads the same record
+      if (rank == 0 && threadIdx.x == 0) R.status = s == -1 ? MG_ENONFINITE : MG_EUNSUPPORTED;
+      cl.sync();
+      return;
+    }
+    const double center = rec[0], inv_rho = rec[1];
+    const int kt = (int)rec[3];
+    max_sub = max(max_sub, s);
+    min_sub = min(min_sub, s);
+    max_deg = max(max_deg, kt);
+    max_rho = fmax(max_rho, rec[4]);
+    const double* crow = J.c + (long long)(J.first + n) * J.K;
+    for (int k = threadIdx.x; k < J.K; k += blockDim.x) cn[k] = crow[k];
+    for (int k = threadIdx.x; k <= kt; k += blockDim.x) Jk[k] = rec[5 + k];
+    __syncthreads();
+    for (int li = threadIdx.x; li < nr; li += blockDim.x) {
+      const int i = r0 + li;
+      const int di = J.diag[i] - e_base;
+      for (int e = rp[li]; e < rp[li + 1]; ++e) {
+        double ar = 0.0, ai = 0.0;
+        for (int op = 0; op <= J.K; ++op) {
+          const double coef = op == 0 ? J.dt : cn[op - 1];
+          const double2 v = reinterpret_cast<const double2*>(J.val)[(long long)op * J.nnz + e_base + e];
+          ar = fma(coef, v.x, ar);
+          ai = fma(coef, v.y, ai);
+        }
+        if (e == di) ar -= center;
+        A[e] = make_double2(ar * inv_rho, ai * inv_rho);
+      }
+    }
+    for (int sub = 0; sub < s; ++sub) {
+      // T_0 v = v into every CTA's vx; acc = J_0 v
+      for (int li = threadIdx.x; li < nr; li += blockDim.x) {
+        const double2 v = acc[li];
+        acc[li] = make_double2(Jk[0] * v.x, Jk[0] * v.y);
+        for (int q = 0; q < C; ++q) cl.map_shared_rank(vx, q)[r0 + li] = v;
+      }
+      cl.sync();
+      for (int k = 1; k <= kt; ++k) {
+        const double2* cur = (k & 1) ? vx : vy;
+        double2* old = (k & 1) ? vy : vx;
+        const double two = k == 1 ? 1.0 : 2.0;
+        const double twoJ = 2.0 * Jk[k];
+        for (int li = threadIdx.x; li < nr; li += blockDim.x) {
+          const int i = r0 + li;
+          double2 y0 = make_double2(0.0, 0.0), y1 = make_double2(0.0, 0.0);
+          const int e1 = rp[li + 1];
+          int e = rp[li];
+          for (; e + 1 < e1; e += 2) {
+            y0 = cfma(A[e], cur[col[e]], y0);
+            y1 = cfma(A[e + 1], cur[col[e + 1]], y1);
+          }
+          if (e < e1) y0 = cfma(A[e], cur[col[e]], y0);
+          double2 t = make_double2(two * (y0.x + y1.x), two * (y0.y + y1.y));
+          if (k > 1) {
+            const double2 o = old[i];
+            t.x -= o.x;
+            t.y -= o.y;
+          }
+          acc[li] = add_term(acc[li], t, twoJ, k);
+          for (int q = 0; q < C; ++q) cl.map_shared_rank(old, q)[i] = t;
+        }
+        cl.sync();
+      }
+      matvecs += kt;
+    }
+    double sn, cs;
+    sincos(center, &sn, &cs);
+    for (int li = threadIdx.x; li < nr; li += blockDim.x) {
+      const double2 v = acc[li];
+      acc[li] = make_double2(cs * v.x + sn * v.y, cs * v.y - sn * v.x);
+    }
+    __syncthreads();
+  }
+  for (int li = threadIdx.x; li < nr; li += blockDim.x) reinterpret_cast<double2*>(J.psi)[r0 + li] = acc[li];
+  if (rank == 0 && threadIdx.x == 0) {
+    R.matvecs = matvecs;
+    R.max_sub = max_sub;
+    R.min_sub = J.N > 0 ? min_sub : 0;
+    R.max_terms = max_deg;
+    R.max_nu = max_rho;
+  }
+  cl.sync();   // no CTA leaves while another may still address its shared memory
+}
+
+size_t action_cluster_smem_bytes(int dmax, int C, int cap_loc) {
+  const size_t rows_max = (size_t)(dmax + C - 1) / C;
+  return sizeof(double2) * (2 * (size_t)dmax + rows_max) + (sizeof(double2) + sizeof(int)) * (size_t)cap_loc +
+         sizeof(int) * (rows_max + 1);
+}
+
+// Largest cluster size <= want (a power of two) that the device can co-schedule
+// with this shared memory, or 1.
+int action_cluster_size(int want, int dmax, int cap_loc) {
+  for (int C = want; C >= 2; C >>= 1) {
+    const size_t smem = action_cluster_smem_bytes(dmax, C, cap_loc);
+    if (smem > 225 * 1024) continue;
+    if (cudaFuncSetAttribute(action_chain_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem) != cudaSuccess ||
+        cudaFuncSetAttribute(action_chain_cluster_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
+            cudaSuccess) {
+      cudaGetLastError();
+      return 1;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(C, 1, 1);
+    cfg.blockDim = dim3(ACTION_THREADS, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int active = 0;
+    if (cudaOccupancyMaxActiveClusters(&active, action_chain_cluster_kernel, &cfg) == cudaSuccess && active >= 1)
+      return C;
+    cudaGetLastError();
+  }
+  return 1;
+}
+
+int launch_action_cluster(int njobs, ActionJob* jobs_dev, int dmax, int C, int cap_loc, cudaStream_t s) {
+  const size_t smem = action_cluster_smem_bytes(dmax, C, cap_loc);
+  MG_CUDA_TRY(cudaFuncSetAttribute(action_chain_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)smem));
+  MG_CUDA_TRY(cudaFuncSetAttribute(action_chain_cluster_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(njobs * C, 1, 1);
+  cfg.blockDim = dim3(ACTION_THREADS, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = C;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  const cudaError_t e = cudaLaunchKernelEx(&cfg, action_chain_cluster_kernel, jobs_dev, dmax, cap_loc);
+  if (e != cudaSuccess) {
+    set_last_cuda_error(e, "cudaLaunchKernelEx(action_chain_cluster_kernel)", __FILE__, __LINE__);
+    return MG_ECUDA;
+  }
+  return check_launch("action_chain_cluster_kernel");
+}
+
 size_t action_smem_bytes(int dmax, int nnz_cap) {
   size_t b = sizeof(double2) * 3 * (size_t)dmax;
   if (nnz_cap > 0) b += (sizeof(double2) + sizeof(int)) * (size_t)nnz_cap + sizeof(int) * ((size_t)dmax + 1);
   return b;
 }
 
-int launch_action_chain(int njobs, ActionJob* jobs_dev, int dmax, int nmax, int nnz_cap, cudaStream_t s) {
+int launch_action_chain(int njobs, ActionJob* jobs_dev, int dmax, int nmax, int nnz_cap, int cluster,
+                        cudaStream_t s) {
   if (njobs <= 0) return MG_OK;
   if (nmax > 0) {
     dim3 grid((nmax + 7) / 8, njobs);
     action_bounds_kernel<<<grid, 256, 0, s>>>(jobs_dev);
     MG_TRY(check_launch("action_bounds_kernel"));
   }
+  if (cluster > 1) return launch_action_cluster(njobs, jobs_dev, dmax, cluster, nnz_cap, s);
   const size_t smem = action_smem_bytes(dmax, nnz_cap);
   if (smem > 48 * 1024)
     MG_CUDA_TRY(cudaFuncSetAttribute(action_chain_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));

@@ -72,6 +72,7 @@ struct mg_ctx {
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   // optional per-launch timing of matrix-product kernels
   bool timing = false;
+  int last_action_cluster = 0;   // CTAs per job of the last action launch
   std::vector<cudaEvent_t> ev_pool;
   std::vector<std::pair<int, int>> ev_pending;   // indices into ev_pool
   size_t ev_next = 0;
@@ -101,6 +102,7 @@ struct mg_plan {
   int* csr_diag = nullptr;       // position of each row's diagonal entry
   double* csr_val = nullptr;     // (1 + K) x nnz complex, operator-major
   long long csr_nnz = 0;
+  std::vector<int> csr_rowptr_h;  // host copy of the row offsets (cluster partitioning)
 };
 
 namespace {
@@ -603,6 +605,7 @@ int ensure_csr(mg_plan* p) {
   MG_TRY(up(reinterpret_cast<void**>(&p->csr_diag), diag.data(), sizeof(int) * diag.size()));
   MG_TRY(up(reinterpret_cast<void**>(&p->csr_val), val.data(), sizeof(double) * val.size()));
   p->csr_nnz = (long long)nnz;
+  p->csr_rowptr_h = rowptr;
   p->csr_ok = true;
   return MG_OK;
 }
@@ -623,34 +626,68 @@ ActionJob action_job(mg_plan* p, double* psi) {
   return j;
 }
 // Runs the action path for `jobs` (records with the operator, coefficient and
-// state pointers set): places the interval records and any off-chip interval
-// matrices in workspace, uploads the records to `jbuf` (device), launches the
-// bounds and chain kernels on the context's stream, reads the records back and
-// waits.  Jobs are launched heaviest first.  With per-launch timing on, the
-// chain kernel is timed and its work (8 flops per pattern nonzero per operator
-// application) is added to the context's counters.
-int run_action(mg_ctx* ctx, std::vector<ActionJob>& jobs, void* jbuf) {
+// state pointers set; rowptr_h[q] the host row offsets of job q): places the
+// interval records and any off-chip interval matrices in workspace, uploads the
+// records to `jbuf` (device), launches the bounds and chain kernels on the
+// context's stream, reads the records back and waits.  A few large jobs run as
+// one thread block cluster each (up to 16 CTAs, about 1024 nonzeros per CTA or
+// more); otherwise one CTA per job, heaviest first.  With per-launch timing on,
+// the chain kernel is timed and its work (8 flops per pattern nonzero per
+// operator application) is added to the context's counters.
+int run_action(mg_ctx* ctx, std::vector<ActionJob>& jobs, const std::vector<const std::vector<int>*>& rowptr_h,
+               void* jbuf) {
   const size_t nj = jobs.size();
   std::vector<size_t> order(nj);
   for (size_t q = 0; q < nj; ++q) order[q] = q;
   std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) {
     return (double)jobs[a].N * jobs[a].nnz > (double)jobs[b].N * jobs[b].nnz;
   });
-  int dmax = 1, nmax = 0;
+  int dmax = 1, nmax = 0, nnz_max = 0;
   for (auto& j : jobs) {
     dmax = std::max(dmax, j.d);
     nmax = std::max(nmax, j.N);
+    nnz_max = std::max(nnz_max, j.nnz);
   }
-  // nonzeros held on chip: all of a lone job's if they fit in 200 KiB; in a
-  // batch the largest count that keeps a CTA within 72 KiB (three per SM)
-  const size_t budget = nj <= 152 ? 200 * 1024 : 72 * 1024;
-  int cap = 0;
-  for (auto& j : jobs)
-    if (j.nnz > cap && action_smem_bytes(dmax, j.nnz) <= budget) cap = j.nnz;
+  // cluster size: the largest power of two <= 16 with ~1024+ nonzeros per CTA
+  // that keeps every job's cluster resident at once (nj * C <= 152)
+  int want = 1;
+  while (want < 16 && 2 * want * 1024 <= nnz_max && (size_t)(2 * want) * nj <= 152) want *= 2;
+  int cluster = 1, cap = 0;
+  if (want >= 2) {
+    // own-row nonzeros held on chip: the largest count over the CTAs that fits
+    for (int C = want; C >= 2; C >>= 1) {
+      std::vector<int> loc;
+      for (size_t q = 0; q < nj; ++q) {
+        const std::vector<int>& rp = *rowptr_h[q];
+        const int d = jobs[q].d, per = (d + C - 1) / C;
+        for (int r = 0; r < C; ++r) {
+          const int r0 = std::min(d, r * per), r1 = std::min(d, r0 + per);
+          loc.push_back(rp[r1] - rp[r0]);
+        }
+      }
+      int c = 0;
+      for (int v : loc)
+        if (v > c && action_cluster_smem_bytes(dmax, C, v) <= 200 * 1024) c = v;
+      if (action_cluster_smem_bytes(dmax, C, c) > 225 * 1024) continue;
+      const int got = action_cluster_size(C, dmax, c);
+      if (got == C) {
+        cluster = C;
+        cap = c;
+        break;
+      }
+    }
+  }
+  if (cluster == 1) {
+    // nonzeros held on chip: all of a lone job's if they fit in 200 KiB; in a
+    // batch the largest count that keeps a CTA within 72 KiB (three per SM)
+    const size_t budget = nj <= 152 ? 200 * 1024 : 72 * 1024;
+    for (auto& j : jobs)
+      if (j.nnz > cap && action_smem_bytes(dmax, j.nnz) <= budget) cap = j.nnz;
+  }
   size_t rec_total = 0, mat_total = 0;
   for (auto& j : jobs) {
     rec_total += (size_t)j.N * ACTION_REC;
-    if (j.nnz > cap) mat_total += 2 * (size_t)j.nnz;
+    if (cluster > 1 || j.nnz > cap) mat_total += 2 * (size_t)j.nnz;
   }
   double *rec, *mat;
   MG_TRY(ws(ctx, WS_ACT_REC, rec_total, &rec));
@@ -662,7 +699,7 @@ int run_action(mg_ctx* ctx, std::vector<ActionJob>& jobs, void* jbuf) {
     j.cheb = rec + ro;
     ro += (size_t)j.N * ACTION_REC;
     j.abuf = nullptr;
-    if (j.nnz > cap) {
+    if (cluster > 1 || j.nnz > cap) {
       j.abuf = mat + mo;
       mo += 2 * (size_t)j.nnz;
     }
@@ -672,7 +709,7 @@ int run_action(mg_ctx* ctx, std::vector<ActionJob>& jobs, void* jbuf) {
   MG_CUDA_TRY(cudaMemcpyAsync(dev, launch.data(), sizeof(ActionJob) * nj, cudaMemcpyHostToDevice, ctx->stream));
   int e0 = -1, e1 = -1;
   if (ctx->timing) MG_TRY(timing_mark(ctx, &e0));
-  MG_TRY(launch_action_chain((int)nj, dev, dmax, nmax, cap, ctx->stream));
+  MG_TRY(launch_action_chain((int)nj, dev, dmax, nmax, cap, cluster, ctx->stream));
   if (ctx->timing) {
     MG_TRY(timing_mark(ctx, &e1));
     ctx->ev_pending.emplace_back(e0, e1);
@@ -680,6 +717,7 @@ int run_action(mg_ctx* ctx, std::vector<ActionJob>& jobs, void* jbuf) {
   }
   MG_CUDA_TRY(cudaMemcpyAsync(launch.data(), dev, sizeof(ActionJob) * nj, cudaMemcpyDeviceToHost, ctx->stream));
   MG_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  ctx->last_action_cluster = cluster;
   for (size_t q = 0; q < nj; ++q) {
     jobs[order[q]] = launch[q];
     if (ctx->timing) ctx->t_flops += 8.0 * (double)launch[q].nnz * (double)launch[q].matvecs;
@@ -1189,7 +1227,7 @@ int mg_evolve(mg_plan* p, int output, const double* in, double* out, int reorth_
     std::vector<ActionJob> jv{action_job(p, ps.psi)};
     double* jbuf;
     MG_TRY(ws(ctx, WS_VEC, sizeof(ActionJob) / sizeof(double) + 1, &jbuf));
-    MG_TRY(run_action(ctx, jv, jbuf));
+    MG_TRY(run_action(ctx, jv, {&p->csr_rowptr_h}, jbuf));
     const ActionJob& job = jv[0];
     if (job.status != MG_OK) {
       set_last_message("action-based state path stopped: %s", job.status == MG_ENONFINITE
@@ -1210,6 +1248,7 @@ int mg_evolve(mg_plan* p, int output, const double* in, double* out, int reorth_
       rep->max_norm1 = job.max_nu;
       rep->sparse_matvecs = job.matvecs;
       rep->sparse_nnz = p->csr_nnz;
+      rep->action_ctas = ctx->last_action_cluster;
     }
     MG_CUDA_TRY(cudaStreamSynchronize(s));
     return MG_OK;
@@ -1578,7 +1617,9 @@ int mg_evolve_batch(mg_ctx* ctx, int n, mg_plan* const* plans, const int* output
         MG_CUDA_TRY(cudaMemcpyAsync(psis + off, in[aidx[q]], sizeof(double) * 2 * p->d, h2d, ctx->stream));
         off += 2 * (size_t)p->d;
       }
-      MG_TRY(run_action(ctx, aj, jb));
+      std::vector<const std::vector<int>*> rps;
+      for (size_t q = 0; q < aidx.size(); ++q) rps.push_back(&plans[aidx[q]]->csr_rowptr_h);
+      MG_TRY(run_action(ctx, aj, rps, jb));
       off = 0;
       for (size_t q = 0; q < aidx.size(); ++q) {
         mg_plan* p = plans[aidx[q]];

@@ -171,7 +171,15 @@ struct ActionJob {
 // shared memory of the chain kernel for the largest d and the largest nonzero
 // count held on chip (0: every interval matrix in global memory)
 size_t action_smem_bytes(int dmax, int nnz_cap);
-int launch_action_chain(int njobs, ActionJob* jobs_dev, int dmax, int nmax, int nnz_cap, cudaStream_t s);
+// the same for the cluster variant: C CTAs per job, cap_loc own-row nonzeros on chip
+size_t action_cluster_smem_bytes(int dmax, int C, int cap_loc);
+// largest power-of-two cluster size <= want that the device co-schedules, else 1
+int action_cluster_size(int want, int dmax, int cap_loc);
+// bounds kernel, then the chain: one CTA per job (cluster <= 1, nnz_cap = the
+// nonzeros held on chip) or one cluster of `cluster` CTAs per job (nnz_cap =
+// own-row nonzeros held on chip per CTA)
+int launch_action_chain(int njobs, ActionJob* jobs_dev, int dmax, int nmax, int nnz_cap, int cluster,
+                        cudaStream_t s);
 
 // dst (dp x dp, zero padded) <- src (d x d), for `count` stacked matrices
 int launch_pad_copy(int count, int d, int dp, const double* src, double* dst, cudaStream_t s);

@@ -52,6 +52,7 @@ class mg_report(ctypes.Structure):
         ("matrix_products", ctypes.c_int64),
         ("sparse_matvecs", ctypes.c_int64),
         ("sparse_nnz", ctypes.c_int64),
+        ("action_ctas", ctypes.c_int64),
     ]
 
     def as_dict(self):

@@ -432,6 +432,21 @@ def test_action_state_path_matches_oracle(ctx, order):
         assert err <= 1e-11, (wl.name, err)
 
 
+def test_action_state_path_cluster_matches_oracle(ctx):
+    # large sparse jobs run as one thread block cluster per job (rows split over the
+    # CTAs, ragged last block); d = 729 chain and d = 512 three-site 8-level chain
+    cases = [W.transmon_chain(n_sites=6, levels=3, J=0.01, seed=1, omega0_max=0.05, T=1.0, sigma=0.3, N=8,
+                              P=16, unitary=False, name="chain729_state"),
+             W.transmon_chain(n_sites=3, levels=8, J=0.02, seed=5, omega0_max=0.1, T=0.8, sigma=0.3, N=6, P=8,
+                              all_to_all=True, unitary=False, name="a2a512_state")]
+    for wl in cases:
+        out, rep = M.evolve_workload(ctx, wl, M.MG_PREC_FP64, flags=M.MG_FLAG_STATE_ACTION)
+        assert rep["action_ctas"] >= 2, (wl.name, rep["action_ctas"])
+        ref = oracle.evolve_workload(wl)
+        err = np.abs(out.cpu().numpy() - ref).max()
+        assert err <= 1e-11, (wl.name, err)
+
+
 def test_action_state_path_in_batch(ctx):
     jobs = _small_jobs(seed=31, n=6)
     plans, outs, ins, kinds = [], [], [], []
