@@ -389,7 +389,7 @@ def run_config(args):
         if args.action:
             rep = plan.evolve(M.MG_OUT_STATE, inp, out, 0)
             out_line["action"] = {k: rep[k] for k in ("sparse_matvecs", "sparse_nnz", "max_squarings",
-                                                      "taylor_degree", "max_norm1")}
+                                                      "taylor_degree", "max_norm1", "action_ctas")}
         if not args.no_cpu_baseline:
             n_s = 128 if args.config == 0 else 1
             t0 = time.perf_counter()
@@ -472,7 +472,8 @@ def run_config(args):
                 time.sleep(arr - now)
             kind = M.MG_OUT_STATE if inp is not None else M.MG_OUT_PROPAGATOR
             while True:
-                jid = srv.submit(H0, Hk, wl.N, wl.P, wl.t0, wl.dt, w, S, kind, inp, o, M.MG_PREC_SPLIT, args.slices)
+                jid = srv.submit(H0, Hk, wl.N, wl.P, wl.t0, wl.dt, w, S, kind, inp, o, M.MG_PREC_SPLIT, args.slices,
+                                 action=args.action and kind == M.MG_OUT_STATE)
                 if jid is not None:
                     break
                 rejected += 1
@@ -489,7 +490,8 @@ def run_config(args):
                         dtype=f"bf16 digits x{args.slices} (fp32 accumulate) + f64",
                         config={"workload": "poisson_200_per_s_mixed_d32_2048", "requests": len(ids),
                                 "arrival_span_s": stream_spec[-1][0], "d_max": max(wl.d for wl in built),
-                                "intervals_total": intervals, "quantum_intervals": 256},
+                                "intervals_total": intervals, "quantum_intervals": 256,
+                                "state_requests": "action path (FP64)" if args.action else "split path"},
                         latency_ms={"p50": st["p50_ms"], "p99": st["p99_ms"], "max": lat[-1]},
                         admission_retries=rejected, clocks=clk)
         srv.close()

@@ -550,16 +550,55 @@ int validate_prec(int precision, int L) {
 namespace {
 // CSR copies of H0 and the plan's Kx operators (host-built once from the dense
 // device copies), with each operator's trace mean and shifted 1-norm.
+// Host CSR of 1 + K dense d x d complex operators (`dense`, operator-major):
+// the union of their nonzeros plus the diagonal, one value array per operator.
+struct CsrHost {
+  std::vector<int> rowptr, col, diag;
+  std::vector<double> val;   // (1 + K) x nnz complex
+};
+void build_csr_host(const double* dense, int d, int nops, CsrHost& h) {
+  const size_t dd = (size_t)d * d;
+  h.rowptr.assign(d + 1, 0);
+  h.col.clear();
+  h.diag.assign(d, 0);
+  for (int i = 0; i < d; ++i) {
+    for (int j = 0; j < d; ++j) {
+      bool nz = i == j;
+      for (int op = 0; op < nops && !nz; ++op) {
+        const double* v = dense + (size_t)op * 2 * dd + 2 * ((size_t)i * d + j);
+        nz = v[0] != 0.0 || v[1] != 0.0;
+      }
+      if (nz) {
+        if (i == j) h.diag[i] = (int)h.col.size();
+        h.col.push_back(j);
+      }
+    }
+    h.rowptr[i + 1] = (int)h.col.size();
+  }
+  const size_t nnz = h.col.size();
+  h.val.assign((size_t)nops * nnz * 2, 0.0);
+  for (int op = 0; op < nops; ++op)
+    for (int i = 0; i < d; ++i)
+      for (int e = h.rowptr[i]; e < h.rowptr[i + 1]; ++e) {
+        const double* v = dense + (size_t)op * 2 * dd + 2 * ((size_t)i * d + h.col[e]);
+        h.val[2 * ((size_t)op * nnz + e)] = v[0];
+        h.val[2 * ((size_t)op * nnz + e) + 1] = v[1];
+      }
+}
+int check_action_limits(int d, int nops) {
+  if (nops > 256) {
+    set_last_message("action-based state path supports at most 255 control operators (job has %d)", nops - 1);
+    return MG_EUNSUPPORTED;
+  }
+  if (action_smem_bytes(d, 0) > 225 * 1024) {   // three complex FP64 vectors in shared memory
+    set_last_message("action-based state path supports d <= %d (job has d = %d)", 225 * 1024 / 48, d);
+    return MG_EUNSUPPORTED;
+  }
+  return MG_OK;
+}
 int ensure_csr(mg_plan* p) {
   if (p->csr_ok) return MG_OK;
-  if (p->Kx + 1 > 256) {
-    set_last_message("action-based state path supports at most 255 control operators (plan has %d)", p->Kx);
-    return MG_EUNSUPPORTED;
-  }
-  if (action_smem_bytes(p->d, 0) > 225 * 1024) {   // three complex FP64 vectors in shared memory
-    set_last_message("action-based state path supports d <= %d (plan has d = %d)", 225 * 1024 / 48, p->d);
-    return MG_EUNSUPPORTED;
-  }
+  MG_TRY(check_action_limits(p->d, 1 + p->Kx));
   const int d = p->d, nops = 1 + p->Kx;
   const size_t dd = (size_t)d * d;
   std::vector<double> dense((size_t)nops * 2 * dd);
@@ -568,31 +607,8 @@ int ensure_csr(mg_plan* p) {
     MG_CUDA_TRY(cudaMemcpy(dense.data() + (size_t)op * 2 * dd, src, sizeof(double) * 2 * dd,
                            cudaMemcpyDeviceToHost));
   }
-  std::vector<int> rowptr(d + 1), col, diag(d);
-  rowptr[0] = 0;
-  for (int i = 0; i < d; ++i) {
-    for (int j = 0; j < d; ++j) {
-      bool nz = i == j;
-      for (int op = 0; op < nops && !nz; ++op) {
-        const double* v = dense.data() + (size_t)op * 2 * dd + 2 * ((size_t)i * d + j);
-        nz = v[0] != 0.0 || v[1] != 0.0;
-      }
-      if (nz) {
-        if (i == j) diag[i] = (int)col.size();
-        col.push_back(j);
-      }
-    }
-    rowptr[i + 1] = (int)col.size();
-  }
-  const size_t nnz = col.size();
-  std::vector<double> val((size_t)nops * nnz * 2);
-  for (int op = 0; op < nops; ++op)
-    for (int i = 0; i < d; ++i)
-      for (int e = rowptr[i]; e < rowptr[i + 1]; ++e) {
-        const double* v = dense.data() + (size_t)op * 2 * dd + 2 * ((size_t)i * d + col[e]);
-        val[2 * ((size_t)op * nnz + e)] = v[0];
-        val[2 * ((size_t)op * nnz + e) + 1] = v[1];
-      }
+  CsrHost h;
+  build_csr_host(dense.data(), d, nops, h);
   auto up = [&](void** dst, const void* src, size_t bytes) -> int {
     cudaFree(*dst);
     *dst = nullptr;
@@ -600,12 +616,12 @@ int ensure_csr(mg_plan* p) {
     MG_CUDA_TRY(cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice));
     return MG_OK;
   };
-  MG_TRY(up(reinterpret_cast<void**>(&p->csr_rowptr), rowptr.data(), sizeof(int) * rowptr.size()));
-  MG_TRY(up(reinterpret_cast<void**>(&p->csr_col), col.data(), sizeof(int) * col.size()));
-  MG_TRY(up(reinterpret_cast<void**>(&p->csr_diag), diag.data(), sizeof(int) * diag.size()));
-  MG_TRY(up(reinterpret_cast<void**>(&p->csr_val), val.data(), sizeof(double) * val.size()));
-  p->csr_nnz = (long long)nnz;
-  p->csr_rowptr_h = rowptr;
+  MG_TRY(up(reinterpret_cast<void**>(&p->csr_rowptr), h.rowptr.data(), sizeof(int) * h.rowptr.size()));
+  MG_TRY(up(reinterpret_cast<void**>(&p->csr_col), h.col.data(), sizeof(int) * h.col.size()));
+  MG_TRY(up(reinterpret_cast<void**>(&p->csr_diag), h.diag.data(), sizeof(int) * h.diag.size()));
+  MG_TRY(up(reinterpret_cast<void**>(&p->csr_val), h.val.data(), sizeof(double) * h.val.size()));
+  p->csr_nnz = (long long)h.col.size();
+  p->csr_rowptr_h = h.rowptr;
   p->csr_ok = true;
   return MG_OK;
 }
@@ -625,91 +641,106 @@ ActionJob action_job(mg_plan* p, double* psi) {
   j.psi = psi;
   return j;
 }
-// Runs the action path for `jobs` (records with the operator, coefficient and
-// state pointers set; rowptr_h[q] the host row offsets of job q): places the
-// interval records and any off-chip interval matrices in workspace, uploads the
-// records to `jbuf` (device), launches the bounds and chain kernels on the
-// context's stream, reads the records back and waits.  A few large jobs run as
-// one thread block cluster each (up to 16 CTAs, about 1024 nonzeros per CTA or
-// more); otherwise one CTA per job, heaviest first.  With per-launch timing on,
-// the chain kernel is timed and its work (8 flops per pattern nonzero per
-// operator application) is added to the context's counters.
-int run_action(mg_ctx* ctx, std::vector<ActionJob>& jobs, const std::vector<const std::vector<int>*>& rowptr_h,
-               void* jbuf) {
+// Launch shape of one action launch: job order (heaviest first), the largest
+// d and N, the cluster size (1: one CTA per job) and the nonzeros held on chip,
+// and the workspace it needs (interval records; interval matrices off chip).
+struct ActionShape {
+  std::vector<size_t> order;
+  int dmax = 1, nmax = 0, cluster = 1, cap = 0;
+  size_t rec_doubles = 0, mat_doubles = 0;
+};
+// A few large jobs run as one thread block cluster each (up to 16 CTAs, about
+// 1024 nonzeros per CTA or more, every job's cluster resident at once);
+// otherwise one CTA per job.
+void shape_action(const std::vector<ActionJob>& jobs, const std::vector<const std::vector<int>*>& rowptr_h,
+                  ActionShape& S) {
   const size_t nj = jobs.size();
-  std::vector<size_t> order(nj);
-  for (size_t q = 0; q < nj; ++q) order[q] = q;
-  std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) {
+  S.order.resize(nj);
+  for (size_t q = 0; q < nj; ++q) S.order[q] = q;
+  std::stable_sort(S.order.begin(), S.order.end(), [&](size_t a, size_t b) {
     return (double)jobs[a].N * jobs[a].nnz > (double)jobs[b].N * jobs[b].nnz;
   });
-  int dmax = 1, nmax = 0, nnz_max = 0;
+  int nnz_max = 0;
   for (auto& j : jobs) {
-    dmax = std::max(dmax, j.d);
-    nmax = std::max(nmax, j.N);
+    S.dmax = std::max(S.dmax, j.d);
+    S.nmax = std::max(S.nmax, j.N);
     nnz_max = std::max(nnz_max, j.nnz);
   }
-  // cluster size: the largest power of two <= 16 with ~1024+ nonzeros per CTA
-  // that keeps every job's cluster resident at once (nj * C <= 152)
   int want = 1;
   while (want < 16 && 2 * want * 1024 <= nnz_max && (size_t)(2 * want) * nj <= 152) want *= 2;
-  int cluster = 1, cap = 0;
-  if (want >= 2) {
+  S.cluster = 1;
+  S.cap = 0;
+  for (int C = want; C >= 2; C >>= 1) {
     // own-row nonzeros held on chip: the largest count over the CTAs that fits
-    for (int C = want; C >= 2; C >>= 1) {
-      std::vector<int> loc;
-      for (size_t q = 0; q < nj; ++q) {
-        const std::vector<int>& rp = *rowptr_h[q];
-        const int d = jobs[q].d, per = (d + C - 1) / C;
-        for (int r = 0; r < C; ++r) {
-          const int r0 = std::min(d, r * per), r1 = std::min(d, r0 + per);
-          loc.push_back(rp[r1] - rp[r0]);
-        }
-      }
-      int c = 0;
-      for (int v : loc)
-        if (v > c && action_cluster_smem_bytes(dmax, C, v) <= 200 * 1024) c = v;
-      if (action_cluster_smem_bytes(dmax, C, c) > 225 * 1024) continue;
-      const int got = action_cluster_size(C, dmax, c);
-      if (got == C) {
-        cluster = C;
-        cap = c;
-        break;
+    int c = 0;
+    for (size_t q = 0; q < nj; ++q) {
+      const std::vector<int>& rp = *rowptr_h[q];
+      const int d = jobs[q].d, per = (d + C - 1) / C;
+      for (int r = 0; r < C; ++r) {
+        const int r0 = std::min(d, r * per), r1 = std::min(d, r0 + per);
+        const int v = rp[r1] - rp[r0];
+        if (v > c && action_cluster_smem_bytes(S.dmax, C, v) <= 200 * 1024) c = v;
       }
     }
+    if (action_cluster_smem_bytes(S.dmax, C, c) > 225 * 1024) continue;
+    if (action_cluster_size(C, S.dmax, c) == C) {
+      S.cluster = C;
+      S.cap = c;
+      break;
+    }
   }
-  if (cluster == 1) {
+  if (S.cluster == 1) {
     // nonzeros held on chip: all of a lone job's if they fit in 200 KiB; in a
     // batch the largest count that keeps a CTA within 72 KiB (three per SM)
     const size_t budget = nj <= 152 ? 200 * 1024 : 72 * 1024;
     for (auto& j : jobs)
-      if (j.nnz > cap && action_smem_bytes(dmax, j.nnz) <= budget) cap = j.nnz;
+      if (j.nnz > S.cap && action_smem_bytes(S.dmax, j.nnz) <= budget) S.cap = j.nnz;
   }
-  size_t rec_total = 0, mat_total = 0;
+  S.rec_doubles = 0;
+  S.mat_doubles = 0;
   for (auto& j : jobs) {
-    rec_total += (size_t)j.N * ACTION_REC;
-    if (cluster > 1 || j.nnz > cap) mat_total += 2 * (size_t)j.nnz;
+    S.rec_doubles += (size_t)j.N * ACTION_REC;
+    if (S.cluster > 1 || j.nnz > S.cap) S.mat_doubles += 2 * (size_t)j.nnz;
   }
-  double *rec, *mat;
-  MG_TRY(ws(ctx, WS_ACT_REC, rec_total, &rec));
-  MG_TRY(ws(ctx, WS_ACT_MAT, std::max<size_t>(mat_total, 2), &mat));
-  std::vector<ActionJob> launch(nj);
+}
+// Launch-ordered records with their interval-record and matrix pointers set.
+void layout_action(const std::vector<ActionJob>& jobs, const ActionShape& S, double* rec, double* mat,
+                   std::vector<ActionJob>& launch) {
+  launch.resize(jobs.size());
   size_t ro = 0, mo = 0;
-  for (size_t q = 0; q < nj; ++q) {
-    ActionJob j = jobs[order[q]];
+  for (size_t q = 0; q < jobs.size(); ++q) {
+    ActionJob j = jobs[S.order[q]];
     j.cheb = rec + ro;
     ro += (size_t)j.N * ACTION_REC;
     j.abuf = nullptr;
-    if (cluster > 1 || j.nnz > cap) {
+    if (S.cluster > 1 || j.nnz > S.cap) {
       j.abuf = mat + mo;
       mo += 2 * (size_t)j.nnz;
     }
     launch[q] = j;
   }
+}
+// Runs the action path for `jobs` (records with the operator, coefficient and
+// state pointers set; rowptr_h[q] the host row offsets of job q) on the
+// context's stream with workspace from the context, uploads the records to
+// `jbuf` (device), reads them back and waits.  With per-launch timing on, the
+// chain is timed and its work (8 flops per pattern nonzero per operator
+// application) is added to the context's counters.
+int run_action(mg_ctx* ctx, std::vector<ActionJob>& jobs, const std::vector<const std::vector<int>*>& rowptr_h,
+               void* jbuf) {
+  const size_t nj = jobs.size();
+  ActionShape S;
+  shape_action(jobs, rowptr_h, S);
+  double *rec, *mat;
+  MG_TRY(ws(ctx, WS_ACT_REC, S.rec_doubles, &rec));
+  MG_TRY(ws(ctx, WS_ACT_MAT, std::max<size_t>(S.mat_doubles, 2), &mat));
+  std::vector<ActionJob> launch;
+  layout_action(jobs, S, rec, mat, launch);
   ActionJob* dev = reinterpret_cast<ActionJob*>(jbuf);
   MG_CUDA_TRY(cudaMemcpyAsync(dev, launch.data(), sizeof(ActionJob) * nj, cudaMemcpyHostToDevice, ctx->stream));
   int e0 = -1, e1 = -1;
   if (ctx->timing) MG_TRY(timing_mark(ctx, &e0));
-  MG_TRY(launch_action_chain((int)nj, dev, dmax, nmax, cap, cluster, ctx->stream));
+  MG_TRY(launch_action_chain((int)nj, dev, S.dmax, S.nmax, S.cap, S.cluster, ctx->stream));
   if (ctx->timing) {
     MG_TRY(timing_mark(ctx, &e1));
     ctx->ev_pending.emplace_back(e0, e1);
@@ -717,9 +748,9 @@ int run_action(mg_ctx* ctx, std::vector<ActionJob>& jobs, const std::vector<cons
   }
   MG_CUDA_TRY(cudaMemcpyAsync(launch.data(), dev, sizeof(ActionJob) * nj, cudaMemcpyDeviceToHost, ctx->stream));
   MG_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
-  ctx->last_action_cluster = cluster;
+  ctx->last_action_cluster = S.cluster;
   for (size_t q = 0; q < nj; ++q) {
-    jobs[order[q]] = launch[q];
+    jobs[S.order[q]] = launch[q];
     if (ctx->timing) ctx->t_flops += 8.0 * (double)launch[q].nnz * (double)launch[q].matvecs;
   }
   return MG_OK;
@@ -1664,13 +1695,28 @@ struct SJob {
   int dp = 0, prec = 0, L = 6;
   double* out = nullptr;
   cudaMemcpyKind out_kind = cudaMemcpyDeviceToDevice;
-  std::vector<void*> owned;     // device buffers of this job
+  std::vector<void*> owned;     // device buffers of this job (stream-ordered allocations)
   size_t bytes = 0;
   cudaEvent_t ready = nullptr;  // uploads finished
   clk::time_point t_submit, t_start, t_done;
   bool started = false, finished = false;
   int status = MG_OK;
+  // action-based state job (MG_FLAG_STATE_ACTION): its record and host row offsets
+  bool action = false;
+  ActionJob arec{};
+  std::vector<int> rowptr_h;
 };
+
+// Action jobs launched together on one of the server's action streams.
+struct SActionGroup {
+  std::vector<SJob*> jobs;
+  int slot = 0;                   // index of the action stream
+  cudaEvent_t done = nullptr;
+  void* mem = nullptr;            // interval records, off-chip matrices, job records
+  std::vector<ActionJob> launch;  // launch-ordered records (kept until completion)
+  ActionShape shape;
+};
+constexpr int SERVER_ACTION_STREAMS = 4;
 
 }  // namespace
 
@@ -1683,6 +1729,9 @@ struct mg_server {
   std::condition_variable cv, done_cv;
   std::deque<SJob*> pending;
   std::vector<SJob*> active;
+  std::deque<SJob*> apending;     // admitted action jobs not yet launched
+  cudaStream_t astream[SERVER_ACTION_STREAMS] = {};
+  bool astream_busy[SERVER_ACTION_STREAMS] = {};
   std::map<uint64_t, SJob*> jobs;
   std::thread worker;
   bool stop = false;
@@ -1699,8 +1748,10 @@ struct mg_server {
 
 namespace {
 
-void free_job_memory(SJob* j) {
-  for (void* q : j->owned) cudaFree(q);
+// Stream-ordered release after the work already queued on `s`: no device-wide
+// synchronisation, so long action chains in flight do not stall the worker.
+void free_job_memory(SJob* j, cudaStream_t s) {
+  for (void* q : j->owned) cudaFreeAsync(q, s);
   j->owned.clear();
   if (j->ready) cudaEventDestroy(j->ready);
   j->ready = nullptr;
@@ -1717,15 +1768,93 @@ void finish_job(mg_server* srv, SJob* j, int status) {
   srv->done_cv.notify_all();
 }
 
+// Launches every job of `g` (uploads done on the upload stream) on its action
+// stream: records, bounds kernel, chain kernel, completion event.
+int launch_action_group(mg_server* srv, SActionGroup& g) {
+  cudaStream_t s = srv->astream[g.slot];
+  std::vector<ActionJob> recs;
+  std::vector<const std::vector<int>*> rps;
+  for (SJob* j : g.jobs) {
+    MG_CUDA_TRY(cudaStreamWaitEvent(s, j->ready, 0));
+    recs.push_back(j->arec);
+    rps.push_back(&j->rowptr_h);
+  }
+  shape_action(recs, rps, g.shape);
+  const size_t rec_b = sizeof(double) * g.shape.rec_doubles, mat_b = sizeof(double) * g.shape.mat_doubles;
+  const size_t job_b = sizeof(ActionJob) * recs.size();
+  if (cudaMallocAsync(&g.mem, rec_b + mat_b + job_b + 256, s) != cudaSuccess) {
+    cudaGetLastError();
+    g.mem = nullptr;
+    set_last_message("device allocation of %zu bytes failed (action launch)", rec_b + mat_b + job_b);
+    return MG_ENOMEM;
+  }
+  char* base = reinterpret_cast<char*>(g.mem);
+  double* rec = reinterpret_cast<double*>(base);
+  double* mat = reinterpret_cast<double*>(base + rec_b);
+  ActionJob* dev = reinterpret_cast<ActionJob*>(base + ((rec_b + mat_b + 255) / 256) * 256);
+  layout_action(recs, g.shape, rec, mat, g.launch);
+  MG_CUDA_TRY(cudaMemcpyAsync(dev, g.launch.data(), job_b, cudaMemcpyHostToDevice, s));
+  MG_TRY(launch_action_chain((int)recs.size(), dev, g.shape.dmax, g.shape.nmax, g.shape.cap, g.shape.cluster, s));
+  MG_CUDA_TRY(cudaEventCreateWithFlags(&g.done, cudaEventDisableTiming));
+  MG_CUDA_TRY(cudaEventRecord(g.done, s));
+  return MG_OK;
+}
+
+// After g.done: reads the job records back (the stream is idle, so the copies
+// are immediate), writes each job's state to its output, releases the memory
+// and completes the jobs.  `rc` != MG_OK fails every job of the group.
+void complete_action_group(mg_server* srv, SActionGroup& g, int rc) {
+  cudaStream_t s = srv->astream[g.slot];
+  if (rc == MG_OK && cudaStreamSynchronize(s) != cudaSuccess) rc = MG_ECUDA;
+  const size_t rec_b = sizeof(double) * g.shape.rec_doubles, mat_b = sizeof(double) * g.shape.mat_doubles;
+  if (rc == MG_OK && g.mem) {
+    const char* dev = reinterpret_cast<const char*>(g.mem) + ((rec_b + mat_b + 255) / 256) * 256;
+    if (cudaMemcpy(g.launch.data(), dev, sizeof(ActionJob) * g.launch.size(), cudaMemcpyDeviceToHost) !=
+        cudaSuccess)
+      rc = MG_ECUDA;
+  }
+  std::vector<int> st(g.jobs.size(), rc);
+  for (size_t q = 0; q < g.launch.size() && rc == MG_OK; ++q) {
+    SJob* j = g.jobs[g.shape.order[q]];
+    st[g.shape.order[q]] = g.launch[q].status;
+    if (g.launch[q].status == MG_OK &&
+        cudaMemcpyAsync(j->out, j->arec.psi, sizeof(double) * 2 * j->b.d, j->out_kind, s) != cudaSuccess)
+      st[g.shape.order[q]] = MG_ECUDA;
+  }
+  cudaStreamSynchronize(s);
+  if (g.mem) cudaFreeAsync(g.mem, s);
+  g.mem = nullptr;
+  if (g.done) cudaEventDestroy(g.done);
+  g.done = nullptr;
+  for (size_t q = 0; q < g.jobs.size(); ++q) {
+    free_job_memory(g.jobs[q], s);
+    finish_job(srv, g.jobs[q], st[q]);
+  }
+  std::lock_guard<std::mutex> lock(srv->mu);
+  srv->astream_busy[g.slot] = false;
+}
+
+
 void server_loop(mg_server* srv) {
   mg_ctx* ctx = srv->ctx;
   cudaSetDevice(ctx->device);
+  std::vector<SActionGroup*> inflight;   // action launches on the action streams
   for (;;) {
     std::vector<SJob*> group;
+    SActionGroup* ag = nullptr;
     {
       std::unique_lock<std::mutex> lock(srv->mu);
-      srv->cv.wait(lock, [&] { return srv->stop || !srv->pending.empty() || !srv->active.empty(); });
-      if (srv->stop && srv->pending.empty() && srv->active.empty()) return;
+      const auto work = [&] {
+        return srv->stop || !srv->pending.empty() || !srv->active.empty() || !srv->apending.empty();
+      };
+      if (inflight.empty()) {
+        srv->cv.wait(lock, work);
+      } else if (!work()) {
+        // only action launches in flight: poll them every 100 us
+        srv->cv.wait_for(lock, std::chrono::microseconds(100), work);
+      }
+      if (srv->stop && srv->pending.empty() && srv->active.empty() && srv->apending.empty() && inflight.empty())
+        return;
       // continuous admission: every request that arrived joins at this chunk boundary
       while (!srv->pending.empty()) {
         SJob* j = srv->pending.front();
@@ -1734,12 +1863,52 @@ void server_loop(mg_server* srv) {
         j->started = true;
         srv->active.push_back(j);
       }
+      // every admitted action job goes out in one launch on a free action stream
+      if (!srv->apending.empty()) {
+        for (int q = 0; q < SERVER_ACTION_STREAMS; ++q)
+          if (!srv->astream_busy[q]) {
+            ag = new SActionGroup();
+            ag->slot = q;
+            srv->astream_busy[q] = true;
+            while (!srv->apending.empty() && ag->jobs.size() < 4096) {
+              SJob* j = srv->apending.front();
+              srv->apending.pop_front();
+              j->t_start = clk::now();
+              j->started = true;
+              ag->jobs.push_back(j);
+            }
+            break;
+          }
+      }
       // the oldest job picks the group; its peers with the same key share the chunk
-      SJob* head = srv->active.front();
-      for (SJob* j : srv->active)
-        if (j->dp == head->dp && j->prec == head->prec && j->L == head->L && (int)group.size() < srv->seg_cap)
-          group.push_back(j);
+      if (!srv->active.empty()) {
+        SJob* head = srv->active.front();
+        for (SJob* j : srv->active)
+          if (j->dp == head->dp && j->prec == head->prec && j->L == head->L && (int)group.size() < srv->seg_cap)
+            group.push_back(j);
+      }
     }
+    if (ag) {
+      const int rc = launch_action_group(srv, *ag);
+      if (rc != MG_OK) {
+        complete_action_group(srv, *ag, rc);
+        delete ag;
+      } else {
+        inflight.push_back(ag);
+      }
+    }
+    for (size_t q = 0; q < inflight.size();) {
+      const cudaError_t e = cudaEventQuery(inflight[q]->done);
+      if (e == cudaErrorNotReady) {
+        ++q;
+        continue;
+      }
+      if (e != cudaSuccess) cudaGetLastError();
+      complete_action_group(srv, *inflight[q], e == cudaSuccess ? MG_OK : MG_ECUDA);
+      delete inflight[q];
+      inflight.erase(inflight.begin() + q);
+    }
+    if (group.empty()) continue;
     const auto t0 = clk::now();
     Engine eng{ctx, group[0]->dp, group[0]->prec, group[0]->L};
     int rc = MG_OK;
@@ -1766,7 +1935,7 @@ void server_loop(mg_server* srv) {
       if (jr == MG_OK) jr = write_job_output(ctx, eng, j->b, j->out, j->out_kind);
       if (jr == MG_OK && j->b.failed) jr = MG_ENONFINITE;
       cudaStreamSynchronize(ctx->stream);
-      free_job_memory(j);
+      free_job_memory(j, ctx->stream);
       {
         std::lock_guard<std::mutex> lock(srv->mu);
         srv->active.erase(std::find(srv->active.begin(), srv->active.end(), j));
@@ -1788,10 +1957,15 @@ int mg_server_create(mg_ctx* ctx, size_t mem_budget_bytes, int quantum_intervals
   srv->ctx = ctx;
   srv->budget = mem_budget_bytes;
   srv->quantum = quantum_intervals;
-  if (cudaStreamCreateWithFlags(&srv->upload, cudaStreamNonBlocking) != cudaSuccess ||
+  bool streams_ok = true;
+  for (int q = 0; q < SERVER_ACTION_STREAMS; ++q)
+    streams_ok = streams_ok && cudaStreamCreateWithFlags(&srv->astream[q], cudaStreamNonBlocking) == cudaSuccess;
+  if (!streams_ok || cudaStreamCreateWithFlags(&srv->upload, cudaStreamNonBlocking) != cudaSuccess ||
       cudaMalloc(&srv->segs_dev, sizeof(ChainSeg) * srv->seg_cap) != cudaSuccess ||
       cudaMalloc(&srv->psi_dev, sizeof(double*) * srv->seg_cap) != cudaSuccess) {
     cudaGetLastError();
+    for (int q = 0; q < SERVER_ACTION_STREAMS; ++q)
+      if (srv->astream[q]) cudaStreamDestroy(srv->astream[q]);
     if (srv->upload) cudaStreamDestroy(srv->upload);
     cudaFree(srv->segs_dev);
     cudaFree(srv->psi_dev);
@@ -1803,6 +1977,125 @@ int mg_server_create(mg_ctx* ctx, size_t mem_budget_bytes, int quantum_intervals
   return MG_OK;
 }
 
+namespace {
+// Admission and upload of an action-based state job: the host builds the
+// operators' CSR (from host memory or a device-to-host copy), the coefficients
+// are formed on the device, and the job waits for the next action launch.
+int submit_action(mg_server* srv, const mg_job* job, uint64_t* job_id) {
+  const int d = job->d, K = job->K, N = job->N, P = job->P;
+  MG_TRY(check_action_limits(d, 1 + K));
+  MG_CUDA_TRY(cudaSetDevice(srv->ctx->device));
+  const bool host = (job->flags & MG_FLAG_HOST_PTRS) != 0;
+  const size_t dd2 = 2 * (size_t)d * d;
+  std::vector<double> dense((size_t)(1 + K) * dd2);
+  if (host) {
+    std::memcpy(dense.data(), job->H0, sizeof(double) * dd2);
+    if (K > 0) std::memcpy(dense.data() + dd2, job->Hk, sizeof(double) * dd2 * K);
+  } else {
+    MG_CUDA_TRY(cudaMemcpy(dense.data(), job->H0, sizeof(double) * dd2, cudaMemcpyDeviceToHost));
+    if (K > 0) MG_CUDA_TRY(cudaMemcpy(dense.data() + dd2, job->Hk, sizeof(double) * dd2 * K, cudaMemcpyDeviceToHost));
+  }
+  CsrHost h;
+  build_csr_host(dense.data(), d, 1 + K, h);
+  const size_t nnz = h.col.size();
+  const size_t csr_bytes = sizeof(int) * (h.rowptr.size() + h.col.size() + h.diag.size()) + sizeof(double) * h.val.size();
+  const size_t c_bytes = sizeof(double) * std::max<size_t>(1, (size_t)N * K);
+  const size_t tmp_bytes = sizeof(double) * ((size_t)N * P * K + P);
+  const size_t bytes = csr_bytes + c_bytes + sizeof(double) * 2 * d + sizeof(double) * ACTION_REC * (size_t)N +
+                       sizeof(double) * 2 * nnz + tmp_bytes;
+  {
+    std::lock_guard<std::mutex> lock(srv->mu);
+    if (srv->used + bytes > srv->budget) {
+      set_last_message("job of %zu bytes not admissible now (%zu of %zu bytes in use)", bytes, srv->used, srv->budget);
+      return MG_EAGAIN;
+    }
+    srv->used += bytes;
+  }
+  SJob* j = new SJob();
+  j->action = true;
+  j->bytes = bytes;
+  j->out = job->out;
+  j->out_kind = host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+  j->b.output = MG_OUT_STATE;
+  j->b.d = d;
+  j->b.K = K;
+  j->b.N = N;
+  j->b.dt = job->dt;
+  const cudaMemcpyKind h2d = host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+  cudaStream_t s = srv->upload;
+  auto dmalloc = [&](size_t n, void** ptr) -> int {
+    if (cudaMallocAsync(ptr, std::max<size_t>(n, 16), s) != cudaSuccess) {
+      cudaGetLastError();
+      set_last_message("device allocation of %zu bytes failed (job upload)", n);
+      return MG_ENOMEM;
+    }
+    j->owned.push_back(*ptr);
+    return MG_OK;
+  };
+  auto upload = [&]() -> int {
+    void *rp, *col, *dg, *val, *c, *psi, *tmp;
+    MG_TRY(dmalloc(sizeof(int) * h.rowptr.size(), &rp));
+    MG_TRY(dmalloc(sizeof(int) * h.col.size(), &col));
+    MG_TRY(dmalloc(sizeof(int) * h.diag.size(), &dg));
+    MG_TRY(dmalloc(sizeof(double) * h.val.size(), &val));
+    MG_TRY(dmalloc(c_bytes, &c));
+    MG_TRY(dmalloc(sizeof(double) * 2 * d, &psi));
+    if (cudaMallocAsync(&tmp, tmp_bytes, s) != cudaSuccess) { cudaGetLastError(); return MG_ENOMEM; }
+    double* Tw = reinterpret_cast<double*>(tmp);
+    double* Ts = Tw + P;
+    int r = MG_OK;
+    if (cudaMemcpyAsync(rp, h.rowptr.data(), sizeof(int) * h.rowptr.size(), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(col, h.col.data(), sizeof(int) * h.col.size(), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(dg, h.diag.data(), sizeof(int) * h.diag.size(), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(val, h.val.data(), sizeof(double) * h.val.size(), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(Tw, job->w, sizeof(double) * P, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        (K > 0 && cudaMemcpyAsync(Ts, job->samples, sizeof(double) * (size_t)N * P * K, h2d, s) != cudaSuccess) ||
+        cudaMemcpyAsync(psi, job->in, sizeof(double) * 2 * d, h2d, s) != cudaSuccess)
+      r = MG_ECUDA;
+    if (r == MG_OK && K > 0) r = launch_coefficients(N, P, K, job->dt, Tw, Ts, reinterpret_cast<double*>(c), s);
+    cudaFreeAsync(tmp, s);
+    if (cudaStreamSynchronize(s) != cudaSuccess && r == MG_OK) r = MG_ECUDA;
+    if (r == MG_OK && cudaEventCreateWithFlags(&j->ready, cudaEventDisableTiming) != cudaSuccess) r = MG_ECUDA;
+    if (r == MG_OK && cudaEventRecord(j->ready, s) != cudaSuccess) r = MG_ECUDA;
+    ActionJob& a = j->arec;
+    a = ActionJob{};
+    a.d = d;
+    a.K = K;
+    a.N = N;
+    a.nnz = (int)nnz;
+    a.dt = job->dt;
+    a.rowptr = reinterpret_cast<const int*>(rp);
+    a.col = reinterpret_cast<const int*>(col);
+    a.diag = reinterpret_cast<const int*>(dg);
+    a.val = reinterpret_cast<const double*>(val);
+    a.c = reinterpret_cast<const double*>(c);
+    a.psi = reinterpret_cast<double*>(psi);
+    return r;
+  };
+  const int rc = upload();
+  if (rc != MG_OK) {
+    free_job_memory(j, s);
+    cudaStreamSynchronize(s);
+    std::lock_guard<std::mutex> lock(srv->mu);
+    srv->used -= bytes;
+    delete j;
+    return rc;
+  }
+  j->rowptr_h = std::move(h.rowptr);
+  {
+    std::lock_guard<std::mutex> lock(srv->mu);
+    j->id = srv->next_id++;
+    j->t_submit = clk::now();
+    if (!srv->any) { srv->any = true; srv->t_first = j->t_submit; }
+    srv->jobs[j->id] = j;
+    srv->apending.push_back(j);
+    *job_id = j->id;
+  }
+  srv->cv.notify_all();
+  return MG_OK;
+}
+}  // namespace
+
 int mg_submit(mg_server* srv, const mg_job* job, uint64_t* job_id) {
   if (!srv || !job || !job_id) return MG_EINVAL;
   const int d = job->d, K = job->K, N = job->N, P = job->P;
@@ -1811,10 +2104,8 @@ int mg_submit(mg_server* srv, const mg_job* job, uint64_t* job_id) {
       (job->output != MG_OUT_STATE && job->output != MG_OUT_PROPAGATOR) ||
       (job->output == MG_OUT_STATE && !job->in) || (job->output == MG_OUT_PROPAGATOR && job->in))
     return MG_EINVAL;
+  if (job->output == MG_OUT_STATE && (job->flags & MG_FLAG_STATE_ACTION)) return submit_action(srv, job, job_id);
   MG_TRY(validate_prec(job->precision, job->slices));
-  if (job->output == MG_OUT_STATE && round_dim(d) > 256 && d > 256) {
-    // large-d states run one chain launch per interval; allowed
-  }
   const int dp = round_dim(d);
   const long long md = mat_doubles(dp);
   const size_t op_bytes = sizeof(double) * md * (1 + K);
@@ -1848,7 +2139,7 @@ int mg_submit(mg_server* srv, const mg_job* job, uint64_t* job_id) {
   int rc = MG_OK;
   cudaStream_t s = srv->upload;
   auto dmalloc = [&](size_t n, void** ptr) -> int {
-    if (cudaMalloc(ptr, n) != cudaSuccess) {
+    if (cudaMallocAsync(ptr, n, s) != cudaSuccess) {
       cudaGetLastError();
       set_last_message("device allocation of %zu bytes failed (job upload)", n);
       return MG_ENOMEM;
@@ -1862,7 +2153,7 @@ int mg_submit(mg_server* srv, const mg_job* job, uint64_t* job_id) {
     MG_TRY(dmalloc(op_bytes, &ops));
     MG_TRY(dmalloc(c_bytes, &c));
     MG_TRY(dmalloc(st_bytes, &st));
-    if (cudaMalloc(&tmp, tmp_bytes) != cudaSuccess) { cudaGetLastError(); return MG_ENOMEM; }
+    if (cudaMallocAsync(&tmp, tmp_bytes, s) != cudaSuccess) { cudaGetLastError(); return MG_ENOMEM; }
     double* T = reinterpret_cast<double*>(tmp);
     double* Tw = T + mat_doubles(d) * (1 + K);
     double* Ts = Tw + P;
@@ -1886,15 +2177,16 @@ int mg_submit(mg_server* srv, const mg_job* job, uint64_t* job_id) {
         r = MG_ECUDA;
       b.init = true;
     }
+    cudaFreeAsync(tmp, s);
     if (cudaStreamSynchronize(s) != cudaSuccess && r == MG_OK) r = MG_ECUDA;
-    cudaFree(tmp);
     if (r == MG_OK && cudaEventCreateWithFlags(&j->ready, cudaEventDisableTiming) != cudaSuccess) r = MG_ECUDA;
     if (r == MG_OK && cudaEventRecord(j->ready, s) != cudaSuccess) r = MG_ECUDA;
     return r;
   };
   rc = upload();
   if (rc != MG_OK) {
-    free_job_memory(j);
+    free_job_memory(j, s);
+    cudaStreamSynchronize(s);
     std::lock_guard<std::mutex> lock(srv->mu);
     srv->used -= bytes;
     delete j;
@@ -1967,11 +2259,13 @@ int mg_server_destroy(mg_server* srv) {
   srv->cv.notify_all();
   if (srv->worker.joinable()) srv->worker.join();
   for (auto& kv : srv->jobs) {
-    free_job_memory(kv.second);
+    free_job_memory(kv.second, srv->upload);
     delete kv.second;
   }
+  cudaStreamSynchronize(srv->upload);
   cudaFree(srv->segs_dev);
   cudaFree(srv->psi_dev);
+  for (int q = 0; q < SERVER_ACTION_STREAMS; ++q) cudaStreamDestroy(srv->astream[q]);
   cudaStreamDestroy(srv->upload);
   delete srv;
   return MG_OK;

@@ -253,15 +253,16 @@ class Server:
         self._keep = {}
 
     def submit(self, H0, Hk, N, P, t0, dt, w, samples, output, inp, out, precision=MG_PREC_SPLIT, slices=6,
-               host=False):
-        """Returns the job id, or None when the job is not admissible now (MG_EAGAIN)."""
+               host=False, action=False):
+        """Returns the job id, or None when the job is not admissible now (MG_EAGAIN).
+        action=True runs a state job on the action-based path (MG_FLAG_STATE_ACTION)."""
         import numpy as np
         w = np.ascontiguousarray(w, dtype=np.float64)
         j = mg_job(int(H0.shape[0]), int(Hk.shape[0]) if Hk is not None else 0, H0.data_ptr(),
                    Hk.data_ptr() if Hk is not None else None, int(N), int(P), float(t0), float(dt),
                    w.ctypes.data_as(ctypes.c_void_p), samples.data_ptr() if samples is not None else None,
                    int(output), inp.data_ptr() if inp is not None else None, out.data_ptr(), int(precision),
-                   int(slices), MG_FLAG_HOST_PTRS if host else 0)
+                   int(slices), (MG_FLAG_HOST_PTRS if host else 0) | (MG_FLAG_STATE_ACTION if action else 0))
         jid = ctypes.c_uint64()
         r = load().mg_submit(self.h, ctypes.byref(j), ctypes.byref(jid))
         if r == MG_EAGAIN:

@@ -29,7 +29,7 @@ def make_jobs(seed=3, n=10):
     return jobs
 
 
-def submit(srv, wl, out, precision=M.MG_PREC_SPLIT, host=False):
+def submit(srv, wl, out, precision=M.MG_PREC_SPLIT, host=False, action=False):
     samples, w = M.node_samples(wl)
     if host:
         H0, Hk, S = (torch.from_numpy(np.ascontiguousarray(x)) for x in (wl.H0, wl.Hk, samples))
@@ -38,7 +38,8 @@ def submit(srv, wl, out, precision=M.MG_PREC_SPLIT, host=False):
         H0, Hk, S = cuda(wl.H0), cuda(wl.Hk), cuda(samples)
         inp = cuda(wl.psi0) if wl.psi0 is not None else None
     kind = M.MG_OUT_STATE if wl.psi0 is not None else M.MG_OUT_PROPAGATOR
-    jid = srv.submit(H0, Hk, wl.N, wl.P, wl.t0, wl.dt, w, S, kind, inp, out, precision, 6, host=host)
+    jid = srv.submit(H0, Hk, wl.N, wl.P, wl.t0, wl.dt, w, S, kind, inp, out, precision, 6, host=host,
+                     action=action)
     return jid, (H0, Hk, S, inp)
 
 
@@ -115,5 +116,37 @@ def test_admission_by_memory_budget_and_wait_timeout():
     first = srv.wait(jid2, 0.0)    # None (MG_ETIMEOUT) while it runs; the job keeps running
     rep = first if first is not None else srv.wait(jid2, 120.0)
     assert rep is not None and rep["status"] == 0
+    srv.close()
+    ctx.close()
+
+
+def test_served_action_jobs_match_oracle_next_to_dense_jobs():
+    # action-flagged state jobs (small ones batched per CTA, a d = 729 one as a
+    # cluster) run on the action streams while dense jobs advance chunk by chunk
+    ctx = M.Context(0)
+    srv = M.Server(ctx, mem_budget_bytes=8 << 30, quantum_intervals=8)
+    action_jobs = [W.transmon_resonator(nt=3, nr=5, N=30, name="a1"), W.config(0, N=60),
+                   W.transmon_chain(n_sites=6, levels=3, J=0.01, seed=1, omega0_max=0.05, T=1.0, sigma=0.3, N=6,
+                                    P=16, unitary=False, name="chain729_state")]
+    dense_jobs = [W.transmon_resonator(nt=2, nr=9, N=40, name="d1", unitary=True), W.config(0, N=50)]
+    outs, ids, keep, refs = [], [], [], []
+    for i, wl in enumerate(action_jobs + dense_jobs):
+        host = i == 1
+        o = out_for(wl, "cpu" if host else "cuda")
+        if host:
+            o = o.pin_memory()
+        jid, k = submit(srv, wl, o, precision=M.MG_PREC_FP64, host=host, action=wl in action_jobs)
+        assert jid is not None
+        outs.append(o)
+        ids.append(jid)
+        keep.append(k)
+        refs.append(oracle.evolve_workload(wl))
+    for j in ids:
+        rep = srv.wait(j, 120.0)
+        assert rep is not None and rep["status"] == 0
+    for wl, o, ref in zip(action_jobs + dense_jobs, outs, refs):
+        assert np.abs(o.cpu().numpy() - ref).max() <= 1e-11, wl.name
+    st = srv.stats()
+    assert st["completed"] == len(ids)
     srv.close()
     ctx.close()
