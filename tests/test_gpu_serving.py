@@ -135,7 +135,7 @@ def test_served_action_jobs_match_oracle_next_to_dense_jobs():
         o = out_for(wl, "cpu" if host else "cuda")
         if host:
             o = o.pin_memory()
-        jid, k = submit(srv, wl, o, precision=M.MG_PREC_FP64, host=host, action=wl in action_jobs)
+        jid, k = submit(srv, wl, o, precision=M.MG_PREC_FP64, host=host, action=i < len(action_jobs))
         assert jid is not None
         outs.append(o)
         ids.append(jid)
