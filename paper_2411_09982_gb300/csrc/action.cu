@@ -33,10 +33,11 @@
 // interval matrix and its pattern in shared memory.  The chain runs either as
 // one CTA per job (batches: every SM busy with its own jobs) or as one thread
 // block cluster of up to 16 CTAs per job (a few large jobs): each CTA owns a
-// contiguous block of rows and keeps full copies of the two recurrence vectors,
-// writes its new rows into every CTA of the cluster through distributed shared
-// memory after each operator application, and the cluster barrier that follows
-// orders them before the next application reads.
+// contiguous block of rows and keeps copies of the two recurrence vectors,
+// writes each new row through distributed shared memory into the CTAs whose
+// nonzeros read it (a per-row mask built on the host: for banded operators only
+// the neighbouring blocks) after each operator application, and the cluster
+// barrier that follows orders them before the next application reads.
 #include "common.cuh"
 
 #include <cooperative_groups.h>
@@ -371,7 +372,7 @@ action_chain_cluster_kernel(ActionJob* __restrict__ jobs, int dmax, int cap_loc)
       for (int li = threadIdx.x; li < nr; li += blockDim.x) {
         const double2 v = acc[li];
         acc[li] = make_double2(Jk[0] * v.x, Jk[0] * v.y);
-        for (int q = 0; q < C; ++q) cl.map_shared_rank(vx, q)[r0 + li] = v;
+        for (unsigned m = J.sendmask[r0 + li]; m; m &= m - 1) cl.map_shared_rank(vx, __ffs(m) - 1)[r0 + li] = v;
       }
       cl.sync();
       for (int k = 1; k <= kt; ++k) {
@@ -396,7 +397,7 @@ action_chain_cluster_kernel(ActionJob* __restrict__ jobs, int dmax, int cap_loc)
             t.y -= o.y;
           }
           acc[li] = add_term(acc[li], t, twoJ, k);
-          for (int q = 0; q < C; ++q) cl.map_shared_rank(old, q)[i] = t;
+          for (unsigned m = J.sendmask[i]; m; m &= m - 1) cl.map_shared_rank(old, __ffs(m) - 1)[i] = t;
         }
         cl.sync();
       }

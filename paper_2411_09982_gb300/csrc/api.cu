@@ -102,7 +102,8 @@ struct mg_plan {
   int* csr_diag = nullptr;       // position of each row's diagonal entry
   double* csr_val = nullptr;     // (1 + K) x nnz complex, operator-major
   long long csr_nnz = 0;
-  std::vector<int> csr_rowptr_h;  // host copy of the row offsets (cluster partitioning)
+  std::vector<int> csr_rowptr_h;  // host copies of the pattern (cluster partitioning, send masks)
+  std::vector<int> csr_col_h;
 };
 
 namespace {
@@ -113,7 +114,7 @@ enum Slot {
   WS_ABUF, WS_BBUF0, WS_BBUF1,
   WS_TAU, WS_NORM, WS_ACC, WS_ACC2, WS_NS_G, WS_NS_H, WS_VEC,
   WS_TREE0, WS_TREE1, WS_UBUF, WS_NS_Z, WS_OUT,
-  WS_ACT_REC, WS_ACT_MAT,   // action path: interval records, interval matrices off chip
+  WS_ACT_REC,   // action path: interval records, off-chip interval matrices, send masks, job records
   WS_COUNT
 };
 
@@ -622,6 +623,7 @@ int ensure_csr(mg_plan* p) {
   MG_TRY(up(reinterpret_cast<void**>(&p->csr_val), h.val.data(), sizeof(double) * h.val.size()));
   p->csr_nnz = (long long)h.col.size();
   p->csr_rowptr_h = h.rowptr;
+  p->csr_col_h = h.col;
   p->csr_ok = true;
   return MG_OK;
 }
@@ -641,19 +643,24 @@ ActionJob action_job(mg_plan* p, double* psi) {
   j.psi = psi;
   return j;
 }
+// Host copies of one job's CSR pattern.
+struct CsrRef {
+  const std::vector<int>* rowptr;
+  const std::vector<int>* col;
+};
 // Launch shape of one action launch: job order (heaviest first), the largest
 // d and N, the cluster size (1: one CTA per job) and the nonzeros held on chip,
 // and the workspace it needs (interval records; interval matrices off chip).
 struct ActionShape {
   std::vector<size_t> order;
   int dmax = 1, nmax = 0, cluster = 1, cap = 0;
-  size_t rec_doubles = 0, mat_doubles = 0;
+  size_t rec_doubles = 0, mat_doubles = 0, mask_words = 0;
+  std::vector<uint16_t> masks;   // launch order, d per job (cluster variant)
 };
 // A few large jobs run as one thread block cluster each (up to 16 CTAs, about
 // 1024 nonzeros per CTA or more, every job's cluster resident at once);
 // otherwise one CTA per job.
-void shape_action(const std::vector<ActionJob>& jobs, const std::vector<const std::vector<int>*>& rowptr_h,
-                  ActionShape& S) {
+void shape_action(const std::vector<ActionJob>& jobs, const std::vector<CsrRef>& pat, ActionShape& S) {
   const size_t nj = jobs.size();
   S.order.resize(nj);
   for (size_t q = 0; q < nj; ++q) S.order[q] = q;
@@ -667,14 +674,14 @@ void shape_action(const std::vector<ActionJob>& jobs, const std::vector<const st
     nnz_max = std::max(nnz_max, j.nnz);
   }
   int want = 1;
-  while (want < 16 && 2 * want * 1024 <= nnz_max && (size_t)(2 * want) * nj <= 152) want *= 2;
+  while (want < 16 && 2 * want * 512 <= nnz_max && (size_t)(2 * want) * nj <= 152) want *= 2;
   S.cluster = 1;
   S.cap = 0;
   for (int C = want; C >= 2; C >>= 1) {
     // own-row nonzeros held on chip: the largest count over the CTAs that fits
     int c = 0;
     for (size_t q = 0; q < nj; ++q) {
-      const std::vector<int>& rp = *rowptr_h[q];
+      const std::vector<int>& rp = *pat[q].rowptr;
       const int d = jobs[q].d, per = (d + C - 1) / C;
       for (int r = 0; r < C; ++r) {
         const int r0 = std::min(d, r * per), r1 = std::min(d, r0 + per);
@@ -698,16 +705,32 @@ void shape_action(const std::vector<ActionJob>& jobs, const std::vector<const st
   }
   S.rec_doubles = 0;
   S.mat_doubles = 0;
+  S.mask_words = 0;
   for (auto& j : jobs) {
     S.rec_doubles += (size_t)j.N * ACTION_REC;
     if (S.cluster > 1 || j.nnz > S.cap) S.mat_doubles += 2 * (size_t)j.nnz;
+    if (S.cluster > 1) S.mask_words += (size_t)j.d;
+  }
+  // send masks of the cluster variant: row j goes to every CTA with a nonzero in column j
+  S.masks.assign(S.mask_words, 0);
+  if (S.cluster > 1) {
+    size_t off = 0;
+    for (size_t q = 0; q < nj; ++q) {
+      const size_t jq = S.order[q];
+      const std::vector<int>& rp = *pat[jq].rowptr;
+      const std::vector<int>& col = *pat[jq].col;
+      const int d = jobs[jq].d, per = (d + S.cluster - 1) / S.cluster;
+      for (int i = 0; i < d; ++i)
+        for (int e = rp[i]; e < rp[i + 1]; ++e) S.masks[off + col[e]] |= (uint16_t)(1u << (i / per));
+      off += (size_t)d;
+    }
   }
 }
 // Launch-ordered records with their interval-record and matrix pointers set.
 void layout_action(const std::vector<ActionJob>& jobs, const ActionShape& S, double* rec, double* mat,
-                   std::vector<ActionJob>& launch) {
+                   uint16_t* masks, std::vector<ActionJob>& launch) {
   launch.resize(jobs.size());
-  size_t ro = 0, mo = 0;
+  size_t ro = 0, mo = 0, ko = 0;
   for (size_t q = 0; q < jobs.size(); ++q) {
     ActionJob j = jobs[S.order[q]];
     j.cheb = rec + ro;
@@ -717,8 +740,21 @@ void layout_action(const std::vector<ActionJob>& jobs, const ActionShape& S, dou
       j.abuf = mat + mo;
       mo += 2 * (size_t)j.nnz;
     }
+    j.sendmask = nullptr;
+    if (S.cluster > 1) {
+      j.sendmask = masks + ko;
+      ko += (size_t)j.d;
+    }
     launch[q] = j;
   }
+}
+// device bytes of one launch's workspace: records, matrices, masks, job records (256-byte aligned parts)
+size_t action_ws_bytes(const ActionShape& S, size_t nj, size_t* off_mat, size_t* off_mask, size_t* off_jobs) {
+  auto up = [](size_t b) { return (b + 255) / 256 * 256; };
+  *off_mat = up(sizeof(double) * S.rec_doubles);
+  *off_mask = *off_mat + up(sizeof(double) * S.mat_doubles);
+  *off_jobs = *off_mask + up(sizeof(uint16_t) * S.mask_words);
+  return *off_jobs + up(sizeof(ActionJob) * nj);
 }
 // Runs the action path for `jobs` (records with the operator, coefficient and
 // state pointers set; rowptr_h[q] the host row offsets of job q) on the
@@ -726,17 +762,21 @@ void layout_action(const std::vector<ActionJob>& jobs, const ActionShape& S, dou
 // `jbuf` (device), reads them back and waits.  With per-launch timing on, the
 // chain is timed and its work (8 flops per pattern nonzero per operator
 // application) is added to the context's counters.
-int run_action(mg_ctx* ctx, std::vector<ActionJob>& jobs, const std::vector<const std::vector<int>*>& rowptr_h,
-               void* jbuf) {
+int run_action(mg_ctx* ctx, std::vector<ActionJob>& jobs, const std::vector<CsrRef>& pat) {
   const size_t nj = jobs.size();
   ActionShape S;
-  shape_action(jobs, rowptr_h, S);
-  double *rec, *mat;
-  MG_TRY(ws(ctx, WS_ACT_REC, S.rec_doubles, &rec));
-  MG_TRY(ws(ctx, WS_ACT_MAT, std::max<size_t>(S.mat_doubles, 2), &mat));
+  shape_action(jobs, pat, S);
+  size_t o_mat, o_mask, o_jobs;
+  const size_t bytes = action_ws_bytes(S, nj, &o_mat, &o_mask, &o_jobs);
+  char* base;
+  MG_TRY(ws(ctx, WS_ACT_REC, bytes, &base));
   std::vector<ActionJob> launch;
-  layout_action(jobs, S, rec, mat, launch);
-  ActionJob* dev = reinterpret_cast<ActionJob*>(jbuf);
+  layout_action(jobs, S, reinterpret_cast<double*>(base), reinterpret_cast<double*>(base + o_mat),
+                reinterpret_cast<uint16_t*>(base + o_mask), launch);
+  ActionJob* dev = reinterpret_cast<ActionJob*>(base + o_jobs);
+  if (S.mask_words)
+    MG_CUDA_TRY(cudaMemcpyAsync(base + o_mask, S.masks.data(), sizeof(uint16_t) * S.mask_words,
+                                cudaMemcpyHostToDevice, ctx->stream));
   MG_CUDA_TRY(cudaMemcpyAsync(dev, launch.data(), sizeof(ActionJob) * nj, cudaMemcpyHostToDevice, ctx->stream));
   int e0 = -1, e1 = -1;
   if (ctx->timing) MG_TRY(timing_mark(ctx, &e0));
@@ -1256,9 +1296,7 @@ int mg_evolve(mg_plan* p, int output, const double* in, double* out, int reorth_
     // action-based: exp(-i Hbar_n) applied to the state by sparse Taylor steps
     MG_TRY(ensure_csr(p));
     std::vector<ActionJob> jv{action_job(p, ps.psi)};
-    double* jbuf;
-    MG_TRY(ws(ctx, WS_VEC, sizeof(ActionJob) / sizeof(double) + 1, &jbuf));
-    MG_TRY(run_action(ctx, jv, {&p->csr_rowptr_h}, jbuf));
+    MG_TRY(run_action(ctx, jv, {CsrRef{&p->csr_rowptr_h, &p->csr_col_h}}));
     const ActionJob& job = jv[0];
     if (job.status != MG_OK) {
       set_last_message("action-based state path stopped: %s", job.status == MG_ENONFINITE
@@ -1636,9 +1674,8 @@ int mg_evolve_batch(mg_ctx* ctx, int n, mg_plan* const* plans, const int* output
       const cudaMemcpyKind d2h = (flags & MG_FLAG_HOST_PTRS) ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
       size_t total = 0;
       for (int q : aidx) total += 2 * (size_t)plans[q]->d;
-      double *psis, *jb;
+      double* psis;
       MG_TRY(ws(ctx, WS_ACC, total, &psis));
-      MG_TRY(ws(ctx, WS_VEC, (sizeof(ActionJob) * aj.size()) / sizeof(double) + 1, &jb));
       size_t off = 0;
       for (size_t q = 0; q < aidx.size(); ++q) {
         mg_plan* p = plans[aidx[q]];
@@ -1648,9 +1685,9 @@ int mg_evolve_batch(mg_ctx* ctx, int n, mg_plan* const* plans, const int* output
         MG_CUDA_TRY(cudaMemcpyAsync(psis + off, in[aidx[q]], sizeof(double) * 2 * p->d, h2d, ctx->stream));
         off += 2 * (size_t)p->d;
       }
-      std::vector<const std::vector<int>*> rps;
-      for (size_t q = 0; q < aidx.size(); ++q) rps.push_back(&plans[aidx[q]]->csr_rowptr_h);
-      MG_TRY(run_action(ctx, aj, rps, jb));
+      std::vector<CsrRef> pat;
+      for (size_t q = 0; q < aidx.size(); ++q) pat.push_back({&plans[aidx[q]]->csr_rowptr_h, &plans[aidx[q]]->csr_col_h});
+      MG_TRY(run_action(ctx, aj, pat));
       off = 0;
       for (size_t q = 0; q < aidx.size(); ++q) {
         mg_plan* p = plans[aidx[q]];
@@ -1704,7 +1741,7 @@ struct SJob {
   // action-based state job (MG_FLAG_STATE_ACTION): its record and host row offsets
   bool action = false;
   ActionJob arec{};
-  std::vector<int> rowptr_h;
+  std::vector<int> rowptr_h, col_h;
 };
 
 // Action jobs launched together on one of the server's action streams.
@@ -1712,11 +1749,12 @@ struct SActionGroup {
   std::vector<SJob*> jobs;
   int slot = 0;                   // index of the action stream
   cudaEvent_t done = nullptr;
-  void* mem = nullptr;            // interval records, off-chip matrices, job records
+  void* mem = nullptr;            // interval records, off-chip matrices, send masks, job records
+  size_t off_jobs = 0;            // byte offset of the job records in mem
   std::vector<ActionJob> launch;  // launch-ordered records (kept until completion)
   ActionShape shape;
 };
-constexpr int SERVER_ACTION_STREAMS = 4;
+constexpr int SERVER_ACTION_STREAMS = 16;
 
 }  // namespace
 
@@ -1773,27 +1811,29 @@ void finish_job(mg_server* srv, SJob* j, int status) {
 int launch_action_group(mg_server* srv, SActionGroup& g) {
   cudaStream_t s = srv->astream[g.slot];
   std::vector<ActionJob> recs;
-  std::vector<const std::vector<int>*> rps;
+  std::vector<CsrRef> pat;
   for (SJob* j : g.jobs) {
     MG_CUDA_TRY(cudaStreamWaitEvent(s, j->ready, 0));
     recs.push_back(j->arec);
-    rps.push_back(&j->rowptr_h);
+    pat.push_back({&j->rowptr_h, &j->col_h});
   }
-  shape_action(recs, rps, g.shape);
-  const size_t rec_b = sizeof(double) * g.shape.rec_doubles, mat_b = sizeof(double) * g.shape.mat_doubles;
-  const size_t job_b = sizeof(ActionJob) * recs.size();
-  if (cudaMallocAsync(&g.mem, rec_b + mat_b + job_b + 256, s) != cudaSuccess) {
+  shape_action(recs, pat, g.shape);
+  size_t o_mat, o_mask;
+  const size_t bytes = action_ws_bytes(g.shape, recs.size(), &o_mat, &o_mask, &g.off_jobs);
+  if (cudaMallocAsync(&g.mem, bytes, s) != cudaSuccess) {
     cudaGetLastError();
     g.mem = nullptr;
-    set_last_message("device allocation of %zu bytes failed (action launch)", rec_b + mat_b + job_b);
+    set_last_message("device allocation of %zu bytes failed (action launch)", bytes);
     return MG_ENOMEM;
   }
   char* base = reinterpret_cast<char*>(g.mem);
-  double* rec = reinterpret_cast<double*>(base);
-  double* mat = reinterpret_cast<double*>(base + rec_b);
-  ActionJob* dev = reinterpret_cast<ActionJob*>(base + ((rec_b + mat_b + 255) / 256) * 256);
-  layout_action(recs, g.shape, rec, mat, g.launch);
-  MG_CUDA_TRY(cudaMemcpyAsync(dev, g.launch.data(), job_b, cudaMemcpyHostToDevice, s));
+  ActionJob* dev = reinterpret_cast<ActionJob*>(base + g.off_jobs);
+  layout_action(recs, g.shape, reinterpret_cast<double*>(base), reinterpret_cast<double*>(base + o_mat),
+                reinterpret_cast<uint16_t*>(base + o_mask), g.launch);
+  if (g.shape.mask_words)
+    MG_CUDA_TRY(cudaMemcpyAsync(base + o_mask, g.shape.masks.data(), sizeof(uint16_t) * g.shape.mask_words,
+                                cudaMemcpyHostToDevice, s));
+  MG_CUDA_TRY(cudaMemcpyAsync(dev, g.launch.data(), sizeof(ActionJob) * recs.size(), cudaMemcpyHostToDevice, s));
   MG_TRY(launch_action_chain((int)recs.size(), dev, g.shape.dmax, g.shape.nmax, g.shape.cap, g.shape.cluster, s));
   MG_CUDA_TRY(cudaEventCreateWithFlags(&g.done, cudaEventDisableTiming));
   MG_CUDA_TRY(cudaEventRecord(g.done, s));
@@ -1806,9 +1846,8 @@ int launch_action_group(mg_server* srv, SActionGroup& g) {
 void complete_action_group(mg_server* srv, SActionGroup& g, int rc) {
   cudaStream_t s = srv->astream[g.slot];
   if (rc == MG_OK && cudaStreamSynchronize(s) != cudaSuccess) rc = MG_ECUDA;
-  const size_t rec_b = sizeof(double) * g.shape.rec_doubles, mat_b = sizeof(double) * g.shape.mat_doubles;
   if (rc == MG_OK && g.mem) {
-    const char* dev = reinterpret_cast<const char*>(g.mem) + ((rec_b + mat_b + 255) / 256) * 256;
+    const char* dev = reinterpret_cast<const char*>(g.mem) + g.off_jobs;
     if (cudaMemcpy(g.launch.data(), dev, sizeof(ActionJob) * g.launch.size(), cudaMemcpyDeviceToHost) !=
         cudaSuccess)
       rc = MG_ECUDA;
@@ -1841,7 +1880,7 @@ void server_loop(mg_server* srv) {
   std::vector<SActionGroup*> inflight;   // action launches on the action streams
   for (;;) {
     std::vector<SJob*> group;
-    SActionGroup* ag = nullptr;
+    std::vector<SActionGroup*> ags;
     {
       std::unique_lock<std::mutex> lock(srv->mu);
       const auto work = [&] {
@@ -1863,22 +1902,27 @@ void server_loop(mg_server* srv) {
         j->started = true;
         srv->active.push_back(j);
       }
-      // every admitted action job goes out in one launch on a free action stream
+      // admitted action jobs spread over the free action streams (one launch
+      // each, so a job completes with its own launch, not with a longer one)
       if (!srv->apending.empty()) {
+        std::vector<int> free_slots;
         for (int q = 0; q < SERVER_ACTION_STREAMS; ++q)
-          if (!srv->astream_busy[q]) {
-            ag = new SActionGroup();
-            ag->slot = q;
-            srv->astream_busy[q] = true;
-            while (!srv->apending.empty() && ag->jobs.size() < 4096) {
-              SJob* j = srv->apending.front();
-              srv->apending.pop_front();
-              j->t_start = clk::now();
-              j->started = true;
-              ag->jobs.push_back(j);
-            }
-            break;
+          if (!srv->astream_busy[q]) free_slots.push_back(q);
+        const size_t per = free_slots.empty() ? 0 : (srv->apending.size() + free_slots.size() - 1) / free_slots.size();
+        for (int q : free_slots) {
+          if (srv->apending.empty()) break;
+          SActionGroup* g = new SActionGroup();
+          g->slot = q;
+          srv->astream_busy[q] = true;
+          while (!srv->apending.empty() && g->jobs.size() < per) {
+            SJob* j = srv->apending.front();
+            srv->apending.pop_front();
+            j->t_start = clk::now();
+            j->started = true;
+            g->jobs.push_back(j);
           }
+          ags.push_back(g);
+        }
       }
       // the oldest job picks the group; its peers with the same key share the chunk
       if (!srv->active.empty()) {
@@ -1888,7 +1932,7 @@ void server_loop(mg_server* srv) {
             group.push_back(j);
       }
     }
-    if (ag) {
+    for (SActionGroup* ag : ags) {
       const int rc = launch_action_group(srv, *ag);
       if (rc != MG_OK) {
         complete_action_group(srv, *ag, rc);
@@ -2082,6 +2126,7 @@ int submit_action(mg_server* srv, const mg_job* job, uint64_t* job_id) {
     return rc;
   }
   j->rowptr_h = std::move(h.rowptr);
+  j->col_h = std::move(h.col);
   {
     std::lock_guard<std::mutex> lock(srv->mu);
     j->id = srv->next_id++;

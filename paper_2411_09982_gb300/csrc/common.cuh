@@ -162,6 +162,7 @@ struct ActionJob {
   double* cheb;         // N x ACTION_REC interval records (written by the bounds kernel)
   double* abuf;         // nnz complex: the interval matrix when it does not fit in shared memory
   double* psi;          // d complex, in and out
+  const uint16_t* sendmask;  // cluster variant: per row, bit q set if CTA q reads that row
   int status;           // MG_OK, or set by the kernel when the job stopped early
   // written by the kernel: operator applications, sub-step counts, degree, half-width
   long long matvecs;
