@@ -196,8 +196,12 @@ int mg_evolve_batch(mg_ctx* ctx, int n, mg_plan* const* plans, const int* output
  * `quantum_intervals` intervals in one shared chunk step (batched exponential,
  * multi-job propagation), admitting new arrivals at every chunk boundary, so
  * requests that arrive while others run join them on the device instead of
- * waiting for them to finish (continuous batching).  While a server runs, the
- * caller must not use its context for anything else. */
+ * waiting for them to finish (continuous batching).  State jobs flagged
+ * MG_FLAG_STATE_ACTION take the action-based path instead: a second thread
+ * launches them on up to 16 streams of their own (one launch per job while
+ * streams are free), concurrently with the chunk steps, and completes each
+ * when its launch ends.  While a server runs, the caller must not use its
+ * context for anything else. */
 typedef struct mg_server mg_server;
 
 typedef struct mg_job {

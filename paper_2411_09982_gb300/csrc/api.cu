@@ -1770,6 +1770,8 @@ struct mg_server {
   std::deque<SJob*> apending;     // admitted action jobs not yet launched
   cudaStream_t astream[SERVER_ACTION_STREAMS] = {};
   bool astream_busy[SERVER_ACTION_STREAMS] = {};
+  std::condition_variable acv;    // wakes the action thread
+  std::thread aworker;            // launches and completes action jobs
   std::map<uint64_t, SJob*> jobs;
   std::thread worker;
   bool stop = false;
@@ -1877,23 +1879,12 @@ void complete_action_group(mg_server* srv, SActionGroup& g, int rc) {
 void server_loop(mg_server* srv) {
   mg_ctx* ctx = srv->ctx;
   cudaSetDevice(ctx->device);
-  std::vector<SActionGroup*> inflight;   // action launches on the action streams
   for (;;) {
     std::vector<SJob*> group;
-    std::vector<SActionGroup*> ags;
     {
       std::unique_lock<std::mutex> lock(srv->mu);
-      const auto work = [&] {
-        return srv->stop || !srv->pending.empty() || !srv->active.empty() || !srv->apending.empty();
-      };
-      if (inflight.empty()) {
-        srv->cv.wait(lock, work);
-      } else if (!work()) {
-        // only action launches in flight: poll them every 100 us
-        srv->cv.wait_for(lock, std::chrono::microseconds(100), work);
-      }
-      if (srv->stop && srv->pending.empty() && srv->active.empty() && srv->apending.empty() && inflight.empty())
-        return;
+      srv->cv.wait(lock, [&] { return srv->stop || !srv->pending.empty() || !srv->active.empty(); });
+      if (srv->stop && srv->pending.empty() && srv->active.empty()) return;
       // continuous admission: every request that arrived joins at this chunk boundary
       while (!srv->pending.empty()) {
         SJob* j = srv->pending.front();
@@ -1902,28 +1893,6 @@ void server_loop(mg_server* srv) {
         j->started = true;
         srv->active.push_back(j);
       }
-      // admitted action jobs spread over the free action streams (one launch
-      // each, so a job completes with its own launch, not with a longer one)
-      if (!srv->apending.empty()) {
-        std::vector<int> free_slots;
-        for (int q = 0; q < SERVER_ACTION_STREAMS; ++q)
-          if (!srv->astream_busy[q]) free_slots.push_back(q);
-        const size_t per = free_slots.empty() ? 0 : (srv->apending.size() + free_slots.size() - 1) / free_slots.size();
-        for (int q : free_slots) {
-          if (srv->apending.empty()) break;
-          SActionGroup* g = new SActionGroup();
-          g->slot = q;
-          srv->astream_busy[q] = true;
-          while (!srv->apending.empty() && g->jobs.size() < per) {
-            SJob* j = srv->apending.front();
-            srv->apending.pop_front();
-            j->t_start = clk::now();
-            j->started = true;
-            g->jobs.push_back(j);
-          }
-          ags.push_back(g);
-        }
-      }
       // the oldest job picks the group; its peers with the same key share the chunk
       if (!srv->active.empty()) {
         SJob* head = srv->active.front();
@@ -1931,26 +1900,6 @@ void server_loop(mg_server* srv) {
           if (j->dp == head->dp && j->prec == head->prec && j->L == head->L && (int)group.size() < srv->seg_cap)
             group.push_back(j);
       }
-    }
-    for (SActionGroup* ag : ags) {
-      const int rc = launch_action_group(srv, *ag);
-      if (rc != MG_OK) {
-        complete_action_group(srv, *ag, rc);
-        delete ag;
-      } else {
-        inflight.push_back(ag);
-      }
-    }
-    for (size_t q = 0; q < inflight.size();) {
-      const cudaError_t e = cudaEventQuery(inflight[q]->done);
-      if (e == cudaErrorNotReady) {
-        ++q;
-        continue;
-      }
-      if (e != cudaSuccess) cudaGetLastError();
-      complete_action_group(srv, *inflight[q], e == cudaSuccess ? MG_OK : MG_ECUDA);
-      delete inflight[q];
-      inflight.erase(inflight.begin() + q);
     }
     if (group.empty()) continue;
     const auto t0 = clk::now();
@@ -1991,6 +1940,66 @@ void server_loop(mg_server* srv) {
   }
 }
 
+// The action thread: spreads admitted action jobs over the free action streams
+// (one launch each, so a job completes with its own launch, not with a longer
+// one), polls the launches in flight every 100 us and completes them.  It runs
+// beside the chunk-step worker, so a long chunk step delays no action job.
+void action_loop(mg_server* srv) {
+  cudaSetDevice(srv->ctx->device);
+  std::vector<SActionGroup*> inflight;
+  for (;;) {
+    std::vector<SActionGroup*> ags;
+    {
+      std::unique_lock<std::mutex> lock(srv->mu);
+      const auto work = [&] { return srv->stop || !srv->apending.empty(); };
+      if (inflight.empty())
+        srv->acv.wait(lock, work);
+      else if (!work())
+        srv->acv.wait_for(lock, std::chrono::microseconds(100), work);
+      if (srv->stop && srv->apending.empty() && inflight.empty()) return;
+      std::vector<int> free_slots;
+      for (int q = 0; q < SERVER_ACTION_STREAMS; ++q)
+        if (!srv->astream_busy[q]) free_slots.push_back(q);
+      const size_t per =
+          free_slots.empty() ? 0 : (srv->apending.size() + free_slots.size() - 1) / free_slots.size();
+      for (int q : free_slots) {
+        if (srv->apending.empty()) break;
+        SActionGroup* g = new SActionGroup();
+        g->slot = q;
+        srv->astream_busy[q] = true;
+        while (!srv->apending.empty() && g->jobs.size() < per) {
+          SJob* j = srv->apending.front();
+          srv->apending.pop_front();
+          j->t_start = clk::now();
+          j->started = true;
+          g->jobs.push_back(j);
+        }
+        ags.push_back(g);
+      }
+    }
+    for (SActionGroup* ag : ags) {
+      const int rc = launch_action_group(srv, *ag);
+      if (rc != MG_OK) {
+        complete_action_group(srv, *ag, rc);
+        delete ag;
+      } else {
+        inflight.push_back(ag);
+      }
+    }
+    for (size_t q = 0; q < inflight.size();) {
+      const cudaError_t e = cudaEventQuery(inflight[q]->done);
+      if (e == cudaErrorNotReady) {
+        ++q;
+        continue;
+      }
+      if (e != cudaSuccess) cudaGetLastError();
+      complete_action_group(srv, *inflight[q], e == cudaSuccess ? MG_OK : MG_ECUDA);
+      delete inflight[q];
+      inflight.erase(inflight.begin() + q);
+    }
+  }
+}
+
 }  // namespace
 
 int mg_server_create(mg_ctx* ctx, size_t mem_budget_bytes, int quantum_intervals, mg_server** out) {
@@ -2017,6 +2026,7 @@ int mg_server_create(mg_ctx* ctx, size_t mem_budget_bytes, int quantum_intervals
     return MG_ENOMEM;
   }
   srv->worker = std::thread(server_loop, srv);
+  srv->aworker = std::thread(action_loop, srv);
   *out = srv;
   return MG_OK;
 }
@@ -2136,7 +2146,7 @@ int submit_action(mg_server* srv, const mg_job* job, uint64_t* job_id) {
     srv->apending.push_back(j);
     *job_id = j->id;
   }
-  srv->cv.notify_all();
+  srv->acv.notify_all();
   return MG_OK;
 }
 }  // namespace
@@ -2302,7 +2312,9 @@ int mg_server_destroy(mg_server* srv) {
     srv->stop = true;
   }
   srv->cv.notify_all();
+  srv->acv.notify_all();
   if (srv->worker.joinable()) srv->worker.join();
+  if (srv->aworker.joinable()) srv->aworker.join();
   for (auto& kv : srv->jobs) {
     free_job_memory(kv.second, srv->upload);
     delete kv.second;
