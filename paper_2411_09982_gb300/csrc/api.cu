@@ -124,15 +124,17 @@ int ws_get(mg_ctx* ctx, int slot, size_t bytes, void** out) {
     ctx->slot_size.resize(WS_COUNT, 0);
   }
   if (bytes == 0) bytes = 256;
+  // stream-ordered on the context's stream, the only stream that uses the
+  // slots: no device-wide synchronisation (kernels of other streams, e.g. a
+  // server's action launches, keep running while a slot grows)
   if (ctx->slot_size[slot] < bytes) {
     if (ctx->slot_ptr[slot]) {
-      MG_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
-      MG_CUDA_TRY(cudaFree(ctx->slot_ptr[slot]));
+      MG_CUDA_TRY(cudaFreeAsync(ctx->slot_ptr[slot], ctx->stream));
       ctx->slot_ptr[slot] = nullptr;
       ctx->slot_size[slot] = 0;
     }
     void* p = nullptr;
-    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    if (cudaMallocAsync(&p, bytes, ctx->stream) != cudaSuccess) {
       cudaGetLastError();
       set_last_message("device allocation of %zu bytes failed", bytes);
       return MG_ENOMEM;
@@ -155,12 +157,11 @@ int ws(mg_ctx* ctx, int slot, size_t count, T** out) {
 int small_scratch(mg_ctx* ctx, size_t n, double** out) {
   if (ctx->small_n < n) {
     if (ctx->small) {
-      MG_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
-      cudaFree(ctx->small);
+      MG_CUDA_TRY(cudaFreeAsync(ctx->small, ctx->stream));
       ctx->small = nullptr;
     }
     size_t m = std::max<size_t>(n, 4096);
-    if (cudaMalloc(&ctx->small, m * sizeof(double)) != cudaSuccess) {
+    if (cudaMallocAsync(reinterpret_cast<void**>(&ctx->small), m * sizeof(double), ctx->stream) != cudaSuccess) {
       cudaGetLastError();
       set_last_message("device allocation of %zu doubles failed", m);
       return MG_ENOMEM;
@@ -177,8 +178,8 @@ int check_status(mg_ctx* ctx) {
   MG_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
   if (st == MG_DEV_TIMEOUT) {
     set_last_message("a bounded device-side wait gave up (tensor-core product)");
-    int z = 0;
-    cudaMemcpy(ctx->status, &z, sizeof(int), cudaMemcpyHostToDevice);
+    cudaMemsetAsync(ctx->status, 0, sizeof(int), ctx->stream);
+    cudaStreamSynchronize(ctx->stream);
     return MG_ETIMEOUT;
   }
   return MG_OK;
@@ -1850,8 +1851,9 @@ void complete_action_group(mg_server* srv, SActionGroup& g, int rc) {
   if (rc == MG_OK && cudaStreamSynchronize(s) != cudaSuccess) rc = MG_ECUDA;
   if (rc == MG_OK && g.mem) {
     const char* dev = reinterpret_cast<const char*>(g.mem) + g.off_jobs;
-    if (cudaMemcpy(g.launch.data(), dev, sizeof(ActionJob) * g.launch.size(), cudaMemcpyDeviceToHost) !=
-        cudaSuccess)
+    if (cudaMemcpyAsync(g.launch.data(), dev, sizeof(ActionJob) * g.launch.size(), cudaMemcpyDeviceToHost, s) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
       rc = MG_ECUDA;
   }
   std::vector<int> st(g.jobs.size(), rc);
@@ -2046,8 +2048,11 @@ int submit_action(mg_server* srv, const mg_job* job, uint64_t* job_id) {
     std::memcpy(dense.data(), job->H0, sizeof(double) * dd2);
     if (K > 0) std::memcpy(dense.data() + dd2, job->Hk, sizeof(double) * dd2 * K);
   } else {
-    MG_CUDA_TRY(cudaMemcpy(dense.data(), job->H0, sizeof(double) * dd2, cudaMemcpyDeviceToHost));
-    if (K > 0) MG_CUDA_TRY(cudaMemcpy(dense.data() + dd2, job->Hk, sizeof(double) * dd2 * K, cudaMemcpyDeviceToHost));
+    MG_CUDA_TRY(cudaMemcpyAsync(dense.data(), job->H0, sizeof(double) * dd2, cudaMemcpyDeviceToHost, srv->upload));
+    if (K > 0)
+      MG_CUDA_TRY(cudaMemcpyAsync(dense.data() + dd2, job->Hk, sizeof(double) * dd2 * K, cudaMemcpyDeviceToHost,
+                                  srv->upload));
+    MG_CUDA_TRY(cudaStreamSynchronize(srv->upload));
   }
   CsrHost h;
   build_csr_host(dense.data(), d, 1 + K, h);
