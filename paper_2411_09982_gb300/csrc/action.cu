@@ -43,6 +43,8 @@
 #include <cooperative_groups.h>
 
 #include <algorithm>
+#include <map>
+#include <mutex>
 
 namespace mg {
 
@@ -428,18 +430,35 @@ size_t action_cluster_smem_bytes(int dmax, int C, int cap_loc) {
          sizeof(int) * (rows_max + 1);
 }
 
+// Both chain kernels get the largest dynamic shared memory any launch uses
+// (and the cluster kernel non-portable cluster sizes) once, up front.
+constexpr int ACTION_SMEM_LIMIT = 225 * 1024;
+int action_attrs() {
+  MG_TRY(ensure_smem_limit(reinterpret_cast<const void*>(action_chain_kernel), ACTION_SMEM_LIMIT));
+  MG_TRY(ensure_smem_limit(reinterpret_cast<const void*>(action_chain_cluster_kernel), ACTION_SMEM_LIMIT));
+  return ensure_func_attr(reinterpret_cast<const void*>(action_chain_cluster_kernel),
+                          cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+}
+
 // Largest cluster size <= want (a power of two) that the device can co-schedule
-// with this shared memory, or 1.
+// with this shared memory, or 1; answers are cached per (size, shared memory).
 int action_cluster_size(int want, int dmax, int cap_loc) {
+  static std::mutex mu;
+  static std::map<std::pair<int, size_t>, bool> fits;
+  if (action_attrs() != MG_OK) {
+    cudaGetLastError();
+    return 1;
+  }
   for (int C = want; C >= 2; C >>= 1) {
     const size_t smem = action_cluster_smem_bytes(dmax, C, cap_loc);
-    if (smem > 225 * 1024) continue;
-    if (cudaFuncSetAttribute(action_chain_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem) != cudaSuccess ||
-        cudaFuncSetAttribute(action_chain_cluster_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
-            cudaSuccess) {
-      cudaGetLastError();
-      return 1;
+    if (smem > (size_t)ACTION_SMEM_LIMIT) continue;
+    {
+      std::lock_guard<std::mutex> lock(mu);
+      auto it = fits.find({C, smem});
+      if (it != fits.end()) {
+        if (it->second) return C;
+        continue;
+      }
     }
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(C, 1, 1);
@@ -453,18 +472,19 @@ int action_cluster_size(int want, int dmax, int cap_loc) {
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     int active = 0;
-    if (cudaOccupancyMaxActiveClusters(&active, action_chain_cluster_kernel, &cfg) == cudaSuccess && active >= 1)
-      return C;
-    cudaGetLastError();
+    const bool ok = cudaOccupancyMaxActiveClusters(&active, action_chain_cluster_kernel, &cfg) == cudaSuccess &&
+                    active >= 1;
+    if (!ok) cudaGetLastError();
+    std::lock_guard<std::mutex> lock(mu);
+    fits[{C, smem}] = ok;
+    if (ok) return C;
   }
   return 1;
 }
 
 int launch_action_cluster(int njobs, ActionJob* jobs_dev, int dmax, int C, int cap_loc, cudaStream_t s) {
   const size_t smem = action_cluster_smem_bytes(dmax, C, cap_loc);
-  MG_CUDA_TRY(cudaFuncSetAttribute(action_chain_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)smem));
-  MG_CUDA_TRY(cudaFuncSetAttribute(action_chain_cluster_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+  MG_TRY(action_attrs());
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(njobs * C, 1, 1);
   cfg.blockDim = dim3(ACTION_THREADS, 1, 1);
@@ -501,8 +521,7 @@ int launch_action_chain(int njobs, ActionJob* jobs_dev, int dmax, int nmax, int 
   }
   if (cluster > 1) return launch_action_cluster(njobs, jobs_dev, dmax, cluster, nnz_cap, s);
   const size_t smem = action_smem_bytes(dmax, nnz_cap);
-  if (smem > 48 * 1024)
-    MG_CUDA_TRY(cudaFuncSetAttribute(action_chain_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  MG_TRY(action_attrs());
   // one thread per row up to ACTION_THREADS; small jobs take fewer warps
   const int threads = std::min(ACTION_THREADS, (dmax + 31) / 32 * 32);
   action_chain_kernel<<<njobs, threads, smem, s>>>(jobs_dev, dmax, nnz_cap);

@@ -22,6 +22,7 @@
 #include <condition_variable>
 #include <deque>
 #include <map>
+#include <tuple>
 #include <mutex>
 #include <thread>
 #include <string>
@@ -44,6 +45,29 @@ void set_last_cuda_error(cudaError_t e, const char* what, const char* file, int 
   set_last_message("%s failed: %s (%s:%d)", what, cudaGetErrorString(e), file, line);
 }
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+namespace {
+std::mutex g_attr_mu;
+std::map<std::tuple<const void*, int, int>, int> g_attr;   // (kernel, attribute, device) -> value set
+}  // namespace
+
+int ensure_func_attr(const void* func, cudaFuncAttribute attr, int value) {
+  int dev = 0;
+  MG_CUDA_TRY(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lock(g_attr_mu);
+  const auto key = std::make_tuple(func, (int)attr, dev);
+  auto it = g_attr.find(key);
+  const bool grow = attr == cudaFuncAttributeMaxDynamicSharedMemorySize;
+  if (it != g_attr.end() && (grow ? it->second >= value : it->second == value)) return MG_OK;
+  MG_CUDA_TRY(cudaFuncSetAttribute(func, attr, value));
+  g_attr[key] = value;
+  return MG_OK;
+}
+
+int ensure_smem_limit(const void* func, int bytes) {
+  if (bytes <= 48 * 1024) return MG_OK;
+  return ensure_func_attr(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
 int check_launch(const char* name) {
   count_launch();
   cudaError_t e = cudaGetLastError();

@@ -56,6 +56,12 @@ inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
 // converts a launch error into MG_ECUDA with a message.
 int check_launch(const char* name);
 void count_launch();
+// Raises a kernel's dynamic shared-memory limit to at least `bytes` and sets
+// its other launch attributes, calling cudaFuncSetAttribute only the first
+// time a value is needed on the current device (a kernel whose attributes
+// change while launches of it are in flight on other streams can stall them).
+int ensure_smem_limit(const void* func, int bytes);
+int ensure_func_attr(const void* func, cudaFuncAttribute attr, int value);
 
 // ---------------------------------------------------------------------------
 // kernels shared between translation units (launch wrappers)

@@ -237,10 +237,7 @@ int launch_build_omega(int N, int d, int K, double dt, const double* H0, const d
   MG_CUDA_TRY(cudaMemsetAsync(bits, 0, sizeof(unsigned long long) * N, s));
   dim3 grid(ceil_div(d, OMEGA_COLS), ceil_div(N, OMEGA_NB));
   size_t smem = sizeof(double) * (OMEGA_NB * (K > 0 ? K : 1) + OMEGA_NB + OMEGA_WARPS * OMEGA_NB * 32);
-  if (smem > 48 * 1024) {
-    MG_CUDA_TRY(cudaFuncSetAttribute(build_omega_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)smem));
-  }
+  MG_TRY(ensure_smem_limit(reinterpret_cast<const void*>(build_omega_kernel), (int)smem));
   build_omega_kernel<<<grid, 256, smem, s>>>(N, d, K, dt, H0, Hk, c, tr, omega, tau, bits, shift,
                                             write_shifted);
   MG_TRY(check_launch("build_omega_kernel"));

@@ -761,11 +761,11 @@ static int launch_split_gemm_L(const SplitGeom& g, int batch, const __nv_bfloat1
   cudaError_t e;
   if (cm == 2) {
     auto kern = split_gemm_kernel<L, STAGES, 2>;
-    MG_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    MG_TRY(ensure_smem_limit(reinterpret_cast<const void*>(kern), (int)smem));
     e = cudaLaunchKernelEx(&cfg, kern, ma, mb, mbh, g.d, g.Kp, g.Mp, g.Np, g.beta, ea, eb, C, sC, epi, status);
   } else {
     auto kern = split_gemm_kernel<L, STAGES, 1>;
-    MG_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    MG_TRY(ensure_smem_limit(reinterpret_cast<const void*>(kern), (int)smem));
     e = cudaLaunchKernelEx(&cfg, kern, ma, mb, mbh, g.d, g.Kp, g.Mp, g.Np, g.beta, ea, eb, C, sC, epi, status);
   }
   if (e != cudaSuccess) {
