@@ -81,7 +81,7 @@ extern "C" {
  * (Tal-Ezer and Kosloff 1984) over the Gershgorin interval of Hbar_n, with
  * sparse (CSR) matrix-vector products in FP64; exact up to the unit roundoff,
  * cheaper whenever the operators are sparse.  One thread block per job, so it
- * suits batches of jobs or large sparse d.  Limits: d <= 4800, at most 255
+ * suits batches of jobs or large sparse d.  Limits: d <= 4693, at most 255
  * operators (after the commutators of order 2), and a Gershgorin half-width of
  * Hbar_n of at most 327680 (16384 sub-steps of 20); beyond it the call (or the
  * job's batch status) returns MG_EUNSUPPORTED, a non-finite bound

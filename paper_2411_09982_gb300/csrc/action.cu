@@ -432,7 +432,6 @@ size_t action_cluster_smem_bytes(int dmax, int C, int cap_loc) {
 
 // Both chain kernels get the largest dynamic shared memory any launch uses
 // (and the cluster kernel non-portable cluster sizes) once, up front.
-constexpr int ACTION_SMEM_LIMIT = 225 * 1024;
 int action_attrs() {
   MG_TRY(ensure_smem_limit(reinterpret_cast<const void*>(action_chain_kernel), ACTION_SMEM_LIMIT));
   MG_TRY(ensure_smem_limit(reinterpret_cast<const void*>(action_chain_cluster_kernel), ACTION_SMEM_LIMIT));

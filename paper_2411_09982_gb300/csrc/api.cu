@@ -616,8 +616,8 @@ int check_action_limits(int d, int nops) {
     set_last_message("action-based state path supports at most 255 control operators (job has %d)", nops - 1);
     return MG_EUNSUPPORTED;
   }
-  if (action_smem_bytes(d, 0) > 225 * 1024) {   // three complex FP64 vectors in shared memory
-    set_last_message("action-based state path supports d <= %d (job has d = %d)", 225 * 1024 / 48, d);
+  if (action_smem_bytes(d, 0) > (size_t)ACTION_SMEM_LIMIT) {   // three complex FP64 vectors in shared memory
+    set_last_message("action-based state path supports d <= %d (job has d = %d)", ACTION_SMEM_LIMIT / 48, d);
     return MG_EUNSUPPORTED;
   }
   return MG_OK;
@@ -714,7 +714,7 @@ void shape_action(const std::vector<ActionJob>& jobs, const std::vector<CsrRef>&
         if (v > c && action_cluster_smem_bytes(S.dmax, C, v) <= 200 * 1024) c = v;
       }
     }
-    if (action_cluster_smem_bytes(S.dmax, C, c) > 225 * 1024) continue;
+    if (action_cluster_smem_bytes(S.dmax, C, c) > (size_t)ACTION_SMEM_LIMIT) continue;
     if (action_cluster_size(C, S.dmax, c) == C) {
       S.cluster = C;
       S.cap = c;

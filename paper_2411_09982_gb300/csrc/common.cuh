@@ -153,6 +153,9 @@ int launch_multi_chain(int nseg, int d, const ChainSeg* segs_dev, const double* 
 // CSR pattern (union of the nonzeros of H0, H_1.. H_K plus the diagonal) with
 // one complex value array per operator, operator-major: val[(op * nnz + e)].
 constexpr int ACTION_REC = 72;   // doubles per interval record
+// dynamic shared memory limit of the action chain kernels (their static
+// shared memory, ~2.5 KB, stays within the 227 KB a block may hold)
+constexpr int ACTION_SMEM_LIMIT = 220 * 1024;
 struct ActionJob {
   int d;
   int K;
