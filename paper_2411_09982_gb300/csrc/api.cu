@@ -2037,8 +2037,13 @@ int mg_server_create(mg_ctx* ctx, size_t mem_budget_bytes, int quantum_intervals
   srv->budget = mem_budget_bytes;
   srv->quantum = quantum_intervals;
   bool streams_ok = true;
+  // action streams at the device's highest priority: their CTAs go ahead of
+  // pending chunk-step CTAs whenever an SM frees
+  int prio_lo = 0, prio_hi = 0;
+  cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
   for (int q = 0; q < SERVER_ACTION_STREAMS; ++q)
-    streams_ok = streams_ok && cudaStreamCreateWithFlags(&srv->astream[q], cudaStreamNonBlocking) == cudaSuccess;
+    streams_ok = streams_ok && cudaStreamCreateWithPriority(&srv->astream[q], cudaStreamNonBlocking, prio_hi) ==
+                                   cudaSuccess;
   if (!streams_ok || cudaStreamCreateWithFlags(&srv->upload, cudaStreamNonBlocking) != cudaSuccess ||
       cudaMalloc(&srv->segs_dev, sizeof(ChainSeg) * srv->seg_cap) != cudaSuccess ||
       cudaMalloc(&srv->psi_dev, sizeof(double*) * srv->seg_cap) != cudaSuccess) {
