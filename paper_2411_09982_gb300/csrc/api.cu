@@ -102,6 +102,10 @@ struct mg_ctx {
   size_t ev_next = 0;
   long long t_launches = 0;
   double t_flops = 0.0, t_ms = 0.0;
+  // stream-ordered allocations of the context and its servers: freed blocks stay
+  // in the pool (no release at synchronisation points, which would wait for every
+  // kernel on the device) and are reused only without cross-stream waits
+  cudaMemPool_t pool = nullptr;
 };
 
 struct mg_plan {
@@ -158,7 +162,7 @@ int ws_get(mg_ctx* ctx, int slot, size_t bytes, void** out) {
       ctx->slot_size[slot] = 0;
     }
     void* p = nullptr;
-    if (cudaMallocAsync(&p, bytes, ctx->stream) != cudaSuccess) {
+    if (cudaMallocFromPoolAsync(&p, bytes, ctx->pool, ctx->stream) != cudaSuccess) {
       cudaGetLastError();
       set_last_message("device allocation of %zu bytes failed", bytes);
       return MG_ENOMEM;
@@ -185,7 +189,7 @@ int small_scratch(mg_ctx* ctx, size_t n, double** out) {
       ctx->small = nullptr;
     }
     size_t m = std::max<size_t>(n, 4096);
-    if (cudaMallocAsync(reinterpret_cast<void**>(&ctx->small), m * sizeof(double), ctx->stream) != cudaSuccess) {
+    if (cudaMallocFromPoolAsync(reinterpret_cast<void**>(&ctx->small), m * sizeof(double), ctx->pool, ctx->stream) != cudaSuccess) {
       cudaGetLastError();
       set_last_message("device allocation of %zu doubles failed", m);
       return MG_ENOMEM;
@@ -893,7 +897,22 @@ int mg_ctx_create(mg_ctx** out, int device, void* stream) {
   mg_ctx* c = new mg_ctx();
   c->device = device;
   c->stream = reinterpret_cast<cudaStream_t>(stream);
+  cudaMemPoolProps props = {};
+  props.allocType = cudaMemAllocationTypePinned;
+  props.location.type = cudaMemLocationTypeDevice;
+  props.location.id = device;
+  if (cudaMemPoolCreate(&c->pool, &props) != cudaSuccess) {
+    cudaGetLastError();
+    delete c;
+    set_last_message("creating the context's memory pool failed");
+    return MG_ECUDA;
+  }
+  uint64_t keep = UINT64_MAX;
+  int no = 0;
+  cudaMemPoolSetAttribute(c->pool, cudaMemPoolAttrReleaseThreshold, &keep);
+  cudaMemPoolSetAttribute(c->pool, cudaMemPoolReuseAllowInternalDependencies, &no);
   if (cudaMalloc(&c->status, sizeof(int)) != cudaSuccess) {
+    cudaMemPoolDestroy(c->pool);
     delete c;
     return MG_ENOMEM;
   }
@@ -915,6 +934,7 @@ int mg_ctx_destroy(mg_ctx* ctx) {
   if (ctx->ev0) cudaEventDestroy(ctx->ev0);
   if (ctx->ev1) cudaEventDestroy(ctx->ev1);
   for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
+  if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
   delete ctx;
   return MG_OK;
 }
@@ -1847,7 +1867,7 @@ int launch_action_group(mg_server* srv, SActionGroup& g) {
   shape_action(recs, pat, g.shape);
   size_t o_mat, o_mask;
   const size_t bytes = action_ws_bytes(g.shape, recs.size(), &o_mat, &o_mask, &g.off_jobs);
-  if (cudaMallocAsync(&g.mem, bytes, s) != cudaSuccess) {
+  if (cudaMallocFromPoolAsync(&g.mem, bytes, srv->ctx->pool, s) != cudaSuccess) {
     cudaGetLastError();
     g.mem = nullptr;
     set_last_message("device allocation of %zu bytes failed (action launch)", bytes);
@@ -2112,7 +2132,7 @@ int submit_action(mg_server* srv, const mg_job* job, uint64_t* job_id) {
   const cudaMemcpyKind h2d = host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
   cudaStream_t s = srv->upload;
   auto dmalloc = [&](size_t n, void** ptr) -> int {
-    if (cudaMallocAsync(ptr, std::max<size_t>(n, 16), s) != cudaSuccess) {
+    if (cudaMallocFromPoolAsync(ptr, std::max<size_t>(n, 16), srv->ctx->pool, s) != cudaSuccess) {
       cudaGetLastError();
       set_last_message("device allocation of %zu bytes failed (job upload)", n);
       return MG_ENOMEM;
@@ -2128,7 +2148,7 @@ int submit_action(mg_server* srv, const mg_job* job, uint64_t* job_id) {
     MG_TRY(dmalloc(sizeof(double) * h.val.size(), &val));
     MG_TRY(dmalloc(c_bytes, &c));
     MG_TRY(dmalloc(sizeof(double) * 2 * d, &psi));
-    if (cudaMallocAsync(&tmp, tmp_bytes, s) != cudaSuccess) { cudaGetLastError(); return MG_ENOMEM; }
+    if (cudaMallocFromPoolAsync(&tmp, tmp_bytes, srv->ctx->pool, s) != cudaSuccess) { cudaGetLastError(); return MG_ENOMEM; }
     double* Tw = reinterpret_cast<double*>(tmp);
     double* Ts = Tw + P;
     int r = MG_OK;
@@ -2228,7 +2248,7 @@ int mg_submit(mg_server* srv, const mg_job* job, uint64_t* job_id) {
   int rc = MG_OK;
   cudaStream_t s = srv->upload;
   auto dmalloc = [&](size_t n, void** ptr) -> int {
-    if (cudaMallocAsync(ptr, n, s) != cudaSuccess) {
+    if (cudaMallocFromPoolAsync(ptr, n, srv->ctx->pool, s) != cudaSuccess) {
       cudaGetLastError();
       set_last_message("device allocation of %zu bytes failed (job upload)", n);
       return MG_ENOMEM;
@@ -2242,7 +2262,7 @@ int mg_submit(mg_server* srv, const mg_job* job, uint64_t* job_id) {
     MG_TRY(dmalloc(op_bytes, &ops));
     MG_TRY(dmalloc(c_bytes, &c));
     MG_TRY(dmalloc(st_bytes, &st));
-    if (cudaMallocAsync(&tmp, tmp_bytes, s) != cudaSuccess) { cudaGetLastError(); return MG_ENOMEM; }
+    if (cudaMallocFromPoolAsync(&tmp, tmp_bytes, srv->ctx->pool, s) != cudaSuccess) { cudaGetLastError(); return MG_ENOMEM; }
     double* T = reinterpret_cast<double*>(tmp);
     double* Tw = T + mat_doubles(d) * (1 + K);
     double* Ts = Tw + P;
