@@ -198,10 +198,11 @@ int mg_evolve_batch(mg_ctx* ctx, int n, mg_plan* const* plans, const int* output
  * requests that arrive while others run join them on the device instead of
  * waiting for them to finish (continuous batching).  State jobs flagged
  * MG_FLAG_STATE_ACTION take the action-based path instead: a second thread
- * launches them on up to 16 streams of their own (one launch per job while
- * streams are free), concurrently with the chunk steps, and completes each
- * when its launch ends.  While a server runs, the caller must not use its
- * context for anything else. */
+ * launches them on four high-priority streams of their own, concurrently with
+ * the chunk steps, in slices of about 10 ms of work per job, and completes
+ * each job at the end of the slice that finishes it (so no long kernel holds
+ * up work queued behind it on the device's shared hardware queues).  While a
+ * server runs, the caller must not use its context for anything else. */
 typedef struct mg_server mg_server;
 
 typedef struct mg_job {

@@ -203,7 +203,7 @@ action_chain_kernel(ActionJob* __restrict__ jobs, int dmax, int nnz_cap) {
   }
   for (int i = threadIdx.x; i < d; i += blockDim.x) acc[i] = reinterpret_cast<const double2*>(J.psi)[i];
   long long matvecs = 0;
-  int max_sub = 0, min_sub = 1 << 30, max_deg = 0;
+  int max_sub = 0, min_sub = 1 << 30, max_deg = 0, done = 0;
   double max_rho = 0.0;
   __syncthreads();
   for (int n = 0; n < J.N; ++n) {
@@ -283,9 +283,12 @@ action_chain_kernel(ActionJob* __restrict__ jobs, int dmax, int nnz_cap) {
       acc[i] = make_double2(cs * v.x + sn * v.y, cs * v.y - sn * v.x);
     }
     __syncthreads();
+    done = n + 1;
+    if (J.max_steps > 0 && matvecs >= J.max_steps) break;   // uniform: the same count in every thread
   }
   for (int i = threadIdx.x; i < d; i += blockDim.x) reinterpret_cast<double2*>(J.psi)[i] = acc[i];
   if (threadIdx.x == 0) {
+    R.done = done;
     R.matvecs = matvecs;
     R.max_sub = max_sub;
     R.min_sub = J.N > 0 ? min_sub : 0;
@@ -333,7 +336,7 @@ action_chain_cluster_kernel(ActionJob* __restrict__ jobs, int dmax, int cap_loc)
   for (int li = threadIdx.x; li < nr; li += blockDim.x)
     acc[li] = reinterpret_cast<const double2*>(J.psi)[r0 + li];
   long long matvecs = 0;
-  int max_sub = 0, min_sub = 1 << 30, max_deg = 0;
+  int max_sub = 0, min_sub = 1 << 30, max_deg = 0, done = 0;
   double max_rho = 0.0;
   cl.sync();   // every CTA of the cluster runs before any remote write
   for (int n = 0; n < J.N; ++n) {
@@ -412,9 +415,12 @@ action_chain_cluster_kernel(ActionJob* __restrict__ jobs, int dmax, int cap_loc)
       acc[li] = make_double2(cs * v.x + sn * v.y, cs * v.y - sn * v.x);
     }
     __syncthreads();
+    done = n + 1;
+    if (J.max_steps > 0 && matvecs >= J.max_steps) break;   // uniform over the cluster
   }
   for (int li = threadIdx.x; li < nr; li += blockDim.x) reinterpret_cast<double2*>(J.psi)[r0 + li] = acc[li];
   if (rank == 0 && threadIdx.x == 0) {
+    R.done = done;
     R.matvecs = matvecs;
     R.max_sub = max_sub;
     R.min_sub = J.N > 0 ? min_sub : 0;

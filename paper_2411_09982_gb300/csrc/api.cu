@@ -1791,15 +1791,21 @@ struct SJob {
 
 // Action jobs launched together on one of the server's action streams.
 struct SActionGroup {
-  std::vector<SJob*> jobs;
+  std::vector<SJob*> jobs;        // launch order: jobs[q] owns launch[q]
   int slot = 0;                   // index of the action stream
-  cudaEvent_t done = nullptr;
+  cudaEvent_t done = nullptr;     // end of the current slice
   void* mem = nullptr;            // interval records, off-chip matrices, send masks, job records
   size_t off_jobs = 0;            // byte offset of the job records in mem
-  std::vector<ActionJob> launch;  // launch-ordered records (kept until completion)
+  std::vector<ActionJob> launch;  // every job's record, advanced past the intervals done
+  std::vector<int> running;       // jobs (indices into launch) of the current slice
+  std::vector<ActionJob> xfer;    // the current slice's records (host side of the copies)
   ActionShape shape;
 };
-constexpr int SERVER_ACTION_STREAMS = 16;
+constexpr int SERVER_ACTION_STREAMS = 4;
+// Action chains in the server run in slices of about this many seconds of work:
+// streams share the device's few hardware queues, so a copy or kernel queued on
+// another stream waits at most one slice behind a long chain.
+constexpr double ACTION_SLICE_S = 0.01;
 
 }  // namespace
 
@@ -1855,6 +1861,22 @@ void finish_job(mg_server* srv, SJob* j, int status) {
 
 // Launches every job of `g` (uploads done on the upload stream) on its action
 // stream: records, bounds kernel, chain kernel, completion event.
+// Uploads the running jobs' records and launches one slice of their chains
+// (with the bounds kernel first when `bounds`), then records g.done.
+int issue_action_slice(mg_server* srv, SActionGroup& g, bool bounds) {
+  cudaStream_t s = srv->astream[g.slot];
+  g.xfer.clear();
+  for (int q : g.running) g.xfer.push_back(g.launch[q]);
+  ActionJob* dev = reinterpret_cast<ActionJob*>(reinterpret_cast<char*>(g.mem) + g.off_jobs);
+  MG_CUDA_TRY(cudaMemcpyAsync(dev, g.xfer.data(), sizeof(ActionJob) * g.xfer.size(), cudaMemcpyHostToDevice, s));
+  MG_TRY(launch_action_chain((int)g.xfer.size(), dev, g.shape.dmax, bounds ? g.shape.nmax : 0, g.shape.cap,
+                             g.shape.cluster, s));
+  if (!g.done) MG_CUDA_TRY(cudaEventCreateWithFlags(&g.done, cudaEventDisableTiming));
+  MG_CUDA_TRY(cudaEventRecord(g.done, s));
+  return MG_OK;
+}
+
+// First slice of a group: launch shape, workspace, records, bounds and chain.
 int launch_action_group(mg_server* srv, SActionGroup& g) {
   cudaStream_t s = srv->astream[g.slot];
   std::vector<ActionJob> recs;
@@ -1874,53 +1896,79 @@ int launch_action_group(mg_server* srv, SActionGroup& g) {
     return MG_ENOMEM;
   }
   char* base = reinterpret_cast<char*>(g.mem);
-  ActionJob* dev = reinterpret_cast<ActionJob*>(base + g.off_jobs);
   layout_action(recs, g.shape, reinterpret_cast<double*>(base), reinterpret_cast<double*>(base + o_mat),
                 reinterpret_cast<uint16_t*>(base + o_mask), g.launch);
+  std::vector<SJob*> ordered(g.jobs.size());
+  for (size_t q = 0; q < g.jobs.size(); ++q) ordered[q] = g.jobs[g.shape.order[q]];
+  g.jobs.swap(ordered);
+  // slice length: ~ACTION_SLICE_S of operator applications, from a per-application
+  // time of max(1.6 us, 3.3 ns per nonzero of a CTA's rows)
+  for (ActionJob& a : g.launch) {
+    const double per = std::max(1.6e-6, 3.3e-9 * (double)a.nnz / g.shape.cluster);
+    a.max_steps = std::max<long long>(64, (long long)(ACTION_SLICE_S / per));
+  }
+  g.running.clear();
+  for (size_t q = 0; q < g.launch.size(); ++q) g.running.push_back((int)q);
   if (g.shape.mask_words)
     MG_CUDA_TRY(cudaMemcpyAsync(base + o_mask, g.shape.masks.data(), sizeof(uint16_t) * g.shape.mask_words,
                                 cudaMemcpyHostToDevice, s));
-  MG_CUDA_TRY(cudaMemcpyAsync(dev, g.launch.data(), sizeof(ActionJob) * recs.size(), cudaMemcpyHostToDevice, s));
-  MG_TRY(launch_action_chain((int)recs.size(), dev, g.shape.dmax, g.shape.nmax, g.shape.cap, g.shape.cluster, s));
-  MG_CUDA_TRY(cudaEventCreateWithFlags(&g.done, cudaEventDisableTiming));
-  MG_CUDA_TRY(cudaEventRecord(g.done, s));
-  return MG_OK;
+  return issue_action_slice(srv, g, true);
 }
 
-// After g.done: reads the job records back (the stream is idle, so the copies
-// are immediate), writes each job's state to its output, releases the memory
-// and completes the jobs.  `rc` != MG_OK fails every job of the group.
-void complete_action_group(mg_server* srv, SActionGroup& g, int rc) {
+// After a slice: reads the running records back, advances every job past the
+// intervals it completed, completes the finished (or failed) jobs and launches
+// the next slice for the rest.  Returns true while the group still has a slice
+// in flight.  `rc` != MG_OK fails every running job.
+bool advance_action_group(mg_server* srv, SActionGroup& g, int rc) {
   cudaStream_t s = srv->astream[g.slot];
   if (rc == MG_OK && cudaStreamSynchronize(s) != cudaSuccess) rc = MG_ECUDA;
-  if (rc == MG_OK && g.mem) {
+  if (rc == MG_OK && g.mem && !g.xfer.empty()) {
     const char* dev = reinterpret_cast<const char*>(g.mem) + g.off_jobs;
-    if (cudaMemcpyAsync(g.launch.data(), dev, sizeof(ActionJob) * g.launch.size(), cudaMemcpyDeviceToHost, s) !=
+    if (cudaMemcpyAsync(g.xfer.data(), dev, sizeof(ActionJob) * g.xfer.size(), cudaMemcpyDeviceToHost, s) !=
             cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess)
       rc = MG_ECUDA;
   }
-  std::vector<int> st(g.jobs.size(), rc);
-  for (size_t q = 0; q < g.launch.size() && rc == MG_OK; ++q) {
-    SJob* j = g.jobs[g.shape.order[q]];
-    st[g.shape.order[q]] = g.launch[q].status;
-    if (g.launch[q].status == MG_OK &&
-        cudaMemcpyAsync(j->out, j->arec.psi, sizeof(double) * 2 * j->b.d, j->out_kind, s) != cudaSuccess)
-      st[g.shape.order[q]] = MG_ECUDA;
+  std::vector<std::pair<SJob*, int>> finished;
+  std::vector<int> next;
+  for (size_t i = 0; i < g.running.size(); ++i) {
+    const int q = g.running[i];
+    SJob* j = g.jobs[q];
+    int st = rc == MG_OK ? g.xfer[i].status : rc;
+    if (st == MG_OK) {
+      ActionJob& a = g.launch[q];
+      const int dn = std::max(0, std::min(g.xfer[i].done, a.N));
+      a.first += dn;
+      a.cheb += (size_t)dn * ACTION_REC;
+      a.N -= dn;
+      if (a.N > 0) {
+        next.push_back(q);
+        continue;
+      }
+      if (cudaMemcpyAsync(j->out, j->arec.psi, sizeof(double) * 2 * j->b.d, j->out_kind, s) != cudaSuccess)
+        st = MG_ECUDA;
+    }
+    finished.emplace_back(j, st);
   }
   cudaStreamSynchronize(s);
+  for (auto& f : finished) {
+    free_job_memory(f.first, s);
+    finish_job(srv, f.first, f.second);
+  }
+  g.running.swap(next);
+  if (!g.running.empty()) {
+    const int r = issue_action_slice(srv, g, false);
+    if (r == MG_OK) return true;
+    return advance_action_group(srv, g, r);   // fails the remaining jobs
+  }
   if (g.mem) cudaFreeAsync(g.mem, s);
   g.mem = nullptr;
   if (g.done) cudaEventDestroy(g.done);
   g.done = nullptr;
-  for (size_t q = 0; q < g.jobs.size(); ++q) {
-    free_job_memory(g.jobs[q], s);
-    finish_job(srv, g.jobs[q], st[q]);
-  }
   std::lock_guard<std::mutex> lock(srv->mu);
   srv->astream_busy[g.slot] = false;
+  return false;
 }
-
 
 void server_loop(mg_server* srv) {
   mg_ctx* ctx = srv->ctx;
@@ -1986,9 +2034,9 @@ void server_loop(mg_server* srv) {
   }
 }
 
-// The action thread: spreads admitted action jobs over the free action streams
-// (one launch each, so a job completes with its own launch, not with a longer
-// one), polls the launches in flight every 100 us and completes them.  It runs
+// The action thread: spreads admitted action jobs over the free action streams,
+// polls the slices in flight every 100 us, completes the jobs that finished
+// and launches the next slice of the others.  It runs
 // beside the chunk-step worker, so a long chunk step delays no action job.
 void action_loop(mg_server* srv) {
   cudaSetDevice(srv->ctx->device);
@@ -2026,7 +2074,10 @@ void action_loop(mg_server* srv) {
     for (SActionGroup* ag : ags) {
       const int rc = launch_action_group(srv, *ag);
       if (rc != MG_OK) {
-        complete_action_group(srv, *ag, rc);
+        if (ag->running.empty())
+          for (size_t q = 0; q < ag->jobs.size(); ++q) ag->running.push_back((int)q);
+        if (ag->launch.size() < ag->jobs.size()) ag->launch.resize(ag->jobs.size());
+        advance_action_group(srv, *ag, rc);
         delete ag;
       } else {
         inflight.push_back(ag);
@@ -2039,7 +2090,10 @@ void action_loop(mg_server* srv) {
         continue;
       }
       if (e != cudaSuccess) cudaGetLastError();
-      complete_action_group(srv, *inflight[q], e == cudaSuccess ? MG_OK : MG_ECUDA);
+      if (advance_action_group(srv, *inflight[q], e == cudaSuccess ? MG_OK : MG_ECUDA)) {
+        ++q;
+        continue;
+      }
       delete inflight[q];
       inflight.erase(inflight.begin() + q);
     }

@@ -173,6 +173,8 @@ struct ActionJob {
   double* psi;          // d complex, in and out
   const uint16_t* sendmask;  // cluster variant: per row, bit q set if CTA q reads that row
   int status;           // MG_OK, or set by the kernel when the job stopped early
+  long long max_steps;  // operator applications after which a launch stops at an interval end (0: none)
+  int done;             // written by the kernel: intervals this launch completed
   // written by the kernel: operator applications, sub-step counts, degree, half-width
   long long matvecs;
   int max_sub, min_sub, max_terms;
