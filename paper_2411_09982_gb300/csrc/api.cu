@@ -12,6 +12,7 @@
 // workspace; within a chunk every step is one batched launch over all of the
 // chunk's intervals.
 #include "common.cuh"
+#include "taylor18.h"
 
 #include <cmath>
 #include <cstdarg>
@@ -252,19 +253,22 @@ double unit_roundoff(int precision, int L, int d) {
   return std::max(u64, std::ldexp(1.0, -beta * L));
 }
 
+// Degrees: Paterson-Stockmeyer m = 2..16 (p = block size), and m = 18 in five
+// products (p = 0: the scheme of kTaylor18, csrc/taylor18.h).
 TaylorChoice choose_taylor(double norm1, double u) {
-  static const int ms[] = {2, 4, 6, 9, 12, 16};
-  static const int ps[] = {2, 2, 3, 3, 4, 4};
-  static const int cost[] = {1, 2, 3, 4, 5, 6};
+  static const int ms[] = {2, 4, 6, 9, 12, 16, 18};
+  static const int ps[] = {2, 2, 3, 3, 4, 4, 0};
+  static const int cost[] = {1, 2, 3, 4, 5, 6, 5};
   TaylorChoice best{16, 4, 6, 0, 0.0};
   int best_total = 1 << 30;
-  for (int i = 0; i < 6; ++i) {
+  for (int i = 0; i < 7; ++i) {
     double th = taylor_theta(ms[i], u);
     int s = 0;
     if (norm1 > th) s = (int)std::ceil(std::log2(norm1 / th));
     while (s > 0 && norm1 * std::ldexp(1.0, -(s - 1)) <= th) --s;
     while (norm1 * std::ldexp(1.0, -s) > th) ++s;
     int total = cost[i] + s;
+    // ties go to the smaller degree first (m = 18 ties m = 12 at equal s)
     if (total < best_total || (total == best_total && s < best.s)) {
       best_total = total;
       best = TaylorChoice{ms[i], ps[i], cost[i], s, th};
@@ -329,6 +333,11 @@ struct Engine {
   int lincomb(int batch, double* dst, int n, const double* const* src, const double* coef, double diag) {
     return df() ? launch_lincomb_df(batch, d, dst, n, src, coef, diag, ctx->stream)
                 : launch_lincomb(batch, d, dst, n, src, coef, diag, ctx->stream);
+  }
+  int lincomb_multi(int batch, int nout, double* const* dst, int n, const double* const* src, const double* coef,
+                    const double* diag) {
+    return df() ? launch_lincomb_multi_df(batch, d, nout, dst, n, src, coef, diag, ctx->stream)
+                : launch_lincomb_multi(batch, d, nout, dst, n, src, coef, diag, ctx->stream);
   }
   int identity(int batch, double* dst) {
     return df() ? launch_identity_df(batch, d, dst, ctx->stream) : launch_identity(batch, d, dst, ctx->stream);
@@ -432,6 +441,54 @@ int expm_chunk(mg_ctx* ctx, Engine& eng, int batch, double* W, const double* tau
   MG_TRY(eng.scale_x(batch, W, W, tc.s));
   const double* X = W;
 
+  double* R = R0;
+  double* Rn = R1;
+  if (tc.p == 0) {
+    // degree 18 in five products: A2, A3, A6, A9 = B1 B5 + B4, T = B2 + (B3 + A9) A9
+    AddTerms none;
+    MG_TRY(eng.prepA(batch, X, md));
+    MG_TRY(eng.prepB(0, batch, X, md));
+    MG_TRY(eng.mul(batch, X, md, 0, X, md, P2, md, none));        // A2
+    MG_TRY(eng.prepA(batch, P2, md));
+    MG_TRY(eng.mul(batch, P2, md, 0, X, md, P3, md, none));       // A3
+    MG_TRY(eng.prepA(batch, P3, md));
+    MG_TRY(eng.prepB(1, batch, P3, md));
+    MG_TRY(eng.mul(batch, P3, md, 1, P3, md, Y, md, none));       // A6
+    // B1 -> R0, B5 -> R1, B4 -> P2, B3 -> P3, B2 -> Y (in place over A2, A3, A6)
+    const double* srcs[4] = {X, P2, P3, Y};
+    double* dsts[5] = {R0, R1, P2, P3, Y};
+    const double* k = kTaylor18;
+    const double cf[5 * 4] = {k[1], k[2], k[3], 0.0,  k[5], k[6], k[7], k[8],  k[10], k[11], k[12], k[13],
+                              k[15], k[16], k[17], k[18],  k[20], k[21], k[22], k[23]};
+    const double dg[5] = {k[0], k[4], k[9], k[14], k[19]};
+    MG_TRY(eng.lincomb_multi(batch, 5, dsts, 4, srcs, cf, dg));
+    AddTerms add4;
+    add4.n = 1;
+    add4.src[0] = P2;
+    add4.coef[0] = 1.0;
+    add4.stride = md;
+    add4.diag = 0.0;
+    MG_TRY(eng.prepA(batch, R0, md));
+    MG_TRY(eng.prepB(0, batch, R1, md));
+    MG_TRY(eng.mul(batch, R0, md, 0, R1, md, W, md, add4));       // A9 (over X)
+    {
+      const double* qs[2] = {W, P3};
+      const double qc[2] = {1.0, 1.0};
+      MG_TRY(eng.lincomb(batch, P3, 2, qs, qc, 0.0));             // B3 + A9
+    }
+    AddTerms add2;
+    add2.n = 1;
+    add2.src[0] = Y;
+    add2.coef[0] = 1.0;
+    add2.stride = md;
+    add2.diag = 0.0;
+    MG_TRY(eng.prepA(batch, P3, md));
+    MG_TRY(eng.prepB(1, batch, W, md));
+    MG_TRY(eng.mul(batch, P3, md, 1, W, md, R0, md, add2));       // T
+    R = R0;
+    Rn = R1;
+  } else {
+
   // coefficients 1/j!
   double a[17];
   a[0] = 1.0;
@@ -452,8 +509,6 @@ int expm_chunk(mg_ctx* ctx, Engine& eng, int batch, double* W, const double* tau
   }
   // Horner in Y = X^p over blocks B_i = sum_{j<p} a_{ip+j} X^j
   const int q = m / p, r = m - q * p;
-  double* R = R0;
-  double* Rn = R1;
   int i_next;
   {
     const double* src[4];
@@ -476,6 +531,7 @@ int expm_chunk(mg_ctx* ctx, Engine& eng, int batch, double* W, const double* tau
     MG_TRY(eng.prepA(batch, R, md));
     MG_TRY(eng.mul(batch, R, md, 1, P[p], md, Rn, md, add));
     std::swap(R, Rn);
+  }
   }
   // squarings
   for (int k = 0; k < tc.s; ++k) {

@@ -202,6 +202,12 @@ int launch_unpad_copy(int d, int dp, const double* src, double* dst, cudaStream_
 
 // Double-float (DF32) elementwise kernels of the split path; see elementwise.cu.
 int launch_scale_minus_i_df(int batch, int d, const double* src_fp64, double* dst_df, int sq, cudaStream_t s);
+// dst[o] = sum_m coef[o * nsrc + m] src[m] + diag[o] I, o < nout <= 5, nsrc <= 4, one pass
+// (a destination may alias a source); FP64 and double-float storage
+int launch_lincomb_multi(int batch, int d, int nout, double* const* dst, int nsrc, const double* const* src,
+                         const double* coef, const double* diag, cudaStream_t s);
+int launch_lincomb_multi_df(int batch, int d, int nout, double* const* dst, int nsrc, const double* const* src,
+                            const double* coef, const double* diag, cudaStream_t s);
 int launch_lincomb_df(int batch, int d, double* dst, int nsrc, const double* const* src, const double* coef,
                       double diag, cudaStream_t s);
 int launch_apply_phase_df(int batch, int d, const double* phase, const double* src, double* dst, cudaStream_t s);

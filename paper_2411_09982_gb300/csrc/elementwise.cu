@@ -71,6 +71,51 @@ int launch_lincomb(int batch, int d, double* dst, int nsrc, const double* const*
   return check_launch("lincomb_kernel");
 }
 
+// Several linear combinations of the same sources in one pass: dst_o =
+// sum_m coef[o][m] src_m + diag[o] I for o < nout (nout <= 5, nsrc <= 4).  Every
+// thread reads all sources of its element before writing, so a destination may
+// alias a source.
+struct LincombMultiArgs {
+  const double* src[4];
+  double* dst[5];
+  double coef[5][4];
+  double diag[5];
+};
+
+__global__ void lincomb_multi_kernel(int d, long long total, int nsrc, int nout, LincombMultiArgs a) {
+  const long long per = (long long)d * d;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    double2 v[4];
+    for (int m = 0; m < nsrc; ++m) v[m] = reinterpret_cast<const double2*>(a.src[m])[e];
+    const long long r = e % per;
+    const bool on_diag = r / d == r % d;
+    for (int o = 0; o < nout; ++o) {
+      double re = on_diag ? a.diag[o] : 0.0, im = 0.0;
+      for (int m = 0; m < nsrc; ++m) {
+        re = fma(a.coef[o][m], v[m].x, re);
+        im = fma(a.coef[o][m], v[m].y, im);
+      }
+      reinterpret_cast<double2*>(a.dst[o])[e] = make_double2(re, im);
+    }
+  }
+}
+
+int launch_lincomb_multi(int batch, int d, int nout, double* const* dst, int nsrc, const double* const* src,
+                         const double* coef, const double* diag, cudaStream_t s) {
+  if (nsrc < 1 || nsrc > 4 || nout < 1 || nout > 5) return MG_EINVAL;
+  LincombMultiArgs a{};
+  for (int m = 0; m < nsrc; ++m) a.src[m] = src[m];
+  for (int o = 0; o < nout; ++o) {
+    a.dst[o] = dst[o];
+    a.diag[o] = diag[o];
+    for (int m = 0; m < nsrc; ++m) a.coef[o][m] = coef[o * nsrc + m];
+  }
+  const long long total = (long long)d * d * batch;
+  lincomb_multi_kernel<<<grid_for(total), 256, 0, s>>>(d, total, nsrc, nout, a);
+  return check_launch("lincomb_multi_kernel");
+}
+
 // ---------------------------------------------------------------------------
 // grid (chunks, batch): the phase factor is formed once per block, not per element.
 __global__ void apply_phase_kernel(long long per_item, const double* __restrict__ phase,
@@ -213,6 +258,48 @@ int launch_lincomb_df(int batch, int d, double* dst, int nsrc, const double* con
   lincomb_df_kernel<<<grid_for(total), 256, 0, s>>>(d, total, nsrc, a, df_from_double(diag),
                                                     reinterpret_cast<float4*>(dst));
   return check_launch("lincomb_df_kernel");
+}
+
+// the multi-output combination in double-float (see lincomb_multi_kernel)
+struct LincombMultiDfArgs {
+  const float4* src[4];
+  float4* dst[5];
+  df32 coef[5][4];
+  df32 diag[5];
+};
+
+__global__ void lincomb_multi_df_kernel(int d, long long total, int nsrc, int nout, LincombMultiDfArgs a) {
+  const long long per = (long long)d * d;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    float4 v[4];
+    for (int m = 0; m < nsrc; ++m) v[m] = a.src[m][e];
+    const long long r = e % per;
+    const bool on_diag = r / d == r % d;
+    for (int o = 0; o < nout; ++o) {
+      df32 re = on_diag ? a.diag[o] : df32{0.f, 0.f}, im{0.f, 0.f};
+      for (int m = 0; m < nsrc; ++m) {
+        re = df_add(re, df_mul(df32{v[m].x, v[m].y}, a.coef[o][m]));
+        im = df_add(im, df_mul(df32{v[m].z, v[m].w}, a.coef[o][m]));
+      }
+      a.dst[o][e] = make_float4(re.hi, re.lo, im.hi, im.lo);
+    }
+  }
+}
+
+int launch_lincomb_multi_df(int batch, int d, int nout, double* const* dst, int nsrc, const double* const* src,
+                            const double* coef, const double* diag, cudaStream_t s) {
+  if (nsrc < 1 || nsrc > 4 || nout < 1 || nout > 5) return MG_EINVAL;
+  LincombMultiDfArgs a{};
+  for (int m = 0; m < nsrc; ++m) a.src[m] = reinterpret_cast<const float4*>(src[m]);
+  for (int o = 0; o < nout; ++o) {
+    a.dst[o] = reinterpret_cast<float4*>(dst[o]);
+    a.diag[o] = df_from_double(diag[o]);
+    for (int m = 0; m < nsrc; ++m) a.coef[o][m] = df_from_double(coef[o * nsrc + m]);
+  }
+  const long long total = (long long)d * d * batch;
+  lincomb_multi_df_kernel<<<grid_for(total), 256, 0, s>>>(d, total, nsrc, nout, a);
+  return check_launch("lincomb_multi_df_kernel");
 }
 
 // dst_b = e^{-i phase_b} src_b in DF32; the phase factor is formed once per block in FP64

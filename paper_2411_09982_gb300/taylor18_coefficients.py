@@ -1,0 +1,121 @@
+"""Coefficients of the degree-18 Taylor evaluation with five matrix products.
+
+The scheme (Bader, Blanes and Casas, "Computing the matrix exponential with an
+optimized Taylor polynomial approximation", Mathematics 7 (2019) 1174) forms
+A2 = A A, A3 = A2 A, A6 = A3 A3 and then
+
+    B1 = a0 I + a1 A + a2 A2 + a3 A3
+    B5, B4, B3, B2 = linear combinations of I, A, A2, A3, A6
+    A9 = B1 B5 + B4
+    T  = B2 + (B3 + A9) A9,
+
+which is a polynomial of degree 18 in A.  Its 24 coefficients must make T equal
+to sum_{k<=18} A^k / k! (19 conditions), so they form a 5-parameter family.
+Members differ in rounding behaviour: the starting point below was chosen by a
+search over the family that minimised the measured rounding error of the
+evaluation on random anti-Hermitian matrices of norm 1.76 in single precision
+(1.2-2x that of Paterson-Stockmeyer of degree 16 for the same matrices, against
+up to several hundred times for arbitrary members).  This script refines it to
+an exact member of the family in 60-digit arithmetic (minimum-norm Newton
+steps), checks the 19 conditions and writes csrc/taylor18.h.
+
+Run:  python paper_2411_09982_gb300/taylor18_coefficients.py
+"""
+import os
+
+import mpmath as mp
+
+mp.mp.dps = 60
+
+# order: B1 (I, A, A2, A3) | B5, B4, B3, B2 (each I, A, A2, A3, A6)
+START = [
+    1.0058693655583843e-03, 9.4047600873797300e-03, 7.5238080699037847e-04, 8.3597867443375382e-05,
+    -1.7591892250863039e+00, -4.9164249027178322e+00, -2.3900877321888991e+00, -2.4665646642921854e-02,
+    -1.4949762421967222e-04,
+    -2.2300257288977538e-03, 8.9130485715093050e-02, -1.7630637239740329e-02, -1.2473559364650560e-02,
+    1.0206980602001412e-06,
+    1.1156502052331549e+01, -1.6801581387890618e+00, -5.7177984647886794e-02, 6.9821012248804633e-03,
+    -3.3497501708607081e-05,
+    1.0446048830045054e+00, 2.3919036075052777e-01, 1.3624383975555356e+00, 4.9894895088677021e-01,
+    -6.4106140466585416e-04,
+]
+POW5 = [0, 1, 2, 3, 6]
+
+
+def series(c, pows, n=19):
+    a = [mp.mpf(0)] * n
+    for v, k in zip(c, pows):
+        a[k] += v
+    return a
+
+
+def mul(a, b, n=19):
+    out = [mp.mpf(0)] * n
+    for i, x in enumerate(a):
+        if x == 0:
+            continue
+        for j, y in enumerate(b):
+            if i + j < n:
+                out[i + j] += x * y
+    return out
+
+
+def polynomial(x):
+    """Coefficients of T(A) in powers of A up to degree 18 (the scheme has no higher terms)."""
+    B1 = series(x[0:4], [0, 1, 2, 3])
+    B5, B4, B3, B2 = (series(x[q:q + 5], POW5) for q in (4, 9, 14, 19))
+    A9 = [p + q for p, q in zip(mul(B1, B5), B4)]
+    Q = [p + q for p, q in zip(B3, A9)]
+    return [p + q for p, q in zip(B2, mul(Q, A9))]
+
+
+def residual(x):
+    T = polynomial(x)
+    return [(T[k] - 1 / mp.factorial(k)) * mp.factorial(k) for k in range(19)]
+
+
+def refine(x, steps=12):
+    x = [mp.mpf(v) for v in x]
+    for _ in range(steps):
+        r = mp.matrix(residual(x))
+        if mp.norm(r, mp.inf) < mp.mpf(10) ** -55:
+            break
+        h = mp.mpf(10) ** -30
+        J = mp.matrix(19, 24)
+        for i in range(24):
+            xp = list(x)
+            xp[i] += h
+            rp = residual(xp)
+            for k in range(19):
+                J[k, i] = (rp[k] - r[k]) / h
+        # minimum-norm step: dx = J^T (J J^T)^{-1} r
+        dx = J.T * mp.lu_solve(J * J.T, r)
+        x = [x[i] - dx[i] for i in range(24)]
+    return x
+
+
+def main():
+    x = refine(START)
+    worst = max(abs(v) for v in residual(x))
+    assert worst < mp.mpf(10) ** -40, worst
+    rounded = [float(v) for v in x]
+    worst_rounded = max(abs(v) for v in residual(rounded))
+    names = ["B1"] * 4 + ["B5"] * 5 + ["B4"] * 5 + ["B3"] * 5 + ["B2"] * 5
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "csrc", "taylor18.h")
+    with open(path, "w") as f:
+        f.write("// Degree-18 Taylor polynomial in five matrix products: the coefficients of\n"
+                "// B1 (I, A, A2, A3) and of B5, B4, B3, B2 (I, A, A2, A3, A6) in\n"
+                "//   A9 = B1 B5 + B4,   T = B2 + (B3 + A9) A9  =  sum_{k<=18} A^k / k!\n"
+                "// (the scheme of Bader, Blanes and Casas, Mathematics 7 (2019) 1174).\n"
+                "// Written by paper_2411_09982_gb300/taylor18_coefficients.py, which derives\n"
+                "// this member of the coefficient family and checks the 19 conditions; rounded\n"
+                f"// to double they hold to {float(worst_rounded):.1e} relative.\n"
+                "#pragma once\n\nnamespace mg {\nconstexpr double kTaylor18[24] = {\n")
+        for v, n in zip(rounded, names):
+            f.write(f"    {v!r},  // {n}\n")
+        f.write("};\n}  // namespace mg\n")
+    print(path, "max relative condition error after rounding:", float(worst_rounded))
+
+
+if __name__ == "__main__":
+    main()
