@@ -253,15 +253,22 @@ double unit_roundoff(int precision, int L, int d) {
   return std::max(u64, std::ldexp(1.0, -beta * L));
 }
 
-// Degrees: Paterson-Stockmeyer m = 2..16 (p = block size), and m = 18 in five
-// products (p = 0: the scheme of kTaylor18, csrc/taylor18.h).
-TaylorChoice choose_taylor(double norm1, double u) {
+// Degrees: Paterson-Stockmeyer m = 2..16 (p = block size), and, when allowed,
+// m = 18 in five products (p = 0: the scheme of kTaylor18, csrc/taylor18.h).
+// The five-product scheme is offered to the split-precision path only: its
+// coefficients, rounded to double, perturb the low-degree Taylor terms by
+// ~1e-16 relative, a bias that is the same in every interval and so adds up
+// linearly over long runs of near-identical intervals (measured: 1e-12 after
+// 1000 intervals of the d = 30 workload in FP64, against 1e-13 with
+// Paterson-Stockmeyer), while the split products round at 2^{-beta L}.
+TaylorChoice choose_taylor(double norm1, double u, bool allow18) {
   static const int ms[] = {2, 4, 6, 9, 12, 16, 18};
   static const int ps[] = {2, 2, 3, 3, 4, 4, 0};
   static const int cost[] = {1, 2, 3, 4, 5, 6, 5};
   TaylorChoice best{16, 4, 6, 0, 0.0};
   int best_total = 1 << 30;
   for (int i = 0; i < 7; ++i) {
+    if (ps[i] == 0 && !allow18) continue;
     double th = taylor_theta(ms[i], u);
     int s = 0;
     if (norm1 > th) s = (int)std::ceil(std::log2(norm1 / th));
@@ -416,7 +423,7 @@ int expm_chunk(mg_ctx* ctx, Engine& eng, int batch, double* W, const double* tau
     nmax = std::max(nmax, nrm[b]);
   }
   const double u = unit_roundoff(eng.prec, eng.L, d);
-  TaylorChoice tc = choose_taylor(nmax, u);
+  TaylorChoice tc = choose_taylor(nmax, u, eng.prec == MG_PREC_SPLIT);
   if (st) {
     st->m = tc.m;
     st->s_applied = tc.s;
