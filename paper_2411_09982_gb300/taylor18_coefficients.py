@@ -17,7 +17,10 @@ evaluation on random anti-Hermitian matrices of norm 1.76 in single precision
 (1.2-2x that of Paterson-Stockmeyer of degree 16 for the same matrices, against
 up to several hundred times for arbitrary members).  This script refines it to
 an exact member of the family in 60-digit arithmetic (minimum-norm Newton
-steps), checks the 19 conditions and writes csrc/taylor18.h.
+steps), checks the 19 conditions and writes csrc/taylor18.h.  The library
+offers the scheme to its split-precision path only (choose_taylor in
+csrc/api.cu): rounded to double, these coefficients bias the low-degree terms
+by ~1e-16 relative, which matters only at FP64 accuracy.
 
 Run:  python paper_2411_09982_gb300/taylor18_coefficients.py
 """
