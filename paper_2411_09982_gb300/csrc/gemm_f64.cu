@@ -5,13 +5,14 @@
 //
 // with opA = identity or conjugate transpose.  GB300's FP64 throughput is a
 // small fraction of its tensor-core throughput, so this kernel is ALU-bound on
-// the FP64 pipe: 64 x 64 complex output tiles per CTA, 4 x 4 complex outputs
-// per thread, operands staged through shared memory in K-slabs of 8.
+// the FP64 pipe: TM x TM complex output tiles per CTA (TM = 64, or 32 / 16 for
+// small d, so that padding does not multiply the FP64 work), (TM/16)^2 complex
+// outputs per thread, operands staged through shared memory in K-slabs of 8.
 #include "common.cuh"
 
 namespace mg {
 
-constexpr int FBM = 64, FBN = 64, FBK = 8;
+constexpr int FBK = 8;
 
 struct AddDev {
   const double* src[3];
@@ -22,38 +23,41 @@ struct AddDev {
   double scale;
 };
 
+template <int TM>
 __global__ void __launch_bounds__(256)
 cgemm_f64_kernel(int d, const double* __restrict__ A, long long sA, int opA,
                  const double* __restrict__ B, long long sB, double* __restrict__ C, long long sC,
                  AddDev add) {
-  __shared__ double2 As[FBK][FBM];   // As[k][i] = opA(A)[i][k]
-  __shared__ double2 Bs[FBK][FBN];   // Bs[k][j] = B[k][j]
+  constexpr int RT = TM / 16;                   // outputs per thread along each dimension
+  constexpr int STAGE = (TM * FBK + 255) / 256; // staged elements per thread per operand
+  __shared__ double2 As[FBK][TM];   // As[k][i] = opA(A)[i][k]
+  __shared__ double2 Bs[FBK][TM];   // Bs[k][j] = B[k][j]
 
   const int b = blockIdx.z;
   const double2* Ab = reinterpret_cast<const double2*>(A + b * sA);
   const double2* Bb = reinterpret_cast<const double2*>(B + b * sB);
-  const int i0 = blockIdx.y * FBM, j0 = blockIdx.x * FBN;
+  const int i0 = blockIdx.y * TM, j0 = blockIdx.x * TM;
   const int tid = threadIdx.x;
   const int tx = tid & 15, ty = tid >> 4;
 
-  double accr[4][4], acci[4][4];
+  double accr[RT][RT], acci[RT][RT];
 #pragma unroll
-  for (int r = 0; r < 4; ++r)
+  for (int r = 0; r < RT; ++r)
 #pragma unroll
-    for (int c = 0; c < 4; ++c) { accr[r][c] = 0.0; acci[r][c] = 0.0; }
+    for (int c = 0; c < RT; ++c) { accr[r][c] = 0.0; acci[r][c] = 0.0; }
 
   for (int k0 = 0; k0 < d; k0 += FBK) {
-    // stage A: 64 x 8 complex = 512 -> 2 per thread
 #pragma unroll
-    for (int t = 0; t < 2; ++t) {
-      int e = tid + t * 256;
+    for (int t = 0; t < STAGE; ++t) {
+      const int e = tid + t * 256;
+      if (e >= TM * FBK) break;
       double2 v = make_double2(0.0, 0.0);
       int i, k;
       if (opA == 0) {  // A[i][k]: contiguous along k
         i = e / FBK; k = e % FBK;
         if (i0 + i < d && k0 + k < d) v = Ab[(long long)(i0 + i) * d + (k0 + k)];
       } else {         // conj(A[k][i]): contiguous along i
-        k = e / FBM; i = e % FBM;
+        k = e / TM; i = e % TM;
         if (i0 + i < d && k0 + k < d) {
           v = Ab[(long long)(k0 + k) * d + (i0 + i)];
           v.y = -v.y;
@@ -62,25 +66,28 @@ cgemm_f64_kernel(int d, const double* __restrict__ A, long long sA, int opA,
       As[k][i] = v;
     }
 #pragma unroll
-    for (int t = 0; t < 2; ++t) {
-      int e = tid + t * 256;
-      int k = e / FBN, j = e % FBN;
+    for (int t = 0; t < STAGE; ++t) {
+      const int e = tid + t * 256;
+      if (e >= TM * FBK) break;
+      const int k = e / TM, j = e % TM;
       double2 v = make_double2(0.0, 0.0);
       if (k0 + k < d && j0 + j < d) v = Bb[(long long)(k0 + k) * d + (j0 + j)];
       Bs[k][j] = v;
     }
     __syncthreads();
+    const int kmax = min(FBK, d - k0);
 #pragma unroll
     for (int k = 0; k < FBK; ++k) {
-      double2 a[4], bb[4];
+      if (k >= kmax) break;   // zero padding beyond d adds nothing
+      double2 a[RT], bb[RT];
 #pragma unroll
-      for (int r = 0; r < 4; ++r) a[r] = As[k][ty + 16 * r];
+      for (int r = 0; r < RT; ++r) a[r] = As[k][ty + 16 * r];
 #pragma unroll
-      for (int c = 0; c < 4; ++c) bb[c] = Bs[k][tx + 16 * c];
+      for (int c = 0; c < RT; ++c) bb[c] = Bs[k][tx + 16 * c];
 #pragma unroll
-      for (int r = 0; r < 4; ++r)
+      for (int r = 0; r < RT; ++r)
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
+        for (int c = 0; c < RT; ++c) {
           accr[r][c] = fma(a[r].x, bb[c].x, accr[r][c]);
           accr[r][c] = fma(-a[r].y, bb[c].y, accr[r][c]);
           acci[r][c] = fma(a[r].x, bb[c].y, acci[r][c]);
@@ -92,11 +99,11 @@ cgemm_f64_kernel(int d, const double* __restrict__ A, long long sA, int opA,
 
   double2* Cb = reinterpret_cast<double2*>(C + b * sC);
 #pragma unroll
-  for (int r = 0; r < 4; ++r) {
+  for (int r = 0; r < RT; ++r) {
     const int i = i0 + ty + 16 * r;
     if (i >= d) continue;
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
+    for (int c = 0; c < RT; ++c) {
       const int j = j0 + tx + 16 * c;
       if (j >= d) continue;
       const long long off = (long long)i * d + j;
@@ -123,8 +130,15 @@ int launch_cgemm_f64(int batch, int d, const double* A, long long strideA, int o
   a.stride = add.stride;
   a.diag = add.diag;
   a.scale = add.scale;
-  dim3 grid(ceil_div(d, FBN), ceil_div(d, FBM), batch);
-  cgemm_f64_kernel<<<grid, 256, 0, s>>>(d, A, strideA, opA, B, strideB, C, strideC, a);
+  // tile edge: the smallest of 16, 32, 64 that covers d (64 beyond)
+  if (d <= 16) {
+    cgemm_f64_kernel<16><<<dim3(1, 1, batch), 256, 0, s>>>(d, A, strideA, opA, B, strideB, C, strideC, a);
+  } else if (d <= 32) {
+    cgemm_f64_kernel<32><<<dim3(1, 1, batch), 256, 0, s>>>(d, A, strideA, opA, B, strideB, C, strideC, a);
+  } else {
+    dim3 grid(ceil_div(d, 64), ceil_div(d, 64), batch);
+    cgemm_f64_kernel<64><<<grid, 256, 0, s>>>(d, A, strideA, opA, B, strideB, C, strideC, a);
+  }
   return check_launch("cgemm_f64_kernel");
 }
 
