@@ -70,6 +70,9 @@ extern "C" {
 /* ---- outputs --------------------------------------------------------------- */
 #define MG_OUT_STATE       0  /* psi(T) = U_{N-1} ... U_0 psi0            */
 #define MG_OUT_PROPAGATOR  1  /* U(T)   = U_{N-1} ... U_0                 */
+/* mg_evolve only: the stroboscopic states psi_n = U_{n-1} ... U_0 psi0 at every
+ * interval end, n = 0..N, written as (N + 1) x d complex rows (row 0 = psi0). */
+#define MG_OUT_TRAJECTORY  2
 
 /* ---- flags ----------------------------------------------------------------- */
 #define MG_FLAG_HOST_PTRS        1  /* the call's data pointers are host memory */
@@ -164,6 +167,10 @@ int mg_set_controls(mg_plan* plan, int N, int P, double t0, double dt, const dou
  *   output = MG_OUT_STATE:      in = psi0 (d complex), out = psi(T) (d complex)
  *   output = MG_OUT_PROPAGATOR: in = NULL (identity start) or U0 (d x d),
  *                               out = U(T) U0 (d x d)
+ *   output = MG_OUT_TRAJECTORY: in = psi0, out = psi_0 .. psi_N ((N + 1) x d
+ *                               complex), the state at every interval end
+ * A run can be resumed from any psi_n (or U) with controls for the remaining
+ * intervals (t0 moved to t0 + n dt). 
  * reorth_every = R > 0 re-orthonormalises the running product every R
  * intervals in FP64 (propagator: one Newton-Schulz polar step
  * U <- U (3I - U^dag U)/2; state: psi <- psi/|psi|); 0 disables it.

@@ -278,9 +278,11 @@ action_chain_kernel(ActionJob* __restrict__ jobs, int dmax, int nnz_cap) {
     // exact phase of the spectral centre
     double sn, cs;
     sincos(center, &sn, &cs);
+    double2* trow = J.traj ? reinterpret_cast<double2*>(J.traj) + (long long)(J.first + n + 1) * d : nullptr;
     for (int i = threadIdx.x; i < d; i += blockDim.x) {
       const double2 v = acc[i];
       acc[i] = make_double2(cs * v.x + sn * v.y, cs * v.y - sn * v.x);
+      if (trow) trow[i] = acc[i];
     }
     __syncthreads();
     done = n + 1;
@@ -410,9 +412,11 @@ action_chain_cluster_kernel(ActionJob* __restrict__ jobs, int dmax, int cap_loc)
     }
     double sn, cs;
     sincos(center, &sn, &cs);
+    double2* trow = J.traj ? reinterpret_cast<double2*>(J.traj) + (long long)(J.first + n + 1) * d + r0 : nullptr;
     for (int li = threadIdx.x; li < nr; li += blockDim.x) {
       const double2 v = acc[li];
       acc[li] = make_double2(cs * v.x + sn * v.y, cs * v.y - sn * v.x);
+      if (trow) trow[li] = acc[li];
     }
     __syncthreads();
     done = n + 1;

@@ -144,6 +144,7 @@ enum Slot {
   WS_TAU, WS_NORM, WS_ACC, WS_ACC2, WS_NS_G, WS_NS_H, WS_VEC,
   WS_TREE0, WS_TREE1, WS_UBUF, WS_NS_Z, WS_OUT,
   WS_ACT_REC,   // action path: interval records, off-chip interval matrices, send masks, job records
+  WS_TRAJ,      // trajectory output staged on the device (host output buffers)
   WS_COUNT
 };
 
@@ -1278,8 +1279,11 @@ int mg_expm(mg_ctx* ctx, int batch, int d, const double* A, double* U, int preci
 namespace {
 
 struct PropState {
-  int output;
+  int output;                // MG_OUT_STATE (also for trajectories) or MG_OUT_PROPAGATOR
   int d;
+  double* traj = nullptr;    // trajectory rows psi_0..psi_N (device: the caller's buffer or workspace)
+  bool traj_staged = false;  // traj is workspace, copied to the host output at the end
+  int traj_rows = 0;
   double* psi = nullptr;     // state mode (device, workspace)
   double* acc = nullptr;     // propagator mode: running product (device, workspace)
   bool acc_init = false;
@@ -1300,7 +1304,7 @@ int fold_chunk(mg_ctx* ctx, Engine& eng, PropState& ps, int n, const double* U, 
       MG_TRY(eng.to_fp64(n, U, md, conv, md));
       Uf = conv;
     }
-    MG_TRY(launch_state_chain(n, d, Uf, md, ps.psi, tmp + 2, reorth, ps.done, ctx->stream));
+    MG_TRY(launch_state_chain(n, d, Uf, md, ps.psi, tmp + 2, reorth, ps.done, ctx->stream, ps.traj));
     ps.done += n;
     return MG_OK;
   }
@@ -1330,7 +1334,9 @@ int fold_chunk(mg_ctx* ctx, Engine& eng, PropState& ps, int n, const double* U, 
   return MG_OK;
 }
 
-int begin_prop(mg_ctx* ctx, Engine& eng, PropState& ps, const double* in, int flags) {
+// traj_out: the caller's trajectory buffer ((traj_rows) x d complex) or null
+int begin_prop(mg_ctx* ctx, Engine& eng, PropState& ps, const double* in, int flags, double* traj_out = nullptr,
+               int traj_rows = 0) {
   const int d = ps.d;
   const long long md = mat_doubles(d);
   const cudaMemcpyKind kind = (flags & MG_FLAG_HOST_PTRS) ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
@@ -1338,6 +1344,16 @@ int begin_prop(mg_ctx* ctx, Engine& eng, PropState& ps, const double* in, int fl
     if (!in) return MG_EINVAL;
     MG_TRY(ws(ctx, WS_ACC, 2 * d, &ps.psi));
     MG_CUDA_TRY(cudaMemcpyAsync(ps.psi, in, sizeof(double) * 2 * d, kind, ctx->stream));
+    if (traj_out) {
+      ps.traj_rows = traj_rows;
+      if (flags & MG_FLAG_HOST_PTRS) {
+        MG_TRY(ws(ctx, WS_TRAJ, (size_t)traj_rows * 2 * d, &ps.traj));
+        ps.traj_staged = true;
+      } else {
+        ps.traj = traj_out;
+      }
+      MG_CUDA_TRY(cudaMemcpyAsync(ps.traj, ps.psi, sizeof(double) * 2 * d, cudaMemcpyDeviceToDevice, ctx->stream));
+    }
   } else {
     MG_TRY(ws(ctx, WS_ACC, md, &ps.acc));
     if (in) {
@@ -1356,7 +1372,10 @@ int finish_prop(mg_ctx* ctx, Engine& eng, PropState& ps, double* out, int flags,
   const long long md = mat_doubles(d);
   const cudaMemcpyKind kind = (flags & MG_FLAG_HOST_PTRS) ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
   double* accf = nullptr;   // FP64 propagator
-  if (ps.output == MG_OUT_STATE) {
+  if (ps.output == MG_OUT_STATE && ps.traj) {
+    if (ps.traj_staged)
+      MG_CUDA_TRY(cudaMemcpyAsync(out, ps.traj, sizeof(double) * 2 * d * ps.traj_rows, kind, ctx->stream));
+  } else if (ps.output == MG_OUT_STATE) {
     MG_CUDA_TRY(cudaMemcpyAsync(out, ps.psi, sizeof(double) * 2 * d, kind, ctx->stream));
   } else {
     if (!ps.acc_init) MG_TRY(eng.identity(1, ps.acc));
@@ -1384,8 +1403,11 @@ int finish_prop(mg_ctx* ctx, Engine& eng, PropState& ps, double* out, int flags,
 }  // namespace
 
 int mg_evolve(mg_plan* p, int output, const double* in, double* out, int reorth_every, int flags, mg_report* rep) {
-  if (!p || !out || p->N < 1 || (output != MG_OUT_STATE && output != MG_OUT_PROPAGATOR) || reorth_every < 0)
+  if (!p || !out || p->N < 1 || reorth_every < 0 ||
+      (output != MG_OUT_STATE && output != MG_OUT_PROPAGATOR && output != MG_OUT_TRAJECTORY))
     return MG_EINVAL;
+  const bool trajectory = output == MG_OUT_TRAJECTORY;
+  if (trajectory) output = MG_OUT_STATE;
   mg_ctx* ctx = p->ctx;
   MG_CUDA_TRY(cudaSetDevice(ctx->device));
   cudaStream_t s = ctx->stream;
@@ -1399,11 +1421,12 @@ int mg_evolve(mg_plan* p, int output, const double* in, double* out, int reorth_
   PropState ps;
   ps.output = output;
   ps.d = d;
-  MG_TRY(begin_prop(ctx, eng, ps, in, flags));
+  MG_TRY(begin_prop(ctx, eng, ps, in, flags, trajectory ? out : nullptr, p->N + 1));
   if (output == MG_OUT_STATE && (p->flags & MG_FLAG_STATE_ACTION)) {
-    // action-based: exp(-i Hbar_n) applied to the state by sparse Taylor steps
+    // action-based: exp(-i Hbar_n) applied to the state (Chebyshev, sparse operators)
     MG_TRY(ensure_csr(p));
     std::vector<ActionJob> jv{action_job(p, ps.psi)};
+    jv[0].traj = ps.traj;
     MG_TRY(run_action(ctx, jv, {CsrRef{&p->csr_rowptr_h, &p->csr_col_h}}));
     const ActionJob& job = jv[0];
     if (job.status != MG_OK) {

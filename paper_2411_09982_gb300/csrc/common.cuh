@@ -138,7 +138,7 @@ int split_gemm(int d, int L, int batch, const void* abuf, const void* bbuf, doub
 
 // State propagation; see propagate.cu.
 int launch_state_chain(int n_steps, int d, const double* U, long long sU, double* psi, double* tmp,
-                       int reorth_every, int step_offset, cudaStream_t s);
+                       int reorth_every, int step_offset, cudaStream_t s, double* traj = nullptr);
 int launch_norm_defect(int d, const double* psi, double* out, cudaStream_t s);
 // A job's stretch of intervals inside a chunk of the batched path.
 struct ChainSeg {
@@ -171,6 +171,7 @@ struct ActionJob {
   double* cheb;         // N x ACTION_REC interval records (written by the bounds kernel)
   double* abuf;         // nnz complex: the interval matrix when it does not fit in shared memory
   double* psi;          // d complex, in and out
+  double* traj;         // null, or (first + N + 1) x d complex: the state after interval n at row first + n + 1
   const uint16_t* sendmask;  // cluster variant: per row, bit q set if CTA q reads that row
   int status;           // MG_OK, or set by the kernel when the job stopped early
   long long max_steps;  // operator applications after which a launch stops at an interval end (0: none)

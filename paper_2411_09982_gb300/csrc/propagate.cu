@@ -14,9 +14,10 @@ namespace mg {
 constexpr int CHAIN_THREADS = 1024;
 
 // One CTA carries psi (d complex, global) through n_steps propagators.
+// traj (may be null): psi after every step is also written to traj + (step_offset + n + 1) d.
 __device__ void chain_body(int n_steps, int d, const double* __restrict__ U, long long sU,
                            double* __restrict__ psi, int reorth_every, int step_offset, double2* sh,
-                           double* red) {
+                           double* red, double* __restrict__ traj) {
   double2* cur = sh;
   double2* nxt = sh + d;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -59,16 +60,20 @@ __device__ void chain_body(int n_steps, int d, const double* __restrict__ U, lon
       for (int i = threadIdx.x; i < d; i += blockDim.x) { cur[i].x *= inv; cur[i].y *= inv; }
       __syncthreads();
     }
+    if (traj) {
+      double2* t_out = reinterpret_cast<double2*>(traj) + (long long)done * d;
+      for (int i = threadIdx.x; i < d; i += blockDim.x) t_out[i] = cur[i];
+    }
   }
   for (int i = threadIdx.x; i < d; i += blockDim.x) reinterpret_cast<double2*>(psi)[i] = cur[i];
 }
 
 __global__ void __launch_bounds__(CHAIN_THREADS)
 state_chain_kernel(int n_steps, int d, const double* __restrict__ U, long long sU,
-                   double* __restrict__ psi, int reorth_every, int step_offset) {
+                   double* __restrict__ psi, int reorth_every, int step_offset, double* __restrict__ traj) {
   extern __shared__ double2 sh[];
   __shared__ double red[CHAIN_THREADS / 32];
-  chain_body(n_steps, d, U, sU, psi, reorth_every, step_offset, sh, red);
+  chain_body(n_steps, d, U, sU, psi, reorth_every, step_offset, sh, red, traj);
 }
 
 // Many jobs at once: CTA b carries job segs[b].job through its segment of the chunk.
@@ -78,7 +83,7 @@ multi_chain_kernel(int d, const ChainSeg* __restrict__ segs, const double* __res
   extern __shared__ double2 sh[];
   __shared__ double red[CHAIN_THREADS / 32];
   const ChainSeg g = segs[blockIdx.x];
-  chain_body(g.count, d, U + g.first * sU, sU, psi[g.job], reorth_every, g.done_before, sh, red);
+  chain_body(g.count, d, U + g.first * sU, sU, psi[g.job], reorth_every, g.done_before, sh, red, nullptr);
 }
 
 // out = U psi (one interval), rows split over CTAs: 8 warps per CTA, one row per warp.
@@ -136,15 +141,16 @@ __global__ void norm_defect_kernel(int d, const double* __restrict__ psi, double
 }
 
 // psi (device, d complex) is carried through n_steps propagators U (stride sU doubles).
-// tmp: d complex of scratch for the large-d path.
+// tmp: d complex of scratch for the large-d path.  traj (may be null): the state
+// after step n is also written to traj + (step_offset + n + 1) d complex.
 int launch_state_chain(int n_steps, int d, const double* U, long long sU, double* psi, double* tmp,
-                       int reorth_every, int step_offset, cudaStream_t s) {
+                       int reorth_every, int step_offset, cudaStream_t s, double* traj) {
   if (n_steps <= 0) return MG_OK;
   if (d <= 256) {
     int threads = d <= 32 ? ((d + 31) / 32) * 32 * 8 : CHAIN_THREADS;
     if (threads > CHAIN_THREADS) threads = CHAIN_THREADS;
     size_t smem = sizeof(double2) * 2 * d;
-    state_chain_kernel<<<1, threads, smem, s>>>(n_steps, d, U, sU, psi, reorth_every, step_offset);
+    state_chain_kernel<<<1, threads, smem, s>>>(n_steps, d, U, sU, psi, reorth_every, step_offset, traj);
     return check_launch("state_chain_kernel");
   }
   double* a = psi;
@@ -158,6 +164,9 @@ int launch_state_chain(int n_steps, int d, const double* U, long long sU, double
       normalize_kernel<<<1, 1024, 0, s>>>(d, a);
       MG_TRY(check_launch("normalize_kernel"));
     }
+    if (traj)
+      MG_CUDA_TRY(cudaMemcpyAsync(traj + (long long)done * 2 * d, a, sizeof(double) * 2 * d,
+                                  cudaMemcpyDeviceToDevice, s));
   }
   if (a != psi) MG_CUDA_TRY(cudaMemcpyAsync(psi, a, sizeof(double) * 2 * d, cudaMemcpyDeviceToDevice, s));
   return MG_OK;

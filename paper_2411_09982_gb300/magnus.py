@@ -28,6 +28,7 @@ MG_PREC_FP64 = 0
 MG_PREC_SPLIT = 1
 MG_OUT_STATE = 0
 MG_OUT_PROPAGATOR = 1
+MG_OUT_TRAJECTORY = 2
 MG_FLAG_HOST_PTRS = 1
 MG_FLAG_CHECK_HERMITIAN = 2
 MG_FLAG_NO_TRACE_SHIFT = 4
@@ -375,8 +376,9 @@ def node_samples(wl, N=None):
 
 
 def evolve_workload(ctx, wl, precision=MG_PREC_FP64, slices=6, N=None, reorth_every=0, device="cuda", order=1,
-                    flags=0):
-    """Run a workloads.Workload through mg_plan_create / mg_set_controls / mg_evolve."""
+                    flags=0, trajectory=False):
+    """Run a workloads.Workload through mg_plan_create / mg_set_controls / mg_evolve
+    (trajectory=True: the (N + 1) x d stroboscopic states of a state workload)."""
     import torch
     N = wl.N if N is None else N
     samples, w = node_samples(wl, N)
@@ -390,8 +392,9 @@ def evolve_workload(ctx, wl, precision=MG_PREC_FP64, slices=6, N=None, reorth_ev
         rep = plan.evolve(MG_OUT_PROPAGATOR, None, out, reorth_every)
     else:
         psi0 = torch.from_numpy(wl.psi0).to(device)
-        out = torch.empty(wl.d, dtype=torch.complex128, device=device)
-        rep = plan.evolve(MG_OUT_STATE, psi0, out, reorth_every)
+        shape = (N + 1, wl.d) if trajectory else (wl.d,)
+        out = torch.empty(shape, dtype=torch.complex128, device=device)
+        rep = plan.evolve(MG_OUT_TRAJECTORY if trajectory else MG_OUT_STATE, psi0, out, reorth_every)
     torch.cuda.synchronize()
     plan.close()
     return out, rep

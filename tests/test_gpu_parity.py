@@ -478,3 +478,34 @@ def test_action_state_path_rejects_unbounded_work(ctx):
     wl.H0 = wl.H0 * 100.0
     with pytest.raises(RuntimeError, match="sub-steps"):
         M.evolve_workload(ctx, wl, M.MG_PREC_FP64, flags=M.MG_FLAG_STATE_ACTION)
+
+
+# ----------------------------------------------------------------------------
+# stroboscopic trajectory output (MG_OUT_TRAJECTORY)
+# ----------------------------------------------------------------------------
+@pytest.mark.parametrize("prec,flags,tol", [(0, 0, 1e-11), (1, 0, 1e-6), (0, 8, 1e-11)])
+def test_trajectory_matches_oracle(ctx, prec, flags, tol):
+    wl = W.config(0, N=150)
+    out, rep = M.evolve_workload(ctx, wl, prec, 6, flags=flags, trajectory=True)
+    U = oracle.evolve_workload(wl, return_parts=True)[1]["U"]
+    _, ref = oracle.propagate_state(U, wl.psi0, trajectory=True)
+    got = out.cpu().numpy()
+    assert got.shape == ref.shape == (wl.N + 1, wl.d)
+    assert np.array_equal(got[0], wl.psi0)
+    assert np.abs(got - ref).max() <= tol
+
+
+def test_trajectory_large_d_and_host_buffers(ctx):
+    # d > 256 takes the one-launch-per-interval state path; host output buffer
+    wl = W.transmon_chain(n_sites=6, levels=3, J=0.01, seed=2, omega0_max=0.05, T=0.5, sigma=0.2, N=5, P=16,
+                          unitary=False)
+    samples, w = M.node_samples(wl)
+    plan = M.Plan(ctx, cuda(wl.H0), cuda(wl.Hk), M.MG_PREC_FP64, 6)
+    plan.set_controls(wl.N, wl.P, wl.t0, wl.dt, w, cuda(samples))
+    out = torch.empty((wl.N + 1, wl.d), dtype=torch.complex128).pin_memory()
+    psi0 = torch.from_numpy(wl.psi0).pin_memory()
+    plan.evolve(M.MG_OUT_TRAJECTORY, psi0, out, 0, host=True)
+    plan.close()
+    U = oracle.evolve_workload(wl, return_parts=True)[1]["U"]
+    _, ref = oracle.propagate_state(U, wl.psi0, trajectory=True)
+    assert np.abs(out.numpy() - ref).max() <= 1e-11
