@@ -385,7 +385,7 @@ def run_config(args):
                         f"bf16 digits x{args.slices} (fp32 accumulate) + f64",
                         config={"workload": wl.name, "d": wl.d, "intervals": wl.N, "quadrature_points": wl.P,
                                 "controls": wl.K, "output": "state" if state else "full propagator",
-                                "method": "action (sparse Taylor)" if args.action else "interval propagators",
+                                "method": "action (Chebyshev, sparse)" if args.action else "interval propagators",
                                 "reorth_every": reorth, "l2": "256 MiB buffer written before every timed step"},
                         roofline=gemm_roof(g, 0 if prec == M.MG_PREC_FP64 else args.slices * (args.slices + 1) // 2),
                         clocks=clk, gpu_launches=int(launches))
@@ -436,7 +436,7 @@ def run_config(args):
                         config={"workload": "uneven_batch_512", "jobs": len(jobs), "intervals_total": total,
                                 "d_min": ds[0], "d_median": ds[len(ds) // 2], "d_max": ds[-1],
                                 "output": "state",
-                                "method": "action (sparse Taylor)" if args.action else "interval propagators",
+                                "method": "action (Chebyshev, sparse)" if args.action else "interval propagators",
                                 "l2": "256 MiB buffer written before every timed step"},
                         roofline=gemm_roof(g, 0 if args.action else args.slices * (args.slices + 1) // 2),
                         clocks=clk, gpu_launches=int(launches))

@@ -642,8 +642,6 @@ int validate_prec(int precision, int L) {
 }  // namespace
 
 namespace {
-// CSR copies of H0 and the plan's Kx operators (host-built once from the dense
-// device copies), with each operator's trace mean and shifted 1-norm.
 // Host CSR of 1 + K dense d x d complex operators (`dense`, operator-major):
 // the union of their nonzeros plus the diagonal, one value array per operator.
 struct CsrHost {
