@@ -62,7 +62,7 @@ constexpr int SG_TILE_BYTES = SG_BM * SG_BK * 2;   // 8192 bytes per digit tile
 
 struct SplitGeom {
   int d, L, beta;
-  int Kp;      // padded 2d (multiple of 16)
+  int Kp;      // 2 Kh, Kh = d rounded up to 16: the K axis holds [Re (d) | 0 | Im (d) | 0], each half Kh long
   int Mp;      // padded d rows (multiple of 128)
   int Np;      // padded B rows: 128 per 64 complex columns
   long long a_item_elems() const { return (long long)L * Mp * Kp; }   // BF16 elements
@@ -83,7 +83,7 @@ SplitGeom split_geom(int d, int L) {
   g.d = d;
   g.L = L;
   g.beta = split_beta_for(d);
-  g.Kp = ceil_div(2 * d, SG_BK) * SG_BK;
+  g.Kp = 2 * ceil_div(d, 16) * 16;
   g.Mp = ceil_div(d, SG_BM) * SG_BM;
   g.Np = ceil_div(d, SG_BNC) * 2 * SG_BNC;
   return g;
@@ -181,7 +181,15 @@ __device__ __forceinline__ void make_digits(V a, int sh, int beta, __nv_bfloat16
   }
 }
 
-// A digits: rows of [Re A | Im A].  grid (ceil(Mp/8), batch), block 256 (one warp per row).
+// four BF16 digits as one 8-byte word (lowest k first)
+__device__ __forceinline__ uint2 pack4(__nv_bfloat16 a, __nv_bfloat16 b, __nv_bfloat16 c, __nv_bfloat16 e) {
+  return make_uint2((uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(b) << 16),
+                    (uint32_t)__bfloat16_as_ushort(c) | ((uint32_t)__bfloat16_as_ushort(e) << 16));
+}
+
+// A digits: rows of [Re A | 0 | Im A | 0] (halves of Kh = Kp / 2 columns).
+// grid (ceil(Mp/8), batch), block 256 (one warp per row); each lane writes the
+// digits of 4 consecutive elements per plane as one 8-byte store.
 // T = double (FP64 input) or df32 (double-float input); strides count doubles.
 template <int L, typename T>
 __global__ void __launch_bounds__(256)
@@ -192,13 +200,13 @@ slice_a_kernel(int d, int Kp, int Mp, int beta, const double* __restrict__ A, lo
   const int row = blockIdx.x * 8 + (threadIdx.x >> 5);
   const int b = blockIdx.y;
   if (row >= Mp) return;
+  const int Kh = Kp / 2;
   const long long slice_stride = (long long)Mp * Kp;
   __nv_bfloat16* o = out + (long long)b * L * slice_stride + (long long)row * Kp;
-  const __nv_bfloat16 zero = __float2bfloat16_rn(0.0f);
   if (row >= d) {
-    for (int k = lane; k < Kp; k += 32)
+    for (int k = 4 * lane; k < Kp; k += 128)
 #pragma unroll
-      for (int s = 0; s < L; ++s) o[s * slice_stride + k] = zero;
+      for (int s = 0; s < L; ++s) *reinterpret_cast<uint2*>(o + s * slice_stride + k) = make_uint2(0u, 0u);
     return;
   }
   const double* a = A + b * sA;
@@ -212,20 +220,26 @@ slice_a_kernel(int d, int Kp, int Mp, int beta, const double* __restrict__ A, lo
   if (E < -(1 << 28)) E = 0;   // all-zero row
   if (lane == 0) ea[(long long)b * Mp + row] = E;
   const int sh = beta * L - E - 1;
-  for (int k = lane; k < d; k += 32) {
-    const auto v = E_::load(a, r0 + k);
-    __nv_bfloat16 dr[L], di[L];
-    make_digits<L>(v.re, sh, beta, dr);
-    make_digits<L>(v.im, sh, beta, di);
+  const __nv_bfloat16 zero = __float2bfloat16_rn(0.0f);
+  for (int k = 4 * lane; k < Kh; k += 128) {
+    __nv_bfloat16 dr[4][L], di[4][L];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      if (k + q < d) {
+        const auto v = E_::load(a, r0 + k + q);
+        make_digits<L>(v.re, sh, beta, dr[q]);
+        make_digits<L>(v.im, sh, beta, di[q]);
+      } else {
+#pragma unroll
+        for (int s = 0; s < L; ++s) { dr[q][s] = zero; di[q][s] = zero; }
+      }
+    }
 #pragma unroll
     for (int s = 0; s < L; ++s) {
-      o[s * slice_stride + k] = dr[s];
-      o[s * slice_stride + d + k] = di[s];
+      *reinterpret_cast<uint2*>(o + s * slice_stride + k) = pack4(dr[0][s], dr[1][s], dr[2][s], dr[3][s]);
+      *reinterpret_cast<uint2*>(o + s * slice_stride + Kh + k) = pack4(di[0][s], di[1][s], di[2][s], di[3][s]);
     }
   }
-  for (int k = 2 * d + lane; k < Kp; k += 32)
-#pragma unroll
-    for (int s = 0; s < L; ++s) o[s * slice_stride + k] = zero;
 }
 
 // B digits: K-major rows of [[Br, Bi], [-Bi, Br]]^T, tile-interleaved: for the
@@ -262,7 +276,8 @@ col_exponent_kernel(int d, int Np, const double* __restrict__ B, long long sB, i
 
 constexpr int SB_KCHUNK = 32;
 // Digits of one 32 (k) x 64 (j) block: grid (ceil(d/64), ceil(d/32), batch), block 256.
-// The blocks with blockIdx.y == 0 also zero the K tail and the rows beyond d.
+// Each thread writes 4 consecutive k of one column per plane as 8-byte stores.
+// The blocks with blockIdx.y == 0 also zero the rows beyond d.
 template <int L, typename T>
 __global__ void __launch_bounds__(256)
 slice_b_kernel(int d, int Kp, int Np, int beta, const double* __restrict__ B, long long sB,
@@ -274,6 +289,7 @@ slice_b_kernel(int d, int Kp, int Np, int beta, const double* __restrict__ B, lo
   const int t = blockIdx.x, b = blockIdx.z;
   const int j0 = t * SG_BNC, k0 = blockIdx.y * SB_KCHUNK;
   const int tid = threadIdx.x;
+  const int Kh = Kp / 2;
   const double* Bb = B + b * sB;
   const long long slice_stride = (long long)Np * Kp;
   __nv_bfloat16* ob = out + (long long)b * L * slice_stride;
@@ -289,41 +305,49 @@ slice_b_kernel(int d, int Kp, int Np, int beta, const double* __restrict__ B, lo
     tile[kk][c] = v;
   }
   __syncthreads();
-  for (int e = tid; e < SB_KCHUNK * SG_BNC; e += 256) {
-    const int kk = e % SB_KCHUNK, r = e / SB_KCHUNK;
-    const int k = k0 + kk;
-    if (k >= d || j0 + r >= d) continue;
-    const V v = tile[kk][r];
-    __nv_bfloat16 dr[L], di[L];
-    make_digits<L>(v.re, shift[r], beta, dr);
-    make_digits<L>(v.im, shift[r], beta, di);
+  const __nv_bfloat16 zero = __float2bfloat16_rn(0.0f);
+  for (int e = tid; e < (SB_KCHUNK / 4) * SG_BNC; e += 256) {
+    const int g = e % (SB_KCHUNK / 4), r = e / (SB_KCHUNK / 4);
+    const int k = k0 + 4 * g;
+    if (k >= Kh || j0 + r >= d) continue;
+    __nv_bfloat16 dr[4][L], di[4][L];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      if (k + q < d) {
+        const V v = tile[4 * g + q][r];
+        make_digits<L>(v.re, shift[r], beta, dr[q]);
+        make_digits<L>(v.im, shift[r], beta, di[q]);
+      } else {
+#pragma unroll
+        for (int s = 0; s < L; ++s) { dr[q][s] = zero; di[q][s] = zero; }
+      }
+    }
     __nv_bfloat16* row_re = ob + (long long)(t * 2 * SG_BNC + r) * Kp;          // [Re | -Im]
     __nv_bfloat16* row_im = ob + (long long)(t * 2 * SG_BNC + SG_BNC + r) * Kp; // [Im | Re]
 #pragma unroll
     for (int s = 0; s < L; ++s) {
       const long long so = s * slice_stride;
-      row_re[so + k] = dr[s];
-      row_re[so + d + k] = __hneg(di[s]);
-      row_im[so + k] = di[s];
-      row_im[so + d + k] = dr[s];
+      const uint2 re = pack4(dr[0][s], dr[1][s], dr[2][s], dr[3][s]);
+      const uint2 im = pack4(di[0][s], di[1][s], di[2][s], di[3][s]);
+      const uint2 mim = pack4(__hneg(di[0][s]), __hneg(di[1][s]), __hneg(di[2][s]), __hneg(di[3][s]));
+      *reinterpret_cast<uint2*>(row_re + so + k) = re;
+      *reinterpret_cast<uint2*>(row_re + so + Kh + k) = mim;
+      *reinterpret_cast<uint2*>(row_im + so + k) = im;
+      *reinterpret_cast<uint2*>(row_im + so + Kh + k) = re;
     }
   }
   if (blockIdx.y != 0) return;
-  const __nv_bfloat16 zero = __float2bfloat16_rn(0.0f);
-  const int tail = Kp - 2 * d;
-  for (int e = tid; e < 2 * SG_BNC * tail; e += 256) {
-    const int rr = e / tail, k = 2 * d + e % tail;
-#pragma unroll
-    for (int s = 0; s < L; ++s) ob[s * slice_stride + (long long)(t * 2 * SG_BNC + rr) * Kp + k] = zero;
-  }
   const int live = min(SG_BNC, d - j0);
   if (live < SG_BNC) {
-    for (int e = tid; e < (SG_BNC - live) * 2 * d; e += 256) {
-      const int rr = live + e / (2 * d), k = e % (2 * d);
+    const int words = Kp / 4;
+    for (int e = tid; e < (SG_BNC - live) * words; e += 256) {
+      const int rr = live + e / words, k = 4 * (e % words);
 #pragma unroll
       for (int s = 0; s < L; ++s) {
-        ob[s * slice_stride + (long long)(t * 2 * SG_BNC + rr) * Kp + k] = zero;
-        ob[s * slice_stride + (long long)(t * 2 * SG_BNC + SG_BNC + rr) * Kp + k] = zero;
+        *reinterpret_cast<uint2*>(ob + s * slice_stride + (long long)(t * 2 * SG_BNC + rr) * Kp + k) =
+            make_uint2(0u, 0u);
+        *reinterpret_cast<uint2*>(ob + s * slice_stride + (long long)(t * 2 * SG_BNC + SG_BNC + rr) * Kp + k) =
+            make_uint2(0u, 0u);
       }
     }
   }
