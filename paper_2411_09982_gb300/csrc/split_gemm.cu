@@ -181,11 +181,13 @@ __device__ __forceinline__ void make_digits(V a, int sh, int beta, __nv_bfloat16
   }
 }
 
-// four BF16 digits as one 8-byte word (lowest k first)
-__device__ __forceinline__ uint2 pack4(__nv_bfloat16 a, __nv_bfloat16 b, __nv_bfloat16 c, __nv_bfloat16 e) {
-  return make_uint2((uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(b) << 16),
-                    (uint32_t)__bfloat16_as_ushort(c) | ((uint32_t)__bfloat16_as_ushort(e) << 16));
+// digit q (0..3, lowest k first) of a four-digit 8-byte word
+__device__ __forceinline__ void put_digit(uint2& w, int q, __nv_bfloat16 v) {
+  const uint32_t bits = (uint32_t)__bfloat16_as_ushort(v) << (16 * (q & 1));
+  if (q < 2) w.x |= bits; else w.y |= bits;
 }
+// the word with every digit negated (BF16 sign bits)
+__device__ __forceinline__ uint2 neg4(uint2 w) { return make_uint2(w.x ^ 0x80008000u, w.y ^ 0x80008000u); }
 
 // A digits: rows of [Re A | 0 | Im A | 0] (halves of Kh = Kp / 2 columns).
 // grid (ceil(Mp/8), batch), block 256 (one warp per row); each lane writes the
@@ -220,24 +222,25 @@ slice_a_kernel(int d, int Kp, int Mp, int beta, const double* __restrict__ A, lo
   if (E < -(1 << 28)) E = 0;   // all-zero row
   if (lane == 0) ea[(long long)b * Mp + row] = E;
   const int sh = beta * L - E - 1;
-  const __nv_bfloat16 zero = __float2bfloat16_rn(0.0f);
   for (int k = 4 * lane; k < Kh; k += 128) {
-    __nv_bfloat16 dr[4][L], di[4][L];
+    uint2 wr[L], wi[L];   // digits of the 4 elements, packed as they are made
+#pragma unroll
+    for (int s = 0; s < L; ++s) { wr[s] = make_uint2(0u, 0u); wi[s] = make_uint2(0u, 0u); }
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       if (k + q < d) {
         const auto v = E_::load(a, r0 + k + q);
-        make_digits<L>(v.re, sh, beta, dr[q]);
-        make_digits<L>(v.im, sh, beta, di[q]);
-      } else {
+        __nv_bfloat16 dr[L], di[L];
+        make_digits<L>(v.re, sh, beta, dr);
+        make_digits<L>(v.im, sh, beta, di);
 #pragma unroll
-        for (int s = 0; s < L; ++s) { dr[q][s] = zero; di[q][s] = zero; }
+        for (int s = 0; s < L; ++s) put_digit(wr[s], q, dr[s]), put_digit(wi[s], q, di[s]);
       }
     }
 #pragma unroll
     for (int s = 0; s < L; ++s) {
-      *reinterpret_cast<uint2*>(o + s * slice_stride + k) = pack4(dr[0][s], dr[1][s], dr[2][s], dr[3][s]);
-      *reinterpret_cast<uint2*>(o + s * slice_stride + Kh + k) = pack4(di[0][s], di[1][s], di[2][s], di[3][s]);
+      *reinterpret_cast<uint2*>(o + s * slice_stride + k) = wr[s];
+      *reinterpret_cast<uint2*>(o + s * slice_stride + Kh + k) = wi[s];
     }
   }
 }
@@ -305,21 +308,22 @@ slice_b_kernel(int d, int Kp, int Np, int beta, const double* __restrict__ B, lo
     tile[kk][c] = v;
   }
   __syncthreads();
-  const __nv_bfloat16 zero = __float2bfloat16_rn(0.0f);
   for (int e = tid; e < (SB_KCHUNK / 4) * SG_BNC; e += 256) {
     const int g = e % (SB_KCHUNK / 4), r = e / (SB_KCHUNK / 4);
     const int k = k0 + 4 * g;
     if (k >= Kh || j0 + r >= d) continue;
-    __nv_bfloat16 dr[4][L], di[4][L];
+    uint2 wr[L], wi[L];   // digits of the 4 elements, packed as they are made
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
+    for (int s = 0; s < L; ++s) { wr[s] = make_uint2(0u, 0u); wi[s] = make_uint2(0u, 0u); }
+#pragma unroll 1
+    for (int q = 0; q < 4; ++q) {   // one element at a time keeps the register count low
       if (k + q < d) {
         const V v = tile[4 * g + q][r];
-        make_digits<L>(v.re, shift[r], beta, dr[q]);
-        make_digits<L>(v.im, shift[r], beta, di[q]);
-      } else {
+        __nv_bfloat16 dr[L], di[L];
+        make_digits<L>(v.re, shift[r], beta, dr);
+        make_digits<L>(v.im, shift[r], beta, di);
 #pragma unroll
-        for (int s = 0; s < L; ++s) { dr[q][s] = zero; di[q][s] = zero; }
+        for (int s = 0; s < L; ++s) put_digit(wr[s], q, dr[s]), put_digit(wi[s], q, di[s]);
       }
     }
     __nv_bfloat16* row_re = ob + (long long)(t * 2 * SG_BNC + r) * Kp;          // [Re | -Im]
@@ -327,13 +331,10 @@ slice_b_kernel(int d, int Kp, int Np, int beta, const double* __restrict__ B, lo
 #pragma unroll
     for (int s = 0; s < L; ++s) {
       const long long so = s * slice_stride;
-      const uint2 re = pack4(dr[0][s], dr[1][s], dr[2][s], dr[3][s]);
-      const uint2 im = pack4(di[0][s], di[1][s], di[2][s], di[3][s]);
-      const uint2 mim = pack4(__hneg(di[0][s]), __hneg(di[1][s]), __hneg(di[2][s]), __hneg(di[3][s]));
-      *reinterpret_cast<uint2*>(row_re + so + k) = re;
-      *reinterpret_cast<uint2*>(row_re + so + Kh + k) = mim;
-      *reinterpret_cast<uint2*>(row_im + so + k) = im;
-      *reinterpret_cast<uint2*>(row_im + so + Kh + k) = re;
+      *reinterpret_cast<uint2*>(row_re + so + k) = wr[s];
+      *reinterpret_cast<uint2*>(row_re + so + Kh + k) = neg4(wi[s]);
+      *reinterpret_cast<uint2*>(row_im + so + k) = wi[s];
+      *reinterpret_cast<uint2*>(row_im + so + Kh + k) = wr[s];
     }
   }
   if (blockIdx.y != 0) return;
