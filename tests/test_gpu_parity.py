@@ -509,3 +509,32 @@ def test_trajectory_large_d_and_host_buffers(ctx):
     U = oracle.evolve_workload(wl, return_parts=True)[1]["U"]
     _, ref = oracle.propagate_state(U, wl.psi0, trajectory=True)
     assert np.abs(out.numpy() - ref).max() <= 1e-11
+
+
+@pytest.mark.parametrize("flags", [0, M.MG_FLAG_STATE_ACTION])
+def test_state_edge_cases_d1_k0_and_time_independent(ctx, flags):
+    # d = 1, no controls: psi(T) = e^{-i h T} psi0
+    wl = W.Workload("d1_k0", np.array([[2.0 + 0j]]), np.zeros((0, 1, 1), complex), W.ConstantDrive(np.zeros(0)),
+                    0.0, 1.3, 3, 4, np.array([1.0 + 0j]))
+    out, _ = M.evolve_workload(ctx, wl, M.MG_PREC_FP64, flags=flags)
+    assert abs(out.cpu().numpy()[0] - np.exp(-2.6j)) < 1e-14
+    # time-independent d = 21 (constant drive): psi(T) = exp(-i H T) psi0 for any N, incl. N = 1
+    rng = np.random.default_rng(8)
+    d = 21
+    H0, H1 = rand_herm(rng, d, 2.0), rand_herm(rng, d)
+    psi0 = rand_c(rng, d)
+    psi0 /= np.linalg.norm(psi0)
+    for N in (1, 7):
+        wl = W.Workload("const_state", H0, H1[None], W.ConstantDrive(np.array([0.3])), 0.0, 1.7, N, 4, psi0)
+        out, _ = M.evolve_workload(ctx, wl, M.MG_PREC_FP64, flags=flags)
+        ref = oracle.expm_minus_i(wl.T * (H0 + 0.3 * H1)) @ psi0
+        assert np.abs(out.cpu().numpy() - ref).max() <= 1e-12, N
+
+
+def test_trajectory_single_interval(ctx):
+    wl = W.config(0, N=1)
+    out, _ = M.evolve_workload(ctx, wl, M.MG_PREC_FP64, trajectory=True)
+    ref = oracle.evolve_workload(wl)
+    got = out.cpu().numpy()
+    assert got.shape == (2, wl.d)
+    assert np.array_equal(got[0], wl.psi0) and np.abs(got[1] - ref).max() <= 1e-13
