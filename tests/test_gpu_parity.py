@@ -532,7 +532,7 @@ def test_state_edge_cases_d1_k0_and_time_independent(ctx, flags):
 
 
 def test_trajectory_single_interval(ctx):
-    wl = W.config(0, N=1)
+    wl = W.config(0, N=1, T=0.5)   # one interval of 0.5 ns (||Hbar|| ~ 100 rad)
     out, _ = M.evolve_workload(ctx, wl, M.MG_PREC_FP64, trajectory=True)
     ref = oracle.evolve_workload(wl)
     got = out.cpu().numpy()
