@@ -48,13 +48,13 @@
 
 namespace mg {
 
-constexpr int ACTION_THREADS = 256;
+constexpr int ACTION_THREADS = 256;   // chain kernels: up to 3 CTAs per SM (80 registers)
 constexpr int ACTION_MAX_OPS = 256;
 constexpr double ACTION_ZMAX = 20.0;          // largest z = rho / s of one sub-step
 constexpr int ACTION_MAX_SUBSTEPS = 1 << 14;  // per interval
 // z <= 20 needs degrees below 64: 2 (10^{k+1} / (k+1)!) <= 2^-56 from k = 53
 constexpr int ACTION_KMAX = 64;
-static_assert(5 + ACTION_KMAX + 1 <= ACTION_REC, "interval record too small");
+static_assert(5 + ACTION_KMAX + 1 + 2 <= ACTION_REC, "interval record too small");
 
 __device__ __forceinline__ double2 cfma(double2 a, double2 b, double2 acc) {   // acc + a b
   acc.x = fma(a.x, b.x, acc.x);
@@ -109,7 +109,7 @@ __device__ int bessel_series(double z, double* J) {
 
 // One warp per (job, interval): Gershgorin bounds of Hbar_n, the sub-step
 // count and the Chebyshev coefficients.  Record layout (ACTION_REC doubles):
-// [c_n, 1/rho_n, s_n, k_t, rho_n, J_0 .. J_{k_t}]; s_n = -1 marks a
+// [c_n, 1/rho_n, s_n, k_t, rho_n, J_0 .. J_{k_t}, ..., cos c_n, sin c_n]; s_n = -1 marks a
 // non-finite bound, -2 one that needs more than ACTION_MAX_SUBSTEPS sub-steps.
 __global__ void __launch_bounds__(256) action_bounds_kernel(const ActionJob* __restrict__ jobs) {
   const ActionJob& J = jobs[blockIdx.y];
@@ -167,20 +167,56 @@ __global__ void __launch_bounds__(256) action_bounds_kernel(const ActionJob* __r
   rec[2] = (double)s;
   rec[3] = (double)kt;
   rec[4] = rho;
+  sincos(center, &rec[ACTION_REC - 1], &rec[ACTION_REC - 2]);   // the phase e^{-i c_n}: cos, sin
 }
 
-// acc + 2 (-i)^k J_k v, with twoJ = 2 J_k
-__device__ __forceinline__ double2 add_term(double2 acc, double2 v, double twoJ, int k) {
-  switch (k & 3) {
-    case 0: acc.x = fma(twoJ, v.x, acc.x); acc.y = fma(twoJ, v.y, acc.y); break;
-    case 1: acc.x = fma(twoJ, v.y, acc.x); acc.y = fma(-twoJ, v.x, acc.y); break;
-    case 2: acc.x = fma(-twoJ, v.x, acc.x); acc.y = fma(-twoJ, v.y, acc.y); break;
-    default: acc.x = fma(-twoJ, v.y, acc.x); acc.y = fma(twoJ, v.x, acc.y); break;
+
+// acc + 2 (-i)^k J_k t without a branch on k: (a, b) = (t.y, -t.x) for odd k,
+// (t.x, t.y) for even k, times +2 J_k for k mod 4 < 2 and -2 J_k otherwise
+__device__ __forceinline__ double2 add_term_sel(double2 acc, double2 t, double f, bool odd) {
+  const double a = odd ? t.y : t.x, b = odd ? -t.x : t.y;
+  return make_double2(fma(f, a, acc.x), fma(f, b, acc.y));
+}
+
+// One sub-step on rows threadIdx.x, threadIdx.x + blockDim.x, ... of d:
+// acc <- J_0 acc + 2 sum_{k=1..kt} (-i)^k J_k T_k(X) acc, vx / vy the recurrence
+// vectors.  Inlined at two call sites, one with the interval matrix and pattern
+// in shared memory and one with them in global memory, so that each copy
+// addresses its operands directly rather than through generic pointers.
+__device__ __forceinline__ void cheb_substep(int d, int kt, const double* Jk, const double2* A, const int* col,
+                                             const int* rp, double2* acc, double2* vx, double2* vy) {
+  for (int i = threadIdx.x; i < d; i += blockDim.x) {
+    const double2 v = acc[i];
+    vx[i] = v;
+    acc[i] = make_double2(Jk[0] * v.x, Jk[0] * v.y);
   }
-  return acc;
+  __syncthreads();
+  for (int k = 1; k <= kt; ++k) {
+    // k odd: vy <- 2 X vx - vy (k = 1: X vx); k even: vx <- 2 X vy - vx
+    const double2* cur = (k & 1) ? vx : vy;
+    double2* old = (k & 1) ? vy : vx;
+    const double two = k == 1 ? 1.0 : 2.0;
+    const double f = ((k & 3) < 2 ? 2.0 : -2.0) * Jk[k];
+    const bool odd = k & 1;
+    for (int i = threadIdx.x; i < d; i += blockDim.x) {
+      double2 y0 = make_double2(0.0, 0.0), y1 = make_double2(0.0, 0.0);
+      const int e1 = rp[i + 1];
+      int e = rp[i];
+      for (; e + 1 < e1; e += 2) {   // two independent accumulators
+        y0 = cfma(A[e], cur[col[e]], y0);
+        y1 = cfma(A[e + 1], cur[col[e + 1]], y1);
+      }
+      if (e < e1) y0 = cfma(A[e], cur[col[e]], y0);
+      const double2 o = k > 1 ? old[i] : make_double2(0.0, 0.0);
+      const double2 t = make_double2(fma(two, y0.x + y1.x, -o.x), fma(two, y0.y + y1.y, -o.y));
+      old[i] = t;
+      acc[i] = add_term_sel(acc[i], t, f, odd);
+    }
+    __syncthreads();
+  }
 }
 
-__global__ void __launch_bounds__(ACTION_THREADS)
+__global__ void __launch_bounds__(ACTION_THREADS, 3)
 action_chain_kernel(ActionJob* __restrict__ jobs, int dmax, int nnz_cap) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double cn[ACTION_MAX_OPS];
@@ -195,7 +231,6 @@ action_chain_kernel(ActionJob* __restrict__ jobs, int dmax, int nnz_cap) {
   double2* A = in_smem ? acc + 3 * dmax : reinterpret_cast<double2*>(J.abuf);
   int* col_s = reinterpret_cast<int*>(acc + 3 * dmax + nnz_cap);
   int* rp_s = col_s + nnz_cap;
-  const int* col = in_smem ? col_s : J.col;
   const int* rp = in_smem ? rp_s : J.rowptr;
   if (in_smem) {
     for (int e = threadIdx.x; e < J.nnz; e += blockDim.x) col_s[e] = J.col[e];
@@ -240,44 +275,14 @@ action_chain_kernel(ActionJob* __restrict__ jobs, int dmax, int nnz_cap) {
     }
     __syncthreads();
     for (int sub = 0; sub < s; ++sub) {
-      // T_0 v = v (in vx); acc = J_0 v
-      for (int i = threadIdx.x; i < d; i += blockDim.x) {
-        const double2 v = acc[i];
-        vx[i] = v;
-        acc[i] = make_double2(Jk[0] * v.x, Jk[0] * v.y);
-      }
-      __syncthreads();
-      for (int k = 1; k <= kt; ++k) {
-        // k odd: vy <- 2 X vx - vy (k = 1: X vx); k even: vx <- 2 X vy - vx
-        const double2* cur = (k & 1) ? vx : vy;
-        double2* old = (k & 1) ? vy : vx;
-        const double two = k == 1 ? 1.0 : 2.0;
-        const double twoJ = 2.0 * Jk[k];
-        for (int i = threadIdx.x; i < d; i += blockDim.x) {
-          double2 y0 = make_double2(0.0, 0.0), y1 = make_double2(0.0, 0.0);
-          const int e1 = rp[i + 1];
-          int e = rp[i];
-          for (; e + 1 < e1; e += 2) {   // two independent accumulators
-            y0 = cfma(A[e], cur[col[e]], y0);
-            y1 = cfma(A[e + 1], cur[col[e + 1]], y1);
-          }
-          if (e < e1) y0 = cfma(A[e], cur[col[e]], y0);
-          double2 t = make_double2(two * (y0.x + y1.x), two * (y0.y + y1.y));
-          if (k > 1) {
-            const double2 o = old[i];
-            t.x -= o.x;
-            t.y -= o.y;
-          }
-          old[i] = t;
-          acc[i] = add_term(acc[i], t, twoJ, k);
-        }
-        __syncthreads();
-      }
+      if (in_smem)
+        cheb_substep(d, kt, Jk, acc + 3 * dmax, col_s, rp_s, acc, vx, vy);
+      else
+        cheb_substep(d, kt, Jk, reinterpret_cast<const double2*>(J.abuf), J.col, J.rowptr, acc, vx, vy);
       matvecs += kt;
     }
-    // exact phase of the spectral centre
-    double sn, cs;
-    sincos(center, &sn, &cs);
+    // exact phase of the spectral centre (cos, sin from the bounds kernel)
+    const double cs = rec[ACTION_REC - 2], sn = rec[ACTION_REC - 1];
     double2* trow = J.traj ? reinterpret_cast<double2*>(J.traj) + (long long)(J.first + n + 1) * d : nullptr;
     for (int i = threadIdx.x; i < d; i += blockDim.x) {
       const double2 v = acc[i];
@@ -299,12 +304,44 @@ action_chain_kernel(ActionJob* __restrict__ jobs, int dmax, int nnz_cap) {
   }
 }
 
+// The recurrence of one sub-step in the cluster variant (own rows r0 .. r0 + nr,
+// local pattern offsets rp); inlined once for on-chip and once for global
+// operands, as cheb_substep.
+__device__ __forceinline__ void cluster_recurrence(cooperative_groups::cluster_group& cl, int kt, const double* Jk,
+                                                   int r0, int nr, const double2* A, const int* col, const int* rp,
+                                                   const uint16_t* sendmask, double2* acc, double2* vx,
+                                                   double2* vy) {
+  for (int k = 1; k <= kt; ++k) {
+    const double2* cur = (k & 1) ? vx : vy;
+    double2* old = (k & 1) ? vy : vx;
+    const double two = k == 1 ? 1.0 : 2.0;
+    const double f = ((k & 3) < 2 ? 2.0 : -2.0) * Jk[k];
+    const bool odd = k & 1;
+    for (int li = threadIdx.x; li < nr; li += blockDim.x) {
+      const int i = r0 + li;
+      double2 y0 = make_double2(0.0, 0.0), y1 = make_double2(0.0, 0.0);
+      const int e1 = rp[li + 1];
+      int e = rp[li];
+      for (; e + 1 < e1; e += 2) {
+        y0 = cfma(A[e], cur[col[e]], y0);
+        y1 = cfma(A[e + 1], cur[col[e + 1]], y1);
+      }
+      if (e < e1) y0 = cfma(A[e], cur[col[e]], y0);
+      const double2 o = k > 1 ? old[i] : make_double2(0.0, 0.0);
+      const double2 t = make_double2(fma(two, y0.x + y1.x, -o.x), fma(two, y0.y + y1.y, -o.y));
+      acc[li] = add_term_sel(acc[li], t, f, odd);
+      for (unsigned m = sendmask[i]; m; m &= m - 1) cl.map_shared_rank(old, __ffs(m) - 1)[i] = t;
+    }
+    cl.sync();
+  }
+}
+
 // One cluster of C CTAs per job (blockIdx.x / C); CTA r of the cluster owns
 // rows [r * ceil(d / C), ...).  Shared memory: full copies of the two
 // recurrence vectors (dmax each), the state of the own rows (rows_max), then,
 // where cap_loc > 0 and the job's own-row nonzeros fit, the own rows' interval
 // matrix and column indices; the own rows' local row offsets always.
-__global__ void __launch_bounds__(ACTION_THREADS)
+__global__ void __launch_bounds__(ACTION_THREADS, 3)
 action_chain_cluster_kernel(ActionJob* __restrict__ jobs, int dmax, int cap_loc) {
   namespace cg = cooperative_groups;
   cg::cluster_group cl = cg::this_cluster();
@@ -331,7 +368,6 @@ action_chain_cluster_kernel(ActionJob* __restrict__ jobs, int dmax, int cap_loc)
   int* col_s = reinterpret_cast<int*>(A_s + cap_loc);
   int* rp = col_s + cap_loc;   // rows_max + 1 local offsets
   double2* A = in_smem ? A_s : reinterpret_cast<double2*>(J.abuf) + e_base;
-  const int* col = in_smem ? col_s : J.col + e_base;
   for (int li = threadIdx.x; li <= nr; li += blockDim.x) rp[li] = J.rowptr[r0 + li] - e_base;
   if (in_smem)
     for (int e = threadIdx.x; e < nnz_loc; e += blockDim.x) col_s[e] = J.col[e_base + e];
@@ -382,36 +418,14 @@ action_chain_cluster_kernel(ActionJob* __restrict__ jobs, int dmax, int cap_loc)
         for (unsigned m = J.sendmask[r0 + li]; m; m &= m - 1) cl.map_shared_rank(vx, __ffs(m) - 1)[r0 + li] = v;
       }
       cl.sync();
-      for (int k = 1; k <= kt; ++k) {
-        const double2* cur = (k & 1) ? vx : vy;
-        double2* old = (k & 1) ? vy : vx;
-        const double two = k == 1 ? 1.0 : 2.0;
-        const double twoJ = 2.0 * Jk[k];
-        for (int li = threadIdx.x; li < nr; li += blockDim.x) {
-          const int i = r0 + li;
-          double2 y0 = make_double2(0.0, 0.0), y1 = make_double2(0.0, 0.0);
-          const int e1 = rp[li + 1];
-          int e = rp[li];
-          for (; e + 1 < e1; e += 2) {
-            y0 = cfma(A[e], cur[col[e]], y0);
-            y1 = cfma(A[e + 1], cur[col[e + 1]], y1);
-          }
-          if (e < e1) y0 = cfma(A[e], cur[col[e]], y0);
-          double2 t = make_double2(two * (y0.x + y1.x), two * (y0.y + y1.y));
-          if (k > 1) {
-            const double2 o = old[i];
-            t.x -= o.x;
-            t.y -= o.y;
-          }
-          acc[li] = add_term(acc[li], t, twoJ, k);
-          for (unsigned m = J.sendmask[i]; m; m &= m - 1) cl.map_shared_rank(old, __ffs(m) - 1)[i] = t;
-        }
-        cl.sync();
-      }
+      if (in_smem)
+        cluster_recurrence(cl, kt, Jk, r0, nr, A_s, col_s, rp, J.sendmask, acc, vx, vy);
+      else
+        cluster_recurrence(cl, kt, Jk, r0, nr, reinterpret_cast<const double2*>(J.abuf) + e_base, J.col + e_base, rp,
+                           J.sendmask, acc, vx, vy);
       matvecs += kt;
     }
-    double sn, cs;
-    sincos(center, &sn, &cs);
+    const double cs = rec[ACTION_REC - 2], sn = rec[ACTION_REC - 1];
     double2* trow = J.traj ? reinterpret_cast<double2*>(J.traj) + (long long)(J.first + n + 1) * d + r0 : nullptr;
     for (int li = threadIdx.x; li < nr; li += blockDim.x) {
       const double2 v = acc[li];
