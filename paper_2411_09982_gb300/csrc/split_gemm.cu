@@ -62,11 +62,13 @@ constexpr int SG_TILE_BYTES = SG_BM * SG_BK * 2;   // 8192 bytes per digit tile
 
 struct SplitGeom {
   int d, L, beta;
-  int Kp;      // 2 Kh, Kh = d rounded up to 16: the K axis holds [Re (d) | 0 | Im (d) | 0], each half Kh long
+  int Kp;      // 2 Kh, Kh = d rounded up to 32: the K axis holds [Re (d) | 0 | Im (d) | 0], each half Kh long
   int Mp;      // padded d rows (multiple of 128)
-  int Np;      // padded B rows: 128 per 64 complex columns
+  int Np;      // 2 x padded d columns (128 per 64 complex columns)
+  int Kh() const { return Kp / 2; }
   long long a_item_elems() const { return (long long)L * Mp * Kp; }   // BF16 elements
-  long long b_item_elems() const { return (long long)L * Np * Kp; }
+  // B: per digit, two planes (Re B, Im B) of Np / 2 rows (one per column of B) of Kh
+  long long b_item_elems() const { return (long long)L * Np * Kh(); }
 };
 
 int split_beta_for(int d) {
@@ -83,7 +85,7 @@ SplitGeom split_geom(int d, int L) {
   g.d = d;
   g.L = L;
   g.beta = split_beta_for(d);
-  g.Kp = 2 * ceil_div(d, 16) * 16;
+  g.Kp = 2 * ceil_div(d, SG_BK) * SG_BK;   // each half a whole number of K stages
   g.Mp = ceil_div(d, SG_BM) * SG_BM;
   g.Np = ceil_div(d, SG_BNC) * 2 * SG_BNC;
   return g;
@@ -245,9 +247,12 @@ slice_a_kernel(int d, int Kp, int Mp, int beta, const double* __restrict__ A, lo
   }
 }
 
-// B digits: K-major rows of [[Br, Bi], [-Bi, Br]]^T, tile-interleaved: for the
-// 64 complex columns of tile t, rows 128t + r hold [Re B[:, j] | -Im B[:, j]] and
-// rows 128t + 64 + r hold [Im B[:, j] | Re B[:, j]] (j = 64t + r).
+// B digits: for every digit, two planes of K-major rows, plane 0 = Re B and
+// plane 1 = Im B: row j of a plane holds column j of that part of B along k
+// (Kh = Kp / 2 entries, zero beyond d); rows j >= d up to Np / 2 are zero.  The
+// product kernel reads each plane where the real embedding
+// [[Br, Bi], [-Bi, Br]] needs it (the minus through the MMA's negate flag), so
+// the digits are stored once.
 // Two launches with many CTAs each (a column-exponent pass, then the digits of
 // 32 x 64 blocks), so that the HBM-bound work has enough warps in flight.
 
@@ -292,12 +297,13 @@ slice_b_kernel(int d, int Kp, int Np, int beta, const double* __restrict__ B, lo
   const int t = blockIdx.x, b = blockIdx.z;
   const int j0 = t * SG_BNC, k0 = blockIdx.y * SB_KCHUNK;
   const int tid = threadIdx.x;
-  const int Kh = Kp / 2;
+  const int Kh = Kp / 2, rows = Np / 2;
   const double* Bb = B + b * sB;
-  const long long slice_stride = (long long)Np * Kp;
+  const long long plane_stride = (long long)rows * Kh;
+  const long long slice_stride = 2 * plane_stride;
   __nv_bfloat16* ob = out + (long long)b * L * slice_stride;
   if (tid < SG_BNC) {
-    int E = j0 + tid < d ? eb[(long long)b * (Np / 2) + j0 + tid] : 0;
+    int E = j0 + tid < d ? eb[(long long)b * rows + j0 + tid] : 0;
     if (E < -(1 << 28)) E = 0;   // all-zero column
     shift[tid] = beta * L - E - 1;
   }
@@ -326,28 +332,25 @@ slice_b_kernel(int d, int Kp, int Np, int beta, const double* __restrict__ B, lo
         for (int s = 0; s < L; ++s) put_digit(wr[s], q, dr[s]), put_digit(wi[s], q, di[s]);
       }
     }
-    __nv_bfloat16* row_re = ob + (long long)(t * 2 * SG_BNC + r) * Kp;          // [Re | -Im]
-    __nv_bfloat16* row_im = ob + (long long)(t * 2 * SG_BNC + SG_BNC + r) * Kp; // [Im | Re]
+    __nv_bfloat16* row_re = ob + (long long)(j0 + r) * Kh;                 // plane 0: Re B[:, j]
+    __nv_bfloat16* row_im = ob + plane_stride + (long long)(j0 + r) * Kh;  // plane 1: Im B[:, j]
 #pragma unroll
     for (int s = 0; s < L; ++s) {
       const long long so = s * slice_stride;
       *reinterpret_cast<uint2*>(row_re + so + k) = wr[s];
-      *reinterpret_cast<uint2*>(row_re + so + Kh + k) = neg4(wi[s]);
       *reinterpret_cast<uint2*>(row_im + so + k) = wi[s];
-      *reinterpret_cast<uint2*>(row_im + so + Kh + k) = wr[s];
     }
   }
   if (blockIdx.y != 0) return;
   const int live = min(SG_BNC, d - j0);
   if (live < SG_BNC) {
-    const int words = Kp / 4;
+    const int words = Kh / 4;
     for (int e = tid; e < (SG_BNC - live) * words; e += 256) {
       const int rr = live + e / words, k = 4 * (e % words);
 #pragma unroll
       for (int s = 0; s < L; ++s) {
-        *reinterpret_cast<uint2*>(ob + s * slice_stride + (long long)(t * 2 * SG_BNC + rr) * Kp + k) =
-            make_uint2(0u, 0u);
-        *reinterpret_cast<uint2*>(ob + s * slice_stride + (long long)(t * 2 * SG_BNC + SG_BNC + rr) * Kp + k) =
+        *reinterpret_cast<uint2*>(ob + s * slice_stride + (long long)(j0 + rr) * Kh + k) = make_uint2(0u, 0u);
+        *reinterpret_cast<uint2*>(ob + s * slice_stride + plane_stride + (long long)(j0 + rr) * Kh + k) =
             make_uint2(0u, 0u);
       }
     }
@@ -396,6 +399,23 @@ __device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, u
       "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes"
       " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(smem_u32(dst)),
       "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void tma_load_5d(void* dst, const CUtensorMap* map, uint64_t* bar, int c0, int c1,
+                                            int c2, int c3, int c4) {
+  asm volatile(
+      "cp.async.bulk.tensor.5d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void tma_load_5d_mc(void* dst, const CUtensorMap* map, uint64_t* bar, int c0, int c1,
+                                               int c2, int c3, int c4, uint16_t mask) {
+  asm volatile(
+      "cp.async.bulk.tensor.5d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster"
+      " [%0], [%1, {%2, %3, %4, %5, %6}], [%7], %8;" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(smem_u32(bar)),
+      "h"(mask)
       : "memory");
 }
 __device__ __forceinline__ void tma_load_4d_mc(void* dst, const CUtensorMap* map, uint64_t* bar, int c0, int c1,
@@ -464,6 +484,9 @@ __device__ __forceinline__ uint64_t sw64_kmajor_desc(uint32_t saddr) {
 
 // Instruction descriptor: kind::f16, A = B = BF16, D = F32, both K-major, M = 128, N = 128.
 constexpr uint32_t kIdescBf16 = (1u << 4) | (1u << 7) | (1u << 10) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
+// N = 64 halves of the tile for the imaginary part of K; the first negates B (bit 14)
+constexpr uint32_t kIdescBf16N64 = (1u << 4) | (1u << 7) | (1u << 10) | ((64u >> 3) << 17) | ((128u >> 4) << 24);
+constexpr uint32_t kIdescBf16N64NegB = kIdescBf16N64 | (1u << 14);
 
 constexpr int SG_THREADS = 320;   // producer warp, MMA warp, 8 epilogue warps
 constexpr int SG_EPI_WARPS = 8;
@@ -519,6 +542,7 @@ split_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nt = blockIdx.x, mt = blockIdx.y, b = blockIdx.z;
   const int num_k = Kp / SG_BK;
+  const int nkh = num_k / 2;   // K stages of the real half
 
   const uint32_t crank = CM > 1 ? cluster_rank() : 0u;
   if (threadIdx.x == 0) {
@@ -565,15 +589,17 @@ split_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
         unsigned char* st = smem + s * STAGE_BYTES;
         mbar_expect_tx(&full[s], STAGE_BYTES);
         tma_load_4d(st, &tmA, &full[s], kb * SG_BK, mt * SG_BM, 0, b);
+        // B: the same K range of both planes (the real and imaginary halves of K read
+        // the same B digits; the MMA warp assigns them to the outputs)
+        const int kbb = (kb < nkh ? kb : kb - nkh) * SG_BK;
         if (CM == 1) {
-          tma_load_4d(st + L * SG_TILE_BYTES, &tmB, &full[s], kb * SG_BK, nt * 2 * SG_BNC, 0, b);
+          tma_load_5d(st + L * SG_TILE_BYTES, &tmB, &full[s], kbb, nt * SG_BNC, 0, 0, b);
         } else {
-          // this CTA's half (64 of the 128 B rows) of every digit tile, to both CTAs
+          // this CTA's plane (64 rows) of every digit tile, to both CTAs
 #pragma unroll
           for (int sd = 0; sd < L; ++sd)
-            tma_load_4d_mc(st + L * SG_TILE_BYTES + sd * SG_TILE_BYTES + crank * (SG_TILE_BYTES / 2), &tmBh,
-                           &full[s], kb * SG_BK, nt * 2 * SG_BNC + (int)crank * (SG_BM / 2), sd, b,
-                           (uint16_t)((1u << CM) - 1u));
+            tma_load_5d_mc(st + L * SG_TILE_BYTES + sd * SG_TILE_BYTES + crank * (SG_TILE_BYTES / 2), &tmBh,
+                           &full[s], kbb, nt * SG_BNC, (int)crank, sd, b, (uint16_t)((1u << CM) - 1u));
         }
         issued = kb + 1;
       }
@@ -598,6 +624,10 @@ split_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
         const uint32_t a0 = smem_u32(smem + s * STAGE_BYTES);
         const uint32_t b0 = a0 + L * SG_TILE_BYTES;
         bool first[SG_GROUPS] = {kb == 0, kb == 0, kb == 0, kb == 0};
+        // B tile rows: 0..63 = Re B columns, 64..127 = Im B columns.  Real half of K
+        // (A = Re A): one N = 128 MMA gives Re C += Ar Br and Im C += Ar Bi.  Imaginary
+        // half (A = Im A): Re C -= Ai Bi (rows 64..127, negated) and Im C += Ai Br (rows 0..63).
+        const bool imag = kb >= nkh;
 #pragma unroll
         for (int kk = 0; kk < SG_BK / SG_MMA_K; ++kk) {
 #pragma unroll
@@ -607,8 +637,14 @@ split_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
               const int g = (sa + sb) < SG_GROUPS - 1 ? (sa + sb) : SG_GROUPS - 1;
               const uint32_t acc = first[g] ? 0u : 1u;
               first[g] = false;
-              tc_mma_bf16(tmem + g * 128, sw64_kmajor_desc(a0 + sa * SG_TILE_BYTES + kk * SG_MMA_K * 2),
-                          sw64_kmajor_desc(b0 + sb * SG_TILE_BYTES + kk * SG_MMA_K * 2), kIdescBf16, acc);
+              const uint64_t ad = sw64_kmajor_desc(a0 + sa * SG_TILE_BYTES + kk * SG_MMA_K * 2);
+              const uint32_t bt = b0 + sb * SG_TILE_BYTES + kk * SG_MMA_K * 2;
+              if (!imag) {
+                tc_mma_bf16(tmem + g * 128, ad, sw64_kmajor_desc(bt), kIdescBf16, acc);
+              } else {
+                tc_mma_bf16(tmem + g * 128, ad, sw64_kmajor_desc(bt + SG_TILE_BYTES / 2), kIdescBf16N64NegB, acc);
+                tc_mma_bf16(tmem + g * 128 + SG_BNC, ad, sw64_kmajor_desc(bt), kIdescBf16N64, acc);
+              }
             }
           }
         }
@@ -733,6 +769,24 @@ static int get_encoder() {
 }
 
 // 4-D map over digit tiles: (k, row, slice, batch), box (32, box_rows, box_slices, 1), SWIZZLE_64B.
+// B digits: dims {Kh, rows (= Np / 2), 2 planes, L, batch}; box {32, 64, planes, digits, 1}
+static int make_bplane_map(CUtensorMap* map, const void* base, int Kh, int rows, int L, int batch, int box_planes,
+                           int box_digits) {
+  MG_TRY(get_encoder());
+  cuuint64_t dims[5] = {(cuuint64_t)Kh, (cuuint64_t)rows, 2, (cuuint64_t)L, (cuuint64_t)batch};
+  cuuint64_t strides[4] = {(cuuint64_t)Kh * 2, (cuuint64_t)rows * Kh * 2, (cuuint64_t)2 * rows * Kh * 2,
+                           (cuuint64_t)L * 2 * rows * Kh * 2};
+  cuuint32_t box[5] = {(cuuint32_t)SG_BK, (cuuint32_t)SG_BNC, (cuuint32_t)box_planes, (cuuint32_t)box_digits, 1};
+  cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+  CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<void*>(base), dims, strides, box,
+                        estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    set_last_message("cuTensorMapEncodeTiled failed (%d): Kh=%d rows=%d L=%d batch=%d", (int)r, Kh, rows, L, batch);
+    return MG_ECUDA;
+  }
+  return MG_OK;
+}
 static int make_digit_map(CUtensorMap* map, const void* base, int Kp, int rows, int L, int batch,
                           int box_rows = SG_BM, int box_slices = -1) {
   MG_TRY(get_encoder());
@@ -765,8 +819,8 @@ static int launch_split_gemm_L(const SplitGeom& g, int batch, const __nv_bfloat1
   constexpr int STAGES = stages_for<L>();
   CUtensorMap ma, mb, mbh;
   MG_TRY(make_digit_map(&ma, Ad, g.Kp, g.Mp, L, batch));
-  MG_TRY(make_digit_map(&mb, Bd, g.Kp, g.Np, L, batch));
-  MG_TRY(make_digit_map(&mbh, Bd, g.Kp, g.Np, L, batch, SG_BM / 2, 1));
+  MG_TRY(make_bplane_map(&mb, Bd, g.Kh(), g.Np / 2, L, batch, 2, L));
+  MG_TRY(make_bplane_map(&mbh, Bd, g.Kh(), g.Np / 2, L, batch, 1, 1));
   const size_t ring = std::max<size_t>((size_t)STAGES * 2 * L * SG_TILE_BYTES, (size_t)SG_EPI_BYTES);
   const size_t smem = ring + 1024 /*barriers, exponents*/ + 1024 /*align*/;
   const int mtiles = g.Mp / SG_BM;
