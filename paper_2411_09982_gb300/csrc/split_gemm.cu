@@ -67,8 +67,8 @@ struct SplitGeom {
   int Np;      // 2 x padded d columns (128 per 64 complex columns)
   int Kh() const { return Kp / 2; }
   long long a_item_elems() const { return (long long)L * Mp * Kp; }   // BF16 elements
-  // B: per digit, two planes (Re B, Im B) of Np / 2 rows (one per column of B) of Kh
-  long long b_item_elems() const { return (long long)L * Np * Kh(); }
+  // B: per digit, three planes (-Im B, Re B, Im B) of Np / 2 rows (one per column of B) of Kh
+  long long b_item_elems() const { return (long long)L * 3 * (Np / 2) * Kh(); }
 };
 
 int split_beta_for(int d) {
@@ -247,12 +247,12 @@ slice_a_kernel(int d, int Kp, int Mp, int beta, const double* __restrict__ A, lo
   }
 }
 
-// B digits: for every digit, two planes of K-major rows, plane 0 = Re B and
-// plane 1 = Im B: row j of a plane holds column j of that part of B along k
+// B digits: for every digit, three planes of K-major rows in the order
+// -Im B, Re B, Im B: row j of a plane holds column j of that part of B along k
 // (Kh = Kp / 2 entries, zero beyond d); rows j >= d up to Np / 2 are zero.  The
-// product kernel reads each plane where the real embedding
-// [[Br, Bi], [-Bi, Br]] needs it (the minus through the MMA's negate flag), so
-// the digits are stored once.
+// real embedding [[Br, Bi], [-Bi, Br]] needs, for the real half of K, the rows
+// [Br; Bi] (planes 1, 2) and, for the imaginary half, [-Bi; Br] (planes 0, 1):
+// both are two consecutive planes, so one box per stage loads them.
 // Two launches with many CTAs each (a column-exponent pass, then the digits of
 // 32 x 64 blocks), so that the HBM-bound work has enough warps in flight.
 
@@ -300,7 +300,7 @@ slice_b_kernel(int d, int Kp, int Np, int beta, const double* __restrict__ B, lo
   const int Kh = Kp / 2, rows = Np / 2;
   const double* Bb = B + b * sB;
   const long long plane_stride = (long long)rows * Kh;
-  const long long slice_stride = 2 * plane_stride;
+  const long long slice_stride = 3 * plane_stride;
   __nv_bfloat16* ob = out + (long long)b * L * slice_stride;
   if (tid < SG_BNC) {
     int E = j0 + tid < d ? eb[(long long)b * rows + j0 + tid] : 0;
@@ -332,13 +332,13 @@ slice_b_kernel(int d, int Kp, int Np, int beta, const double* __restrict__ B, lo
         for (int s = 0; s < L; ++s) put_digit(wr[s], q, dr[s]), put_digit(wi[s], q, di[s]);
       }
     }
-    __nv_bfloat16* row_re = ob + (long long)(j0 + r) * Kh;                 // plane 0: Re B[:, j]
-    __nv_bfloat16* row_im = ob + plane_stride + (long long)(j0 + r) * Kh;  // plane 1: Im B[:, j]
+    __nv_bfloat16* row = ob + (long long)(j0 + r) * Kh;   // plane 0: -Im B, 1: Re B, 2: Im B
 #pragma unroll
     for (int s = 0; s < L; ++s) {
       const long long so = s * slice_stride;
-      *reinterpret_cast<uint2*>(row_re + so + k) = wr[s];
-      *reinterpret_cast<uint2*>(row_im + so + k) = wi[s];
+      *reinterpret_cast<uint2*>(row + so + k) = neg4(wi[s]);
+      *reinterpret_cast<uint2*>(row + so + plane_stride + k) = wr[s];
+      *reinterpret_cast<uint2*>(row + so + 2 * plane_stride + k) = wi[s];
     }
   }
   if (blockIdx.y != 0) return;
@@ -348,11 +348,11 @@ slice_b_kernel(int d, int Kp, int Np, int beta, const double* __restrict__ B, lo
     for (int e = tid; e < (SG_BNC - live) * words; e += 256) {
       const int rr = live + e / words, k = 4 * (e % words);
 #pragma unroll
-      for (int s = 0; s < L; ++s) {
-        *reinterpret_cast<uint2*>(ob + s * slice_stride + (long long)(j0 + rr) * Kh + k) = make_uint2(0u, 0u);
-        *reinterpret_cast<uint2*>(ob + s * slice_stride + plane_stride + (long long)(j0 + rr) * Kh + k) =
-            make_uint2(0u, 0u);
-      }
+      for (int s = 0; s < L; ++s)
+#pragma unroll
+        for (int pl = 0; pl < 3; ++pl)
+          *reinterpret_cast<uint2*>(ob + s * slice_stride + pl * plane_stride + (long long)(j0 + rr) * Kh + k) =
+              make_uint2(0u, 0u);
     }
   }
 }
@@ -484,9 +484,6 @@ __device__ __forceinline__ uint64_t sw64_kmajor_desc(uint32_t saddr) {
 
 // Instruction descriptor: kind::f16, A = B = BF16, D = F32, both K-major, M = 128, N = 128.
 constexpr uint32_t kIdescBf16 = (1u << 4) | (1u << 7) | (1u << 10) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
-// N = 64 halves of the tile for the imaginary part of K; the first negates B (bit 14)
-constexpr uint32_t kIdescBf16N64 = (1u << 4) | (1u << 7) | (1u << 10) | ((64u >> 3) << 17) | ((128u >> 4) << 24);
-constexpr uint32_t kIdescBf16N64NegB = kIdescBf16N64 | (1u << 14);
 
 constexpr int SG_THREADS = 320;   // producer warp, MMA warp, 8 epilogue warps
 constexpr int SG_EPI_WARPS = 8;
@@ -589,17 +586,19 @@ split_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
         unsigned char* st = smem + s * STAGE_BYTES;
         mbar_expect_tx(&full[s], STAGE_BYTES);
         tma_load_4d(st, &tmA, &full[s], kb * SG_BK, mt * SG_BM, 0, b);
-        // B: the same K range of both planes (the real and imaginary halves of K read
-        // the same B digits; the MMA warp assigns them to the outputs)
-        const int kbb = (kb < nkh ? kb : kb - nkh) * SG_BK;
+        // B: the same K range in both halves of K; planes [Re B; Im B] (1, 2) for the
+        // real half, [-Im B; Re B] (0, 1) for the imaginary half
+        const bool imag = kb >= nkh;
+        const int kbb = (imag ? kb - nkh : kb) * SG_BK;
+        const int plane0 = imag ? 0 : 1;
         if (CM == 1) {
-          tma_load_5d(st + L * SG_TILE_BYTES, &tmB, &full[s], kbb, nt * SG_BNC, 0, 0, b);
+          tma_load_5d(st + L * SG_TILE_BYTES, &tmB, &full[s], kbb, nt * SG_BNC, plane0, 0, b);
         } else {
           // this CTA's plane (64 rows) of every digit tile, to both CTAs
 #pragma unroll
           for (int sd = 0; sd < L; ++sd)
             tma_load_5d_mc(st + L * SG_TILE_BYTES + sd * SG_TILE_BYTES + crank * (SG_TILE_BYTES / 2), &tmBh,
-                           &full[s], kbb, nt * SG_BNC, (int)crank, sd, b, (uint16_t)((1u << CM) - 1u));
+                           &full[s], kbb, nt * SG_BNC, plane0 + (int)crank, sd, b, (uint16_t)((1u << CM) - 1u));
         }
         issued = kb + 1;
       }
@@ -624,10 +623,6 @@ split_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
         const uint32_t a0 = smem_u32(smem + s * STAGE_BYTES);
         const uint32_t b0 = a0 + L * SG_TILE_BYTES;
         bool first[SG_GROUPS] = {kb == 0, kb == 0, kb == 0, kb == 0};
-        // B tile rows: 0..63 = Re B columns, 64..127 = Im B columns.  Real half of K
-        // (A = Re A): one N = 128 MMA gives Re C += Ar Br and Im C += Ar Bi.  Imaginary
-        // half (A = Im A): Re C -= Ai Bi (rows 64..127, negated) and Im C += Ai Br (rows 0..63).
-        const bool imag = kb >= nkh;
 #pragma unroll
         for (int kk = 0; kk < SG_BK / SG_MMA_K; ++kk) {
 #pragma unroll
@@ -637,14 +632,8 @@ split_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
               const int g = (sa + sb) < SG_GROUPS - 1 ? (sa + sb) : SG_GROUPS - 1;
               const uint32_t acc = first[g] ? 0u : 1u;
               first[g] = false;
-              const uint64_t ad = sw64_kmajor_desc(a0 + sa * SG_TILE_BYTES + kk * SG_MMA_K * 2);
-              const uint32_t bt = b0 + sb * SG_TILE_BYTES + kk * SG_MMA_K * 2;
-              if (!imag) {
-                tc_mma_bf16(tmem + g * 128, ad, sw64_kmajor_desc(bt), kIdescBf16, acc);
-              } else {
-                tc_mma_bf16(tmem + g * 128, ad, sw64_kmajor_desc(bt + SG_TILE_BYTES / 2), kIdescBf16N64NegB, acc);
-                tc_mma_bf16(tmem + g * 128 + SG_BNC, ad, sw64_kmajor_desc(bt), kIdescBf16N64, acc);
-              }
+              tc_mma_bf16(tmem + g * 128, sw64_kmajor_desc(a0 + sa * SG_TILE_BYTES + kk * SG_MMA_K * 2),
+                          sw64_kmajor_desc(b0 + sb * SG_TILE_BYTES + kk * SG_MMA_K * 2), kIdescBf16, acc);
             }
           }
         }
@@ -769,13 +758,13 @@ static int get_encoder() {
 }
 
 // 4-D map over digit tiles: (k, row, slice, batch), box (32, box_rows, box_slices, 1), SWIZZLE_64B.
-// B digits: dims {Kh, rows (= Np / 2), 2 planes, L, batch}; box {32, 64, planes, digits, 1}
+// B digits: dims {Kh, rows (= Np / 2), 3 planes, L, batch}; box {32, 64, planes, digits, 1}
 static int make_bplane_map(CUtensorMap* map, const void* base, int Kh, int rows, int L, int batch, int box_planes,
                            int box_digits) {
   MG_TRY(get_encoder());
-  cuuint64_t dims[5] = {(cuuint64_t)Kh, (cuuint64_t)rows, 2, (cuuint64_t)L, (cuuint64_t)batch};
-  cuuint64_t strides[4] = {(cuuint64_t)Kh * 2, (cuuint64_t)rows * Kh * 2, (cuuint64_t)2 * rows * Kh * 2,
-                           (cuuint64_t)L * 2 * rows * Kh * 2};
+  cuuint64_t dims[5] = {(cuuint64_t)Kh, (cuuint64_t)rows, 3, (cuuint64_t)L, (cuuint64_t)batch};
+  cuuint64_t strides[4] = {(cuuint64_t)Kh * 2, (cuuint64_t)rows * Kh * 2, (cuuint64_t)3 * rows * Kh * 2,
+                           (cuuint64_t)L * 3 * rows * Kh * 2};
   cuuint32_t box[5] = {(cuuint32_t)SG_BK, (cuuint32_t)SG_BNC, (cuuint32_t)box_planes, (cuuint32_t)box_digits, 1};
   cuuint32_t estr[5] = {1, 1, 1, 1, 1};
   CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<void*>(base), dims, strides, box,
