@@ -198,8 +198,9 @@ int mg_evolve_batch(mg_ctx* ctx, int n, mg_plan* const* plans, const int* output
  * (padded operators, coefficients, state, upload staging) fits the budget next
  * to the jobs already resident, otherwise returns MG_EAGAIN; the job's inputs
  * are uploaded on a separate stream and stay resident until it completes.  A
- * worker thread repeatedly takes every admitted job that shares the oldest
- * job's (precision, padded dimension) key and advances each by up to
+ * worker thread repeatedly takes every admitted job that shares the key
+ * (precision, padded dimension) of the job with the least remaining work
+ * (d^3 x intervals left: shortest remaining work first) and advances each by up to
  * `quantum_intervals` intervals in one shared chunk step (batched exponential,
  * multi-job propagation), admitting new arrivals at every chunk boundary, so
  * requests that arrive while others run join them on the device instead of

@@ -2071,9 +2071,20 @@ void server_loop(mg_server* srv) {
         j->started = true;
         srv->active.push_back(j);
       }
-      // the oldest job picks the group; its peers with the same key share the chunk
+      // the job with the least remaining work (d^3 x intervals left) picks the group;
+      // its peers with the same key share the chunk.  Short requests thus pass long
+      // ones (shortest remaining work first); a long request advances whenever no
+      // shorter one is active.
       if (!srv->active.empty()) {
         SJob* head = srv->active.front();
+        double best = 1e300;
+        for (SJob* j : srv->active) {
+          const double w = (double)j->dp * j->dp * j->dp * (double)(j->b.N - j->b.done);
+          if (w < best) {
+            best = w;
+            head = j;
+          }
+        }
         for (SJob* j : srv->active)
           if (j->dp == head->dp && j->prec == head->prec && j->L == head->L && (int)group.size() < srv->seg_cap)
             group.push_back(j);
