@@ -1295,6 +1295,16 @@ int fold_chunk(mg_ctx* ctx, Engine& eng, PropState& ps, int n, const double* U, 
   if (ps.output == MG_OUT_STATE) {
     double* tmp;
     MG_TRY(ws(ctx, WS_VEC, 2 * d + 2, &tmp));
+    if (!eng.df() && !ps.traj && reorth == 0 && d <= 64 && n >= 8) {
+      // small d in FP64: the n dependent matrix-vector steps of the chain are
+      // latency-bound; the chunk's product by the batched tree (log2 n launches
+      // of d^3 products) and one application to psi take less time
+      double* chunk_prod = nullptr;
+      MG_TRY(tree_product(ctx, eng, n, U, &chunk_prod, 0));
+      MG_TRY(launch_state_chain(1, d, chunk_prod, md, ps.psi, tmp + 2, 0, ps.done, ctx->stream));
+      ps.done += n;
+      return MG_OK;
+    }
     const double* Uf = U;
     if (eng.df()) {
       double* conv;
