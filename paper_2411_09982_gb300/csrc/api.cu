@@ -145,6 +145,7 @@ enum Slot {
   WS_TREE0, WS_TREE1, WS_UBUF, WS_NS_Z, WS_OUT,
   WS_ACT_REC,   // action path: interval records, off-chip interval matrices, send masks, job records
   WS_TRAJ,      // trajectory output staged on the device (host output buffers)
+  WS_SEG_A, WS_SEG_B, WS_SEG_I,   // segmented tree: gathered operand pairs, their indices
   WS_COUNT
 };
 
@@ -618,7 +619,7 @@ int tree_product(mg_ctx* ctx, Engine& eng, int n, const double* U, double** out,
 // 9 matrices), plus the BF16 digits of one A and two B operands.
 size_t per_interval_bytes(int d, int prec, int L) {
   size_t md = (size_t)mat_doubles(d) * sizeof(double);
-  size_t b = 9 * md;
+  size_t b = 10 * md;   // (one more for the gathered pairs of a segmented tree)
   if (prec == MG_PREC_SPLIT) b += split_a_bytes(d, L, 1) + 2 * split_b_bytes(d, L, 1);
   return b;
 }
@@ -1623,11 +1624,87 @@ int process_chunk(mg_ctx* ctx, Engine& eng, std::vector<ChunkSeg>& segs, int fil
     j.done += g.n;
   }
   if (!cs.empty()) {
-    const double* Uf = Ub;
+    const double* Ucur = Ub;
+    int nitems = fill;
+    if (reorth_every == 0 && dp <= 256) {
+      // Segmented tree: every state job's chunk product by batched products of
+      // operand pairs gathered from all jobs at once (one gather, one product
+      // launch per level), then one application per job below -- instead of each
+      // job's n dependent, latency-bound matrix-vector steps.
+      std::vector<std::vector<int>> items(cs.size());
+      for (size_t q = 0; q < cs.size(); ++q)
+        for (int i = 0; i < cs[q].count; ++i) items[q].push_back(cs[q].first + i);
+      // the tree's shape follows from the segment lengths alone: plan every level
+      // on the host, upload all indices once, then issue the levels back to back
+      struct Level { int P, C; size_t off; };
+      std::vector<Level> levels;
+      std::vector<int> host_idx;
+      for (;;) {
+        bool more = false;
+        for (auto& it : items) more |= it.size() > 1;
+        if (!more) break;
+        std::vector<int> L, R, Cs;
+        std::vector<std::vector<int>> next(items.size());
+        for (size_t q = 0; q < items.size(); ++q) {
+          const std::vector<int>& it = items[q];
+          size_t i = 0;
+          for (; i + 1 < it.size(); i += 2) {   // later interval on the left
+            next[q].push_back((int)L.size());
+            L.push_back(it[i + 1]);
+            R.push_back(it[i]);
+          }
+          if (i < it.size()) {                    // odd one out: carried to the next level
+            next[q].push_back(-1 - (int)Cs.size());
+            Cs.push_back(it[i]);
+          }
+        }
+        const int P = (int)L.size(), C = (int)Cs.size();
+        for (auto& v : next)
+          for (int& x : v) x = x >= 0 ? x : P + (-1 - x);
+        levels.push_back({P, C, host_idx.size()});
+        host_idx.insert(host_idx.end(), L.begin(), L.end());
+        host_idx.insert(host_idx.end(), R.begin(), R.end());
+        host_idx.insert(host_idx.end(), Cs.begin(), Cs.end());
+        items.swap(next);
+      }
+      if (!levels.empty()) {
+        const size_t cap = (size_t)fill / 2 + cs.size() + 1;
+        double *t0, *t1, *ga, *gb;
+        int* idx_dev;
+        MG_TRY(ws(ctx, WS_TREE0, md * cap, &t0));
+        MG_TRY(ws(ctx, WS_TREE1, md * cap, &t1));
+        MG_TRY(ws(ctx, WS_SEG_A, md * cap, &ga));
+        MG_TRY(ws(ctx, WS_SEG_B, md * cap, &gb));
+        MG_TRY(ws(ctx, WS_SEG_I, host_idx.size(), &idx_dev));
+        MG_CUDA_TRY(cudaMemcpyAsync(idx_dev, host_idx.data(), sizeof(int) * host_idx.size(), cudaMemcpyHostToDevice, s));
+        for (size_t lv = 0; lv < levels.size(); ++lv) {
+          const Level& v = levels[lv];
+          const int* li = idx_dev + v.off;
+          double* out = (lv % 2 == 0) ? t0 : t1;
+          MG_TRY(launch_gather_mats(v.P, md, Ucur, li, ga, s));
+          MG_TRY(launch_gather_mats(v.P, md, Ucur, li + v.P, gb, s));
+          MG_TRY(launch_gather_mats(v.C, md, Ucur, li + 2 * v.P, out + (long long)v.P * md, s));
+          if (v.P > 0) {
+            MG_TRY(eng.reserve(v.P));
+            MG_TRY(eng.prepA(v.P, ga, md));
+            MG_TRY(eng.prepB(0, v.P, gb, md));
+            AddTerms none;
+            MG_TRY(eng.mul(v.P, ga, md, 0, gb, md, out, md, none));
+          }
+          Ucur = out;
+          nitems = v.P + v.C;
+        }
+      }
+      for (size_t q = 0; q < cs.size(); ++q) {
+        cs[q].first = items[q][0];
+        cs[q].count = 1;
+      }
+    }
+    const double* Uf = Ucur;
     if (eng.df()) {
       double* conv;
-      MG_TRY(ws(ctx, WS_NS_Z, md * fill, &conv));
-      MG_TRY(eng.to_fp64(fill, Ub, md, conv, md));
+      MG_TRY(ws(ctx, WS_NS_Z, md * nitems, &conv));
+      MG_TRY(eng.to_fp64(nitems, Ucur, md, conv, md));
       Uf = conv;
     }
     MG_CUDA_TRY(cudaMemcpyAsync(segs_dev, cs.data(), sizeof(ChainSeg) * cs.size(), cudaMemcpyHostToDevice, s));

@@ -104,6 +104,8 @@ int launch_apply_phase(int batch, int d, long long count_per_item, const double*
 int launch_identity(int batch, int d, double* dst, cudaStream_t s);
 
 // copy a strided batch: dst[b] = src[b * src_stride] (strides in doubles)
+// dst[p] = src[idx[p]] for p < n matrices of md doubles (idx on the device)
+int launch_gather_mats(int n, long long md, const double* src, const int* idx_dev, double* dst, cudaStream_t s);
 int launch_copy_strided(int batch, long long elems, const double* src, long long src_stride,
                         double* dst, long long dst_stride, cudaStream_t s);
 

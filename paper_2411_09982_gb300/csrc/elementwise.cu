@@ -116,6 +116,26 @@ int launch_lincomb_multi(int batch, int d, int nout, double* const* dst, int nsr
   return check_launch("lincomb_multi_kernel");
 }
 
+// dst[p] = src[idx[p]] for p < n matrices of md doubles (gathering the operand
+// pairs of a segmented tree product into contiguous batches)
+__global__ void gather_mats_kernel(int n, long long md2, const double2* __restrict__ src, const int* __restrict__ idx,
+                                   double2* __restrict__ dst) {
+  const long long total = md2 * n;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long p = e / md2, r = e - p * md2;
+    dst[e] = src[(long long)idx[p] * md2 + r];
+  }
+}
+
+int launch_gather_mats(int n, long long md, const double* src, const int* idx_dev, double* dst, cudaStream_t s) {
+  if (n <= 0) return MG_OK;
+  const long long md2 = md / 2;
+  gather_mats_kernel<<<grid_for(md2 * n), 256, 0, s>>>(n, md2, reinterpret_cast<const double2*>(src), idx_dev,
+                                                        reinterpret_cast<double2*>(dst));
+  return check_launch("gather_mats_kernel");
+}
+
 // ---------------------------------------------------------------------------
 // grid (chunks, batch): the phase factor is formed once per block, not per element.
 __global__ void apply_phase_kernel(long long per_item, const double* __restrict__ phase,
