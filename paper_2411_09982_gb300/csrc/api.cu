@@ -1296,19 +1296,12 @@ int fold_chunk(mg_ctx* ctx, Engine& eng, PropState& ps, int n, const double* U, 
   if (ps.output == MG_OUT_STATE) {
     double* tmp;
     MG_TRY(ws(ctx, WS_VEC, 2 * d + 2, &tmp));
-    if (!ps.traj && reorth == 0 && n >= 8 && d <= (eng.df() ? 256 : 64)) {
-      // small d: the n dependent matrix-vector steps of the chain are latency-bound;
-      // the chunk's product by the batched tree (log2 n launches of d^3 products;
-      // on the tensor cores up to d = 256, in FP64 up to d = 64) and one
-      // application to psi take less time
+    if (!eng.df() && !ps.traj && reorth == 0 && d <= 64 && n >= 8) {
+      // small d in FP64: the n dependent matrix-vector steps of the chain are
+      // latency-bound; the chunk's product by the batched tree (log2 n launches
+      // of d^3 products) and one application to psi take less time
       double* chunk_prod = nullptr;
       MG_TRY(tree_product(ctx, eng, n, U, &chunk_prod, 0));
-      if (eng.df()) {
-        double* conv;
-        MG_TRY(ws(ctx, WS_NS_Z, md, &conv));
-        MG_TRY(eng.to_fp64(1, chunk_prod, md, conv, md));
-        chunk_prod = conv;
-      }
       MG_TRY(launch_state_chain(1, d, chunk_prod, md, ps.psi, tmp + 2, 0, ps.done, ctx->stream));
       ps.done += n;
       return MG_OK;
