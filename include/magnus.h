@@ -226,10 +226,11 @@ typedef struct mg_job {
   double* out;              /* written when the job completes; keep it valid until mg_wait returns */
   int precision, slices;
   int flags;                /* MG_FLAG_HOST_PTRS: H0, Hk, samples, in and out are host memory;
-                               MG_FLAG_STATE_ACTION: a state job runs on the action-based path
-                               (FP64; precision and slices are ignored), launched with the other
-                               admitted action jobs on one of the server's action streams,
-                               concurrently with the chunk steps of the other jobs */
+                               MG_FLAG_STATE_ACTION: a state job of d >= 256 runs on the
+                               action-based path (FP64; precision and slices are ignored) on one
+                               of the server's action streams, concurrently with the chunk steps
+                               of the other jobs; smaller flagged jobs, which finish sooner in the
+                               shared chunk steps, stay there */
 } mg_job;
 
 typedef struct mg_job_report {

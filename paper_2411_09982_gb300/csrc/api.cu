@@ -1973,6 +1973,7 @@ struct SActionGroup {
   ActionShape shape;
 };
 constexpr int SERVER_ACTION_STREAMS = 4;
+constexpr int SERVER_ACTION_MIN_D = 256;   // smaller flagged state jobs ride the chunk steps
 // Action chains in the server run in slices of about this many seconds of work:
 // streams share the device's few hardware queues, so a copy or kernel queued on
 // another stream waits at most one slice behind a long chain.
@@ -2449,7 +2450,10 @@ int mg_submit(mg_server* srv, const mg_job* job, uint64_t* job_id) {
       (job->output != MG_OUT_STATE && job->output != MG_OUT_PROPAGATOR) ||
       (job->output == MG_OUT_STATE && !job->in) || (job->output == MG_OUT_PROPAGATOR && job->in))
     return MG_EINVAL;
-  if (job->output == MG_OUT_STATE && (job->flags & MG_FLAG_STATE_ACTION)) return submit_action(srv, job, job_id);
+  // flagged state jobs of d >= 256 take the action path; smaller ones finish sooner
+  // in the shared chunk steps (measured on the mixed request stream)
+  if (job->output == MG_OUT_STATE && (job->flags & MG_FLAG_STATE_ACTION) && job->d >= SERVER_ACTION_MIN_D)
+    return submit_action(srv, job, job_id);
   MG_TRY(validate_prec(job->precision, job->slices));
   const int dp = round_dim(d);
   const long long md = mat_doubles(dp);
