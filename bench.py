@@ -304,7 +304,7 @@ def run_ours(args):
 
 
 # ----------------------------------------------------------------------------
-# the other workloads (one GPU; not the driver's default line)
+# the other workloads (one GPU; not the default line)
 # ----------------------------------------------------------------------------
 def run_config(args):
     import numpy as np

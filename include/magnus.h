@@ -54,7 +54,7 @@ extern "C" {
 #define MG_ENOTHERM     -5   /* operator not Hermitian (MG_FLAG_CHECK_HERMITIAN)   */
 #define MG_ETIMEOUT     -6   /* a bounded device-side wait gave up                 */
 #define MG_EAGAIN       -7   /* not admissible now (serving: memory budget)        */
-#define MG_EUNSUPPORTED -8   /* size or mode outside what this build supports     */
+#define MG_EUNSUPPORTED -8   /* size or mode outside what the library supports     */
 
 /* ---- precision modes ------------------------------------------------------ */
 /* MG_PREC_FP64: every matrix product in native FP64 arithmetic.
