@@ -207,12 +207,7 @@ slice_a_kernel(int d, int Kp, int Mp, int beta, const double* __restrict__ A, lo
   const int Kh = Kp / 2;
   const long long slice_stride = (long long)Mp * Kp;
   __nv_bfloat16* o = out + (long long)b * L * slice_stride + (long long)row * Kp;
-  if (row >= d) {
-    for (int k = 4 * lane; k < Kp; k += 128)
-#pragma unroll
-      for (int s = 0; s < L; ++s) *reinterpret_cast<uint2*>(o + s * slice_stride + k) = make_uint2(0u, 0u);
-    return;
-  }
+  if (row >= d) return;   // rows d..Mp are never read: the tensor map ends at row d (TMA fills zeros)
   const double* a = A + b * sA;
   const long long r0 = (long long)row * d;
   int E = -(1 << 29);
@@ -285,7 +280,6 @@ col_exponent_kernel(int d, int Np, const double* __restrict__ B, long long sB, i
 constexpr int SB_KCHUNK = 32;
 // Digits of one 32 (k) x 64 (j) block: grid (ceil(d/64), ceil(d/32), batch), block 256.
 // Each thread writes 4 consecutive k of one column per plane as 8-byte stores.
-// The blocks with blockIdx.y == 0 also zero the rows beyond d.
 template <int L, typename T>
 __global__ void __launch_bounds__(256)
 slice_b_kernel(int d, int Kp, int Np, int beta, const double* __restrict__ B, long long sB,
@@ -341,20 +335,7 @@ slice_b_kernel(int d, int Kp, int Np, int beta, const double* __restrict__ B, lo
       *reinterpret_cast<uint2*>(row + so + 2 * plane_stride + k) = wi[s];
     }
   }
-  if (blockIdx.y != 0) return;
-  const int live = min(SG_BNC, d - j0);
-  if (live < SG_BNC) {
-    const int words = Kh / 4;
-    for (int e = tid; e < (SG_BNC - live) * words; e += 256) {
-      const int rr = live + e / words, k = 4 * (e % words);
-#pragma unroll
-      for (int s = 0; s < L; ++s)
-#pragma unroll
-        for (int pl = 0; pl < 3; ++pl)
-          *reinterpret_cast<uint2*>(ob + s * slice_stride + pl * plane_stride + (long long)(j0 + rr) * Kh + k) =
-              make_uint2(0u, 0u);
-    }
-  }
+  // rows d..Np/2 of every plane are never read: the tensor map ends at row d (TMA fills zeros)
 }
 
 // ---------------------------------------------------------------------------
@@ -758,11 +739,12 @@ static int get_encoder() {
 }
 
 // 4-D map over digit tiles: (k, row, slice, batch), box (32, box_rows, box_slices, 1), SWIZZLE_64B.
-// B digits: dims {Kh, rows (= Np / 2), 3 planes, L, batch}; box {32, 64, planes, digits, 1}
-static int make_bplane_map(CUtensorMap* map, const void* base, int Kh, int rows, int L, int batch, int box_planes,
-                           int box_digits) {
+// B digits: dims {Kh, d valid rows (of Np / 2 allocated), 3 planes, L, batch};
+// box {32, 64, planes, digits, 1}; rows from d on read as zeros
+static int make_bplane_map(CUtensorMap* map, const void* base, int Kh, int rows, int valid_rows, int L, int batch,
+                           int box_planes, int box_digits) {
   MG_TRY(get_encoder());
-  cuuint64_t dims[5] = {(cuuint64_t)Kh, (cuuint64_t)rows, 3, (cuuint64_t)L, (cuuint64_t)batch};
+  cuuint64_t dims[5] = {(cuuint64_t)Kh, (cuuint64_t)valid_rows, 3, (cuuint64_t)L, (cuuint64_t)batch};
   cuuint64_t strides[4] = {(cuuint64_t)Kh * 2, (cuuint64_t)rows * Kh * 2, (cuuint64_t)3 * rows * Kh * 2,
                            (cuuint64_t)L * 3 * rows * Kh * 2};
   cuuint32_t box[5] = {(cuuint32_t)SG_BK, (cuuint32_t)SG_BNC, (cuuint32_t)box_planes, (cuuint32_t)box_digits, 1};
@@ -776,10 +758,11 @@ static int make_bplane_map(CUtensorMap* map, const void* base, int Kh, int rows,
   }
   return MG_OK;
 }
-static int make_digit_map(CUtensorMap* map, const void* base, int Kp, int rows, int L, int batch,
+// A digits: dims {Kp, d valid rows (of `rows` allocated), L, batch}; rows from d on read as zeros
+static int make_digit_map(CUtensorMap* map, const void* base, int Kp, int rows, int valid_rows, int L, int batch,
                           int box_rows = SG_BM, int box_slices = -1) {
   MG_TRY(get_encoder());
-  cuuint64_t dims[4] = {(cuuint64_t)Kp, (cuuint64_t)rows, (cuuint64_t)L, (cuuint64_t)batch};
+  cuuint64_t dims[4] = {(cuuint64_t)Kp, (cuuint64_t)valid_rows, (cuuint64_t)L, (cuuint64_t)batch};
   cuuint64_t strides[3] = {(cuuint64_t)Kp * 2, (cuuint64_t)rows * Kp * 2, (cuuint64_t)L * rows * Kp * 2};
   cuuint32_t box[4] = {(cuuint32_t)SG_BK, (cuuint32_t)box_rows, (cuuint32_t)(box_slices < 0 ? L : box_slices), 1};
   cuuint32_t estr[4] = {1, 1, 1, 1};
@@ -807,9 +790,9 @@ static int launch_split_gemm_L(const SplitGeom& g, int batch, const __nv_bfloat1
                                const SplitEpi& epi, int* status, cudaStream_t s) {
   constexpr int STAGES = stages_for<L>();
   CUtensorMap ma, mb, mbh;
-  MG_TRY(make_digit_map(&ma, Ad, g.Kp, g.Mp, L, batch));
-  MG_TRY(make_bplane_map(&mb, Bd, g.Kh(), g.Np / 2, L, batch, 2, L));
-  MG_TRY(make_bplane_map(&mbh, Bd, g.Kh(), g.Np / 2, L, batch, 1, 1));
+  MG_TRY(make_digit_map(&ma, Ad, g.Kp, g.Mp, g.d, L, batch));
+  MG_TRY(make_bplane_map(&mb, Bd, g.Kh(), g.Np / 2, g.d, L, batch, 2, L));
+  MG_TRY(make_bplane_map(&mbh, Bd, g.Kh(), g.Np / 2, g.d, L, batch, 1, 1));
   const size_t ring = std::max<size_t>((size_t)STAGES * 2 * L * SG_TILE_BYTES, (size_t)SG_EPI_BYTES);
   const size_t smem = ring + 1024 /*barriers, exponents*/ + 1024 /*align*/;
   const int mtiles = g.Mp / SG_BM;
