@@ -97,12 +97,18 @@ def refine(x, steps=12):
     return x
 
 
-def main():
+def derive():
+    """The refined member of the family, rounded to double, and its worst relative
+    condition error after rounding."""
     x = refine(START)
     worst = max(abs(v) for v in residual(x))
     assert worst < mp.mpf(10) ** -40, worst
     rounded = [float(v) for v in x]
-    worst_rounded = max(abs(v) for v in residual(rounded))
+    return rounded, max(abs(v) for v in residual(rounded))
+
+
+def main():
+    rounded, worst_rounded = derive()
     names = ["B1"] * 4 + ["B5"] * 5 + ["B4"] * 5 + ["B3"] * 5 + ["B2"] * 5
     path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "csrc", "taylor18.h")
     with open(path, "w") as f:

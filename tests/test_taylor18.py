@@ -48,3 +48,16 @@ def test_scheme_reproduces_taylor_coefficients():
     for k in range(19):
         rel = abs(T[k] * math.factorial(k) - 1)
         assert rel < Fraction(1, 10**15), (k, float(rel))
+
+
+def test_header_is_what_the_derivation_script_writes():
+    pytest = __import__("pytest")
+    pytest.importorskip("mpmath")
+    import importlib.util
+    path = os.path.join(os.path.dirname(__file__), "..", "paper_2411_09982_gb300", "taylor18_coefficients.py")
+    spec = importlib.util.spec_from_file_location("taylor18_coefficients", path)
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    rounded, worst = mod.derive()
+    assert [Fraction(v) for v in rounded] == coefficients()
+    assert worst < 1e-15
