@@ -183,13 +183,18 @@ int mg_evolve(mg_plan* plan, int output, const double* in, double* out, int reor
  * dimension and length together: jobs are grouped by precision mode and by
  * dimension rounded up to a multiple of 16 (zero padding is exact: the padded
  * block of exp(-i Hbar) is the identity), and within a group all intervals of
- * all jobs share one batched launch per step of the exponential; states of all
- * jobs of a chunk advance in one multi-job launch.  outputs[i], in[i], out[i]
- * are as for mg_evolve (in[i] may be NULL for propagators; in may be NULL when
- * no job needs an input).  State jobs need d <= 256.  job_status (HOST, may be
- * NULL) receives MG_OK or MG_ENONFINITE per job: a job whose Magnus exponent
- * has a NaN/Inf norm fails alone, the others complete.  flags:
- * MG_FLAG_HOST_PTRS when every in[i]/out[i] is host memory. */
+ * all jobs share one batched launch per step of the exponential.  Propagator
+ * jobs fold each chunk by a tree product; state jobs of d <= 256 (without
+ * renormalisation) reduce each chunk by a segmented tree shared by all jobs and
+ * then advance in one multi-job launch, larger ones by matrix-vector steps.
+ * State jobs whose plan has MG_FLAG_STATE_ACTION run together in one
+ * action-path launch instead.  outputs[i], in[i], out[i] are as for mg_evolve
+ * (MG_OUT_STATE or MG_OUT_PROPAGATOR; in[i] may be NULL for propagators; in may
+ * be NULL when no job needs an input).  job_status (HOST, may be NULL) receives
+ * MG_OK or the job's own error: a job whose Magnus exponent has a NaN/Inf norm
+ * fails alone with MG_ENONFINITE (an action-path job also with MG_EUNSUPPORTED
+ * when its spectral bound exceeds the sub-step limit), the others complete.
+ * flags: MG_FLAG_HOST_PTRS when every in[i]/out[i] is host memory. */
 int mg_evolve_batch(mg_ctx* ctx, int n, mg_plan* const* plans, const int* outputs, const double* const* in,
                     double* const* out, int reorth_every, int flags, int* job_status);
 
