@@ -62,7 +62,9 @@ def parse():
                          "from 200/s to this rate; the requests themselves are unchanged)")
     ap.add_argument("--action", action="store_true",
                     help="configs 0, 2, 3: state outputs by the action of exp(-i Hbar_n) on psi (sparse "
-                         "operators, FP64); config 3 then evolves the state |0> instead of the full propagator")
+                         "operators, FP64); config 3 then evolves the state |0> instead of the full propagator; "
+                         "config 4: state requests are flagged for the action path (the server takes it "
+                         "from d = 256)")
     return ap.parse_args()
 
 
