@@ -538,3 +538,45 @@ def test_trajectory_single_interval(ctx):
     got = out.cpu().numpy()
     assert got.shape == (2, wl.d)
     assert np.array_equal(got[0], wl.psi0) and np.abs(got[1] - ref).max() <= 1e-13
+
+
+@pytest.mark.parametrize("prec,L,tol", [(M.MG_PREC_FP64, 6, 1e-13), (M.MG_PREC_SPLIT, 6, 1e-8)])
+def test_expm_nilpotent_is_finite_taylor_sum(ctx, prec, L, tol):
+    """A strictly upper-triangular exponent: exp(-i A) is the finite sum of (-i A)^j / j!, j < d.
+    The evaluation uses no Hermitian structure beyond the real trace shift, and the trace is 0."""
+    rng = np.random.default_rng(41)
+    d = 12
+    A = np.triu(rng.uniform(-1.0, 1.0, (2, d, d)), 1).astype(np.complex128)
+    U = torch.empty_like(cuda(A))
+    M.mg_expm(ctx, 2, d, cuda(A), U, prec, L)
+    torch.cuda.synchronize()
+    for b in range(2):
+        X = -1j * A[b]
+        ref, term = np.eye(d, dtype=complex), np.eye(d, dtype=complex)
+        for j in range(1, d):
+            term = term @ X / j
+            ref = ref + term
+        assert np.abs(U[b].cpu().numpy() - ref).max() <= tol * np.abs(ref).max(), b
+
+
+@pytest.mark.parametrize("d", [64, 129])
+def test_cgemm_split_adversarial_row_and_column_scales(ctx, d):
+    """Rows of A and columns of B scaled by powers of two from 2^-12 to 2^12: the per-row and
+    per-column exponents keep every element within the unscaled digit bound times its scale."""
+    rng = np.random.default_rng(5 * d)
+    L = 6
+    A0, B0 = rand_c(rng, (1, d, d)), rand_c(rng, (1, d, d))
+    r = 2.0 ** rng.integers(-12, 13, d)
+    c = 2.0 ** rng.integers(-12, 13, d)
+    A, B = A0 * r[None, :, None], B0 * c[None, None, :]
+    C = torch.empty((1, d, d), dtype=torch.complex128, device="cuda")
+    M.mg_cgemm(ctx, 1, d, cuda(A), cuda(B), C, M.MG_PREC_SPLIT, L)
+    torch.cuda.synchronize()
+    ref = A[0] @ B[0]
+    beta = split_beta(d)
+    ma = np.abs(np.stack([A0.real, A0.imag])).max()
+    mb = np.abs(np.stack([B0.real, B0.imag])).max()
+    bound = (L + 2) * 2 * d * (2 * ma) * (2 * mb) * (2.0 ** (-beta * L) + L * 2.0 ** (-22 - 3 * beta)) \
+        + 1e-13 * d * ma * mb
+    scaled_err = np.abs(C[0].cpu().numpy() - ref) / (r[:, None] * c[None, :])
+    assert scaled_err.max() <= bound, (scaled_err.max(), bound)

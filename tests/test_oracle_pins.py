@@ -344,3 +344,21 @@ def test_second_order_magnus_converges_at_fourth_order():
         errs.append(np.linalg.norm(oracle.propagate_state(U, wl.psi0) - ref))
     slopes = np.diff(np.log(errs)) / np.diff(np.log(Ns))
     assert np.all(slopes < -3.6) and np.all(slopes > -4.5), (errs, slopes)
+
+
+def test_workload_generators_give_hermitian_operators():
+    """Every synthetic model generator returns exactly Hermitian H0 and H_k (the
+    inputs the method assumes), drives of the declared width, and a normalised psi0."""
+    rng = np.random.default_rng(3)
+    models = [W.config(0, N=10), W.config(1, N=10),
+              W.transmon_chain(n_sites=3, levels=4, seed=3, N=5, all_to_all=True, two_tone=True),
+              W.transmon_resonator(nt=4, nr=6, N=5, unitary=True), W.spin_chain(n=4, N=5),
+              W.driven_qubit_rot(N=5), W.random_instance(rng, N_range=(5, 9), d_range=(16, 40))]
+    for wl in models:
+        assert np.array_equal(wl.H0, wl.H0.conj().T), wl.name
+        for h in wl.Hk:
+            assert np.array_equal(h, h.conj().T), wl.name
+        t = oracle.node_times(wl.t0, wl.dt, wl.N, oracle.gauss_legendre(wl.P)[0])
+        assert wl.drive(t).shape == (wl.N, wl.P, wl.K), wl.name
+        if wl.psi0 is not None:
+            assert abs(np.linalg.norm(wl.psi0) - 1.0) < 1e-15, wl.name
