@@ -209,6 +209,44 @@ def test_propagate_tree_matches_sequential_product(ctx, N, d, prec):
     np.testing.assert_allclose(psi.cpu().numpy(), oracle.propagate_state(Us, psi0), atol=1e-12, rtol=0)
 
 
+@pytest.mark.parametrize("d,prec", [(24, M.MG_PREC_FP64), (24, M.MG_PREC_SPLIT), (300, M.MG_PREC_FP64)])
+def test_reorth_removes_scale_drift(ctx, d, prec):
+    """Propagators scaled by (1 + 1e-6) make the product drift by (1 + 1e-6)^N.  The polar
+    factor of c V (c > 0, V unitary) is V, so re-orthonormalising every R intervals (N a
+    multiple of R) takes the product back to that of the unitaries, and renormalising psi
+    takes the state back to the unit-norm result."""
+    rng = np.random.default_rng(d + 100 * prec)
+    N, R, eps = 32, 8, 1e-6
+    Us = np.stack([oracle.expm_minus_i(rand_herm(rng, d, 0.7)) for _ in range(N)])
+    psi0 = W.basis_state(d, 1)
+    ref_U, ref_psi = oracle.propagate_unitary(Us), oracle.propagate_state(Us, psi0)
+    Ud = cuda((1.0 + eps) * Us)
+    tol_U = 1e-11 if prec == M.MG_PREC_FP64 else 1e-9
+    for reorth in (0, R):
+        U = torch.empty((d, d), dtype=torch.complex128, device="cuda")
+        M.mg_propagate(ctx, N, d, Ud, M.MG_OUT_PROPAGATOR, None, U, reorth, prec, 6)
+        psi = torch.empty(d, dtype=torch.complex128, device="cuda")
+        M.mg_propagate(ctx, N, d, Ud, M.MG_OUT_STATE, cuda(psi0), psi, reorth, prec, 6)
+        torch.cuda.synchronize()
+        err_U = np.abs(U.cpu().numpy() - ref_U).max()
+        err_psi = np.abs(psi.cpu().numpy() - ref_psi).max()
+        if reorth:
+            assert err_U <= tol_U and err_psi <= 1e-12, (err_U, err_psi)
+        else:   # the drift the step removes is there: 3.2e-5 relative
+            assert err_U > 1e-5 * np.abs(ref_U).max() and err_psi > 1e-5 * np.abs(ref_psi).max(), (err_U, err_psi)
+
+
+@pytest.mark.parametrize("prec,L,tol", [(M.MG_PREC_FP64, 6, 1e-11), (M.MG_PREC_SPLIT, 6, 1e-6)])
+def test_evolve_with_reorth_matches_oracle(ctx, prec, L, tol):
+    """Whole evolutions with re-orthonormalisation every 7 intervals (no chunk or tree level
+    aligns with 7) give the oracle's result, for a state and for a full propagator."""
+    for wl in (W.config(0, N=100), W.transmon_resonator(nt=3, nr=10, N=60, unitary=True)):
+        out, rep = M.evolve_workload(ctx, wl, prec, L, reorth_every=7)
+        ref = oracle.evolve_workload(wl)
+        err = np.abs(out.cpu().numpy() - ref).max()
+        assert err <= tol, (wl.name, err)
+
+
 # ----------------------------------------------------------------------------
 # whole evolutions
 # ----------------------------------------------------------------------------
@@ -290,8 +328,10 @@ def _small_jobs(seed=21, n=10):
     return jobs
 
 
-@pytest.mark.parametrize("prec,L,tol", [(0, 6, 1e-11), (1, 6, 1e-6)])
-def test_evolve_batch_matches_oracle_per_job(ctx, prec, L, tol):
+@pytest.mark.parametrize("prec,L,tol,reorth", [(0, 6, 1e-11, 0), (1, 6, 1e-6, 0), (0, 6, 1e-11, 5), (1, 6, 1e-6, 5)])
+def test_evolve_batch_matches_oracle_per_job(ctx, prec, L, tol, reorth):
+    """Every job of an uneven batch against the oracle, also with re-orthonormalisation
+    every 5 intervals (which moves a result by its unitarity defect only)."""
     jobs = _small_jobs()
     plans, outs, ins, kinds = [], [], [], []
     for wl in jobs:
@@ -308,7 +348,7 @@ def test_evolve_batch_matches_oracle_per_job(ctx, prec, L, tol):
             ins.append(cuda(wl.psi0))
             outs.append(torch.empty(wl.d, dtype=torch.complex128, device="cuda"))
     try:
-        status = M.mg_evolve_batch(ctx, plans, kinds, ins, outs)
+        status = M.mg_evolve_batch(ctx, plans, kinds, ins, outs, reorth)
         torch.cuda.synchronize()
         assert status == [0] * len(jobs)
         for wl, o in zip(jobs, outs):
