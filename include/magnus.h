@@ -132,6 +132,20 @@ int mg_ctx_set_workspace_limit(mg_ctx* ctx, size_t bytes);
  * 1 <= P <= 64. */
 int mg_quadrature_nodes(int P, double* x, double* w);
 
+/* ---- exponential parameters (host only) ---------------------------------- */
+/* The Taylor degree m and squaring count s that mg_expm and mg_evolve take for a
+ * batch whose largest FP64 1-norm of Hbar_n - tau_n I is norm1 (Sec. "Magnus
+ * Expansion": U_n = exp(-i Hbar_n) by scaling and squaring), and theta, the
+ * largest 1-norm that degree m takes unscaled: the largest theta with
+ * sum_{j>m} theta^j / j! <= u theta, u = 2^-53 in FP64 and max(2^-53,
+ * 2^(-beta slices)) in split precision (beta = the digit width the split
+ * product uses at dimension d).  m is one of 2, 4, 6, 9, 12, 16 (Paterson-
+ * Stockmeyer) or 18 (five products, split precision only); (m, s) minimises
+ * products + s, ties to the smaller s.  No context or device is used.
+ * Errors: MG_EINVAL for a negative or non-finite norm1, d outside 1..4096,
+ * NULL outputs, or precision/slices as for plans. */
+int mg_taylor_choice(double norm1, int precision, int slices, int d, int* m, int* s, double* theta);
+
 /* ---- plan: resident operators -------------------------------------------- */
 /* Copy H0 (d x d) and H_k (K x d x d, consecutive) into device memory owned by
  * the plan.  `precision` is MG_PREC_FP64 or MG_PREC_SPLIT; `slices` (2..8) is

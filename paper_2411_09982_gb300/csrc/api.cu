@@ -1076,6 +1076,16 @@ int mg_quadrature_nodes(int P, double* x, double* w) {
   return MG_OK;
 }
 
+int mg_taylor_choice(double norm1, int precision, int slices, int d, int* m, int* s, double* theta) {
+  if (!m || !s || !theta || !(norm1 >= 0.0) || !std::isfinite(norm1) || d < 1 || d > 4096) return MG_EINVAL;
+  MG_TRY(validate_prec(precision, slices));
+  const TaylorChoice tc = choose_taylor(norm1, unit_roundoff(precision, slices, d), precision == MG_PREC_SPLIT);
+  *m = tc.m;
+  *s = tc.s;
+  *theta = tc.theta;
+  return MG_OK;
+}
+
 int mg_plan_create(mg_ctx* ctx, mg_plan** out, int d, int K, const double* H0, const double* Hk, int precision,
                    int slices, int flags) {
   if (!ctx || !out || !H0 || d < 1 || d > 4096 || K < 0 || K > 64 || (K > 0 && !Hk)) return MG_EINVAL;

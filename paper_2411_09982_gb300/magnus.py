@@ -87,6 +87,7 @@ SIGNATURES = {
     "mg_ctx_destroy": (_I, [_P]),
     "mg_ctx_set_workspace_limit": (_I, [_P, ctypes.c_size_t]),
     "mg_quadrature_nodes": (_I, [_I, _P, _P]),
+    "mg_taylor_choice": (_I, [_D, _I, _I, _I, _P, _P, _P]),
     "mg_plan_create": (_I, [_P, ctypes.POINTER(_P), _I, _I, _P, _P, _I, _I, _I]),
     "mg_plan_destroy": (_I, [_P]),
     "mg_plan_set_magnus_order": (_I, [_P, _I]),
@@ -328,6 +329,14 @@ def mg_quadrature_nodes(P: int):
     _check(lib.mg_quadrature_nodes(P, x.ctypes.data_as(ctypes.c_void_p), w.ctypes.data_as(ctypes.c_void_p)),
            "mg_quadrature_nodes")
     return x, w
+
+
+def mg_taylor_choice(norm1: float, precision=MG_PREC_FP64, slices=6, d=1):
+    """(m, s, theta) the exponential takes for a batch of largest 1-norm norm1 (host only)."""
+    m, s, th = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+    _check(load().mg_taylor_choice(norm1, precision, slices, d, ctypes.byref(m), ctypes.byref(s), ctypes.byref(th)),
+           "mg_taylor_choice")
+    return m.value, s.value, th.value
 
 
 def mg_coefficients(ctx, N, P, K, dt, w_dev, samples, c):

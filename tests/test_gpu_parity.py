@@ -56,8 +56,9 @@ def split_beta(d):
 def test_quadrature_nodes_match_leggauss(P):
     x, w = M.mg_quadrature_nodes(P)
     xr, wr = oracle.gauss_legendre(P)
-    np.testing.assert_allclose(x, xr, atol=2e-15, rtol=0)
-    np.testing.assert_allclose(w, wr, atol=2e-15, rtol=0)
+    # numpy's own weights err by up to 2.3e-15 at P = 64 (numpy 2.5)
+    np.testing.assert_allclose(x, xr, atol=4e-15, rtol=0)
+    np.testing.assert_allclose(w, wr, atol=4e-15, rtol=0)
 
 
 def test_coefficients_match_oracle(ctx):

@@ -1,0 +1,128 @@
+"""Host-side arithmetic of the library that needs no device: the Gauss-Legendre
+rule behind the drive samples, and the choice of Taylor degree and squaring
+count for U_n = exp(-i Hbar_n).  CPU only; the library is built and loaded, but
+no context is created."""
+import math
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+from paper_2411_09982_gb300 import magnus as M
+
+DEGREES = {2: 1, 4: 2, 6: 3, 9: 4, 12: 5, 16: 6, 18: 5}   # degree -> matrix products
+
+
+def split_beta(d):
+    """Digit width of the split product: largest beta <= 8 with 2^(2 beta - 1) 2d <= 2^24."""
+    return max(b for b in range(2, 9) if 2.0 ** (2 * b - 1) * 2 * d <= 2.0 ** 24)
+
+
+def unit_roundoff(prec, L, d):
+    return 2.0 ** -53 if prec == M.MG_PREC_FP64 else max(2.0 ** -53, 2.0 ** (-split_beta(d) * L))
+
+
+def tail_over_theta_exact(m, theta):
+    """sum_{j>m} theta^j / j! divided by theta, in rational arithmetic (80 terms: the
+    rest is below 1e-60 of the sum for theta <= 40)."""
+    t = Fraction(theta)
+    term = Fraction(1)
+    for j in range(1, m + 1):
+        term = term * t / j
+    s = Fraction(0)
+    for j in range(m + 1, m + 81):
+        term = term * t / j
+        s += term
+    return s / t
+
+
+def theta_by_bisection(m, u):
+    """Largest theta with tail/theta <= u, by bisection on a log-space float evaluation."""
+    def ratio(th):
+        return math.fsum(math.exp(j * math.log(th) - math.lgamma(j + 1)) for j in range(m + 1, m + 81)) / th
+    lo, hi = 1e-6, 40.0
+    for _ in range(100):
+        mid = 0.5 * (lo + hi)
+        lo, hi = (mid, hi) if ratio(mid) <= u else (lo, mid)
+    return lo
+
+
+@pytest.mark.parametrize("P", [1, 2, 3, 5, 8, 16, 33, 64])
+def test_quadrature_rule_is_gauss_legendre_on_host(P):
+    """The rule integrates x^k exactly on [-1, 1] for k <= 2P - 1 (the defining property,
+    up to rounding of the sum), and agrees with numpy's leggauss within the error of the
+    latter (2.3e-15 in the weights at P = 64, against 40-digit Newton nodes)."""
+    x, w = M.mg_quadrature_nodes(P)
+    assert np.all(np.diff(x) > 0) and np.all(w > 0)
+    for k in range(2 * P):
+        exact = 2.0 / (k + 1) if k % 2 == 0 else 0.0
+        assert abs(math.fsum(w * x ** k) - exact) <= 4e-15, (k, math.fsum(w * x ** k), exact)
+    xr, wr = np.polynomial.legendre.leggauss(P)
+    np.testing.assert_allclose(x, xr, atol=4e-15, rtol=0)
+    np.testing.assert_allclose(w, wr, atol=4e-15, rtol=0)
+
+
+@pytest.mark.parametrize("prec,L,d", [(M.MG_PREC_FP64, 6, 30), (M.MG_PREC_SPLIT, 6, 729), (M.MG_PREC_SPLIT, 4, 64),
+                                      (M.MG_PREC_SPLIT, 8, 4096), (M.MG_PREC_SPLIT, 2, 30)])
+def test_taylor_theta_is_the_largest_within_the_remainder_bound(prec, L, d):
+    """theta_m: the truncated series errs by at most u relative at 1-norm theta (exact
+    rational check), and by more than u just above it."""
+    u = unit_roundoff(prec, L, d)
+    seen = set()
+    for norm in [1e-3, 0.3, 1.0, 2.5, 6.0, 40.0, 1e3]:
+        m, s, th = M.mg_taylor_choice(norm, prec, L, d)
+        if m in seen:
+            continue
+        seen.add(m)
+        assert tail_over_theta_exact(m, th) <= Fraction(u) * (1 + Fraction(1, 10 ** 12)), (m, th)
+        above = th * (1 + 1e-9)
+        assert tail_over_theta_exact(m, above) > Fraction(u), (m, th)
+        assert th == pytest.approx(theta_by_bisection(m, u), rel=1e-10)
+
+
+@pytest.mark.parametrize("prec,L,d", [(M.MG_PREC_FP64, 6, 30), (M.MG_PREC_SPLIT, 6, 729), (M.MG_PREC_SPLIT, 4, 100)])
+def test_taylor_choice_minimises_products(prec, L, d):
+    """(m, s) minimises products(m) + s over the offered degrees (18 on the split path
+    only), ties to fewer squarings, and s is the least with norm1 / 2^s <= theta_m."""
+    u = unit_roundoff(prec, L, d)
+    offered = {m: c for m, c in DEGREES.items() if m != 18 or prec == M.MG_PREC_SPLIT}
+    thetas = {m: theta_by_bisection(m, u) for m in offered}
+    rng = np.random.default_rng(11)
+    norms = [0.0, 1e-12, 1e-4] + list(10.0 ** rng.uniform(-3, 5, 300))
+    for norm in norms:
+        # skip norms within 1e-8 of a switching point, where float rounding of theta decides
+        if any(abs(norm / (t * 2.0 ** k) - 1) < 1e-8 for t in thetas.values() for k in range(0, 40)):
+            continue
+        m, s, th = M.mg_taylor_choice(norm, prec, L, d)
+        assert m in offered, m
+        assert norm * 2.0 ** -s <= th and (s == 0 or norm * 2.0 ** -(s - 1) > th), (norm, m, s, th)
+
+        def least_s(t):
+            k = 0
+            while norm * 2.0 ** -k > t:
+                k += 1
+            return k
+        costs = {mm: offered[mm] + least_s(t) for mm, t in thetas.items()}
+        best = min(costs.values())
+        assert costs[m] == best, (norm, m, s, costs)
+        assert s == min(least_s(thetas[mm]) for mm in offered if costs[mm] == best), (norm, m, s, costs)
+
+
+def test_taylor_choice_small_norms_take_low_degrees_and_no_squaring():
+    assert M.mg_taylor_choice(0.0, M.MG_PREC_FP64, 6, 30)[:2] == (2, 0)
+    m, s, _ = M.mg_taylor_choice(1e-9, M.MG_PREC_FP64, 6, 30)
+    assert s == 0 and m <= 4
+    # a coarser unit roundoff never needs a higher degree or more squarings at the same norm
+    for norm in [0.5, 3.0, 50.0]:
+        m64, s64, _ = M.mg_taylor_choice(norm, M.MG_PREC_FP64, 6, 30)
+        for L in (2, 4, 6):
+            m_l, s_l, _ = M.mg_taylor_choice(norm, M.MG_PREC_SPLIT, L, 729)
+            assert DEGREES[m_l] + s_l <= DEGREES[m64] + s64
+
+
+@pytest.mark.parametrize("args", [(-1.0, 0, 6, 30), (float("nan"), 0, 6, 30), (float("inf"), 0, 6, 30),
+                                  (1.0, 1, 1, 30), (1.0, 1, 9, 30), (1.0, 2, 6, 30), (1.0, 0, 6, 0),
+                                  (1.0, 0, 6, 4097)])
+def test_taylor_choice_rejects_invalid_arguments(args):
+    with pytest.raises(M.MagnusError):
+        M.mg_taylor_choice(*args)
