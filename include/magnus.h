@@ -264,7 +264,8 @@ int mg_submit(mg_server* srv, const mg_job* job, uint64_t* job_id);
 /* Block until the job completes (timeout_s < 0: no limit).  Returns the job's
  * status, or MG_ETIMEOUT if it has not completed in time (the job keeps
  * running and can be waited for again).  A completed job is forgotten once
- * waited for. */
+ * waited for: an unknown id, or a job whose result another (concurrent) mg_wait
+ * took, gives MG_EINVAL. */
 int mg_wait(mg_server* srv, uint64_t job_id, double timeout_s, mg_job_report* rep);
 /* Latency percentiles of completed jobs and intervals completed per second of
  * wall time since the first submission. */
@@ -273,21 +274,23 @@ int mg_server_destroy(mg_server* srv);
 
 /* ---- steps of the path (device pointers) --------------------------------- */
 /* c[n][k] = (dt/2) sum_p w[p] samples[n][p][k]   (Eq. magnus-first-order-coeff).
- * samples N x P x K, w P doubles (device), c N x K. */
+ * samples N x P x K, w P doubles (device), c N x K.  1 <= P <= 64. */
 int mg_coefficients(mg_ctx* ctx, int N, int P, int K, double dt, const double* w,
                     const double* samples, double* c);
 
 /* Hbar[n] = dt H0 + sum_k c[n][k] H_k   (Eq. magnus-first-order-term), N x d x d
  * complex output; also tau[n] = Re tr(Hbar_n)/d and norm1[n] =
  * ||Hbar_n - tau_n I||_1 (largest absolute column sum), both N doubles (device,
- * may be NULL). */
+ * may be NULL).  1 <= d <= 4096, 0 <= K <= 64. */
 int mg_build_omega(mg_ctx* ctx, int N, int d, int K, double dt, const double* H0,
                    const double* Hk, const double* c, double* Hbar, double* tau, double* norm1);
 
 /* U[b] = exp(-i A[b]) for a batch of Hermitian d x d matrices A (trace shift,
  * scaling and squaring of a Taylor polynomial).  precision/slices as for plans.
- * The squaring count of every matrix is chosen from its own FP64 1-norm;
- * squarings (device int[batch], may be NULL) receives it. */
+ * The batch runs in chunks that fit the workspace; every chunk takes one degree
+ * and squaring count, mg_taylor_choice of its largest FP64 1-norm of
+ * A[b] - tau_b I (tau_b = Re tr(A[b])/d).  squarings (device int[batch], may be
+ * NULL) receives the count applied to each matrix. */
 int mg_expm(mg_ctx* ctx, int batch, int d, const double* A, double* U, int precision,
             int slices, int* squarings);
 

@@ -1208,14 +1208,15 @@ int mg_set_controls(mg_plan* p, int N, int P, double t0, double dt, const double
 
 int mg_coefficients(mg_ctx* ctx, int N, int P, int K, double dt, const double* w, const double* samples,
                     double* c) {
-  if (!ctx || N < 1 || P < 1 || K < 0 || !w || (K > 0 && (!samples || !c))) return MG_EINVAL;
+  if (!ctx || N < 1 || P < 1 || P > 64 || K < 0 || !w || (K > 0 && (!samples || !c))) return MG_EINVAL;
   MG_CUDA_TRY(cudaSetDevice(ctx->device));
   return launch_coefficients(N, P, K, dt, w, samples, c, ctx->stream);
 }
 
 int mg_build_omega(mg_ctx* ctx, int N, int d, int K, double dt, const double* H0, const double* Hk,
                    const double* c, double* Hbar, double* tau, double* norm1) {
-  if (!ctx || N < 1 || d < 1 || K < 0 || !H0 || !Hbar || (K > 0 && (!Hk || !c))) return MG_EINVAL;
+  if (!ctx || N < 1 || d < 1 || d > 4096 || K < 0 || K > 64 || !H0 || !Hbar || (K > 0 && (!Hk || !c)))
+    return MG_EINVAL;
   MG_CUDA_TRY(cudaSetDevice(ctx->device));
   double* sc;
   MG_TRY(small_scratch(ctx, (size_t)K + 1 + N, &sc));
@@ -2567,16 +2568,25 @@ int mg_submit(mg_server* srv, const mg_job* job, uint64_t* job_id) {
 int mg_wait(mg_server* srv, uint64_t job_id, double timeout_s, mg_job_report* rep) {
   if (!srv) return MG_EINVAL;
   std::unique_lock<std::mutex> lock(srv->mu);
-  auto it = srv->jobs.find(job_id);
-  if (it == srv->jobs.end()) return MG_EINVAL;
-  SJob* j = it->second;
-  const auto pred = [&] { return j->finished; };
+  if (srv->jobs.find(job_id) == srv->jobs.end()) return MG_EINVAL;
+  // looked up again at every wake-up: another mg_wait on the same id may have
+  // taken the result and forgotten the job meanwhile
+  const auto pred = [&] {
+    auto f = srv->jobs.find(job_id);
+    return f == srv->jobs.end() || f->second->finished;
+  };
   if (timeout_s < 0) {
     srv->done_cv.wait(lock, pred);
   } else if (!srv->done_cv.wait_for(lock, std::chrono::duration<double>(timeout_s), pred)) {
     set_last_message("job %llu not finished within %g s", (unsigned long long)job_id, timeout_s);
     return MG_ETIMEOUT;
   }
+  auto it = srv->jobs.find(job_id);
+  if (it == srv->jobs.end()) {
+    set_last_message("job %llu was completed by another mg_wait", (unsigned long long)job_id);
+    return MG_EINVAL;
+  }
+  SJob* j = it->second;
   if (rep) {
     rep->status = j->status;
     rep->latency_ms = std::chrono::duration<double, std::milli>(j->t_done - j->t_submit).count();
