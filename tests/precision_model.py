@@ -126,8 +126,8 @@ def digits(M, L, beta, axis):
 # ----------------------------------------------------------------------------
 # the split product
 # ----------------------------------------------------------------------------
-def _level(s, t):
-    return min(s + t, 3)
+def _level(s, t, groups=4):
+    return min(s + t, groups - 1)
 
 
 def _to_f32(x, mode):
@@ -140,12 +140,13 @@ def _to_f32(x, mode):
     return f
 
 
-def split_product(A, B, L, beta=None, addends=(), diag=0.0, accumulate="zero"):
+def split_product(A, B, L, beta=None, addends=(), diag=0.0, accumulate="zero", groups=4):
     """C = A B (+ sum coef S + diag I) through L-digit split arithmetic, stored as double-float.
 
     A, B: (..., d, d) complex128 or double-float; addends: (coef, S) pairs with S of
     the same kind; accumulate: rounding of each FP32 accumulator update, "nearest"
-    or "zero" (truncation).  Returns (hi, lo)."""
+    or "zero" (truncation); groups: number of level accumulators (the last one takes
+    every level from groups - 1 up).  Returns (hi, lo)."""
     Av, Bv = (A[0] if isinstance(A, tuple) else A), (B[0] if isinstance(B, tuple) else B)
     d = Av.shape[-1]
     beta = split_beta(d) if beta is None else beta
@@ -166,7 +167,7 @@ def split_product(A, B, L, beta=None, addends=(), diag=0.0, accumulate="zero"):
     # blocks of K as a stack dimension: (L, ..., nblk, d, KBLOCK) and (L, ..., nblk, KBLOCK, 2d)
     Ab = np.moveaxis(Ae.reshape((L,) + batch + (d, nblk, KBLOCK)), -2, -3)
     Bb = Be.reshape((L,) + batch + (nblk, KBLOCK, 2 * d))
-    g = np.zeros((4,) + batch + (d, 2 * d), dtype=np.float32)
+    g = np.zeros((groups,) + batch + (d, 2 * d), dtype=np.float32)
     # bound the partial products held at once to about 2^25 doubles
     step = max(1, (1 << 25) // max(1, int(np.prod(batch, dtype=np.int64)) * d * 2 * d))
     for b0 in range(0, nblk, step):
@@ -174,7 +175,7 @@ def split_product(A, B, L, beta=None, addends=(), diag=0.0, accumulate="zero"):
         for s in range(L):
             for t in range(L - s):
                 part = np.matmul(Ab[s][..., sl, :, :], Bb[t][..., sl, :, :])   # exact 16-deep sums
-                lv = _level(s, t)
+                lv = _level(s, t, groups)
                 for k in range(part.shape[-3]):
                     g[lv] = _to_f32(g[lv].astype(np.float64) + part[..., k, :, :], accumulate)
     tot = g.astype(np.float64).sum(axis=0)

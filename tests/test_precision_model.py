@@ -98,3 +98,16 @@ def test_config0_tolerance_reached_from_five_digits():
         psi, _ = PM.evolve_state_split(parts["Hbar"], wl.psi0, L)
         errs[L] = np.abs(psi - ref).max()
     assert errs[3] > 1e-5 and errs[5] < 1e-7 and errs[6] < errs[5], errs
+
+
+def test_a_separate_level3_accumulator_lowers_the_floor():
+    """With truncating accumulation, the shared level->=3 accumulator sets the error floor
+    from L = 6 on; keeping level 3 apart (five accumulators) lowers it by well over 10x."""
+    rng = np.random.default_rng(9)
+    d = 64
+    A, B = rand_c(rng, (d, d)), rand_c(rng, (d, d))
+    ref = A @ B
+    e4 = np.abs(PM.df_value(PM.split_product(A, B, 7, groups=4)) - ref).max()
+    e5 = np.abs(PM.df_value(PM.split_product(A, B, 7, groups=5)) - ref).max()
+    e4_l6 = np.abs(PM.df_value(PM.split_product(A, B, 6, groups=4)) - ref).max()
+    assert e4 > 0.5 * e4_l6 and e5 < e4 / 10, (e4_l6, e4, e5)
