@@ -135,8 +135,11 @@ def _to_f32(x, mode):
     f = x.astype(np.float32)
     if mode == "nearest":
         return f
-    over = np.abs(f.astype(np.float64)) > np.abs(x)
-    f[over] = np.nextafter(f[over], np.float32(0))
+    # where rounding to nearest went past x (away from zero), step one unit back: in
+    # sign-magnitude bits that is the integer minus one, for either sign
+    over = (f.astype(np.float64) - x) * x > 0
+    bits = f.view(np.int32)
+    bits -= over
     return f
 
 
