@@ -362,3 +362,18 @@ def test_workload_generators_give_hermitian_operators():
         assert wl.drive(t).shape == (wl.N, wl.P, wl.K), wl.name
         if wl.psi0 is not None:
             assert abs(np.linalg.norm(wl.psi0) - 1.0) < 1e-15, wl.name
+
+
+def test_oracle_self_consistency_on_high_norm_instances():
+    """The uneven random instances with long intervals (||Hbar_n||_1 up to ~1e4 rad): the
+    oracle (eigendecomposition per interval) and the same evolution through
+    scipy.linalg.expm (scaling and squaring with Pade) agree to a few u ||Hbar|| N, the
+    oracle's own rounding scale on these jobs."""
+    rng = np.random.default_rng(21)
+    for i in range(6):
+        wl = W.random_instance(rng, name=f"job{i}", N_range=(5, 40), d_range=(16, 110))
+        ref, parts = oracle.evolve_workload(wl, return_parts=True)
+        U = np.stack([scipy.linalg.expm(-1j * h) for h in parts["Hbar"]])
+        alt = oracle.propagate_unitary(U) if wl.psi0 is None else oracle.propagate_state(U, wl.psi0)
+        hmax = max(np.abs(h).sum(axis=0).max() for h in parts["Hbar"])
+        assert np.abs(alt - ref).max() <= 4 * 2.0 ** -53 * hmax * wl.N, (wl.d, wl.N, hmax)
