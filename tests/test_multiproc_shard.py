@@ -1,5 +1,6 @@
-"""World-size-2 gloo tests (CPU) of the multi-process path: interval-range sharding of one job
-with a single all-gather of partial products, and the max-over-ranks timing reduction."""
+"""Gloo tests (CPU, world size 2 and 3) of the multi-process path: interval-range sharding of
+one job with a single all-gather of partial products, the state form that passes psi from
+rank to rank, and the max-over-ranks timing reduction."""
 import os
 import socket
 
@@ -73,3 +74,46 @@ def test_two_rank_sharded_propagator_matches_single_process():
     for rank, U, slowest in results:
         np.testing.assert_allclose(U, ref, atol=1e-12, rtol=0)
         assert slowest == 2.0
+
+
+def _state_worker(rank, world, port, N, q):
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        wl = W.transmon_resonator(nt=3, nr=4, N=N, T=3.0, sigma=0.7, omega0=0.4)
+        x, w = oracle.gauss_legendre(wl.P)
+
+        def local_partial(start, count):
+            t = oracle.node_times(wl.t0 + start * wl.dt, wl.dt, count, x)
+            U, _, _ = oracle.interval_propagators(wl.H0, wl.Hk, wl.drive(t), w, wl.dt)
+            return oracle.propagate_unitary(U)
+
+        q.put((rank, shard.sharded_state(local_partial, wl.N, wl.d, wl.psi0)))
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.timeout(180)
+@pytest.mark.parametrize("world,N", [(2, 37), (3, 37), (3, 2)])
+def test_sharded_state_matches_single_process(world, N):
+    """psi(T) from ranks that each own a range of intervals (N = 2 over 3 ranks leaves one
+    range empty) equals the single-process evolution on every rank."""
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_state_worker, args=(r, world, port, N, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    results = [q.get(timeout=150) for _ in range(world)]
+    for p in procs:
+        p.join(timeout=30)
+        assert p.exitcode == 0
+    wl = W.transmon_resonator(nt=3, nr=4, N=N, T=3.0, sigma=0.7, omega0=0.4)
+    assert wl.psi0 is not None
+    ref = oracle.evolve_workload(wl)
+    assert sorted(r for r, _ in results) == list(range(world))
+    for _, psi in results:
+        np.testing.assert_allclose(psi, ref, atol=1e-12, rtol=0)
