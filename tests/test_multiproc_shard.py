@@ -117,3 +117,46 @@ def test_sharded_state_matches_single_process(world, N):
     assert sorted(r for r, _ in results) == list(range(world))
     for _, psi in results:
         np.testing.assert_allclose(psi, ref, atol=1e-12, rtol=0)
+
+
+def _failing_worker(rank, world, port, q):
+    import datetime
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world, timeout=datetime.timedelta(seconds=10))
+    d = 4
+
+    def local_partial(start, count):
+        if rank == 1:
+            raise RuntimeError("rank 1 failed while forming its partial product")
+        return np.eye(d, dtype=np.complex128)
+
+    try:
+        shard.sharded_state(local_partial, 8, d, np.eye(d)[0])
+        q.put((rank, "ok"))
+    except Exception as e:   # the failure reaches every rank as an exception, not a hang
+        q.put((rank, type(e).__name__))
+    finally:
+        try:
+            dist.destroy_process_group()
+        except Exception:
+            pass
+
+
+@pytest.mark.timeout(120)
+def test_rank_failure_surfaces_as_an_error_on_the_other_rank():
+    """A rank that fails before its exchange: the rank waiting for its message gets an error
+    from the process group (peer gone or timeout) instead of waiting forever."""
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_failing_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    results = dict(q.get(timeout=90) for _ in range(2))
+    for p in procs:
+        p.join(timeout=30)
+    assert results[1] == "RuntimeError"
+    assert results[0] != "ok", results
