@@ -29,8 +29,9 @@ measures.  It models, it does not reproduce bit for bit:
   Taylor evaluation (degree m, block p) with the products above, s squarings,
   then the exact phase e^(-i tau).  The degree and squaring count minimise
   products + s under the remainder bound sum_{j>m} theta^j / j! <= u theta with
-  u = max(2^-53, 2^(-beta L)).  The library's degree-18 five-product scheme is
-  not modelled: the model takes the best Paterson-Stockmeyer degree instead.
+  u = max(2^-53, 2^(-beta L)); as on the library's split path, degree 18 in
+  five products (A2, A3, A6, A9 = B1 B5 + B4, T = B2 + (B3 + A9) A9, with the
+  coefficients of csrc/taylor18.h) is offered beside Paterson-Stockmeyer.
 * propagation of a state: each U_n read back to FP64, psi carried in FP64.
 """
 from __future__ import annotations
@@ -219,33 +220,74 @@ def theta(m, u):
     return lo
 
 
-def taylor_choice(norm1, u):
-    """(m, p, s) minimising Paterson-Stockmeyer products + s with norm1 / 2^s <= theta_m."""
+def taylor18_coefficients():
+    """The 24 coefficients of the degree-18 five-product scheme as the library stores them
+    (csrc/taylor18.h): B1 on I, A, A2, A3, then B5, B4, B3, B2 on I, A, A2, A3, A6."""
+    import os
+    import re
+    path = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                        "paper_2411_09982_gb300", "csrc", "taylor18.h")
+    text = open(path).read()
+    body = text[text.index("{", text.index("kTaylor18")) + 1:text.index("};")]
+    vals = [float(v) for v in re.findall(r"(-?[0-9][0-9.eE+-]*)\s*,", body)]
+    assert len(vals) == 24
+    return vals
+
+
+def taylor_choice(norm1, u, allow18=False):
+    """(m, p, s) minimising products + s with norm1 / 2^s <= theta_m over the
+    Paterson-Stockmeyer degrees and, when allowed, degree 18 in five products (p = 0);
+    ties go to fewer squarings, then to the lower degree."""
     best = None
-    for m, p in PS_DEGREES:
+    for m, p in PS_DEGREES + ([(18, 0)] if allow18 else []):
         th = theta(m, u)
         s = 0 if norm1 <= th else math.ceil(math.log2(norm1 / th))
         while norm1 * 2.0 ** -s > th:
             s += 1
         while s > 0 and norm1 * 2.0 ** -(s - 1) <= th:
             s -= 1
-        cost = _ps_products(m, p) + s
+        cost = (5 if p == 0 else _ps_products(m, p)) + s
         if best is None or cost < best[0] or (cost == best[0] and s < best[3]):
             best = (cost, m, p, s)
     return best[1:]
 
 
-def expm_split(W, L, tau=None):
+def _taylor18(X, L, beta):
+    """sum_{k<=18} X^k / k! in five modelled products: A2, A3, A6, A9 = B1 B5 + B4 and
+    T = B2 + (B3 + A9) A9, the B's combined in FP64 from double-float inputs."""
+    k = taylor18_coefficients()
+    d = X[0].shape[-1]
+    eye = np.eye(d)
+    A2 = split_product(X, X, L, beta)
+    A3 = split_product(A2, X, L, beta)
+    A6 = split_product(A3, A3, L, beta)
+    P = [df_value(M) for M in (X, A2, A3, A6)]
+    B1 = df_round(k[0] * eye + k[1] * P[0] + k[2] * P[1] + k[3] * P[2])
+    B5, B4, B3, B2 = (df_round(k[q] * eye + sum(k[q + 1 + j] * P[j] for j in range(4))) for q in (4, 9, 14, 19))
+    A9 = split_product(B1, B5, L, beta, addends=[(1.0, B4)])
+    Q = df_round(df_value(B3) + df_value(A9))
+    return split_product(Q, A9, L, beta, addends=[(1.0, B2)])
+
+
+def expm_split(W, L, tau=None, allow18=True):
     """exp(-i W) (times e^(-i tau) if tau is given) for a batch of Hermitian W (b, d, d),
     through the modelled split arithmetic; one (m, s) for the batch from its largest
-    FP64 1-norm.  Returns the double-float result and (m, s)."""
+    FP64 1-norm, with the degree-18 scheme offered as on the library's split path.
+    Returns the double-float result and (m, s)."""
     W = np.asarray(W, dtype=np.complex128)
     d = W.shape[-1]
     beta = split_beta(d)
     u = max(2.0 ** -53, 2.0 ** (-beta * L))
     norm1 = float(np.abs(W).sum(axis=-2).max())
-    m, p, s = taylor_choice(norm1, u)
+    m, p, s = taylor_choice(norm1, u, allow18)
     X = df_round(-1j * W * 2.0 ** -s)
+    if p == 0:
+        R = _taylor18(X, L, beta)
+        for _ in range(s):
+            R = split_product(R, R, L, beta)
+        if tau is not None:
+            R = df_round(np.exp(-1j * np.asarray(tau))[..., None, None] * df_value(R))
+        return R, (m, s)
     a = [1.0 / math.factorial(j) if j <= m else 0.0 for j in range(m + p + 1)]
     Pw = {1: X}
     for j in range(2, p + 1):
@@ -270,7 +312,7 @@ def expm_split(W, L, tau=None):
 # ----------------------------------------------------------------------------
 # a whole evolution of a state
 # ----------------------------------------------------------------------------
-def evolve_state_split(Hbar, psi0, L, chunk=256):
+def evolve_state_split(Hbar, psi0, L, chunk=256, allow18=True):
     """psi(T) = U_{N-1} ... U_0 psi0 with U_n = e^(-i tau_n) exp(-i (Hbar_n - tau_n I))
     from the modelled split exponential, in batches of `chunk` intervals (one (m, s)
     per batch), U_n read back to FP64 and psi carried in FP64.  Returns psi and the
@@ -282,7 +324,7 @@ def evolve_state_split(Hbar, psi0, L, chunk=256):
     for n0 in range(0, Hbar.shape[0], chunk):
         H = Hbar[n0:n0 + chunk]
         tau = np.real(np.trace(H, axis1=-2, axis2=-1)) / d
-        U, ms = expm_split(H - tau[:, None, None] * np.eye(d), L, tau)
+        U, ms = expm_split(H - tau[:, None, None] * np.eye(d), L, tau, allow18)
         choices.append(ms)
         U = df_value(U)
         for n in range(U.shape[0]):

@@ -67,17 +67,20 @@ def test_product_within_the_digit_bound(d, accumulate):
         assert errs[L - 1] < errs[L - 2] * 2.0 ** (4 - beta), errs
 
 
-def test_expm_model_matches_eigendecomposition():
-    """The modelled split exponential against the oracle's exp(-i H) (eigendecomposition)."""
+@pytest.mark.parametrize("allow18", [False, True])
+def test_expm_model_matches_eigendecomposition(allow18):
+    """The modelled split exponential, by Paterson-Stockmeyer or by the degree-18
+    five-product scheme, against the oracle's exp(-i H) (eigendecomposition)."""
     rng = np.random.default_rng(4)
     d = 24
     H = np.stack([0.4 * (a + a.conj().T) for a in rand_c(rng, (3, d, d))])
     ref = np.stack([oracle.expm_minus_i(h) for h in H])
     errs = {}
     for L in (3, 6):
-        U, _ = PM.expm_split(H, L)
+        U, (m, _) = PM.expm_split(H, L, allow18=allow18)
+        assert (m == 18) == allow18
         errs[L] = np.abs(PM.df_value(U) - ref).max()
-    assert errs[6] < 1e-11 and errs[3] > 100 * errs[6], errs
+    assert errs[6] < 1e-10 and errs[3] > 100 * errs[6], errs
 
 
 def test_expm_model_of_a_diagonal_is_the_exact_phase():
