@@ -126,3 +126,22 @@ def test_taylor_choice_small_norms_take_low_degrees_and_no_squaring():
 def test_taylor_choice_rejects_invalid_arguments(args):
     with pytest.raises(M.MagnusError):
         M.mg_taylor_choice(*args)
+
+
+def test_node_samples_follow_the_header_node_map():
+    """The binding's drive samples sit at t0 + n dt + (1 + x_p) dt / 2 (the node map the
+    header documents), N x P x K contiguous; with them, (dt/2) sum_p w_p u(t_{n,p})
+    integrates a polynomial drive of degree <= 2P - 1 exactly over every interval."""
+    import oracle
+    import workloads as W
+    wl = W.config(0, N=12)
+    samples, w = M.node_samples(wl)
+    assert samples.shape == (wl.N, wl.P, wl.K) and samples.flags["C_CONTIGUOUS"]
+    x, _ = M.mg_quadrature_nodes(wl.P)
+    np.testing.assert_allclose(samples, wl.drive(oracle.node_times(wl.t0, wl.dt, wl.N, x)), rtol=0, atol=1e-15)
+    # a cubic drive u(t) = t^3: the integral over [t_n, t_n + dt] is exact
+    wl3 = W.Workload("cubic", wl.H0, wl.Hk, lambda t: (t ** 3)[..., None], 0.5, 0.25, 6, wl.P, None)
+    s3, w3 = M.node_samples(wl3)
+    c = 0.5 * wl3.dt * (s3[..., 0] * w3[None, :]).sum(axis=1)
+    tn = wl3.t0 + wl3.dt * np.arange(wl3.N)
+    np.testing.assert_allclose(c, ((tn + wl3.dt) ** 4 - tn ** 4) / 4, rtol=1e-14, atol=0)
