@@ -377,3 +377,27 @@ def test_oracle_self_consistency_on_high_norm_instances():
         alt = oracle.propagate_unitary(U) if wl.psi0 is None else oracle.propagate_state(U, wl.psi0)
         hmax = max(np.abs(h).sum(axis=0).max() for h in parts["Hbar"])
         assert np.abs(alt - ref).max() <= 4 * 2.0 ** -53 * hmax * wl.N, (wl.d, wl.N, hmax)
+
+
+def test_workload_recipes_match_the_stated_configurations():
+    """The uneven batch: 512 state jobs, d = nt nr in [16, 256], N in [200, 2000], P = 16,
+    one drive.  The served stream: Poisson arrivals at 200/s over 60 s, d the largest
+    family member not above a log-uniform draw on [32, 2048], N in [100, 5000], state or
+    unitary with probability 1/2 each."""
+    jobs = W.uneven_batch()
+    assert len(jobs) == 512
+    assert all(16 <= j.d <= 256 and 200 <= j.N <= 2000 and j.P == 16 and j.K == 1 for j in jobs)
+    assert all(j.psi0 is not None for j in jobs)
+    stream = W.serving_stream()
+    t = np.array([a for a, _ in stream])
+    assert np.all(np.diff(t) > 0) and t[-1] <= 60.0
+    assert abs(len(stream) - 12000) < 4 * math.sqrt(12000)
+    for _, s in stream:
+        assert 100 <= s["N"] <= 5000 and s["dt"] == 0.05 and s["output"] in ("state", "unitary")
+        if s["family"] == "chain3":
+            n = round(math.log(s["d"]) / math.log(3))
+            assert 3 ** n == s["d"] and 27 <= s["d"] <= 729
+        else:
+            assert s["family"] == "transmon_resonator" and 16 <= s["d"] <= 2048
+    frac_state = np.mean([s["output"] == "state" for _, s in stream])
+    assert abs(frac_state - 0.5) < 4 * math.sqrt(0.25 / len(stream))
