@@ -58,12 +58,15 @@ extern "C" {
 
 /* ---- precision modes ------------------------------------------------------ */
 /* MG_PREC_FP64: every matrix product in native FP64 arithmetic.
- * MG_PREC_SPLIT: matrix products on the tcgen05 tensor cores.  Each FP64
- *   operand row (column) is scaled by a power of two and cut into `slices`
- *   signed BF16 digits of `beta` bits; digit products are accumulated in FP32
- *   TMEM accumulators that stay exact for the leading digits, and combined in
- *   FP64.  More slices give more accuracy (about beta*slices bits).  All other
- *   steps (quadrature, Hbar_n, norms, phases, re-orthonormalisation) run in FP64. */
+ * MG_PREC_SPLIT: matrix products on the tcgen05 tensor cores.  Each operand row
+ *   (column) is scaled by a power of two and cut into `slices` signed BF16
+ *   digits of `beta` bits; digit products are accumulated in FP32 TMEM
+ *   accumulators that stay exact for the leading digits, and combined in
+ *   double-float (FP32 hi + lo, about 48 bits).  The exponential's intermediate
+ *   matrices (powers, Taylor blocks, squarings, U_n) are stored and combined as
+ *   double-float.  More slices give more accuracy (about beta*slices bits, down
+ *   to the rounding of the FP32 accumulators).  Quadrature, Hbar_n, the norms,
+ *   the trace phases, the state chain and re-orthonormalisation run in FP64. */
 #define MG_PREC_FP64   0
 #define MG_PREC_SPLIT  1
 
