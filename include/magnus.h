@@ -262,7 +262,16 @@ typedef struct mg_job_report {
   int64_t intervals;
 } mg_job_report;
 
+/* Start a server on `ctx`: mem_budget_bytes (> 0) bounds the device memory of
+ * the admitted jobs together; quantum_intervals (>= 1) is how many intervals a
+ * job advances per chunk step.  Starts the worker threads and the action
+ * streams.  MG_EINVAL for bad arguments, MG_ENOMEM if its streams or tables
+ * cannot be created. */
 int mg_server_create(mg_ctx* ctx, size_t mem_budget_bytes, int quantum_intervals, mg_server** out);
+/* Admit one job (see mg_job); *job_id names it for mg_wait.  MG_EAGAIN when it
+ * does not fit the memory budget now (retry after jobs complete), MG_EINVAL for
+ * bad arguments, MG_EUNSUPPORTED for an action-path job beyond that path's
+ * limits, MG_ENOMEM if its upload allocation fails. */
 int mg_submit(mg_server* srv, const mg_job* job, uint64_t* job_id);
 /* Block until the job completes (timeout_s < 0: no limit).  Returns the job's
  * status, or MG_ETIMEOUT if it has not completed in time (the job keeps
@@ -273,6 +282,9 @@ int mg_wait(mg_server* srv, uint64_t job_id, double timeout_s, mg_job_report* re
 /* Latency percentiles of completed jobs and intervals completed per second of
  * wall time since the first submission. */
 int mg_server_stats(mg_server* srv, double* p50_ms, double* p99_ms, double* intervals_per_s, int64_t* completed);
+/* Stop the server: waits until every admitted job has completed (their outputs
+ * are written), then frees the server's streams and memory.  Results that were
+ * not waited for are discarded. */
 int mg_server_destroy(mg_server* srv);
 
 /* ---- steps of the path (device pointers) --------------------------------- */
