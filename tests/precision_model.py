@@ -330,3 +330,41 @@ def evolve_state_split(Hbar, psi0, L, chunk=256, allow18=True):
         for n in range(U.shape[0]):
             psi = U[n] @ psi
     return psi, choices
+
+
+# ----------------------------------------------------------------------------
+# command line: predicted error of a state workload against the FP64 oracle
+# ----------------------------------------------------------------------------
+def main(argv=None):
+    """python tests/precision_model.py [--config 0 | --batch-job I] [--slices L]
+    [--intervals N] [--no-taylor18]: the modelled split-precision psi(T) against the
+    oracle's, max-abs error printed with the (m, s) choices."""
+    import argparse
+    import os
+    import sys
+    import time
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    sys.path.insert(0, root)
+    import oracle
+    import workloads as W
+    ap = argparse.ArgumentParser(description=main.__doc__)
+    ap.add_argument("--config", type=int, default=0, help="single-job state workload (0)")
+    ap.add_argument("--batch-job", type=int, default=None, help="job I of the 512-instance uneven batch instead")
+    ap.add_argument("--slices", type=int, default=6)
+    ap.add_argument("--intervals", type=int, default=None, help="first N intervals only")
+    ap.add_argument("--chunk", type=int, default=64, help="intervals per modelled batch (one (m, s) each)")
+    ap.add_argument("--no-taylor18", action="store_true", help="Paterson-Stockmeyer only")
+    a = ap.parse_args(argv)
+    wl = W.uneven_batch()[a.batch_job] if a.batch_job is not None else W.config(a.config)
+    if wl.psi0 is None:
+        raise SystemExit(f"{wl.name} has no initial state: the model evolves states only")
+    t = time.time()
+    ref, parts = oracle.evolve_workload(wl, n_intervals=a.intervals, return_parts=True)
+    psi, ms = evolve_state_split(parts["Hbar"], wl.psi0, a.slices, chunk=a.chunk, allow18=not a.no_taylor18)
+    print(f"{wl.name}: d = {wl.d}, {parts['Hbar'].shape[0]} intervals, L = {a.slices}, "
+          f"(m, s) = {sorted(set(ms))}: max |psi_model - psi_oracle| = {np.abs(psi - ref).max():.3e} "
+          f"({time.time() - t:.1f} s)")
+
+
+if __name__ == "__main__":
+    main()
