@@ -29,10 +29,22 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 // ---------------------------------------------------------------------------
 // error reporting
 // ---------------------------------------------------------------------------
 namespace mg {
+// Named NVTX range over a host-side phase (Hbar, exponential, propagation,
+// re-orthonormalisation, action, chunk step): a profiler can filter kernels by
+// phase; without one attached the calls do nothing.
+struct PhaseRange {
+  explicit PhaseRange(const char* name) { nvtxRangePushA(name); }
+  ~PhaseRange() { nvtxRangePop(); }
+  PhaseRange(const PhaseRange&) = delete;
+  PhaseRange& operator=(const PhaseRange&) = delete;
+};
+
 static thread_local char g_msg[512] = "";
 static std::atomic<long long> g_launches{0};
 
@@ -404,6 +416,7 @@ struct ExpmStats {
 
 int expm_chunk(mg_ctx* ctx, Engine& eng, int batch, double* W, const double* tau, const double* norm1_dev,
                double* U, long long sU, ExpmStats* st, const std::vector<double>* host_norms = nullptr) {
+  PhaseRange range("expm");
   const int d = eng.d;
   const long long md = mat_doubles(d);
   cudaStream_t s = ctx->stream;
@@ -559,6 +572,7 @@ int expm_chunk(mg_ctx* ctx, Engine& eng, int batch, double* W, const double* tau
 // One Newton-Schulz polar step in FP64 on a batch: Z <- Z (3I - Z^dag Z)/2.
 // Z is in the engine's storage format; the step itself runs in FP64.
 int reorth_batch(mg_ctx* ctx, Engine& eng, int batch, double* Z, long long sZ) {
+  PhaseRange range("reorth");
   const int d = eng.d;
   const long long md = mat_doubles(d);
   double *Zf, *G, *H;
@@ -855,6 +869,7 @@ size_t action_ws_bytes(const ActionShape& S, size_t nj, size_t* off_mat, size_t*
 // chain is timed and its work (8 flops per pattern nonzero per operator
 // application) is added to the context's counters.
 int run_action(mg_ctx* ctx, std::vector<ActionJob>& jobs, const std::vector<CsrRef>& pat) {
+  PhaseRange range("action");
   const size_t nj = jobs.size();
   ActionShape S;
   shape_action(jobs, pat, S);
@@ -1302,6 +1317,7 @@ struct PropState {
 
 // Fold the chunk's propagators U (n of them, stride md) into the running state.
 int fold_chunk(mg_ctx* ctx, Engine& eng, PropState& ps, int n, const double* U, int reorth) {
+  PhaseRange range("propagate");
   const int d = ps.d;
   const long long md = mat_doubles(d);
   if (ps.output == MG_OUT_STATE) {
@@ -1485,8 +1501,11 @@ int mg_evolve(mg_plan* p, int output, const double* in, double* out, int reorth_
     MG_TRY(ws(ctx, WS_TAU, nb, &tau));
     MG_TRY(ws(ctx, WS_NORM, nb, &nrm));
     MG_TRY(small_scratch(ctx, (size_t)p->Kx + 1 + nb, &sc));
-    MG_TRY(launch_build_omega(nb, d, p->Kx, p->dt, p->H0, p->Hk, p->c + (long long)n0 * p->Kx, W, tau, nrm, shift,
-                              /*write_shifted=*/1, sc, s));
+    {
+      PhaseRange range("hbar");
+      MG_TRY(launch_build_omega(nb, d, p->Kx, p->dt, p->H0, p->Hk, p->c + (long long)n0 * p->Kx, W, tau, nrm,
+                                shift, /*write_shifted=*/1, sc, s));
+    }
     double* Ubuf;
     MG_TRY(ws(ctx, WS_UBUF, md * nb, &Ubuf));
     MG_TRY(expm_chunk(ctx, eng, nb, W, tau, nrm, Ubuf, md, &st));
@@ -1575,6 +1594,7 @@ struct ChunkSeg {
 // launch (capacity >= number of segments).
 int process_chunk(mg_ctx* ctx, Engine& eng, std::vector<ChunkSeg>& segs, int fill, int reorth_every,
                   ChainSeg* segs_dev, double** psi_dev, ExpmStats* st) {
+  PhaseRange range("batch_chunk");
   cudaStream_t s = ctx->stream;
   const int dp = eng.d;
   const long long md = mat_doubles(dp);
