@@ -4,7 +4,7 @@ mg_cgemm_split_static serves callers that cannot allocate device memory: its
 scratch is a static device array inside the library instead of cudaMalloc.  It
 must return what the allocating entry point returns for the same inputs, on
 every call, although all calls reuse the same scratch.  This file is collected
-last so that a failure here leaves every other test already run.
+after the parity tests, so that a failure here leaves them already run.
 """
 import numpy as np
 import pytest
