@@ -135,6 +135,17 @@ int mg_ctx_set_workspace_limit(mg_ctx* ctx, size_t bytes);
  * 1 <= P <= 64. */
 int mg_quadrature_nodes(int P, double* x, double* w);
 
+/* ---- second-order weights (host only) ------------------------------------ */
+/* The P x P matrix behind the second-order term (Eq. magnus-avg, second line) as
+ * the plans of order 2 use it: with s_r = (1 + x_r)/2 the mg_quadrature_nodes
+ * mapped to [0, 1] and l_r their Lagrange basis,
+ *     M[p][q] = int_0^1 l_p(s1) int_0^{s1} l_q(s2) ds2 ds1,
+ * so that the double integral over t_n <= t2 <= t1 <= t_n + dt of g(t1) f(t2) is
+ * dt^2 sum_{p,q} g_p f_q M[p][q] for the interpolating polynomials of the samples.
+ * M (HOST, P*P + 2P doubles) receives M row-major (row p: the t1 node), then the
+ * column sums C_q, then the row sums R_p.  1 <= P <= 64. */
+int mg_second_order_weights(int P, double* M);
+
 /* ---- exponential parameters (host only) ---------------------------------- */
 /* The Taylor degree m and squaring count s that mg_expm and mg_evolve take for a
  * batch whose largest FP64 1-norm of Hbar_n - tau_n I is norm1 (Sec. "Magnus

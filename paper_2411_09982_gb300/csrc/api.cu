@@ -1091,6 +1091,14 @@ int mg_quadrature_nodes(int P, double* x, double* w) {
   return MG_OK;
 }
 
+int mg_second_order_weights(int P, double* M) {
+  if (P < 1 || P > 64 || !M) return MG_EINVAL;
+  std::vector<double> mrc;
+  MG_TRY(lagrange_triangle(P, mrc));
+  std::memcpy(M, mrc.data(), sizeof(double) * mrc.size());
+  return MG_OK;
+}
+
 int mg_taylor_choice(double norm1, int precision, int slices, int d, int* m, int* s, double* theta) {
   if (!m || !s || !theta || !(norm1 >= 0.0) || !std::isfinite(norm1) || d < 1 || d > 4096) return MG_EINVAL;
   MG_TRY(validate_prec(precision, slices));

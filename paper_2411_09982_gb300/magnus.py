@@ -88,6 +88,7 @@ SIGNATURES = {
     "mg_ctx_set_workspace_limit": (_I, [_P, ctypes.c_size_t]),
     "mg_quadrature_nodes": (_I, [_I, _P, _P]),
     "mg_taylor_choice": (_I, [_D, _I, _I, _I, _P, _P, _P]),
+    "mg_second_order_weights": (_I, [_I, _P]),
     "mg_plan_create": (_I, [_P, ctypes.POINTER(_P), _I, _I, _P, _P, _I, _I, _I]),
     "mg_plan_destroy": (_I, [_P]),
     "mg_plan_set_magnus_order": (_I, [_P, _I]),
@@ -329,6 +330,14 @@ def mg_quadrature_nodes(P: int):
     _check(lib.mg_quadrature_nodes(P, x.ctypes.data_as(ctypes.c_void_p), w.ctypes.data_as(ctypes.c_void_p)),
            "mg_quadrature_nodes")
     return x, w
+
+
+def mg_second_order_weights(P: int):
+    """(M, C, R): the P x P second-order weight matrix, its column and row sums (host only)."""
+    import numpy as np
+    out = np.zeros(P * P + 2 * P)
+    _check(load().mg_second_order_weights(P, out.ctypes.data_as(ctypes.c_void_p)), "mg_second_order_weights")
+    return out[:P * P].reshape(P, P), out[P * P:P * P + P], out[P * P + P:]
 
 
 def mg_taylor_choice(norm1: float, precision=MG_PREC_FP64, slices=6, d=1):

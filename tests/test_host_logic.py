@@ -145,3 +145,49 @@ def test_node_samples_follow_the_header_node_map():
     c = 0.5 * wl3.dt * (s3[..., 0] * w3[None, :]).sum(axis=1)
     tn = wl3.t0 + wl3.dt * np.arange(wl3.N)
     np.testing.assert_allclose(c, ((tn + wl3.dt) ** 4 - tn ** 4) / 4, rtol=1e-14, atol=0)
+
+
+@pytest.mark.parametrize("P", [1, 2, 3, 5, 8, 16])
+def test_second_order_weights_satisfy_their_exact_identities(P):
+    """M[p][q] = int_0^1 l_p(s1) int_0^{s1} l_q(s2): its row sums are int_0^1 l_p(s) s ds =
+    (w_p/2) s_p, its column sums int_0^1 l_q(s)(1 - s) ds = (w_q/2)(1 - s_q), and
+    M[p][q] + M[q][p] is the full square's integral (w_p/2)(w_q/2) (Gauss-Legendre is
+    exact for these degrees); the stored sums equal the matrix's."""
+    Mw, C, R = M.mg_second_order_weights(P)
+    x, w = np.polynomial.legendre.leggauss(P)
+    s, h = 0.5 * (1.0 + x), 0.5 * w
+    np.testing.assert_allclose(Mw.sum(axis=1), h * s, atol=1e-14, rtol=0)
+    np.testing.assert_allclose(Mw.sum(axis=0), h * (1.0 - s), atol=1e-14, rtol=0)
+    np.testing.assert_allclose(Mw + Mw.T, np.outer(h, h), atol=1e-14, rtol=0)
+    np.testing.assert_allclose(R, Mw.sum(axis=1), atol=1e-15, rtol=0)
+    np.testing.assert_allclose(C, Mw.sum(axis=0), atol=1e-15, rtol=0)
+
+
+@pytest.mark.parametrize("P", [2, 3, 5])
+def test_second_order_weights_by_exact_integration(P):
+    """Small P: each entry by exact rational integration of the Lagrange polynomials on
+    the same (double) nodes, to the rounding of the result."""
+    Mw, _, _ = M.mg_second_order_weights(P)
+    s = [Fraction(v) for v in 0.5 * (1.0 + np.polynomial.legendre.leggauss(P)[0])]
+
+    def mul(a, b):
+        out = [Fraction(0)] * (len(a) + len(b) - 1)
+        for i, u in enumerate(a):
+            for j, v in enumerate(b):
+                out[i + j] += u * v
+        return out
+
+    def integ(a):   # antiderivative vanishing at 0
+        return [Fraction(0)] + [c / (k + 1) for k, c in enumerate(a)]
+
+    ell = []
+    for p in range(P):
+        poly = [Fraction(1)]
+        for r in range(P):
+            if r != p:
+                poly = mul(poly, [-s[r] / (s[p] - s[r]), 1 / (s[p] - s[r])])
+        ell.append(poly)
+    for p in range(P):
+        for q in range(P):
+            val = float(sum(integ(mul(ell[p], integ(ell[q])))))   # evaluated at s1 = 1
+            assert abs(Mw[p, q] - val) <= 4e-16, (p, q, Mw[p, q], val)
