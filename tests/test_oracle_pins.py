@@ -379,6 +379,17 @@ def test_oracle_self_consistency_on_high_norm_instances():
         assert np.abs(alt - ref).max() <= 4 * 2.0 ** -53 * hmax * wl.N, (wl.d, wl.N, hmax)
 
 
+def test_single_job_workloads_have_the_stated_sizes():
+    """d = 30 transmon-resonator: K = 1, N = 1000, P = 16, T = 50 ns, a state from |0,0>.
+    d = 729 chain of six three-level transmons: K = 6, N = 2000, P = 16, T = 50 ns, full
+    propagator."""
+    wl0, wl1 = W.config(0), W.config(1)
+    assert (wl0.d, wl0.K, wl0.N, wl0.P, wl0.T) == (30, 1, 1000, 16, 50.0)
+    assert wl0.psi0 is not None and wl0.psi0[0] == 1.0 and np.count_nonzero(wl0.psi0) == 1
+    assert (wl1.d, wl1.K, wl1.N, wl1.P, wl1.T) == (729, 6, 2000, 16, 50.0) and wl1.psi0 is None
+    assert abs(wl1.dt - 0.025) < 1e-15 and abs(wl0.dt - 0.05) < 1e-15
+
+
 def test_workload_recipes_match_the_stated_configurations():
     """The uneven batch: 512 state jobs, d = nt nr in [16, 256], N in [200, 2000], P = 16,
     one drive.  The served stream: Poisson arrivals at 200/s over 60 s, d the largest
