@@ -135,6 +135,18 @@ int mg_ctx_set_workspace_limit(mg_ctx* ctx, size_t bytes);
  * 1 <= P <= 64. */
 int mg_quadrature_nodes(int P, double* x, double* w);
 
+/* ---- sparse pattern of the action path (host only) ----------------------- */
+/* The CSR form MG_FLAG_STATE_ACTION plans build from their nops = 1 + K dense
+ * operators (`dense`: HOST, nops x d x d complex, H0 first): one pattern, the
+ * union of the operators' nonzero entries plus the whole diagonal, with columns
+ * ascending in each row, and one value array per operator on that pattern.
+ * *nnz receives the pattern's size.  With rowptr NULL the call only reports
+ * *nnz; otherwise rowptr (d + 1 ints), col (nnz ints), diag (d ints: the index in
+ * col of each row's diagonal entry) and val (nops x nnz complex, operator-major)
+ * are filled (HOST arrays).  1 <= d <= 4096, 1 <= nops <= 256. */
+int mg_csr_pattern(int d, int nops, const double* dense, int64_t* nnz, int* rowptr, int* col, int* diag,
+                   double* val);
+
 /* ---- second-order weights (host only) ------------------------------------ */
 /* The P x P matrix behind the second-order term (Eq. magnus-avg, second line) as
  * the plans of order 2 use it: with s_r = (1 + x_r)/2 the mg_quadrature_nodes

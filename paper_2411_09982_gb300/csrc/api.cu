@@ -1091,6 +1091,21 @@ int mg_quadrature_nodes(int P, double* x, double* w) {
   return MG_OK;
 }
 
+int mg_csr_pattern(int d, int nops, const double* dense, int64_t* nnz, int* rowptr, int* col, int* diag,
+                   double* val) {
+  if (d < 1 || d > 4096 || nops < 1 || nops > 256 || !dense || !nnz) return MG_EINVAL;
+  CsrHost h;
+  build_csr_host(dense, d, nops, h);
+  *nnz = (int64_t)h.col.size();
+  if (!rowptr) return MG_OK;   // size query
+  if (!col || !diag || !val) return MG_EINVAL;
+  std::memcpy(rowptr, h.rowptr.data(), sizeof(int) * h.rowptr.size());
+  std::memcpy(col, h.col.data(), sizeof(int) * h.col.size());
+  std::memcpy(diag, h.diag.data(), sizeof(int) * h.diag.size());
+  std::memcpy(val, h.val.data(), sizeof(double) * h.val.size());
+  return MG_OK;
+}
+
 int mg_second_order_weights(int P, double* M) {
   if (P < 1 || P > 64 || !M) return MG_EINVAL;
   std::vector<double> mrc;

@@ -89,6 +89,7 @@ SIGNATURES = {
     "mg_quadrature_nodes": (_I, [_I, _P, _P]),
     "mg_taylor_choice": (_I, [_D, _I, _I, _I, _P, _P, _P]),
     "mg_second_order_weights": (_I, [_I, _P]),
+    "mg_csr_pattern": (_I, [_I, _I, _P, _P, _P, _P, _P, _P]),
     "mg_plan_create": (_I, [_P, ctypes.POINTER(_P), _I, _I, _P, _P, _I, _I, _I]),
     "mg_plan_destroy": (_I, [_P]),
     "mg_plan_set_magnus_order": (_I, [_P, _I]),
@@ -330,6 +331,25 @@ def mg_quadrature_nodes(P: int):
     _check(lib.mg_quadrature_nodes(P, x.ctypes.data_as(ctypes.c_void_p), w.ctypes.data_as(ctypes.c_void_p)),
            "mg_quadrature_nodes")
     return x, w
+
+
+def mg_csr_pattern(ops):
+    """(rowptr, col, diag, val) of the action path's CSR form of `ops` (nops x d x d
+    complex, H0 first; host only): val is nops x nnz complex."""
+    import numpy as np
+    ops = np.ascontiguousarray(ops, dtype=np.complex128)
+    nops, d = ops.shape[0], ops.shape[1]
+    lib = load()
+    nnz = ctypes.c_int64()
+    src = ops.ctypes.data_as(ctypes.c_void_p)
+    _check(lib.mg_csr_pattern(d, nops, src, ctypes.byref(nnz), None, None, None, None), "mg_csr_pattern")
+    n = nnz.value
+    rowptr, col, diag = np.zeros(d + 1, np.int32), np.zeros(max(n, 1), np.int32), np.zeros(d, np.int32)
+    val = np.zeros((nops, max(n, 1)), np.complex128)
+    _check(lib.mg_csr_pattern(d, nops, src, ctypes.byref(nnz), rowptr.ctypes.data_as(ctypes.c_void_p),
+                              col.ctypes.data_as(ctypes.c_void_p), diag.ctypes.data_as(ctypes.c_void_p),
+                              val.ctypes.data_as(ctypes.c_void_p)), "mg_csr_pattern")
+    return rowptr, col[:n], diag, val[:, :n]
 
 
 def mg_second_order_weights(P: int):

@@ -191,3 +191,27 @@ def test_second_order_weights_by_exact_integration(P):
         for q in range(P):
             val = float(sum(integ(mul(ell[p], integ(ell[q])))))   # evaluated at s1 = 1
             assert abs(Mw[p, q] - val) <= 4e-16, (p, q, Mw[p, q], val)
+
+
+@pytest.mark.parametrize("d,nops,density", [(1, 1, 1.0), (7, 3, 0.2), (40, 5, 0.05), (33, 2, 0.0)])
+def test_csr_pattern_is_the_union_with_the_diagonal(d, nops, density):
+    """The action path's CSR form: the pattern is exactly the union of the operators'
+    nonzeros plus the diagonal, columns ascending per row, diag pointing at (i, i), and
+    every operator's values scattered back on the pattern reproduce it exactly."""
+    rng = np.random.default_rng(d * 10 + nops)
+    ops = (rng.normal(size=(nops, d, d)) + 1j * rng.normal(size=(nops, d, d))) * (rng.uniform(size=(nops, d, d)) < density)
+    ops[0, 0, d - 1] = 0.5j   # an entry with a zero real part still counts
+    rowptr, col, diag, val = M.mg_csr_pattern(ops)
+    want = (ops != 0).any(axis=0) | np.eye(d, dtype=bool)
+    got = np.zeros((d, d), bool)
+    for i in range(d):
+        cols = col[rowptr[i]:rowptr[i + 1]]
+        assert np.all(np.diff(cols) > 0)
+        got[i, cols] = True
+        assert col[diag[i]] == i and rowptr[i] <= diag[i] < rowptr[i + 1]
+    assert np.array_equal(got, want) and rowptr[-1] == want.sum()
+    for k in range(nops):
+        dense = np.zeros((d, d), complex)
+        for i in range(d):
+            dense[i, col[rowptr[i]:rowptr[i + 1]]] = val[k, rowptr[i]:rowptr[i + 1]]
+        assert np.array_equal(dense, ops[k])
