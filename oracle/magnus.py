@@ -172,6 +172,31 @@ def evolve_workload(wl, n_intervals=None, return_parts=False):
     return out
 
 
+def evolve_workload_streamed(wl, n_intervals=None, snapshots=()):
+    """The result of `evolve_workload`, formed one interval at a time.
+
+    For every n: c_{k,n} (Eq. magnus-first-order-coeff), Hbar_n
+    (Eq. magnus-first-order-term), U_n = exp(-i Hbar_n), and the running
+    product (U_n @ U or U_n @ psi) -- the same steps in the same order as
+    `evolve_workload`, but no interval's matrices are kept, so memory stays at a
+    few d x d matrices for the large workloads (d = 4096).  Returns the final
+    psi or U, and a dict {n: value after n intervals} for every n in `snapshots`.
+    """
+    x, w = gauss_legendre(wl.P)
+    N = wl.N if n_intervals is None else int(n_intervals)
+    d = wl.H0.shape[0]
+    acc = np.eye(d, dtype=np.complex128) if wl.psi0 is None else np.asarray(wl.psi0, np.complex128).copy()
+    snaps = {}
+    for n in range(N):
+        t = node_times(wl.t0 + n * wl.dt, wl.dt, 1, x)
+        c = drive_coefficients(wl.drive(t), w, wl.dt)[0]
+        Un = expm_minus_i(first_order_term(wl.H0, wl.Hk, c, wl.dt))
+        acc = Un @ acc
+        if n + 1 in snapshots:
+            snaps[n + 1] = acc.copy()
+    return acc, snaps
+
+
 def interval_propagators_second_order(H0, Hk, drive, t0, dt, N, P):
     """U_n = exp(-i (Hbar^(1)_n + Hbar^(2)_n)) with both Magnus terms of Eq. magnus-avg over
     every interval: Hbar^(1) by P-point Gauss-Legendre quadrature of the drive, Hbar^(2) by

@@ -412,3 +412,15 @@ def test_workload_recipes_match_the_stated_configurations():
             assert s["family"] == "transmon_resonator" and 16 <= s["d"] <= 2048
     frac_state = np.mean([s["output"] == "state" for _, s in stream])
     assert abs(frac_state - 0.5) < 4 * math.sqrt(0.25 / len(stream))
+
+
+def test_streamed_evolution_equals_stored_evolution():
+    """The streamed form (one interval at a time, used for the d = 4096 stored values) takes
+    the same steps in the same order as evolve_workload: identical results, bit for bit,
+    for propagators and states, and snapshots equal the shorter runs."""
+    for wl in (W.config(1, N=4), W.config(0, N=6)):
+        full = oracle.evolve_workload(wl)
+        streamed, snaps = oracle.evolve_workload_streamed(wl, snapshots=(1, 3))
+        assert np.array_equal(full, streamed)
+        for n, v in snaps.items():
+            assert np.array_equal(v, oracle.evolve_workload(wl, n_intervals=n))
