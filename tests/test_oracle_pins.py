@@ -418,7 +418,9 @@ def test_streamed_evolution_equals_stored_evolution():
     """The streamed form (one interval at a time, used for the d = 4096 stored values) takes
     the same steps in the same order as evolve_workload: identical results, bit for bit,
     for propagators and states, and snapshots equal the shorter runs."""
-    for wl in (W.config(1, N=4), W.config(0, N=6)):
+    chain = W.transmon_chain(n_sites=3, levels=3, J=0.02, seed=4, omega0_max=0.2, T=5.0, sigma=1.2, N=5, P=8,
+                             unitary=True)
+    for wl in (chain, W.config(0, N=6)):
         full = oracle.evolve_workload(wl)
         streamed, snaps = oracle.evolve_workload_streamed(wl, snapshots=(1, 3))
         assert np.array_equal(full, streamed)
