@@ -32,12 +32,11 @@ METRIC = "Magnus intervals/sec at dim 729 vs FP64 err; p50/p99 latency, mixed st
 UNIT = "intervals/s"
 WORKLOAD = "transmon_chain_d729_N2000_P16_K6_propagator"
 SAMPLE_INTERVALS = 128          # oracle sample (cpu_baseline) and accuracy prefix
-# DRAM bytes (read + write) per complex d = 729 product of split_gemm_kernel<6,2,2> (64-byte
-# swizzled K = 32 stages, 2-CTA clusters sharing B by multicast, B digits as three planes, tensor
-# maps ending at row d), from the ncu capture summarised in profiles/split_gemm_d729_batch32_L6.md
-# (1.494 GB for 32 products); scaled to a launch by the products it computes.  Valid for that
-# kernel build only.
-GEMM_DRAM_BYTES_PER_PRODUCT = {(729, 6): 1.493893e9 / 32}
+# DRAM bytes (read + write) per complex product of the split-product kernel in its current
+# form, keyed by (d, digits): one ncu capture of a 32-product launch divided by 32; the bench
+# scales it to the average timed launch by the products that launch computes.  An entry is
+# valid for the kernel build it was captured from only, and is removed when the kernel changes.
+GEMM_DRAM_BYTES_PER_PRODUCT = {}
 REFERENCE_STEP_INTERVALS = 16   # oracle intervals per step of --impl reference
 
 

@@ -377,6 +377,20 @@ int mg_cgemm_split_static(int device, void* stream, int batch, int d, const doub
  * action kernel of MG_FLAG_STATE_ACTION counts as one launch with 8 flops per
  * stored operator nonzero per operator application. */
 int mg_ctx_enable_gemm_timing(mg_ctx* ctx, int enable);
+/* Failure detection of the tensor-core product (MG_PREC_SPLIT).  Every wait of
+ * its kernel on an mbarrier is bounded: a CTA that gives up records
+ * MG_ETIMEOUT for the call and winds down without touching its outputs.  Only
+ * the waits whose abandonment is safe take `seconds` (0 <= seconds <= 4; the
+ * default is 4): the MMA issuer's wait for loaded operands and the loader's
+ * wait for a free stage.  The wait for the accumulators and the loader's final
+ * wait for its own copies keep the 4 s limit, so no CTA frees on-chip memory
+ * while a copy or tensor-core operation into it is in flight.  stall_test != 0
+ * (tests only) makes the MMA issuer of every product first wait on a barrier
+ * that nothing completes, so each product of the context ends in MG_ETIMEOUT
+ * after about `seconds`; the context stays usable, and calling again with
+ * stall_test = 0 restores normal products.  MG_EINVAL for seconds outside
+ * [0, 4]. */
+int mg_ctx_set_wait_limit(mg_ctx* ctx, double seconds, int stall_test);
 int mg_ctx_gemm_stats(mg_ctx* ctx, int64_t* launches, double* ms, double* flops, int reset);
 
 const char* mg_strerror(int code);

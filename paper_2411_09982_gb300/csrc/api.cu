@@ -119,6 +119,10 @@ struct mg_ctx {
   // in the pool (no release at synchronisation points, which would wait for every
   // kernel on the device) and are reused only without cross-stream waits
   cudaMemPool_t pool = nullptr;
+  // bounded device waits of the split product: the limit of the waits a CTA may
+  // abandon, and the stall test (mg_ctx_set_wait_limit)
+  unsigned long long wait_ns = 4000000000ull;
+  int stall_test = 0;
 };
 
 struct mg_plan {
@@ -387,8 +391,12 @@ struct Engine {
     int e0 = -1, e1 = -1;
     if (ctx->timing) MG_TRY(timing_begin(&e0));
     int r;
-    if (prec == MG_PREC_SPLIT)
-      r = split_gemm(d, L, batch, abuf, bbuf[slot], C, sC, add, ctx->status, ctx->stream);
+    if (prec == MG_PREC_SPLIT) {
+      SplitCtl ctl;
+      ctl.wait_ns = ctx->wait_ns;
+      ctl.stall = ctx->stall_test;
+      r = split_gemm(d, L, batch, abuf, bbuf[slot], C, sC, add, ctx->status, ctx->stream, ctl);
+    }
     else
       r = launch_cgemm_f64(batch, d, A, sA, 0, B, sB, C, sC, add, ctx->stream);
     if (r != MG_OK) return r;
@@ -1041,6 +1049,13 @@ int mg_ctx_gemm_stats(mg_ctx* ctx, int64_t* launches, double* ms, double* flops,
     ctx->t_ms = 0.0;
     ctx->t_flops = 0.0;
   }
+  return MG_OK;
+}
+
+int mg_ctx_set_wait_limit(mg_ctx* ctx, double seconds, int stall_test) {
+  if (!ctx || !(seconds >= 0.0) || seconds > 4.0) return MG_EINVAL;
+  ctx->wait_ns = (unsigned long long)(seconds * 1e9);
+  ctx->stall_test = stall_test ? 1 : 0;
   return MG_OK;
 }
 

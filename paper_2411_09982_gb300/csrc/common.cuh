@@ -133,10 +133,21 @@ size_t split_a_bytes(int d, int L, int batch);
 size_t split_b_bytes(int d, int L, int batch);
 // Inputs are FP64 (in_df32 = 0) or double-float (in_df32 = 1) complex matrices; the
 // product C and the addends are double-float (see df32.cuh).
-int split_slice_a(int d, int L, int batch, const double* A, long long sA, int in_df32, void* buf, cudaStream_t s);
-int split_slice_b(int d, int L, int batch, const double* B, long long sB, int in_df32, void* buf, cudaStream_t s);
+// Launch controls of the split product and its slicers.
+struct SplitCtl {
+  // limit of the waits a CTA may abandon (the MMA issuer's wait for a loaded stage,
+  // the producer's wait for a free one); the others keep the 4 s limit
+  unsigned long long wait_ns = 4000000000ull;
+  int stall = 0;                 // test only: the MMA issuer waits on a barrier nothing completes
+  const int* item_sq = nullptr;  // per-item squaring counts (device) or null: every item active
+  int sq_step = 0;               // with item_sq: only items with item_sq[b] > sq_step are computed
+};
+int split_slice_a(int d, int L, int batch, const double* A, long long sA, int in_df32, void* buf, cudaStream_t s,
+                  const SplitCtl& ctl = SplitCtl());
+int split_slice_b(int d, int L, int batch, const double* B, long long sB, int in_df32, void* buf, cudaStream_t s,
+                  const SplitCtl& ctl = SplitCtl());
 int split_gemm(int d, int L, int batch, const void* abuf, const void* bbuf, double* C, long long sC,
-               const AddTerms& add, int* status, cudaStream_t s);
+               const AddTerms& add, int* status, cudaStream_t s, const SplitCtl& ctl = SplitCtl());
 
 // State propagation; see propagate.cu.
 int launch_state_chain(int n_steps, int d, const double* U, long long sU, double* psi, double* tmp,

@@ -25,11 +25,13 @@
 // products of the exponential; everything else of the path stays FP64.
 //
 // Kernel structure (one 128 x 64-complex output tile per CTA, 320 threads):
-//   warp 0      TMA producer: per K-step of 16 one 4-D box of all L A-digit
-//               tiles (128 x 16 BF16 each) and one of all L B-digit tiles,
-//               SWIZZLE_64B (64-byte rows: half the TMA row requests of 32-byte
-//               rows, which capped operand delivery at ~58 GB/s per SM), into a
-//               STAGES-deep ring of shared-memory stages.
+//   warp 0      TMA producer: per K-step of 32 one 4-D box of all L A-digit
+//               tiles (128 x 32 BF16 each) and one 5-D box of all L B-digit tiles
+//               (two consecutive planes of 64 rows), SWIZZLE_64B (64-byte rows:
+//               half the TMA row requests of 32-byte rows, which capped operand
+//               delivery at ~58 GB/s per SM), into a STAGES-deep ring of
+//               shared-memory stages.  Every CTA loads its own operands from this
+//               GPU's memory; no load is shared between CTAs.
 //   warp 1      TMEM owner and MMA issuer: tcgen05.mma kind::f16 (BF16 in,
 //               FP32 accumulate), M = 128, N = 128 (64 real + 64 imaginary
 //               output columns), K = 16, two instructions per digit pair and
@@ -37,7 +39,12 @@
 //   warps 2..9  epilogue: tcgen05.ld of the four accumulators (two warps per TMEM
 //               lane quarter, 32 complex columns each), double-float combine.
 // Every mbarrier wait is bounded by a wall-clock deadline; a wait that gives up
-// records MG_DEV_TIMEOUT in the status word and the CTA winds down.
+// records MG_DEV_TIMEOUT in the status word and the CTA winds down.  Only the
+// waits whose abandonment is safe take the caller's (possibly short) limit: the
+// MMA issuer's wait for a loaded stage and the producer's wait for a free one.
+// The epilogue's wait for the accumulators and the producer's final drain of
+// its own copies always use the long limit, so no CTA releases TMEM or shared
+// memory while a tensor-core operation or a copy into it is still in flight.
 #include "common.cuh"
 #include "df32.cuh"
 
@@ -198,12 +205,13 @@ __device__ __forceinline__ uint2 neg4(uint2 w) { return make_uint2(w.x ^ 0x80008
 template <int L, typename T>
 __global__ void __launch_bounds__(256)
 slice_a_kernel(int d, int Kp, int Mp, int beta, const double* __restrict__ A, long long sA,
-               __nv_bfloat16* __restrict__ out, int* __restrict__ ea) {
+               __nv_bfloat16* __restrict__ out, int* __restrict__ ea, const int* __restrict__ item_sq, int sq_step) {
   using E_ = Elem<T>;
   const int lane = threadIdx.x & 31;
   const int row = blockIdx.x * 8 + (threadIdx.x >> 5);
   const int b = blockIdx.y;
   if (row >= Mp) return;
+  if (item_sq && item_sq[b] <= sq_step) return;   // inactive item: its digits are not read
   const int Kh = Kp / 2;
   const long long slice_stride = (long long)Mp * Kp;
   __nv_bfloat16* o = out + (long long)b * L * slice_stride + (long long)row * Kp;
@@ -255,10 +263,12 @@ slice_a_kernel(int d, int Kp, int Mp, int beta, const double* __restrict__ A, lo
 // eb must be preset below -2^28 (byte 0x80); blocks combine with atomicMax.
 template <typename T>
 __global__ void __launch_bounds__(256)
-col_exponent_kernel(int d, int Np, const double* __restrict__ B, long long sB, int* __restrict__ eb) {
+col_exponent_kernel(int d, int Np, const double* __restrict__ B, long long sB, int* __restrict__ eb,
+                    const int* __restrict__ item_sq, int sq_step) {
   using E_ = Elem<T>;
   __shared__ int red[4][SG_BNC];
   const int j0 = blockIdx.x * SG_BNC, k0 = blockIdx.y * 64, b = blockIdx.z;
+  if (item_sq && item_sq[b] <= sq_step) return;
   const int c = threadIdx.x & 63, g = threadIdx.x >> 6;
   const double* Bb = B + b * sB;
   int E = -(1 << 29);
@@ -283,12 +293,14 @@ constexpr int SB_KCHUNK = 32;
 template <int L, typename T>
 __global__ void __launch_bounds__(256)
 slice_b_kernel(int d, int Kp, int Np, int beta, const double* __restrict__ B, long long sB,
-               __nv_bfloat16* __restrict__ out, const int* __restrict__ eb) {
+               __nv_bfloat16* __restrict__ out, const int* __restrict__ eb, const int* __restrict__ item_sq,
+               int sq_step) {
   using E_ = Elem<T>;
   using V = typename E_::type;
   __shared__ V tile[SB_KCHUNK][SG_BNC + 1];
   __shared__ int shift[SG_BNC];
   const int t = blockIdx.x, b = blockIdx.z;
+  if (item_sq && item_sq[b] <= sq_step) return;
   const int j0 = t * SG_BNC, k0 = blockIdx.y * SB_KCHUNK;
   const int tid = threadIdx.x;
   const int Kh = Kp / 2, rows = Np / 2;
@@ -390,36 +402,6 @@ __device__ __forceinline__ void tma_load_5d(void* dst, const CUtensorMap* map, u
       "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(smem_u32(bar))
       : "memory");
 }
-__device__ __forceinline__ void tma_load_5d_mc(void* dst, const CUtensorMap* map, uint64_t* bar, int c0, int c1,
-                                               int c2, int c3, int c4, uint16_t mask) {
-  asm volatile(
-      "cp.async.bulk.tensor.5d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster"
-      " [%0], [%1, {%2, %3, %4, %5, %6}], [%7], %8;" ::"r"(smem_u32(dst)),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(smem_u32(bar)),
-      "h"(mask)
-      : "memory");
-}
-__device__ __forceinline__ void tma_load_4d_mc(void* dst, const CUtensorMap* map, uint64_t* bar, int c0, int c1,
-                                               int c2, int c3, uint16_t mask) {
-  asm volatile(
-      "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster"
-      " [%0], [%1, {%2, %3, %4, %5}], [%6], %7;" ::"r"(smem_u32(dst)),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar)), "h"(mask)
-      : "memory");
-}
-__device__ __forceinline__ uint32_t cluster_rank() {
-  uint32_t r;
-  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-  return r;
-}
-__device__ __forceinline__ void cluster_sync_all() {
-  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
-}
-__device__ __forceinline__ void tc_commit_mc(uint64_t* bar, uint16_t mask) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;"
-               ::"r"(smem_u32(bar)), "h"(mask)
-               : "memory");
-}
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
@@ -494,17 +476,16 @@ struct SplitEpi {
   df32 diag;
 };
 
-// CM = 1: one CTA per tile.  CM = 2: CTAs (mt = 2c, 2c + 1) of one cluster compute the
-// same 64 complex columns, so they share the B digit tile: each loads half of it (one
-// 64-row box per digit) and multicasts it to both, cutting L2 reads per tile by 25%.
-// A stage may then be refilled only when both CTAs' MMAs have released it.
-template <int L, int STAGES, int CM>
+// One CTA per 128 x 64-complex output tile of one batch item.  With ctl.item_sq set,
+// item b is computed only while ctl.item_sq[b] > ctl.sq_step (per-item squaring
+// counts: an item whose squarings are done keeps its matrix, which the product
+// would otherwise overwrite in place); the CTAs of an inactive item return at once.
+template <int L, int STAGES>
 __global__ void __launch_bounds__(SG_THREADS, 1)
 split_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                  const __grid_constant__ CUtensorMap tmBh,
                   int d, int Kp, int Mp, int Np, int beta, const int* __restrict__ ea,
                   const int* __restrict__ eb, double* __restrict__ C, long long sC, SplitEpi epi,
-                  int* __restrict__ status) {
+                  int* __restrict__ status, SplitCtl ctl) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   constexpr int STAGE_BYTES = 2 * L * SG_TILE_BYTES;
@@ -512,23 +493,25 @@ split_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + RING_BYTES);
   uint64_t* empty = full + STAGES;
   uint64_t* accfull = empty + STAGES;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accfull + 1);
+  uint64_t* never = accfull + 1;   // no thread ever arrives here (the stall test waits on it)
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(never + 1);
   int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
   int* eb_s = abort_flag + 1;   // column exponents of this tile's 64 columns
   int* epi_flag = eb_s + SG_BNC;  // epilogue verdict (accumulators ready and no abort)
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nt = blockIdx.x, mt = blockIdx.y, b = blockIdx.z;
+  if (ctl.item_sq && ctl.item_sq[b] <= ctl.sq_step) return;   // uniform over the CTA
   const int num_k = Kp / SG_BK;
   const int nkh = num_k / 2;   // K stages of the real half
 
-  const uint32_t crank = CM > 1 ? cluster_rank() : 0u;
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(&full[s], 1);
-      mbar_init(&empty[s], CM);   // released by the MMA warp of every CTA that writes the stage
+      mbar_init(&empty[s], 1);
     }
     mbar_init(accfull, 1);
+    mbar_init(never, 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -544,13 +527,12 @@ split_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   tc_fence_before();
-  if (CM > 1)
-    cluster_sync_all();   // barriers of both CTAs initialised before any multicast touches them
-  else
-    __syncthreads();
+  __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
-  const uint64_t deadline = global_ns() + SG_WAIT_NS;
+  const uint64_t t_start = global_ns();
+  const uint64_t deadline = t_start + SG_WAIT_NS;   // waits that must not be abandoned early
+  const uint64_t deadline_short = t_start + (ctl.wait_ns < SG_WAIT_NS ? ctl.wait_ns : SG_WAIT_NS);
 
   if (warp == 0) {
     if (lane == 0) {
@@ -559,7 +541,7 @@ split_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
       for (int kb = 0; kb < num_k; ++kb) {
         const int s = kb % STAGES;
         const uint32_t ph = (kb / STAGES) & 1;
-        if (!mbar_wait(&empty[s], ph ^ 1, deadline)) {
+        if (!mbar_wait(&empty[s], ph ^ 1, deadline_short)) {
           atomicExch(status, MG_DEV_TIMEOUT);
           *(volatile int*)abort_flag = 1;
           break;
@@ -572,15 +554,7 @@ split_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
         const bool imag = kb >= nkh;
         const int kbb = (imag ? kb - nkh : kb) * SG_BK;
         const int plane0 = imag ? 0 : 1;
-        if (CM == 1) {
-          tma_load_5d(st + L * SG_TILE_BYTES, &tmB, &full[s], kbb, nt * SG_BNC, plane0, 0, b);
-        } else {
-          // this CTA's plane (64 rows) of every digit tile, to both CTAs
-#pragma unroll
-          for (int sd = 0; sd < L; ++sd)
-            tma_load_5d_mc(st + L * SG_TILE_BYTES + sd * SG_TILE_BYTES + crank * (SG_TILE_BYTES / 2), &tmBh,
-                           &full[s], kbb, nt * SG_BNC, plane0 + (int)crank, sd, b, (uint16_t)((1u << CM) - 1u));
-        }
+        tma_load_5d(st + L * SG_TILE_BYTES, &tmB, &full[s], kbb, nt * SG_BNC, plane0, 0, b);
         issued = kb + 1;
       }
       // never leave the CTA with a bulk copy still in flight into its shared memory
@@ -592,10 +566,14 @@ split_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
     if (lane == 0) {
       // ---------------- MMA issuer ----------------
       bool ok = true;
+      if (ctl.stall && !mbar_wait(never, 0, deadline_short)) {
+        atomicExch(status, MG_DEV_TIMEOUT);
+        ok = false;
+      }
       for (int kb = 0; kb < num_k && ok; ++kb) {
         const int s = kb % STAGES;
         const uint32_t ph = (kb / STAGES) & 1;
-        if (!mbar_wait(&full[s], ph, deadline)) {
+        if (!mbar_wait(&full[s], ph, deadline_short)) {
           atomicExch(status, MG_DEV_TIMEOUT);
           ok = false;
           break;
@@ -618,10 +596,7 @@ split_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
             }
           }
         }
-        if (CM == 1)
-          tc_commit(&empty[s]);
-        else
-          tc_commit_mc(&empty[s], (uint16_t)((1u << CM) - 1u));
+        tc_commit(&empty[s]);
       }
       tc_commit(accfull);   // fires once every issued MMA has completed
       if (!ok) *(volatile int*)abort_flag = 1;
@@ -706,9 +681,6 @@ split_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
     tc_fence_before();
   }
   __syncthreads();
-  // no CTA of a cluster leaves while its partner may still multicast into it or
-  // release its stages
-  if (CM > 1) cluster_sync_all();
   if (warp == 1) {
     __syncwarp();
     tc_fence_after();
@@ -787,58 +759,36 @@ static constexpr int stages_for() {
 template <int L>
 static int launch_split_gemm_L(const SplitGeom& g, int batch, const __nv_bfloat16* Ad, const int* ea,
                                const __nv_bfloat16* Bd, const int* eb, double* C, long long sC,
-                               const SplitEpi& epi, int* status, cudaStream_t s) {
+                               const SplitEpi& epi, int* status, const SplitCtl& ctl, cudaStream_t s) {
   constexpr int STAGES = stages_for<L>();
-  CUtensorMap ma, mb, mbh;
+  CUtensorMap ma, mb;
   MG_TRY(make_digit_map(&ma, Ad, g.Kp, g.Mp, g.d, L, batch));
   MG_TRY(make_bplane_map(&mb, Bd, g.Kh(), g.Np / 2, g.d, L, batch, 2, L));
-  MG_TRY(make_bplane_map(&mbh, Bd, g.Kh(), g.Np / 2, g.d, L, batch, 1, 1));
   const size_t ring = std::max<size_t>((size_t)STAGES * 2 * L * SG_TILE_BYTES, (size_t)SG_EPI_BYTES);
   const size_t smem = ring + 1024 /*barriers, exponents*/ + 1024 /*align*/;
-  const int mtiles = g.Mp / SG_BM;
-  const int cm = mtiles >= 2 ? 2 : 1;
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(ceil_div(g.d, SG_BNC), ceil_div(mtiles, cm) * cm, batch);
-  cfg.blockDim = dim3(SG_THREADS, 1, 1);
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = s;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = 1;
-  attr[0].val.clusterDim.y = cm;
-  attr[0].val.clusterDim.z = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  cudaError_t e;
-  if (cm == 2) {
-    auto kern = split_gemm_kernel<L, STAGES, 2>;
-    MG_TRY(ensure_smem_limit(reinterpret_cast<const void*>(kern), (int)smem));
-    e = cudaLaunchKernelEx(&cfg, kern, ma, mb, mbh, g.d, g.Kp, g.Mp, g.Np, g.beta, ea, eb, C, sC, epi, status);
-  } else {
-    auto kern = split_gemm_kernel<L, STAGES, 1>;
-    MG_TRY(ensure_smem_limit(reinterpret_cast<const void*>(kern), (int)smem));
-    e = cudaLaunchKernelEx(&cfg, kern, ma, mb, mbh, g.d, g.Kp, g.Mp, g.Np, g.beta, ea, eb, C, sC, epi, status);
-  }
-  if (e != cudaSuccess) {
-    set_last_cuda_error(e, "cudaLaunchKernelEx(split_gemm_kernel)", __FILE__, __LINE__);
-    return MG_ECUDA;
-  }
+  auto kern = split_gemm_kernel<L, STAGES>;
+  MG_TRY(ensure_smem_limit(reinterpret_cast<const void*>(kern), (int)smem));
+  kern<<<dim3(ceil_div(g.d, SG_BNC), g.Mp / SG_BM, batch), SG_THREADS, smem, s>>>(
+      ma, mb, g.d, g.Kp, g.Mp, g.Np, g.beta, ea, eb, C, sC, epi, status, ctl);
   return check_launch("split_gemm_kernel");
 }
 
 template <int L, typename T>
 static int launch_slicers_LT(const SplitGeom& g, int batch, const double* A, long long sA, __nv_bfloat16* Ad,
-                             int* ea, const double* B, long long sB, __nv_bfloat16* Bd, int* eb, cudaStream_t s) {
+                             int* ea, const double* B, long long sB, __nv_bfloat16* Bd, int* eb, cudaStream_t s,
+                             const SplitCtl& ctl) {
   if (A) {
-    slice_a_kernel<L, T><<<dim3(g.Mp / 8, batch), 256, 0, s>>>(g.d, g.Kp, g.Mp, g.beta, A, sA, Ad, ea);
+    slice_a_kernel<L, T><<<dim3(g.Mp / 8, batch), 256, 0, s>>>(g.d, g.Kp, g.Mp, g.beta, A, sA, Ad, ea, ctl.item_sq,
+                                                                ctl.sq_step);
     MG_TRY(check_launch("slice_a_kernel"));
   }
   if (B) {
     MG_CUDA_TRY(cudaMemsetAsync(eb, 0x80, sizeof(int) * (size_t)(g.Np / 2) * batch, s));
-    col_exponent_kernel<T><<<dim3(ceil_div(g.d, SG_BNC), ceil_div(g.d, 64), batch), 256, 0, s>>>(g.d, g.Np, B, sB, eb);
+    col_exponent_kernel<T><<<dim3(ceil_div(g.d, SG_BNC), ceil_div(g.d, 64), batch), 256, 0, s>>>(
+        g.d, g.Np, B, sB, eb, ctl.item_sq, ctl.sq_step);
     MG_TRY(check_launch("col_exponent_kernel"));
     slice_b_kernel<L, T><<<dim3(ceil_div(g.d, SG_BNC), ceil_div(g.d, SB_KCHUNK), batch), 256, 0, s>>>(
-        g.d, g.Kp, g.Np, g.beta, B, sB, Bd, eb);
+        g.d, g.Kp, g.Np, g.beta, B, sB, Bd, eb, ctl.item_sq, ctl.sq_step);
     MG_TRY(check_launch("slice_b_kernel"));
   }
   return MG_OK;
@@ -847,22 +797,22 @@ static int launch_slicers_LT(const SplitGeom& g, int batch, const double* A, lon
 template <int L>
 static int launch_slicers_L(const SplitGeom& g, int batch, int in_df32, const double* A, long long sA,
                             __nv_bfloat16* Ad, int* ea, const double* B, long long sB, __nv_bfloat16* Bd, int* eb,
-                            cudaStream_t s) {
-  if (in_df32) return launch_slicers_LT<L, df32>(g, batch, A, sA, Ad, ea, B, sB, Bd, eb, s);
-  return launch_slicers_LT<L, double>(g, batch, A, sA, Ad, ea, B, sB, Bd, eb, s);
+                            cudaStream_t s, const SplitCtl& ctl) {
+  if (in_df32) return launch_slicers_LT<L, df32>(g, batch, A, sA, Ad, ea, B, sB, Bd, eb, s, ctl);
+  return launch_slicers_LT<L, double>(g, batch, A, sA, Ad, ea, B, sB, Bd, eb, s, ctl);
 }
 
 static int launch_slicers(const SplitGeom& g, int batch, int in_df32, const double* A, long long sA,
                           __nv_bfloat16* Ad, int* ea, const double* B, long long sB, __nv_bfloat16* Bd, int* eb,
-                          cudaStream_t s) {
+                          cudaStream_t s, const SplitCtl& ctl) {
   switch (g.L) {
-    case 2: return launch_slicers_L<2>(g, batch, in_df32, A, sA, Ad, ea, B, sB, Bd, eb, s);
-    case 3: return launch_slicers_L<3>(g, batch, in_df32, A, sA, Ad, ea, B, sB, Bd, eb, s);
-    case 4: return launch_slicers_L<4>(g, batch, in_df32, A, sA, Ad, ea, B, sB, Bd, eb, s);
-    case 5: return launch_slicers_L<5>(g, batch, in_df32, A, sA, Ad, ea, B, sB, Bd, eb, s);
-    case 6: return launch_slicers_L<6>(g, batch, in_df32, A, sA, Ad, ea, B, sB, Bd, eb, s);
-    case 7: return launch_slicers_L<7>(g, batch, in_df32, A, sA, Ad, ea, B, sB, Bd, eb, s);
-    case 8: return launch_slicers_L<8>(g, batch, in_df32, A, sA, Ad, ea, B, sB, Bd, eb, s);
+    case 2: return launch_slicers_L<2>(g, batch, in_df32, A, sA, Ad, ea, B, sB, Bd, eb, s, ctl);
+    case 3: return launch_slicers_L<3>(g, batch, in_df32, A, sA, Ad, ea, B, sB, Bd, eb, s, ctl);
+    case 4: return launch_slicers_L<4>(g, batch, in_df32, A, sA, Ad, ea, B, sB, Bd, eb, s, ctl);
+    case 5: return launch_slicers_L<5>(g, batch, in_df32, A, sA, Ad, ea, B, sB, Bd, eb, s, ctl);
+    case 6: return launch_slicers_L<6>(g, batch, in_df32, A, sA, Ad, ea, B, sB, Bd, eb, s, ctl);
+    case 7: return launch_slicers_L<7>(g, batch, in_df32, A, sA, Ad, ea, B, sB, Bd, eb, s, ctl);
+    case 8: return launch_slicers_L<8>(g, batch, in_df32, A, sA, Ad, ea, B, sB, Bd, eb, s, ctl);
   }
   return MG_EINVAL;
 }
@@ -879,23 +829,25 @@ size_t split_b_bytes(int d, int L, int batch) {
 }
 
 // A-side digits of a batch (FP64 or DF32 input): layout [digits | exponents] in one buffer.
-int split_slice_a(int d, int L, int batch, const double* A, long long sA, int in_df32, void* buf, cudaStream_t s) {
+int split_slice_a(int d, int L, int batch, const double* A, long long sA, int in_df32, void* buf, cudaStream_t s,
+                  const SplitCtl& ctl) {
   SplitGeom g = split_geom(d, L);
   __nv_bfloat16* Ad = reinterpret_cast<__nv_bfloat16*>(buf);
   int* ea = reinterpret_cast<int*>(Ad + g.a_item_elems() * batch);
-  return launch_slicers(g, batch, in_df32, A, sA, Ad, ea, nullptr, 0, nullptr, nullptr, s);
+  return launch_slicers(g, batch, in_df32, A, sA, Ad, ea, nullptr, 0, nullptr, nullptr, s, ctl);
 }
 
-int split_slice_b(int d, int L, int batch, const double* B, long long sB, int in_df32, void* buf, cudaStream_t s) {
+int split_slice_b(int d, int L, int batch, const double* B, long long sB, int in_df32, void* buf, cudaStream_t s,
+                  const SplitCtl& ctl) {
   SplitGeom g = split_geom(d, L);
   __nv_bfloat16* Bd = reinterpret_cast<__nv_bfloat16*>(buf);
   int* eb = reinterpret_cast<int*>(Bd + g.b_item_elems() * batch);
-  return launch_slicers(g, batch, in_df32, nullptr, 0, nullptr, nullptr, B, sB, Bd, eb, s);
+  return launch_slicers(g, batch, in_df32, nullptr, 0, nullptr, nullptr, B, sB, Bd, eb, s, ctl);
 }
 
 // C[b] = A[b] B[b] + addends (C and addends DF32), from digit buffers made by split_slice_a/b.
 int split_gemm(int d, int L, int batch, const void* abuf, const void* bbuf, double* C, long long sC,
-               const AddTerms& add, int* status, cudaStream_t s) {
+               const AddTerms& add, int* status, cudaStream_t s, const SplitCtl& ctl) {
   if (batch <= 0) return MG_OK;
   if (batch > 65535) return MG_EUNSUPPORTED;
   if (add.scale != 1.0) return MG_EINVAL;
@@ -910,13 +862,13 @@ int split_gemm(int d, int L, int batch, const void* abuf, const void* bbuf, doub
   e.add_stride = add.stride;
   e.diag = df_from_double(add.diag);
   switch (L) {
-    case 2: return launch_split_gemm_L<2>(g, batch, Ad, ea, Bd, eb, C, sC, e, status, s);
-    case 3: return launch_split_gemm_L<3>(g, batch, Ad, ea, Bd, eb, C, sC, e, status, s);
-    case 4: return launch_split_gemm_L<4>(g, batch, Ad, ea, Bd, eb, C, sC, e, status, s);
-    case 5: return launch_split_gemm_L<5>(g, batch, Ad, ea, Bd, eb, C, sC, e, status, s);
-    case 6: return launch_split_gemm_L<6>(g, batch, Ad, ea, Bd, eb, C, sC, e, status, s);
-    case 7: return launch_split_gemm_L<7>(g, batch, Ad, ea, Bd, eb, C, sC, e, status, s);
-    case 8: return launch_split_gemm_L<8>(g, batch, Ad, ea, Bd, eb, C, sC, e, status, s);
+    case 2: return launch_split_gemm_L<2>(g, batch, Ad, ea, Bd, eb, C, sC, e, status, ctl, s);
+    case 3: return launch_split_gemm_L<3>(g, batch, Ad, ea, Bd, eb, C, sC, e, status, ctl, s);
+    case 4: return launch_split_gemm_L<4>(g, batch, Ad, ea, Bd, eb, C, sC, e, status, ctl, s);
+    case 5: return launch_split_gemm_L<5>(g, batch, Ad, ea, Bd, eb, C, sC, e, status, ctl, s);
+    case 6: return launch_split_gemm_L<6>(g, batch, Ad, ea, Bd, eb, C, sC, e, status, ctl, s);
+    case 7: return launch_split_gemm_L<7>(g, batch, Ad, ea, Bd, eb, C, sC, e, status, ctl, s);
+    case 8: return launch_split_gemm_L<8>(g, batch, Ad, ea, Bd, eb, C, sC, e, status, ctl, s);
   }
   return MG_EINVAL;
 }
@@ -938,7 +890,10 @@ static void* g_static_addr[128];
 
 static int static_scratch_address(int device, void** out) {
   std::lock_guard<std::mutex> lock(g_static_mu);
-  if (device < 0 || device >= 128) return MG_EINVAL;
+  if (device < 0 || device >= 128) {
+    set_last_message("mg_cgemm_split_static: device %d is outside 0..127", device);
+    return MG_EINVAL;
+  }
   if (!g_static_addr[device]) {
     int prev = 0;
     MG_CUDA_TRY(cudaGetDevice(&prev));
@@ -997,13 +952,29 @@ extern "C" int mg_cgemm_split_static(int device, void* stream, int batch, int d,
   int st = 0;
   // the status word is the only scratch that must start at zero; the digit
   // buffers (padding included) and the product are fully rewritten
-  if (cudaMemsetAsync(status, 0, sizeof(int), s) != cudaSuccess) r = MG_ECUDA;
+  const cudaError_t me = cudaMemsetAsync(status, 0, sizeof(int), s);
+  if (me != cudaSuccess) {
+    set_last_cuda_error(me, "cudaMemsetAsync(status word)", __FILE__, __LINE__);
+    r = MG_ECUDA;
+  }
   if (r == MG_OK) r = split_slice_a(d, slices, batch, A, md, 0, abuf, s);
   if (r == MG_OK) r = split_slice_b(d, slices, batch, B, md, 0, bbuf, s);
   if (r == MG_OK) r = split_gemm(d, slices, batch, abuf, bbuf, prod, md, none, status, s);
   if (r == MG_OK) r = launch_df_to_fp64(batch, d, prod, md, C, md, s);
-  if (r == MG_OK && cudaMemcpyAsync(&st, status, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess) r = MG_ECUDA;
-  if (r == MG_OK && cudaStreamSynchronize(s) != cudaSuccess) r = MG_ECUDA;
+  if (r == MG_OK) {
+    const cudaError_t ce = cudaMemcpyAsync(&st, status, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (ce != cudaSuccess) {
+      set_last_cuda_error(ce, "cudaMemcpyAsync(status word)", __FILE__, __LINE__);
+      r = MG_ECUDA;
+    }
+  }
+  if (r == MG_OK) {
+    const cudaError_t se = cudaStreamSynchronize(s);
+    if (se != cudaSuccess) {
+      set_last_cuda_error(se, "cudaStreamSynchronize", __FILE__, __LINE__);
+      r = MG_ECUDA;
+    }
+  }
   if (r == MG_OK && st == MG_DEV_TIMEOUT) {
     set_last_message("mg_cgemm_split_static: a bounded device-side wait gave up");
     r = MG_ETIMEOUT;

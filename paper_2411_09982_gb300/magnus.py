@@ -102,6 +102,7 @@ SIGNATURES = {
     "mg_cgemm": (_I, [_P, _I, _I, _P, _P, _P, _I, _I]),
     "mg_propagate": (_I, [_P, _I, _I, _P, _I, _P, _P, _I, _I, _I]),
     "mg_ctx_enable_gemm_timing": (_I, [_P, _I]),
+    "mg_ctx_set_wait_limit": (_I, [_P, _D, _I]),
     "mg_ctx_gemm_stats": (_I, [_P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(_D), ctypes.POINTER(_D), _I]),
     "mg_cgemm_split_static": (_I, [_I, _P, _I, _I, _P, _P, _P, _I]),
     "mg_server_create": (_I, [_P, ctypes.c_size_t, _I, ctypes.POINTER(_P)]),
@@ -173,6 +174,9 @@ class Context:
 
     def enable_gemm_timing(self, on=True):
         _check(load().mg_ctx_enable_gemm_timing(self.h, 1 if on else 0), "mg_ctx_enable_gemm_timing")
+
+    def set_wait_limit(self, seconds=4.0, stall_test=False):
+        _check(load().mg_ctx_set_wait_limit(self.h, float(seconds), 1 if stall_test else 0), "mg_ctx_set_wait_limit")
 
     def gemm_stats(self, reset=True):
         n = ctypes.c_int64()
