@@ -307,12 +307,19 @@ def test_evolve_host_pointers_match_device(ctx):
 # ----------------------------------------------------------------------------
 # many uneven jobs in shared launches (mg_evolve_batch)
 # ----------------------------------------------------------------------------
-def _norm_scaled_tol(wl, base):
-    """Rounding grows with the phase of the exponent: these random jobs have |Hbar_n|
-    up to ~1e4 rad (few long intervals); the named workloads ~20."""
+def _ref_and_tol(wl, prec):
+    """The oracle's result and the bound a GPU result must meet.
+
+    Split mode: the stated 1e-6, flat.  FP64 mode: the stated 1e-11, or, for the random
+    jobs with very long intervals (|Hbar_n|_1 up to ~1e4 rad), 4 u |Hbar|_1 N (u = 2^-53)
+    if that is larger -- the rounding scale of any FP64 evolution of these jobs: the oracle
+    itself and its evolution through scipy's expm differ by up to that bound
+    (test_oracle_self_consistency_on_high_norm_instances)."""
     ref, parts = oracle.evolve_workload(wl, return_parts=True)
+    if prec == M.MG_PREC_SPLIT:
+        return ref, 1e-6
     hmax = max(np.abs(h).sum(axis=0).max() for h in parts["Hbar"])
-    return ref, base * max(1.0, hmax / 25.0)
+    return ref, max(1e-11, 4 * 2.0 ** -53 * hmax * wl.N)
 
 
 def _small_jobs(seed=21, n=10):
@@ -353,9 +360,9 @@ def test_evolve_batch_matches_oracle_per_job(ctx, prec, L, tol, reorth):
         torch.cuda.synchronize()
         assert status == [0] * len(jobs)
         for wl, o in zip(jobs, outs):
-            ref, t = _norm_scaled_tol(wl, tol)
+            ref, t = _ref_and_tol(wl, prec)
             err = np.abs(o.cpu().numpy() - ref).max()
-            assert err <= t, (wl.name, wl.d, wl.N, err)
+            assert err <= t, (wl.name, wl.d, wl.N, err, t)
     finally:
         for p in plans:
             p.close()
@@ -405,7 +412,7 @@ def test_evolve_batch_nonfinite_job_fails_alone(ctx):
         if i == 1:
             continue
         assert status[i] == 0
-        ref, t = _norm_scaled_tol(wl, 1e-11)
+        ref, t = _ref_and_tol(wl, M.MG_PREC_FP64)
         assert np.abs(o.cpu().numpy() - ref).max() <= t
     for p in plans:
         p.close()
@@ -505,8 +512,9 @@ def test_action_state_path_in_batch(ctx):
         torch.cuda.synchronize()
         assert status == [0] * len(jobs)
         for wl, o in zip(jobs, outs):
-            ref, t = _norm_scaled_tol(wl, 1e-11)
-            assert np.abs(o.cpu().numpy() - ref).max() <= t, wl.name
+            ref, t = _ref_and_tol(wl, M.MG_PREC_FP64)
+            err = np.abs(o.cpu().numpy() - ref).max()
+            assert err <= t, (wl.name, err, t)
     finally:
         for p in plans:
             p.close()
