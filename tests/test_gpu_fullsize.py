@@ -68,3 +68,71 @@ def test_alltoall_d4096_first_intervals(ctx, prec, L, tol):
     wl = W.config(3)
     U, rep = M.evolve_workload(ctx, wl, prec, L, N=g["workload"]["intervals_applied"])
     check(U.cpu().numpy(), g, tol)
+
+
+GOLDEN_4096_130 = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
+                               "alltoall_d4096_N500_first130_propagator.json")
+
+
+def test_alltoall_d4096_130_intervals_split_with_reorth(ctx):
+    """The d = 4096 workload's first 130 intervals in split precision with FP64
+    re-orthonormalisation every 64 intervals (two re-orthonormalisation boundaries; the
+    tree product spans several levels and, with a small workspace, several chunks) against
+    the oracle's sampled entries."""
+    with open(GOLDEN_4096_130) as f:
+        g = json.load(f)
+    n = g["workload"]["intervals_applied"]
+    assert n >= 130
+    wl = W.config(3)
+    for ws in (None, 3 << 30):
+        c = M.Context(0, workspace_limit=ws) if ws else ctx
+        U, rep = M.evolve_workload(c, wl, M.MG_PREC_SPLIT, 6, N=n, reorth_every=64)
+        err = check(U.cpu().numpy(), g, 1e-6)
+        assert rep["unitarity_defect"] < 1e-6, rep["unitarity_defect"]
+        if ws:
+            c.close()
+
+
+GOLDEN_UNEVEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
+                             "uneven_batch512_every32nd_state.json")
+
+
+def _uneven_batch_run(ctx, prec, flags):
+    jobs = W.uneven_batch()
+    plans, kinds, ins, outs = [], [], [], []
+    for wl in jobs:
+        sn, w = M.node_samples(wl)
+        p = M.Plan(ctx, torch.from_numpy(wl.H0).cuda(), torch.from_numpy(wl.Hk).cuda(), prec, 6, flags)
+        p.set_controls(wl.N, wl.P, wl.t0, wl.dt, w, torch.from_numpy(sn).cuda())
+        plans.append(p)
+        kinds.append(M.MG_OUT_STATE)
+        ins.append(torch.from_numpy(wl.psi0).cuda())
+        outs.append(torch.empty(wl.d, dtype=torch.complex128, device="cuda"))
+    try:
+        status = M.mg_evolve_batch(ctx, plans, kinds, ins, outs)
+        torch.cuda.synchronize()
+    finally:
+        for p in plans:
+            p.close()
+    return jobs, status, outs
+
+
+@pytest.mark.parametrize("prec,flags,tol", [(M.MG_PREC_SPLIT, 0, 1e-6),
+                                            (M.MG_PREC_FP64, M.MG_FLAG_STATE_ACTION, 1e-11)])
+def test_uneven_batch_512_all_in_one_call(ctx, prec, flags, tol):
+    """All 512 uneven instances (d 16..256, N 200..2000) in one mg_evolve_batch call;
+    every 32nd instance against the oracle's psi(T).  Split products: the stated 1e-6;
+    the action path (FP64): the stated 1e-11."""
+    with open(GOLDEN_UNEVEN) as f:
+        g = json.load(f)
+    jobs, status, outs = _uneven_batch_run(ctx, prec, flags)
+    assert status == [0] * len(jobs)
+    worst = 0.0
+    for rec in g["jobs"]:
+        q = rec["index"]
+        assert (jobs[q].d, jobs[q].N) == (rec["d"], rec["N"])
+        ref = np.array([complex(a, b) for a, b in rec["psi"]])
+        err = float(np.abs(outs[q].cpu().numpy() - ref).max())
+        worst = max(worst, err)
+        assert err <= tol, (q, rec["d"], rec["N"], err)
+    print(f"uneven batch, worst error over {len(g['jobs'])} instances: {worst:.3e}")
