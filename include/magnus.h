@@ -223,7 +223,8 @@ int mg_evolve(mg_plan* plan, int output, const double* in, double* out, int reor
  * dimension and length together: jobs are grouped by precision mode and by
  * dimension rounded up to a multiple of 16 (zero padding is exact: the padded
  * block of exp(-i Hbar) is the identity), and within a group all intervals of
- * all jobs share one batched launch per step of the exponential.  Propagator
+ * all jobs share one batched launch per step of the exponential, each interval
+ * with its own squaring count (see mg_batch_graph_create).  Propagator
  * jobs fold each chunk by a tree product; state jobs of d <= 256 (without
  * renormalisation) reduce each chunk by a segmented tree shared by all jobs and
  * then advance in one multi-job launch, larger ones by matrix-vector steps.
@@ -237,6 +238,40 @@ int mg_evolve(mg_plan* plan, int output, const double* in, double* out, int reor
  * flags: MG_FLAG_HOST_PTRS when every in[i]/out[i] is host memory. */
 int mg_evolve_batch(mg_ctx* ctx, int n, mg_plan* const* plans, const int* outputs, const double* const* in,
                     double* const* out, int reorth_every, int flags, int* job_status);
+
+/* ---- a batch captured once, replayed many times ------------------------------ */
+/* mg_evolve_batch issues every launch of a batch without reading anything back to
+ * the host between them: the Taylor degree m and the number S of squaring
+ * launches come from a bound on every interval's ||Hbar_n - tau_n I||_1 (the
+ * operators' norms times the largest coefficients, formed when the batch is
+ * planned), while each interval's own squaring count s_n (Sec. "Magnus
+ * Expansion": U_n = exp(-i Hbar_n) by scaling and squaring) and the failure of a
+ * job with a non-finite norm are decided on the device; each squaring launch
+ * multiplies only the intervals whose s_n exceeds it.
+ * mg_batch_graph_create plans such a batch and captures all of its launches
+ * (every chunk of every group: Hbar_n, exponentials, tree products, state
+ * chains, output copies) in one CUDA graph; mg_batch_graph_launch replays it
+ * with one graph launch.  Arguments are those of mg_evolve_batch with device
+ * pointers only; the input and output buffers and the plans' coefficient
+ * buffers are bound into the graph, so a replay evolves whatever they hold at
+ * launch time: call mg_set_controls with the same N, P and dt (new drive
+ * samples) and/or rewrite in[i] between launches.  The context's stream must
+ * not be the legacy default stream (it cannot be captured); the graph has a
+ * workspace of its own.  Action-flagged state jobs (MG_FLAG_STATE_ACTION) are
+ * rejected with MG_EUNSUPPORTED.  Creation runs the batch once uncaptured (which
+ * sizes the workspace), so it costs one evolution.
+ * mg_batch_graph_launch synchronises the context's stream; job_status (HOST,
+ * may be NULL) is filled as by mg_evolve_batch.  It returns MG_EINVAL when a
+ * plan's N, dt or coefficient buffer changed since the capture, and
+ * MG_EUNSUPPORTED when new controls made an interval's norm exceed the bound
+ * the squaring launches were planned for (recreate the graph).
+ * mg_batch_graph_stats gives the graph's kernel nodes and all nodes. */
+typedef struct mg_batch_graph mg_batch_graph;
+int mg_batch_graph_create(mg_ctx* ctx, int n, mg_plan* const* plans, const int* outputs, const double* const* in,
+                          double* const* out, int reorth_every, mg_batch_graph** graph);
+int mg_batch_graph_launch(mg_batch_graph* graph, int* job_status);
+int mg_batch_graph_stats(mg_batch_graph* graph, int64_t* kernel_nodes, int64_t* nodes);
+int mg_batch_graph_destroy(mg_batch_graph* graph);
 
 /* ---- serving ---------------------------------------------------------------- */
 /* A request loop over one context: mg_submit admits a job if its device memory

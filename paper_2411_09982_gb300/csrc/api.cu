@@ -23,6 +23,7 @@
 #include <condition_variable>
 #include <deque>
 #include <map>
+#include <memory>
 #include <tuple>
 #include <mutex>
 #include <thread>
@@ -123,6 +124,8 @@ struct mg_ctx {
   // abandon, and the stall test (mg_ctx_set_wait_limit)
   unsigned long long wait_ns = 4000000000ull;
   int stall_test = 0;
+  // algorithmic work of predicated squaring launches, added on the device (timing on)
+  double* dev_flops = nullptr;
 };
 
 struct mg_plan {
@@ -149,6 +152,10 @@ struct mg_plan {
   long long csr_nnz = 0;
   std::vector<int> csr_rowptr_h;  // host copies of the pattern (cluster partitioning, send masks)
   std::vector<int> csr_col_h;
+  // ||H - tau I||_1 of H0 and the Kx operators padded to dimension opnorm_dp (bounds of
+  // the exponents' norms in the batched path), once formed
+  std::vector<double> opnorm;
+  int opnorm_dp = 0;
 };
 
 namespace {
@@ -333,6 +340,18 @@ struct Engine {
   void* abuf = nullptr;
   void* bbuf[2] = {nullptr, nullptr};
   long long products = 0;
+  // split products: with item_sq set, only items with item_sq[b] > sq_step are sliced and
+  // multiplied (per-interval squaring counts; see expm_chunk_dev)
+  const int* item_sq = nullptr;
+  int sq_step = 0;
+  SplitCtl ctl() const {
+    SplitCtl c;
+    c.wait_ns = ctx->wait_ns;
+    c.stall = ctx->stall_test;
+    c.item_sq = item_sq;
+    c.sq_step = sq_step;
+    return c;
+  }
 
   int reserve(int batch) {
     if (prec != MG_PREC_SPLIT) return MG_OK;
@@ -346,11 +365,11 @@ struct Engine {
   bool df() const { return prec == MG_PREC_SPLIT; }
   int prepA(int batch, const double* A, long long sA, int in_df) {
     if (prec != MG_PREC_SPLIT) return MG_OK;
-    return split_slice_a(d, L, batch, A, sA, in_df, abuf, ctx->stream);
+    return split_slice_a(d, L, batch, A, sA, in_df, abuf, ctx->stream, ctl());
   }
   int prepB(int slot, int batch, const double* B, long long sB, int in_df) {
     if (prec != MG_PREC_SPLIT) return MG_OK;
-    return split_slice_b(d, L, batch, B, sB, in_df, bbuf[slot], ctx->stream);
+    return split_slice_b(d, L, batch, B, sB, in_df, bbuf[slot], ctx->stream, ctl());
   }
   int prepA(int batch, const double* A, long long sA) { return prepA(batch, A, sA, df() ? 1 : 0); }
   int prepB(int slot, int batch, const double* B, long long sB) { return prepB(slot, batch, B, sB, df() ? 1 : 0); }
@@ -371,10 +390,10 @@ struct Engine {
     return df() ? launch_apply_phase_df(batch, d, tau, src, dst, ctx->stream)
                 : launch_apply_phase(batch, d, (long long)d * d, tau, src, dst, ctx->stream);
   }
-  // X = -i 2^{-sq} W (W FP64, X in engine storage; may alias)
-  int scale_x(int batch, const double* W, double* X, int sq) {
-    return df() ? launch_scale_minus_i_df(batch, d, W, X, sq, ctx->stream)
-                : launch_scale_minus_i(batch, d, W, X, nullptr, sq, ctx->stream);
+  // X = -i 2^{-sq} W (W FP64, X in engine storage; may alias); sq_dev: per-item counts
+  int scale_x(int batch, const double* W, double* X, int sq, const int* sq_dev = nullptr) {
+    return df() ? launch_scale_minus_i_df(batch, d, W, X, sq, ctx->stream, sq_dev)
+                : launch_scale_minus_i(batch, d, W, X, sq_dev, sq, ctx->stream);
   }
   int to_fp64(int batch, const double* src, long long ss, double* dst, long long ds) {
     return df() ? launch_df_to_fp64(batch, d, src, ss, dst, ds, ctx->stream)
@@ -392,19 +411,21 @@ struct Engine {
     if (ctx->timing) MG_TRY(timing_begin(&e0));
     int r;
     if (prec == MG_PREC_SPLIT) {
-      SplitCtl ctl;
-      ctl.wait_ns = ctx->wait_ns;
-      ctl.stall = ctx->stall_test;
-      r = split_gemm(d, L, batch, abuf, bbuf[slot], C, sC, add, ctx->status, ctx->stream, ctl);
+      r = split_gemm(d, L, batch, abuf, bbuf[slot], C, sC, add, ctx->status, ctx->stream, ctl());
+    } else {
+      AddTerms a = add;
+      a.item_sq = item_sq;
+      a.sq_step = sq_step;
+      r = launch_cgemm_f64(batch, d, A, sA, 0, B, sB, C, sC, a, ctx->stream);
     }
-    else
-      r = launch_cgemm_f64(batch, d, A, sA, 0, B, sB, C, sC, add, ctx->stream);
     if (r != MG_OK) return r;
     if (ctx->timing) {
       MG_TRY(timing_begin(&e1));
       ctx->ev_pending.emplace_back(e0, e1);
       ctx->t_launches += 1;
-      ctx->t_flops += 8.0 * (double)d * d * d * batch;
+      // predicated launches (per-item squarings): the device adds the work of the
+      // active items to the context's device counter instead
+      if (!item_sq) ctx->t_flops += 8.0 * (double)d * d * d * batch;
     }
     return MG_OK;
   }
@@ -422,43 +443,14 @@ struct ExpmStats {
   double max_norm = 0.0;
 };
 
-int expm_chunk(mg_ctx* ctx, Engine& eng, int batch, double* W, const double* tau, const double* norm1_dev,
-               double* U, long long sU, ExpmStats* st, const std::vector<double>* host_norms = nullptr) {
-  PhaseRange range("expm");
+// Taylor polynomial T_m(X) of a batch (degree tc.m; p = 0: the five-product degree-18
+// scheme, else Paterson-Stockmeyer with block size p).  X = W (engine storage) is
+// overwritten where the scheme reuses it.  *R receives the result, *Rn the other
+// Horner buffer (free for the squarings).
+int taylor_poly(mg_ctx* ctx, Engine& eng, int batch, double* W, const TaylorChoice& tc, double** R_out,
+                double** Rn_out) {
   const int d = eng.d;
   const long long md = mat_doubles(d);
-  cudaStream_t s = ctx->stream;
-
-  // FP64 norms -> host: squaring count per interval and for the batch
-  std::vector<double> nrm(batch);
-  if (host_norms) {
-    nrm = *host_norms;
-  } else {
-    MG_CUDA_TRY(cudaMemcpyAsync(nrm.data(), norm1_dev, sizeof(double) * batch, cudaMemcpyDeviceToHost, s));
-    MG_CUDA_TRY(cudaStreamSynchronize(s));
-  }
-  double nmax = 0.0;
-  for (int b = 0; b < batch; ++b) {
-    if (!std::isfinite(nrm[b])) {
-      set_last_message("non-finite norm of the Magnus exponent in item %d of the batch", b);
-      return MG_ENONFINITE;
-    }
-    nmax = std::max(nmax, nrm[b]);
-  }
-  const double u = unit_roundoff(eng.prec, eng.L, d);
-  TaylorChoice tc = choose_taylor(nmax, u, eng.prec == MG_PREC_SPLIT);
-  if (st) {
-    st->m = tc.m;
-    st->s_applied = tc.s;
-    st->max_norm = std::max(st->max_norm, nmax);
-    for (int b = 0; b < batch; ++b) {
-      int sb = 0;
-      while (nrm[b] * std::ldexp(1.0, -sb) > tc.theta) ++sb;
-      st->s_min = std::min(st->s_min, sb);
-      st->s_max = std::max(st->s_max, sb);
-    }
-  }
-
   double *P2, *P3, *Y, *R0, *R1;
   MG_TRY(ws(ctx, WS_P2, md * batch, &P2));
   MG_TRY(ws(ctx, WS_P3, md * batch, &P3));
@@ -466,9 +458,6 @@ int expm_chunk(mg_ctx* ctx, Engine& eng, int batch, double* W, const double* tau
   MG_TRY(ws(ctx, WS_R0, md * batch, &R0));
   MG_TRY(ws(ctx, WS_R1, md * batch, &R1));
   MG_TRY(eng.reserve(batch));
-
-  // X = -i 2^{-s} W   (in place, into the engine's storage format)
-  MG_TRY(eng.scale_x(batch, W, W, tc.s));
   const double* X = W;
 
   double* R = R0;
@@ -563,6 +552,52 @@ int expm_chunk(mg_ctx* ctx, Engine& eng, int batch, double* W, const double* tau
     std::swap(R, Rn);
   }
   }
+  *R_out = R;
+  *Rn_out = Rn;
+  return MG_OK;
+}
+
+int expm_chunk(mg_ctx* ctx, Engine& eng, int batch, double* W, const double* tau, const double* norm1_dev,
+               double* U, long long sU, ExpmStats* st, const std::vector<double>* host_norms = nullptr) {
+  PhaseRange range("expm");
+  const int d = eng.d;
+  const long long md = mat_doubles(d);
+  cudaStream_t s = ctx->stream;
+
+  // FP64 norms -> host: squaring count per interval and for the batch
+  std::vector<double> nrm(batch);
+  if (host_norms) {
+    nrm = *host_norms;
+  } else {
+    MG_CUDA_TRY(cudaMemcpyAsync(nrm.data(), norm1_dev, sizeof(double) * batch, cudaMemcpyDeviceToHost, s));
+    MG_CUDA_TRY(cudaStreamSynchronize(s));
+  }
+  double nmax = 0.0;
+  for (int b = 0; b < batch; ++b) {
+    if (!std::isfinite(nrm[b])) {
+      set_last_message("non-finite norm of the Magnus exponent in item %d of the batch", b);
+      return MG_ENONFINITE;
+    }
+    nmax = std::max(nmax, nrm[b]);
+  }
+  const double u = unit_roundoff(eng.prec, eng.L, d);
+  TaylorChoice tc = choose_taylor(nmax, u, eng.prec == MG_PREC_SPLIT);
+  if (st) {
+    st->m = tc.m;
+    st->s_applied = tc.s;
+    st->max_norm = std::max(st->max_norm, nmax);
+    for (int b = 0; b < batch; ++b) {
+      int sb = 0;
+      while (nrm[b] * std::ldexp(1.0, -sb) > tc.theta) ++sb;
+      st->s_min = std::min(st->s_min, sb);
+      st->s_max = std::max(st->s_max, sb);
+    }
+  }
+
+  // X = -i 2^{-s} W   (in place, into the engine's storage format)
+  MG_TRY(eng.scale_x(batch, W, W, tc.s));
+  double *R, *Rn;
+  MG_TRY(taylor_poly(ctx, eng, batch, W, tc, &R, &Rn));
   // squarings
   for (int k = 0; k < tc.s; ++k) {
     MG_TRY(eng.prepA(batch, R, md));
@@ -575,6 +610,46 @@ int expm_chunk(mg_ctx* ctx, Engine& eng, int batch, double* W, const double* tau
   if (sU != md) return MG_EINVAL;
   if (tau) return eng.phase(batch, tau, R, U);
   return launch_copy_strided(batch, md, R, md, U, sU, s);
+}
+
+// The exponential of a chunk with every decision already on the device: degree tc
+// (chosen from a bound on the batch's norms), per-interval squaring counts sq_dev
+// (squarings_kernel), and S squaring launches, each of which squares only the items
+// whose count exceeds the launch index.  Split products square in place (the product
+// reads only the digit copies of its operands, so C may alias them); the FP64 product
+// reads its operands directly, so it squares into the other buffer and the active
+// items are copied back.
+int expm_chunk_dev(mg_ctx* ctx, Engine& eng, int batch, double* W, const double* tau, const int* sq_dev,
+                   const TaylorChoice& tc, int S, double* U) {
+  PhaseRange range("expm");
+  const long long md = mat_doubles(eng.d);
+  MG_TRY(eng.scale_x(batch, W, W, 0, sq_dev));
+  double *R, *Rn;
+  MG_TRY(taylor_poly(ctx, eng, batch, W, tc, &R, &Rn));
+  AddTerms none;
+  if (eng.df()) {
+    for (int k = 0; k < S; ++k) {
+      eng.item_sq = sq_dev;
+      eng.sq_step = k;
+      int r = eng.prepA(batch, R, md);
+      if (r == MG_OK) r = eng.prepB(0, batch, R, md);
+      if (r == MG_OK) r = eng.mul(batch, R, md, 0, R, md, R, md, none);
+      eng.item_sq = nullptr;
+      eng.sq_step = 0;
+      MG_TRY(r);
+    }
+  } else {
+    for (int k = 0; k < S; ++k) {
+      eng.item_sq = sq_dev;
+      eng.sq_step = k;
+      int r = eng.mul(batch, R, md, 0, R, md, Rn, md, none);
+      if (r == MG_OK) r = launch_copy_active(batch, md, Rn, R, sq_dev, k, ctx->stream);
+      eng.item_sq = nullptr;
+      eng.sq_step = 0;
+      MG_TRY(r);
+    }
+  }
+  return eng.phase(batch, tau, R, U);
 }
 
 // One Newton-Schulz polar step in FP64 on a batch: Z <- Z (3I - Z^dag Z)/2.
@@ -1003,6 +1078,13 @@ int mg_ctx_create(mg_ctx** out, int device, void* stream) {
     return MG_ENOMEM;
   }
   cudaMemset(c->status, 0, sizeof(int));
+  if (cudaMalloc(&c->dev_flops, sizeof(double)) != cudaSuccess) {
+    cudaFree(c->status);
+    cudaMemPoolDestroy(c->pool);
+    delete c;
+    return MG_ENOMEM;
+  }
+  cudaMemset(c->dev_flops, 0, sizeof(double));
   cudaEventCreate(&c->ev0);
   cudaEventCreate(&c->ev1);
   *out = c;
@@ -1017,6 +1099,7 @@ int mg_ctx_destroy(mg_ctx* ctx) {
     if (p) cudaFree(p);
   if (ctx->small) cudaFree(ctx->small);
   if (ctx->status) cudaFree(ctx->status);
+  if (ctx->dev_flops) cudaFree(ctx->dev_flops);
   if (ctx->ev0) cudaEventDestroy(ctx->ev0);
   if (ctx->ev1) cudaEventDestroy(ctx->ev1);
   for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
@@ -1041,13 +1124,16 @@ int mg_ctx_gemm_stats(mg_ctx* ctx, int64_t* launches, double* ms, double* flops,
   }
   ctx->ev_pending.clear();
   ctx->ev_next = 0;
+  double dflops = 0.0;   // work of the predicated (per-item) squaring launches
+  MG_CUDA_TRY(cudaMemcpy(&dflops, ctx->dev_flops, sizeof(double), cudaMemcpyDeviceToHost));
   if (launches) *launches = ctx->t_launches;
   if (ms) *ms = ctx->t_ms;
-  if (flops) *flops = ctx->t_flops;
+  if (flops) *flops = ctx->t_flops + dflops;
   if (reset) {
     ctx->t_launches = 0;
     ctx->t_ms = 0.0;
     ctx->t_flops = 0.0;
+    MG_CUDA_TRY(cudaMemset(ctx->dev_flops, 0, sizeof(double)));
   }
   return MG_OK;
 }
@@ -1837,80 +1923,447 @@ int init_job_state(mg_ctx* ctx, Engine& eng, BatchJob& j, const double* in, cuda
   return MG_OK;
 }
 
-// Run all jobs of one (precision, digits, padded dimension) group.
-int run_group(mg_ctx* ctx, std::vector<BatchJob>& jobs, std::vector<mg_plan*>& plans, int dp, int prec, int L,
-              const double* const* in, double* const* out, int reorth_every, int flags, int* job_status) {
-  cudaStream_t s = ctx->stream;
-  Engine eng{ctx, dp, prec, L};
-  const long long md = mat_doubles(dp);
-  const cudaMemcpyKind h2d = (flags & MG_FLAG_HOST_PTRS) ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
-  const cudaMemcpyKind d2h = (flags & MG_FLAG_HOST_PTRS) ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+// ---------------------------------------------------------------------------
+// device-driven batch programs: a group's whole evolution issued without host
+// synchronisation (and so capturable in one CUDA graph)
+// ---------------------------------------------------------------------------
+// Everything the host needs to issue a group's launches follows from the jobs'
+// dimensions and interval counts alone: the chunks, their segments, the levels of
+// the segmented trees and the chain tables are planned once and uploaded in one
+// table.  The data-dependent decisions run on the device: non-finite norms fail
+// their job (fail_segments_kernel), every interval takes its own squaring count
+// (squarings_kernel); the degree m and the number S of squaring launches come
+// from a bound on every interval's norm formed from the operators' norms and the
+// largest coefficients (one read-back when the program is built).
+struct ChunkPlan {
+  std::vector<ChunkSeg> segs;
+  int fill = 0;
+  size_t seg_tab = 0, seg_of_item = 0;   // offsets (ints) into the program's int table
+  // state jobs: segmented tree levels (P pairs, C carried, index offset) and the chain
+  struct Level { int P, C; size_t off; };
+  std::vector<Level> levels;
+  int nitems = 0;                        // items after the tree (its last level's output count)
+  size_t chain_off = 0;                  // offset (ChainSeg) into the chain table
+  std::vector<ChainSeg> chain;           // host copy (large-d states use per-job launches)
+};
+
+struct GroupProgram {
+  int dp = 0, prec = MG_PREC_FP64, L = 6, reorth = 0;
+  std::vector<BatchJob> jobs;
+  std::vector<mg_plan*> plans;
+  TaylorChoice tc{};
+  int S = 0;
+  double bound = 0.0;                    // largest bound on ||Hbar_n - tau_n I||_1
+  std::vector<ChunkPlan> chunks;
+  int max_fill = 0, max_segs = 0;
+  // device (owned)
+  int* itab = nullptr;
+  ChainSeg* ctab = nullptr;
+  double** psi_tab = nullptr;            // state pointer of every job (propagator jobs: unused)
+  int* job_fail = nullptr;               // one flag per job
+  int* sq = nullptr;                     // squaring count per item of the largest chunk
+  int* seg_bad = nullptr;                // per segment of the largest chunk
+  int* overflow = nullptr;               // an interval needed more than S squarings
   std::vector<void*> owned;
-  int rc = MG_OK;
-  auto dmalloc = [&](size_t bytes, void** ptr) -> int {
-    if (cudaMalloc(ptr, bytes) != cudaSuccess) {
+};
+
+void free_program(GroupProgram& G) {
+  for (void* q : G.owned) cudaFree(q);
+  G.owned.clear();
+}
+
+// ||H - tau I||_1 of a job's H0 and Kx operators as the group evolves them: padded to
+// the group's dimension dp (the padded block of H - tau I is -tau I, so the padded norm
+// can exceed the unpadded one).  Formed once per plan (dp is a function of d); one
+// read-back for all plans that lack them.
+int ensure_opnorms(mg_ctx* ctx, const std::vector<BatchJob>& jobs, const std::vector<mg_plan*>& plans, int dp) {
+  std::vector<size_t> need;
+  for (size_t q = 0; q < plans.size(); ++q) {
+    mg_plan* p = plans[q];
+    if ((int)p->opnorm.size() == 1 + p->Kx && p->opnorm_dp == dp) continue;
+    bool dup = false;
+    for (size_t r : need) dup |= plans[r] == p;
+    if (!dup) need.push_back(q);
+  }
+  if (need.empty()) return MG_OK;
+  size_t total = 0;
+  for (size_t q : need) total += 1 + plans[q]->Kx;
+  double* dn = nullptr;
+  if (cudaMalloc(&dn, total * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    set_last_message("device allocation of %zu doubles failed", total);
+    return MG_ENOMEM;
+  }
+  int r = MG_OK;
+  size_t off = 0;
+  for (size_t q : need) {
+    if (r == MG_OK) r = launch_op_norm1(1, dp, jobs[q].H0, dn + off, ctx->stream);
+    if (r == MG_OK) r = launch_op_norm1(jobs[q].K, dp, jobs[q].Hk, dn + off + 1, ctx->stream);
+    off += 1 + plans[q]->Kx;
+  }
+  std::vector<double> h(total);
+  if (r == MG_OK && cudaMemcpyAsync(h.data(), dn, total * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream) !=
+                        cudaSuccess)
+    r = MG_ECUDA;
+  if (r == MG_OK && cudaStreamSynchronize(ctx->stream) != cudaSuccess) r = MG_ECUDA;
+  cudaFree(dn);
+  if (r != MG_OK) return r;
+  off = 0;
+  for (size_t q : need) {
+    mg_plan* p = plans[q];
+    p->opnorm.assign(h.begin() + off, h.begin() + off + 1 + p->Kx);
+    p->opnorm_dp = dp;
+    off += 1 + p->Kx;
+  }
+  return MG_OK;
+}
+
+// Bound of every job's ||Hbar_n - tau_n I||_1: dt |H0 - tau0|_1 + sum_k max_n |c_kn| |H_k - tau_k|_1,
+// widened by 2^-16 (the norm kernel's own upper bound lies within 2^-19 of the exact norm).
+// A job with a non-finite coefficient gets a bound of 0 (it fails on the device).
+int norm_bounds(mg_ctx* ctx, std::vector<BatchJob>& jobs, const std::vector<mg_plan*>& plans, int dp,
+                std::vector<double>& bound) {
+  MG_TRY(ensure_opnorms(ctx, jobs, plans, dp));
+  std::vector<CoefRef> refs(jobs.size());
+  size_t total = 0;
+  for (size_t q = 0; q < jobs.size(); ++q) {
+    refs[q] = CoefRef{jobs[q].c, jobs[q].N, jobs[q].K, (int)total};
+    total += jobs[q].K;
+  }
+  std::vector<double> cmax(std::max<size_t>(total, 1), 0.0);
+  if (total > 0) {
+    void* buf = nullptr;
+    const size_t rb = refs.size() * sizeof(CoefRef);
+    if (cudaMalloc(&buf, rb + total * sizeof(double)) != cudaSuccess) {
       cudaGetLastError();
-      set_last_message("device allocation of %zu bytes failed (batched jobs)", bytes);
+      set_last_message("device allocation for the norm bounds failed");
       return MG_ENOMEM;
     }
-    owned.push_back(*ptr);
+    double* out = reinterpret_cast<double*>(static_cast<char*>(buf) + rb);
+    int r = cudaMemcpyAsync(buf, refs.data(), rb, cudaMemcpyHostToDevice, ctx->stream) == cudaSuccess ? MG_OK
+                                                                                                         : MG_ECUDA;
+    if (r == MG_OK) r = launch_coef_absmax((int)refs.size(), reinterpret_cast<CoefRef*>(buf), out, ctx->stream);
+    if (r == MG_OK && cudaMemcpyAsync(cmax.data(), out, total * sizeof(double), cudaMemcpyDeviceToHost,
+                                      ctx->stream) != cudaSuccess)
+      r = MG_ECUDA;
+    if (r == MG_OK && cudaStreamSynchronize(ctx->stream) != cudaSuccess) r = MG_ECUDA;
+    cudaFree(buf);
+    if (r != MG_OK) return r;
+  }
+  bound.assign(jobs.size(), 0.0);
+  for (size_t q = 0; q < jobs.size(); ++q) {
+    const std::vector<double>& on = plans[q]->opnorm;
+    double b = jobs[q].dt * on[0];
+    for (int k = 0; k < jobs[q].K; ++k) b += cmax[refs[q].off + k] * on[1 + k];
+    bound[q] = std::isfinite(b) ? b * (1.0 + std::ldexp(1.0, -16)) : 0.0;
+  }
+  return MG_OK;
+}
+
+// Plan the chunks of a group (jobs already padded and with their states allocated).
+int build_program(mg_ctx* ctx, GroupProgram& G) {
+  const int dp = G.dp;
+  long long total = 0;
+  for (auto& j : G.jobs) total += j.N;
+  const int chunk = chunk_size(ctx, dp, G.prec, G.L, (int)std::min<long long>(total, 1 << 30), 1);
+  std::vector<int> itab;
+  std::vector<ChainSeg> ctab;
+  size_t jcur = 0;
+  int jlocal = 0;
+  while (jcur < G.jobs.size()) {
+    ChunkPlan ch;
+    while (jcur < G.jobs.size() && ch.fill < chunk) {
+      BatchJob& j = G.jobs[jcur];
+      const int take = std::min(chunk - ch.fill, j.N - jlocal);
+      ch.segs.push_back({&j, jlocal, take, ch.fill});
+      ch.fill += take;
+      jlocal += take;
+      if (jlocal == j.N) { ++jcur; jlocal = 0; }
+    }
+    // segment table (job index, first item, items) and the segment of every item
+    ch.seg_tab = itab.size();
+    for (const ChunkSeg& g : ch.segs) {
+      itab.push_back((int)(g.job - G.jobs.data()));
+      itab.push_back(g.off);
+      itab.push_back(g.n);
+    }
+    ch.seg_of_item = itab.size();
+    for (size_t q = 0; q < ch.segs.size(); ++q)
+      for (int i = 0; i < ch.segs[q].n; ++i) itab.push_back((int)q);
+    // state segments: chain records and, for d <= 256 without renormalisation, the
+    // segmented tree that first reduces every segment to its chunk product
+    std::vector<ChainSeg> cs;
+    for (const ChunkSeg& g : ch.segs)
+      if (g.job->output == MG_OUT_STATE) cs.push_back(ChainSeg{(int)(g.job - G.jobs.data()), g.off, g.n, g.a});
+    ch.nitems = ch.fill;
+    if (!cs.empty() && G.reorth == 0 && dp <= 256) {
+      std::vector<std::vector<int>> items(cs.size());
+      for (size_t q = 0; q < cs.size(); ++q)
+        for (int i = 0; i < cs[q].count; ++i) items[q].push_back(cs[q].first + i);
+      for (;;) {
+        bool more = false;
+        for (auto& it : items) more |= it.size() > 1;
+        if (!more) break;
+        std::vector<int> Lx, Rx, Cx;
+        std::vector<std::vector<int>> next(items.size());
+        for (size_t q = 0; q < items.size(); ++q) {
+          const std::vector<int>& it = items[q];
+          size_t i = 0;
+          for (; i + 1 < it.size(); i += 2) {   // later interval on the left
+            next[q].push_back((int)Lx.size());
+            Lx.push_back(it[i + 1]);
+            Rx.push_back(it[i]);
+          }
+          if (i < it.size()) {                    // odd one out: carried to the next level
+            next[q].push_back(-1 - (int)Cx.size());
+            Cx.push_back(it[i]);
+          }
+        }
+        const int P = (int)Lx.size(), C = (int)Cx.size();
+        for (auto& v : next)
+          for (int& x : v) x = x >= 0 ? x : P + (-1 - x);
+        ch.levels.push_back({P, C, itab.size()});
+        itab.insert(itab.end(), Lx.begin(), Lx.end());
+        itab.insert(itab.end(), Rx.begin(), Rx.end());
+        itab.insert(itab.end(), Cx.begin(), Cx.end());
+        items.swap(next);
+        ch.nitems = P + C;
+      }
+      for (size_t q = 0; q < cs.size(); ++q) {
+        cs[q].first = items[q][0];
+        cs[q].count = 1;
+      }
+    }
+    ch.chain = cs;
+    ch.chain_off = ctab.size();
+    ctab.insert(ctab.end(), cs.begin(), cs.end());
+    G.max_fill = std::max(G.max_fill, ch.fill);
+    G.max_segs = std::max(G.max_segs, (int)ch.segs.size());
+    G.chunks.push_back(std::move(ch));
+  }
+  // device tables
+  auto dalloc = [&](size_t bytes, void** ptr) -> int {
+    if (cudaMalloc(ptr, std::max<size_t>(bytes, 16)) != cudaSuccess) {
+      cudaGetLastError();
+      set_last_message("device allocation of %zu bytes failed (batch program)", bytes);
+      return MG_ENOMEM;
+    }
+    G.owned.push_back(*ptr);
     return MG_OK;
   };
-  auto body = [&]() -> int {
-    long long total = 0;
-    for (size_t q = 0; q < jobs.size(); ++q) {
-      BatchJob& j = jobs[q];
-      mg_plan* p = plans[q];
-      total += j.N;
-      if (j.d == dp) {
-        j.H0 = p->H0;
-        j.Hk = p->Hk;
-      } else {
-        void* buf;
-        MG_TRY(dmalloc(sizeof(double) * md * (1 + j.K), &buf));
-        double* H = reinterpret_cast<double*>(buf);
-        MG_TRY(launch_pad_copy(1, j.d, dp, p->H0, H, s));
-        if (j.K > 0) MG_TRY(launch_pad_copy(j.K, j.d, dp, p->Hk, H + md, s));
-        j.H0 = H;
-        j.Hk = H + md;
+  void* p;
+  MG_TRY(dalloc(itab.size() * sizeof(int), &p));
+  G.itab = static_cast<int*>(p);
+  MG_TRY(dalloc(ctab.size() * sizeof(ChainSeg), &p));
+  G.ctab = static_cast<ChainSeg*>(p);
+  MG_TRY(dalloc(G.jobs.size() * sizeof(double*), &p));
+  G.psi_tab = static_cast<double**>(p);
+  MG_TRY(dalloc(G.jobs.size() * sizeof(int), &p));
+  G.job_fail = static_cast<int*>(p);
+  MG_TRY(dalloc((size_t)G.max_fill * sizeof(int), &p));
+  G.sq = static_cast<int*>(p);
+  MG_TRY(dalloc((size_t)G.max_segs * sizeof(int), &p));
+  G.seg_bad = static_cast<int*>(p);
+  MG_TRY(dalloc(sizeof(int), &p));
+  G.overflow = static_cast<int*>(p);
+  std::vector<double*> psis(G.jobs.size());
+  for (size_t q = 0; q < G.jobs.size(); ++q) psis[q] = G.jobs[q].state;
+  cudaStream_t s = ctx->stream;
+  if (!itab.empty()) MG_CUDA_TRY(cudaMemcpyAsync(G.itab, itab.data(), itab.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+  if (!ctab.empty())
+    MG_CUDA_TRY(cudaMemcpyAsync(G.ctab, ctab.data(), ctab.size() * sizeof(ChainSeg), cudaMemcpyHostToDevice, s));
+  MG_CUDA_TRY(cudaMemcpyAsync(G.psi_tab, psis.data(), psis.size() * sizeof(double*), cudaMemcpyHostToDevice, s));
+  MG_CUDA_TRY(cudaStreamSynchronize(s));   // the host tables go out of scope
+  // degree and squaring launches from the norm bound
+  std::vector<double> bound;
+  MG_TRY(norm_bounds(ctx, G.jobs, G.plans, dp, bound));
+  G.bound = 0.0;
+  for (double b : bound) G.bound = std::max(G.bound, b);
+  G.tc = choose_taylor(G.bound, unit_roundoff(G.prec, G.L, dp), G.prec == MG_PREC_SPLIT);
+  G.S = G.tc.s;
+  return MG_OK;
+}
+
+// Issue one chunk of a program on the context's stream: no host synchronisation.
+int issue_chunk(mg_ctx* ctx, Engine& eng, GroupProgram& G, ChunkPlan& ch) {
+  PhaseRange range("batch_chunk");
+  cudaStream_t s = ctx->stream;
+  const int dp = G.dp;
+  const long long md = mat_doubles(dp);
+  const int fill = ch.fill;
+  double *W, *tau, *nrm, *Ub, *sc;
+  MG_TRY(ws(ctx, WS_W, md * fill, &W));
+  MG_TRY(ws(ctx, WS_TAU, fill, &tau));
+  MG_TRY(ws(ctx, WS_NORM, fill, &nrm));
+  MG_TRY(ws(ctx, WS_UBUF, md * fill, &Ub));
+  size_t scn = 1;
+  for (const ChunkSeg& g : ch.segs) scn = std::max(scn, (size_t)g.job->K + 1 + g.n);
+  MG_TRY(small_scratch(ctx, scn, &sc));
+  {
+    PhaseRange hr("hbar");
+    for (const ChunkSeg& g : ch.segs) {
+      const BatchJob& j = *g.job;
+      MG_TRY(launch_build_omega(g.n, dp, j.K, j.dt, j.H0, j.Hk, j.c + (long long)g.a * j.K, W + g.off * md,
+                                tau + g.off, nrm + g.off, 1, 1, sc, s));
+    }
+  }
+  MG_TRY(launch_fail_segments((int)ch.segs.size(), fill, md, G.itab + ch.seg_tab, G.itab + ch.seg_of_item, nrm, tau,
+                              G.job_fail, G.seg_bad, W, s));
+  MG_TRY(launch_squarings(fill, nrm, G.tc.theta, G.S, 0, G.sq, G.overflow, ctx->timing ? ctx->dev_flops : nullptr,
+                          8.0 * (double)dp * dp * dp, s));
+  MG_TRY(expm_chunk_dev(ctx, eng, fill, W, tau, G.sq, G.tc, G.S, Ub));
+  PhaseRange pr("propagate");
+  // propagator jobs: tree product of the segment, folded into the running product
+  for (const ChunkSeg& g : ch.segs) {
+    BatchJob& j = *g.job;
+    if (j.output != MG_OUT_PROPAGATOR) continue;
+    int span = 0;
+    if (G.reorth > 1) { span = 1; while (span * 2 <= G.reorth) span *= 2; if (span < 2) span = 0; }
+    double* prod;
+    MG_TRY(tree_product(ctx, eng, g.n, Ub + g.off * md, &prod, span));
+    if (!j.init) {
+      MG_TRY(launch_copy_strided(1, md, prod, md, j.state, md, s));
+      j.init = true;
+    } else {
+      double* acc2;
+      MG_TRY(ws(ctx, WS_ACC2, md, &acc2));
+      MG_TRY(eng.reserve(1));
+      MG_TRY(eng.prepA(1, prod, md));
+      MG_TRY(eng.prepB(0, 1, j.state, md));
+      AddTerms none;
+      MG_TRY(eng.mul(1, prod, md, 0, j.state, md, acc2, md, none));
+      MG_TRY(launch_copy_strided(1, md, acc2, md, j.state, md, s));
+    }
+    if (G.reorth > 0 && (g.a + g.n) / G.reorth != g.a / G.reorth) MG_TRY(reorth_batch(ctx, eng, 1, j.state, md));
+  }
+  if (ch.chain.empty()) return MG_OK;
+  // state jobs: segmented tree (planned), then the chain
+  const double* Ucur = Ub;
+  if (!ch.levels.empty()) {
+    const size_t cap = (size_t)fill / 2 + ch.chain.size() + 1;
+    double *t0, *t1, *ga, *gb;
+    MG_TRY(ws(ctx, WS_TREE0, md * cap, &t0));
+    MG_TRY(ws(ctx, WS_TREE1, md * cap, &t1));
+    MG_TRY(ws(ctx, WS_SEG_A, md * cap, &ga));
+    MG_TRY(ws(ctx, WS_SEG_B, md * cap, &gb));
+    for (size_t lv = 0; lv < ch.levels.size(); ++lv) {
+      const ChunkPlan::Level& v = ch.levels[lv];
+      const int* li = G.itab + v.off;
+      double* out = (lv % 2 == 0) ? t0 : t1;
+      MG_TRY(launch_gather_mats(v.P, md, Ucur, li, ga, s));
+      MG_TRY(launch_gather_mats(v.P, md, Ucur, li + v.P, gb, s));
+      MG_TRY(launch_gather_mats(v.C, md, Ucur, li + 2 * v.P, out + (long long)v.P * md, s));
+      if (v.P > 0) {
+        MG_TRY(eng.reserve(v.P));
+        MG_TRY(eng.prepA(v.P, ga, md));
+        MG_TRY(eng.prepB(0, v.P, gb, md));
+        AddTerms none;
+        MG_TRY(eng.mul(v.P, ga, md, 0, gb, md, out, md, none));
       }
-      void* st;
-      MG_TRY(dmalloc(j.output == MG_OUT_STATE ? sizeof(double) * 2 * dp : sizeof(double) * md, &st));
-      j.state = reinterpret_cast<double*>(st);
-      MG_TRY(init_job_state(ctx, eng, j, in ? in[j.idx] : nullptr, h2d, s));
+      Ucur = out;
     }
-    void *pbuf, *sbuf;
-    MG_TRY(dmalloc(sizeof(double*) * jobs.size(), &pbuf));
-    MG_TRY(dmalloc(sizeof(ChainSeg) * jobs.size(), &sbuf));
-    const int chunk = chunk_size(ctx, dp, prec, L, (int)std::min<long long>(total, 1 << 30), 1);
-    size_t jcur = 0;
-    int jlocal = 0;
-    ExpmStats st;
-    while (jcur < jobs.size()) {
-      std::vector<ChunkSeg> segs;
-      int fill = 0;
-      while (jcur < jobs.size() && fill < chunk) {
-        BatchJob& j = jobs[jcur];
-        const int take = std::min(chunk - fill, j.N - jlocal);
-        segs.push_back({&j, jlocal, take, fill});
-        fill += take;
-        jlocal += take;
-        if (jlocal == j.N) { ++jcur; jlocal = 0; }
+  }
+  const double* Uf = Ucur;
+  if (eng.df()) {
+    double* conv;
+    MG_TRY(ws(ctx, WS_NS_Z, md * ch.nitems, &conv));
+    MG_TRY(eng.to_fp64(ch.nitems, Ucur, md, conv, md));
+    Uf = conv;
+  }
+  if (dp <= 256) {
+    MG_TRY(launch_multi_chain((int)ch.chain.size(), dp, G.ctab + ch.chain_off, Uf, md, G.psi_tab, G.reorth, s));
+  } else {
+    double* tmp;
+    MG_TRY(ws(ctx, WS_VEC, 2 * dp + 2, &tmp));
+    for (const ChainSeg& c : ch.chain)
+      MG_TRY(launch_state_chain(c.count, dp, Uf + (long long)c.first * md, md, G.jobs[c.job].state, tmp + 2, G.reorth,
+                                c.done_before, s));
+  }
+  return MG_OK;
+}
+
+// Set up a group: padded operators, job states and the program.
+int setup_group(mg_ctx* ctx, GroupProgram& G) {
+  cudaStream_t s = ctx->stream;
+  const int dp = G.dp;
+  const long long md = mat_doubles(dp);
+  for (size_t q = 0; q < G.jobs.size(); ++q) {
+    BatchJob& j = G.jobs[q];
+    mg_plan* p = G.plans[q];
+    void* buf;
+    if (j.d == dp) {
+      j.H0 = p->H0;
+      j.Hk = p->Hk;
+    } else {
+      if (cudaMalloc(&buf, sizeof(double) * md * (1 + j.K)) != cudaSuccess) {
+        cudaGetLastError();
+        set_last_message("device allocation failed (padded operators)");
+        return MG_ENOMEM;
       }
-      MG_TRY(process_chunk(ctx, eng, segs, fill, reorth_every, reinterpret_cast<ChainSeg*>(sbuf),
-                           reinterpret_cast<double**>(pbuf), &st));
+      G.owned.push_back(buf);
+      double* H = static_cast<double*>(buf);
+      MG_TRY(launch_pad_copy(1, j.d, dp, p->H0, H, s));
+      if (j.K > 0) MG_TRY(launch_pad_copy(j.K, j.d, dp, p->Hk, H + md, s));
+      j.H0 = H;
+      j.Hk = H + md;
     }
-    for (auto& j : jobs) {
-      MG_TRY(write_job_output(ctx, eng, j, out[j.idx], d2h));
-      if (job_status) job_status[j.idx] = j.failed ? MG_ENONFINITE : MG_OK;
+    if (cudaMalloc(&buf, j.output == MG_OUT_STATE ? sizeof(double) * 2 * dp : sizeof(double) * md) != cudaSuccess) {
+      cudaGetLastError();
+      set_last_message("device allocation failed (job state)");
+      return MG_ENOMEM;
     }
-    return MG_OK;
-  };
-  rc = body();
-  cudaStreamSynchronize(s);
-  for (void* q : owned) cudaFree(q);
-  if (rc == MG_OK && prec == MG_PREC_SPLIT) rc = check_status(ctx);
-  return rc;
+    G.owned.push_back(buf);
+    j.state = static_cast<double*>(buf);
+  }
+  return build_program(ctx, G);
+}
+
+// Issue a whole group: job states from in[], every chunk, outputs to out[]; no host sync.
+int issue_group(mg_ctx* ctx, GroupProgram& G, const double* const* in, double* const* out, cudaMemcpyKind h2d,
+                cudaMemcpyKind d2h) {
+  cudaStream_t s = ctx->stream;
+  const int dp = G.dp;
+  const long long md = mat_doubles(dp);
+  Engine eng{ctx, dp, G.prec, G.L};
+  MG_CUDA_TRY(cudaMemsetAsync(G.job_fail, 0, sizeof(int) * G.jobs.size(), s));
+  MG_CUDA_TRY(cudaMemsetAsync(G.overflow, 0, sizeof(int), s));
+  for (BatchJob& j : G.jobs) {
+    j.init = false;
+    j.done = 0;
+    MG_TRY(init_job_state(ctx, eng, j, in ? in[j.idx] : nullptr, h2d, s));
+  }
+  for (ChunkPlan& ch : G.chunks) MG_TRY(issue_chunk(ctx, eng, G, ch));
+  for (BatchJob& j : G.jobs) {
+    double* o = out[j.idx];
+    if (j.output == MG_OUT_STATE) {
+      MG_CUDA_TRY(cudaMemcpyAsync(o, j.state, sizeof(double) * 2 * j.d, d2h, s));
+    } else {
+      double *f, *t;
+      MG_TRY(ws(ctx, WS_NS_G, md, &f));
+      MG_TRY(ws(ctx, WS_OUT, mat_doubles(j.d), &t));
+      if (!j.init) MG_TRY(eng.identity(1, j.state));
+      MG_TRY(eng.to_fp64(1, j.state, md, f, md));
+      MG_TRY(launch_unpad_copy(j.d, dp, f, t, s));
+      MG_CUDA_TRY(cudaMemcpyAsync(o, t, sizeof(double) * mat_doubles(j.d), d2h, s));
+    }
+  }
+  return MG_OK;
+}
+
+// After the stream has synchronised: per-job status and the squaring-bound check.
+int collect_group(mg_ctx* ctx, GroupProgram& G, int* job_status) {
+  std::vector<int> fail(G.jobs.size());
+  int over = 0;
+  MG_CUDA_TRY(cudaMemcpy(fail.data(), G.job_fail, sizeof(int) * fail.size(), cudaMemcpyDeviceToHost));
+  MG_CUDA_TRY(cudaMemcpy(&over, G.overflow, sizeof(int), cudaMemcpyDeviceToHost));
+  if (job_status)
+    for (size_t q = 0; q < G.jobs.size(); ++q) job_status[G.jobs[q].idx] = fail[q] ? MG_ENONFINITE : MG_OK;
+  if (over) {
+    set_last_message("an interval's norm exceeded the bound the squaring launches were planned for "
+                     "(controls changed since the batch was planned)");
+    return MG_EUNSUPPORTED;
+  }
+  return check_status(ctx);
 }
 
 }  // namespace
@@ -1987,21 +2440,251 @@ int mg_evolve_batch(mg_ctx* ctx, int n, mg_plan* const* plans, const int* output
     if (all.empty()) return MG_OK;
   }
   std::stable_sort(all.begin(), all.end(), [](const Item& a, const Item& b) { return a.k < b.k; });
+  const cudaMemcpyKind h2d = (flags & MG_FLAG_HOST_PTRS) ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+  const cudaMemcpyKind d2h = (flags & MG_FLAG_HOST_PTRS) ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
   int rc = MG_OK;
   for (size_t g0 = 0; g0 < all.size() && rc == MG_OK;) {
     size_t g1 = g0;
-    std::vector<BatchJob> jobs;
-    std::vector<mg_plan*> ps;
+    GroupProgram G;
+    const Key k = all[g0].k;
+    G.dp = k.dp;
+    G.prec = k.prec;
+    G.L = k.L == 0 ? 6 : k.L;
+    G.reorth = reorth_every;
     while (g1 < all.size() && !(all[g0].k < all[g1].k) && !(all[g1].k < all[g0].k)) {
-      jobs.push_back(all[g1].j);
-      ps.push_back(all[g1].p);
+      G.jobs.push_back(all[g1].j);
+      G.plans.push_back(all[g1].p);
       ++g1;
     }
-    const Key k = all[g0].k;
-    rc = run_group(ctx, jobs, ps, k.dp, k.prec, k.L == 0 ? 6 : k.L, in, out, reorth_every, flags, job_status);
+    rc = setup_group(ctx, G);
+    if (rc == MG_OK) rc = issue_group(ctx, G, in, out, h2d, d2h);
+    const cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    if (rc == MG_OK && e != cudaSuccess) {
+      set_last_cuda_error(e, "cudaStreamSynchronize", __FILE__, __LINE__);
+      rc = MG_ECUDA;
+    }
+    if (rc == MG_OK) rc = collect_group(ctx, G, job_status);
+    free_program(G);
     g0 = g1;
   }
   return rc;
+}
+
+// ---------------------------------------------------------------------------
+// a batch captured once in a CUDA graph and replayed
+// ---------------------------------------------------------------------------
+struct mg_batch_graph {
+  mg_ctx* ctx = nullptr;
+  std::vector<std::unique_ptr<GroupProgram>> groups;
+  std::vector<mg_plan*> plans;
+  std::vector<const double*> c_ptr;   // the plans' coefficient buffers, N and dt at capture
+  std::vector<int> N, Kx;
+  std::vector<double> dt;
+  std::vector<const double*> in;
+  std::vector<double*> out;
+  // workspace of the captured launches (private: the context's own slots may move later)
+  std::vector<void*> slot_ptr;
+  std::vector<size_t> slot_size;
+  double* small = nullptr;
+  size_t small_n = 0;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int64_t kernel_nodes = 0, nodes = 0;
+};
+
+namespace {
+
+void swap_workspace(mg_ctx* c, mg_batch_graph* g) {
+  std::swap(c->slot_ptr, g->slot_ptr);
+  std::swap(c->slot_size, g->slot_size);
+  std::swap(c->small, g->small);
+  std::swap(c->small_n, g->small_n);
+}
+
+void free_batch_graph(mg_batch_graph* g) {
+  if (g->exec) cudaGraphExecDestroy(g->exec);
+  if (g->graph) cudaGraphDestroy(g->graph);
+  for (auto& G : g->groups) free_program(*G);
+  for (void* q : g->slot_ptr)
+    if (q) cudaFree(q);
+  if (g->small) cudaFree(g->small);
+  delete g;
+}
+
+int issue_all(mg_batch_graph* g) {
+  for (auto& G : g->groups)
+    MG_TRY(issue_group(g->ctx, *G, g->in.data(), g->out.data(), cudaMemcpyDeviceToDevice, cudaMemcpyDeviceToDevice));
+  return MG_OK;
+}
+
+int collect_all(mg_batch_graph* g, int* job_status) {
+  int rc = MG_OK;
+  for (auto& G : g->groups) {
+    const int r = collect_group(g->ctx, *G, job_status);
+    if (rc == MG_OK) rc = r;
+  }
+  return rc;
+}
+
+}  // namespace
+
+int mg_batch_graph_create(mg_ctx* ctx, int n, mg_plan* const* plans, const int* outputs, const double* const* in,
+                          double* const* out, int reorth_every, mg_batch_graph** graph) {
+  if (!ctx || n < 1 || !plans || !outputs || !out || !graph || reorth_every < 0) return MG_EINVAL;
+  *graph = nullptr;
+  if (!ctx->stream) {
+    set_last_message("mg_batch_graph_create: the context's stream is the legacy default stream, which cannot "
+                     "be captured; create the context on a stream of its own");
+    return MG_EINVAL;
+  }
+  MG_CUDA_TRY(cudaSetDevice(ctx->device));
+  struct Key {
+    int prec, L, dp;
+    bool operator<(const Key& o) const { return prec != o.prec ? prec < o.prec : (L != o.L ? L < o.L : dp < o.dp); }
+  };
+  struct Item { Key k; BatchJob j; mg_plan* p; };
+  std::vector<Item> all;
+  mg_batch_graph* g = new mg_batch_graph();
+  g->ctx = ctx;
+  for (int i = 0; i < n; ++i) {
+    mg_plan* p = plans[i];
+    if (!p || p->ctx != ctx || p->N < 1 || !out[i] ||
+        (outputs[i] != MG_OUT_STATE && outputs[i] != MG_OUT_PROPAGATOR) ||
+        (outputs[i] == MG_OUT_STATE && (!in || !in[i]))) {
+      delete g;
+      set_last_message("mg_batch_graph_create: job %d: invalid plan, output kind or buffers", i);
+      return MG_EINVAL;
+    }
+    if (outputs[i] == MG_OUT_STATE && (p->flags & MG_FLAG_STATE_ACTION)) {
+      delete g;
+      set_last_message("mg_batch_graph_create: job %d is flagged for the action path, which a captured batch "
+                       "does not take", i);
+      return MG_EUNSUPPORTED;
+    }
+    BatchJob j;
+    j.idx = i;
+    j.output = outputs[i];
+    j.d = p->d;
+    j.K = p->Kx;
+    j.N = p->N;
+    j.dt = p->dt;
+    j.c = p->c;
+    all.push_back({Key{p->precision, p->precision == MG_PREC_SPLIT ? p->L : 0, round_dim(p->d)}, j, p});
+    g->plans.push_back(p);
+    g->c_ptr.push_back(p->c);
+    g->N.push_back(p->N);
+    g->Kx.push_back(p->Kx);
+    g->dt.push_back(p->dt);
+    g->in.push_back(in ? in[i] : nullptr);
+    g->out.push_back(out[i]);
+  }
+  std::stable_sort(all.begin(), all.end(), [](const Item& a, const Item& b) { return a.k < b.k; });
+  swap_workspace(ctx, g);
+  const bool timing = ctx->timing;
+  int rc = MG_OK;
+  for (size_t g0 = 0; g0 < all.size() && rc == MG_OK;) {
+    size_t g1 = g0;
+    auto G = std::make_unique<GroupProgram>();
+    const Key k = all[g0].k;
+    G->dp = k.dp;
+    G->prec = k.prec;
+    G->L = k.L == 0 ? 6 : k.L;
+    G->reorth = reorth_every;
+    while (g1 < all.size() && !(all[g0].k < all[g1].k) && !(all[g1].k < all[g0].k)) {
+      G->jobs.push_back(all[g1].j);
+      G->plans.push_back(all[g1].p);
+      ++g1;
+    }
+    rc = setup_group(ctx, *G);
+    g->groups.push_back(std::move(G));
+    g0 = g1;
+  }
+  // one uncaptured pass sizes the private workspace (no allocation may happen while capturing)
+  if (rc == MG_OK) rc = issue_all(g);
+  if (rc == MG_OK) {
+    const cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) {
+      set_last_cuda_error(e, "cudaStreamSynchronize", __FILE__, __LINE__);
+      rc = MG_ECUDA;
+    }
+  }
+  if (rc == MG_OK) rc = collect_all(g, nullptr);
+  if (rc == MG_OK) {
+    ctx->timing = false;
+    cudaError_t e = cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+      set_last_cuda_error(e, "cudaStreamBeginCapture", __FILE__, __LINE__);
+      rc = MG_ECUDA;
+    } else {
+      rc = issue_all(g);
+      cudaGraph_t gr = nullptr;
+      e = cudaStreamEndCapture(ctx->stream, &gr);
+      if (rc == MG_OK && e != cudaSuccess) {
+        set_last_cuda_error(e, "cudaStreamEndCapture", __FILE__, __LINE__);
+        rc = MG_ECUDA;
+      }
+      cudaGetLastError();
+      g->graph = gr;
+    }
+    ctx->timing = timing;
+  }
+  if (rc == MG_OK) {
+    size_t nn = 0;
+    MG_CUDA_TRY(cudaGraphGetNodes(g->graph, nullptr, &nn));
+    std::vector<cudaGraphNode_t> nodes(nn);
+    if (nn) MG_CUDA_TRY(cudaGraphGetNodes(g->graph, nodes.data(), &nn));
+    g->nodes = (int64_t)nn;
+    for (cudaGraphNode_t nd : nodes) {
+      cudaGraphNodeType t;
+      if (cudaGraphNodeGetType(nd, &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++g->kernel_nodes;
+    }
+    const cudaError_t e = cudaGraphInstantiate(&g->exec, g->graph, 0);
+    if (e != cudaSuccess) {
+      set_last_cuda_error(e, "cudaGraphInstantiate", __FILE__, __LINE__);
+      rc = MG_ECUDA;
+    }
+  }
+  swap_workspace(ctx, g);
+  if (rc != MG_OK) {
+    cudaStreamSynchronize(ctx->stream);
+    free_batch_graph(g);
+    return rc;
+  }
+  *graph = g;
+  return MG_OK;
+}
+
+int mg_batch_graph_launch(mg_batch_graph* g, int* job_status) {
+  if (!g) return MG_EINVAL;
+  mg_ctx* ctx = g->ctx;
+  for (size_t q = 0; q < g->plans.size(); ++q) {
+    const mg_plan* p = g->plans[q];
+    if (p->c != g->c_ptr[q] || p->N != g->N[q] || p->Kx != g->Kx[q] || p->dt != g->dt[q]) {
+      set_last_message("mg_batch_graph_launch: job %zu: its plan's interval count, step or coefficient buffer "
+                       "changed since the capture; create a new graph", q);
+      return MG_EINVAL;
+    }
+  }
+  MG_CUDA_TRY(cudaSetDevice(ctx->device));
+  MG_CUDA_TRY(cudaGraphLaunch(g->exec, ctx->stream));
+  g_launches.fetch_add(g->kernel_nodes, std::memory_order_relaxed);
+  MG_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  return collect_all(g, job_status);
+}
+
+int mg_batch_graph_stats(mg_batch_graph* g, int64_t* kernel_nodes, int64_t* nodes) {
+  if (!g) return MG_EINVAL;
+  if (kernel_nodes) *kernel_nodes = g->kernel_nodes;
+  if (nodes) *nodes = g->nodes;
+  return MG_OK;
+}
+
+int mg_batch_graph_destroy(mg_batch_graph* g) {
+  if (!g) return MG_EINVAL;
+  cudaSetDevice(g->ctx->device);
+  cudaStreamSynchronize(g->ctx->stream);
+  free_batch_graph(g);
+  return MG_OK;
 }
 
 // ---------------------------------------------------------------------------
@@ -2704,6 +3387,7 @@ int mg_plan_set_magnus_order(mg_plan* p, int order) {
   if (!p || (order != 1 && order != 2)) return MG_EINVAL;
   mg_ctx* ctx = p->ctx;
   MG_CUDA_TRY(cudaSetDevice(ctx->device));
+  p->opnorm.clear();   // the operator set changes
   const int K = p->K, d = p->d;
   if (order == 1 || K == 0) {
     p->order = order;

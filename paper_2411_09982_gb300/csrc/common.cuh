@@ -118,6 +118,9 @@ struct AddTerms {
   long long stride = 0;   // batch stride of the addend matrices (doubles)
   double diag = 0.0;
   double scale = 1.0;
+  // FP64 product only: with item_sq set, items with item_sq[b] <= sq_step are skipped
+  const int* item_sq = nullptr;
+  int sq_step = 0;
 };
 int launch_cgemm_f64(int batch, int d, const double* A, long long strideA, int opA,
                      const double* B, long long strideB, double* C, long long strideC,
@@ -214,8 +217,32 @@ int launch_pad_into(int d, int dp, const double* src, double* dst, cudaStream_t 
 // dst (d x d) <- top-left block of src (dp x dp)
 int launch_unpad_copy(int d, int dp, const double* src, double* dst, cudaStream_t s);
 
+// Device-side decisions of the batched path; see batch.cu.
+// out[q] = ||A_q - tau_q I||_1 for `count` consecutive d x d operators
+int launch_op_norm1(int count, int d, const double* ops, double* out, cudaStream_t s);
+struct CoefRef {
+  const double* c;   // N x K coefficients (device)
+  int N, K;
+  int off;           // first output slot of the job
+};
+// out[off_j + k] = max_n |c_j[n][k]| (NaN if any is non-finite), one block per job
+int launch_coef_absmax(int njobs, const CoefRef* refs_dev, double* out, cudaStream_t s);
+// per segment (seg_tab: job, first item, items): a non-finite norm or phase sets
+// job_fail[job] and seg_bad, zeroes the segment's norms, phases and exponents W
+int launch_fail_segments(int nseg, int fill, long long md, const int* seg_tab, const int* seg_of_item, double* norm,
+                         double* tau, int* job_fail, int* seg_bad, double* W, cudaStream_t s);
+// dst[b] = src[b] (md doubles each) for the items with item_sq[b] > sq_step
+int launch_copy_active(int batch, long long md, const double* src, double* dst, const int* item_sq, int sq_step,
+                       cudaStream_t s);
+// sq[i] = smallest s with 2^-s norm[i] <= theta (uniform: S for every item); s > S sets *overflow.
+// flops_acc (may be null): += flops_per_square * sq[i] summed over the items (per-item mode)
+int launch_squarings(int n, const double* norm, double theta, int S, int uniform, int* sq, int* overflow,
+                     double* flops_acc, double flops_per_square, cudaStream_t s);
+
 // Double-float (DF32) elementwise kernels of the split path; see elementwise.cu.
-int launch_scale_minus_i_df(int batch, int d, const double* src_fp64, double* dst_df, int sq, cudaStream_t s);
+// X_b = -i 2^{-sq_b} W_b with sq_b from sq_dev (device, per item) or the constant sq
+int launch_scale_minus_i_df(int batch, int d, const double* src_fp64, double* dst_df, int sq, cudaStream_t s,
+                            const int* sq_dev = nullptr);
 // dst[o] = sum_m coef[o * nsrc + m] src[m] + diag[o] I, o < nout <= 5, nsrc <= 4, one pass
 // (a destination may alias a source); FP64 and double-float storage
 int launch_lincomb_multi(int batch, int d, int nout, double* const* dst, int nsrc, const double* const* src,

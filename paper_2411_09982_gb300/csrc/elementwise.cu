@@ -227,20 +227,25 @@ int launch_max_identity_defect(int batch, int d, const double* G, double* out_de
 // double-float (DF32) versions used by the split-precision path
 // ---------------------------------------------------------------------------
 // X = (-i) 2^{-sq} src: FP64 in, DF32 out
-__global__ void scale_minus_i_df_kernel(long long total, const double* __restrict__ src, float4* __restrict__ dst,
-                                        double f) {
+__global__ void scale_minus_i_df_kernel(long long total, long long per_item, const double* __restrict__ src,
+                                        float4* __restrict__ dst, double f, const int* __restrict__ sq_dev) {
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
        e += (long long)gridDim.x * blockDim.x) {
+    // 2^{-s} exactly (0 <= s < 1023)
+    const double g = sq_dev ? __longlong_as_double((long long)(1023 - sq_dev[e / per_item]) << 52) : f;
     const double2 v = reinterpret_cast<const double2*>(src)[e];
-    const df32 re = df_from_double(f * v.y), im = df_from_double(-f * v.x);
+    const df32 re = df_from_double(g * v.y), im = df_from_double(-g * v.x);
     dst[e] = make_float4(re.hi, re.lo, im.hi, im.lo);
   }
 }
 
-int launch_scale_minus_i_df(int batch, int d, const double* src_fp64, double* dst_df, int sq, cudaStream_t s) {
-  const long long total = (long long)d * d * batch;
+int launch_scale_minus_i_df(int batch, int d, const double* src_fp64, double* dst_df, int sq, cudaStream_t s,
+                            const int* sq_dev) {
+  const long long per = (long long)d * d;
+  const long long total = per * batch;
   const double f = std::ldexp(1.0, -sq);
-  scale_minus_i_df_kernel<<<grid_for(total), 256, 0, s>>>(total, src_fp64, reinterpret_cast<float4*>(dst_df), f);
+  scale_minus_i_df_kernel<<<grid_for(total), 256, 0, s>>>(total, per, src_fp64, reinterpret_cast<float4*>(dst_df), f,
+                                                          sq_dev);
   return check_launch("scale_minus_i_df_kernel");
 }
 

@@ -21,6 +21,8 @@ struct AddDev {
   int n;
   double diag;
   double scale;
+  const int* item_sq;   // null, or per-item squaring counts: item b is skipped when item_sq[b] <= sq_step
+  int sq_step;
 };
 
 template <int TM>
@@ -34,6 +36,7 @@ cgemm_f64_kernel(int d, const double* __restrict__ A, long long sA, int opA,
   __shared__ double2 Bs[FBK][TM];   // Bs[k][j] = B[k][j]
 
   const int b = blockIdx.z;
+  if (add.item_sq && add.item_sq[b] <= add.sq_step) return;   // uniform over the CTA
   const double2* Ab = reinterpret_cast<const double2*>(A + b * sA);
   const double2* Bb = reinterpret_cast<const double2*>(B + b * sB);
   const int i0 = blockIdx.y * TM, j0 = blockIdx.x * TM;
@@ -130,6 +133,8 @@ int launch_cgemm_f64(int batch, int d, const double* A, long long strideA, int o
   a.stride = add.stride;
   a.diag = add.diag;
   a.scale = add.scale;
+  a.item_sq = add.item_sq;
+  a.sq_step = add.sq_step;
   // tile edge: the smallest of 16, 32, 64 that covers d (64 beyond)
   if (d <= 16) {
     cgemm_f64_kernel<16><<<dim3(1, 1, batch), 256, 0, s>>>(d, A, strideA, opA, B, strideB, C, strideC, a);

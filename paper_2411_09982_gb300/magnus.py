@@ -105,6 +105,10 @@ SIGNATURES = {
     "mg_ctx_set_wait_limit": (_I, [_P, _D, _I]),
     "mg_ctx_gemm_stats": (_I, [_P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(_D), ctypes.POINTER(_D), _I]),
     "mg_cgemm_split_static": (_I, [_I, _P, _I, _I, _P, _P, _P, _I]),
+    "mg_batch_graph_create": (_I, [_P, _I, _P, _P, _P, _P, _I, ctypes.POINTER(_P)]),
+    "mg_batch_graph_launch": (_I, [_P, _P]),
+    "mg_batch_graph_stats": (_I, [_P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
+    "mg_batch_graph_destroy": (_I, [_P]),
     "mg_server_create": (_I, [_P, ctypes.c_size_t, _I, ctypes.POINTER(_P)]),
     "mg_submit": (_I, [_P, ctypes.POINTER(mg_job), ctypes.POINTER(ctypes.c_uint64)]),
     "mg_wait": (_I, [_P, ctypes.c_uint64, _D, ctypes.POINTER(mg_job_report)]),
@@ -325,6 +329,49 @@ def mg_evolve_batch(ctx, plans, outputs, inputs, outs, reorth_every=0, host=Fals
                                   MG_FLAG_HOST_PTRS if host else 0, ctypes.cast(st, ctypes.c_void_p)),
            "mg_evolve_batch")
     return list(st)
+
+
+class BatchGraph:
+    """mg_batch_graph: a batch of plans captured once in a CUDA graph and replayed."""
+
+    def __init__(self, ctx, plans, outputs, inputs, outs, reorth_every=0):
+        n = len(plans)
+        PA = ctypes.c_void_p * n
+        IA = ctypes.c_int * n
+        self._arrays = (PA(*[p.h.value for p in plans]), IA(*outputs),
+                        PA(*[(t.data_ptr() if t is not None else None) for t in inputs]),
+                        PA(*[t.data_ptr() for t in outs]))
+        self._keep = (list(plans), list(inputs), list(outs))
+        self.n = n
+        h = ctypes.c_void_p()
+        hp, oa, ia, oa2 = self._arrays
+        _check(load().mg_batch_graph_create(ctx.h, n, ctypes.cast(hp, ctypes.c_void_p),
+                                            ctypes.cast(oa, ctypes.c_void_p), ctypes.cast(ia, ctypes.c_void_p),
+                                            ctypes.cast(oa2, ctypes.c_void_p), reorth_every, ctypes.byref(h)),
+               "mg_batch_graph_create")
+        self.h = h
+
+    def launch(self):
+        """Replay the batch; returns the per-job status list."""
+        st = (ctypes.c_int * self.n)(*([0] * self.n))
+        _check(load().mg_batch_graph_launch(self.h, ctypes.cast(st, ctypes.c_void_p)), "mg_batch_graph_launch")
+        return list(st)
+
+    def stats(self):
+        k, a = ctypes.c_int64(), ctypes.c_int64()
+        _check(load().mg_batch_graph_stats(self.h, ctypes.byref(k), ctypes.byref(a)), "mg_batch_graph_stats")
+        return dict(kernel_nodes=k.value, nodes=a.value)
+
+    def close(self):
+        if self.h:
+            load().mg_batch_graph_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def mg_quadrature_nodes(P: int):

@@ -136,3 +136,39 @@ def test_uneven_batch_512_all_in_one_call(ctx, prec, flags, tol):
         worst = max(worst, err)
         assert err <= tol, (q, rec["d"], rec["N"], err)
     print(f"uneven batch, worst error over {len(g['jobs'])} instances: {worst:.3e}")
+
+
+def test_uneven_batch_512_captured_graph():
+    """The 512-instance batch captured once in a CUDA graph and replayed twice: every 32nd
+    instance against the oracle's psi(T) within the stated 1e-6 (split, 6 digits)."""
+    with open(GOLDEN_UNEVEN) as f:
+        g = json.load(f)
+    stream = torch.cuda.Stream()
+    c = M.Context(0, stream)
+    jobs = W.uneven_batch()
+    plans, kinds, ins, outs = [], [], [], []
+    for wl in jobs:
+        sn, w = M.node_samples(wl)
+        p = M.Plan(c, torch.from_numpy(wl.H0).cuda(), torch.from_numpy(wl.Hk).cuda(), M.MG_PREC_SPLIT, 6)
+        p.set_controls(wl.N, wl.P, wl.t0, wl.dt, w, torch.from_numpy(sn).cuda())
+        plans.append(p)
+        kinds.append(M.MG_OUT_STATE)
+        ins.append(torch.from_numpy(wl.psi0).cuda())
+        outs.append(torch.empty(wl.d, dtype=torch.complex128, device="cuda"))
+    graph = M.BatchGraph(c, plans, kinds, ins, outs)
+    try:
+        for rep in range(2):
+            for o in outs:
+                o.fill_(float("nan"))
+            torch.cuda.synchronize()
+            assert graph.launch() == [0] * len(jobs)
+            for rec in g["jobs"]:
+                q = rec["index"]
+                ref = np.array([complex(a, b) for a, b in rec["psi"]])
+                err = float(np.abs(outs[q].cpu().numpy() - ref).max())
+                assert err <= 1e-6, (rep, q, err)
+    finally:
+        graph.close()
+        for p in plans:
+            p.close()
+        c.close()
