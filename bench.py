@@ -59,6 +59,12 @@ def parse():
     ap.add_argument("--rate", type=float, default=200.0,
                     help="config 4: offered request rate (the Poisson stream's arrival times are stretched "
                          "from 200/s to this rate; the requests themselves are unchanged)")
+    ap.add_argument("--peaks", action="store_true",
+                    help="measure the FP64 and TF32 matrix-product peaks with torch.matmul (CUDA events, best "
+                         "of 10) and print them")
+    ap.add_argument("--tune", action="store_true",
+                    help="run the autotuner (mg_plan_autotune) on the d = 30, d = 729 and a 512-batch instance "
+                         "workload and print every measured candidate")
     ap.add_argument("--graph", action="store_true",
                     help="config 2: the batch captured once in a CUDA graph (mg_batch_graph_*) and replayed "
                          "every step")
@@ -544,6 +550,78 @@ def run_config(args):
 
 
 # ----------------------------------------------------------------------------
+# FP64 and TF32 peaks (torch.matmul), for the fractions of the FP64 and TF32 paths
+# ----------------------------------------------------------------------------
+def run_peaks(args):
+    import torch
+    out = {}
+    for name, dtype, tf32, n in (("fp64", torch.float64, False, 8192), ("tf32", torch.float32, True, 8192),
+                                 ("bf16", torch.bfloat16, False, 8192)):
+        torch.backends.cuda.matmul.allow_tf32 = tf32
+        a = torch.randn(n, n, device="cuda", dtype=dtype)
+        b = torch.randn(n, n, device="cuda", dtype=dtype)
+        for _ in range(3):
+            torch.matmul(a, b)
+        torch.cuda.synchronize()
+        best = 1e30
+        for _ in range(10):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            torch.matmul(a, b)
+            e1.record()
+            e1.synchronize()
+            best = min(best, e0.elapsed_time(e1))
+        out[f"{name}_tflops"] = 2.0 * n ** 3 / (best * 1e-3) / 1e12
+        del a, b
+    torch.backends.cuda.matmul.allow_tf32 = False
+    out["how"] = "torch.matmul n = 8192 (2 n^3 flops), best of 10 after 3 warm-up, CUDA events"
+    out["gpu"] = torch.cuda.get_device_name(0)
+    print(json.dumps(out), flush=True)
+
+
+# ----------------------------------------------------------------------------
+# the autotuner's measured tables
+# ----------------------------------------------------------------------------
+def run_tune(args):
+    import tempfile
+
+    import torch
+
+    import workloads as W
+    from paper_2411_09982_gb300 import build as B
+    from paper_2411_09982_gb300 import magnus as M
+
+    B.build()
+    M.load()
+    ctx = M.Context(0, torch.cuda.Stream())
+    cases = [(W.config(0), M.MG_OUT_STATE, 1e-11), (W.config(0), M.MG_OUT_STATE, 1e-6),
+             (W.config(1), M.MG_OUT_PROPAGATOR, 1e-6), (W.config(1), M.MG_OUT_PROPAGATOR, 1e-4),
+             (W.uneven_batch()[0], M.MG_OUT_STATE, 1e-6)]
+    names = {(0, 0): "fp64", (1, 0): "split"}
+    for wl, output, tol in cases:
+        fd, path = tempfile.mkstemp(suffix=".txt")
+        os.close(fd)
+        os.unlink(path)
+        sn, w = M.node_samples(wl)
+        plan = M.Plan(ctx, torch.from_numpy(wl.H0).cuda(), torch.from_numpy(wl.Hk).cuda(), M.MG_PREC_SPLIT, 6)
+        plan.set_controls(wl.N, wl.P, wl.t0, wl.dt, w, torch.from_numpy(sn).cuda())
+        chosen = plan.autotune(output, tol, path)
+        key, sel, ents = open(path).read().strip().split("\t")
+        table = []
+        for e in ents.split(";"):
+            p, s_, t, a, err, us = e.split()
+            table.append({"path": "action" if int(a) else names[(int(p), 0)], "digits": int(s_) or None,
+                          "taylor": "ps" if int(t) else "deg18", "error_est": float(err),
+                          "us_per_interval": float(us)})
+        print(json.dumps({"workload": wl.name, "d": wl.d, "N": wl.N, "output": "state" if output == 0 else "U",
+                          "tolerance": tol, "key": key, "selected": int(sel), "chosen": chosen,
+                          "candidates": table}), flush=True)
+        plan.close()
+        os.unlink(path)
+    ctx.close()
+
+
+# ----------------------------------------------------------------------------
 # reference arm: the CPU FP64 oracle, timed on the host cores (rank 0 only)
 # ----------------------------------------------------------------------------
 def run_reference(args):
@@ -580,6 +658,10 @@ if __name__ == "__main__":
     a = parse()
     if a.impl == "reference":
         run_reference(a)
+    elif a.tune:
+        run_tune(a)
+    elif a.peaks:
+        run_peaks(a)
     elif a.config != 1:
         run_config(a)
     else:

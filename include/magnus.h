@@ -69,6 +69,13 @@ extern "C" {
  *   the trace phases, the state chain and re-orthonormalisation run in FP64. */
 #define MG_PREC_FP64   0
 #define MG_PREC_SPLIT  1
+/* mg_job only: the server looks the job's configuration up in its context's
+ * tuning cache (mg_ctx_set_tune_cache; see mg_plan_autotune). */
+#define MG_PREC_AUTO   2
+
+/* Taylor scheme of the exponential (mg_plan_set_taylor, tuning entries). */
+#define MG_TAYLOR_AUTO 0  /* split precision may take degree 18 in five products */
+#define MG_TAYLOR_PS   1  /* Paterson-Stockmeyer degrees only */
 
 /* ---- outputs --------------------------------------------------------------- */
 #define MG_OUT_STATE       0  /* psi(T) = U_{N-1} ... U_0 psi0            */
@@ -239,6 +246,56 @@ int mg_evolve(mg_plan* plan, int output, const double* in, double* out, int reor
 int mg_evolve_batch(mg_ctx* ctx, int n, mg_plan* const* plans, const int* outputs, const double* const* in,
                     double* const* out, int reorth_every, int flags, int* job_status);
 
+/* ---- autotuning ------------------------------------------------------------ */
+/* One way of evolving a job and what it measured: the arithmetic of the matrix
+ * products (precision, slices), the Taylor scheme (MG_TAYLOR_*), for state
+ * outputs the action-based path (action = 1), the estimated max-abs error over
+ * the job's N intervals and the device time per interval in microseconds. */
+typedef struct mg_tune_entry {
+  int32_t precision;
+  int32_t slices;
+  int32_t taylor;
+  int32_t action;
+  double error;
+  double us_per_interval;
+} mg_tune_entry;
+
+/* Host only: the index of the fastest entry whose error times `safety` (>= 1)
+ * is at most `tolerance` (> 0).  MG_EUNSUPPORTED when none qualifies. */
+int mg_tune_select(int n, const mg_tune_entry* entries, double tolerance, double safety, int* index);
+/* Host only: append a tuning (key, all measured entries, the selected one) to
+ * the cache file at `path` (created if absent; appends are serialised with a
+ * file lock).  Keys contain no tab, newline or ';'. */
+int mg_tune_cache_store(const char* path, const char* key, int n, const mg_tune_entry* entries, int selected);
+/* Host only: the selected entry of the last tuning stored under `key` -- the key
+ * itself, or a longer key that continues it after a '|' (so a caller that knows
+ * only the leading fields of a key finds the latest tuning of that family).
+ * MG_EAGAIN when the file or the key is absent. */
+int mg_tune_cache_lookup(const char* path, const char* key, mg_tune_entry* entry);
+
+/* Choose, by measurement on this GPU, how `plan` evolves `output`
+ * (MG_OUT_STATE or MG_OUT_PROPAGATOR) within max-abs `tolerance`, and set it on
+ * the plan (precision, slices, Taylor scheme, MG_FLAG_STATE_ACTION).  The
+ * controls must be set.  The cache at `cache_path` (may be NULL: no cache) is
+ * consulted first under the key
+ *   gpu=<name>|d=<d>|K=<K>|out=<output>|tol=<tolerance>|nu=<e>|N=<n>
+ * with nu = the binary exponent of the largest bound on ||Hbar_n - tau_n I||_1
+ * and N the interval count rounded up to a power of two.  On a miss every
+ * candidate -- FP64; split with 4..7 digits, each with and without the
+ * degree-18 scheme; for states the action path -- evolves the plan's first
+ * n_probe <= 64 intervals; the reference is the FP64 path (the most accurate
+ * split candidate for d > 1024, where FP64 products are slow); a candidate's
+ * error is its deviation from the reference times N / n_probe (errors of
+ * near-identical intervals add up), FP64's own u nu N; the fastest candidate
+ * within tolerance / 4 is taken and the whole table is stored.  chosen (may be
+ * NULL) receives it.  MG_EUNSUPPORTED when no candidate qualifies (the plan is
+ * left unchanged). */
+int mg_plan_autotune(mg_plan* plan, int output, double tolerance, const char* cache_path, mg_tune_entry* chosen);
+/* Taylor scheme of a plan (MG_TAYLOR_AUTO, the default, or MG_TAYLOR_PS). */
+int mg_plan_set_taylor(mg_plan* plan, int taylor);
+/* Tuning cache of a context's servers (NULL: none); see MG_PREC_AUTO. */
+int mg_ctx_set_tune_cache(mg_ctx* ctx, const char* path);
+
 /* ---- a batch captured once, replayed many times ------------------------------ */
 /* mg_evolve_batch issues every launch of a batch without reading anything back to
  * the host between them: the Taylor degree m and the number S of squaring
@@ -304,13 +361,15 @@ typedef struct mg_job {
   int output;               /* MG_OUT_STATE (in = psi0) or MG_OUT_PROPAGATOR (in must be NULL) */
   const double* in;
   double* out;              /* written when the job completes; keep it valid until mg_wait returns */
-  int precision, slices;
+  int precision, slices;    /* MG_PREC_AUTO: the latest tuning of the context's cache under
+                               gpu|d|K|out|tol (tolerance below); on a miss split, 6 digits */
   int flags;                /* MG_FLAG_HOST_PTRS: H0, Hk, samples, in and out are host memory;
                                MG_FLAG_STATE_ACTION: a state job of d >= 256 runs on the
                                action-based path (FP64; precision and slices are ignored) on one
                                of the server's action streams, concurrently with the chunk steps
                                of the other jobs; smaller flagged jobs, which finish sooner in the
                                shared chunk steps, stay there */
+  double tolerance;         /* MG_PREC_AUTO only: the max-abs error the job was tuned for */
 } mg_job;
 
 typedef struct mg_job_report {

@@ -126,6 +126,7 @@ struct mg_ctx {
   int stall_test = 0;
   // algorithmic work of predicated squaring launches, added on the device (timing on)
   double* dev_flops = nullptr;
+  std::string tune_cache;   // tuning cache consulted by servers for MG_PREC_AUTO jobs
 };
 
 struct mg_plan {
@@ -156,6 +157,7 @@ struct mg_plan {
   // the exponents' norms in the batched path), once formed
   std::vector<double> opnorm;
   int opnorm_dp = 0;
+  int taylor_mode = MG_TAYLOR_AUTO;   // MG_TAYLOR_PS: Paterson-Stockmeyer degrees only
 };
 
 namespace {
@@ -344,6 +346,8 @@ struct Engine {
   // multiplied (per-interval squaring counts; see expm_chunk_dev)
   const int* item_sq = nullptr;
   int sq_step = 0;
+  int taylor_mode = MG_TAYLOR_AUTO;   // MG_TAYLOR_PS: no degree-18 scheme
+  bool allow18() const { return prec == MG_PREC_SPLIT && taylor_mode != MG_TAYLOR_PS; }
   SplitCtl ctl() const {
     SplitCtl c;
     c.wait_ns = ctx->wait_ns;
@@ -581,7 +585,7 @@ int expm_chunk(mg_ctx* ctx, Engine& eng, int batch, double* W, const double* tau
     nmax = std::max(nmax, nrm[b]);
   }
   const double u = unit_roundoff(eng.prec, eng.L, d);
-  TaylorChoice tc = choose_taylor(nmax, u, eng.prec == MG_PREC_SPLIT);
+  TaylorChoice tc = choose_taylor(nmax, u, eng.allow18());
   if (st) {
     st->m = tc.m;
     st->s_applied = tc.s;
@@ -792,11 +796,14 @@ int ensure_csr(mg_plan* p) {
   const int d = p->d, nops = 1 + p->Kx;
   const size_t dd = (size_t)d * d;
   std::vector<double> dense((size_t)nops * 2 * dd);
+  // ordered after the operator uploads on the context's stream (which need not
+  // synchronise with the legacy stream)
   for (int op = 0; op < nops; ++op) {
     const double* src = op == 0 ? p->H0 : p->Hk + (size_t)(op - 1) * 2 * dd;
-    MG_CUDA_TRY(cudaMemcpy(dense.data() + (size_t)op * 2 * dd, src, sizeof(double) * 2 * dd,
-                           cudaMemcpyDeviceToHost));
+    MG_CUDA_TRY(cudaMemcpyAsync(dense.data() + (size_t)op * 2 * dd, src, sizeof(double) * 2 * dd,
+                                cudaMemcpyDeviceToHost, p->ctx->stream));
   }
+  MG_CUDA_TRY(cudaStreamSynchronize(p->ctx->stream));
   CsrHost h;
   build_csr_host(dense.data(), d, nops, h);
   auto up = [&](void** dst, const void* src, size_t bytes) -> int {
@@ -1014,6 +1021,19 @@ int lagrange_triangle(int P, std::vector<double>& mrc) {
 }
 }  // namespace
 
+// Leading fields of a tuning-cache key: the GPU, the problem's shape, the output and
+// the tolerance (mg_plan_autotune appends the norm and interval-count buckets).
+int tune_key_prefix(mg_ctx* ctx, int d, int K, int output, double tol, std::string* key) {
+  cudaDeviceProp prop;
+  MG_CUDA_TRY(cudaGetDeviceProperties(&prop, ctx->device));
+  char buf[512];
+  std::snprintf(buf, sizeof(buf), "gpu=%s|d=%d|K=%d|out=%d|tol=%.3g", prop.name, d, K, output, tol);
+  for (char* c = buf; *c; ++c)
+    if (*c == '\t' || *c == '\n' || *c == ';') *c = ' ';
+  *key = buf;
+  return MG_OK;
+}
+
 // ---------------------------------------------------------------------------
 // C ABI
 // ---------------------------------------------------------------------------
@@ -1125,7 +1145,8 @@ int mg_ctx_gemm_stats(mg_ctx* ctx, int64_t* launches, double* ms, double* flops,
   ctx->ev_pending.clear();
   ctx->ev_next = 0;
   double dflops = 0.0;   // work of the predicated (per-item) squaring launches
-  MG_CUDA_TRY(cudaMemcpy(&dflops, ctx->dev_flops, sizeof(double), cudaMemcpyDeviceToHost));
+  MG_CUDA_TRY(cudaMemcpyAsync(&dflops, ctx->dev_flops, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  MG_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
   if (launches) *launches = ctx->t_launches;
   if (ms) *ms = ctx->t_ms;
   if (flops) *flops = ctx->t_flops + dflops;
@@ -1133,7 +1154,8 @@ int mg_ctx_gemm_stats(mg_ctx* ctx, int64_t* launches, double* ms, double* flops,
     ctx->t_launches = 0;
     ctx->t_ms = 0.0;
     ctx->t_flops = 0.0;
-    MG_CUDA_TRY(cudaMemset(ctx->dev_flops, 0, sizeof(double)));
+    MG_CUDA_TRY(cudaMemsetAsync(ctx->dev_flops, 0, sizeof(double), ctx->stream));
+    MG_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
   }
   return MG_OK;
 }
@@ -1260,7 +1282,9 @@ int mg_plan_create(mg_ctx* ctx, mg_plan** out, int d, int K, const double* H0, c
     for (int k = 0; r == MG_OK && k <= K; ++k) {
       const double* H = k == 0 ? p->H0 : p->Hk + (k - 1) * mat_doubles(d);
       r = launch_hermitian_defect(d, 1, H, reinterpret_cast<unsigned long long*>(sc), ctx->stream);
-      if (r == MG_OK && cudaMemcpy(hb, sc, sizeof(hb), cudaMemcpyDeviceToHost) != cudaSuccess) r = MG_ECUDA;
+      if (r == MG_OK && (cudaMemcpyAsync(hb, sc, sizeof(hb), cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess ||
+                         cudaStreamSynchronize(ctx->stream) != cudaSuccess))
+        r = MG_ECUDA;
       if (r == MG_OK) {
         double dm, hm;
         memcpy(&dm, &hb[0], 8);
@@ -1578,6 +1602,7 @@ int mg_evolve(mg_plan* p, int output, const double* in, double* out, int reorth_
     MG_CUDA_TRY(cudaEventRecord(ctx->ev0, s));
   }
   Engine eng{ctx, d, p->precision, p->L};
+  eng.taylor_mode = p->taylor_mode;
   PropState ps;
   ps.output = output;
   ps.d = d;
@@ -1948,7 +1973,7 @@ struct ChunkPlan {
 };
 
 struct GroupProgram {
-  int dp = 0, prec = MG_PREC_FP64, L = 6, reorth = 0;
+  int dp = 0, prec = MG_PREC_FP64, L = 6, reorth = 0, taylor = MG_TAYLOR_AUTO;
   std::vector<BatchJob> jobs;
   std::vector<mg_plan*> plans;
   TaylorChoice tc{};
@@ -2179,7 +2204,7 @@ int build_program(mg_ctx* ctx, GroupProgram& G) {
   MG_TRY(norm_bounds(ctx, G.jobs, G.plans, dp, bound));
   G.bound = 0.0;
   for (double b : bound) G.bound = std::max(G.bound, b);
-  G.tc = choose_taylor(G.bound, unit_roundoff(G.prec, G.L, dp), G.prec == MG_PREC_SPLIT);
+  G.tc = choose_taylor(G.bound, unit_roundoff(G.prec, G.L, dp), G.prec == MG_PREC_SPLIT && G.taylor != MG_TAYLOR_PS);
   G.S = G.tc.s;
   return MG_OK;
 }
@@ -2325,6 +2350,7 @@ int issue_group(mg_ctx* ctx, GroupProgram& G, const double* const* in, double* c
   const int dp = G.dp;
   const long long md = mat_doubles(dp);
   Engine eng{ctx, dp, G.prec, G.L};
+  eng.taylor_mode = G.taylor;
   MG_CUDA_TRY(cudaMemsetAsync(G.job_fail, 0, sizeof(int) * G.jobs.size(), s));
   MG_CUDA_TRY(cudaMemsetAsync(G.overflow, 0, sizeof(int), s));
   for (BatchJob& j : G.jobs) {
@@ -2354,8 +2380,10 @@ int issue_group(mg_ctx* ctx, GroupProgram& G, const double* const* in, double* c
 int collect_group(mg_ctx* ctx, GroupProgram& G, int* job_status) {
   std::vector<int> fail(G.jobs.size());
   int over = 0;
-  MG_CUDA_TRY(cudaMemcpy(fail.data(), G.job_fail, sizeof(int) * fail.size(), cudaMemcpyDeviceToHost));
-  MG_CUDA_TRY(cudaMemcpy(&over, G.overflow, sizeof(int), cudaMemcpyDeviceToHost));
+  MG_CUDA_TRY(cudaMemcpyAsync(fail.data(), G.job_fail, sizeof(int) * fail.size(), cudaMemcpyDeviceToHost,
+                              ctx->stream));
+  MG_CUDA_TRY(cudaMemcpyAsync(&over, G.overflow, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  MG_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
   if (job_status)
     for (size_t q = 0; q < G.jobs.size(); ++q) job_status[G.jobs[q].idx] = fail[q] ? MG_ENONFINITE : MG_OK;
   if (over) {
@@ -2374,8 +2402,10 @@ int mg_evolve_batch(mg_ctx* ctx, int n, mg_plan* const* plans, const int* output
   MG_CUDA_TRY(cudaSetDevice(ctx->device));
   // group by (precision, digits, padded dimension); one group at a time
   struct Key {
-    int prec, L, dp;
-    bool operator<(const Key& o) const { return prec != o.prec ? prec < o.prec : (L != o.L ? L < o.L : dp < o.dp); }
+    int prec, L, dp, taylor;
+    bool operator<(const Key& o) const {
+      return prec != o.prec ? prec < o.prec : (L != o.L ? L < o.L : (dp != o.dp ? dp < o.dp : taylor < o.taylor));
+    }
   };
   struct Item { Key k; BatchJob j; mg_plan* p; };
   std::vector<Item> all;
@@ -2392,7 +2422,7 @@ int mg_evolve_batch(mg_ctx* ctx, int n, mg_plan* const* plans, const int* output
     j.dt = p->dt;
     j.c = p->c;
     const int L = p->precision == MG_PREC_SPLIT ? p->L : 0;
-    all.push_back({Key{p->precision, L, round_dim(p->d)}, j, p});
+    all.push_back({Key{p->precision, L, round_dim(p->d), p->taylor_mode}, j, p});
   }
   // state jobs of action-flagged plans: every one in a single launch, one CTA per job
   {
@@ -2451,6 +2481,7 @@ int mg_evolve_batch(mg_ctx* ctx, int n, mg_plan* const* plans, const int* output
     G.prec = k.prec;
     G.L = k.L == 0 ? 6 : k.L;
     G.reorth = reorth_every;
+    G.taylor = k.taylor;
     while (g1 < all.size() && !(all[g0].k < all[g1].k) && !(all[g1].k < all[g0].k)) {
       G.jobs.push_back(all[g1].j);
       G.plans.push_back(all[g1].p);
@@ -2539,8 +2570,10 @@ int mg_batch_graph_create(mg_ctx* ctx, int n, mg_plan* const* plans, const int* 
   }
   MG_CUDA_TRY(cudaSetDevice(ctx->device));
   struct Key {
-    int prec, L, dp;
-    bool operator<(const Key& o) const { return prec != o.prec ? prec < o.prec : (L != o.L ? L < o.L : dp < o.dp); }
+    int prec, L, dp, taylor;
+    bool operator<(const Key& o) const {
+      return prec != o.prec ? prec < o.prec : (L != o.L ? L < o.L : (dp != o.dp ? dp < o.dp : taylor < o.taylor));
+    }
   };
   struct Item { Key k; BatchJob j; mg_plan* p; };
   std::vector<Item> all;
@@ -2569,7 +2602,7 @@ int mg_batch_graph_create(mg_ctx* ctx, int n, mg_plan* const* plans, const int* 
     j.N = p->N;
     j.dt = p->dt;
     j.c = p->c;
-    all.push_back({Key{p->precision, p->precision == MG_PREC_SPLIT ? p->L : 0, round_dim(p->d)}, j, p});
+    all.push_back({Key{p->precision, p->precision == MG_PREC_SPLIT ? p->L : 0, round_dim(p->d), p->taylor_mode}, j, p});
     g->plans.push_back(p);
     g->c_ptr.push_back(p->c);
     g->N.push_back(p->N);
@@ -2590,6 +2623,7 @@ int mg_batch_graph_create(mg_ctx* ctx, int n, mg_plan* const* plans, const int* 
     G->prec = k.prec;
     G->L = k.L == 0 ? 6 : k.L;
     G->reorth = reorth_every;
+    G->taylor = k.taylor;
     while (g1 < all.size() && !(all[g0].k < all[g1].k) && !(all[g1].k < all[g0].k)) {
       G->jobs.push_back(all[g1].j);
       G->plans.push_back(all[g1].p);
@@ -2697,7 +2731,7 @@ using clk = std::chrono::steady_clock;
 struct SJob {
   uint64_t id = 0;
   BatchJob b;
-  int dp = 0, prec = 0, L = 6;
+  int dp = 0, prec = 0, L = 6, taylor = MG_TAYLOR_AUTO;
   double* out = nullptr;
   cudaMemcpyKind out_kind = cudaMemcpyDeviceToDevice;
   std::vector<void*> owned;     // device buffers of this job (stream-ordered allocations)
@@ -2926,13 +2960,15 @@ void server_loop(mg_server* srv) {
           }
         }
         for (SJob* j : srv->active)
-          if (j->dp == head->dp && j->prec == head->prec && j->L == head->L && (int)group.size() < srv->seg_cap)
+          if (j->dp == head->dp && j->prec == head->prec && j->L == head->L && j->taylor == head->taylor &&
+              (int)group.size() < srv->seg_cap)
             group.push_back(j);
       }
     }
     if (group.empty()) continue;
     const auto t0 = clk::now();
     Engine eng{ctx, group[0]->dp, group[0]->prec, group[0]->L};
+    eng.taylor_mode = group[0]->taylor;
     int rc = MG_OK;
     for (SJob* j : group) cudaStreamWaitEvent(ctx->stream, j->ready, 0);
     const int chunk = chunk_size(ctx, eng.d, eng.prec, eng.L, 1 << 30, 1);
@@ -3194,8 +3230,30 @@ int submit_action(mg_server* srv, const mg_job* job, uint64_t* job_id) {
 }
 }  // namespace
 
-int mg_submit(mg_server* srv, const mg_job* job, uint64_t* job_id) {
-  if (!srv || !job || !job_id) return MG_EINVAL;
+int mg_submit(mg_server* srv, const mg_job* job_in, uint64_t* job_id) {
+  if (!srv || !job_in || !job_id) return MG_EINVAL;
+  mg_job resolved = *job_in;
+  const mg_job* job = &resolved;
+  int taylor = MG_TAYLOR_AUTO;
+  if (resolved.precision == MG_PREC_AUTO) {
+    // the latest tuning of this job's family in the context's cache; split, 6 digits on a miss
+    mg_tune_entry e{};
+    std::string key;
+    int rk = tune_key_prefix(srv->ctx, resolved.d, resolved.K, resolved.output, resolved.tolerance, &key);
+    if (rk == MG_OK && !srv->ctx->tune_cache.empty() &&
+        mg_tune_cache_lookup(srv->ctx->tune_cache.c_str(), key.c_str(), &e) == MG_OK) {
+      resolved.precision = e.precision;
+      resolved.slices = e.slices;
+      taylor = e.taylor;
+      if (resolved.output == MG_OUT_STATE) {
+        if (e.action) resolved.flags |= MG_FLAG_STATE_ACTION;
+        else resolved.flags &= ~MG_FLAG_STATE_ACTION;
+      }
+    } else {
+      resolved.precision = MG_PREC_SPLIT;
+      resolved.slices = 6;
+    }
+  }
   const int d = job->d, K = job->K, N = job->N, P = job->P;
   if (d < 1 || d > 4096 || K < 0 || K > 64 || N < 1 || P < 1 || P > 64 || !job->H0 || (K > 0 && !job->Hk) ||
       !job->w || (K > 0 && !job->samples) || !job->out || !(job->dt > 0.0) ||
@@ -3227,6 +3285,7 @@ int mg_submit(mg_server* srv, const mg_job* job, uint64_t* job_id) {
   j->dp = dp;
   j->prec = job->precision;
   j->L = job->precision == MG_PREC_SPLIT ? job->slices : 6;
+  j->taylor = taylor;
   j->out = job->out;
   const bool host = (job->flags & MG_FLAG_HOST_PTRS) != 0;
   j->out_kind = host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
@@ -3380,6 +3439,159 @@ int mg_server_destroy(mg_server* srv) {
   for (int q = 0; q < SERVER_ACTION_STREAMS; ++q) cudaStreamDestroy(srv->astream[q]);
   cudaStreamDestroy(srv->upload);
   delete srv;
+  return MG_OK;
+}
+
+int mg_plan_set_taylor(mg_plan* p, int taylor) {
+  if (!p || (taylor != MG_TAYLOR_AUTO && taylor != MG_TAYLOR_PS)) return MG_EINVAL;
+  p->taylor_mode = taylor;
+  return MG_OK;
+}
+
+int mg_ctx_set_tune_cache(mg_ctx* ctx, const char* path) {
+  if (!ctx) return MG_EINVAL;
+  ctx->tune_cache = path ? path : "";
+  return MG_OK;
+}
+
+namespace {
+
+void apply_tuning(mg_plan* p, int output, const mg_tune_entry& e) {
+  p->precision = e.precision;
+  if (e.precision == MG_PREC_SPLIT) p->L = e.slices;
+  p->taylor_mode = e.taylor;
+  if (output == MG_OUT_STATE) {
+    if (e.action) p->flags |= MG_FLAG_STATE_ACTION;
+    else p->flags &= ~MG_FLAG_STATE_ACTION;
+  }
+}
+
+}  // namespace
+
+int mg_plan_autotune(mg_plan* p, int output, double tolerance, const char* cache_path, mg_tune_entry* chosen) {
+  if (!p || p->N < 1 || !(tolerance > 0.0) || (output != MG_OUT_STATE && output != MG_OUT_PROPAGATOR))
+    return MG_EINVAL;
+  mg_ctx* ctx = p->ctx;
+  MG_CUDA_TRY(cudaSetDevice(ctx->device));
+  const int d = p->d;
+  // the largest bound on ||Hbar_n - tau_n I||_1 over the plan's intervals
+  std::vector<BatchJob> jv(1);
+  jv[0].d = d;
+  jv[0].K = p->Kx;
+  jv[0].N = p->N;
+  jv[0].dt = p->dt;
+  jv[0].c = p->c;
+  jv[0].H0 = p->H0;
+  jv[0].Hk = p->Hk;
+  std::vector<mg_plan*> pv{p};
+  std::vector<double> bound;
+  MG_TRY(norm_bounds(ctx, jv, pv, d, bound));
+  const double nu = bound[0];
+  int nb = 1;
+  while (nb < p->N) nb *= 2;
+  std::string key;
+  MG_TRY(tune_key_prefix(ctx, d, p->Kx, output, tolerance, &key));
+  key += "|nu=" + std::to_string(nu > 0.0 ? std::ilogb(nu) + 1 : 0) + "|N=" + std::to_string(nb);
+  mg_tune_entry hit{};
+  if (cache_path && mg_tune_cache_lookup(cache_path, key.c_str(), &hit) == MG_OK) {
+    apply_tuning(p, output, hit);
+    if (chosen) *chosen = hit;
+    return MG_OK;
+  }
+  // candidates
+  std::vector<mg_tune_entry> cand;
+  const bool fp64_ok = d <= 1024;   // above, FP64 products take seconds per interval
+  if (fp64_ok) cand.push_back(mg_tune_entry{MG_PREC_FP64, 0, MG_TAYLOR_PS, 0, 0.0, 0.0});
+  for (int L = 4; L <= 7; ++L)
+    for (int t : {MG_TAYLOR_AUTO, MG_TAYLOR_PS}) cand.push_back(mg_tune_entry{MG_PREC_SPLIT, L, t, 0, 0.0, 0.0});
+  if (output == MG_OUT_STATE && check_action_limits(d, 1 + p->Kx) == MG_OK)
+    cand.push_back(mg_tune_entry{MG_PREC_FP64, 0, MG_TAYLOR_PS, 1, 0.0, 0.0});
+  const int n_probe = std::min(p->N, d > 1024 ? 8 : 64);
+  const int saveN = p->N, savePrec = p->precision, saveL = p->L, saveFlags = p->flags, saveT = p->taylor_mode;
+  const long long outn = output == MG_OUT_STATE ? 2LL * d : mat_doubles(d);
+  double *ref = nullptr, *out = nullptr, *in = nullptr, *dmax = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  int rc = MG_OK;
+  if (cudaMalloc(&ref, sizeof(double) * outn) != cudaSuccess || cudaMalloc(&out, sizeof(double) * outn) != cudaSuccess ||
+      cudaMalloc(&in, sizeof(double) * 2 * d) != cudaSuccess || cudaMalloc(&dmax, sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    set_last_message("device allocation failed (autotune)");
+    rc = MG_ENOMEM;
+  }
+  if (rc == MG_OK && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)) rc = MG_ECUDA;
+  if (rc == MG_OK) {
+    // psi0 = |0> for state outputs (a basis state, as the workloads start from)
+    std::vector<double> h(2 * d, 0.0);
+    h[0] = 1.0;
+    if (cudaMemcpyAsync(in, h.data(), sizeof(double) * 2 * d, cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess ||
+        cudaStreamSynchronize(ctx->stream) != cudaSuccess)
+      rc = MG_ECUDA;
+  }
+  p->N = n_probe;
+  auto run = [&](const mg_tune_entry& e, double* dst, double* us) -> int {
+    mg_tune_entry f = e;
+    apply_tuning(p, output, f);
+    const double* src = output == MG_OUT_STATE ? in : nullptr;
+    MG_TRY(mg_evolve(p, output, src, dst, 0, 0, nullptr));   // first call sizes the workspace
+    MG_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    MG_CUDA_TRY(cudaEventRecord(e0, ctx->stream));
+    MG_TRY(mg_evolve(p, output, src, dst, 0, 0, nullptr));
+    MG_CUDA_TRY(cudaEventRecord(e1, ctx->stream));
+    MG_CUDA_TRY(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    MG_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+    *us = 1000.0 * ms / n_probe;
+    return MG_OK;
+  };
+  const double scale = (double)saveN / n_probe;
+  if (rc == MG_OK) {
+    // reference: the FP64 path, or above d = 1024 the most accurate split candidate
+    double us = 0.0;
+    mg_tune_entry r = fp64_ok ? cand[0] : mg_tune_entry{MG_PREC_SPLIT, 8, MG_TAYLOR_PS, 0, 0.0, 0.0};
+    rc = run(r, ref, &us);
+    if (rc == MG_OK && fp64_ok) {
+      cand[0].us_per_interval = us;
+      // FP64's own rounding: u per unit of phase per interval (the oracle and an independent
+      // Pade evolution differ by at most 1.3 u |Hbar|_1 N on the long-interval test jobs)
+      cand[0].error = std::ldexp(1.0, -53) * nu * saveN;
+    }
+  }
+  for (size_t q = fp64_ok ? 1 : 0; q < cand.size() && rc == MG_OK; ++q) {
+    double us = 0.0;
+    int r = run(cand[q], out, &us);
+    if (r == MG_EUNSUPPORTED || r == MG_ENONFINITE) {   // a candidate the job cannot take
+      cand[q].error = NAN;
+      cand[q].us_per_interval = NAN;
+      continue;
+    }
+    rc = r;
+    if (rc != MG_OK) break;
+    double err = 0.0;
+    rc = launch_max_abs_diff(outn, out, ref, dmax, ctx->stream);
+    // on the context's stream (which need not synchronise with the legacy stream)
+    if (rc == MG_OK && cudaMemcpyAsync(&err, dmax, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess)
+      rc = MG_ECUDA;
+    if (rc == MG_OK && cudaStreamSynchronize(ctx->stream) != cudaSuccess) rc = MG_ECUDA;
+    cand[q].error = err * scale;
+    cand[q].us_per_interval = us;
+  }
+  p->N = saveN;
+  p->precision = savePrec;
+  p->L = saveL;
+  p->flags = saveFlags;
+  p->taylor_mode = saveT;
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFree(ref);
+  cudaFree(out);
+  cudaFree(in);
+  cudaFree(dmax);
+  if (rc != MG_OK) return rc;
+  int idx = -1;
+  MG_TRY(mg_tune_select((int)cand.size(), cand.data(), tolerance, 4.0, &idx));
+  if (cache_path) MG_TRY(mg_tune_cache_store(cache_path, key.c_str(), (int)cand.size(), cand.data(), idx));
+  apply_tuning(p, output, cand[idx]);
+  if (chosen) *chosen = cand[idx];
   return MG_OK;
 }
 

@@ -146,6 +146,29 @@ int launch_copy_active(int batch, long long md, const double* src, double* dst, 
   return check_launch("copy_active_kernel");
 }
 
+// *out = max |a_e - b_e| over n doubles (out preset to 0; non-negative doubles order as integers)
+__global__ void max_abs_diff_kernel(long long n, const double* __restrict__ a, const double* __restrict__ b,
+                                    unsigned long long* __restrict__ out) {
+  double m = 0.0;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    const double v = fabs(a[e] - b[e]);
+    m = v > m || v != v ? v : m;   // a NaN difference wins (it marks a failed candidate)
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    const double w = __shfl_xor_sync(0xffffffffu, m, o);
+    m = w > m || w != w ? w : m;
+  }
+  if ((threadIdx.x & 31) == 0) atomicMax(out, (unsigned long long)__double_as_longlong(m));
+}
+
+int launch_max_abs_diff(long long n, const double* a, const double* b, double* out, cudaStream_t s) {
+  MG_CUDA_TRY(cudaMemsetAsync(out, 0, sizeof(double), s));
+  if (n <= 0) return MG_OK;
+  const int grid = (int)std::min<long long>((n + 255) / 256, 152 * 8);
+  max_abs_diff_kernel<<<grid, 256, 0, s>>>(n, a, b, reinterpret_cast<unsigned long long*>(out));
+  return check_launch("max_abs_diff_kernel");
+}
+
 __global__ void squarings_kernel(int n, const double* __restrict__ norm, double theta, int S, int uniform,
                                  int* __restrict__ sq, int* __restrict__ overflow, double* __restrict__ flops_acc,
                                  double flops_per_square) {

@@ -231,6 +231,8 @@ int launch_coef_absmax(int njobs, const CoefRef* refs_dev, double* out, cudaStre
 // job_fail[job] and seg_bad, zeroes the segment's norms, phases and exponents W
 int launch_fail_segments(int nseg, int fill, long long md, const int* seg_tab, const int* seg_of_item, double* norm,
                          double* tau, int* job_fail, int* seg_bad, double* W, cudaStream_t s);
+// *out = max |a_e - b_e| over n doubles (device; a NaN difference gives NaN)
+int launch_max_abs_diff(long long n, const double* a, const double* b, double* out, cudaStream_t s);
 // dst[b] = src[b] (md doubles each) for the items with item_sq[b] > sq_step
 int launch_copy_active(int batch, long long md, const double* src, double* dst, const int* item_sq, int sq_step,
                        cudaStream_t s);

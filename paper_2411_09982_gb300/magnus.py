@@ -26,6 +26,9 @@ MG_EUNSUPPORTED = -8
 
 MG_PREC_FP64 = 0
 MG_PREC_SPLIT = 1
+MG_PREC_AUTO = 2
+MG_TAYLOR_AUTO = 0
+MG_TAYLOR_PS = 1
 MG_OUT_STATE = 0
 MG_OUT_PROPAGATOR = 1
 MG_OUT_TRAJECTORY = 2
@@ -69,7 +72,16 @@ class mg_job(ctypes.Structure):
         ("w", ctypes.c_void_p), ("samples", ctypes.c_void_p),
         ("output", ctypes.c_int), ("input", ctypes.c_void_p), ("out", ctypes.c_void_p),
         ("precision", ctypes.c_int), ("slices", ctypes.c_int), ("flags", ctypes.c_int),
+        ("tolerance", ctypes.c_double),
     ]
+
+
+class mg_tune_entry(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int32), ("slices", ctypes.c_int32), ("taylor", ctypes.c_int32),
+                ("action", ctypes.c_int32), ("error", ctypes.c_double), ("us_per_interval", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class mg_job_report(ctypes.Structure):
@@ -105,6 +117,12 @@ SIGNATURES = {
     "mg_ctx_set_wait_limit": (_I, [_P, _D, _I]),
     "mg_ctx_gemm_stats": (_I, [_P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(_D), ctypes.POINTER(_D), _I]),
     "mg_cgemm_split_static": (_I, [_I, _P, _I, _I, _P, _P, _P, _I]),
+    "mg_tune_select": (_I, [_I, ctypes.POINTER(mg_tune_entry), _D, _D, ctypes.POINTER(_I)]),
+    "mg_tune_cache_store": (_I, [ctypes.c_char_p, ctypes.c_char_p, _I, ctypes.POINTER(mg_tune_entry), _I]),
+    "mg_tune_cache_lookup": (_I, [ctypes.c_char_p, ctypes.c_char_p, ctypes.POINTER(mg_tune_entry)]),
+    "mg_plan_autotune": (_I, [_P, _I, _D, ctypes.c_char_p, ctypes.POINTER(mg_tune_entry)]),
+    "mg_plan_set_taylor": (_I, [_P, _I]),
+    "mg_ctx_set_tune_cache": (_I, [_P, ctypes.c_char_p]),
     "mg_batch_graph_create": (_I, [_P, _I, _P, _P, _P, _P, _I, ctypes.POINTER(_P)]),
     "mg_batch_graph_launch": (_I, [_P, _P]),
     "mg_batch_graph_stats": (_I, [_P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
@@ -179,6 +197,9 @@ class Context:
     def enable_gemm_timing(self, on=True):
         _check(load().mg_ctx_enable_gemm_timing(self.h, 1 if on else 0), "mg_ctx_enable_gemm_timing")
 
+    def set_tune_cache(self, path):
+        _check(load().mg_ctx_set_tune_cache(self.h, path.encode() if path else None), "mg_ctx_set_tune_cache")
+
     def set_wait_limit(self, seconds=4.0, stall_test=False):
         _check(load().mg_ctx_set_wait_limit(self.h, float(seconds), 1 if stall_test else 0), "mg_ctx_set_wait_limit")
 
@@ -218,6 +239,17 @@ class Plan:
         _check(lib.mg_plan_create(ctx.h, ctypes.byref(h), self.d, self.K, _ptr(H0), _ptr(Hk_t), precision,
                                   slices, flags | (MG_FLAG_HOST_PTRS if host else 0)), "mg_plan_create")
         self.h = h
+
+    def autotune(self, output, tolerance, cache_path=None):
+        """Measure and set the fastest configuration within `tolerance` (mg_plan_autotune)."""
+        e = mg_tune_entry()
+        _check(load().mg_plan_autotune(self.h, output, float(tolerance),
+                                       cache_path.encode() if cache_path else None, ctypes.byref(e)),
+               "mg_plan_autotune")
+        return e.as_dict()
+
+    def set_taylor(self, taylor):
+        _check(load().mg_plan_set_taylor(self.h, int(taylor)), "mg_plan_set_taylor")
 
     def set_magnus_order(self, order):
         _check(load().mg_plan_set_magnus_order(self.h, int(order)), "mg_plan_set_magnus_order")
@@ -265,7 +297,7 @@ class Server:
         self._keep = {}
 
     def submit(self, H0, Hk, N, P, t0, dt, w, samples, output, inp, out, precision=MG_PREC_SPLIT, slices=6,
-               host=False, action=False):
+               host=False, action=False, tolerance=0.0):
         """Returns the job id, or None when the job is not admissible now (MG_EAGAIN).
         action=True runs a state job on the action-based path (MG_FLAG_STATE_ACTION)."""
         import numpy as np
@@ -274,7 +306,8 @@ class Server:
                    Hk.data_ptr() if Hk is not None else None, int(N), int(P), float(t0), float(dt),
                    w.ctypes.data_as(ctypes.c_void_p), samples.data_ptr() if samples is not None else None,
                    int(output), inp.data_ptr() if inp is not None else None, out.data_ptr(), int(precision),
-                   int(slices), (MG_FLAG_HOST_PTRS if host else 0) | (MG_FLAG_STATE_ACTION if action else 0))
+                   int(slices), (MG_FLAG_HOST_PTRS if host else 0) | (MG_FLAG_STATE_ACTION if action else 0),
+                   float(tolerance))
         jid = ctypes.c_uint64()
         r = load().mg_submit(self.h, ctypes.byref(j), ctypes.byref(jid))
         if r == MG_EAGAIN:
@@ -372,6 +405,37 @@ class BatchGraph:
             self.close()
         except Exception:
             pass
+
+
+def _entries(entries):
+    arr = (mg_tune_entry * len(entries))()
+    for i, e in enumerate(entries):
+        for k, _ in mg_tune_entry._fields_:
+            setattr(arr[i], k, e[k])
+    return arr
+
+
+def mg_tune_select(entries, tolerance, safety=4.0):
+    """Index of the fastest entry whose error x safety is within tolerance (host only)."""
+    idx = ctypes.c_int()
+    _check(load().mg_tune_select(len(entries), _entries(entries), float(tolerance), float(safety), ctypes.byref(idx)),
+           "mg_tune_select")
+    return idx.value
+
+
+def mg_tune_cache_store(path, key, entries, selected):
+    _check(load().mg_tune_cache_store(path.encode(), key.encode(), len(entries), _entries(entries), int(selected)),
+           "mg_tune_cache_store")
+
+
+def mg_tune_cache_lookup(path, key):
+    """The selected entry of the latest tuning under `key` (or a key continuing it), or None."""
+    e = mg_tune_entry()
+    r = load().mg_tune_cache_lookup(path.encode(), key.encode(), ctypes.byref(e))
+    if r == MG_EAGAIN:
+        return None
+    _check(r, "mg_tune_cache_lookup")
+    return e.as_dict()
 
 
 def mg_quadrature_nodes(P: int):
