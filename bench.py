@@ -38,6 +38,10 @@ SAMPLE_INTERVALS = 128          # oracle sample (cpu_baseline) and accuracy pref
 # valid for the kernel build it was captured from only, and is removed when the kernel changes.
 GEMM_DRAM_BYTES_PER_PRODUCT = {}
 REFERENCE_STEP_INTERVALS = 16   # oracle intervals per step of --impl reference
+# FP64 and TF32 dense matrix-product peaks of GB300 measured by `python bench.py --peaks`
+# (torch.matmul, n = 8192, best of 10, CUDA events); the BF16 peaks come from MEASURED_PEAKS.json
+FP64_TFLOPS_MEASURED = 1.10
+TF32_TFLOPS_MEASURED = 1024.0
 
 
 def parse():
@@ -51,6 +55,10 @@ def parse():
     ap.add_argument("--intervals", type=int, default=2000)
     ap.add_argument("--e2e-steps", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serving", action="store_true",
+                    help="default line: skip the served-stream measurement (p50/p99 on a prefix of the stream)")
+    ap.add_argument("--serve-requests", type=int, default=64,
+                    help="default line: requests of the served stream's prefix")
     ap.add_argument("--config", type=int, default=1,
                     help="1: d = 729 chain (headline); 0: d = 30 transmon-resonator state, FP64; "
                          "2: 512 uneven instances batched; 3: d = 4096 all-to-all, tree product; "
@@ -263,10 +271,10 @@ def run_ours(args):
                     "note": f"achieved counts 8 d^3 flops per complex product; the tensor pipe issues "
                             f"{pairs} BF16 digit-pair products per such flop"}
         else:
-            fp64_peak = 1.25   # TFLOP/s, nominal GB300 FP64 rate (no measured FP64 peak on this machine)
+            fp64_peak = FP64_TFLOPS_MEASURED
             roof = {"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
                     "frac": achieved / fp64_peak, "traffic": None, "kernel": "cgemm_f64_kernel",
-                    "peak_source": "nominal GB300 FP64 rate"}
+                    "peak_source": "FP64 torch.matmul, measured (bench.py --peaks)"}
         result = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": max(3, args.warmup), "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -307,11 +315,111 @@ def run_ours(args):
             result["accuracy"] = {"max_abs_err_vs_fp64_oracle": err, "intervals_compared": n_s,
                                   "tolerance": 1e-6 if prec == M.MG_PREC_SPLIT else 1e-11}
     plan.close()
+    if result is not None and ws == 1 and not args.no_serving:
+        # the served stream beside the headline: the first requests of the Poisson(200/s)
+        # mixed stream at the stated rate (an overload) and at half the capacity that run
+        # measured; state requests of d >= 256 on the action path, the rest split 6 digits
+        with torch.cuda.stream(stream):
+            over = serve_prefix(M, W, torch, ctx, dev, args.serve_requests, 200.0, args.slices, True)
+            cap = over["requests"] / over["makespan_s"]
+            half = serve_prefix(M, W, torch, ctx, dev, args.serve_requests, 0.5 * cap, args.slices, True)
+        keys = ("offered_rate_per_s", "latency_ms", "intervals_per_s", "completed", "makespan_s", "arrival_span_s",
+                "admission_retries", "clocks")
+        result["serving"] = {
+            "workload": f"first {over['requests']} requests of the Poisson(200/s) mixed stream "
+                        f"(d up to {over['d_max']}, {over['intervals_total']} intervals, state or full U)",
+            "state_requests": "action path (FP64) from d = 256, split 6 digits below",
+            "at_stated_rate": {k: over[k] for k in keys},
+            "capacity_requests_per_s": cap,
+            "at_half_capacity": {k: half[k] for k in keys},
+        }
+        if not args.no_cpu_baseline:
+            import oracle
+            acc, _ = serve_accuracy(oracle, np, half, len(os.sched_getaffinity(0)))
+            result["serving"]["accuracy"] = acc
     ctx.close()
     if ws > 1:
         torch.distributed.destroy_process_group()
     if result is not None:
         print(json.dumps(result), flush=True)
+
+
+# ----------------------------------------------------------------------------
+# the served stream (config 4): a prefix of the Poisson request stream
+# ----------------------------------------------------------------------------
+def serve_prefix(M, W, torch, ctx, dev, requests, rate, slices, action):
+    """Submit the first `requests` requests of the 200/s Poisson stream to one server at their
+    arrival times stretched to `rate` requests/s (the requests themselves unchanged) and wait
+    for all.  State requests take the action path from d = 256 when `action`."""
+    stretch = 200.0 / rate
+    stream_spec = [(arr * stretch, sp) for arr, sp in W.serving_stream()[:requests]]
+    built = [W.serving_job(sp) for _, sp in stream_spec]
+    inputs = []
+    for wl in built:
+        sn, w = M.node_samples(wl)
+        inputs.append((torch.from_numpy(wl.H0).to(dev), torch.from_numpy(wl.Hk).to(dev),
+                       torch.from_numpy(sn).to(dev), w,
+                       torch.from_numpy(wl.psi0).to(dev) if wl.psi0 is not None else None,
+                       torch.empty(wl.d if wl.psi0 is not None else (wl.d, wl.d), dtype=torch.complex128,
+                                   device=dev)))
+    torch.cuda.synchronize()
+    srv = M.Server(ctx, mem_budget_bytes=64 << 30, quantum_intervals=256)
+    clocks = ClockSampler(dev.index or 0)
+    clocks.start()
+    t_start = time.perf_counter()
+    ids, rejected, flagged = [], 0, []
+    for (arr, sp), wl, (H0, Hk, S, w, inp, o) in zip(stream_spec, built, inputs):
+        now = time.perf_counter() - t_start
+        if arr > now:
+            time.sleep(arr - now)
+        kind = M.MG_OUT_STATE if inp is not None else M.MG_OUT_PROPAGATOR
+        act = action and kind == M.MG_OUT_STATE
+        while True:
+            jid = srv.submit(H0, Hk, wl.N, wl.P, wl.t0, wl.dt, w, S, kind, inp, o, M.MG_PREC_SPLIT, slices,
+                             action=act)
+            if jid is not None:
+                break
+            rejected += 1
+            time.sleep(0.01)
+        ids.append(jid)
+        flagged.append(act and wl.d >= 256)
+    reps = [srv.wait(j, 3600.0) for j in ids]
+    wall = time.perf_counter() - t_start
+    clk = clocks.stop()
+    st = srv.stats()
+    srv.close()
+    assert all(r["status"] == 0 for r in reps), "a served request failed"
+    lat = sorted(r["latency_ms"] for r in reps)
+    intervals = sum(wl.N for wl in built)
+    return {"requests": len(ids), "offered_rate_per_s": rate, "arrival_span_s": stream_spec[-1][0],
+            "d_max": max(wl.d for wl in built), "intervals_total": intervals, "makespan_s": wall,
+            "intervals_per_s": intervals / wall, "completed": st["completed"],
+            "latency_ms": {"p50": st["p50_ms"], "p99": st["p99_ms"], "max": lat[-1]},
+            "admission_retries": rejected, "clocks": clk, "_built": built, "_inputs": inputs, "_fp64": flagged}
+
+
+def serve_accuracy(oracle, np, res, cores, budget_s=15.0, at_least=8):
+    """The oracle on the cheapest served requests (by d^3 N), at least `at_least` of them and
+    more while the host budget lasts, against the served results."""
+    built, inputs, fp64 = res["_built"], res["_inputs"], res["_fp64"]
+    order = sorted(range(len(built)), key=lambda q: built[q].d ** 3 * built[q].N)
+    t0 = time.perf_counter()
+    done_n, errs = 0, {"split": [], "fp64_action": []}
+    for k, q in enumerate(order):
+        if k >= at_least and time.perf_counter() - t0 > budget_s:
+            break
+        ref = oracle.evolve_workload(built[q])
+        errs["fp64_action" if fp64[q] else "split"].append(float(np.abs(inputs[q][5].cpu().numpy() - ref).max()))
+        done_n += built[q].N
+    cpu_s = time.perf_counter() - t0
+    n = sum(len(v) for v in errs.values())
+    acc = {"requests_compared": n,
+           "max_abs_err_vs_fp64_oracle_split": max(errs["split"]) if errs["split"] else None,
+           "max_abs_err_vs_fp64_oracle_action": max(errs["fp64_action"]) if errs["fp64_action"] else None,
+           "tolerance": {"split": 1e-6, "action (FP64)": 1e-11}}
+    cpu = {"value": done_n / cpu_s, "unit": UNIT, "cores": cores, "kind": "oracle",
+           "sample": f"the {n} cheapest requests of the stream (by d^3 N)"}
+    return acc, cpu
 
 
 # ----------------------------------------------------------------------------
@@ -365,10 +473,12 @@ def run_config(args):
         ach = g["flops"] / (g["ms"] * 1e-3) / 1e12
         peaks, src = measured_peaks()
         peak = float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops")))
-        return {"bound": "tensor" if pairs else "alu", "achieved": ach, "peak": peak if pairs else 1.25,
-                "unit": "TFLOP/s", "frac": ach / (peak if pairs else 1.25), "traffic": None,
+        p64 = FP64_TFLOPS_MEASURED
+        return {"bound": "tensor" if pairs else "alu", "achieved": ach, "peak": peak if pairs else p64,
+                "unit": "TFLOP/s", "frac": ach / (peak if pairs else p64), "traffic": None,
                 "tensor_pipe_frac": ach * pairs / peak if pairs else None,
-                "peak_source": f"bf16 dense sustained, {src}" if pairs else "nominal GB300 FP64 rate"}
+                "peak_source": f"bf16 dense sustained, {src}" if pairs else
+                "FP64 torch.matmul, measured (bench.py --peaks)"}
 
     aflag = M.MG_FLAG_STATE_ACTION if args.action else 0
     if args.config in (0, 3):
@@ -481,70 +591,21 @@ def run_config(args):
         for p in plans:
             p.close()
     elif args.config == 4:
-        stretch = 200.0 / args.rate
-        stream_spec = [(arr * stretch, sp) for arr, sp in W.serving_stream()[: args.requests]]
-        srv = M.Server(ctx, mem_budget_bytes=64 << 30, quantum_intervals=256)
-        built = [W.serving_job(sp) for _, sp in stream_spec]
-        inputs = []
-        for wl in built:
-            sn, w = M.node_samples(wl)
-            inputs.append((torch.from_numpy(wl.H0).to(dev), torch.from_numpy(wl.Hk).to(dev),
-                           torch.from_numpy(sn).to(dev), w,
-                           torch.from_numpy(wl.psi0).to(dev) if wl.psi0 is not None else None,
-                           torch.empty(wl.d if wl.psi0 is not None else (wl.d, wl.d), dtype=torch.complex128,
-                                       device=dev)))
-        torch.cuda.synchronize()
-        clocks = ClockSampler(0)
-        clocks.start()
-        t_start = time.perf_counter()
-        ids, rejected = [], 0
-        for (arr, sp), wl, (H0, Hk, S, w, inp, o) in zip(stream_spec, built, inputs):
-            now = time.perf_counter() - t_start
-            if arr > now:
-                time.sleep(arr - now)
-            kind = M.MG_OUT_STATE if inp is not None else M.MG_OUT_PROPAGATOR
-            while True:
-                jid = srv.submit(H0, Hk, wl.N, wl.P, wl.t0, wl.dt, w, S, kind, inp, o, M.MG_PREC_SPLIT, args.slices,
-                                 action=args.action and kind == M.MG_OUT_STATE)
-                if jid is not None:
-                    break
-                rejected += 1
-                time.sleep(0.01)
-            ids.append(jid)
-        reps = [srv.wait(j, 3600.0) for j in ids]
-        wall = time.perf_counter() - t_start
-        clk = clocks.stop()
-        st = srv.stats()
-        lat = sorted(r["latency_ms"] for r in reps)
-        intervals = sum(wl.N for wl in built)
+        res = serve_prefix(M, W, torch, ctx, dev, args.requests, args.rate, args.slices, args.action)
         out_line.update(metric="served Magnus stream: intervals/sec with p50/p99 request latency",
-                        value=intervals / wall, ms_per_step=None, steps=1, warmup=0,
+                        value=res["intervals_per_s"], ms_per_step=None, steps=1, warmup=0,
                         dtype=f"bf16 digits x{args.slices} (fp32 accumulate) + f64",
-                        config={"workload": "poisson_200_per_s_mixed_d32_2048", "requests": len(ids),
-                                "offered_rate_per_s": args.rate,
-                                "arrival_span_s": stream_spec[-1][0], "d_max": max(wl.d for wl in built),
-                                "intervals_total": intervals, "quantum_intervals": 256,
-                                "state_requests": "action path (FP64)" if args.action else "split path"},
-                        latency_ms={"p50": st["p50_ms"], "p99": st["p99_ms"], "max": lat[-1]},
-                        admission_retries=rejected, clocks=clk)
-        srv.close()
+                        config={"workload": "poisson_200_per_s_mixed_d32_2048", "requests": res["requests"],
+                                "offered_rate_per_s": args.rate, "arrival_span_s": res["arrival_span_s"],
+                                "d_max": res["d_max"], "intervals_total": res["intervals_total"],
+                                "quantum_intervals": 256,
+                                "state_requests": "action path (FP64) from d = 256" if args.action else "split path"},
+                        latency_ms=res["latency_ms"], admission_retries=res["admission_retries"],
+                        clocks=res["clocks"])
         if not args.no_cpu_baseline:
-            # the oracle on the cheapest requests (by d^3 N) until ~15 s of host time, and
-            # the served results of those requests against it
-            order = sorted(range(len(built)), key=lambda q: built[q].d ** 3 * built[q].N)
-            t0 = time.perf_counter()
-            done_n, errs = 0, []
-            for q in order:
-                if time.perf_counter() - t0 > 15.0:
-                    break
-                ref = oracle.evolve_workload(built[q])
-                errs.append(float(np.abs(inputs[q][5].cpu().numpy() - ref).max()))
-                done_n += built[q].N
-            cpu_s = time.perf_counter() - t0
-            out_line["cpu_baseline"] = {"value": done_n / cpu_s, "unit": UNIT, "cores": cores, "kind": "oracle",
-                                        "sample": f"the {len(errs)} cheapest requests of the stream (by d^3 N)"}
-            out_line["accuracy"] = {"max_abs_err_vs_fp64_oracle": max(errs), "requests_compared": len(errs),
-                                    "tolerance": 1e-6}
+            acc, cpu = serve_accuracy(oracle, np, res, cores)
+            out_line["cpu_baseline"] = cpu
+            out_line["accuracy"] = acc
     ctx.close()
     print(json.dumps(out_line), flush=True)
 
