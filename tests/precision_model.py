@@ -196,6 +196,70 @@ def split_product(A, B, L, beta=None, addends=(), diag=0.0, accumulate="zero", g
 
 
 # ----------------------------------------------------------------------------
+# the alternative the design rejects: three-pass TF32 products ("3xTF32")
+# ----------------------------------------------------------------------------
+TF32_KBLOCK = 8    # depth of one TF32 tensor-core step along K
+
+
+def tf32_round(x):
+    """float32 values rounded to TF32 (10 explicit mantissa bits), to nearest even."""
+    x = np.asarray(x, dtype=np.float32)
+    b = x.view(np.uint32).astype(np.uint64)
+    b = (b + 0xFFF + ((b >> 13) & 1)) & ~np.uint64(0x1FFF)
+    return b.astype(np.uint32).view(np.float32)
+
+
+def tf32x3_product(A, B, accumulate="zero"):
+    """C = A B as three TF32 passes, hi hi + hi lo + lo hi, with a = hi + lo, hi = tf32(a),
+    lo = tf32(a - hi) (both from the FP32 value of a), in the 4M real embedding; each
+    8-deep block of K of each pass is summed exactly and added to ONE FP32 accumulator
+    with one rounding.  Returns complex128 (the FP32 accumulator's value)."""
+    A, B = df_value(A), df_value(B)
+    d = A.shape[-1]
+    Ae = np.concatenate([A.real, A.imag], axis=-1).astype(np.float32)                  # (d, 2d)
+    Be = np.block([[B.real, B.imag], [-B.imag, B.real]]).astype(np.float32)            # (2d, 2d)
+    ah = tf32_round(Ae)
+    al = tf32_round(Ae - ah)
+    bh = tf32_round(Be)
+    bl = tf32_round(Be - bh)
+    K = 2 * d
+    acc = np.zeros((d, 2 * d), dtype=np.float32)
+    for k0 in range(0, K, TF32_KBLOCK):
+        k1 = min(K, k0 + TF32_KBLOCK)
+        for a_, b_ in ((ah, bh), (ah, bl), (al, bh)):
+            part = a_[:, k0:k1].astype(np.float64) @ b_[k0:k1, :].astype(np.float64)
+            acc = _to_f32(acc.astype(np.float64) + part, accumulate)
+    acc = acc.astype(np.float64)
+    return acc[:, :d] + 1j * acc[:, d:]
+
+
+def expm_tf32x3(W, tau=None):
+    """exp(-i W) for one Hermitian W with every product a 3xTF32 product: Paterson-Stockmeyer
+    at the (m, s) of unit roundoff 2^-22 (what three TF32 passes carry), s squarings."""
+    W = np.asarray(W, dtype=np.complex128)
+    d = W.shape[-1]
+    m, p, s = taylor_choice(float(np.abs(W).sum(axis=-2).max()), 2.0 ** -22, False)
+    X = (-1j * W * 2.0 ** -s).astype(np.complex64).astype(np.complex128)
+    a = [1.0 / math.factorial(j) if j <= m else 0.0 for j in range(m + p + 1)]
+    Pw = {1: X}
+    for j in range(2, p + 1):
+        Pw[j] = tf32x3_product(Pw[j - 1], X)
+    q, r = divmod(m, p)
+    top = q - 1 if r == 0 else q
+    R = a[top * p] * np.eye(d) + sum(a[top * p + j] * Pw[j] for j in range(1, p))
+    if r == 0:
+        R = R + a[m] * Pw[p]
+    for i in range(top - 1, -1, -1):
+        R = tf32x3_product(R, Pw[p]) + sum(a[i * p + j] * Pw[j] for j in range(1, p)) + a[i * p] * np.eye(d)
+        R = R.astype(np.complex64).astype(np.complex128)
+    for _ in range(s):
+        R = tf32x3_product(R, R)
+    if tau is not None:
+        R = np.exp(-1j * tau) * R
+    return R
+
+
+# ----------------------------------------------------------------------------
 # the exponential
 # ----------------------------------------------------------------------------
 PS_DEGREES = [(2, 2), (4, 2), (6, 3), (9, 3), (12, 4), (16, 4)]   # (m, block p)

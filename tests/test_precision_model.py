@@ -114,3 +114,26 @@ def test_a_separate_level3_accumulator_lowers_the_floor():
     e5 = np.abs(PM.df_value(PM.split_product(A, B, 7, groups=5)) - ref).max()
     e4_l6 = np.abs(PM.df_value(PM.split_product(A, B, 6, groups=4)) - ref).max()
     assert e4 > 0.5 * e4_l6 and e5 < e4 / 10, (e4_l6, e4, e5)
+
+
+def test_three_pass_tf32_products_cannot_reach_the_split_tolerance():
+    """The interface sketch's TF32x3 mode: products hi hi + hi lo + lo hi of TF32 halves,
+    accumulated in one FP32 accumulator, carry about 2^-22 of relative error per product
+    (the FP32 accumulator, not the operand halves, sets it), 10^4 times the 6-digit split
+    product's; over 200 intervals of the d = 30 workload the modelled state misses the
+    stated 1e-6 while the 5-digit split stays two orders inside it."""
+    rng = np.random.default_rng(17)
+    d = 64
+    A, B = rand_c(rng, (d, d)), rand_c(rng, (d, d))
+    ref = A @ B
+    rel_tf = np.abs(PM.tf32x3_product(A, B) - ref).max() / np.abs(ref).max()
+    rel_l6 = np.abs(PM.df_value(PM.split_product(A, B, 6)) - ref).max() / np.abs(ref).max()
+    assert 1e-8 < rel_tf < 1e-5 and rel_l6 < 1e-4 * rel_tf, (rel_tf, rel_l6)
+    wl = W.config(0, N=200)
+    ref_psi, parts = oracle.evolve_workload(wl, return_parts=True)
+    psi = np.asarray(wl.psi0, dtype=np.complex128)
+    for H in parts["Hbar"]:
+        tau = np.trace(H).real / wl.d
+        psi = PM.expm_tf32x3(H - tau * np.eye(wl.d), tau) @ psi
+    err_tf = np.abs(psi - ref_psi).max()
+    assert err_tf > 1e-6, err_tf
