@@ -36,7 +36,7 @@ SAMPLE_INTERVALS = 128          # oracle sample (cpu_baseline) and accuracy pref
 # form, keyed by (d, digits): one ncu capture of a 32-product launch divided by 32; the bench
 # scales it to the average timed launch by the products that launch computes.  An entry is
 # valid for the kernel build it was captured from only, and is removed when the kernel changes.
-GEMM_DRAM_BYTES_PER_PRODUCT = {}
+GEMM_DRAM_BYTES_PER_PRODUCT = {(729, 6): (1.269396e9 + 0.254560e9) / 32}
 REFERENCE_STEP_INTERVALS = 16   # oracle intervals per step of --impl reference
 # FP64 and TF32 dense matrix-product peaks of GB300 measured by `python bench.py --peaks`
 # (torch.matmul, n = 8192, best of 10, CUDA events); the BF16 peaks come from MEASURED_PEAKS.json

@@ -5,6 +5,7 @@
 #include "common.cuh"
 #include "df32.cuh"
 
+#include <algorithm>
 #include <cmath>
 
 namespace mg {
@@ -227,25 +228,36 @@ int launch_max_identity_defect(int batch, int d, const double* G, double* out_de
 // double-float (DF32) versions used by the split-precision path
 // ---------------------------------------------------------------------------
 // X = (-i) 2^{-sq} src: FP64 in, DF32 out
-__global__ void scale_minus_i_df_kernel(long long total, long long per_item, const double* __restrict__ src,
-                                        float4* __restrict__ dst, double f, const int* __restrict__ sq_dev) {
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
-       e += (long long)gridDim.x * blockDim.x) {
-    // 2^{-s} exactly (0 <= s < 1023)
-    const double g = sq_dev ? __longlong_as_double((long long)(1023 - sq_dev[e / per_item]) << 52) : f;
-    const double2 v = reinterpret_cast<const double2*>(src)[e];
+// Grid of the per-item double-float kernels: y = batch item, x strides over the
+// item's d^2 elements, so that the element index and the diagonal test (r is on the
+// diagonal iff r % (d + 1) == 0) stay 32-bit: no 64-bit division per element.
+static dim3 item_grid(int batch, long long per) {
+  long long gx = (per + 255) / 256;
+  const long long cap = std::max<long long>(1, (152LL * 32) / std::max(1, batch));
+  if (gx > cap) gx = cap;
+  return dim3((unsigned)std::max<long long>(gx, 1), (unsigned)batch);
+}
+
+__global__ void scale_minus_i_df_kernel(int per, const double* __restrict__ src, float4* __restrict__ dst, double f,
+                                        const int* __restrict__ sq_dev) {
+  const long long base = (long long)blockIdx.y * per;
+  // 2^{-s} exactly (0 <= s < 1023)
+  const double g = sq_dev ? __longlong_as_double((long long)(1023 - sq_dev[blockIdx.y]) << 52) : f;
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < per; r += gridDim.x * blockDim.x) {
+    const double2 v = reinterpret_cast<const double2*>(src)[base + r];
     const df32 re = df_from_double(g * v.y), im = df_from_double(-g * v.x);
-    dst[e] = make_float4(re.hi, re.lo, im.hi, im.lo);
+    dst[base + r] = make_float4(re.hi, re.lo, im.hi, im.lo);
   }
 }
 
 int launch_scale_minus_i_df(int batch, int d, const double* src_fp64, double* dst_df, int sq, cudaStream_t s,
                             const int* sq_dev) {
-  const long long per = (long long)d * d;
-  const long long total = per * batch;
+  if (batch <= 0) return MG_OK;
+  if (batch > 65535) return MG_EUNSUPPORTED;
   const double f = std::ldexp(1.0, -sq);
-  scale_minus_i_df_kernel<<<grid_for(total), 256, 0, s>>>(total, per, src_fp64, reinterpret_cast<float4*>(dst_df), f,
-                                                          sq_dev);
+  scale_minus_i_df_kernel<<<item_grid(batch, (long long)d * d), 256, 0, s>>>(d * d, src_fp64,
+                                                                             reinterpret_cast<float4*>(dst_df), f,
+                                                                             sq_dev);
   return check_launch("scale_minus_i_df_kernel");
 }
 
@@ -254,19 +266,25 @@ struct LincombDfArgs {
   df32 coef[4];
 };
 
-__global__ void lincomb_df_kernel(int d, long long total, int nsrc, LincombDfArgs a, df32 diag,
-                                  float4* __restrict__ dst) {
-  const long long per = (long long)d * d;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
-       e += (long long)gridDim.x * blockDim.x) {
+// x + y in double-float with one fewer error-free step than df_add (error below
+// ~2^-46 of |x| + |y|; the combinations below add terms of like size)
+__device__ __forceinline__ df32 df_add_fast(df32 x, df32 y) {
+  const df32 s = two_sum(x.hi, y.hi);
+  return fast_two_sum(s.hi, s.lo + (x.lo + y.lo));
+}
+
+__global__ void lincomb_df_kernel(int d, int nsrc, LincombDfArgs a, df32 diag, float4* __restrict__ dst) {
+  const int per = d * d;
+  const long long base = (long long)blockIdx.y * per;
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < per; r += gridDim.x * blockDim.x) {
+    const long long e = base + r;
     df32 re{0.f, 0.f}, im{0.f, 0.f};
     for (int m = 0; m < nsrc; ++m) {
       const float4 v = a.src[m][e];
       re = df_add(re, df_mul(df32{v.x, v.y}, a.coef[m]));
       im = df_add(im, df_mul(df32{v.z, v.w}, a.coef[m]));
     }
-    const long long r = e % per;
-    if (r / d == r % d) re = df_add(re, diag);
+    if (r % (d + 1) == 0) re = df_add(re, diag);
     dst[e] = make_float4(re.hi, re.lo, im.hi, im.lo);
   }
 }
@@ -274,14 +292,15 @@ __global__ void lincomb_df_kernel(int d, long long total, int nsrc, LincombDfArg
 int launch_lincomb_df(int batch, int d, double* dst, int nsrc, const double* const* src, const double* coef,
                       double diag, cudaStream_t s) {
   if (nsrc < 0 || nsrc > 4) return MG_EINVAL;
+  if (batch <= 0) return MG_OK;
+  if (batch > 65535) return MG_EUNSUPPORTED;
   LincombDfArgs a{};
   for (int m = 0; m < nsrc; ++m) {
     a.src[m] = reinterpret_cast<const float4*>(src[m]);
     a.coef[m] = df_from_double(coef[m]);
   }
-  const long long total = (long long)d * d * batch;
-  lincomb_df_kernel<<<grid_for(total), 256, 0, s>>>(d, total, nsrc, a, df_from_double(diag),
-                                                    reinterpret_cast<float4*>(dst));
+  lincomb_df_kernel<<<item_grid(batch, (long long)d * d), 256, 0, s>>>(d, nsrc, a, df_from_double(diag),
+                                                                       reinterpret_cast<float4*>(dst));
   return check_launch("lincomb_df_kernel");
 }
 
@@ -293,20 +312,24 @@ struct LincombMultiDfArgs {
   df32 diag[5];
 };
 
-__global__ void lincomb_multi_df_kernel(int d, long long total, int nsrc, int nout, LincombMultiDfArgs a) {
-  const long long per = (long long)d * d;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
-       e += (long long)gridDim.x * blockDim.x) {
-    float4 v[4];
-    for (int m = 0; m < nsrc; ++m) v[m] = a.src[m][e];
-    const long long r = e % per;
-    const bool on_diag = r / d == r % d;
+template <int NSRC>
+__global__ void lincomb_multi_df_kernel(int d, int nout, LincombMultiDfArgs a) {
+  const int per = d * d;
+  const long long base = (long long)blockIdx.y * per;
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < per; r += gridDim.x * blockDim.x) {
+    const long long e = base + r;
+    float4 v[NSRC];
+#pragma unroll
+    for (int m = 0; m < NSRC; ++m) v[m] = a.src[m][e];
+    const bool on_diag = r % (d + 1) == 0;
     for (int o = 0; o < nout; ++o) {
-      df32 re = on_diag ? a.diag[o] : df32{0.f, 0.f}, im{0.f, 0.f};
-      for (int m = 0; m < nsrc; ++m) {
-        re = df_add(re, df_mul(df32{v[m].x, v[m].y}, a.coef[o][m]));
-        im = df_add(im, df_mul(df32{v[m].z, v[m].w}, a.coef[o][m]));
+      df32 re = df_mul(df32{v[0].x, v[0].y}, a.coef[o][0]), im = df_mul(df32{v[0].z, v[0].w}, a.coef[o][0]);
+#pragma unroll
+      for (int m = 1; m < NSRC; ++m) {
+        re = df_add_fast(re, df_mul(df32{v[m].x, v[m].y}, a.coef[o][m]));
+        im = df_add_fast(im, df_mul(df32{v[m].z, v[m].w}, a.coef[o][m]));
       }
+      if (on_diag) re = df_add(re, a.diag[o]);
       a.dst[o][e] = make_float4(re.hi, re.lo, im.hi, im.lo);
     }
   }
@@ -315,6 +338,8 @@ __global__ void lincomb_multi_df_kernel(int d, long long total, int nsrc, int no
 int launch_lincomb_multi_df(int batch, int d, int nout, double* const* dst, int nsrc, const double* const* src,
                             const double* coef, const double* diag, cudaStream_t s) {
   if (nsrc < 1 || nsrc > 4 || nout < 1 || nout > 5) return MG_EINVAL;
+  if (batch <= 0) return MG_OK;
+  if (batch > 65535) return MG_EUNSUPPORTED;
   LincombMultiDfArgs a{};
   for (int m = 0; m < nsrc; ++m) a.src[m] = reinterpret_cast<const float4*>(src[m]);
   for (int o = 0; o < nout; ++o) {
@@ -322,8 +347,13 @@ int launch_lincomb_multi_df(int batch, int d, int nout, double* const* dst, int 
     a.diag[o] = df_from_double(diag[o]);
     for (int m = 0; m < nsrc; ++m) a.coef[o][m] = df_from_double(coef[o * nsrc + m]);
   }
-  const long long total = (long long)d * d * batch;
-  lincomb_multi_df_kernel<<<grid_for(total), 256, 0, s>>>(d, total, nsrc, nout, a);
+  const dim3 grid = item_grid(batch, (long long)d * d);
+  switch (nsrc) {
+    case 1: lincomb_multi_df_kernel<1><<<grid, 256, 0, s>>>(d, nout, a); break;
+    case 2: lincomb_multi_df_kernel<2><<<grid, 256, 0, s>>>(d, nout, a); break;
+    case 3: lincomb_multi_df_kernel<3><<<grid, 256, 0, s>>>(d, nout, a); break;
+    default: lincomb_multi_df_kernel<4><<<grid, 256, 0, s>>>(d, nout, a); break;
+  }
   return check_launch("lincomb_multi_df_kernel");
 }
 

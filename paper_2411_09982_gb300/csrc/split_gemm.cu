@@ -101,14 +101,18 @@ SplitGeom split_geom(int d, int L) {
 // ---------------------------------------------------------------------------
 // digit extraction (shared by the A and B slicers)
 // ---------------------------------------------------------------------------
-// GB300's FP64 pipe is narrow, so digits are cut with integer arithmetic on the
-// IEEE-754 bits: a value a of a row whose largest magnitude is below 2^E becomes
-// the fixed-point integer X = round(a 2^{beta L - E - 1}), |X| < 2^{beta L - 1},
-// which is written in balanced base 2^beta:
-//     X = sum_{s<L} q_s 2^{beta (L-1-s)},  q_1..q_{L-1} in [-2^{beta-1}, 2^{beta-1}),
-// and the leading q_0 in [-2^{beta-1}, 2^{beta-1}].  Then
-//     a ~= 2^{E+1-beta} sum_s v_s,   v_s = q_s 2^{-beta s}  (exact in BF16),
-// with an error below 2^{E - beta L} (the rounding of X).
+// A value a of a row (column) whose entries all lie below 2^E in magnitude is
+// scaled to x = a 2^{beta - 1 - E}, |x| < 2^{beta-1}, held exactly as a pair of
+// FP32 numbers x + y (a double-float input is exact in two FP32 numbers; an FP64
+// input is first split into two).  Its balanced base-2^beta digits are peeled on
+// the FP32 pipe, every step exact:
+//     (x, y) <- TwoSum(x, y);  q_s = round(x);  (x, y) <- ((x - q_s) 2^beta, y 2^beta)
+// (x - q_s is exact by Sterbenz's lemma, the scaling by a power of two), so
+//     a = 2^{E+1-beta} (sum_{s<L} q_s 2^{-beta s} + r),  |r| <= 2^{-beta (L-1) - 1} (1 + 2^-20),
+// with |q_s| <= 2^{beta-1}; every v_s = q_s 2^{-beta s} is exact in BF16.  The
+// rounding to an integer is (x + 1.5 2^23) - 1.5 2^23 (to nearest even, exact for
+// |x| < 2^22), so the whole extraction runs on the FMA pipe; the earlier
+// 64-bit-integer form of the same digits kept GB300's integer pipe 72% busy.
 
 // exponent E of |a| with |a| < 2^E (biased exponent - 1022); zero and subnormals -> -2^29
 __device__ __forceinline__ int exp_bound(double a) {
@@ -121,35 +125,6 @@ __device__ __forceinline__ int exp_bound(df32 a) {
   const int bits = __float_as_int(a.hi);
   const int bexp = (bits >> 23) & 0xFF;
   return bexp == 0 ? -(1 << 29) : bexp - 126;
-}
-
-// round(a * 2^sh) as a signed 64-bit integer (sh chosen so that the result fits)
-__device__ __forceinline__ long long fixed_point(double a, int sh) {
-  const long long bits = __double_as_longlong(a);
-  const int bexp = (int)((bits >> 52) & 0x7FF);
-  if (bexp == 0) return 0;
-  const long long mant = (bits & 0xFFFFFFFFFFFFFLL) | 0x10000000000000LL;   // a = mant 2^{bexp-1075}
-  const int shift = bexp - 1075 + sh;
-  long long X;
-  if (shift >= 0) X = mant << shift;
-  else if (shift > -62) X = (mant + (1LL << (-shift - 1))) >> (-shift);
-  else X = 0;
-  return bits < 0 ? -X : X;
-}
-__device__ __forceinline__ long long fixed_point(float a, int sh) {
-  const int bits = __float_as_int(a);
-  const int bexp = (bits >> 23) & 0xFF;
-  if (bexp == 0) return 0;
-  const long long mant = (long long)((bits & 0x7FFFFF) | 0x800000);          // a = mant 2^{bexp-150}
-  const int shift = bexp - 150 + sh;
-  long long X;
-  if (shift >= 0) X = shift < 40 ? (mant << shift) : 0;
-  else if (shift > -30) X = (mant + (1LL << (-shift - 1))) >> (-shift);
-  else X = 0;
-  return bits < 0 ? -X : X;
-}
-__device__ __forceinline__ long long fixed_point(df32 a, int sh) {
-  return fixed_point(a.hi, sh) + fixed_point(a.lo, sh);
 }
 
 // one complex element of an FP64 or DF32 matrix (16 bytes either way)
@@ -171,30 +146,42 @@ template <> struct Elem<df32> {
   }
 };
 
-template <int L, typename V>
-__device__ __forceinline__ void make_digits(V a, int sh, int beta, __nv_bfloat16 (&v)[L]) {
-  long long X = fixed_point(a, sh);
-  const long long half = 1LL << (beta - 1), mask = (1LL << beta) - 1;
-  int q[L];
-#pragma unroll
-  for (int s = L - 1; s >= 1; --s) {
-    const long long r = ((X + half) & mask) - half;
-    q[s] = (int)r;
-    X = (X - r) >> beta;
-  }
-  q[0] = (int)X;
+// 2^k as the product of two FP32 factors (each in range for |k| <= 250)
+struct Pow2Pair {
+  float f1, f2;
+};
+__device__ __forceinline__ Pow2Pair pow2_pair(int k) {
+  const int k1 = k / 2, k2 = k - k1;
+  return {__int_as_float((127 + k1) << 23), __int_as_float((127 + k2) << 23)};
+}
+// the scaled value as an exact pair of FP32 numbers
+__device__ __forceinline__ df32 scaled_pair(df32 a, Pow2Pair f) { return {(a.hi * f.f1) * f.f2, (a.lo * f.f1) * f.f2}; }
+__device__ __forceinline__ df32 scaled_pair(double a, Pow2Pair f) {
+  const float hi = __double2float_rn(a);
+  const float lo = __double2float_rn(a - (double)hi);
+  return {(hi * f.f1) * f.f2, (lo * f.f1) * f.f2};
+}
+
+constexpr float kRoundMagic = 12582912.0f;   // 1.5 2^23
+__device__ __forceinline__ float round_to_int(float x) { return __fsub_rn(__fadd_rn(x, kRoundMagic), kRoundMagic); }
+
+// digits of two scaled values (the first in the low half of every word): w[s] holds
+// q_s 2^{-beta s} of both as BF16
+template <int L>
+__device__ __forceinline__ void digits_pair(df32 u, df32 v, int beta, uint32_t (&w)[L]) {
+  const float B = __int_as_float((127 + beta) << 23);
 #pragma unroll
   for (int s = 0; s < L; ++s) {
-    const float pw = __int_as_float((127 - beta * s) << 23);   // 2^{-beta s}, exact
-    v[s] = __float2bfloat16_rn(__int2float_rn(q[s]) * pw);
+    const df32 a = two_sum(u.hi, u.lo), b = two_sum(v.hi, v.lo);
+    const float qa = round_to_int(a.hi), qb = round_to_int(b.hi);
+    const float p = __int_as_float((127 - beta * s) << 23);   // 2^{-beta s}
+    const __nv_bfloat162 d2 = __floats2bfloat162_rn(qa * p, qb * p);
+    w[s] = *reinterpret_cast<const uint32_t*>(&d2);
+    u = {__fsub_rn(a.hi, qa) * B, a.lo * B};
+    v = {__fsub_rn(b.hi, qb) * B, b.lo * B};
   }
 }
 
-// digit q (0..3, lowest k first) of a four-digit 8-byte word
-__device__ __forceinline__ void put_digit(uint2& w, int q, __nv_bfloat16 v) {
-  const uint32_t bits = (uint32_t)__bfloat16_as_ushort(v) << (16 * (q & 1));
-  if (q < 2) w.x |= bits; else w.y |= bits;
-}
 // the word with every digit negated (BF16 sign bits)
 __device__ __forceinline__ uint2 neg4(uint2 w) { return make_uint2(w.x ^ 0x80008000u, w.y ^ 0x80008000u); }
 
@@ -226,26 +213,27 @@ slice_a_kernel(int d, int Kp, int Mp, int beta, const double* __restrict__ A, lo
   for (int o2 = 16; o2 > 0; o2 >>= 1) E = max(E, __shfl_xor_sync(0xffffffffu, E, o2));
   if (E < -(1 << 28)) E = 0;   // all-zero row
   if (lane == 0) ea[(long long)b * Mp + row] = E;
-  const int sh = beta * L - E - 1;
+  const Pow2Pair f = pow2_pair(beta - 1 - E);
   for (int k = 4 * lane; k < Kh; k += 128) {
-    uint2 wr[L], wi[L];   // digits of the 4 elements, packed as they are made
-#pragma unroll
-    for (int s = 0; s < L; ++s) { wr[s] = make_uint2(0u, 0u); wi[s] = make_uint2(0u, 0u); }
+    df32 re[4], im[4];   // the 4 elements, scaled (zero beyond d)
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
+      re[q] = im[q] = df32{0.f, 0.f};
       if (k + q < d) {
         const auto v = E_::load(a, r0 + k + q);
-        __nv_bfloat16 dr[L], di[L];
-        make_digits<L>(v.re, sh, beta, dr);
-        make_digits<L>(v.im, sh, beta, di);
-#pragma unroll
-        for (int s = 0; s < L; ++s) put_digit(wr[s], q, dr[s]), put_digit(wi[s], q, di[s]);
+        re[q] = scaled_pair(v.re, f);
+        im[q] = scaled_pair(v.im, f);
       }
     }
+    uint32_t r01[L], r23[L], i01[L], i23[L];
+    digits_pair<L>(re[0], re[1], beta, r01);
+    digits_pair<L>(re[2], re[3], beta, r23);
+    digits_pair<L>(im[0], im[1], beta, i01);
+    digits_pair<L>(im[2], im[3], beta, i23);
 #pragma unroll
     for (int s = 0; s < L; ++s) {
-      *reinterpret_cast<uint2*>(o + s * slice_stride + k) = wr[s];
-      *reinterpret_cast<uint2*>(o + s * slice_stride + Kh + k) = wi[s];
+      *reinterpret_cast<uint2*>(o + s * slice_stride + k) = make_uint2(r01[s], r23[s]);
+      *reinterpret_cast<uint2*>(o + s * slice_stride + Kh + k) = make_uint2(i01[s], i23[s]);
     }
   }
 }
@@ -298,7 +286,7 @@ slice_b_kernel(int d, int Kp, int Np, int beta, const double* __restrict__ B, lo
   using E_ = Elem<T>;
   using V = typename E_::type;
   __shared__ V tile[SB_KCHUNK][SG_BNC + 1];
-  __shared__ int shift[SG_BNC];
+  __shared__ int shift[SG_BNC];   // beta - 1 - F_j: the scaling exponent of column j
   const int t = blockIdx.x, b = blockIdx.z;
   if (item_sq && item_sq[b] <= sq_step) return;
   const int j0 = t * SG_BNC, k0 = blockIdx.y * SB_KCHUNK;
@@ -311,7 +299,7 @@ slice_b_kernel(int d, int Kp, int Np, int beta, const double* __restrict__ B, lo
   if (tid < SG_BNC) {
     int E = j0 + tid < d ? eb[(long long)b * rows + j0 + tid] : 0;
     if (E < -(1 << 28)) E = 0;   // all-zero column
-    shift[tid] = beta * L - E - 1;
+    shift[tid] = beta - 1 - E;
   }
   for (int e = tid; e < SB_KCHUNK * SG_BNC; e += 256) {
     const int kk = e / SG_BNC, c = e % SG_BNC;
@@ -324,27 +312,30 @@ slice_b_kernel(int d, int Kp, int Np, int beta, const double* __restrict__ B, lo
     const int g = e % (SB_KCHUNK / 4), r = e / (SB_KCHUNK / 4);
     const int k = k0 + 4 * g;
     if (k >= Kh || j0 + r >= d) continue;
-    uint2 wr[L], wi[L];   // digits of the 4 elements, packed as they are made
+    const Pow2Pair f = pow2_pair(shift[r]);
+    df32 re[4], im[4];   // the 4 elements, scaled (zero beyond d)
 #pragma unroll
-    for (int s = 0; s < L; ++s) { wr[s] = make_uint2(0u, 0u); wi[s] = make_uint2(0u, 0u); }
-#pragma unroll 1
-    for (int q = 0; q < 4; ++q) {   // one element at a time keeps the register count low
+    for (int q = 0; q < 4; ++q) {
+      re[q] = im[q] = df32{0.f, 0.f};
       if (k + q < d) {
         const V v = tile[4 * g + q][r];
-        __nv_bfloat16 dr[L], di[L];
-        make_digits<L>(v.re, shift[r], beta, dr);
-        make_digits<L>(v.im, shift[r], beta, di);
-#pragma unroll
-        for (int s = 0; s < L; ++s) put_digit(wr[s], q, dr[s]), put_digit(wi[s], q, di[s]);
+        re[q] = scaled_pair(v.re, f);
+        im[q] = scaled_pair(v.im, f);
       }
     }
+    uint32_t r01[L], r23[L], i01[L], i23[L];
+    digits_pair<L>(re[0], re[1], beta, r01);
+    digits_pair<L>(re[2], re[3], beta, r23);
+    digits_pair<L>(im[0], im[1], beta, i01);
+    digits_pair<L>(im[2], im[3], beta, i23);
     __nv_bfloat16* row = ob + (long long)(j0 + r) * Kh;   // plane 0: -Im B, 1: Re B, 2: Im B
 #pragma unroll
     for (int s = 0; s < L; ++s) {
       const long long so = s * slice_stride;
-      *reinterpret_cast<uint2*>(row + so + k) = neg4(wi[s]);
-      *reinterpret_cast<uint2*>(row + so + plane_stride + k) = wr[s];
-      *reinterpret_cast<uint2*>(row + so + 2 * plane_stride + k) = wi[s];
+      const uint2 wr = make_uint2(r01[s], r23[s]), wi = make_uint2(i01[s], i23[s]);
+      *reinterpret_cast<uint2*>(row + so + k) = neg4(wi);
+      *reinterpret_cast<uint2*>(row + so + plane_stride + k) = wr;
+      *reinterpret_cast<uint2*>(row + so + 2 * plane_stride + k) = wi;
     }
   }
   // rows d..Np/2 of every plane are never read: the tensor map ends at row d (TMA fills zeros)

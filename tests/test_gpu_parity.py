@@ -359,10 +359,14 @@ def test_evolve_batch_matches_oracle_per_job(ctx, prec, L, tol, reorth):
         status = M.mg_evolve_batch(ctx, plans, kinds, ins, outs, reorth)
         torch.cuda.synchronize()
         assert status == [0] * len(jobs)
+        worst = []
         for wl, o in zip(jobs, outs):
             ref, t = _ref_and_tol(wl, prec)
             err = np.abs(o.cpu().numpy() - ref).max()
+            worst.append((err / t, wl.name, wl.d, wl.N, err, t))
             assert err <= t, (wl.name, wl.d, wl.N, err, t)
+        r, name, d, n, err, t = max(worst)
+        print(f"batch prec={prec} reorth={reorth}: worst job {name} (d={d}, N={n}) error {err:.2e}, bound {t:.2e}")
     finally:
         for p in plans:
             p.close()
