@@ -70,6 +70,11 @@ def parse():
     ap.add_argument("--peaks", action="store_true",
                     help="measure the FP64 and TF32 matrix-product peaks with torch.matmul (CUDA events, best "
                          "of 10) and print them")
+    ap.add_argument("--shard", action="store_true",
+                    help="d = 729 chain: one job's 2000 intervals shared by the ranks (each rank's ranges by "
+                         "mg_evolve, one NCCL all-gather of the partials, the ordered product by mg_cgemm) "
+                         "instead of one replica per rank")
+    ap.add_argument("--virtual", type=int, default=1, help="--shard: interval ranges per rank")
     ap.add_argument("--tune", action="store_true",
                     help="run the autotuner (mg_plan_autotune) on the d = 30, d = 729 and a 512-batch instance "
                          "workload and print every measured candidate")
@@ -342,6 +347,70 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
     if result is not None:
         print(json.dumps(result), flush=True)
+
+
+# ----------------------------------------------------------------------------
+# one job shared by the ranks (interval-range sharding)
+# ----------------------------------------------------------------------------
+def run_shard(args):
+    import torch
+    import torch.distributed as dist
+
+    import workloads as W
+    from paper_2411_09982_gb300 import build as B
+    from paper_2411_09982_gb300 import magnus as M
+    from paper_2411_09982_gb300 import shard
+
+    ws, rank, local = dist_info()
+    torch.cuda.set_device(local)
+    if not dist.is_initialized():
+        if ws > 1:
+            dist.init_process_group("nccl", init_method="env://")
+        else:
+            import socket
+            sk = socket.socket()
+            sk.bind(("127.0.0.1", 0))
+            port = sk.getsockname()[1]
+            sk.close()
+            dist.init_process_group("nccl", init_method=f"tcp://127.0.0.1:{port}", rank=0, world_size=1)
+    B.build()
+    M.load()
+    dev = torch.device("cuda", local)
+    ctx = M.Context(local)
+    wl = W.config(1)   # the same job on every rank
+    N = args.intervals
+    sn, w = M.node_samples(wl, N)
+    S = torch.from_numpy(sn).to(dev)
+    H0, Hk = torch.from_numpy(wl.H0).to(dev), torch.from_numpy(wl.Hk).to(dev)
+    prec = M.MG_PREC_SPLIT if args.precision == "split" else M.MG_PREC_FP64
+
+    def step():
+        return shard.evolve_propagator_sharded(ctx, H0, Hk, S, N, wl.P, wl.t0, wl.dt, w, prec, args.slices,
+                                               virtual=args.virtual)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        U = step()
+    torch.cuda.synchronize()
+    el = time.perf_counter() - t0
+    el = shard.max_over_ranks(el, device=dev)
+    if rank == 0:
+        print(json.dumps({"metric": METRIC + " (one job shared by the ranks)", "value": N * args.steps / el,
+                          "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": max(3, args.warmup),
+                          "ms_per_step": 1000.0 * el / args.steps, "higher_is_better": True, "scaling": "strong",
+                          "vs_baseline": None, "data": "synthetic",
+                          "config": {"workload": WORKLOAD, "intervals": N, "ranges": ws * args.virtual,
+                                     "precision": args.precision,
+                                     "exchange": "NCCL all-gather of the d x d partials, product by mg_cgemm"},
+                          "unitarity_check": float((U.conj().T @ U - torch.eye(wl.d, device=dev,
+                                                                               dtype=U.dtype)).abs().max())}),
+              flush=True)
+    ctx.close()
+    dist.destroy_process_group()
 
 
 # ----------------------------------------------------------------------------
@@ -721,6 +790,8 @@ if __name__ == "__main__":
         run_reference(a)
     elif a.tune:
         run_tune(a)
+    elif a.shard:
+        run_shard(a)
     elif a.peaks:
         run_peaks(a)
     elif a.config != 1:

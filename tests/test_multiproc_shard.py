@@ -1,6 +1,8 @@
 """Gloo tests (CPU, world size 2 and 3) of the multi-process path: interval-range sharding of
 one job with a single all-gather of partial products, the state form that passes psi from
-rank to rank, and the max-over-ranks timing reduction."""
+rank to rank, and the max-over-ranks timing reduction.  The partial products come from the
+CPU oracle and the products of the exchange from a torch CPU stand-in (on GPUs they are the
+library's mg_evolve and mg_cgemm; see test_gpu_shard.py)."""
 import os
 import socket
 
@@ -20,7 +22,8 @@ def _free_port():
     return port
 
 
-def _worker(rank, world, port, q):
+def _worker(rank, world, port, q, virtual=1):
+    import torch
     import torch.distributed as dist
     os.environ["MASTER_ADDR"] = "127.0.0.1"
     os.environ["MASTER_PORT"] = str(port)
@@ -32,11 +35,11 @@ def _worker(rank, world, port, q):
         def local_partial(start, count):
             t = oracle.node_times(wl.t0 + start * wl.dt, wl.dt, count, x)
             U, _, _ = oracle.interval_propagators(wl.H0, wl.Hk, wl.drive(t), w, wl.dt)
-            return oracle.propagate_unitary(U)
+            return torch.from_numpy(oracle.propagate_unitary(U))
 
-        U = shard.sharded_propagator(local_partial, wl.N, wl.d)
+        U = shard.sharded_propagator(local_partial, wl.N, wl.d, lambda A, B: A @ B, virtual=virtual)
         slowest = shard.max_over_ranks(1.0 + rank)
-        q.put((rank, U, slowest))
+        q.put((rank, U.numpy(), slowest))
     finally:
         dist.destroy_process_group()
 
@@ -51,18 +54,23 @@ def test_interval_ranges_cover_in_order():
 
 
 def test_combine_partials_orders_later_on_the_left():
+    import torch
     rng = np.random.default_rng(0)
-    P = [rng.normal(size=(3, 3)) for _ in range(3)]
-    np.testing.assert_allclose(shard.combine_partials(P), P[2] @ P[1] @ P[0])
+    P = [torch.from_numpy(rng.normal(size=(3, 3))) for _ in range(3)]
+    got = shard.combine_partials([P[0], None, P[1], P[2]], lambda A, B: A @ B)
+    np.testing.assert_allclose(got.numpy(), (P[2] @ P[1] @ P[0]).numpy())
 
 
 @pytest.mark.timeout(180)
-def test_two_rank_sharded_propagator_matches_single_process():
+@pytest.mark.parametrize("virtual", [1, 3])
+def test_two_rank_sharded_propagator_matches_single_process(virtual):
+    """Two ranks, each owning one range (or three consecutive ranges): one all-gather and
+    the ordered product give the single-process propagator on every rank."""
     import multiprocessing as mp
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
     port = _free_port()
-    procs = [ctx.Process(target=_worker, args=(r, 2, port, q)) for r in range(2)]
+    procs = [ctx.Process(target=_worker, args=(r, 2, port, q, virtual)) for r in range(2)]
     for p in procs:
         p.start()
     results = [q.get(timeout=150) for _ in range(2)]
@@ -77,6 +85,7 @@ def test_two_rank_sharded_propagator_matches_single_process():
 
 
 def _state_worker(rank, world, port, N, q):
+    import torch
     import torch.distributed as dist
     os.environ["MASTER_ADDR"] = "127.0.0.1"
     os.environ["MASTER_PORT"] = str(port)
@@ -88,9 +97,10 @@ def _state_worker(rank, world, port, N, q):
         def local_partial(start, count):
             t = oracle.node_times(wl.t0 + start * wl.dt, wl.dt, count, x)
             U, _, _ = oracle.interval_propagators(wl.H0, wl.Hk, wl.drive(t), w, wl.dt)
-            return oracle.propagate_unitary(U)
+            return torch.from_numpy(oracle.propagate_unitary(U))
 
-        q.put((rank, shard.sharded_state(local_partial, wl.N, wl.d, wl.psi0)))
+        psi = shard.sharded_state(local_partial, wl.N, wl.d, torch.from_numpy(wl.psi0), lambda P, v: P @ v)
+        q.put((rank, psi.numpy()))
     finally:
         dist.destroy_process_group()
 
@@ -121,6 +131,7 @@ def test_sharded_state_matches_single_process(world, N):
 
 def _failing_worker(rank, world, port, q):
     import datetime
+    import torch
     import torch.distributed as dist
     os.environ["MASTER_ADDR"] = "127.0.0.1"
     os.environ["MASTER_PORT"] = str(port)
@@ -130,10 +141,10 @@ def _failing_worker(rank, world, port, q):
     def local_partial(start, count):
         if rank == 1:
             raise RuntimeError("rank 1 failed while forming its partial product")
-        return np.eye(d, dtype=np.complex128)
+        return torch.eye(d, dtype=torch.complex128)
 
     try:
-        shard.sharded_state(local_partial, 8, d, np.eye(d)[0])
+        shard.sharded_state(local_partial, 8, d, torch.eye(d, dtype=torch.complex128)[0], lambda P, v: P @ v)
         q.put((rank, "ok"))
     except Exception as e:   # the failure reaches every rank as an exception, not a hang
         q.put((rank, type(e).__name__))
