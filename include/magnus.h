@@ -64,9 +64,12 @@ extern "C" {
  *   accumulators that stay exact for the leading digits, and combined in
  *   double-float (FP32 hi + lo, about 48 bits).  The exponential's intermediate
  *   matrices (powers, Taylor blocks, squarings, U_n) are stored and combined as
- *   double-float.  More slices give more accuracy (about beta*slices bits, down
- *   to the rounding of the FP32 accumulators).  Quadrature, Hbar_n, the norms,
- *   the trace phases, the state chain and re-orthonormalisation run in FP64. */
+ *   double-float, and so is Hbar_n (formed with error-free FP32
+ *   transformations from the operators and coefficients).  More slices give
+ *   more accuracy (about beta*slices bits, down to the rounding of the FP32
+ *   accumulators).  Operand entries are taken as FP32 pairs: magnitudes outside
+ *   about 2^-100 .. 2^100 lose precision.  The quadrature, the trace phases, the
+ *   norms' column sums, the state chain and re-orthonormalisation run in FP64. */
 #define MG_PREC_FP64   0
 #define MG_PREC_SPLIT  1
 /* mg_job only: the server looks the job's configuration up in its context's

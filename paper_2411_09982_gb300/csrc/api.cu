@@ -394,9 +394,10 @@ struct Engine {
     return df() ? launch_apply_phase_df(batch, d, tau, src, dst, ctx->stream)
                 : launch_apply_phase(batch, d, (long long)d * d, tau, src, dst, ctx->stream);
   }
-  // X = -i 2^{-sq} W (W FP64, X in engine storage; may alias); sq_dev: per-item counts
-  int scale_x(int batch, const double* W, double* X, int sq, const int* sq_dev = nullptr) {
-    return df() ? launch_scale_minus_i_df(batch, d, W, X, sq, ctx->stream, sq_dev)
+  // X = -i 2^{-sq} W (X in engine storage; may alias W); sq_dev: per-item counts.  W is
+  // FP64, or double-float when w_df (the split path's own Hbar builder writes it so)
+  int scale_x(int batch, const double* W, double* X, int sq, const int* sq_dev = nullptr, bool w_df = false) {
+    return df() ? launch_scale_minus_i_df(batch, d, W, X, sq, ctx->stream, sq_dev, w_df ? 1 : 0)
                 : launch_scale_minus_i(batch, d, W, X, sq_dev, sq, ctx->stream);
   }
   int to_fp64(int batch, const double* src, long long ss, double* dst, long long ds) {
@@ -562,7 +563,8 @@ int taylor_poly(mg_ctx* ctx, Engine& eng, int batch, double* W, const TaylorChoi
 }
 
 int expm_chunk(mg_ctx* ctx, Engine& eng, int batch, double* W, const double* tau, const double* norm1_dev,
-               double* U, long long sU, ExpmStats* st, const std::vector<double>* host_norms = nullptr) {
+               double* U, long long sU, ExpmStats* st, const std::vector<double>* host_norms = nullptr,
+               bool w_df = false) {
   PhaseRange range("expm");
   const int d = eng.d;
   const long long md = mat_doubles(d);
@@ -599,7 +601,7 @@ int expm_chunk(mg_ctx* ctx, Engine& eng, int batch, double* W, const double* tau
   }
 
   // X = -i 2^{-s} W   (in place, into the engine's storage format)
-  MG_TRY(eng.scale_x(batch, W, W, tc.s));
+  MG_TRY(eng.scale_x(batch, W, W, tc.s, nullptr, w_df));
   double *R, *Rn;
   MG_TRY(taylor_poly(ctx, eng, batch, W, tc, &R, &Rn));
   // squarings
@@ -624,10 +626,10 @@ int expm_chunk(mg_ctx* ctx, Engine& eng, int batch, double* W, const double* tau
 // reads its operands directly, so it squares into the other buffer and the active
 // items are copied back.
 int expm_chunk_dev(mg_ctx* ctx, Engine& eng, int batch, double* W, const double* tau, const int* sq_dev,
-                   const TaylorChoice& tc, int S, double* U) {
+                   const TaylorChoice& tc, int S, double* U, bool w_df) {
   PhaseRange range("expm");
   const long long md = mat_doubles(eng.d);
-  MG_TRY(eng.scale_x(batch, W, W, 0, sq_dev));
+  MG_TRY(eng.scale_x(batch, W, W, 0, sq_dev, w_df));
   double *R, *Rn;
   MG_TRY(taylor_poly(ctx, eng, batch, W, tc, &R, &Rn));
   AddTerms none;
@@ -1653,11 +1655,11 @@ int mg_evolve(mg_plan* p, int output, const double* in, double* out, int reorth_
     {
       PhaseRange range("hbar");
       MG_TRY(launch_build_omega(nb, d, p->Kx, p->dt, p->H0, p->Hk, p->c + (long long)n0 * p->Kx, W, tau, nrm,
-                                shift, /*write_shifted=*/1, sc, s));
+                                shift, /*write_shifted=*/1, sc, s, eng.df() ? 1 : 0));
     }
     double* Ubuf;
     MG_TRY(ws(ctx, WS_UBUF, md * nb, &Ubuf));
-    MG_TRY(expm_chunk(ctx, eng, nb, W, tau, nrm, Ubuf, md, &st));
+    MG_TRY(expm_chunk(ctx, eng, nb, W, tau, nrm, Ubuf, md, &st, nullptr, eng.df()));
     MG_TRY(fold_chunk(ctx, eng, ps, nb, Ubuf, reorth_every));
   }
   MG_TRY(finish_prop(ctx, eng, ps, out, flags, rep));
@@ -1756,7 +1758,7 @@ int process_chunk(mg_ctx* ctx, Engine& eng, std::vector<ChunkSeg>& segs, int fil
     const BatchJob& j = *g.job;
     MG_TRY(small_scratch(ctx, (size_t)j.K + 1 + g.n, &sc));
     MG_TRY(launch_build_omega(g.n, dp, j.K, j.dt, j.H0, j.Hk, j.c + (long long)g.a * j.K, W + g.off * md,
-                              tau + g.off, nrm + g.off, 1, 1, sc, s));
+                              tau + g.off, nrm + g.off, 1, 1, sc, s, eng.df() ? 1 : 0));
   }
   // FP64 norms: a non-finite norm fails its job only (its exponents are zeroed)
   std::vector<double> hn(fill);
@@ -1772,7 +1774,7 @@ int process_chunk(mg_ctx* ctx, Engine& eng, std::vector<ChunkSeg>& segs, int fil
       MG_CUDA_TRY(cudaMemsetAsync(tau + g.off, 0, sizeof(double) * g.n, s));
     }
   }
-  MG_TRY(expm_chunk(ctx, eng, fill, W, tau, nrm, Ub, md, st, &hn));
+  MG_TRY(expm_chunk(ctx, eng, fill, W, tau, nrm, Ub, md, st, &hn, eng.df()));
   std::vector<ChainSeg> cs;
   std::vector<double*> psis;
   for (const ChunkSeg& g : segs) {
@@ -2229,14 +2231,14 @@ int issue_chunk(mg_ctx* ctx, Engine& eng, GroupProgram& G, ChunkPlan& ch) {
     for (const ChunkSeg& g : ch.segs) {
       const BatchJob& j = *g.job;
       MG_TRY(launch_build_omega(g.n, dp, j.K, j.dt, j.H0, j.Hk, j.c + (long long)g.a * j.K, W + g.off * md,
-                                tau + g.off, nrm + g.off, 1, 1, sc, s));
+                                tau + g.off, nrm + g.off, 1, 1, sc, s, eng.df() ? 1 : 0));
     }
   }
   MG_TRY(launch_fail_segments((int)ch.segs.size(), fill, md, G.itab + ch.seg_tab, G.itab + ch.seg_of_item, nrm, tau,
                               G.job_fail, G.seg_bad, W, s));
   MG_TRY(launch_squarings(fill, nrm, G.tc.theta, G.S, 0, G.sq, G.overflow, ctx->timing ? ctx->dev_flops : nullptr,
                           8.0 * (double)dp * dp * dp, s));
-  MG_TRY(expm_chunk_dev(ctx, eng, fill, W, tau, G.sq, G.tc, G.S, Ub));
+  MG_TRY(expm_chunk_dev(ctx, eng, fill, W, tau, G.sq, G.tc, G.S, Ub, eng.df()));
   PhaseRange pr("propagate");
   // propagator jobs: tree product of the segment, folded into the running product
   for (const ChunkSeg& g : ch.segs) {

@@ -78,9 +78,10 @@ int launch_second_order_coefficients(int N, int P, int K, double dt, const doubl
 // omega[n] = dt H0 + sum_k c[n][k] H_k (minus tau_n I when write_shifted), with
 // tau[n] = Re tr/d (0 unless shift) and norm1[n] = ||omega_n - tau_n I||_1.
 // scratch: K + 1 + N doubles of device memory.
+// out_df32: omega is written as double-float (float4 per element; write_shifted required)
 int launch_build_omega(int N, int d, int K, double dt, const double* H0, const double* Hk,
                        const double* c, double* omega, double* tau, double* norm1, int shift,
-                       int write_shifted, double* scratch, cudaStream_t s);
+                       int write_shifted, double* scratch, cudaStream_t s, int out_df32 = 0);
 
 // tau_b = Re tr(A_b)/d (0 unless shift), dst_b = A_b - tau_b I, norm1_b = ||dst_b||_1
 int launch_shift_norm(int batch, int d, const double* A, double* dst, double* tau, double* norm1,
@@ -242,9 +243,10 @@ int launch_squarings(int n, const double* norm, double theta, int S, int uniform
                      double* flops_acc, double flops_per_square, cudaStream_t s);
 
 // Double-float (DF32) elementwise kernels of the split path; see elementwise.cu.
-// X_b = -i 2^{-sq_b} W_b with sq_b from sq_dev (device, per item) or the constant sq
-int launch_scale_minus_i_df(int batch, int d, const double* src_fp64, double* dst_df, int sq, cudaStream_t s,
-                            const int* sq_dev = nullptr);
+// X_b = -i 2^{-sq_b} W_b with sq_b from sq_dev (device, per item) or the constant sq;
+// W FP64 (in_df32 = 0) or double-float (in_df32 = 1), X double-float (may alias W)
+int launch_scale_minus_i_df(int batch, int d, const double* src, double* dst_df, int sq, cudaStream_t s,
+                            const int* sq_dev = nullptr, int in_df32 = 0);
 // dst[o] = sum_m coef[o * nsrc + m] src[m] + diag[o] I, o < nout <= 5, nsrc <= 4, one pass
 // (a destination may alias a source); FP64 and double-float storage
 int launch_lincomb_multi(int batch, int d, int nout, double* const* dst, int nsrc, const double* const* src,

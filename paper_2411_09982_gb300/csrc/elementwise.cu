@@ -250,21 +250,33 @@ __global__ void scale_minus_i_df_kernel(int per, const double* __restrict__ src,
   }
 }
 
-int launch_scale_minus_i_df(int batch, int d, const double* src_fp64, double* dst_df, int sq, cudaStream_t s,
-                            const int* sq_dev) {
-  if (batch <= 0) return MG_OK;
-  if (batch > 65535) return MG_EUNSUPPORTED;
-  const double f = std::ldexp(1.0, -sq);
-  scale_minus_i_df_kernel<<<item_grid(batch, (long long)d * d), 256, 0, s>>>(d * d, src_fp64,
-                                                                             reinterpret_cast<float4*>(dst_df), f,
-                                                                             sq_dev);
-  return check_launch("scale_minus_i_df_kernel");
+// the same from a double-float W: (-i)(a + i b) 2^{-s} = (b - i a) 2^{-s}, exact on the FP32 pipe
+__global__ void scale_minus_i_dfdf_kernel(int per, const float4* __restrict__ src, float4* __restrict__ dst, int sq,
+                                          const int* __restrict__ sq_dev) {
+  const long long base = (long long)blockIdx.y * per;
+  const int s = sq_dev ? sq_dev[blockIdx.y] : sq;
+  const int s1 = s / 2, s2 = s - s1;   // two factors keep each in range
+  const float f1 = __int_as_float((127 - s1) << 23), f2 = __int_as_float((127 - s2) << 23);
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < per; r += gridDim.x * blockDim.x) {
+    const float4 v = src[base + r];
+    dst[base + r] = make_float4((v.z * f1) * f2, (v.w * f1) * f2, -(v.x * f1) * f2, -(v.y * f1) * f2);
+  }
 }
 
-struct LincombDfArgs {
-  const float4* src[4];
-  df32 coef[4];
-};
+int launch_scale_minus_i_df(int batch, int d, const double* src, double* dst_df, int sq, cudaStream_t s,
+                            const int* sq_dev, int in_df32) {
+  if (batch <= 0) return MG_OK;
+  if (batch > 65535) return MG_EUNSUPPORTED;
+  const dim3 grid = item_grid(batch, (long long)d * d);
+  if (in_df32) {
+    scale_minus_i_dfdf_kernel<<<grid, 256, 0, s>>>(d * d, reinterpret_cast<const float4*>(src),
+                                                   reinterpret_cast<float4*>(dst_df), sq, sq_dev);
+    return check_launch("scale_minus_i_dfdf_kernel");
+  }
+  const double f = std::ldexp(1.0, -sq);
+  scale_minus_i_df_kernel<<<grid, 256, 0, s>>>(d * d, src, reinterpret_cast<float4*>(dst_df), f, sq_dev);
+  return check_launch("scale_minus_i_df_kernel");
+}
 
 // x + y in double-float with one fewer error-free step than df_add (error below
 // ~2^-46 of |x| + |y|; the combinations below add terms of like size)
@@ -272,6 +284,11 @@ __device__ __forceinline__ df32 df_add_fast(df32 x, df32 y) {
   const df32 s = two_sum(x.hi, y.hi);
   return fast_two_sum(s.hi, s.lo + (x.lo + y.lo));
 }
+
+struct LincombDfArgs {
+  const float4* src[4];
+  df32 coef[4];
+};
 
 __global__ void lincomb_df_kernel(int d, int nsrc, LincombDfArgs a, df32 diag, float4* __restrict__ dst) {
   const int per = d * d;

@@ -9,6 +9,7 @@
 // the precomputed operator traces) and the FP64 1-norm ||Hbar_n - tau_n I||_1
 // that selects the squaring count of the exponential.
 #include "common.cuh"
+#include "df32.cuh"
 
 namespace mg {
 
@@ -220,6 +221,105 @@ build_omega_kernel(int N, int d, int K, double dt, const double* __restrict__ H0
   }
 }
 
+// The same first-order term for the split-precision path, written as double-float
+// (float4 {re.hi, re.lo, im.hi, im.lo} per element, minus tau_n I) so that the
+// exponential's inputs never pass through the FP64 pipe: each operator entry is split
+// into two FP32 numbers once per block of NB intervals, and every interval's sum
+// dt H0 + sum_k c_{k,n} H_k is formed with error-free FP32 transformations
+// (about 2^-46 relative); only the phases tau_n (K + 1 FP64 FMAs per interval) and
+// the column sums of the norm bound stay in FP64.
+__device__ __forceinline__ float magnitude_upper_f(float x, float y) {
+  // |x + i y| of the hi parts, widened by 2^-20: also covers the lo parts (< 2^-23 relative)
+  return sqrtf(fmaf(x, x, y * y)) * (1.0f + 9.5367431640625e-07f) + 1e-30f;
+}
+__device__ __forceinline__ df32 dfx_add(df32 x, df32 y) {   // double-float sum, one error-free step fewer
+  const df32 s = two_sum(x.hi, y.hi);
+  return fast_two_sum(s.hi, s.lo + (x.lo + y.lo));
+}
+
+__global__ void __launch_bounds__(256)
+build_omega_df_kernel(int N, int d, int K, double dt, const double* __restrict__ H0,
+                      const double* __restrict__ Hk, const double* __restrict__ c,
+                      const double* __restrict__ tr, float4* __restrict__ omega,
+                      double* __restrict__ tau_out, unsigned long long* __restrict__ norm_bits, int shift) {
+  extern __shared__ double sm[];
+  double* taus = sm;                                  // [NB]
+  double* colpart = taus + OMEGA_NB;                  // [WARPS][NB][32]
+  df32* cs = reinterpret_cast<df32*>(colpart + OMEGA_WARPS * OMEGA_NB * 32);   // [NB][K]
+
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int j = blockIdx.x * OMEGA_COLS + lane;
+  const int n0 = blockIdx.y * OMEGA_NB;
+  const int nb = min(OMEGA_NB, N - n0);
+
+  for (int t = threadIdx.x; t < OMEGA_NB * K; t += blockDim.x) {
+    int b = t / K, k = t % K;
+    cs[t] = df_from_double((b < nb) ? c[(long long)(n0 + b) * K + k] : 0.0);
+  }
+  if (threadIdx.x < OMEGA_NB) {
+    int b = threadIdx.x;
+    double t = 0.0;
+    if (shift && b < nb) {
+      t = dt * tr[0];
+      for (int k = 0; k < K; ++k) t += c[(long long)(n0 + b) * K + k] * tr[1 + k];
+      t /= d;
+    }
+    taus[b] = t;
+    if (b < nb && blockIdx.x == 0 && tau_out) tau_out[n0 + b] = t;
+  }
+  __syncthreads();
+  const df32 dtd = df_from_double(dt);
+
+  double colsum[OMEGA_NB];
+#pragma unroll
+  for (int b = 0; b < OMEGA_NB; ++b) colsum[b] = 0.0;
+
+  if (j < d) {
+    const long long dd2 = (long long)d * d * 2;
+    const long long ddc = (long long)d * d;   // complex elements per matrix
+    for (int i = warp; i < d; i += OMEGA_WARPS) {
+      const long long off = 2 * ((long long)i * d + j);
+      const double2 h0 = *reinterpret_cast<const double2*>(H0 + off);
+      const df32 r0 = df_mul(df_from_double(h0.x), dtd), i0 = df_mul(df_from_double(h0.y), dtd);
+      df32 re[OMEGA_NB], im[OMEGA_NB];
+#pragma unroll
+      for (int b = 0; b < OMEGA_NB; ++b) { re[b] = r0; im[b] = i0; }
+      for (int k = 0; k < K; ++k) {
+        const double2 hk = *reinterpret_cast<const double2*>(Hk + k * dd2 + off);
+        if (((__double_as_longlong(hk.x) | __double_as_longlong(hk.y)) << 1) == 0) continue;   // sparse H_k
+        const df32 hx = df_from_double(hk.x), hy = df_from_double(hk.y);
+#pragma unroll
+        for (int b = 0; b < OMEGA_NB; ++b) {
+          const df32 ck = cs[b * K + k];
+          re[b] = dfx_add(re[b], df_mul(hx, ck));
+          im[b] = dfx_add(im[b], df_mul(hy, ck));
+        }
+      }
+#pragma unroll
+      for (int b = 0; b < OMEGA_NB; ++b) {
+        if (b < nb) {
+          df32 r = re[b];
+          if (i == j) r = df_add(r, df_from_double(-taus[b]));
+          colsum[b] += (double)magnitude_upper_f(r.hi, im[b].hi);
+          omega[(long long)(n0 + b) * ddc + off / 2] = make_float4(r.hi, r.lo, im[b].hi, im[b].lo);
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int b = 0; b < OMEGA_NB; ++b) colpart[(warp * OMEGA_NB + b) * 32 + lane] = colsum[b];
+  __syncthreads();
+  if (warp < OMEGA_NB && warp < nb) {
+    const int b = warp;
+    double s = 0.0;
+    for (int w = 0; w < OMEGA_WARPS; ++w) s += colpart[(w * OMEGA_NB + b) * 32 + lane];
+    if (j >= d) s = 0.0;
+    if (!(s <= 1.0e300)) s = __longlong_as_double(0x7ff0000000000000LL);
+    for (int o = 16; o > 0; o >>= 1) s = fmax(s, __shfl_xor_sync(0xffffffffu, s, o));
+    if (lane == 0) atomicMax(norm_bits + n0 + b, nonneg_bits(s));
+  }
+}
+
 __global__ void bits_to_double_kernel(int n, const unsigned long long* bits, double* out) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) out[i] = __longlong_as_double((long long)bits[i]);
@@ -227,7 +327,7 @@ __global__ void bits_to_double_kernel(int n, const unsigned long long* bits, dou
 
 int launch_build_omega(int N, int d, int K, double dt, const double* H0, const double* Hk,
                        const double* c, double* omega, double* tau, double* norm1, int shift,
-                       int write_shifted, double* scratch, cudaStream_t s) {
+                       int write_shifted, double* scratch, cudaStream_t s, int out_df32) {
   // scratch: (K+1) traces + N norm words
   if (N <= 0) return MG_OK;
   double* tr = scratch;
@@ -237,10 +337,18 @@ int launch_build_omega(int N, int d, int K, double dt, const double* H0, const d
   MG_CUDA_TRY(cudaMemsetAsync(bits, 0, sizeof(unsigned long long) * N, s));
   dim3 grid(ceil_div(d, OMEGA_COLS), ceil_div(N, OMEGA_NB));
   size_t smem = sizeof(double) * (OMEGA_NB * (K > 0 ? K : 1) + OMEGA_NB + OMEGA_WARPS * OMEGA_NB * 32);
-  MG_TRY(ensure_smem_limit(reinterpret_cast<const void*>(build_omega_kernel), (int)smem));
-  build_omega_kernel<<<grid, 256, smem, s>>>(N, d, K, dt, H0, Hk, c, tr, omega, tau, bits, shift,
-                                            write_shifted);
-  MG_TRY(check_launch("build_omega_kernel"));
+  if (out_df32) {
+    if (!write_shifted) return MG_EINVAL;
+    MG_TRY(ensure_smem_limit(reinterpret_cast<const void*>(build_omega_df_kernel), (int)smem));
+    build_omega_df_kernel<<<grid, 256, smem, s>>>(N, d, K, dt, H0, Hk, c, tr, reinterpret_cast<float4*>(omega), tau,
+                                                 bits, shift);
+    MG_TRY(check_launch("build_omega_df_kernel"));
+  } else {
+    MG_TRY(ensure_smem_limit(reinterpret_cast<const void*>(build_omega_kernel), (int)smem));
+    build_omega_kernel<<<grid, 256, smem, s>>>(N, d, K, dt, H0, Hk, c, tr, omega, tau, bits, shift,
+                                              write_shifted);
+    MG_TRY(check_launch("build_omega_kernel"));
+  }
   if (norm1) {
     bits_to_double_kernel<<<ceil_div(N, 256), 256, 0, s>>>(N, bits, norm1);
     MG_TRY(check_launch("bits_to_double_kernel"));
