@@ -488,6 +488,11 @@ int mg_ctx_enable_gemm_timing(mg_ctx* ctx, int enable);
  * stall_test = 0 restores normal products.  MG_EINVAL for seconds outside
  * [0, 4]. */
 int mg_ctx_set_wait_limit(mg_ctx* ctx, double seconds, int stall_test);
+/* K per pipeline stage of the tensor-core product (MG_PREC_SPLIT): 32 (the default;
+ * 64-byte operand rows, two MMA K-steps per stage) or 16 (32-byte rows, one K-step
+ * per stage: half the shared memory per stage, so twice as many stages in flight).
+ * The result does not depend on it.  MG_EINVAL for other values. */
+int mg_ctx_set_stage_k(mg_ctx* ctx, int stage_k);
 int mg_ctx_gemm_stats(mg_ctx* ctx, int64_t* launches, double* ms, double* flops, int reset);
 
 const char* mg_strerror(int code);

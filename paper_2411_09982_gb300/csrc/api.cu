@@ -127,6 +127,7 @@ struct mg_ctx {
   // algorithmic work of predicated squaring launches, added on the device (timing on)
   double* dev_flops = nullptr;
   std::string tune_cache;   // tuning cache consulted by servers for MG_PREC_AUTO jobs
+  int stage_k = 32;         // K per pipeline stage of the split product (mg_ctx_set_stage_k)
 };
 
 struct mg_plan {
@@ -354,6 +355,7 @@ struct Engine {
     c.stall = ctx->stall_test;
     c.item_sq = item_sq;
     c.sq_step = sq_step;
+    c.stage_k = ctx->stage_k;
     return c;
   }
 
@@ -1159,6 +1161,12 @@ int mg_ctx_gemm_stats(mg_ctx* ctx, int64_t* launches, double* ms, double* flops,
     MG_CUDA_TRY(cudaMemsetAsync(ctx->dev_flops, 0, sizeof(double), ctx->stream));
     MG_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
   }
+  return MG_OK;
+}
+
+int mg_ctx_set_stage_k(mg_ctx* ctx, int stage_k) {
+  if (!ctx || (stage_k != 16 && stage_k != 32)) return MG_EINVAL;
+  ctx->stage_k = stage_k;
   return MG_OK;
 }
 

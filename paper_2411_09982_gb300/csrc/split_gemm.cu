@@ -63,9 +63,13 @@ namespace mg {
 // ---------------------------------------------------------------------------
 constexpr int SG_BM = 128;      // output rows per tile
 constexpr int SG_BNC = 64;      // complex output columns per tile (N = 128 real)
-constexpr int SG_BK = 32;       // K per stage (64 bytes of BF16: one SW64 atom row, two MMA K-steps)
+constexpr int SG_BK = 32;       // K granularity of the digit layout (each half of K is a multiple of it)
 constexpr int SG_MMA_K = 16;    // K of one tcgen05.mma kind::f16
-constexpr int SG_TILE_BYTES = SG_BM * SG_BK * 2;   // 8192 bytes per digit tile
+// K per pipeline stage: 32 (64-byte rows, SWIZZLE_64B, two MMA K-steps per stage) or 16
+// (32-byte rows, SWIZZLE_32B, one K-step: half the bytes per stage, twice the stages)
+template <int BK> struct StageK {
+  static constexpr int tile_bytes = SG_BM * BK * 2;   // bytes per digit tile of one stage
+};
 
 struct SplitGeom {
   int d, L, beta;
@@ -436,6 +440,21 @@ __device__ __forceinline__ uint64_t sw64_kmajor_desc(uint32_t saddr) {
   return desc;
 }
 
+// The same for 32-byte rows: SWIZZLE_32B, 8-row core groups 256 bytes apart.
+__device__ __forceinline__ uint64_t sw32_kmajor_desc(uint32_t saddr) {
+  uint64_t desc = 0;
+  desc |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  desc |= (uint64_t)1 << 16;            // leading-dimension offset (unused with swizzle)
+  desc |= (uint64_t)(256 >> 4) << 32;   // stride-dimension offset
+  desc |= (uint64_t)1 << 46;            // descriptor version
+  desc |= (uint64_t)6 << 61;            // SWIZZLE_32B
+  return desc;
+}
+template <int BK>
+__device__ __forceinline__ uint64_t kmajor_desc(uint32_t saddr) {
+  return BK == 32 ? sw64_kmajor_desc(saddr) : sw32_kmajor_desc(saddr);
+}
+
 // Instruction descriptor: kind::f16, A = B = BF16, D = F32, both K-major, M = 128, N = 128.
 constexpr uint32_t kIdescBf16 = (1u << 4) | (1u << 7) | (1u << 10) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
 
@@ -471,7 +490,7 @@ struct SplitEpi {
 // item b is computed only while ctl.item_sq[b] > ctl.sq_step (per-item squaring
 // counts: an item whose squarings are done keeps its matrix, which the product
 // would otherwise overwrite in place); the CTAs of an inactive item return at once.
-template <int L, int STAGES>
+template <int L, int STAGES, int BK>
 __global__ void __launch_bounds__(SG_THREADS, 1)
 split_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                   int d, int Kp, int Mp, int Np, int beta, const int* __restrict__ ea,
@@ -479,7 +498,8 @@ split_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
                   int* __restrict__ status, SplitCtl ctl) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  constexpr int STAGE_BYTES = 2 * L * SG_TILE_BYTES;
+  constexpr int TILE_BYTES = StageK<BK>::tile_bytes;
+  constexpr int STAGE_BYTES = 2 * L * TILE_BYTES;
   constexpr int RING_BYTES = STAGES * STAGE_BYTES > SG_EPI_BYTES ? STAGES * STAGE_BYTES : SG_EPI_BYTES;
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + RING_BYTES);
   uint64_t* empty = full + STAGES;
@@ -493,7 +513,7 @@ split_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nt = blockIdx.x, mt = blockIdx.y, b = blockIdx.z;
   if (ctl.item_sq && ctl.item_sq[b] <= ctl.sq_step) return;   // uniform over the CTA
-  const int num_k = Kp / SG_BK;
+  const int num_k = Kp / BK;
   const int nkh = num_k / 2;   // K stages of the real half
 
   if (threadIdx.x == 0) {
@@ -539,13 +559,13 @@ split_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
         }
         unsigned char* st = smem + s * STAGE_BYTES;
         mbar_expect_tx(&full[s], STAGE_BYTES);
-        tma_load_4d(st, &tmA, &full[s], kb * SG_BK, mt * SG_BM, 0, b);
+        tma_load_4d(st, &tmA, &full[s], kb * BK, mt * SG_BM, 0, b);
         // B: the same K range in both halves of K; planes [Re B; Im B] (1, 2) for the
         // real half, [-Im B; Re B] (0, 1) for the imaginary half
         const bool imag = kb >= nkh;
-        const int kbb = (imag ? kb - nkh : kb) * SG_BK;
+        const int kbb = (imag ? kb - nkh : kb) * BK;
         const int plane0 = imag ? 0 : 1;
-        tma_load_5d(st + L * SG_TILE_BYTES, &tmB, &full[s], kbb, nt * SG_BNC, plane0, 0, b);
+        tma_load_5d(st + L * TILE_BYTES, &tmB, &full[s], kbb, nt * SG_BNC, plane0, 0, b);
         issued = kb + 1;
       }
       // never leave the CTA with a bulk copy still in flight into its shared memory
@@ -571,10 +591,10 @@ split_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
         }
         tc_fence_after();
         const uint32_t a0 = smem_u32(smem + s * STAGE_BYTES);
-        const uint32_t b0 = a0 + L * SG_TILE_BYTES;
+        const uint32_t b0 = a0 + L * TILE_BYTES;
         bool first[SG_GROUPS] = {kb == 0, kb == 0, kb == 0, kb == 0};
 #pragma unroll
-        for (int kk = 0; kk < SG_BK / SG_MMA_K; ++kk) {
+        for (int kk = 0; kk < BK / SG_MMA_K; ++kk) {
 #pragma unroll
           for (int sa = 0; sa < L; ++sa) {
 #pragma unroll
@@ -582,8 +602,8 @@ split_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
               const int g = (sa + sb) < SG_GROUPS - 1 ? (sa + sb) : SG_GROUPS - 1;
               const uint32_t acc = first[g] ? 0u : 1u;
               first[g] = false;
-              tc_mma_bf16(tmem + g * 128, sw64_kmajor_desc(a0 + sa * SG_TILE_BYTES + kk * SG_MMA_K * 2),
-                          sw64_kmajor_desc(b0 + sb * SG_TILE_BYTES + kk * SG_MMA_K * 2), kIdescBf16, acc);
+              tc_mma_bf16(tmem + g * 128, kmajor_desc<BK>(a0 + sa * TILE_BYTES + kk * SG_MMA_K * 2),
+                          kmajor_desc<BK>(b0 + sb * TILE_BYTES + kk * SG_MMA_K * 2), kIdescBf16, acc);
             }
           }
         }
@@ -705,15 +725,16 @@ static int get_encoder() {
 // B digits: dims {Kh, d valid rows (of Np / 2 allocated), 3 planes, L, batch};
 // box {32, 64, planes, digits, 1}; rows from d on read as zeros
 static int make_bplane_map(CUtensorMap* map, const void* base, int Kh, int rows, int valid_rows, int L, int batch,
-                           int box_planes, int box_digits) {
+                           int box_planes, int box_digits, int bk) {
   MG_TRY(get_encoder());
   cuuint64_t dims[5] = {(cuuint64_t)Kh, (cuuint64_t)valid_rows, 3, (cuuint64_t)L, (cuuint64_t)batch};
   cuuint64_t strides[4] = {(cuuint64_t)Kh * 2, (cuuint64_t)rows * Kh * 2, (cuuint64_t)3 * rows * Kh * 2,
                            (cuuint64_t)L * 3 * rows * Kh * 2};
-  cuuint32_t box[5] = {(cuuint32_t)SG_BK, (cuuint32_t)SG_BNC, (cuuint32_t)box_planes, (cuuint32_t)box_digits, 1};
+  cuuint32_t box[5] = {(cuuint32_t)bk, (cuuint32_t)SG_BNC, (cuuint32_t)box_planes, (cuuint32_t)box_digits, 1};
   cuuint32_t estr[5] = {1, 1, 1, 1, 1};
   CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<void*>(base), dims, strides, box,
-                        estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+                        estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        bk == 32 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_32B,
                         CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) {
     set_last_message("cuTensorMapEncodeTiled failed (%d): Kh=%d rows=%d L=%d batch=%d", (int)r, Kh, rows, L, batch);
@@ -723,14 +744,15 @@ static int make_bplane_map(CUtensorMap* map, const void* base, int Kh, int rows,
 }
 // A digits: dims {Kp, d valid rows (of `rows` allocated), L, batch}; rows from d on read as zeros
 static int make_digit_map(CUtensorMap* map, const void* base, int Kp, int rows, int valid_rows, int L, int batch,
-                          int box_rows = SG_BM, int box_slices = -1) {
+                          int bk, int box_rows = SG_BM, int box_slices = -1) {
   MG_TRY(get_encoder());
   cuuint64_t dims[4] = {(cuuint64_t)Kp, (cuuint64_t)valid_rows, (cuuint64_t)L, (cuuint64_t)batch};
   cuuint64_t strides[3] = {(cuuint64_t)Kp * 2, (cuuint64_t)rows * Kp * 2, (cuuint64_t)L * rows * Kp * 2};
-  cuuint32_t box[4] = {(cuuint32_t)SG_BK, (cuuint32_t)box_rows, (cuuint32_t)(box_slices < 0 ? L : box_slices), 1};
+  cuuint32_t box[4] = {(cuuint32_t)bk, (cuuint32_t)box_rows, (cuuint32_t)(box_slices < 0 ? L : box_slices), 1};
   cuuint32_t estr[4] = {1, 1, 1, 1};
   CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(base), dims, strides, box,
-                        estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+                        estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        bk == 32 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_32B,
                         CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) {
     set_last_message("cuTensorMapEncodeTiled failed (%d): Kp=%d rows=%d L=%d batch=%d", (int)r, Kp, rows, L,
@@ -740,28 +762,36 @@ static int make_digit_map(CUtensorMap* map, const void* base, int Kp, int rows, 
   return MG_OK;
 }
 
-template <int L>
+template <int L, int BK>
 static constexpr int stages_for() {
   // ring budget 224 KiB (the opt-in limit is 227 KiB per block; 2 KiB go to barriers and alignment)
-  return (229376 / (2 * L * SG_TILE_BYTES)) > 8 ? 8
-         : ((229376 / (2 * L * SG_TILE_BYTES)) < 1 ? 1 : (229376 / (2 * L * SG_TILE_BYTES)));
+  return (229376 / (2 * L * StageK<BK>::tile_bytes)) > 8 ? 8
+         : ((229376 / (2 * L * StageK<BK>::tile_bytes)) < 1 ? 1 : (229376 / (2 * L * StageK<BK>::tile_bytes)));
+}
+
+template <int L, int BK>
+static int launch_split_gemm_LB(const SplitGeom& g, int batch, const __nv_bfloat16* Ad, const int* ea,
+                                const __nv_bfloat16* Bd, const int* eb, double* C, long long sC,
+                                const SplitEpi& epi, int* status, const SplitCtl& ctl, cudaStream_t s) {
+  constexpr int STAGES = stages_for<L, BK>();
+  CUtensorMap ma, mb;
+  MG_TRY(make_digit_map(&ma, Ad, g.Kp, g.Mp, g.d, L, batch, BK));
+  MG_TRY(make_bplane_map(&mb, Bd, g.Kh(), g.Np / 2, g.d, L, batch, 2, L, BK));
+  const size_t ring = std::max<size_t>((size_t)STAGES * 2 * L * StageK<BK>::tile_bytes, (size_t)SG_EPI_BYTES);
+  const size_t smem = ring + 1024 /*barriers, exponents*/ + 1024 /*align*/;
+  auto kern = split_gemm_kernel<L, STAGES, BK>;
+  MG_TRY(ensure_smem_limit(reinterpret_cast<const void*>(kern), (int)smem));
+  kern<<<dim3(ceil_div(g.d, SG_BNC), g.Mp / SG_BM, batch), SG_THREADS, smem, s>>>(
+      ma, mb, g.d, g.Kp, g.Mp, g.Np, g.beta, ea, eb, C, sC, epi, status, ctl);
+  return check_launch("split_gemm_kernel");
 }
 
 template <int L>
 static int launch_split_gemm_L(const SplitGeom& g, int batch, const __nv_bfloat16* Ad, const int* ea,
                                const __nv_bfloat16* Bd, const int* eb, double* C, long long sC,
                                const SplitEpi& epi, int* status, const SplitCtl& ctl, cudaStream_t s) {
-  constexpr int STAGES = stages_for<L>();
-  CUtensorMap ma, mb;
-  MG_TRY(make_digit_map(&ma, Ad, g.Kp, g.Mp, g.d, L, batch));
-  MG_TRY(make_bplane_map(&mb, Bd, g.Kh(), g.Np / 2, g.d, L, batch, 2, L));
-  const size_t ring = std::max<size_t>((size_t)STAGES * 2 * L * SG_TILE_BYTES, (size_t)SG_EPI_BYTES);
-  const size_t smem = ring + 1024 /*barriers, exponents*/ + 1024 /*align*/;
-  auto kern = split_gemm_kernel<L, STAGES>;
-  MG_TRY(ensure_smem_limit(reinterpret_cast<const void*>(kern), (int)smem));
-  kern<<<dim3(ceil_div(g.d, SG_BNC), g.Mp / SG_BM, batch), SG_THREADS, smem, s>>>(
-      ma, mb, g.d, g.Kp, g.Mp, g.Np, g.beta, ea, eb, C, sC, epi, status, ctl);
-  return check_launch("split_gemm_kernel");
+  if (ctl.stage_k == 16) return launch_split_gemm_LB<L, 16>(g, batch, Ad, ea, Bd, eb, C, sC, epi, status, ctl, s);
+  return launch_split_gemm_LB<L, 32>(g, batch, Ad, ea, Bd, eb, C, sC, epi, status, ctl, s);
 }
 
 template <int L, typename T>
