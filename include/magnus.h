@@ -489,9 +489,13 @@ int mg_ctx_enable_gemm_timing(mg_ctx* ctx, int enable);
  * [0, 4]. */
 int mg_ctx_set_wait_limit(mg_ctx* ctx, double seconds, int stall_test);
 /* K per pipeline stage of the tensor-core product (MG_PREC_SPLIT): 32 (the default;
- * 64-byte operand rows, two MMA K-steps per stage) or 16 (32-byte rows, one K-step
- * per stage: half the shared memory per stage, so twice as many stages in flight).
- * The result does not depend on it.  MG_EINVAL for other values. */
+ * 64-byte operand rows, two MMA K-steps per stage), 16 (32-byte rows, one K-step per
+ * stage: half the shared memory per stage, so twice as many stages in flight) or 64
+ * (128-byte rows, four K-steps; taken where slices <= 3 and d rounded up to 32 is a
+ * multiple of 64, else 32).  The result does not depend on it.  Measured on GB300
+ * (algorithmic TFLOP/s of 32 products of d = 700): 3 digits 141 / 187 / 198 and
+ * 2 digits 195 / 254 / 292 for K = 16 / 32 / 64; at d = 729 with 6 digits K = 16
+ * is 5% slower than 32.  MG_EINVAL for other values. */
 int mg_ctx_set_stage_k(mg_ctx* ctx, int stage_k);
 int mg_ctx_gemm_stats(mg_ctx* ctx, int64_t* launches, double* ms, double* flops, int reset);
 

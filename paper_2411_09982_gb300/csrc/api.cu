@@ -1165,7 +1165,7 @@ int mg_ctx_gemm_stats(mg_ctx* ctx, int64_t* launches, double* ms, double* flops,
 }
 
 int mg_ctx_set_stage_k(mg_ctx* ctx, int stage_k) {
-  if (!ctx || (stage_k != 16 && stage_k != 32)) return MG_EINVAL;
+  if (!ctx || (stage_k != 16 && stage_k != 32 && stage_k != 64)) return MG_EINVAL;
   ctx->stage_k = stage_k;
   return MG_OK;
 }

@@ -450,9 +450,19 @@ __device__ __forceinline__ uint64_t sw32_kmajor_desc(uint32_t saddr) {
   desc |= (uint64_t)6 << 61;            // SWIZZLE_32B
   return desc;
 }
+// The same for 128-byte rows: SWIZZLE_128B, 8-row core groups 1024 bytes apart.
+__device__ __forceinline__ uint64_t sw128_kmajor_desc(uint32_t saddr) {
+  uint64_t desc = 0;
+  desc |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  desc |= (uint64_t)1 << 16;            // leading-dimension offset (unused with swizzle)
+  desc |= (uint64_t)(1024 >> 4) << 32;  // stride-dimension offset
+  desc |= (uint64_t)1 << 46;            // descriptor version
+  desc |= (uint64_t)2 << 61;            // SWIZZLE_128B
+  return desc;
+}
 template <int BK>
 __device__ __forceinline__ uint64_t kmajor_desc(uint32_t saddr) {
-  return BK == 32 ? sw64_kmajor_desc(saddr) : sw32_kmajor_desc(saddr);
+  return BK == 64 ? sw128_kmajor_desc(saddr) : (BK == 32 ? sw64_kmajor_desc(saddr) : sw32_kmajor_desc(saddr));
 }
 
 // Instruction descriptor: kind::f16, A = B = BF16, D = F32, both K-major, M = 128, N = 128.
@@ -734,7 +744,8 @@ static int make_bplane_map(CUtensorMap* map, const void* base, int Kh, int rows,
   cuuint32_t estr[5] = {1, 1, 1, 1, 1};
   CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<void*>(base), dims, strides, box,
                         estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                        bk == 32 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_32B,
+                        bk == 64 ? CU_TENSOR_MAP_SWIZZLE_128B
+                                 : (bk == 32 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_32B),
                         CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) {
     set_last_message("cuTensorMapEncodeTiled failed (%d): Kh=%d rows=%d L=%d batch=%d", (int)r, Kh, rows, L, batch);
@@ -752,7 +763,8 @@ static int make_digit_map(CUtensorMap* map, const void* base, int Kp, int rows, 
   cuuint32_t estr[4] = {1, 1, 1, 1};
   CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(base), dims, strides, box,
                         estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                        bk == 32 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_32B,
+                        bk == 64 ? CU_TENSOR_MAP_SWIZZLE_128B
+                                 : (bk == 32 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_32B),
                         CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) {
     set_last_message("cuTensorMapEncodeTiled failed (%d): Kp=%d rows=%d L=%d batch=%d", (int)r, Kp, rows, L,
@@ -791,6 +803,10 @@ static int launch_split_gemm_L(const SplitGeom& g, int batch, const __nv_bfloat1
                                const __nv_bfloat16* Bd, const int* eb, double* C, long long sC,
                                const SplitEpi& epi, int* status, const SplitCtl& ctl, cudaStream_t s) {
   if (ctl.stage_k == 16) return launch_split_gemm_LB<L, 16>(g, batch, Ad, ea, Bd, eb, C, sC, epi, status, ctl, s);
+  // 64 only where each half of K is a whole number of 64-wide stages and two stages fit
+  if constexpr (2 * 2 * L * StageK<64>::tile_bytes <= 229376)
+    if (ctl.stage_k == 64 && g.Kh() % 64 == 0)
+      return launch_split_gemm_LB<L, 64>(g, batch, Ad, ea, Bd, eb, C, sC, epi, status, ctl, s);
   return launch_split_gemm_LB<L, 32>(g, batch, Ad, ea, Bd, eb, C, sC, epi, status, ctl, s);
 }
 
