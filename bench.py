@@ -326,25 +326,29 @@ def run_ours(args):
     if result is not None and ws == 1 and not args.no_serving:
         # the served stream beside the headline: the first requests of the Poisson(200/s)
         # mixed stream at the stated rate (an overload) and at half the capacity that run
-        # measured; state requests of d >= 256 on the action path, the rest split 6 digits
-        with torch.cuda.stream(stream):
-            over = serve_prefix(M, W, torch, ctx, dev, args.serve_requests, 200.0, args.slices, True)
-            cap = over["requests"] / over["makespan_s"]
-            half = serve_prefix(M, W, torch, ctx, dev, args.serve_requests, 0.5 * cap, args.slices, True)
-        keys = ("offered_rate_per_s", "latency_ms", "intervals_per_s", "completed", "makespan_s", "arrival_span_s",
-                "admission_retries", "clocks")
-        result["serving"] = {
-            "workload": f"first {over['requests']} requests of the Poisson(200/s) mixed stream "
-                        f"(d up to {over['d_max']}, {over['intervals_total']} intervals, state or full U)",
-            "state_requests": "action path (FP64) from d = 256, split 6 digits below",
-            "at_stated_rate": {k: over[k] for k in keys},
-            "capacity_requests_per_s": cap,
-            "at_half_capacity": {k: half[k] for k in keys},
-        }
-        if not args.no_cpu_baseline:
-            import oracle
-            acc, _ = serve_accuracy(oracle, np, half, len(os.sched_getaffinity(0)))
-            result["serving"]["accuracy"] = acc
+        # measured; state requests of d >= 256 on the action path, the rest split 6 digits.
+        # A failure here is reported in the line, not raised: the headline stands.
+        try:
+            with torch.cuda.stream(stream):
+                over = serve_prefix(M, W, torch, ctx, dev, args.serve_requests, 200.0, args.slices, True)
+                cap = over["requests"] / over["makespan_s"]
+                half = serve_prefix(M, W, torch, ctx, dev, args.serve_requests, 0.5 * cap, args.slices, True)
+            keys = ("offered_rate_per_s", "latency_ms", "intervals_per_s", "completed", "failed", "makespan_s",
+                    "arrival_span_s", "admission_retries", "clocks")
+            result["serving"] = {
+                "workload": f"first {over['requests']} requests of the Poisson(200/s) mixed stream "
+                            f"(d up to {over['d_max']}, {over['intervals_total']} intervals, state or full U)",
+                "state_requests": "action path (FP64) from d = 256, split 6 digits below",
+                "at_stated_rate": {k: over[k] for k in keys},
+                "capacity_requests_per_s": cap,
+                "at_half_capacity": {k: half[k] for k in keys},
+            }
+            if not args.no_cpu_baseline:
+                import oracle
+                acc, _ = serve_accuracy(oracle, np, half, len(os.sched_getaffinity(0)))
+                result["serving"]["accuracy"] = acc
+        except Exception as e:   # noqa: BLE001
+            result["serving"] = {"error": f"{type(e).__name__}: {e}"}
     ctx.close()
     if ws > 1:
         torch.distributed.destroy_process_group()
@@ -386,10 +390,11 @@ def run_shard(args):
     S = torch.from_numpy(sn).to(dev)
     H0, Hk = torch.from_numpy(wl.H0).to(dev), torch.from_numpy(wl.Hk).to(dev)
     prec = M.MG_PREC_SPLIT if args.precision == "split" else M.MG_PREC_FP64
+    plan = M.Plan(ctx, H0, Hk, prec, args.slices)
 
     def step():
         return shard.evolve_propagator_sharded(ctx, H0, Hk, S, N, wl.P, wl.t0, wl.dt, w, prec, args.slices,
-                                               virtual=args.virtual)
+                                               virtual=args.virtual, plan=plan)
 
     for _ in range(max(3, args.warmup)):
         step()
@@ -412,6 +417,7 @@ def run_shard(args):
                           "unitarity_check": float((U.conj().T @ U - torch.eye(wl.d, device=dev,
                                                                                dtype=U.dtype)).abs().max())}),
               flush=True)
+    plan.close()
     ctx.close()
     dist.destroy_process_group()
 
@@ -460,12 +466,12 @@ def serve_prefix(M, W, torch, ctx, dev, requests, rate, slices, action):
     clk = clocks.stop()
     st = srv.stats()
     srv.close()
-    assert all(r["status"] == 0 for r in reps), "a served request failed"
-    lat = sorted(r["latency_ms"] for r in reps)
+    failed = sum(1 for r in reps if r is None or r["status"] != 0)
+    lat = sorted(r["latency_ms"] for r in reps if r is not None)
     intervals = sum(wl.N for wl in built)
     return {"requests": len(ids), "offered_rate_per_s": rate, "arrival_span_s": stream_spec[-1][0],
             "d_max": max(wl.d for wl in built), "intervals_total": intervals, "makespan_s": wall,
-            "intervals_per_s": intervals / wall, "completed": st["completed"],
+            "intervals_per_s": intervals / wall, "completed": st["completed"], "failed": failed,
             "latency_ms": {"p50": st["p50_ms"], "p99": st["p99_ms"], "max": lat[-1]},
             "admission_retries": rejected, "clocks": clk, "_built": built, "_inputs": inputs, "_fp64": flagged}
 

@@ -315,9 +315,10 @@ int mg_ctx_set_tune_cache(mg_ctx* ctx, const char* path);
  * pointers only; the input and output buffers and the plans' coefficient
  * buffers are bound into the graph, so a replay evolves whatever they hold at
  * launch time: call mg_set_controls with the same N, P and dt (new drive
- * samples) and/or rewrite in[i] between launches.  The context's stream must
- * not be the legacy default stream (it cannot be captured); the graph has a
- * workspace of its own.  Action-flagged state jobs (MG_FLAG_STATE_ACTION) are
+ * samples) and/or rewrite in[i] between launches.  The plans, the buffers and
+ * the context must outlive the graph.  The context's stream must not be the
+ * legacy default stream (it cannot be captured); the graph has a workspace of
+ * its own.  Action-flagged state jobs (MG_FLAG_STATE_ACTION) are
  * rejected with MG_EUNSUPPORTED.  Creation runs the batch once uncaptured (which
  * sizes the workspace), so it costs one evolution.
  * mg_batch_graph_launch synchronises the context's stream; job_status (HOST,

@@ -126,18 +126,22 @@ def max_over_ranks(value: float, group=None, device=None) -> float:
 # ----------------------------------------------------------------------------
 def evolve_propagator_sharded(ctx, H0, Hk, samples, N: int, P: int, t0: float, dt: float, w,
                               precision: Optional[int] = None, slices: int = 6, group=None, virtual: int = 1,
-                              reorth_every: int = 0):
+                              reorth_every: int = 0, plan=None):
     """U(T) of one job whose N intervals are shared by the ranks of `group` (each on its own
     GPU, ctx that GPU's context): every rank evolves its ranges through mg_set_controls /
     mg_evolve (samples: the job's N x P x K drive samples on this device; a range takes its
     rows and starts at t0 + start dt), the partials are all-gathered (NCCL), and every rank
-    multiplies them in time order with mg_cgemm on its GPU.  Returns the d x d device tensor."""
+    multiplies them in time order with mg_cgemm on its GPU.  Returns the d x d device tensor.
+    `plan` (optional) is a Plan of H0, H_k in this precision to reuse across calls (else one
+    is made and freed here)."""
     import torch
     from . import magnus as M
     prec = M.MG_PREC_SPLIT if precision is None else precision
     d = int(H0.shape[0])
     dev = samples.device
-    plan = M.Plan(ctx, H0, Hk, prec, slices)
+    own = plan is None
+    if own:
+        plan = M.Plan(ctx, H0, Hk, prec, slices)
 
     def local_partial(start, count):
         plan.set_controls(count, P, t0 + start * dt, dt, w, samples[start:start + count].contiguous())
@@ -158,4 +162,5 @@ def evolve_propagator_sharded(ctx, H0, Hk, samples, N: int, P: int, t0: float, d
     try:
         return sharded_propagator(local_partial, N, d, mul, group=group, virtual=virtual, device=dev)
     finally:
-        plan.close()
+        if own:
+            plan.close()
