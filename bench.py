@@ -52,8 +52,10 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["split", "fp64"], default="split")
     ap.add_argument("--slices", type=int, default=6)
-    ap.add_argument("--stage-k", type=int, default=32, choices=[16, 32],
+    ap.add_argument("--stage-k", type=int, default=32, choices=[16, 32, 64],
                     help="K per pipeline stage of the split product (mg_ctx_set_stage_k)")
+    ap.add_argument("--digit-pairs", type=int, default=None, choices=[0, 1],
+                    help="paired digit layout of the split product (mg_ctx_set_digit_pairs)")
     ap.add_argument("--intervals", type=int, default=2000)
     ap.add_argument("--e2e-steps", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -188,6 +190,8 @@ def run_ours(args):
     stream = torch.cuda.Stream(device=dev)
     ctx = M.Context(local, stream)
     ctx.set_stage_k(args.stage_k)
+    if args.digit_pairs is not None:
+        ctx.set_digit_pairs(args.digit_pairs)
     prec = M.MG_PREC_SPLIT if args.precision == "split" else M.MG_PREC_FP64
     N = args.intervals
 

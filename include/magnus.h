@@ -496,8 +496,23 @@ int mg_ctx_set_wait_limit(mg_ctx* ctx, double seconds, int stall_test);
  * multiple of 64, else 32).  The result does not depend on it.  Measured on GB300
  * (algorithmic TFLOP/s of 32 products of d = 700): 3 digits 141 / 187 / 198 and
  * 2 digits 195 / 254 / 292 for K = 16 / 32 / 64; at d = 729 with 6 digits K = 16
- * is 5% slower than 32.  MG_EINVAL for other values. */
+ * is 5% slower than 32.  With 8 slices a 32-deep stage leaves room for only one
+ * stage, so the product takes 16 there whatever is set (35 -> 53 TFLOP/s at d = 512).
+ * MG_EINVAL for other values. */
 int mg_ctx_set_stage_k(mg_ctx* ctx, int stage_k);
+/* Operand layout of the tensor-core product (MG_PREC_SPLIT) for an even number of
+ * slices: on = 1 stores digits 2g and 2g + 1 of an element side by side (per 16 K
+ * values of a row, 16 of the even digit, then 16 of the odd one), so each 64-byte row
+ * of a pipeline stage 16 deep in K carries two digits; the stage then takes half the
+ * shared memory of the default 32-deep stage and twice as many stages are in flight.
+ * It replaces mg_ctx_set_stage_k's choice for even slices; odd slice counts keep the
+ * digit-major layout.  The result is bit-identical either way.  on = 0 (the default):
+ * one plane per digit.  MG_EINVAL for other values.  A change applies to products
+ * issued afterwards (a captured batch graph keeps the layout it was captured with).
+ * Measured on GB300 (algorithmic TFLOP/s, 32 products): d = 729, 6 slices 76.5 paired
+ * vs 78.7 digit-major; d = 700, 4 slices 124 vs 142; d = 512, 8 slices 53.0 vs 35.2
+ * (52.7 with digit-major 16-deep stages, which 8 slices now take by default). */
+int mg_ctx_set_digit_pairs(mg_ctx* ctx, int on);
 int mg_ctx_gemm_stats(mg_ctx* ctx, int64_t* launches, double* ms, double* flops, int reset);
 
 const char* mg_strerror(int code);

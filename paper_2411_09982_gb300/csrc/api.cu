@@ -128,6 +128,7 @@ struct mg_ctx {
   double* dev_flops = nullptr;
   std::string tune_cache;   // tuning cache consulted by servers for MG_PREC_AUTO jobs
   int stage_k = 32;         // K per pipeline stage of the split product (mg_ctx_set_stage_k)
+  int digit_pairs = 0;      // paired digit layout of the split product (mg_ctx_set_digit_pairs)
 };
 
 struct mg_plan {
@@ -356,6 +357,7 @@ struct Engine {
     c.item_sq = item_sq;
     c.sq_step = sq_step;
     c.stage_k = ctx->stage_k;
+    c.pairs = ctx->digit_pairs;
     return c;
   }
 
@@ -1167,6 +1169,12 @@ int mg_ctx_gemm_stats(mg_ctx* ctx, int64_t* launches, double* ms, double* flops,
 int mg_ctx_set_stage_k(mg_ctx* ctx, int stage_k) {
   if (!ctx || (stage_k != 16 && stage_k != 32 && stage_k != 64)) return MG_EINVAL;
   ctx->stage_k = stage_k;
+  return MG_OK;
+}
+
+int mg_ctx_set_digit_pairs(mg_ctx* ctx, int on) {
+  if (!ctx || (on != 0 && on != 1)) return MG_EINVAL;
+  ctx->digit_pairs = on;
   return MG_OK;
 }
 

@@ -145,7 +145,9 @@ struct SplitCtl {
   int stall = 0;                 // test only: the MMA issuer waits on a barrier nothing completes
   const int* item_sq = nullptr;  // per-item squaring counts (device) or null: every item active
   int sq_step = 0;               // with item_sq: only items with item_sq[b] > sq_step are computed
-  int stage_k = 32;              // K per pipeline stage of the product: 32 or 16
+  int stage_k = 32;              // K per pipeline stage of the product: 16, 32 or 64
+  int pairs = 0;                 // paired digit layout (even digit counts; 16-deep stages): slicers and product
+                                 // of one set of digit buffers must agree on it
 };
 int split_slice_a(int d, int L, int batch, const double* A, long long sA, int in_df32, void* buf, cudaStream_t s,
                   const SplitCtl& ctl = SplitCtl());

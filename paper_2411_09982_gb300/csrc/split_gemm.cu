@@ -82,6 +82,25 @@ struct SplitGeom {
   long long b_item_elems() const { return (long long)L * 3 * (Np / 2) * Kh(); }
 };
 
+// The paired digit layout applies to even digit counts only (odd counts keep one plane per digit).
+static inline int paired_layout(const SplitGeom& g, const SplitCtl& ctl) { return ctl.pairs && g.L % 2 == 0; }
+
+// Where digit s of an operand element lives, relative to its batch item.  Digit-major
+// layout (pairs = 0): one K-major plane per digit.  Paired layout (pairs = 1, even digit
+// counts): digits 2g and 2g + 1 share the rows of group g, every 16-wide block of K
+// holding 16 values of the even digit and then 16 of the odd one, so that one 64-byte
+// row of a 16-deep K stage carries both digits: half the shared memory per stage of the
+// digit-major form with 64-byte rows, hence twice the stages in the same ring.
+__device__ __forceinline__ long long a_digit_off(int pairs, int s, int row, int k, int Mp, int Kp) {
+  if (!pairs) return (long long)s * Mp * Kp + (long long)row * Kp + k;
+  return (long long)(s >> 1) * Mp * Kp * 2 + (long long)row * Kp * 2 + (k >> 4) * 32 + (s & 1) * 16 + (k & 15);
+}
+__device__ __forceinline__ long long b_digit_off(int pairs, int s, int plane, int j, int k, int rows, int Kh) {
+  if (!pairs) return ((long long)s * 3 + plane) * rows * Kh + (long long)j * Kh + k;
+  return ((long long)(s >> 1) * 3 + plane) * rows * Kh * 2 + (long long)j * Kh * 2 + (k >> 4) * 32 + (s & 1) * 16 +
+         (k & 15);
+}
+
 int split_beta_for(int d) {
   // largest beta <= 8 with 2^{2 beta - 1} * 2d <= 2^24
   for (int beta = 8; beta >= 2; --beta) {
@@ -196,7 +215,8 @@ __device__ __forceinline__ uint2 neg4(uint2 w) { return make_uint2(w.x ^ 0x80008
 template <int L, typename T>
 __global__ void __launch_bounds__(256)
 slice_a_kernel(int d, int Kp, int Mp, int beta, const double* __restrict__ A, long long sA,
-               __nv_bfloat16* __restrict__ out, int* __restrict__ ea, const int* __restrict__ item_sq, int sq_step) {
+               __nv_bfloat16* __restrict__ out, int* __restrict__ ea, const int* __restrict__ item_sq, int sq_step,
+               long long item_elems, int pairs) {
   using E_ = Elem<T>;
   const int lane = threadIdx.x & 31;
   const int row = blockIdx.x * 8 + (threadIdx.x >> 5);
@@ -204,8 +224,7 @@ slice_a_kernel(int d, int Kp, int Mp, int beta, const double* __restrict__ A, lo
   if (row >= Mp) return;
   if (item_sq && item_sq[b] <= sq_step) return;   // inactive item: its digits are not read
   const int Kh = Kp / 2;
-  const long long slice_stride = (long long)Mp * Kp;
-  __nv_bfloat16* o = out + (long long)b * L * slice_stride + (long long)row * Kp;
+  __nv_bfloat16* o = out + (long long)b * item_elems;
   if (row >= d) return;   // rows d..Mp are never read: the tensor map ends at row d (TMA fills zeros)
   const double* a = A + b * sA;
   const long long r0 = (long long)row * d;
@@ -236,8 +255,8 @@ slice_a_kernel(int d, int Kp, int Mp, int beta, const double* __restrict__ A, lo
     digits_pair<L>(im[2], im[3], beta, i23);
 #pragma unroll
     for (int s = 0; s < L; ++s) {
-      *reinterpret_cast<uint2*>(o + s * slice_stride + k) = make_uint2(r01[s], r23[s]);
-      *reinterpret_cast<uint2*>(o + s * slice_stride + Kh + k) = make_uint2(i01[s], i23[s]);
+      *reinterpret_cast<uint2*>(o + a_digit_off(pairs, s, row, k, Mp, Kp)) = make_uint2(r01[s], r23[s]);
+      *reinterpret_cast<uint2*>(o + a_digit_off(pairs, s, row, Kh + k, Mp, Kp)) = make_uint2(i01[s], i23[s]);
     }
   }
 }
@@ -286,7 +305,7 @@ template <int L, typename T>
 __global__ void __launch_bounds__(256)
 slice_b_kernel(int d, int Kp, int Np, int beta, const double* __restrict__ B, long long sB,
                __nv_bfloat16* __restrict__ out, const int* __restrict__ eb, const int* __restrict__ item_sq,
-               int sq_step) {
+               int sq_step, long long item_elems, int pairs) {
   using E_ = Elem<T>;
   using V = typename E_::type;
   __shared__ V tile[SB_KCHUNK][SG_BNC + 1];
@@ -297,9 +316,7 @@ slice_b_kernel(int d, int Kp, int Np, int beta, const double* __restrict__ B, lo
   const int tid = threadIdx.x;
   const int Kh = Kp / 2, rows = Np / 2;
   const double* Bb = B + b * sB;
-  const long long plane_stride = (long long)rows * Kh;
-  const long long slice_stride = 3 * plane_stride;
-  __nv_bfloat16* ob = out + (long long)b * L * slice_stride;
+  __nv_bfloat16* ob = out + (long long)b * item_elems;
   if (tid < SG_BNC) {
     int E = j0 + tid < d ? eb[(long long)b * rows + j0 + tid] : 0;
     if (E < -(1 << 28)) E = 0;   // all-zero column
@@ -332,14 +349,13 @@ slice_b_kernel(int d, int Kp, int Np, int beta, const double* __restrict__ B, lo
     digits_pair<L>(re[2], re[3], beta, r23);
     digits_pair<L>(im[0], im[1], beta, i01);
     digits_pair<L>(im[2], im[3], beta, i23);
-    __nv_bfloat16* row = ob + (long long)(j0 + r) * Kh;   // plane 0: -Im B, 1: Re B, 2: Im B
+    const int j = j0 + r;   // plane 0: -Im B, 1: Re B, 2: Im B
 #pragma unroll
     for (int s = 0; s < L; ++s) {
-      const long long so = s * slice_stride;
       const uint2 wr = make_uint2(r01[s], r23[s]), wi = make_uint2(i01[s], i23[s]);
-      *reinterpret_cast<uint2*>(row + so + k) = neg4(wi);
-      *reinterpret_cast<uint2*>(row + so + plane_stride + k) = wr;
-      *reinterpret_cast<uint2*>(row + so + 2 * plane_stride + k) = wi;
+      *reinterpret_cast<uint2*>(ob + b_digit_off(pairs, s, 0, j, k, rows, Kh)) = neg4(wi);
+      *reinterpret_cast<uint2*>(ob + b_digit_off(pairs, s, 1, j, k, rows, Kh)) = wr;
+      *reinterpret_cast<uint2*>(ob + b_digit_off(pairs, s, 2, j, k, rows, Kh)) = wi;
     }
   }
   // rows d..Np/2 of every plane are never read: the tensor map ends at row d (TMA fills zeros)
@@ -500,7 +516,13 @@ struct SplitEpi {
 // item b is computed only while ctl.item_sq[b] > ctl.sq_step (per-item squaring
 // counts: an item whose squarings are done keeps its matrix, which the product
 // would otherwise overwrite in place); the CTAs of an inactive item return at once.
-template <int L, int STAGES, int BK>
+//
+// PAIRS: operands in the paired digit layout (BK = 16).  The A box of a stage is then
+// L / 2 tiles of 128 rows x 64 bytes, one per digit pair, and digit s sits 32 bytes into
+// the rows of tile s / 2; B likewise.  The MMAs are issued in the same order as with the
+// digit-major layout at any BK (per 16-deep step of K, the pairs (sa, sb) in the same
+// order), so the two layouts give bit-identical products.
+template <int L, int STAGES, int BK, bool PAIRS>
 __global__ void __launch_bounds__(SG_THREADS, 1)
 split_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                   int d, int Kp, int Mp, int Np, int beta, const int* __restrict__ ea,
@@ -569,13 +591,18 @@ split_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
         }
         unsigned char* st = smem + s * STAGE_BYTES;
         mbar_expect_tx(&full[s], STAGE_BYTES);
-        tma_load_4d(st, &tmA, &full[s], kb * BK, mt * SG_BM, 0, b);
         // B: the same K range in both halves of K; planes [Re B; Im B] (1, 2) for the
         // real half, [-Im B; Re B] (0, 1) for the imaginary half
         const bool imag = kb >= nkh;
-        const int kbb = (imag ? kb - nkh : kb) * BK;
+        const int kbb = imag ? kb - nkh : kb;
         const int plane0 = imag ? 0 : 1;
-        tma_load_5d(st + L * TILE_BYTES, &tmB, &full[s], kbb, nt * SG_BNC, plane0, 0, b);
+        if constexpr (PAIRS) {
+          tma_load_4d(st, &tmA, &full[s], 0, kb, mt * SG_BM, b * (L / 2));
+          tma_load_5d(st + L * TILE_BYTES, &tmB, &full[s], 0, kbb, nt * SG_BNC, plane0, b * (L / 2));
+        } else {
+          tma_load_4d(st, &tmA, &full[s], kb * BK, mt * SG_BM, 0, b);
+          tma_load_5d(st + L * TILE_BYTES, &tmB, &full[s], kbb * BK, nt * SG_BNC, plane0, 0, b);
+        }
         issued = kb + 1;
       }
       // never leave the CTA with a bulk copy still in flight into its shared memory
@@ -612,8 +639,15 @@ split_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
               const int g = (sa + sb) < SG_GROUPS - 1 ? (sa + sb) : SG_GROUPS - 1;
               const uint32_t acc = first[g] ? 0u : 1u;
               first[g] = false;
-              tc_mma_bf16(tmem + g * 128, kmajor_desc<BK>(a0 + sa * TILE_BYTES + kk * SG_MMA_K * 2),
-                          kmajor_desc<BK>(b0 + sb * TILE_BYTES + kk * SG_MMA_K * 2), kIdescBf16, acc);
+              uint64_t ad, bd;
+              if constexpr (PAIRS) {
+                ad = sw64_kmajor_desc(a0 + (sa >> 1) * 2 * TILE_BYTES + (sa & 1) * SG_MMA_K * 2);
+                bd = sw64_kmajor_desc(b0 + (sb >> 1) * 2 * TILE_BYTES + (sb & 1) * SG_MMA_K * 2);
+              } else {
+                ad = kmajor_desc<BK>(a0 + sa * TILE_BYTES + kk * SG_MMA_K * 2);
+                bd = kmajor_desc<BK>(b0 + sb * TILE_BYTES + kk * SG_MMA_K * 2);
+              }
+              tc_mma_bf16(tmem + g * 128, ad, bd, kIdescBf16, acc);
             }
           }
         }
@@ -774,6 +808,41 @@ static int make_digit_map(CUtensorMap* map, const void* base, int Kp, int rows, 
   return MG_OK;
 }
 
+// Paired layout (even L): A dims {32, Kp / 16 blocks, d valid rows, batch * L / 2 digit
+// pairs}, box {32, 1, 128, L / 2}; B dims {32, Kh / 16, d valid rows, 3 planes,
+// batch * L / 2}, box {32, 1, 64, 2, L / 2}.  64-byte rows, SWIZZLE_64B.
+static int make_pair_maps(CUtensorMap* ma, CUtensorMap* mb, const SplitGeom& g, const void* Ad, const void* Bd,
+                          int batch) {
+  MG_TRY(get_encoder());
+  const int L = g.L, Kp = g.Kp, Kh = g.Kh(), rows = g.Np / 2;
+  const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+  {
+    cuuint64_t dims[4] = {32, (cuuint64_t)Kp / 16, (cuuint64_t)g.d, (cuuint64_t)batch * (L / 2)};
+    cuuint64_t strides[3] = {64, (cuuint64_t)Kp * 4, (cuuint64_t)g.Mp * Kp * 4};
+    cuuint32_t box[4] = {32, 1, (cuuint32_t)SG_BM, (cuuint32_t)(L / 2)};
+    CUresult r = g_encode(ma, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(Ad), dims, strides, box, estr,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+      set_last_message("cuTensorMapEncodeTiled failed (%d): paired A, Kp=%d L=%d batch=%d", (int)r, Kp, L, batch);
+      return MG_ECUDA;
+    }
+  }
+  {
+    cuuint64_t dims[5] = {32, (cuuint64_t)Kh / 16, (cuuint64_t)g.d, 3, (cuuint64_t)batch * (L / 2)};
+    cuuint64_t strides[4] = {64, (cuuint64_t)Kh * 4, (cuuint64_t)rows * Kh * 4, (cuuint64_t)3 * rows * Kh * 4};
+    cuuint32_t box[5] = {32, 1, (cuuint32_t)SG_BNC, 2, (cuuint32_t)(L / 2)};
+    CUresult r = g_encode(mb, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<void*>(Bd), dims, strides, box, estr,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+      set_last_message("cuTensorMapEncodeTiled failed (%d): paired B, Kh=%d L=%d batch=%d", (int)r, Kh, L, batch);
+      return MG_ECUDA;
+    }
+  }
+  return MG_OK;
+}
+
 template <int L, int BK>
 static constexpr int stages_for() {
   // ring budget 224 KiB (the opt-in limit is 227 KiB per block; 2 KiB go to barriers and alignment)
@@ -781,17 +850,22 @@ static constexpr int stages_for() {
          : ((229376 / (2 * L * StageK<BK>::tile_bytes)) < 1 ? 1 : (229376 / (2 * L * StageK<BK>::tile_bytes)));
 }
 
-template <int L, int BK>
+template <int L, int BK, bool PAIRS = false>
 static int launch_split_gemm_LB(const SplitGeom& g, int batch, const __nv_bfloat16* Ad, const int* ea,
                                 const __nv_bfloat16* Bd, const int* eb, double* C, long long sC,
                                 const SplitEpi& epi, int* status, const SplitCtl& ctl, cudaStream_t s) {
+  static_assert(!PAIRS || (BK == 16 && L % 2 == 0), "the paired layout has 16-deep stages and even L");
   constexpr int STAGES = stages_for<L, BK>();
   CUtensorMap ma, mb;
-  MG_TRY(make_digit_map(&ma, Ad, g.Kp, g.Mp, g.d, L, batch, BK));
-  MG_TRY(make_bplane_map(&mb, Bd, g.Kh(), g.Np / 2, g.d, L, batch, 2, L, BK));
+  if constexpr (PAIRS) {
+    MG_TRY(make_pair_maps(&ma, &mb, g, Ad, Bd, batch));
+  } else {
+    MG_TRY(make_digit_map(&ma, Ad, g.Kp, g.Mp, g.d, L, batch, BK));
+    MG_TRY(make_bplane_map(&mb, Bd, g.Kh(), g.Np / 2, g.d, L, batch, 2, L, BK));
+  }
   const size_t ring = std::max<size_t>((size_t)STAGES * 2 * L * StageK<BK>::tile_bytes, (size_t)SG_EPI_BYTES);
   const size_t smem = ring + 1024 /*barriers, exponents*/ + 1024 /*align*/;
-  auto kern = split_gemm_kernel<L, STAGES, BK>;
+  auto kern = split_gemm_kernel<L, STAGES, BK, PAIRS>;
   MG_TRY(ensure_smem_limit(reinterpret_cast<const void*>(kern), (int)smem));
   kern<<<dim3(ceil_div(g.d, SG_BNC), g.Mp / SG_BM, batch), SG_THREADS, smem, s>>>(
       ma, mb, g.d, g.Kp, g.Mp, g.Np, g.beta, ea, eb, C, sC, epi, status, ctl);
@@ -802,7 +876,13 @@ template <int L>
 static int launch_split_gemm_L(const SplitGeom& g, int batch, const __nv_bfloat16* Ad, const int* ea,
                                const __nv_bfloat16* Bd, const int* eb, double* C, long long sC,
                                const SplitEpi& epi, int* status, const SplitCtl& ctl, cudaStream_t s) {
-  if (ctl.stage_k == 16) return launch_split_gemm_LB<L, 16>(g, batch, Ad, ea, Bd, eb, C, sC, epi, status, ctl, s);
+  if constexpr (L % 2 == 0)
+    if (paired_layout(g, ctl))
+      return launch_split_gemm_LB<L, 16, true>(g, batch, Ad, ea, Bd, eb, C, sC, epi, status, ctl, s);
+  // 16-deep stages also where a 32-deep stage leaves room for only one (L = 8: no
+  // overlap of loads and MMAs; 35 -> 53 algorithmic TFLOP/s measured at d = 512)
+  if (ctl.stage_k == 16 || stages_for<L, 32>() < 2)
+    return launch_split_gemm_LB<L, 16>(g, batch, Ad, ea, Bd, eb, C, sC, epi, status, ctl, s);
   // 64 only where each half of K is a whole number of 64-wide stages and two stages fit
   if constexpr (2 * 2 * L * StageK<64>::tile_bytes <= 229376)
     if (ctl.stage_k == 64 && g.Kh() % 64 == 0)
@@ -816,7 +896,7 @@ static int launch_slicers_LT(const SplitGeom& g, int batch, const double* A, lon
                              const SplitCtl& ctl) {
   if (A) {
     slice_a_kernel<L, T><<<dim3(g.Mp / 8, batch), 256, 0, s>>>(g.d, g.Kp, g.Mp, g.beta, A, sA, Ad, ea, ctl.item_sq,
-                                                                ctl.sq_step);
+                                                                ctl.sq_step, g.a_item_elems(), paired_layout(g, ctl));
     MG_TRY(check_launch("slice_a_kernel"));
   }
   if (B) {
@@ -825,7 +905,7 @@ static int launch_slicers_LT(const SplitGeom& g, int batch, const double* A, lon
         g.d, g.Np, B, sB, eb, ctl.item_sq, ctl.sq_step);
     MG_TRY(check_launch("col_exponent_kernel"));
     slice_b_kernel<L, T><<<dim3(ceil_div(g.d, SG_BNC), ceil_div(g.d, SB_KCHUNK), batch), 256, 0, s>>>(
-        g.d, g.Kp, g.Np, g.beta, B, sB, Bd, eb, ctl.item_sq, ctl.sq_step);
+        g.d, g.Kp, g.Np, g.beta, B, sB, Bd, eb, ctl.item_sq, ctl.sq_step, g.b_item_elems(), paired_layout(g, ctl));
     MG_TRY(check_launch("slice_b_kernel"));
   }
   return MG_OK;

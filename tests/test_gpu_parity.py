@@ -635,24 +635,27 @@ def test_cgemm_split_adversarial_row_and_column_scales(ctx, d):
     assert scaled_err.max() <= bound, (scaled_err.max(), bound)
 
 
-@pytest.mark.parametrize("d,L", [(30, 6), (129, 5), (300, 6), (729, 6), (700, 3), (64, 2)])
+@pytest.mark.parametrize("d,L", [(30, 6), (129, 5), (300, 6), (729, 6), (700, 3), (64, 2), (200, 4), (97, 8)])
 def test_cgemm_split_stage_k_variants_agree_bit_for_bit(d, L):
     """The product's pipeline stage (K = 16, 32 or 64 per stage: 32-, 64- or 128-byte operand
-    rows) does not change its arithmetic: the MMAs run in the same order over K, so the
-    results agree bit for bit (K = 64 applies where L <= 3 and each half of K is a multiple
-    of 64, else the product takes K = 32)."""
+    rows) and the paired digit layout (two digits per 64-byte row, 16-deep stages; even L)
+    do not change its arithmetic: the MMAs run in the same order over K, so the results
+    agree bit for bit (K = 64 applies where L <= 3 and each half of K is a multiple of 64,
+    else the product takes K = 32; odd L ignores the paired layout)."""
     rng = np.random.default_rng(50 + d)
     A, B = rand_c(rng, (2, d, d)), rand_c(rng, (2, d, d))
     c = M.Context(0)
     out = {}
-    for k in (32, 16, 64):
-        c.set_stage_k(k)
+    for k in (32, 16, 64, "pairs"):
+        c.set_digit_pairs(k == "pairs")
+        c.set_stage_k(32 if k == "pairs" else k)
         C = torch.empty((2, d, d), dtype=torch.complex128, device="cuda")
         M.mg_cgemm(c, 2, d, cuda(A), cuda(B), C, M.MG_PREC_SPLIT, L)
         torch.cuda.synchronize()
         out[k] = C.cpu().numpy()
     c.close()
     assert np.array_equal(out[16], out[32]) and np.array_equal(out[64], out[32])
+    assert np.array_equal(out["pairs"], out[32])
     beta = split_beta(d)
     bound = (L + 2) * 2 * d * (2 * np.abs(A).max()) * (2 * np.abs(B).max()) * (2.0 ** (-beta * L) + L * 2.0 ** (-22 - 3 * beta))
     assert np.abs(out[16] - A @ B).max() <= bound
