@@ -56,6 +56,8 @@ def parse():
                     help="K per pipeline stage of the split product (mg_ctx_set_stage_k)")
     ap.add_argument("--digit-pairs", type=int, default=None, choices=[0, 1],
                     help="paired digit layout of the split product (mg_ctx_set_digit_pairs)")
+    ap.add_argument("--cta-pairs", type=int, default=None, choices=[0, 1],
+                    help="split products on CTA pairs (mg_ctx_set_cta_pairs)")
     ap.add_argument("--intervals", type=int, default=2000)
     ap.add_argument("--e2e-steps", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -98,6 +100,20 @@ def dist_info():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return ws, rank, local
+
+
+# dense BF16 tensor rate of one SM per clock (tcgen05 kind::f16); 152 SMs on GB300
+BF16_FLOPS_PER_SM_CLOCK = 8192
+NUM_SMS = 152
+
+
+def digit_mma_frac(achieved_tflops, pairs, clk):
+    """Share of the nominal BF16 tensor rate at the SM clock seen during the run that the
+    digit-pair MMAs occupy (pairs BF16 products per algorithmic flop)."""
+    mhz = (clk or {}).get("sm_mhz")
+    if not pairs or not mhz:
+        return None
+    return achieved_tflops * pairs / (NUM_SMS * BF16_FLOPS_PER_SM_CLOCK * mhz * 1e6 / 1e12)
 
 
 def measured_peaks():
@@ -192,6 +208,8 @@ def run_ours(args):
     ctx.set_stage_k(args.stage_k)
     if args.digit_pairs is not None:
         ctx.set_digit_pairs(args.digit_pairs)
+    if args.cta_pairs is not None:
+        ctx.set_cta_pairs(args.cta_pairs)
     prec = M.MG_PREC_SPLIT if args.precision == "split" else M.MG_PREC_FP64
     N = args.intervals
 
@@ -279,9 +297,10 @@ def run_ours(args):
                     "traffic_note": "bytes per average launch, scaled by products from one ncu capture",
                     "kernel": "split_gemm_kernel",
                     "peak_source": f"bf16 dense sustained, {peak_src}",
-                    "tensor_pipe_frac": achieved * pairs / peak,
+                    "digit_mma_frac_of_nominal_at_clock": digit_mma_frac(achieved, pairs, clk),
                     "note": f"achieved counts 8 d^3 flops per complex product; the tensor pipe issues "
-                            f"{pairs} BF16 digit-pair products per such flop"}
+                            f"{pairs} BF16 digit-pair products per such flop (digit_mma_frac: their share "
+                            f"of 8192 flop/clock/SM x 152 SMs at the run's median SM clock)"}
         else:
             fp64_peak = FP64_TFLOPS_MEASURED
             roof = {"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
@@ -549,7 +568,7 @@ def run_config(args):
             clk = clocks.stop()
         return sum(a.elapsed_time(b) for a, b in ev), g, clk, M.mg_kernel_launch_count() - l0
 
-    def gemm_roof(g, pairs):
+    def gemm_roof(g, pairs, clk=None):
         if not g["launches"]:
             return None
         ach = g["flops"] / (g["ms"] * 1e-3) / 1e12
@@ -558,7 +577,7 @@ def run_config(args):
         p64 = FP64_TFLOPS_MEASURED
         return {"bound": "tensor" if pairs else "alu", "achieved": ach, "peak": peak if pairs else p64,
                 "unit": "TFLOP/s", "frac": ach / (peak if pairs else p64), "traffic": None,
-                "tensor_pipe_frac": ach * pairs / peak if pairs else None,
+                "digit_mma_frac_of_nominal_at_clock": digit_mma_frac(ach, pairs, clk),
                 "peak_source": f"bf16 dense sustained, {src}" if pairs else
                 "FP64 torch.matmul, measured (bench.py --peaks)"}
 
@@ -590,7 +609,7 @@ def run_config(args):
                                 "controls": wl.K, "output": "state" if state else "full propagator",
                                 "method": "action (Chebyshev, sparse)" if args.action else "interval propagators",
                                 "reorth_every": reorth, "l2": "256 MiB buffer written before every timed step"},
-                        roofline=gemm_roof(g, 0 if prec == M.MG_PREC_FP64 else args.slices * (args.slices + 1) // 2),
+                        roofline=gemm_roof(g, 0 if prec == M.MG_PREC_FP64 else args.slices * (args.slices + 1) // 2, clk),
                         clocks=clk, gpu_launches=int(launches))
         if args.action:
             rep = plan.evolve(M.MG_OUT_STATE, inp, out, 0)
@@ -653,7 +672,7 @@ def run_config(args):
                                 "issue": "one captured CUDA graph per step" if graph is not None
                                 else "stream launches, no host synchronisation between chunks",
                                 "l2": "256 MiB buffer written before every timed step"},
-                        roofline=gemm_roof(g, 0 if args.action else args.slices * (args.slices + 1) // 2),
+                        roofline=gemm_roof(g, 0 if args.action else args.slices * (args.slices + 1) // 2, clk),
                         clocks=clk, gpu_launches=int(launches),
                         launches_per_step=int(launches) / args.steps)
         if graph is not None:

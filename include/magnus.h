@@ -513,6 +513,19 @@ int mg_ctx_set_stage_k(mg_ctx* ctx, int stage_k);
  * vs 78.7 digit-major; d = 700, 4 slices 124 vs 142; d = 512, 8 slices 53.0 vs 35.2
  * (52.7 with digit-major 16-deep stages, which 8 slices now take by default). */
 int mg_ctx_set_digit_pairs(mg_ctx* ctx, int on);
+/* Tensor-core product (MG_PREC_SPLIT) on CTA pairs: on = 1 runs each product tile of
+ * 256 rows x 64 complex columns as one M = 256 tcgen05 product of two CTAs on two SMs
+ * (a 2-CTA cluster; each CTA loads its 128 rows of A and half the B tile, which both
+ * tensor cores read), where d > 128; the digit-major layout only (the paired layout of
+ * mg_ctx_set_digit_pairs takes precedence).  on = 0: one CTA per 128-row tile.
+ * on = -1 (the default): pairs for 5 or more slices.  The same digit products are
+ * accumulated in the same order, so the result is bit-identical.  Measured on GB300
+ * (algorithmic TFLOP/s, one CTA vs pairs, 32-deep stages): 6 slices 78.3 vs 80.4 at
+ * d = 729 (32 products) and 96.8 vs 103.4 at d = 4096; 8 slices 52.9 vs 55.2 at d = 512;
+ * 4 slices 142.0 vs 137.7 and 2 slices 255.2 vs 246.1 at d = 700.  The pairs relieve
+ * each SM's shared-memory port, which every MMA reads its operands through (8 KiB
+ * per MMA on one CTA, 6 KiB on a pair).  MG_EINVAL for other values. */
+int mg_ctx_set_cta_pairs(mg_ctx* ctx, int on);
 int mg_ctx_gemm_stats(mg_ctx* ctx, int64_t* launches, double* ms, double* flops, int reset);
 
 const char* mg_strerror(int code);

@@ -129,6 +129,7 @@ struct mg_ctx {
   std::string tune_cache;   // tuning cache consulted by servers for MG_PREC_AUTO jobs
   int stage_k = 32;         // K per pipeline stage of the split product (mg_ctx_set_stage_k)
   int digit_pairs = 0;      // paired digit layout of the split product (mg_ctx_set_digit_pairs)
+  int cta_pairs = -1;       // split products on CTA pairs (mg_ctx_set_cta_pairs; -1: by digit count)
 };
 
 struct mg_plan {
@@ -358,6 +359,7 @@ struct Engine {
     c.sq_step = sq_step;
     c.stage_k = ctx->stage_k;
     c.pairs = ctx->digit_pairs;
+    c.cta_pairs = ctx->cta_pairs;
     return c;
   }
 
@@ -1175,6 +1177,12 @@ int mg_ctx_set_stage_k(mg_ctx* ctx, int stage_k) {
 int mg_ctx_set_digit_pairs(mg_ctx* ctx, int on) {
   if (!ctx || (on != 0 && on != 1)) return MG_EINVAL;
   ctx->digit_pairs = on;
+  return MG_OK;
+}
+
+int mg_ctx_set_cta_pairs(mg_ctx* ctx, int on) {
+  if (!ctx || on < -1 || on > 1) return MG_EINVAL;
+  ctx->cta_pairs = on;
   return MG_OK;
 }
 

@@ -148,6 +148,8 @@ struct SplitCtl {
   int stage_k = 32;              // K per pipeline stage of the product: 16, 32 or 64
   int pairs = 0;                 // paired digit layout (even digit counts; 16-deep stages): slicers and product
                                  // of one set of digit buffers must agree on it
+  int cta_pairs = -1;            // M = 256 products on CTA pairs (tcgen05 cta_group::2) where d > 128:
+                                 // 1 on, 0 off, -1 for five or more digits
 };
 int split_slice_a(int d, int L, int batch, const double* A, long long sA, int in_df32, void* buf, cudaStream_t s,
                   const SplitCtl& ctl = SplitCtl());

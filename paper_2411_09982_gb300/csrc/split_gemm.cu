@@ -413,6 +413,67 @@ __device__ __forceinline__ void tma_load_5d(void* dst, const CUtensorMap* map, u
       "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(smem_u32(bar))
       : "memory");
 }
+// CTA-pair forms (cta_group::2): the copy may signal the barrier of either CTA of the pair
+__device__ __forceinline__ void tma_load_4d_pair(void* dst, const CUtensorMap* map, uint32_t bar_cluster, int c0,
+                                                 int c1, int c2, int c3) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.cta_group::2.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(bar_cluster)
+      : "memory");
+}
+__device__ __forceinline__ void tma_load_5d_pair(void* dst, const CUtensorMap* map, uint32_t bar_cluster, int c0,
+                                                 int c1, int c2, int c3, int c4) {
+  asm volatile(
+      "cp.async.bulk.tensor.5d.cta_group::2.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(bar_cluster)
+      : "memory");
+}
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+// shared::cluster address of this CTA's variable `p` as it lies in CTA `rank` of the cluster
+__device__ __forceinline__ uint32_t cluster_addr(const void* p, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(smem_u32(p)), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait_cluster(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ void tc_mma_bf16_pair(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                                 uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+// arrive on the barrier at this offset in both CTAs of the pair once the issued MMAs
+// complete: one commit per CTA, each naming that CTA's barrier by its cluster address
+__device__ __forceinline__ void tc_commit_pair(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   cluster_addr(bar, 0))
+               : "memory");
+  asm volatile("tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   cluster_addr(bar, 1))
+               : "memory");
+}
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
@@ -483,6 +544,9 @@ __device__ __forceinline__ uint64_t kmajor_desc(uint32_t saddr) {
 
 // Instruction descriptor: kind::f16, A = B = BF16, D = F32, both K-major, M = 128, N = 128.
 constexpr uint32_t kIdescBf16 = (1u << 4) | (1u << 7) | (1u << 10) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
+// the same with M = 256 (a CTA pair, cta_group::2)
+constexpr uint32_t kIdescBf16M256 =
+    (1u << 4) | (1u << 7) | (1u << 10) | ((128u >> 3) << 17) | ((256u >> 4) << 24);
 
 constexpr int SG_THREADS = 320;   // producer warp, MMA warp, 8 epilogue warps
 constexpr int SG_EPI_WARPS = 8;
@@ -522,7 +586,18 @@ struct SplitEpi {
 // the rows of tile s / 2; B likewise.  The MMAs are issued in the same order as with the
 // digit-major layout at any BK (per 16-deep step of K, the pairs (sa, sb) in the same
 // order), so the two layouts give bit-identical products.
-template <int L, int STAGES, int BK, bool PAIRS>
+//
+// CTAS = 2: the two CTAs of a cluster (row tiles mt = 2c, 2c + 1 along x of the grid, the
+// same columns) form
+// one M = 256 product (tcgen05 cta_group::2).  Each CTA loads its own 128 rows of A and
+// one of the two B planes of the stage (64 rows: rank 0 the Re-C plane, rank 1 the
+// Im-C plane); all four copies signal the barrier of rank 0, whose single thread issues
+// every MMA of the pair.  Each SM's tensor core reads its A tile and half the B tile
+// from its own shared memory and the other half from its partner's, so the operand
+// traffic through one SM's shared memory per MMA drops from 8 KiB to 6 KiB and the
+// bytes it loads per stage by a quarter.  TMEM accumulators, layout and epilogue are
+// those of the single-CTA form (each CTA holds its 128 rows).
+template <int L, int STAGES, int BK, bool PAIRS, int CTAS = 1>
 __global__ void __launch_bounds__(SG_THREADS, 1)
 split_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                   int d, int Kp, int Mp, int Np, int beta, const int* __restrict__ ea,
@@ -530,8 +605,10 @@ split_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
                   int* __restrict__ status, SplitCtl ctl) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  static_assert(CTAS == 1 || (CTAS == 2 && !PAIRS), "the CTA pair takes the digit-major layout");
   constexpr int TILE_BYTES = StageK<BK>::tile_bytes;
-  constexpr int STAGE_BYTES = 2 * L * TILE_BYTES;
+  constexpr int B_TILE_BYTES = TILE_BYTES / CTAS;   // one CTA's share of a digit's B tile
+  constexpr int STAGE_BYTES = L * (TILE_BYTES + B_TILE_BYTES);   // loaded into this CTA per stage
   constexpr int RING_BYTES = STAGES * STAGE_BYTES > SG_EPI_BYTES ? STAGES * STAGE_BYTES : SG_EPI_BYTES;
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + RING_BYTES);
   uint64_t* empty = full + STAGES;
@@ -543,8 +620,12 @@ split_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
   int* epi_flag = eb_s + SG_BNC;  // epilogue verdict (accumulators ready and no abort)
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int nt = blockIdx.x, mt = blockIdx.y, b = blockIdx.z;
-  if (ctl.item_sq && ctl.item_sq[b] <= ctl.sq_step) return;   // uniform over the CTA
+  // a CTA pair lies along x of the grid (clusters of 2 x 1 x 1): row tiles on x there
+  const int nt = CTAS == 2 ? blockIdx.y : blockIdx.x, mt = CTAS == 2 ? blockIdx.x : blockIdx.y, b = blockIdx.z;
+  // uniform over the CTA (and over a CTA pair, which shares b): no cluster barrier is reached
+  if (ctl.item_sq && ctl.item_sq[b] <= ctl.sq_step) return;
+  const uint32_t crank = CTAS == 2 ? cluster_rank() : 0u;
+  const bool leader = crank == 0;
   const int num_k = Kp / BK;
   const int nkh = num_k / 2;   // K stages of the real half
 
@@ -564,13 +645,25 @@ split_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
     eb_s[c] = j < d ? eb[(long long)b * (Np / 2) + j] : 0;
   }
   if (warp == 1) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                 "r"(512)
-                 : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    if constexpr (CTAS == 2) {
+      // one warp of each CTA of the pair takes part; each CTA receives its own address
+      asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                       smem_u32(tmem_slot)),
+                   "r"(512)
+                   : "memory");
+      asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+    } else {
+      asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                       smem_u32(tmem_slot)),
+                   "r"(512)
+                   : "memory");
+      asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
   }
   tc_fence_before();
-  __syncthreads();
+  // both CTAs' barriers initialised and TMEM allocated before any copy or MMA of the pair
+  if constexpr (CTAS == 2) cluster_sync_all();
+  else __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
   const uint64_t t_start = global_ns();
@@ -590,28 +683,41 @@ split_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
           break;
         }
         unsigned char* st = smem + s * STAGE_BYTES;
-        mbar_expect_tx(&full[s], STAGE_BYTES);
         // B: the same K range in both halves of K; planes [Re B; Im B] (1, 2) for the
         // real half, [-Im B; Re B] (0, 1) for the imaginary half
         const bool imag = kb >= nkh;
         const int kbb = imag ? kb - nkh : kb;
         const int plane0 = imag ? 0 : 1;
-        if constexpr (PAIRS) {
+        if constexpr (CTAS == 2) {
+          // rank 0 expects the bytes of both CTAs; the copies of both signal its barrier
+          if (leader) mbar_expect_tx(&full[s], 2 * STAGE_BYTES);
+          const uint32_t bar = cluster_addr(&full[s], 0);
+          tma_load_4d_pair(st, &tmA, bar, kb * BK, mt * SG_BM, 0, b);
+          tma_load_5d_pair(st + L * TILE_BYTES, &tmB, bar, kbb * BK, nt * SG_BNC, plane0 + (int)crank, 0, b);
+        } else if constexpr (PAIRS) {
+          mbar_expect_tx(&full[s], STAGE_BYTES);
           tma_load_4d(st, &tmA, &full[s], 0, kb, mt * SG_BM, b * (L / 2));
           tma_load_5d(st + L * TILE_BYTES, &tmB, &full[s], 0, kbb, nt * SG_BNC, plane0, b * (L / 2));
         } else {
+          mbar_expect_tx(&full[s], STAGE_BYTES);
           tma_load_4d(st, &tmA, &full[s], kb * BK, mt * SG_BM, 0, b);
           tma_load_5d(st + L * TILE_BYTES, &tmB, &full[s], kbb * BK, nt * SG_BNC, plane0, 0, b);
         }
         issued = kb + 1;
       }
-      // never leave the CTA with a bulk copy still in flight into its shared memory
-      const uint64_t drain_deadline = global_ns() + SG_WAIT_NS;
-      for (int kb = issued > STAGES ? issued - STAGES : 0; kb < issued; ++kb)
-        mbar_wait(&full[kb % STAGES], (kb / STAGES) & 1, drain_deadline);
+      // never leave the CTA with a bulk copy still in flight into its shared memory.  In
+      // a pair the barriers of rank 0 count the copies of both CTAs: rank 0 drains them,
+      // and rank 1 leaves only after the closing cluster barrier, which rank 0 reaches
+      // after this drain.  (Both producers wait on commits issued together, so they
+      // issue the same stages; a timeout is the one way they could differ.)
+      if (CTAS == 1 || leader) {
+        const uint64_t drain_deadline = global_ns() + SG_WAIT_NS;
+        for (int kb = issued > STAGES ? issued - STAGES : 0; kb < issued; ++kb)
+          mbar_wait(&full[kb % STAGES], (kb / STAGES) & 1, drain_deadline);
+      }
     }
   } else if (warp == 1) {
-    if (lane == 0) {
+    if (lane == 0 && leader) {
       // ---------------- MMA issuer ----------------
       bool ok = true;
       if (ctl.stall && !mbar_wait(never, 0, deadline_short)) {
@@ -628,7 +734,7 @@ split_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
         }
         tc_fence_after();
         const uint32_t a0 = smem_u32(smem + s * STAGE_BYTES);
-        const uint32_t b0 = a0 + L * TILE_BYTES;
+        const uint32_t b0 = a0 + L * TILE_BYTES;   // in a pair: this CTA's half, the partner's at the same offset
         bool first[SG_GROUPS] = {kb == 0, kb == 0, kb == 0, kb == 0};
 #pragma unroll
         for (int kk = 0; kk < BK / SG_MMA_K; ++kk) {
@@ -645,16 +751,29 @@ split_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
                 bd = sw64_kmajor_desc(b0 + (sb >> 1) * 2 * TILE_BYTES + (sb & 1) * SG_MMA_K * 2);
               } else {
                 ad = kmajor_desc<BK>(a0 + sa * TILE_BYTES + kk * SG_MMA_K * 2);
-                bd = kmajor_desc<BK>(b0 + sb * TILE_BYTES + kk * SG_MMA_K * 2);
+                bd = kmajor_desc<BK>(b0 + sb * B_TILE_BYTES + kk * SG_MMA_K * 2);
               }
-              tc_mma_bf16(tmem + g * 128, ad, bd, kIdescBf16, acc);
+              if constexpr (CTAS == 2) tc_mma_bf16_pair(tmem + g * 128, ad, bd, kIdescBf16M256, acc);
+              else tc_mma_bf16(tmem + g * 128, ad, bd, kIdescBf16, acc);
             }
           }
         }
-        tc_commit(&empty[s]);
+        if constexpr (CTAS == 2) tc_commit_pair(&empty[s]);
+        else tc_commit(&empty[s]);
       }
-      tc_commit(accfull);   // fires once every issued MMA has completed
-      if (!ok) *(volatile int*)abort_flag = 1;
+      // the verdict is written before the accumulator barrier can complete
+      if (!ok) {
+        *(volatile int*)abort_flag = 1;
+        if constexpr (CTAS == 2) {
+          asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(cluster_addr(abort_flag, 1)), "r"(1) : "memory");
+          asm volatile("fence.acq_rel.cluster;" ::: "memory");
+        } else {
+          __threadfence_block();
+        }
+      }
+      // fires once every issued MMA has completed (in both CTAs of a pair)
+      if constexpr (CTAS == 2) tc_commit_pair(accfull);
+      else tc_commit(accfull);
     }
   } else {
     // ---------------- epilogue (warps 2..9) ----------------
@@ -663,13 +782,38 @@ split_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
     // one thread polls; all eight epilogue warps follow its verdict, so that they
     // either all reach both named barriers below or none does
     if (warp == 2 && lane == 0) {
-      const bool got = mbar_wait(accfull, 0, deadline);
+      bool got;
+      if constexpr (CTAS == 2) {   // acquire at cluster scope: the verdict may come from rank 0
+        got = true;
+        while (!mbar_try_wait_cluster(accfull, 0)) {
+          if (global_ns() > deadline) {
+            got = false;
+            break;
+          }
+        }
+      } else {
+        got = mbar_wait(accfull, 0, deadline);
+      }
       if (!got) atomicExch(status, MG_DEV_TIMEOUT);
       *epi_flag = (got && *(volatile int*)abort_flag == 0) ? 1 : 0;
     }
     asm volatile("bar.sync 1, %0;" ::"n"(SG_EPI_WARPS * 32) : "memory");
     tc_fence_after();
     if (*(volatile int*)epi_flag != 0) {
+      // pull this tile's addend rows into L2 while phase 1 drains TMEM (8 x 128-byte
+      // lines cover a row's 64 complex double-float values)
+      if (epi.add_n > 0) {
+        const int et = threadIdx.x - 2 * 32;
+        for (int idx = et; idx < epi.add_n * SG_BM * 8; idx += SG_EPI_WARPS * 32) {
+          const int m = idx / (SG_BM * 8), rem = idx % (SG_BM * 8), rr = rem / 8, q = rem % 8;
+          const int grow = mt * SG_BM + rr, j = nt * SG_BNC + q * 8;
+          if (grow < d && j < d) {
+            const double* src = m == 0 ? epi.add_src[0] : (m == 1 ? epi.add_src[1] : epi.add_src[2]);
+            const double* p = src + b * epi.add_stride + 4 * ((long long)grow * d + j);
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+          }
+        }
+      }
       // phase 1 (thread = row): TMEM -> level combine -> double-float tile in shared memory
       // (the stage ring is idle once every MMA has completed)
       float4* stile = reinterpret_cast<float4*>(smem);
@@ -707,39 +851,60 @@ split_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
         addp[m] = epi.add_src[m] ? reinterpret_cast<const float4*>(epi.add_src[m] + b * epi.add_stride) : nullptr;
       float4* Cb = reinterpret_cast<float4*>(C + b * sC);
       const int ew = warp - 2;
-      for (int rr = ew; rr < SG_BM; rr += SG_EPI_WARPS) {
-        const int grow = mt * SG_BM + rr;
-        if (grow >= d) break;
+      // The warp's (row, half) items, EPI_GROUP at a time: every addend load of a group
+      // is issued before the first is used, so that a warp keeps several rows of loads
+      // in flight (one row at a time left the addend products latency-bound).
+      constexpr int HALVES = SG_BNC / 32;
+      constexpr int ITEMS = (SG_BM / SG_EPI_WARPS) * HALVES;
+      constexpr int EPI_GROUP = 4;
+      for (int i0 = 0; i0 < ITEMS; i0 += EPI_GROUP) {
+        float4 ad[EPI_GROUP][3];
+        long long offs[EPI_GROUP];
+        bool ok[EPI_GROUP];
 #pragma unroll
-        for (int h = 0; h < SG_BNC / 32; ++h) {
-          const int c = h * 32 + lane;
-          const int j = nt * SG_BNC + c;
-          if (j >= d) continue;
-          const long long off = (long long)grow * d + j;
-          float4 ad[3];
+        for (int u = 0; u < EPI_GROUP; ++u) {
+          const int it = i0 + u, rr = ew + SG_EPI_WARPS * (it / HALVES), c = (it % HALVES) * 32 + lane;
+          const int grow = mt * SG_BM + rr, j = nt * SG_BNC + c;
+          ok[u] = grow < d && j < d;
+          offs[u] = ok[u] ? (long long)grow * d + j : 0;
 #pragma unroll
-          for (int m = 0; m < 3; ++m) ad[m] = m < epi.add_n ? addp[m][off] : make_float4(0.f, 0.f, 0.f, 0.f);
+          for (int m = 0; m < 3; ++m)
+            ad[u][m] = (ok[u] && m < epi.add_n) ? addp[m][offs[u]] : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int u = 0; u < EPI_GROUP; ++u) {
+          if (!ok[u]) continue;
+          const int it = i0 + u, rr = ew + SG_EPI_WARPS * (it / HALVES), c = (it % HALVES) * 32 + lane;
           const float4 v = stile[rr * SG_EPI_PITCH + c];
           df32 re{v.x, v.y}, im{v.z, v.w};
 #pragma unroll
           for (int m = 0; m < 3; ++m) {
             if (m < epi.add_n) {
-              re = df_add(re, df_mul(df32{ad[m].x, ad[m].y}, epi.add_coef[m]));
-              im = df_add(im, df_mul(df32{ad[m].z, ad[m].w}, epi.add_coef[m]));
+              re = df_add(re, df_mul(df32{ad[u][m].x, ad[u][m].y}, epi.add_coef[m]));
+              im = df_add(im, df_mul(df32{ad[u][m].z, ad[u][m].w}, epi.add_coef[m]));
             }
           }
-          if (grow == j) re = df_add(re, epi.diag);
-          Cb[off] = make_float4(re.hi, re.lo, im.hi, im.lo);
+          if (mt * SG_BM + rr == nt * SG_BNC + c) re = df_add(re, epi.diag);
+          Cb[offs[u]] = make_float4(re.hi, re.lo, im.hi, im.lo);
         }
       }
     }
     tc_fence_before();
   }
-  __syncthreads();
+  // a pair: neither CTA frees TMEM or leaves while its partner may still use them
+  if constexpr (CTAS == 2) {
+    __syncwarp();
+    cluster_sync_all();
+  } else {
+    __syncthreads();
+  }
   if (warp == 1) {
     __syncwarp();
     tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512) : "memory");
+    if constexpr (CTAS == 2)
+      asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512) : "memory");
+    else
+      asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512) : "memory");
   }
 }
 
@@ -843,33 +1008,79 @@ static int make_pair_maps(CUtensorMap* ma, CUtensorMap* mb, const SplitGeom& g, 
   return MG_OK;
 }
 
-template <int L, int BK>
+// bytes one CTA loads per pipeline stage (a CTA pair splits the B tile)
+template <int L, int BK, int CTAS>
+static constexpr int stage_bytes() {
+  return L * (StageK<BK>::tile_bytes + StageK<BK>::tile_bytes / CTAS);
+}
+template <int L, int BK, int CTAS = 1>
 static constexpr int stages_for() {
   // ring budget 224 KiB (the opt-in limit is 227 KiB per block; 2 KiB go to barriers and alignment)
-  return (229376 / (2 * L * StageK<BK>::tile_bytes)) > 8 ? 8
-         : ((229376 / (2 * L * StageK<BK>::tile_bytes)) < 1 ? 1 : (229376 / (2 * L * StageK<BK>::tile_bytes)));
+  return (229376 / stage_bytes<L, BK, CTAS>()) > 8 ? 8
+         : ((229376 / stage_bytes<L, BK, CTAS>()) < 1 ? 1 : (229376 / stage_bytes<L, BK, CTAS>()));
 }
 
-template <int L, int BK, bool PAIRS = false>
+template <int L, int BK, bool PAIRS = false, int CTAS = 1>
 static int launch_split_gemm_LB(const SplitGeom& g, int batch, const __nv_bfloat16* Ad, const int* ea,
                                 const __nv_bfloat16* Bd, const int* eb, double* C, long long sC,
                                 const SplitEpi& epi, int* status, const SplitCtl& ctl, cudaStream_t s) {
   static_assert(!PAIRS || (BK == 16 && L % 2 == 0), "the paired layout has 16-deep stages and even L");
-  constexpr int STAGES = stages_for<L, BK>();
+  constexpr int STAGES = stages_for<L, BK, CTAS>();
   CUtensorMap ma, mb;
   if constexpr (PAIRS) {
     MG_TRY(make_pair_maps(&ma, &mb, g, Ad, Bd, batch));
   } else {
     MG_TRY(make_digit_map(&ma, Ad, g.Kp, g.Mp, g.d, L, batch, BK));
-    MG_TRY(make_bplane_map(&mb, Bd, g.Kh(), g.Np / 2, g.d, L, batch, 2, L, BK));
+    // a CTA of a pair loads one of the two planes of the stage
+    MG_TRY(make_bplane_map(&mb, Bd, g.Kh(), g.Np / 2, g.d, L, batch, CTAS == 2 ? 1 : 2, L, BK));
   }
-  const size_t ring = std::max<size_t>((size_t)STAGES * 2 * L * StageK<BK>::tile_bytes, (size_t)SG_EPI_BYTES);
+  const size_t ring = std::max<size_t>((size_t)STAGES * stage_bytes<L, BK, CTAS>(), (size_t)SG_EPI_BYTES);
   const size_t smem = ring + 1024 /*barriers, exponents*/ + 1024 /*align*/;
-  auto kern = split_gemm_kernel<L, STAGES, BK, PAIRS>;
+  auto kern = split_gemm_kernel<L, STAGES, BK, PAIRS, CTAS>;
   MG_TRY(ensure_smem_limit(reinterpret_cast<const void*>(kern), (int)smem));
-  kern<<<dim3(ceil_div(g.d, SG_BNC), g.Mp / SG_BM, batch), SG_THREADS, smem, s>>>(
-      ma, mb, g.d, g.Kp, g.Mp, g.Np, g.beta, ea, eb, C, sC, epi, status, ctl);
-  return check_launch("split_gemm_kernel");
+  const int mtiles = g.Mp / SG_BM;
+  if constexpr (CTAS == 1) {
+    kern<<<dim3(ceil_div(g.d, SG_BNC), mtiles, batch), SG_THREADS, smem, s>>>(
+        ma, mb, g.d, g.Kp, g.Mp, g.Np, g.beta, ea, eb, C, sC, epi, status, ctl);
+    return check_launch("split_gemm_kernel");
+  } else {
+    // pairs of row tiles; with an odd count the last pair's second CTA lies wholly
+    // beyond row d (its loads read zeros, its epilogue writes nothing)
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(ceil_div(mtiles, 2) * 2, ceil_div(g.d, SG_BNC), batch);
+    cfg.blockDim = dim3(SG_THREADS, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    const cudaError_t e = cudaLaunchKernelEx(&cfg, kern, ma, mb, g.d, g.Kp, g.Mp, g.Np, g.beta, ea, eb, C, sC, epi,
+                                             status, ctl);
+    if (e != cudaSuccess) {
+      set_last_cuda_error(e, "cudaLaunchKernelEx(split_gemm_kernel, CTA pairs)", __FILE__, __LINE__);
+      return MG_ECUDA;
+    }
+    return check_launch("split_gemm_kernel");
+  }
+}
+
+template <int L, int CTAS>
+static int launch_split_gemm_LC(const SplitGeom& g, int batch, const __nv_bfloat16* Ad, const int* ea,
+                                const __nv_bfloat16* Bd, const int* eb, double* C, long long sC,
+                                const SplitEpi& epi, int* status, const SplitCtl& ctl, cudaStream_t s) {
+  // 16-deep stages also where a 32-deep stage leaves room for only one (L = 8 on one
+  // CTA: no overlap of loads and MMAs; 35 -> 53 algorithmic TFLOP/s measured at d = 512)
+  if (ctl.stage_k == 16 || stages_for<L, 32, CTAS>() < 2)
+    return launch_split_gemm_LB<L, 16, false, CTAS>(g, batch, Ad, ea, Bd, eb, C, sC, epi, status, ctl, s);
+  // 64 only where each half of K is a whole number of 64-wide stages and two stages fit
+  if constexpr (stages_for<L, 64, CTAS>() >= 2)
+    if (ctl.stage_k == 64 && g.Kh() % 64 == 0)
+      return launch_split_gemm_LB<L, 64, false, CTAS>(g, batch, Ad, ea, Bd, eb, C, sC, epi, status, ctl, s);
+  return launch_split_gemm_LB<L, 32, false, CTAS>(g, batch, Ad, ea, Bd, eb, C, sC, epi, status, ctl, s);
 }
 
 template <int L>
@@ -879,15 +1090,12 @@ static int launch_split_gemm_L(const SplitGeom& g, int batch, const __nv_bfloat1
   if constexpr (L % 2 == 0)
     if (paired_layout(g, ctl))
       return launch_split_gemm_LB<L, 16, true>(g, batch, Ad, ea, Bd, eb, C, sC, epi, status, ctl, s);
-  // 16-deep stages also where a 32-deep stage leaves room for only one (L = 8: no
-  // overlap of loads and MMAs; 35 -> 53 algorithmic TFLOP/s measured at d = 512)
-  if (ctl.stage_k == 16 || stages_for<L, 32>() < 2)
-    return launch_split_gemm_LB<L, 16>(g, batch, Ad, ea, Bd, eb, C, sC, epi, status, ctl, s);
-  // 64 only where each half of K is a whole number of 64-wide stages and two stages fit
-  if constexpr (2 * 2 * L * StageK<64>::tile_bytes <= 229376)
-    if (ctl.stage_k == 64 && g.Kh() % 64 == 0)
-      return launch_split_gemm_LB<L, 64>(g, batch, Ad, ea, Bd, eb, C, sC, epi, status, ctl, s);
-  return launch_split_gemm_LB<L, 32>(g, batch, Ad, ea, Bd, eb, C, sC, epi, status, ctl, s);
+  // pairs pay where many digit products per stage make each SM's shared-memory port the
+  // limit (measured: +3% at d = 729 and +7% at d = 4096 with 6 digits, 2-4% slower with 2-4)
+  const bool pair = ctl.cta_pairs > 0 || (ctl.cta_pairs < 0 && L >= 5);
+  if (pair && g.Mp / SG_BM >= 2)
+    return launch_split_gemm_LC<L, 2>(g, batch, Ad, ea, Bd, eb, C, sC, epi, status, ctl, s);
+  return launch_split_gemm_LC<L, 1>(g, batch, Ad, ea, Bd, eb, C, sC, epi, status, ctl, s);
 }
 
 template <int L, typename T>

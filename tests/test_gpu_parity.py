@@ -641,14 +641,17 @@ def test_cgemm_split_stage_k_variants_agree_bit_for_bit(d, L):
     rows) and the paired digit layout (two digits per 64-byte row, 16-deep stages; even L)
     do not change its arithmetic: the MMAs run in the same order over K, so the results
     agree bit for bit (K = 64 applies where L <= 3 and each half of K is a multiple of 64,
-    else the product takes K = 32; odd L ignores the paired layout)."""
+    else the product takes K = 32; odd L ignores the paired layout).  The same holds for
+    the M = 256 products of CTA pairs (d > 128; d = 300 has an odd number of row tiles,
+    so its last pair's second CTA lies beyond row d)."""
     rng = np.random.default_rng(50 + d)
     A, B = rand_c(rng, (2, d, d)), rand_c(rng, (2, d, d))
     c = M.Context(0)
     out = {}
-    for k in (32, 16, 64, "pairs"):
+    for k in (32, 16, 64, "pairs", "cta32", "cta16", "cta64"):
         c.set_digit_pairs(k == "pairs")
-        c.set_stage_k(32 if k == "pairs" else k)
+        c.set_cta_pairs(str(k).startswith("cta"))
+        c.set_stage_k(int(str(k)[3:]) if str(k).startswith("cta") else (32 if k == "pairs" else k))
         C = torch.empty((2, d, d), dtype=torch.complex128, device="cuda")
         M.mg_cgemm(c, 2, d, cuda(A), cuda(B), C, M.MG_PREC_SPLIT, L)
         torch.cuda.synchronize()
@@ -656,6 +659,8 @@ def test_cgemm_split_stage_k_variants_agree_bit_for_bit(d, L):
     c.close()
     assert np.array_equal(out[16], out[32]) and np.array_equal(out[64], out[32])
     assert np.array_equal(out["pairs"], out[32])
+    for k in ("cta32", "cta16", "cta64"):
+        assert np.array_equal(out[k], out[32]), (k, np.abs(out[k] - out[32]).max())
     beta = split_beta(d)
     bound = (L + 2) * 2 * d * (2 * np.abs(A).max()) * (2 * np.abs(B).max()) * (2.0 ** (-beta * L) + L * 2.0 ** (-22 - 3 * beta))
     assert np.abs(out[16] - A @ B).max() <= bound

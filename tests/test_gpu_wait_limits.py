@@ -19,8 +19,13 @@ def rand_c(rng, shape):
     return rng.normal(size=shape) + 1j * rng.normal(size=shape)
 
 
-def test_bounded_wait_runs_out_and_context_recovers():
+@pytest.mark.parametrize("cta_pairs", [False, True])
+def test_bounded_wait_runs_out_and_context_recovers(cta_pairs):
+    """With cta_pairs the product of d = 200 runs on 2-CTA clusters: rank 0's MMA issuer
+    gives up, hands its verdict to both CTAs, and both wind down through the closing
+    cluster barrier."""
     ctx = M.Context(0)
+    ctx.set_cta_pairs(cta_pairs)
     try:
         rng = np.random.default_rng(3)
         d, batch = 200, 2
