@@ -58,6 +58,10 @@ def parse():
                     help="paired digit layout of the split product (mg_ctx_set_digit_pairs)")
     ap.add_argument("--cta-pairs", type=int, default=None, choices=[0, 1],
                     help="split products on CTA pairs (mg_ctx_set_cta_pairs)")
+    ap.add_argument("--tolerance", type=float, default=1e-6,
+                    help="max-abs tolerance the headline plan is tuned for (mg_plan_autotune)")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="headline: keep --precision/--slices instead of tuning for --tolerance")
     ap.add_argument("--intervals", type=int, default=2000)
     ap.add_argument("--e2e-steps", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -223,6 +227,25 @@ def run_ours(args):
     out_host = torch.empty((wl.d, wl.d), dtype=torch.complex128).pin_memory()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # 256 MiB > L2
     plan = M.Plan(ctx, H0, Hk, prec, args.slices)
+    slices = args.slices
+    tuning = None
+    if prec == M.MG_PREC_SPLIT and not args.no_tune:
+        # configuration (digits, Taylor scheme and truncation target, hence squarings) chosen
+        # by the library's autotuner for the stated tolerance, measured before the timed region
+        with torch.cuda.stream(stream):
+            plan.set_controls(N, wl.P, wl.t0, wl.dt, w, samples)
+            t_tune = time.perf_counter()
+            chosen = plan.autotune(M.MG_OUT_PROPAGATOR, args.tolerance, None)
+        tuning = {"tolerance": args.tolerance, "safety_factor": 4, "seconds": time.perf_counter() - t_tune,
+                  "chosen": chosen}
+        prec = chosen["precision"]
+        slices = chosen["slices"] if prec == M.MG_PREC_SPLIT else None
+
+    def configure(p):
+        """The headline plan's configuration on another plan of the same operators."""
+        if tuning is not None:
+            p.set_taylor(tuning["chosen"]["taylor"])
+            p.set_taylor_target(tuning["chosen"]["taylor_target"])
 
     def step():
         plan.set_controls(N, wl.P, wl.t0, wl.dt, w, samples)
@@ -288,8 +311,8 @@ def run_ours(args):
         achieved = per_launch_flops / (per_launch_ms * 1e-3) / 1e12
         if prec == M.MG_PREC_SPLIT:
             peak = float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops")))
-            pairs = args.slices * (args.slices + 1) // 2
-            per_prod = GEMM_DRAM_BYTES_PER_PRODUCT.get((wl.d, args.slices))
+            pairs = slices * (slices + 1) // 2
+            per_prod = GEMM_DRAM_BYTES_PER_PRODUCT.get((wl.d, slices))
             products_per_launch = per_launch_flops / (8.0 * wl.d ** 3)
             roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                     "frac": achieved / peak,
@@ -310,11 +333,13 @@ def run_ours(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": max(3, args.warmup), "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": (f"bf16 digits x{args.slices} (fp32 accumulate) + f64" if prec == M.MG_PREC_SPLIT else "f64"),
+            "dtype": (f"bf16 digits x{slices} (fp32 accumulate) + f64" if prec == M.MG_PREC_SPLIT else "f64"),
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "d": wl.d, "intervals": N, "quadrature_points": wl.P,
-                       "controls": wl.K, "output": "full propagator", "precision": args.precision,
-                       "slices": args.slices if prec == M.MG_PREC_SPLIT else None,
+                       "controls": wl.K, "output": "full propagator",
+                       "precision": "split" if prec == M.MG_PREC_SPLIT else "fp64",
+                       "slices": slices if prec == M.MG_PREC_SPLIT else None,
+                       "tuning": tuning,
                        "l2": "256 MiB buffer written before every timed step",
                        "parallelism": "independent replica per GPU"},
             "roofline": roof,
@@ -334,7 +359,8 @@ def run_ours(args):
             ref = oracle.evolve_workload(wl, n_intervals=n_s)
             cpu_s = time.perf_counter() - t0
             with torch.cuda.stream(stream):
-                pre = M.Plan(ctx, H0, Hk, prec, args.slices)
+                pre = M.Plan(ctx, H0, Hk, prec, slices if prec == M.MG_PREC_SPLIT else args.slices)
+                configure(pre)
                 pre.set_controls(n_s, wl.P, wl.t0, wl.dt, w, samples[:n_s].contiguous())
                 pre.evolve(M.MG_OUT_PROPAGATOR, None, out, 0, report=False)
                 stream.synchronize()
@@ -345,6 +371,22 @@ def run_ours(args):
                                                 f"(numpy eigh exponentials, sequential products)"}
             result["accuracy"] = {"max_abs_err_vs_fp64_oracle": err, "intervals_compared": n_s,
                                   "tolerance": 1e-6 if prec == M.MG_PREC_SPLIT else 1e-11}
+        # U(T) of the last timed step over all N intervals against the oracle's sampled entries
+        # (tests/golden, written by a script that runs only the CPU oracle)
+        gold = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tests", "golden",
+                            "chain_d729_N2000_propagator.json")
+        if os.path.exists(gold) and N == 2000 and rank == 0:
+            with open(gold) as f:
+                g = json.load(f)
+            e = np.array(g["entries"])
+            with torch.cuda.stream(stream):
+                plan.set_controls(N, wl.P, wl.t0, wl.dt, w, samples)
+                plan.evolve(M.MG_OUT_PROPAGATOR, None, out, 0, report=False)
+                stream.synchronize()
+            U = out.cpu().numpy()
+            err_all = float(np.abs(U[e[:, 0].astype(int), e[:, 1].astype(int)] - (e[:, 2] + 1j * e[:, 3])).max())
+            result.setdefault("accuracy", {})["max_abs_err_all_intervals"] = err_all
+            result["accuracy"]["all_intervals_compared"] = f"{len(e)} sampled entries of U(T) after all {N}"
     plan.close()
     if result is not None and ws == 1 and not args.no_serving:
         # the served stream beside the headline: the first requests of the Poisson(200/s)
@@ -771,10 +813,10 @@ def run_tune(args):
         key, sel, ents = open(path).read().strip().split("\t")
         table = []
         for e in ents.split(";"):
-            p, s_, t, a, err, us = e.split()
+            p, s_, t, a, err, us, *tu = e.split()
             table.append({"path": "action" if int(a) else names[(int(p), 0)], "digits": int(s_) or None,
                           "taylor": "ps" if int(t) else "deg18", "error_est": float(err),
-                          "us_per_interval": float(us)})
+                          "us_per_interval": float(us), "taylor_target": float(tu[0]) if tu else 0.0})
         print(json.dumps({"workload": wl.name, "d": wl.d, "N": wl.N, "output": "state" if output == 0 else "U",
                           "tolerance": tol, "key": key, "selected": int(sel), "chosen": chosen,
                           "candidates": table}), flush=True)

@@ -261,6 +261,7 @@ typedef struct mg_tune_entry {
   int32_t action;
   double error;
   double us_per_interval;
+  double taylor_target;   /* mg_plan_set_taylor_target's u (0: the arithmetic's unit roundoff) */
 } mg_tune_entry;
 
 /* Host only: the index of the fastest entry whose error times `safety` (>= 1)
@@ -285,7 +286,9 @@ int mg_tune_cache_lookup(const char* path, const char* key, mg_tune_entry* entry
  * with nu = the binary exponent of the largest bound on ||Hbar_n - tau_n I||_1
  * and N the interval count rounded up to a power of two.  On a miss every
  * candidate -- FP64; split with 4..7 digits, each with and without the
- * degree-18 scheme; for states the action path -- evolves the plan's first
+ * degree-18 scheme and with the Taylor truncation target (mg_plan_set_taylor_target)
+ * at its arithmetic's roundoff, 2^-34 and 2^-28 (those coarser than the digits'
+ * roundoff 2^-(beta L)); for states the action path -- evolves the plan's first
  * n_probe <= 64 intervals; the reference is the FP64 path (the most accurate
  * split candidate for d > 1024, where FP64 products are slow); a candidate's
  * error is its deviation from the reference times N / n_probe (errors of
@@ -296,6 +299,17 @@ int mg_tune_cache_lookup(const char* path, const char* key, mg_tune_entry* entry
 int mg_plan_autotune(mg_plan* plan, int output, double tolerance, const char* cache_path, mg_tune_entry* chosen);
 /* Taylor scheme of a plan (MG_TAYLOR_AUTO, the default, or MG_TAYLOR_PS). */
 int mg_plan_set_taylor(mg_plan* plan, int taylor);
+/* Truncation target u of the plan's Taylor series (scaling and squaring of
+ * App. A.5): the degree m and squaring count s are chosen so that the series'
+ * tail, sum_{j>m} theta^j / j!, stays within u theta for ||2^-s X|| <= theta, so
+ * each interval's exponential errs by about u ||Hbar_n||_1 (1-norm) from
+ * truncation.  u = 0 (the default) takes the unit roundoff of the products'
+ * arithmetic (2^-53 for FP64, 2^-(beta L) for split digits); a larger u (at most
+ * 1e-3) trades accuracy for fewer squarings, errors that may add up over N
+ * intervals to N u max ||Hbar_n||_1.  mg_evolve and mg_evolve_batch honour it
+ * (batched plans with different targets form separate groups).  MG_EINVAL for u
+ * outside [0, 1e-3]. */
+int mg_plan_set_taylor_target(mg_plan* plan, double u);
 /* Tuning cache of a context's servers (NULL: none); see MG_PREC_AUTO. */
 int mg_ctx_set_tune_cache(mg_ctx* ctx, const char* path);
 

@@ -161,6 +161,7 @@ struct mg_plan {
   std::vector<double> opnorm;
   int opnorm_dp = 0;
   int taylor_mode = MG_TAYLOR_AUTO;   // MG_TAYLOR_PS: Paterson-Stockmeyer degrees only
+  double taylor_u = 0.0;              // truncation target of the Taylor series (0: the arithmetic's)
 };
 
 namespace {
@@ -350,6 +351,7 @@ struct Engine {
   const int* item_sq = nullptr;
   int sq_step = 0;
   int taylor_mode = MG_TAYLOR_AUTO;   // MG_TAYLOR_PS: no degree-18 scheme
+  double taylor_u = 0.0;              // coarser truncation target than the arithmetic's, or 0
   bool allow18() const { return prec == MG_PREC_SPLIT && taylor_mode != MG_TAYLOR_PS; }
   SplitCtl ctl() const {
     SplitCtl c;
@@ -592,7 +594,7 @@ int expm_chunk(mg_ctx* ctx, Engine& eng, int batch, double* W, const double* tau
     }
     nmax = std::max(nmax, nrm[b]);
   }
-  const double u = unit_roundoff(eng.prec, eng.L, d);
+  const double u = std::max(unit_roundoff(eng.prec, eng.L, d), eng.taylor_u);
   TaylorChoice tc = choose_taylor(nmax, u, eng.allow18());
   if (st) {
     st->m = tc.m;
@@ -1629,6 +1631,7 @@ int mg_evolve(mg_plan* p, int output, const double* in, double* out, int reorth_
   }
   Engine eng{ctx, d, p->precision, p->L};
   eng.taylor_mode = p->taylor_mode;
+  eng.taylor_u = p->taylor_u;
   PropState ps;
   ps.output = output;
   ps.d = d;
@@ -2000,6 +2003,7 @@ struct ChunkPlan {
 
 struct GroupProgram {
   int dp = 0, prec = MG_PREC_FP64, L = 6, reorth = 0, taylor = MG_TAYLOR_AUTO;
+  double taylor_u = 0.0;
   std::vector<BatchJob> jobs;
   std::vector<mg_plan*> plans;
   TaylorChoice tc{};
@@ -2230,7 +2234,8 @@ int build_program(mg_ctx* ctx, GroupProgram& G) {
   MG_TRY(norm_bounds(ctx, G.jobs, G.plans, dp, bound));
   G.bound = 0.0;
   for (double b : bound) G.bound = std::max(G.bound, b);
-  G.tc = choose_taylor(G.bound, unit_roundoff(G.prec, G.L, dp), G.prec == MG_PREC_SPLIT && G.taylor != MG_TAYLOR_PS);
+  G.tc = choose_taylor(G.bound, std::max(unit_roundoff(G.prec, G.L, dp), G.taylor_u),
+                       G.prec == MG_PREC_SPLIT && G.taylor != MG_TAYLOR_PS);
   G.S = G.tc.s;
   return MG_OK;
 }
@@ -2377,6 +2382,7 @@ int issue_group(mg_ctx* ctx, GroupProgram& G, const double* const* in, double* c
   const long long md = mat_doubles(dp);
   Engine eng{ctx, dp, G.prec, G.L};
   eng.taylor_mode = G.taylor;
+  eng.taylor_u = G.taylor_u;
   MG_CUDA_TRY(cudaMemsetAsync(G.job_fail, 0, sizeof(int) * G.jobs.size(), s));
   MG_CUDA_TRY(cudaMemsetAsync(G.overflow, 0, sizeof(int), s));
   for (BatchJob& j : G.jobs) {
@@ -2429,8 +2435,12 @@ int mg_evolve_batch(mg_ctx* ctx, int n, mg_plan* const* plans, const int* output
   // group by (precision, digits, padded dimension); one group at a time
   struct Key {
     int prec, L, dp, taylor;
+    double taylor_u;
     bool operator<(const Key& o) const {
-      return prec != o.prec ? prec < o.prec : (L != o.L ? L < o.L : (dp != o.dp ? dp < o.dp : taylor < o.taylor));
+      if (prec != o.prec) return prec < o.prec;
+      if (L != o.L) return L < o.L;
+      if (dp != o.dp) return dp < o.dp;
+      return taylor != o.taylor ? taylor < o.taylor : taylor_u < o.taylor_u;
     }
   };
   struct Item { Key k; BatchJob j; mg_plan* p; };
@@ -2448,7 +2458,7 @@ int mg_evolve_batch(mg_ctx* ctx, int n, mg_plan* const* plans, const int* output
     j.dt = p->dt;
     j.c = p->c;
     const int L = p->precision == MG_PREC_SPLIT ? p->L : 0;
-    all.push_back({Key{p->precision, L, round_dim(p->d), p->taylor_mode}, j, p});
+    all.push_back({Key{p->precision, L, round_dim(p->d), p->taylor_mode, p->taylor_u}, j, p});
   }
   // state jobs of action-flagged plans: every one in a single launch, one CTA per job
   {
@@ -2508,6 +2518,7 @@ int mg_evolve_batch(mg_ctx* ctx, int n, mg_plan* const* plans, const int* output
     G.L = k.L == 0 ? 6 : k.L;
     G.reorth = reorth_every;
     G.taylor = k.taylor;
+    G.taylor_u = k.taylor_u;
     while (g1 < all.size() && !(all[g0].k < all[g1].k) && !(all[g1].k < all[g0].k)) {
       G.jobs.push_back(all[g1].j);
       G.plans.push_back(all[g1].p);
@@ -2597,8 +2608,12 @@ int mg_batch_graph_create(mg_ctx* ctx, int n, mg_plan* const* plans, const int* 
   MG_CUDA_TRY(cudaSetDevice(ctx->device));
   struct Key {
     int prec, L, dp, taylor;
+    double taylor_u;
     bool operator<(const Key& o) const {
-      return prec != o.prec ? prec < o.prec : (L != o.L ? L < o.L : (dp != o.dp ? dp < o.dp : taylor < o.taylor));
+      if (prec != o.prec) return prec < o.prec;
+      if (L != o.L) return L < o.L;
+      if (dp != o.dp) return dp < o.dp;
+      return taylor != o.taylor ? taylor < o.taylor : taylor_u < o.taylor_u;
     }
   };
   struct Item { Key k; BatchJob j; mg_plan* p; };
@@ -2628,7 +2643,8 @@ int mg_batch_graph_create(mg_ctx* ctx, int n, mg_plan* const* plans, const int* 
     j.N = p->N;
     j.dt = p->dt;
     j.c = p->c;
-    all.push_back({Key{p->precision, p->precision == MG_PREC_SPLIT ? p->L : 0, round_dim(p->d), p->taylor_mode}, j, p});
+    all.push_back({Key{p->precision, p->precision == MG_PREC_SPLIT ? p->L : 0, round_dim(p->d), p->taylor_mode,
+                           p->taylor_u}, j, p});
     g->plans.push_back(p);
     g->c_ptr.push_back(p->c);
     g->N.push_back(p->N);
@@ -2650,6 +2666,7 @@ int mg_batch_graph_create(mg_ctx* ctx, int n, mg_plan* const* plans, const int* 
     G->L = k.L == 0 ? 6 : k.L;
     G->reorth = reorth_every;
     G->taylor = k.taylor;
+    G->taylor_u = k.taylor_u;
     while (g1 < all.size() && !(all[g0].k < all[g1].k) && !(all[g1].k < all[g0].k)) {
       G->jobs.push_back(all[g1].j);
       G->plans.push_back(all[g1].p);
@@ -2758,6 +2775,7 @@ struct SJob {
   uint64_t id = 0;
   BatchJob b;
   int dp = 0, prec = 0, L = 6, taylor = MG_TAYLOR_AUTO;
+  double taylor_u = 0.0;
   double* out = nullptr;
   cudaMemcpyKind out_kind = cudaMemcpyDeviceToDevice;
   std::vector<void*> owned;     // device buffers of this job (stream-ordered allocations)
@@ -2986,7 +3004,7 @@ void server_loop(mg_server* srv) {
           }
         }
         for (SJob* j : srv->active)
-          if (j->dp == head->dp && j->prec == head->prec && j->L == head->L && j->taylor == head->taylor &&
+          if (j->dp == head->dp && j->prec == head->prec && j->L == head->L && j->taylor == head->taylor && j->taylor_u == head->taylor_u &&
               (int)group.size() < srv->seg_cap)
             group.push_back(j);
       }
@@ -2995,6 +3013,7 @@ void server_loop(mg_server* srv) {
     const auto t0 = clk::now();
     Engine eng{ctx, group[0]->dp, group[0]->prec, group[0]->L};
     eng.taylor_mode = group[0]->taylor;
+    eng.taylor_u = group[0]->taylor_u;
     int rc = MG_OK;
     for (SJob* j : group) cudaStreamWaitEvent(ctx->stream, j->ready, 0);
     const int chunk = chunk_size(ctx, eng.d, eng.prec, eng.L, 1 << 30, 1);
@@ -3261,6 +3280,7 @@ int mg_submit(mg_server* srv, const mg_job* job_in, uint64_t* job_id) {
   mg_job resolved = *job_in;
   const mg_job* job = &resolved;
   int taylor = MG_TAYLOR_AUTO;
+  double taylor_u = 0.0;
   if (resolved.precision == MG_PREC_AUTO) {
     // the latest tuning of this job's family in the context's cache; split, 6 digits on a miss
     mg_tune_entry e{};
@@ -3271,6 +3291,7 @@ int mg_submit(mg_server* srv, const mg_job* job_in, uint64_t* job_id) {
       resolved.precision = e.precision;
       resolved.slices = e.slices;
       taylor = e.taylor;
+      taylor_u = e.taylor_target;
       if (resolved.output == MG_OUT_STATE) {
         if (e.action) resolved.flags |= MG_FLAG_STATE_ACTION;
         else resolved.flags &= ~MG_FLAG_STATE_ACTION;
@@ -3312,6 +3333,7 @@ int mg_submit(mg_server* srv, const mg_job* job_in, uint64_t* job_id) {
   j->prec = job->precision;
   j->L = job->precision == MG_PREC_SPLIT ? job->slices : 6;
   j->taylor = taylor;
+  j->taylor_u = taylor_u;
   j->out = job->out;
   const bool host = (job->flags & MG_FLAG_HOST_PTRS) != 0;
   j->out_kind = host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
@@ -3474,6 +3496,12 @@ int mg_plan_set_taylor(mg_plan* p, int taylor) {
   return MG_OK;
 }
 
+int mg_plan_set_taylor_target(mg_plan* p, double u) {
+  if (!p || !(u >= 0.0) || u > 1e-3) return MG_EINVAL;
+  p->taylor_u = u;
+  return MG_OK;
+}
+
 int mg_ctx_set_tune_cache(mg_ctx* ctx, const char* path) {
   if (!ctx) return MG_EINVAL;
   ctx->tune_cache = path ? path : "";
@@ -3486,6 +3514,7 @@ void apply_tuning(mg_plan* p, int output, const mg_tune_entry& e) {
   p->precision = e.precision;
   if (e.precision == MG_PREC_SPLIT) p->L = e.slices;
   p->taylor_mode = e.taylor;
+  p->taylor_u = e.taylor_target;
   if (output == MG_OUT_STATE) {
     if (e.action) p->flags |= MG_FLAG_STATE_ACTION;
     else p->flags &= ~MG_FLAG_STATE_ACTION;
@@ -3527,13 +3556,19 @@ int mg_plan_autotune(mg_plan* p, int output, double tolerance, const char* cache
   // candidates
   std::vector<mg_tune_entry> cand;
   const bool fp64_ok = d <= 1024;   // above, FP64 products take seconds per interval
-  if (fp64_ok) cand.push_back(mg_tune_entry{MG_PREC_FP64, 0, MG_TAYLOR_PS, 0, 0.0, 0.0});
+  if (fp64_ok) cand.push_back(mg_tune_entry{MG_PREC_FP64, 0, MG_TAYLOR_PS, 0, 0.0, 0.0, 0.0});
+  // truncation targets coarser than a candidate's own roundoff trade accuracy for squarings
+  const double targets[] = {0.0, std::ldexp(1.0, -34), std::ldexp(1.0, -28)};
   for (int L = 4; L <= 7; ++L)
-    for (int t : {MG_TAYLOR_AUTO, MG_TAYLOR_PS}) cand.push_back(mg_tune_entry{MG_PREC_SPLIT, L, t, 0, 0.0, 0.0});
+    for (int t : {MG_TAYLOR_AUTO, MG_TAYLOR_PS})
+      for (double tu : targets)
+        if (tu == 0.0 || tu > unit_roundoff(MG_PREC_SPLIT, L, d))
+          cand.push_back(mg_tune_entry{MG_PREC_SPLIT, L, t, 0, 0.0, 0.0, tu});
   if (output == MG_OUT_STATE && check_action_limits(d, 1 + p->Kx) == MG_OK)
-    cand.push_back(mg_tune_entry{MG_PREC_FP64, 0, MG_TAYLOR_PS, 1, 0.0, 0.0});
+    cand.push_back(mg_tune_entry{MG_PREC_FP64, 0, MG_TAYLOR_PS, 1, 0.0, 0.0, 0.0});
   const int n_probe = std::min(p->N, d > 1024 ? 8 : 64);
   const int saveN = p->N, savePrec = p->precision, saveL = p->L, saveFlags = p->flags, saveT = p->taylor_mode;
+  const double saveU = p->taylor_u;
   const long long outn = output == MG_OUT_STATE ? 2LL * d : mat_doubles(d);
   double *ref = nullptr, *out = nullptr, *in = nullptr, *dmax = nullptr;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -3573,7 +3608,7 @@ int mg_plan_autotune(mg_plan* p, int output, double tolerance, const char* cache
   if (rc == MG_OK) {
     // reference: the FP64 path, or above d = 1024 the most accurate split candidate
     double us = 0.0;
-    mg_tune_entry r = fp64_ok ? cand[0] : mg_tune_entry{MG_PREC_SPLIT, 8, MG_TAYLOR_PS, 0, 0.0, 0.0};
+    mg_tune_entry r = fp64_ok ? cand[0] : mg_tune_entry{MG_PREC_SPLIT, 8, MG_TAYLOR_PS, 0, 0.0, 0.0, 0.0};
     rc = run(r, ref, &us);
     if (rc == MG_OK && fp64_ok) {
       cand[0].us_per_interval = us;
@@ -3606,6 +3641,7 @@ int mg_plan_autotune(mg_plan* p, int output, double tolerance, const char* cache
   p->L = saveL;
   p->flags = saveFlags;
   p->taylor_mode = saveT;
+  p->taylor_u = saveU;
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
   cudaFree(ref);

@@ -12,7 +12,8 @@
 //
 // Cache file: plain text, one line per tuning,
 //   <key> TAB <selected index> TAB <entry>;<entry>;...
-// with every entry "precision slices taylor action error us_per_interval".  A
+// with every entry "precision slices taylor action error us_per_interval
+// taylor_target" (entries of six fields read with taylor_target 0).  A
 // lookup takes the last line whose key matches (exactly, or by prefix up to a
 // '|' boundary for callers that know only the leading fields of the key).
 #include "common.cuh"
@@ -46,14 +47,16 @@ bool parse_line(const std::string& line, std::string& key, int& sel, std::vector
     const std::string f = line.substr(pos, end - pos);
     mg_tune_entry e{};
     int p, s, t, a;
-    double err, us;
-    if (std::sscanf(f.c_str(), "%d %d %d %d %lg %lg", &p, &s, &t, &a, &err, &us) == 6) {
+    double err, us, tu = 0.0;
+    const int got = std::sscanf(f.c_str(), "%d %d %d %d %lg %lg %lg", &p, &s, &t, &a, &err, &us, &tu);
+    if (got == 6 || got == 7) {
       e.precision = p;
       e.slices = s;
       e.taylor = t;
       e.action = a;
       e.error = err;
       e.us_per_interval = us;
+      e.taylor_target = got == 7 ? tu : 0.0;
       ents.push_back(e);
     }
     pos = end + 1;
@@ -91,10 +94,10 @@ int mg_tune_cache_store(const char* path, const char* key, int n, const mg_tune_
   if (!path || !key || !*key || n < 1 || !e || selected < 0 || selected >= n) return MG_EINVAL;
   if (std::strchr(key, '\t') || std::strchr(key, '\n') || std::strchr(key, ';')) return MG_EINVAL;
   std::string line = std::string(key) + "\t" + std::to_string(selected) + "\t";
-  char buf[160];
+  char buf[192];
   for (int i = 0; i < n; ++i) {
-    std::snprintf(buf, sizeof(buf), "%s%d %d %d %d %.17g %.17g", i ? ";" : "", e[i].precision, e[i].slices,
-                  e[i].taylor, e[i].action, e[i].error, e[i].us_per_interval);
+    std::snprintf(buf, sizeof(buf), "%s%d %d %d %d %.17g %.17g %.17g", i ? ";" : "", e[i].precision, e[i].slices,
+                  e[i].taylor, e[i].action, e[i].error, e[i].us_per_interval, e[i].taylor_target);
     line += buf;
   }
   line += "\n";

@@ -78,7 +78,8 @@ class mg_job(ctypes.Structure):
 
 class mg_tune_entry(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("slices", ctypes.c_int32), ("taylor", ctypes.c_int32),
-                ("action", ctypes.c_int32), ("error", ctypes.c_double), ("us_per_interval", ctypes.c_double)]
+                ("action", ctypes.c_int32), ("error", ctypes.c_double), ("us_per_interval", ctypes.c_double),
+                ("taylor_target", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -125,6 +126,7 @@ SIGNATURES = {
     "mg_tune_cache_lookup": (_I, [ctypes.c_char_p, ctypes.c_char_p, ctypes.POINTER(mg_tune_entry)]),
     "mg_plan_autotune": (_I, [_P, _I, _D, ctypes.c_char_p, ctypes.POINTER(mg_tune_entry)]),
     "mg_plan_set_taylor": (_I, [_P, _I]),
+    "mg_plan_set_taylor_target": (_I, [_P, ctypes.c_double]),
     "mg_ctx_set_tune_cache": (_I, [_P, ctypes.c_char_p]),
     "mg_batch_graph_create": (_I, [_P, _I, _P, _P, _P, _P, _I, ctypes.POINTER(_P)]),
     "mg_batch_graph_launch": (_I, [_P, _P]),
@@ -263,6 +265,9 @@ class Plan:
 
     def set_taylor(self, taylor):
         _check(load().mg_plan_set_taylor(self.h, int(taylor)), "mg_plan_set_taylor")
+
+    def set_taylor_target(self, u):
+        _check(load().mg_plan_set_taylor_target(self.h, float(u)), "mg_plan_set_taylor_target")
 
     def set_magnus_order(self, order):
         _check(load().mg_plan_set_magnus_order(self.h, int(order)), "mg_plan_set_magnus_order")
@@ -424,7 +429,7 @@ def _entries(entries):
     arr = (mg_tune_entry * len(entries))()
     for i, e in enumerate(entries):
         for k, _ in mg_tune_entry._fields_:
-            setattr(arr[i], k, e[k])
+            setattr(arr[i], k, e.get(k, 0.0) if k == "taylor_target" else e[k])
     return arr
 
 
@@ -542,7 +547,7 @@ def node_samples(wl, N=None):
 
 
 def evolve_workload(ctx, wl, precision=MG_PREC_FP64, slices=6, N=None, reorth_every=0, device="cuda", order=1,
-                    flags=0, trajectory=False):
+                    flags=0, trajectory=False, taylor_target=0.0):
     """Run a workloads.Workload through mg_plan_create / mg_set_controls / mg_evolve
     (trajectory=True: the (N + 1) x d stroboscopic states of a state workload)."""
     import torch
@@ -552,6 +557,8 @@ def evolve_workload(ctx, wl, precision=MG_PREC_FP64, slices=6, N=None, reorth_ev
                 flags)
     if order != 1:
         plan.set_magnus_order(order)
+    if taylor_target:
+        plan.set_taylor_target(taylor_target)
     plan.set_controls(N, wl.P, wl.t0, wl.dt, w, torch.from_numpy(samples).to(device))
     if wl.psi0 is None:
         out = torch.empty((wl.d, wl.d), dtype=torch.complex128, device=device)

@@ -8,8 +8,8 @@ import pytest
 from paper_2411_09982_gb300 import magnus as M
 
 
-def entry(p, s, t, a, err, us):
-    return dict(precision=p, slices=s, taylor=t, action=a, error=err, us_per_interval=us)
+def entry(p, s, t, a, err, us, tu=0.0):
+    return dict(precision=p, slices=s, taylor=t, action=a, error=err, us_per_interval=us, taylor_target=tu)
 
 
 TABLE = [entry(0, 0, 1, 0, 1e-12, 900.0),      # FP64: accurate, slow
@@ -74,3 +74,18 @@ def test_cache_rejects_keys_that_would_break_the_format(tmp_path):
     with pytest.raises(M.MagnusError):
         M.mg_tune_cache_store(path, "k", TABLE, len(TABLE))
     assert not os.path.exists(path)
+
+
+def test_cache_keeps_the_taylor_target_and_reads_six_field_entries(tmp_path):
+    """An entry's Taylor truncation target survives the round trip bit for bit; lines
+    written with six fields per entry (no target) read back with target 0."""
+    path = str(tmp_path / "tune.txt")
+    key = "gpu=GB300|d=729|K=6|out=1|tol=1e-06|nu=3|N=2048"
+    table = [entry(1, 6, 0, 0, 1.5e-8, 310.0, 2.0 ** -34), entry(1, 6, 0, 0, 7.6e-9, 350.0)]
+    M.mg_tune_cache_store(path, key, table, 0)
+    got = M.mg_tune_cache_lookup(path, key)
+    assert got == table[0] and got["taylor_target"] == 2.0 ** -34
+    with open(path, "a") as f:
+        f.write("gpu=GB300|d=30|K=1|out=0|tol=1e-06|nu=5|N=1024\t1\t0 0 1 0 1e-12 900;1 6 0 0 8e-09 350\n")
+    old = M.mg_tune_cache_lookup(path, "gpu=GB300|d=30|K=1|out=0|tol=1e-06|nu=5|N=1024")
+    assert old == entry(1, 6, 0, 0, 8e-9, 350.0)
