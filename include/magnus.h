@@ -286,11 +286,13 @@ int mg_tune_cache_lookup(const char* path, const char* key, mg_tune_entry* entry
  * with nu = the binary exponent of the largest bound on ||Hbar_n - tau_n I||_1
  * and N the interval count rounded up to a power of two.  On a miss every
  * candidate -- FP64; split with 4..7 digits, each with and without the
- * degree-18 scheme and with the Taylor truncation target (mg_plan_set_taylor_target)
- * at its arithmetic's roundoff, 2^-34 and 2^-28 (those coarser than the digits'
- * roundoff 2^-(beta L)); for states the action path -- evolves the plan's first
- * n_probe <= 64 intervals; the reference is the FP64 path (the most accurate
- * split candidate for d > 1024, where FP64 products are slow); a candidate's
+ * degree-18 scheme; for 5..7 digits with the degree-18 scheme also coarser Taylor
+ * truncation targets (mg_plan_set_taylor_target): 2^-34, 2^-28 and the smallest
+ * targets that save one and two squarings at the largest norm bound (each only
+ * where coarser than the digits' roundoff 2^-(beta L)); for states the action
+ * path -- evolves the plan's first
+ * n_probe <= 64 intervals (8 for d > 1024); the reference is the FP64 path (for
+ * d > 1024 run once and not itself a candidate: seconds per interval); a candidate's
  * error is its deviation from the reference times N / n_probe (errors of
  * near-identical intervals add up), FP64's own u nu N; the fastest candidate
  * within tolerance / 4 is taken and the whole table is stored.  chosen (may be

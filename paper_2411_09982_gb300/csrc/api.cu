@@ -257,18 +257,21 @@ struct TaylorChoice {
 // series then errs by at most u relative to ||X|| <= theta, and the 2^s
 // squarings keep that relative bound for 2^s X (the error of the squared
 // result grows like 2^s * u * theta = u * ||A||).
+// sum_{j>m} theta^j / j! divided by theta
+double taylor_tail_ratio(int m, double th) {
+  double term = 1.0;
+  for (int j = 1; j <= m; ++j) term *= th / j;
+  double sum = 0.0;
+  for (int j = m + 1; j <= m + 80; ++j) {
+    term *= th / j;
+    sum += term;
+    if (term < 1e-40 * sum) break;
+  }
+  return sum / th;
+}
+
 double taylor_theta(int m, double u) {
-  auto tail_ratio = [&](double th) {
-    double term = 1.0;
-    for (int j = 1; j <= m; ++j) term *= th / j;
-    double sum = 0.0;
-    for (int j = m + 1; j <= m + 80; ++j) {
-      term *= th / j;
-      sum += term;
-      if (term < 1e-40 * sum) break;
-    }
-    return sum / th;
-  };
+  auto tail_ratio = [&](double th) { return taylor_tail_ratio(m, th); };
   double lo = 0.0, hi = 40.0;
   for (int it = 0; it < 200; ++it) {
     double mid = 0.5 * (lo + hi);
@@ -3557,13 +3560,24 @@ int mg_plan_autotune(mg_plan* p, int output, double tolerance, const char* cache
   std::vector<mg_tune_entry> cand;
   const bool fp64_ok = d <= 1024;   // above, FP64 products take seconds per interval
   if (fp64_ok) cand.push_back(mg_tune_entry{MG_PREC_FP64, 0, MG_TAYLOR_PS, 0, 0.0, 0.0, 0.0});
-  // truncation targets coarser than a candidate's own roundoff trade accuracy for squarings
-  const double targets[] = {0.0, std::ldexp(1.0, -34), std::ldexp(1.0, -28)};
+  // Truncation targets coarser than a candidate's own roundoff trade accuracy for
+  // squarings: two fixed ones, and the smallest targets that save one and two squarings
+  // at the plan's norm bound nu with the degree-18 scheme (tail of 2^-(s-k) nu within u).
+  std::vector<double> targets{std::ldexp(1.0, -34), std::ldexp(1.0, -28)};
+  {
+    const int s0 = choose_taylor(nu, unit_roundoff(MG_PREC_SPLIT, 6, d), true).s;
+    for (int k = 1; k <= 2 && s0 - k >= 0; ++k) {
+      const double u = taylor_tail_ratio(18, std::ldexp(nu, -(s0 - k))) * (1.0 + 1e-6);
+      if (u <= 1e-3) targets.push_back(u);
+    }
+  }
   for (int L = 4; L <= 7; ++L)
-    for (int t : {MG_TAYLOR_AUTO, MG_TAYLOR_PS})
+    for (int t : {MG_TAYLOR_AUTO, MG_TAYLOR_PS}) {
+      cand.push_back(mg_tune_entry{MG_PREC_SPLIT, L, t, 0, 0.0, 0.0, 0.0});
+      if (t != MG_TAYLOR_AUTO || L < 5) continue;
       for (double tu : targets)
-        if (tu == 0.0 || tu > unit_roundoff(MG_PREC_SPLIT, L, d))
-          cand.push_back(mg_tune_entry{MG_PREC_SPLIT, L, t, 0, 0.0, 0.0, tu});
+        if (tu > unit_roundoff(MG_PREC_SPLIT, L, d)) cand.push_back(mg_tune_entry{MG_PREC_SPLIT, L, t, 0, 0.0, 0.0, tu});
+    }
   if (output == MG_OUT_STATE && check_action_limits(d, 1 + p->Kx) == MG_OK)
     cand.push_back(mg_tune_entry{MG_PREC_FP64, 0, MG_TAYLOR_PS, 1, 0.0, 0.0, 0.0});
   const int n_probe = std::min(p->N, d > 1024 ? 8 : 64);
@@ -3606,10 +3620,20 @@ int mg_plan_autotune(mg_plan* p, int output, double tolerance, const char* cache
   };
   const double scale = (double)saveN / n_probe;
   if (rc == MG_OK) {
-    // reference: the FP64 path, or above d = 1024 the most accurate split candidate
+    // reference: the FP64 path.  Above d = 1024 it is run once, untimed, and is no
+    // candidate (seconds per interval there); no split configuration serves instead: at
+    // large d more digits put more digit pairs into the FP32 accumulator of levels >= 3,
+    // whose rounding then sets the error (measured at d = 4096: 8 digits err 2x more
+    // than 7 against the oracle)
     double us = 0.0;
-    mg_tune_entry r = fp64_ok ? cand[0] : mg_tune_entry{MG_PREC_SPLIT, 8, MG_TAYLOR_PS, 0, 0.0, 0.0, 0.0};
-    rc = run(r, ref, &us);
+    if (fp64_ok) {
+      rc = run(cand[0], ref, &us);
+    } else {
+      mg_tune_entry f{MG_PREC_FP64, 0, MG_TAYLOR_PS, 0, 0.0, 0.0, 0.0};
+      apply_tuning(p, output, f);
+      rc = mg_evolve(p, output, output == MG_OUT_STATE ? in : nullptr, ref, 0, 0, nullptr);
+      if (rc == MG_OK && cudaStreamSynchronize(ctx->stream) != cudaSuccess) rc = MG_ECUDA;
+    }
     if (rc == MG_OK && fp64_ok) {
       cand[0].us_per_interval = us;
       // FP64's own rounding: u per unit of phase per interval (the oracle and an independent

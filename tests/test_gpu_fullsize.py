@@ -80,10 +80,13 @@ GOLDEN_4096_130 = os.path.join(os.path.dirname(os.path.abspath(__file__)), "gold
 
 
 def test_alltoall_d4096_130_intervals_split_with_reorth(ctx):
-    """The d = 4096 workload's first 130 intervals in split precision with FP64
-    re-orthonormalisation every 64 intervals (two re-orthonormalisation boundaries; the
-    tree product spans several levels and, with a small workspace, several chunks) against
-    the oracle's sampled entries."""
+    """The d = 4096 workload's first 130 intervals in split precision (7 digits: at
+    beta = 6 six digits carry 36 bits and, extrapolated over all 500 intervals, would
+    exceed 1e-6) with FP64 re-orthonormalisation every 64 intervals (two
+    re-orthonormalisation boundaries; the tree product spans several levels and, with a
+    small workspace, several chunks) against the oracle's sampled entries, held to
+    1e-6 x 130/500: the share of the tolerance these intervals may use when errors
+    grow linearly with the interval count, as they do here (measured 5.7e-8)."""
     with open(GOLDEN_4096_130) as f:
         g = json.load(f)
     n = g["workload"]["intervals_applied"]
@@ -91,8 +94,8 @@ def test_alltoall_d4096_130_intervals_split_with_reorth(ctx):
     wl = W.config(3)
     for ws in (None, 3 << 30):
         c = M.Context(0, workspace_limit=ws) if ws else ctx
-        U, rep = M.evolve_workload(c, wl, M.MG_PREC_SPLIT, 6, N=n, reorth_every=64)
-        err = check(U.cpu().numpy(), g, 1e-6)
+        U, rep = M.evolve_workload(c, wl, M.MG_PREC_SPLIT, 7, N=n, reorth_every=64)
+        err = check(U.cpu().numpy(), g, 1e-6 * n / wl.N)
         assert rep["unitarity_defect"] < 1e-6, rep["unitarity_defect"]
         if ws:
             c.close()
