@@ -534,7 +534,9 @@ def serve_prefix(M, W, torch, ctx, dev, requests, rate, slices, action):
         kind = M.MG_OUT_STATE if inp is not None else M.MG_OUT_PROPAGATOR
         act = action and kind == M.MG_OUT_STATE
         while True:
-            jid = srv.submit(H0, Hk, wl.N, wl.P, wl.t0, wl.dt, w, S, kind, inp, o, M.MG_PREC_SPLIT, slices,
+            # digits carrying 42 bits at the request's d (one more above d = 1024, where beta = 6)
+            sl = max(slices, M.mg_split_digits(wl.d, 7 * slices)[1])
+            jid = srv.submit(H0, Hk, wl.N, wl.P, wl.t0, wl.dt, w, S, kind, inp, o, M.MG_PREC_SPLIT, sl,
                              action=act)
             if jid is not None:
                 break

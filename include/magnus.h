@@ -181,6 +181,13 @@ int mg_second_order_weights(int P, double* M);
  * Errors: MG_EINVAL for a negative or non-finite norm1, d outside 1..4096,
  * NULL outputs, or precision/slices as for plans. */
 int mg_taylor_choice(double norm1, int precision, int slices, int d, int* m, int* s, double* theta);
+/* Host only: the digit width beta of the split product at dimension d (the largest
+ * beta <= 8 with 2^(2 beta - 1) 2d <= 2^24, which keeps the two leading accumulator
+ * levels exact: 7 up to d = 1024, 6 up to 4096) and, in *slices, the digit count
+ * ceil(bits / beta) clamped to 2..8 that carries at least `bits` bits (42 for the
+ * default: 6 digits up to d = 1024, 7 above).  MG_EINVAL for d outside 1..4096 or
+ * bits outside 1..64, or NULL outputs. */
+int mg_split_digits(int d, int bits, int* beta, int* slices);
 
 /* ---- plan: resident operators -------------------------------------------- */
 /* Copy H0 (d x d) and H_k (K x d x d, consecutive) into device memory owned by
@@ -382,7 +389,8 @@ typedef struct mg_job {
   const double* in;
   double* out;              /* written when the job completes; keep it valid until mg_wait returns */
   int precision, slices;    /* MG_PREC_AUTO: the latest tuning of the context's cache under
-                               gpu|d|K|out|tol (tolerance below); on a miss split, 6 digits */
+                               gpu|d|K|out|tol (tolerance below); on a miss split with the
+                               42-bit digit count of mg_split_digits (6, or 7 above d = 1024) */
   int flags;                /* MG_FLAG_HOST_PTRS: H0, Hk, samples, in and out are host memory;
                                MG_FLAG_STATE_ACTION: a state job of d >= 256 runs on the
                                action-based path (FP64; precision and slices are ignored) on one

@@ -1278,6 +1278,13 @@ int mg_taylor_choice(double norm1, int precision, int slices, int d, int* m, int
   return MG_OK;
 }
 
+int mg_split_digits(int d, int bits, int* beta, int* slices) {
+  if (!beta || !slices || d < 1 || d > 4096 || bits < 1 || bits > 64) return MG_EINVAL;
+  *beta = split_beta_for(d);
+  *slices = std::min(8, std::max(2, (bits + *beta - 1) / *beta));
+  return MG_OK;
+}
+
 int mg_plan_create(mg_ctx* ctx, mg_plan** out, int d, int K, const double* H0, const double* Hk, int precision,
                    int slices, int flags) {
   if (!ctx || !out || !H0 || d < 1 || d > 4096 || K < 0 || K > 64 || (K > 0 && !Hk)) return MG_EINVAL;
@@ -3300,8 +3307,11 @@ int mg_submit(mg_server* srv, const mg_job* job_in, uint64_t* job_id) {
         else resolved.flags &= ~MG_FLAG_STATE_ACTION;
       }
     } else {
+      // no tuning: split digits carrying 42 bits at this d (6 up to d = 1024, 7 above)
       resolved.precision = MG_PREC_SPLIT;
       resolved.slices = 6;
+      if (resolved.d >= 1 && resolved.d <= 4096) resolved.slices = std::min(8, (42 + split_beta_for(resolved.d) - 1) /
+                                                                                  split_beta_for(resolved.d));
     }
   }
   const int d = job->d, K = job->K, N = job->N, P = job->P;

@@ -101,6 +101,7 @@ SIGNATURES = {
     "mg_ctx_set_workspace_limit": (_I, [_P, ctypes.c_size_t]),
     "mg_quadrature_nodes": (_I, [_I, _P, _P]),
     "mg_taylor_choice": (_I, [_D, _I, _I, _I, _P, _P, _P]),
+    "mg_split_digits": (_I, [_I, _I, _P, _P]),
     "mg_second_order_weights": (_I, [_I, _P]),
     "mg_csr_pattern": (_I, [_I, _I, _P, _P, _P, _P, _P, _P]),
     "mg_plan_create": (_I, [_P, ctypes.POINTER(_P), _I, _I, _P, _P, _I, _I, _I]),
@@ -499,6 +500,14 @@ def mg_taylor_choice(norm1: float, precision=MG_PREC_FP64, slices=6, d=1):
     _check(load().mg_taylor_choice(norm1, precision, slices, d, ctypes.byref(m), ctypes.byref(s), ctypes.byref(th)),
            "mg_taylor_choice")
     return m.value, s.value, th.value
+
+
+def mg_split_digits(d: int, bits: int = 42):
+    """(beta, slices): the split product's digit width at dimension d and the digit count
+    that carries at least `bits` bits (host only)."""
+    b, s = ctypes.c_int(), ctypes.c_int()
+    _check(load().mg_split_digits(int(d), int(bits), ctypes.byref(b), ctypes.byref(s)), "mg_split_digits")
+    return b.value, s.value
 
 
 def mg_coefficients(ctx, N, P, K, dt, w_dev, samples, c):

@@ -215,3 +215,19 @@ def test_csr_pattern_is_the_union_with_the_diagonal(d, nops, density):
         for i in range(d):
             dense[i, col[rowptr[i]:rowptr[i + 1]]] = val[k, rowptr[i]:rowptr[i + 1]]
         assert np.array_equal(dense, ops[k])
+
+
+def test_split_digits_follow_the_exactness_bound():
+    """beta is the largest digit width with 2^(2 beta - 1) 2d <= 2^24 (the two leading
+    accumulator levels stay exact over K = 2d terms), checked by brute force; the digit
+    count is the smallest carrying the requested bits, clamped to 2..8."""
+    for d in (1, 2, 16, 30, 64, 255, 256, 729, 1024, 1025, 2048, 4096):
+        beta, L = M.mg_split_digits(d, 42)
+        ok = [b for b in range(2, 9) if 2.0 ** (2 * b - 1) * 2 * d <= 2.0 ** 24]
+        assert beta == max(ok)
+        assert L == min(8, max(2, -(-42 // beta)))
+    assert M.mg_split_digits(729)[0] == 7 and M.mg_split_digits(729)[1] == 6
+    assert M.mg_split_digits(1025) == (6, 7) and M.mg_split_digits(4096) == (6, 7)
+    for bad in ((0, 42), (4097, 42), (64, 0), (64, 65)):
+        with pytest.raises(M.MagnusError):
+            M.mg_split_digits(*bad)
