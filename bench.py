@@ -36,7 +36,7 @@ SAMPLE_INTERVALS = 128          # oracle sample (cpu_baseline) and accuracy pref
 # form, keyed by (d, digits): one ncu capture of a 32-product launch divided by 32; the bench
 # scales it to the average timed launch by the products that launch computes.  An entry is
 # valid for the kernel build it was captured from only, and is removed when the kernel changes.
-GEMM_DRAM_BYTES_PER_PRODUCT = {(729, 6): (1.269396e9 + 0.254560e9) / 32}
+GEMM_DRAM_BYTES_PER_PRODUCT = {(729, 6): (1.214349e9 + 0.255134e9) / 32}
 REFERENCE_STEP_INTERVALS = 16   # oracle intervals per step of --impl reference
 # FP64 and TF32 dense matrix-product peaks of GB300 measured by `python bench.py --peaks`
 # (torch.matmul, n = 8192, best of 10, CUDA events); the BF16 peaks come from MEASURED_PEAKS.json
@@ -62,6 +62,8 @@ def parse():
                     help="max-abs tolerance the headline plan is tuned for (mg_plan_autotune)")
     ap.add_argument("--no-tune", action="store_true",
                     help="headline: keep --precision/--slices instead of tuning for --tolerance")
+    ap.add_argument("--taylor-target", type=float, default=0.0,
+                    help="with --no-tune: the headline plan's Taylor truncation target (mg_plan_set_taylor_target)")
     ap.add_argument("--intervals", type=int, default=2000)
     ap.add_argument("--e2e-steps", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -248,6 +250,8 @@ def run_ours(args):
     plan = M.Plan(ctx, H0, Hk, prec, args.slices)
     slices = args.slices
     tuning = None
+    if args.no_tune and args.taylor_target:
+        plan.set_taylor_target(args.taylor_target)
     if prec == M.MG_PREC_SPLIT and not args.no_tune:
         # configuration (digits, Taylor scheme and truncation target, hence squarings) chosen
         # by the library's autotuner for the stated tolerance, measured before the timed region
@@ -262,6 +266,8 @@ def run_ours(args):
         if tuning is not None and tuning.get("chosen"):
             p.set_taylor(tuning["chosen"]["taylor"])
             p.set_taylor_target(tuning["chosen"]["taylor_target"])
+        elif args.no_tune and args.taylor_target:
+            p.set_taylor_target(args.taylor_target)
 
     def step():
         plan.set_controls(N, wl.P, wl.t0, wl.dt, w, samples)
@@ -356,6 +362,7 @@ def run_ours(args):
                        "precision": "split" if prec == M.MG_PREC_SPLIT else "fp64",
                        "slices": slices if prec == M.MG_PREC_SPLIT else None,
                        "tuning": tuning,
+                       "taylor_target": args.taylor_target if args.no_tune and args.taylor_target else None,
                        "l2": "256 MiB buffer written before every timed step",
                        "parallelism": "independent replica per GPU"},
             "roofline": roof,
@@ -407,7 +414,7 @@ def run_ours(args):
     if result is not None and ws == 1 and not args.no_serving:
         # the served stream beside the headline: the first requests of the Poisson(200/s)
         # mixed stream at the stated rate (an overload) and at half the capacity that run
-        # measured; state requests of d >= 256 on the action path, the rest split 6 digits.
+        # measured; state requests of d >= 256 on the action path, the rest split (6 digits, 7 above d = 1024).
         # A failure here is reported in the line, not raised: the headline stands.
         try:
             with torch.cuda.stream(stream):
@@ -419,7 +426,7 @@ def run_ours(args):
             result["serving"] = {
                 "workload": f"first {over['requests']} requests of the Poisson(200/s) mixed stream "
                             f"(d up to {over['d_max']}, {over['intervals_total']} intervals, state or full U)",
-                "state_requests": "action path (FP64) from d = 256, split 6 digits below",
+                "state_requests": "action path (FP64) from d = 256; the rest split, 6 digits (7 above d = 1024)",
                 "at_stated_rate": {k: over[k] for k in keys},
                 "capacity_requests_per_s": cap,
                 "at_half_capacity": {k: half[k] for k in keys},
