@@ -320,6 +320,132 @@ build_omega_df_kernel(int N, int d, int K, double dt, const double* __restrict__
   }
 }
 
+// The split path's builder for up to 8 operators (K <= 7), in two kernels with the
+// arithmetic of build_omega_df_kernel (bit-identical Hbar_n and norms):
+//
+// omega_tile_df_kernel: one CTA per 16 x 32 tile of elements and OT_TZ intervals.  The
+// tile's operator entries are split into FP32 pairs once per CTA and kept in registers
+// (two elements per thread), so an entry passes GB300's FP64 pipe once per OT_TZ
+// intervals instead of once per 8; every interval's tile is then formed on the FP32
+// pipe and stored as coalesced 16-byte rows.  Many CTAs at every dimension (the
+// single-kernel form had one CTA per 32 columns and 8 intervals: a quarter of a wave
+// at small d).
+//
+// omega_norm_df_kernel: the norm bound from the stored values, in the single-kernel
+// form's order (per column, rows i = w mod 8 summed in double, then the eight partial
+// sums in order, then the max over columns as an integer atomic).
+constexpr int OT_ROWS = 16, OT_COLS = 32, OT_TZ = 128, OT_KMAX = 8;
+
+template <int KP1>
+__global__ void __launch_bounds__(256)
+omega_tile_df_kernel(int N, int d, double dt, const double* __restrict__ H0, const double* __restrict__ Hk,
+                     const double* __restrict__ c, const double* __restrict__ tr, float4* __restrict__ omega,
+                     double* __restrict__ tau_out, int shift) {
+  constexpr int K = KP1 - 1;
+  __shared__ df32 cs[OT_TZ][K > 0 ? K : 1];
+  __shared__ df32 mtau[OT_TZ];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int j = blockIdx.x * OT_COLS + lane;
+  const int n0 = blockIdx.z * OT_TZ;
+  const int nb = min(OT_TZ, N - n0);
+  for (int t = threadIdx.x; t < OT_TZ * K; t += blockDim.x) {
+    const int b = t / K, k = t % K;
+    cs[b][k] = df_from_double(b < nb ? c[(long long)(n0 + b) * K + k] : 0.0);
+  }
+  if (threadIdx.x < OT_TZ) {
+    const int b = threadIdx.x;
+    double t = 0.0;
+    if (shift && b < nb) {
+      t = dt * tr[0];
+      for (int k = 0; k < K; ++k) t += c[(long long)(n0 + b) * K + k] * tr[1 + k];
+      t /= d;
+    }
+    mtau[b] = df_from_double(-t);
+    if (b < nb && blockIdx.x == 0 && blockIdx.y == 0 && tau_out) tau_out[n0 + b] = t;
+  }
+  // the thread's two elements: rows warp and warp + 8 of the tile, column j
+  const df32 dtd = df_from_double(dt);
+  const long long dd = (long long)d * d;
+  df32 r0[2], q0[2], hr[2][K > 0 ? K : 1], hq[2][K > 0 ? K : 1];
+  unsigned nz[2] = {0u, 0u};
+  int row[2];
+#pragma unroll
+  for (int e = 0; e < 2; ++e) {
+    row[e] = blockIdx.y * OT_ROWS + warp + 8 * e;
+    r0[e] = q0[e] = df32{0.f, 0.f};
+    if (row[e] < d && j < d) {
+      const long long off = 2 * ((long long)row[e] * d + j);
+      const double2 h0 = *reinterpret_cast<const double2*>(H0 + off);
+      r0[e] = df_mul(df_from_double(h0.x), dtd);
+      q0[e] = df_mul(df_from_double(h0.y), dtd);
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        const double2 hk = *reinterpret_cast<const double2*>(Hk + 2 * dd * k + off);
+        hr[e][k] = df_from_double(hk.x);
+        hq[e][k] = df_from_double(hk.y);
+        if (((__double_as_longlong(hk.x) | __double_as_longlong(hk.y)) << 1) != 0) nz[e] |= 1u << k;   // sparse H_k
+      }
+    }
+  }
+  __syncthreads();
+  for (int b = 0; b < nb; ++b) {
+    float4* ob = omega + (long long)(n0 + b) * dd;
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      if (row[e] >= d || j >= d) continue;
+      df32 re = r0[e], im = q0[e];
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        if (nz[e] & (1u << k)) {
+          const df32 ck = cs[b][k];
+          re = dfx_add(re, df_mul(hr[e][k], ck));
+          im = dfx_add(im, df_mul(hq[e][k], ck));
+        }
+      }
+      if (row[e] == j) re = df_add(re, mtau[b]);
+      ob[(long long)row[e] * d + j] = make_float4(re.hi, re.lo, im.hi, im.lo);
+    }
+  }
+}
+
+// grid (ceil(d / 32), N), block 256; norm_bits zeroed before
+__global__ void __launch_bounds__(256)
+omega_norm_df_kernel(int d, const float4* __restrict__ omega, unsigned long long* __restrict__ norm_bits) {
+  __shared__ double part[8][32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int j = blockIdx.x * 32 + lane;
+  const int n = blockIdx.y;
+  const float4* ob = omega + (long long)n * d * d;
+  double s = 0.0;
+  if (j < d) {
+    for (int i = warp; i < d; i += 8) {
+      const float4 v = ob[(long long)i * d + j];
+      s += (double)magnitude_upper_f(v.x, v.z);
+    }
+  }
+  part[warp][lane] = s;
+  __syncthreads();
+  if (warp == 0) {
+    double v = 0.0;
+    for (int w = 0; w < 8; ++w) v += part[w][lane];
+    if (j >= d) v = 0.0;
+    if (!(v <= 1.0e300)) v = __longlong_as_double(0x7ff0000000000000LL);   // NaN/Inf -> +Inf before the max
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if (lane == 0) atomicMax(norm_bits + n, nonneg_bits(v));
+  }
+}
+
+template <int KP1>
+static int launch_omega_tiles(int N, int d, double dt, const double* H0, const double* Hk, const double* c,
+                              const double* tr, float4* omega, double* tau, unsigned long long* bits, int shift,
+                              cudaStream_t s) {
+  dim3 grid(ceil_div(d, OT_COLS), ceil_div(d, OT_ROWS), ceil_div(N, OT_TZ));
+  omega_tile_df_kernel<KP1><<<grid, 256, 0, s>>>(N, d, dt, H0, Hk, c, tr, omega, tau, shift);
+  MG_TRY(check_launch("omega_tile_df_kernel"));
+  omega_norm_df_kernel<<<dim3(ceil_div(d, 32), N), 256, 0, s>>>(d, omega, bits);
+  return check_launch("omega_norm_df_kernel");
+}
+
 __global__ void bits_to_double_kernel(int n, const unsigned long long* bits, double* out) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) out[i] = __longlong_as_double((long long)bits[i]);
@@ -337,7 +463,20 @@ int launch_build_omega(int N, int d, int K, double dt, const double* H0, const d
   MG_CUDA_TRY(cudaMemsetAsync(bits, 0, sizeof(unsigned long long) * N, s));
   dim3 grid(ceil_div(d, OMEGA_COLS), ceil_div(N, OMEGA_NB));
   size_t smem = sizeof(double) * (OMEGA_NB * (K > 0 ? K : 1) + OMEGA_NB + OMEGA_WARPS * OMEGA_NB * 32);
-  if (out_df32) {
+  if (out_df32 && K + 1 <= OT_KMAX && N <= 65535) {   // N: grid y of the norm kernel
+    if (!write_shifted) return MG_EINVAL;
+    float4* o4 = reinterpret_cast<float4*>(omega);
+    switch (K + 1) {
+      case 1: MG_TRY(launch_omega_tiles<1>(N, d, dt, H0, Hk, c, tr, o4, tau, bits, shift, s)); break;
+      case 2: MG_TRY(launch_omega_tiles<2>(N, d, dt, H0, Hk, c, tr, o4, tau, bits, shift, s)); break;
+      case 3: MG_TRY(launch_omega_tiles<3>(N, d, dt, H0, Hk, c, tr, o4, tau, bits, shift, s)); break;
+      case 4: MG_TRY(launch_omega_tiles<4>(N, d, dt, H0, Hk, c, tr, o4, tau, bits, shift, s)); break;
+      case 5: MG_TRY(launch_omega_tiles<5>(N, d, dt, H0, Hk, c, tr, o4, tau, bits, shift, s)); break;
+      case 6: MG_TRY(launch_omega_tiles<6>(N, d, dt, H0, Hk, c, tr, o4, tau, bits, shift, s)); break;
+      case 7: MG_TRY(launch_omega_tiles<7>(N, d, dt, H0, Hk, c, tr, o4, tau, bits, shift, s)); break;
+      default: MG_TRY(launch_omega_tiles<8>(N, d, dt, H0, Hk, c, tr, o4, tau, bits, shift, s)); break;
+    }
+  } else if (out_df32) {
     if (!write_shifted) return MG_EINVAL;
     MG_TRY(ensure_smem_limit(reinterpret_cast<const void*>(build_omega_df_kernel), (int)smem));
     build_omega_df_kernel<<<grid, 256, smem, s>>>(N, d, K, dt, H0, Hk, c, tr, reinterpret_cast<float4*>(omega), tau,
