@@ -607,6 +607,11 @@ def run_config(args):
     dev = torch.device("cuda", 0)
     stream = torch.cuda.Stream(device=dev)
     ctx = M.Context(0, stream)
+    ctx.set_stage_k(args.stage_k)
+    if args.digit_pairs is not None:
+        ctx.set_digit_pairs(args.digit_pairs)
+    if args.cta_pairs is not None:
+        ctx.set_cta_pairs(args.cta_pairs)
     cores = len(os.sched_getaffinity(0))
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     warm = max(3, args.warmup)

@@ -323,36 +323,37 @@ build_omega_df_kernel(int N, int d, int K, double dt, const double* __restrict__
 // The split path's builder for up to 8 operators (K <= 7), in two kernels with the
 // arithmetic of build_omega_df_kernel (bit-identical Hbar_n and norms):
 //
-// omega_tile_df_kernel: one CTA per 16 x 32 tile of elements and OT_TZ intervals.  The
-// tile's operator entries are split into FP32 pairs once per CTA and kept in registers
-// (two elements per thread), so an entry passes GB300's FP64 pipe once per OT_TZ
-// intervals instead of once per 8; every interval's tile is then formed on the FP32
-// pipe and stored as coalesced 16-byte rows.  Many CTAs at every dimension (the
-// single-kernel form had one CTA per 32 columns and 8 intervals: a quarter of a wave
-// at small d).
+// omega_tile_df_kernel: one CTA per 8 x 32 tile of elements (one per thread) and tz
+// intervals.  The thread's operator entries are split into FP32 pairs once and kept in
+// registers, so an entry passes GB300's FP64 pipe once per tz intervals (up to 128)
+// instead of once per 8; every interval's element is then formed on the FP32 pipe and
+// stored in coalesced 16-byte rows.  tz is chosen per launch so that the grid has about
+// eight CTAs per SM at every dimension (the single-kernel form had one CTA per 32
+// columns and 8 intervals: a quarter of a wave at small d).
 //
 // omega_norm_df_kernel: the norm bound from the stored values, in the single-kernel
 // form's order (per column, rows i = w mod 8 summed in double, then the eight partial
 // sums in order, then the max over columns as an integer atomic).
-constexpr int OT_ROWS = 16, OT_COLS = 32, OT_TZ = 128, OT_KMAX = 8;
+constexpr int OT_ROWS = 8, OT_COLS = 32, OT_TZ = 128, OT_KMAX = 8;
 
 template <int KP1>
 __global__ void __launch_bounds__(256)
 omega_tile_df_kernel(int N, int d, double dt, const double* __restrict__ H0, const double* __restrict__ Hk,
                      const double* __restrict__ c, const double* __restrict__ tr, float4* __restrict__ omega,
-                     double* __restrict__ tau_out, int shift) {
+                     double* __restrict__ tau_out, int shift, int tz) {
   constexpr int K = KP1 - 1;
   __shared__ df32 cs[OT_TZ][K > 0 ? K : 1];
   __shared__ df32 mtau[OT_TZ];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int j = blockIdx.x * OT_COLS + lane;
-  const int n0 = blockIdx.z * OT_TZ;
-  const int nb = min(OT_TZ, N - n0);
-  for (int t = threadIdx.x; t < OT_TZ * K; t += blockDim.x) {
+  const int row = blockIdx.y * OT_ROWS + warp;
+  const int n0 = blockIdx.z * tz;
+  const int nb = min(tz, N - n0);
+  for (int t = threadIdx.x; t < tz * K; t += blockDim.x) {
     const int b = t / K, k = t % K;
     cs[b][k] = df_from_double(b < nb ? c[(long long)(n0 + b) * K + k] : 0.0);
   }
-  if (threadIdx.x < OT_TZ) {
+  if (threadIdx.x < tz) {
     const int b = threadIdx.x;
     double t = 0.0;
     if (shift && b < nb) {
@@ -363,48 +364,40 @@ omega_tile_df_kernel(int N, int d, double dt, const double* __restrict__ H0, con
     mtau[b] = df_from_double(-t);
     if (b < nb && blockIdx.x == 0 && blockIdx.y == 0 && tau_out) tau_out[n0 + b] = t;
   }
-  // the thread's two elements: rows warp and warp + 8 of the tile, column j
+  // the thread's element (row, j): its operator entries as FP32 pairs
   const df32 dtd = df_from_double(dt);
   const long long dd = (long long)d * d;
-  df32 r0[2], q0[2], hr[2][K > 0 ? K : 1], hq[2][K > 0 ? K : 1];
-  unsigned nz[2] = {0u, 0u};
-  int row[2];
+  const bool in = row < d && j < d;
+  df32 r0{0.f, 0.f}, q0{0.f, 0.f}, hr[K > 0 ? K : 1], hq[K > 0 ? K : 1];
+  unsigned nz = 0u;
+  if (in) {
+    const long long off = 2 * ((long long)row * d + j);
+    const double2 h0 = *reinterpret_cast<const double2*>(H0 + off);
+    r0 = df_mul(df_from_double(h0.x), dtd);
+    q0 = df_mul(df_from_double(h0.y), dtd);
 #pragma unroll
-  for (int e = 0; e < 2; ++e) {
-    row[e] = blockIdx.y * OT_ROWS + warp + 8 * e;
-    r0[e] = q0[e] = df32{0.f, 0.f};
-    if (row[e] < d && j < d) {
-      const long long off = 2 * ((long long)row[e] * d + j);
-      const double2 h0 = *reinterpret_cast<const double2*>(H0 + off);
-      r0[e] = df_mul(df_from_double(h0.x), dtd);
-      q0[e] = df_mul(df_from_double(h0.y), dtd);
-#pragma unroll
-      for (int k = 0; k < K; ++k) {
-        const double2 hk = *reinterpret_cast<const double2*>(Hk + 2 * dd * k + off);
-        hr[e][k] = df_from_double(hk.x);
-        hq[e][k] = df_from_double(hk.y);
-        if (((__double_as_longlong(hk.x) | __double_as_longlong(hk.y)) << 1) != 0) nz[e] |= 1u << k;   // sparse H_k
-      }
+    for (int k = 0; k < K; ++k) {
+      const double2 hk = *reinterpret_cast<const double2*>(Hk + 2 * dd * k + off);
+      hr[k] = df_from_double(hk.x);
+      hq[k] = df_from_double(hk.y);
+      if (((__double_as_longlong(hk.x) | __double_as_longlong(hk.y)) << 1) != 0) nz |= 1u << k;   // sparse H_k
     }
   }
   __syncthreads();
+  if (!in) return;
+  float4* o = omega + (long long)n0 * dd + (long long)row * d + j;
   for (int b = 0; b < nb; ++b) {
-    float4* ob = omega + (long long)(n0 + b) * dd;
+    df32 re = r0, im = q0;
 #pragma unroll
-    for (int e = 0; e < 2; ++e) {
-      if (row[e] >= d || j >= d) continue;
-      df32 re = r0[e], im = q0[e];
-#pragma unroll
-      for (int k = 0; k < K; ++k) {
-        if (nz[e] & (1u << k)) {
-          const df32 ck = cs[b][k];
-          re = dfx_add(re, df_mul(hr[e][k], ck));
-          im = dfx_add(im, df_mul(hq[e][k], ck));
-        }
+    for (int k = 0; k < K; ++k) {
+      if (nz & (1u << k)) {
+        const df32 ck = cs[b][k];
+        re = dfx_add(re, df_mul(hr[k], ck));
+        im = dfx_add(im, df_mul(hq[k], ck));
       }
-      if (row[e] == j) re = df_add(re, mtau[b]);
-      ob[(long long)row[e] * d + j] = make_float4(re.hi, re.lo, im.hi, im.lo);
     }
+    if (row == j) re = df_add(re, mtau[b]);
+    o[b * dd] = make_float4(re.hi, re.lo, im.hi, im.lo);
   }
 }
 
@@ -439,8 +432,12 @@ template <int KP1>
 static int launch_omega_tiles(int N, int d, double dt, const double* H0, const double* Hk, const double* c,
                               const double* tr, float4* omega, double* tau, unsigned long long* bits, int shift,
                               cudaStream_t s) {
-  dim3 grid(ceil_div(d, OT_COLS), ceil_div(d, OT_ROWS), ceil_div(N, OT_TZ));
-  omega_tile_df_kernel<KP1><<<grid, 256, 0, s>>>(N, d, dt, H0, Hk, c, tr, omega, tau, shift);
+  // intervals per CTA: about eight CTAs per SM (152 SMs), at most OT_TZ
+  const long long tiles = (long long)ceil_div(d, OT_COLS) * ceil_div(d, OT_ROWS);
+  const long long want = 8LL * 152;
+  int tz = (int)std::min<long long>(OT_TZ, std::max<long long>(1, (tiles * N + want - 1) / want));
+  dim3 grid(ceil_div(d, OT_COLS), ceil_div(d, OT_ROWS), ceil_div(N, tz));
+  omega_tile_df_kernel<KP1><<<grid, 256, 0, s>>>(N, d, dt, H0, Hk, c, tr, omega, tau, shift, tz);
   MG_TRY(check_launch("omega_tile_df_kernel"));
   omega_norm_df_kernel<<<dim3(ceil_div(d, 32), N), 256, 0, s>>>(d, omega, bits);
   return check_launch("omega_norm_df_kernel");

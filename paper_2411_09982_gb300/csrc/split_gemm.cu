@@ -1090,10 +1090,14 @@ static int launch_split_gemm_L(const SplitGeom& g, int batch, const __nv_bfloat1
   if constexpr (L % 2 == 0)
     if (paired_layout(g, ctl))
       return launch_split_gemm_LB<L, 16, true>(g, batch, Ad, ea, Bd, eb, C, sC, epi, status, ctl, s);
-  // pairs pay where many digit products per stage make each SM's shared-memory port the
-  // limit (measured: +3% at d = 729 and +7% at d = 4096 with 6 digits, 2-4% slower with 2-4)
-  const bool pair = ctl.cta_pairs > 0 || (ctl.cta_pairs < 0 && L >= 5);
-  if (pair && g.Mp / SG_BM >= 2)
+  // By default pairs run from 5 digits (measured at 6: +3% at d = 729, +7% at d = 4096,
+  // +6% at d = 256; with 2-4 digits 2-4% slower) where the row tiles pair up evenly from
+  // d = 256 on, or are 7 or more (an odd count leaves the last pair's second CTA
+  // multiplying zeros: -19% at d = 300, three tiles).
+  const int mtiles = g.Mp / SG_BM;
+  const bool shape_ok = (mtiles % 2 == 0) ? g.d >= 256 : mtiles >= 7;
+  const bool pair = ctl.cta_pairs > 0 || (ctl.cta_pairs < 0 && L >= 5 && shape_ok);
+  if (pair && mtiles >= 2)
     return launch_split_gemm_LC<L, 2>(g, batch, Ad, ea, Bd, eb, C, sC, epi, status, ctl, s);
   return launch_split_gemm_LC<L, 1>(g, batch, Ad, ea, Bd, eb, C, sC, epi, status, ctl, s);
 }
