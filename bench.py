@@ -54,7 +54,7 @@ def parse():
     ap.add_argument("--slices", type=int, default=6)
     ap.add_argument("--stage-k", type=int, default=32, choices=[16, 32, 64],
                     help="K per pipeline stage of the split product (mg_ctx_set_stage_k)")
-    ap.add_argument("--digit-pairs", type=int, default=None, choices=[0, 1],
+    ap.add_argument("--digit-pairs", type=int, default=None, choices=[0, 1, 2],
                     help="paired digit layout of the split product (mg_ctx_set_digit_pairs)")
     ap.add_argument("--cta-pairs", type=int, default=None, choices=[0, 1],
                     help="split products on CTA pairs (mg_ctx_set_cta_pairs)")

@@ -529,13 +529,18 @@ int mg_ctx_set_stage_k(mg_ctx* ctx, int stage_k);
  * values of a row, 16 of the even digit, then 16 of the odd one), so each 64-byte row
  * of a pipeline stage 16 deep in K carries two digits; the stage then takes half the
  * shared memory of the default 32-deep stage and twice as many stages are in flight.
- * It replaces mg_ctx_set_stage_k's choice for even slices; odd slice counts keep the
- * digit-major layout.  The result is bit-identical either way.  on = 0 (the default):
- * one plane per digit.  MG_EINVAL for other values.  A change applies to products
+ * on = 2 keeps that memory layout but reads it in 32-deep stages, two 16-value blocks
+ * per row: 128-byte rows (SWIZZLE_128B), the shared memory of the default stage, half
+ * its rows (where two such stages fit, else as on = 1).  Either replaces
+ * mg_ctx_set_stage_k's choice for even slices and combines with CTA pairs; odd slice
+ * counts keep the digit-major layout.  The result is bit-identical either way.  on = 0
+ * (the default): one plane per digit.  MG_EINVAL for other values.  A change applies to products
  * issued afterwards (a captured batch graph keeps the layout it was captured with).
- * Measured on GB300 (algorithmic TFLOP/s, 32 products): d = 729, 6 slices 76.5 paired
- * vs 78.7 digit-major; d = 700, 4 slices 124 vs 142; d = 512, 8 slices 53.0 vs 35.2
- * (52.7 with digit-major 16-deep stages, which 8 slices now take by default). */
+ * Measured on GB300 (algorithmic TFLOP/s, 32 products, single CTAs): on = 1: d = 729,
+ * 6 slices 76.5 paired vs 78.7 digit-major; d = 700, 4 slices 124 vs 142; d = 512,
+ * 8 slices 53.0 vs 35.2 (52.7 with digit-major 16-deep stages, which 8 slices take by
+ * default).  on = 2: d = 729 78.8 vs 77.0, d = 4096 100.1 vs 94.9; with CTA pairs
+ * (the default from 5 slices) within 0.4% of the digit-major layout. */
 int mg_ctx_set_digit_pairs(mg_ctx* ctx, int on);
 /* Tensor-core product (MG_PREC_SPLIT) on CTA pairs: on = 1 runs each product tile of
  * 256 rows x 64 complex columns as one M = 256 tcgen05 product of two CTAs on two SMs

@@ -1180,7 +1180,7 @@ int mg_ctx_set_stage_k(mg_ctx* ctx, int stage_k) {
 }
 
 int mg_ctx_set_digit_pairs(mg_ctx* ctx, int on) {
-  if (!ctx || (on != 0 && on != 1)) return MG_EINVAL;
+  if (!ctx || on < 0 || on > 2) return MG_EINVAL;
   ctx->digit_pairs = on;
   return MG_OK;
 }

@@ -146,8 +146,9 @@ struct SplitCtl {
   const int* item_sq = nullptr;  // per-item squaring counts (device) or null: every item active
   int sq_step = 0;               // with item_sq: only items with item_sq[b] > sq_step are computed
   int stage_k = 32;              // K per pipeline stage of the product: 16, 32 or 64
-  int pairs = 0;                 // paired digit layout (even digit counts; 16-deep stages): slicers and product
-                                 // of one set of digit buffers must agree on it
+  int pairs = 0;                 // paired digit layout (even digit counts; 1: 16-deep stages of 64-byte rows,
+                                 // 2: 32-deep stages of 128-byte rows): slicers and product of one set of
+                                 // digit buffers must agree on it (the memory layout is the same for 1 and 2)
   int cta_pairs = -1;            // M = 256 products on CTA pairs (tcgen05 cta_group::2) where d > 128:
                                  // 1 on, 0 off, -1 for five or more digits
 };

@@ -541,6 +541,11 @@ template <int BK>
 __device__ __forceinline__ uint64_t kmajor_desc(uint32_t saddr) {
   return BK == 64 ? sw128_kmajor_desc(saddr) : (BK == 32 ? sw64_kmajor_desc(saddr) : sw32_kmajor_desc(saddr));
 }
+// the paired layout's rows hold two digits: 64 bytes at BK = 16, 128 bytes at BK = 32
+template <int BK>
+__device__ __forceinline__ uint64_t pair_desc(uint32_t saddr) {
+  return BK == 32 ? sw128_kmajor_desc(saddr) : sw64_kmajor_desc(saddr);
+}
 
 // Instruction descriptor: kind::f16, A = B = BF16, D = F32, both K-major, M = 128, N = 128.
 constexpr uint32_t kIdescBf16 = (1u << 4) | (1u << 7) | (1u << 10) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
@@ -605,7 +610,6 @@ split_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
                   int* __restrict__ status, SplitCtl ctl) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  static_assert(CTAS == 1 || (CTAS == 2 && !PAIRS), "the CTA pair takes the digit-major layout");
   constexpr int TILE_BYTES = StageK<BK>::tile_bytes;
   constexpr int B_TILE_BYTES = TILE_BYTES / CTAS;   // one CTA's share of a digit's B tile
   constexpr int STAGE_BYTES = L * (TILE_BYTES + B_TILE_BYTES);   // loaded into this CTA per stage
@@ -692,8 +696,14 @@ split_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
           // rank 0 expects the bytes of both CTAs; the copies of both signal its barrier
           if (leader) mbar_expect_tx(&full[s], 2 * STAGE_BYTES);
           const uint32_t bar = cluster_addr(&full[s], 0);
-          tma_load_4d_pair(st, &tmA, bar, kb * BK, mt * SG_BM, 0, b);
-          tma_load_5d_pair(st + L * TILE_BYTES, &tmB, bar, kbb * BK, nt * SG_BNC, plane0 + (int)crank, 0, b);
+          if constexpr (PAIRS) {
+            tma_load_4d_pair(st, &tmA, bar, 0, kb, mt * SG_BM, b * (L / 2));
+            tma_load_5d_pair(st + L * TILE_BYTES, &tmB, bar, 0, kbb, nt * SG_BNC, plane0 + (int)crank,
+                             b * (L / 2));
+          } else {
+            tma_load_4d_pair(st, &tmA, bar, kb * BK, mt * SG_BM, 0, b);
+            tma_load_5d_pair(st + L * TILE_BYTES, &tmB, bar, kbb * BK, nt * SG_BNC, plane0 + (int)crank, 0, b);
+          }
         } else if constexpr (PAIRS) {
           mbar_expect_tx(&full[s], STAGE_BYTES);
           tma_load_4d(st, &tmA, &full[s], 0, kb, mt * SG_BM, b * (L / 2));
@@ -747,8 +757,10 @@ split_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
               first[g] = false;
               uint64_t ad, bd;
               if constexpr (PAIRS) {
-                ad = sw64_kmajor_desc(a0 + (sa >> 1) * 2 * TILE_BYTES + (sa & 1) * SG_MMA_K * 2);
-                bd = sw64_kmajor_desc(b0 + (sb >> 1) * 2 * TILE_BYTES + (sb & 1) * SG_MMA_K * 2);
+                // digit s: tile s / 2 (two digits per row), 16-value block kk, the odd digit's
+                // 16 values after the even one's
+                ad = pair_desc<BK>(a0 + (sa >> 1) * 2 * TILE_BYTES + kk * 4 * SG_MMA_K + (sa & 1) * SG_MMA_K * 2);
+                bd = pair_desc<BK>(b0 + (sb >> 1) * 2 * B_TILE_BYTES + kk * 4 * SG_MMA_K + (sb & 1) * SG_MMA_K * 2);
               } else {
                 ad = kmajor_desc<BK>(a0 + sa * TILE_BYTES + kk * SG_MMA_K * 2);
                 bd = kmajor_desc<BK>(b0 + sb * B_TILE_BYTES + kk * SG_MMA_K * 2);
@@ -973,20 +985,24 @@ static int make_digit_map(CUtensorMap* map, const void* base, int Kp, int rows, 
   return MG_OK;
 }
 
-// Paired layout (even L): A dims {32, Kp / 16 blocks, d valid rows, batch * L / 2 digit
-// pairs}, box {32, 1, 128, L / 2}; B dims {32, Kh / 16, d valid rows, 3 planes,
-// batch * L / 2}, box {32, 1, 64, 2, L / 2}.  64-byte rows, SWIZZLE_64B.
+// Paired layout (even L), stages bk = 16 or 32 deep: the two digits' values of bk
+// consecutive k form one row of 4 bk bytes (the layout keeps 16-value blocks of the even
+// and the odd digit in turn, so 32-deep stages read two blocks).  A dims {2 bk, Kp / bk,
+// d valid rows, batch * L / 2 digit pairs}, box {2 bk, 1, 128, L / 2}; B dims {2 bk,
+// Kh / bk, d valid rows, 3 planes, batch * L / 2}, box {2 bk, 1, 64, planes, L / 2}.
+// SWIZZLE_64B for 64-byte rows, SWIZZLE_128B for 128-byte rows.
 static int make_pair_maps(CUtensorMap* ma, CUtensorMap* mb, const SplitGeom& g, const void* Ad, const void* Bd,
-                          int batch) {
+                          int batch, int bk, int b_planes) {
   MG_TRY(get_encoder());
   const int L = g.L, Kp = g.Kp, Kh = g.Kh(), rows = g.Np / 2;
   const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+  const CUtensorMapSwizzle sw = bk == 32 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B;
   {
-    cuuint64_t dims[4] = {32, (cuuint64_t)Kp / 16, (cuuint64_t)g.d, (cuuint64_t)batch * (L / 2)};
-    cuuint64_t strides[3] = {64, (cuuint64_t)Kp * 4, (cuuint64_t)g.Mp * Kp * 4};
-    cuuint32_t box[4] = {32, 1, (cuuint32_t)SG_BM, (cuuint32_t)(L / 2)};
+    cuuint64_t dims[4] = {(cuuint64_t)(2 * bk), (cuuint64_t)(Kp / bk), (cuuint64_t)g.d, (cuuint64_t)batch * (L / 2)};
+    cuuint64_t strides[3] = {(cuuint64_t)(4 * bk), (cuuint64_t)Kp * 4, (cuuint64_t)g.Mp * Kp * 4};
+    cuuint32_t box[4] = {(cuuint32_t)(2 * bk), 1, (cuuint32_t)SG_BM, (cuuint32_t)(L / 2)};
     CUresult r = g_encode(ma, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(Ad), dims, strides, box, estr,
-                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, sw,
                           CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) {
       set_last_message("cuTensorMapEncodeTiled failed (%d): paired A, Kp=%d L=%d batch=%d", (int)r, Kp, L, batch);
@@ -994,11 +1010,13 @@ static int make_pair_maps(CUtensorMap* ma, CUtensorMap* mb, const SplitGeom& g, 
     }
   }
   {
-    cuuint64_t dims[5] = {32, (cuuint64_t)Kh / 16, (cuuint64_t)g.d, 3, (cuuint64_t)batch * (L / 2)};
-    cuuint64_t strides[4] = {64, (cuuint64_t)Kh * 4, (cuuint64_t)rows * Kh * 4, (cuuint64_t)3 * rows * Kh * 4};
-    cuuint32_t box[5] = {32, 1, (cuuint32_t)SG_BNC, 2, (cuuint32_t)(L / 2)};
+    cuuint64_t dims[5] = {(cuuint64_t)(2 * bk), (cuuint64_t)(Kh / bk), (cuuint64_t)g.d, 3,
+                          (cuuint64_t)batch * (L / 2)};
+    cuuint64_t strides[4] = {(cuuint64_t)(4 * bk), (cuuint64_t)Kh * 4, (cuuint64_t)rows * Kh * 4,
+                             (cuuint64_t)3 * rows * Kh * 4};
+    cuuint32_t box[5] = {(cuuint32_t)(2 * bk), 1, (cuuint32_t)SG_BNC, (cuuint32_t)b_planes, (cuuint32_t)(L / 2)};
     CUresult r = g_encode(mb, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<void*>(Bd), dims, strides, box, estr,
-                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, sw,
                           CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) {
       set_last_message("cuTensorMapEncodeTiled failed (%d): paired B, Kh=%d L=%d batch=%d", (int)r, Kh, L, batch);
@@ -1024,11 +1042,11 @@ template <int L, int BK, bool PAIRS = false, int CTAS = 1>
 static int launch_split_gemm_LB(const SplitGeom& g, int batch, const __nv_bfloat16* Ad, const int* ea,
                                 const __nv_bfloat16* Bd, const int* eb, double* C, long long sC,
                                 const SplitEpi& epi, int* status, const SplitCtl& ctl, cudaStream_t s) {
-  static_assert(!PAIRS || (BK == 16 && L % 2 == 0), "the paired layout has 16-deep stages and even L");
+  static_assert(!PAIRS || ((BK == 16 || BK == 32) && L % 2 == 0), "the paired layout: 16- or 32-deep stages, even L");
   constexpr int STAGES = stages_for<L, BK, CTAS>();
   CUtensorMap ma, mb;
   if constexpr (PAIRS) {
-    MG_TRY(make_pair_maps(&ma, &mb, g, Ad, Bd, batch));
+    MG_TRY(make_pair_maps(&ma, &mb, g, Ad, Bd, batch, BK, CTAS == 2 ? 1 : 2));
   } else {
     MG_TRY(make_digit_map(&ma, Ad, g.Kp, g.Mp, g.d, L, batch, BK));
     // a CTA of a pair loads one of the two planes of the stage
@@ -1087,18 +1105,27 @@ template <int L>
 static int launch_split_gemm_L(const SplitGeom& g, int batch, const __nv_bfloat16* Ad, const int* ea,
                                const __nv_bfloat16* Bd, const int* eb, double* C, long long sC,
                                const SplitEpi& epi, int* status, const SplitCtl& ctl, cudaStream_t s) {
-  if constexpr (L % 2 == 0)
-    if (paired_layout(g, ctl))
-      return launch_split_gemm_LB<L, 16, true>(g, batch, Ad, ea, Bd, eb, C, sC, epi, status, ctl, s);
   // By default pairs run from 5 digits (measured at 6: +3% at d = 729, +7% at d = 4096,
   // +6% at d = 256; with 2-4 digits 2-4% slower) where the row tiles pair up evenly from
   // d = 256 on, or are 7 or more (an odd count leaves the last pair's second CTA
   // multiplying zeros: -19% at d = 300, three tiles).
   const int mtiles = g.Mp / SG_BM;
   const bool shape_ok = (mtiles % 2 == 0) ? g.d >= 256 : mtiles >= 7;
-  const bool pair = ctl.cta_pairs > 0 || (ctl.cta_pairs < 0 && L >= 5 && shape_ok);
-  if (pair && mtiles >= 2)
-    return launch_split_gemm_LC<L, 2>(g, batch, Ad, ea, Bd, eb, C, sC, epi, status, ctl, s);
+  const bool pair = mtiles >= 2 && (ctl.cta_pairs > 0 || (ctl.cta_pairs < 0 && L >= 5 && shape_ok));
+  if constexpr (L % 2 == 0) {
+    if (paired_layout(g, ctl)) {
+      // pairs = 2: 32-deep stages of 128-byte rows where two stages fit, else 16-deep
+      if (ctl.pairs == 2) {
+        if constexpr (stages_for<L, 32, 2>() >= 2)
+          if (pair) return launch_split_gemm_LB<L, 32, true, 2>(g, batch, Ad, ea, Bd, eb, C, sC, epi, status, ctl, s);
+        if constexpr (stages_for<L, 32, 1>() >= 2)
+          if (!pair) return launch_split_gemm_LB<L, 32, true, 1>(g, batch, Ad, ea, Bd, eb, C, sC, epi, status, ctl, s);
+      }
+      if (pair) return launch_split_gemm_LB<L, 16, true, 2>(g, batch, Ad, ea, Bd, eb, C, sC, epi, status, ctl, s);
+      return launch_split_gemm_LB<L, 16, true, 1>(g, batch, Ad, ea, Bd, eb, C, sC, epi, status, ctl, s);
+    }
+  }
+  if (pair) return launch_split_gemm_LC<L, 2>(g, batch, Ad, ea, Bd, eb, C, sC, epi, status, ctl, s);
   return launch_split_gemm_LC<L, 1>(g, batch, Ad, ea, Bd, eb, C, sC, epi, status, ctl, s);
 }
 

@@ -210,7 +210,8 @@ class Context:
         _check(load().mg_ctx_set_stage_k(self.h, int(stage_k)), "mg_ctx_set_stage_k")
 
     def set_digit_pairs(self, on):
-        _check(load().mg_ctx_set_digit_pairs(self.h, 1 if on else 0), "mg_ctx_set_digit_pairs")
+        """False/0: digit-major; True/1: paired, 16-deep stages; 2: paired, 32-deep stages."""
+        _check(load().mg_ctx_set_digit_pairs(self.h, int(on)), "mg_ctx_set_digit_pairs")
 
     def set_cta_pairs(self, on):
         """True / False, or None for the library's choice by digit count."""

@@ -638,8 +638,8 @@ def test_cgemm_split_adversarial_row_and_column_scales(ctx, d):
 @pytest.mark.parametrize("d,L", [(30, 6), (129, 5), (300, 6), (729, 6), (700, 3), (64, 2), (200, 4), (97, 8)])
 def test_cgemm_split_stage_k_variants_agree_bit_for_bit(d, L):
     """The product's pipeline stage (K = 16, 32 or 64 per stage: 32-, 64- or 128-byte operand
-    rows) and the paired digit layout (two digits per 64-byte row, 16-deep stages; even L)
-    do not change its arithmetic: the MMAs run in the same order over K, so the results
+    rows) and the paired digit layout (two digits per row: 64-byte rows of 16-deep stages
+    or 128-byte rows of 32-deep ones; even L) do not change its arithmetic: the MMAs run in the same order over K, so the results
     agree bit for bit (K = 64 applies where L <= 3 and each half of K is a multiple of 64,
     else the product takes K = 32; odd L ignores the paired layout).  The same holds for
     the M = 256 products of CTA pairs (d > 128; d = 300 has an odd number of row tiles,
@@ -648,18 +648,18 @@ def test_cgemm_split_stage_k_variants_agree_bit_for_bit(d, L):
     A, B = rand_c(rng, (2, d, d)), rand_c(rng, (2, d, d))
     c = M.Context(0)
     out = {}
-    for k in (32, 16, 64, "pairs", "cta32", "cta16", "cta64"):
-        c.set_digit_pairs(k == "pairs")
+    for k in (32, 16, 64, "pairs", "cta32", "cta16", "cta64", "pairs2", "ctapairs", "ctapairs2"):
+        c.set_digit_pairs({"pairs": 1, "ctapairs": 1, "pairs2": 2, "ctapairs2": 2}.get(str(k), 0))
         c.set_cta_pairs(str(k).startswith("cta"))
-        c.set_stage_k(int(str(k)[3:]) if str(k).startswith("cta") else (32 if k == "pairs" else k))
+        c.set_stage_k(int(str(k)[3:]) if str(k)[3:].isdigit() and str(k).startswith("cta") else
+                      (k if isinstance(k, int) else 32))
         C = torch.empty((2, d, d), dtype=torch.complex128, device="cuda")
         M.mg_cgemm(c, 2, d, cuda(A), cuda(B), C, M.MG_PREC_SPLIT, L)
         torch.cuda.synchronize()
         out[k] = C.cpu().numpy()
     c.close()
     assert np.array_equal(out[16], out[32]) and np.array_equal(out[64], out[32])
-    assert np.array_equal(out["pairs"], out[32])
-    for k in ("cta32", "cta16", "cta64"):
+    for k in ("pairs", "pairs2", "cta32", "cta16", "cta64", "ctapairs", "ctapairs2"):
         assert np.array_equal(out[k], out[32]), (k, np.abs(out[k] - out[32]).max())
     beta = split_beta(d)
     bound = (L + 2) * 2 * d * (2 * np.abs(A).max()) * (2 * np.abs(B).max()) * (2.0 ** (-beta * L) + L * 2.0 ** (-22 - 3 * beta))
