@@ -58,6 +58,8 @@ def parse():
                     help="paired digit layout of the split product (mg_ctx_set_digit_pairs)")
     ap.add_argument("--cta-pairs", type=int, default=None, choices=[0, 1],
                     help="split products on CTA pairs (mg_ctx_set_cta_pairs)")
+    ap.add_argument("--no-structure", action="store_true",
+                    help="full split products even for real operators (mg_ctx_set_structure 0)")
     ap.add_argument("--tolerance", type=float, default=1e-6,
                     help="max-abs tolerance the headline plan is tuned for (mg_plan_autotune)")
     ap.add_argument("--no-tune", action="store_true",
@@ -235,6 +237,8 @@ def run_ours(args):
         ctx.set_digit_pairs(args.digit_pairs)
     if args.cta_pairs is not None:
         ctx.set_cta_pairs(args.cta_pairs)
+    if args.no_structure:
+        ctx.set_structure(False)
     prec = M.MG_PREC_SPLIT if args.precision == "split" else M.MG_PREC_FP64
     N = args.intervals
 
@@ -612,6 +616,8 @@ def run_config(args):
         ctx.set_digit_pairs(args.digit_pairs)
     if args.cta_pairs is not None:
         ctx.set_cta_pairs(args.cta_pairs)
+    if args.no_structure:
+        ctx.set_structure(False)
     cores = len(os.sched_getaffinity(0))
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     warm = max(3, args.warmup)

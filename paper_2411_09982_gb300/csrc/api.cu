@@ -130,6 +130,8 @@ struct mg_ctx {
   int stage_k = 32;         // K per pipeline stage of the split product (mg_ctx_set_stage_k)
   int digit_pairs = 0;      // paired digit layout of the split product (mg_ctx_set_digit_pairs)
   int cta_pairs = -1;       // split products on CTA pairs (mg_ctx_set_cta_pairs; -1: by digit count)
+  int structure = 1;        // split products skip the exactly-zero parts of real operators' powers
+                            // (mg_ctx_set_structure)
 };
 
 struct mg_plan {
@@ -162,6 +164,10 @@ struct mg_plan {
   int opnorm_dp = 0;
   int taylor_mode = MG_TAYLOR_AUTO;   // MG_TAYLOR_PS: Paterson-Stockmeyer degrees only
   double taylor_u = 0.0;              // truncation target of the Taylor series (0: the arithmetic's)
+  // every operator entering Hbar_n (H0 and the Kx operators) has an exactly zero
+  // imaginary part, so every Hbar_n - tau_n I is real and X_n = -i 2^-s (Hbar_n - tau_n I)
+  // purely imaginary (checked on the device whenever the operator set is formed)
+  bool real_ops = false;
 };
 
 namespace {
@@ -355,6 +361,11 @@ struct Engine {
   int sq_step = 0;
   int taylor_mode = MG_TAYLOR_AUTO;   // MG_TAYLOR_PS: no degree-18 scheme
   double taylor_u = 0.0;              // coarser truncation target than the arithmetic's, or 0
+  // X of every item is purely imaginary (real operators, first-order term): the powers
+  // X^j of the Taylor polynomial are real (j even) or imaginary (j odd), and their
+  // split products skip the zero parts (SplitCtl::a_zero, b_zero) of the next product
+  bool x_imag = false;
+  int a_zero = 0, b_zero = 0;         // structure of the next product's operands
   bool allow18() const { return prec == MG_PREC_SPLIT && taylor_mode != MG_TAYLOR_PS; }
   SplitCtl ctl() const {
     SplitCtl c;
@@ -365,6 +376,8 @@ struct Engine {
     c.stage_k = ctx->stage_k;
     c.pairs = ctx->digit_pairs;
     c.cta_pairs = ctx->cta_pairs;
+    c.a_zero = a_zero;
+    c.b_zero = b_zero;
     return c;
   }
 
@@ -426,8 +439,11 @@ struct Engine {
     int e0 = -1, e1 = -1;
     if (ctx->timing) MG_TRY(timing_begin(&e0));
     int r;
+    // algorithmic work: a zero part of an operand halves the real products the complex one needs
+    const double work = (prec == MG_PREC_SPLIT ? (a_zero ? 0.5 : 1.0) * (b_zero ? 0.5 : 1.0) : 1.0);
     if (prec == MG_PREC_SPLIT) {
       r = split_gemm(d, L, batch, abuf, bbuf[slot], C, sC, add, ctx->status, ctx->stream, ctl());
+      a_zero = b_zero = 0;
     } else {
       AddTerms a = add;
       a.item_sq = item_sq;
@@ -441,11 +457,18 @@ struct Engine {
       ctx->t_launches += 1;
       // predicated launches (per-item squarings): the device adds the work of the
       // active items to the context's device counter instead
-      if (!item_sq) ctx->t_flops += 8.0 * (double)d * d * d * batch;
+      if (!item_sq) ctx->t_flops += 8.0 * work * (double)d * d * d * batch;
     }
     return MG_OK;
   }
   int timing_begin(int* idx) { return timing_mark(ctx, idx); }
+  // operand structure of the next split product, where X is known to be imaginary
+  void set_structure(int az, int bz) {
+    if (x_imag && prec == MG_PREC_SPLIT && ctx->structure) {
+      a_zero = az;
+      b_zero = bz;
+    }
+  }
 };
 
 long long mat_doubles(int d) { return 2LL * d * d; }
@@ -483,11 +506,15 @@ int taylor_poly(mg_ctx* ctx, Engine& eng, int batch, double* W, const TaylorChoi
     AddTerms none;
     MG_TRY(eng.prepA(batch, X, md));
     MG_TRY(eng.prepB(0, batch, X, md));
+    // with X imaginary: A2 and A6 real, A3 imaginary
+    eng.set_structure(1, 1);
     MG_TRY(eng.mul(batch, X, md, 0, X, md, P2, md, none));        // A2
     MG_TRY(eng.prepA(batch, P2, md));
+    eng.set_structure(2, 1);
     MG_TRY(eng.mul(batch, P2, md, 0, X, md, P3, md, none));       // A3
     MG_TRY(eng.prepA(batch, P3, md));
     MG_TRY(eng.prepB(1, batch, P3, md));
+    eng.set_structure(1, 1);
     MG_TRY(eng.mul(batch, P3, md, 1, P3, md, Y, md, none));       // A6
     // B1 -> R0, B5 -> R1, B4 -> P2, B3 -> P3, B2 -> Y (in place over A2, A3, A6)
     const double* srcs[4] = {X, P2, P3, Y};
@@ -539,6 +566,7 @@ int taylor_poly(mg_ctx* ctx, Engine& eng, int batch, double* W, const TaylorChoi
   for (int j = 2; j <= p; ++j) {
     MG_TRY(eng.prepA(batch, P[j - 1], md));
     AddTerms none;
+    eng.set_structure((j - 1) % 2 == 1 ? 1 : 2, 1);   // X^{j-1} imaginary for odd j - 1, else real
     MG_TRY(eng.mul(batch, P[j - 1], md, 0, X, md, pow_buf[j], md, none));
     P[j] = pow_buf[j];
   }
@@ -1185,6 +1213,12 @@ int mg_ctx_set_digit_pairs(mg_ctx* ctx, int on) {
   return MG_OK;
 }
 
+int mg_ctx_set_structure(mg_ctx* ctx, int on) {
+  if (!ctx || (on != 0 && on != 1)) return MG_EINVAL;
+  ctx->structure = on;
+  return MG_OK;
+}
+
 int mg_ctx_set_cta_pairs(mg_ctx* ctx, int on) {
   if (!ctx || on < -1 || on > 1) return MG_EINVAL;
   ctx->cta_pairs = on;
@@ -1285,6 +1319,23 @@ int mg_split_digits(int d, int bits, int* beta, int* slices) {
   return MG_OK;
 }
 
+// p->real_ops from the operators now entering Hbar_n (H0 and Kx operators); synchronises
+// the context's stream (plan set-up only)
+static int detect_real_ops(mg_ctx* ctx, mg_plan* p) {
+  double* sc;
+  MG_TRY(small_scratch(ctx, 1, &sc));
+  int* flag = reinterpret_cast<int*>(sc);
+  const long long md = mat_doubles(p->d);
+  MG_CUDA_TRY(cudaMemsetAsync(flag, 0, sizeof(int), ctx->stream));
+  MG_TRY(launch_imag_nonzero(md / 2, p->H0, flag, ctx->stream));
+  if (p->Kx > 0) MG_TRY(launch_imag_nonzero(md / 2 * p->Kx, p->Hk, flag, ctx->stream));
+  int any = 1;
+  MG_CUDA_TRY(cudaMemcpyAsync(&any, flag, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  MG_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  p->real_ops = any == 0;
+  return MG_OK;
+}
+
 int mg_plan_create(mg_ctx* ctx, mg_plan** out, int d, int K, const double* H0, const double* Hk, int precision,
                    int slices, int flags) {
   if (!ctx || !out || !H0 || d < 1 || d > 4096 || K < 0 || K > 64 || (K > 0 && !Hk)) return MG_EINVAL;
@@ -1337,6 +1388,11 @@ int mg_plan_create(mg_ctx* ctx, mg_plan** out, int d, int K, const double* H0, c
       mg_plan_destroy(p);
       return r;
     }
+  }
+  const int rr = detect_real_ops(ctx, p);
+  if (rr != MG_OK) {
+    mg_plan_destroy(p);
+    return rr;
   }
   *out = p;
   return MG_OK;
@@ -1642,6 +1698,7 @@ int mg_evolve(mg_plan* p, int output, const double* in, double* out, int reorth_
   Engine eng{ctx, d, p->precision, p->L};
   eng.taylor_mode = p->taylor_mode;
   eng.taylor_u = p->taylor_u;
+  eng.x_imag = p->real_ops;
   PropState ps;
   ps.output = output;
   ps.d = d;
@@ -2393,6 +2450,8 @@ int issue_group(mg_ctx* ctx, GroupProgram& G, const double* const* in, double* c
   Engine eng{ctx, dp, G.prec, G.L};
   eng.taylor_mode = G.taylor;
   eng.taylor_u = G.taylor_u;
+  eng.x_imag = !G.plans.empty();
+  for (const mg_plan* q : G.plans) eng.x_imag = eng.x_imag && q->real_ops;
   MG_CUDA_TRY(cudaMemsetAsync(G.job_fail, 0, sizeof(int) * G.jobs.size(), s));
   MG_CUDA_TRY(cudaMemsetAsync(G.overflow, 0, sizeof(int), s));
   for (BatchJob& j : G.jobs) {
@@ -3702,7 +3761,7 @@ int mg_plan_set_magnus_order(mg_plan* p, int order) {
     p->Kx = K;
     p->csr_ok = false;
     p->N = 0;   // controls must be set again
-    return MG_OK;
+    return detect_real_ops(ctx, p);
   }
   const int Kx = 2 * K + K * (K - 1) / 2;
   const long long md = mat_doubles(d);
@@ -3749,7 +3808,7 @@ int mg_plan_set_magnus_order(mg_plan* p, int order) {
   p->c_cap = 0;
   cudaFree(p->c);
   p->c = nullptr;
-  return MG_OK;
+  return detect_real_ops(ctx, p);
 }
 
 }  // extern "C"

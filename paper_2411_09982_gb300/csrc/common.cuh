@@ -90,6 +90,9 @@ int launch_shift_norm(int batch, int d, const double* A, double* dst, double* ta
 // out[0] = max|H - H^dag|, out[1] = max|H| over `count` stacked d x d operators (as double bits)
 int launch_hermitian_defect(int d, int count, const double* H, unsigned long long* out, cudaStream_t s);
 
+// *out |= 1 if any of the n complex entries at M has a nonzero imaginary part
+int launch_imag_nonzero(long long n, const double* M, int* out, cudaStream_t s);
+
 // X_b = (-i) 2^{-sq_b} src_b, sq from a device int array (sq_dev) or the constant sq
 int launch_scale_minus_i(int batch, int d, const double* src, double* dst, const int* sq_dev,
                          int sq, cudaStream_t s);
@@ -151,6 +154,14 @@ struct SplitCtl {
                                  // digit buffers must agree on it (the memory layout is the same for 1 and 2)
   int cta_pairs = -1;            // M = 256 products on CTA pairs (tcgen05 cta_group::2) where d > 128:
                                  // 1 on, 0 off, -1 for five or more digits
+  // Operand structure of one product (bit 0: the real part is exactly zero, bit 1: the
+  // imaginary part is).  A's zero half of K is neither loaded nor multiplied; with one
+  // part of B zero, each half of K multiplies the other plane only (N = 64) into the
+  // output half it feeds, on one CTA per tile.  The skipped digit products are exact
+  // zeros, so the product is the same; a flag set on an operand that is not so
+  // structured gives a wrong product.  3 (both parts zero) is treated as 0.
+  int a_zero = 0;
+  int b_zero = 0;
 };
 int split_slice_a(int d, int L, int batch, const double* A, long long sA, int in_df32, void* buf, cudaStream_t s,
                   const SplitCtl& ctl = SplitCtl());

@@ -587,4 +587,20 @@ int launch_hermitian_defect(int d, int count, const double* H, unsigned long lon
   return check_launch("hermitian_defect_kernel");
 }
 
+// Whether any of n complex entries has a nonzero imaginary part: *out = 1 if so (out
+// must be preset to 0).  A stack of real operators keeps every Hbar_n of the first-order
+// term real, so the split products of its exponential can skip exactly-zero parts.
+__global__ void imag_nonzero_kernel(long long n, const double* __restrict__ M, int* __restrict__ out) {
+  int any = 0;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
+    any |= M[2 * e + 1] != 0.0;
+  if (__any_sync(0xffffffffu, any) && (threadIdx.x & 31) == 0) atomicOr(out, 1);
+}
+
+int launch_imag_nonzero(long long n, const double* M, int* out, cudaStream_t s) {
+  if (n <= 0) return MG_OK;
+  imag_nonzero_kernel<<<304, 256, 0, s>>>(n, M, out);
+  return check_launch("imag_nonzero_kernel");
+}
+
 }  // namespace mg

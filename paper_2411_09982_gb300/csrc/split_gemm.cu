@@ -549,6 +549,8 @@ __device__ __forceinline__ uint64_t pair_desc(uint32_t saddr) {
 
 // Instruction descriptor: kind::f16, A = B = BF16, D = F32, both K-major, M = 128, N = 128.
 constexpr uint32_t kIdescBf16 = (1u << 4) | (1u << 7) | (1u << 10) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
+// the same with N = 64: one B plane (a product whose B operand has a zero part)
+constexpr uint32_t kIdescBf16N64 = (1u << 4) | (1u << 7) | (1u << 10) | ((64u >> 3) << 17) | ((128u >> 4) << 24);
 // the same with M = 256 (a CTA pair, cta_group::2)
 constexpr uint32_t kIdescBf16M256 =
     (1u << 4) | (1u << 7) | (1u << 10) | ((128u >> 3) << 17) | ((256u >> 4) << 24);
@@ -632,6 +634,11 @@ split_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
   const bool leader = crank == 0;
   const int num_k = Kp / BK;
   const int nkh = num_k / 2;   // K stages of the real half
+  // operand structure (uniform over the launch; see SplitCtl): the K stages [kbeg, kend)
+  // are loaded and multiplied; bz != 0 (one CTA per tile only) selects N = 64 products
+  const int az = ctl.a_zero == 3 ? 0 : ctl.a_zero;
+  const int bz = (CTAS == 1 && ctl.b_zero != 3) ? ctl.b_zero : 0;
+  const int kbeg = (az & 1) ? nkh : 0, kend = (az & 2) ? nkh : num_k;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -678,9 +685,10 @@ split_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
     if (lane == 0) {
       // ---------------- TMA producer ----------------
       int issued = 0;
-      for (int kb = 0; kb < num_k; ++kb) {
-        const int s = kb % STAGES;
-        const uint32_t ph = (kb / STAGES) & 1;
+      for (int kb = kbeg; kb < kend; ++kb) {
+        const int i = kb - kbeg;   // position in the ring's sequence of stages
+        const int s = i % STAGES;
+        const uint32_t ph = (i / STAGES) & 1;
         if (!mbar_wait(&empty[s], ph ^ 1, deadline_short)) {
           atomicExch(status, MG_DEV_TIMEOUT);
           *(volatile int*)abort_flag = 1;
@@ -713,7 +721,7 @@ split_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
           tma_load_4d(st, &tmA, &full[s], kb * BK, mt * SG_BM, 0, b);
           tma_load_5d(st + L * TILE_BYTES, &tmB, &full[s], kbb * BK, nt * SG_BNC, plane0, 0, b);
         }
-        issued = kb + 1;
+        issued = i + 1;
       }
       // never leave the CTA with a bulk copy still in flight into its shared memory.  In
       // a pair the barriers of rank 0 count the copies of both CTAs: rank 0 drains them,
@@ -722,8 +730,8 @@ split_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
       // issue the same stages; a timeout is the one way they could differ.)
       if (CTAS == 1 || leader) {
         const uint64_t drain_deadline = global_ns() + SG_WAIT_NS;
-        for (int kb = issued > STAGES ? issued - STAGES : 0; kb < issued; ++kb)
-          mbar_wait(&full[kb % STAGES], (kb / STAGES) & 1, drain_deadline);
+        for (int i = issued > STAGES ? issued - STAGES : 0; i < issued; ++i)
+          mbar_wait(&full[i % STAGES], (i / STAGES) & 1, drain_deadline);
       }
     }
   } else if (warp == 1) {
@@ -734,9 +742,15 @@ split_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
         atomicExch(status, MG_DEV_TIMEOUT);
         ok = false;
       }
-      for (int kb = 0; kb < num_k && ok; ++kb) {
-        const int s = kb % STAGES;
-        const uint32_t ph = (kb / STAGES) & 1;
+      // N = 64 products (bz != 0): each half of K feeds one output half, from one B plane
+      // (the tile's first or second 64 rows): with Im B = 0 the real half feeds Re C from
+      // Re B and the imaginary half Im C from Re B; with Re B = 0 the real half feeds Im C
+      // from Im B and the imaginary half Re C from -Im B
+      constexpr uint32_t B_HALF = PAIRS ? B_TILE_BYTES : B_TILE_BYTES / 2;
+      for (int kb = kbeg; kb < kend && ok; ++kb) {
+        const int i = kb - kbeg;
+        const int s = i % STAGES;
+        const uint32_t ph = (i / STAGES) & 1;
         if (!mbar_wait(&full[s], ph, deadline_short)) {
           atomicExch(status, MG_DEV_TIMEOUT);
           ok = false;
@@ -744,8 +758,15 @@ split_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
         }
         tc_fence_after();
         const uint32_t a0 = smem_u32(smem + s * STAGE_BYTES);
-        const uint32_t b0 = a0 + L * TILE_BYTES;   // in a pair: this CTA's half, the partner's at the same offset
-        bool first[SG_GROUPS] = {kb == 0, kb == 0, kb == 0, kb == 0};
+        const int oh = bz == 0 ? 0 : ((bz & 2) ? (kb >= nkh) : (kb < nkh));   // output half (N = 64)
+        // in a pair: this CTA's half, the partner's at the same offset
+        const uint32_t b0 = a0 + L * TILE_BYTES + (uint32_t)oh * B_HALF;
+        const uint32_t dcol = (uint32_t)oh * SG_BNC;
+        const uint32_t idesc = bz ? kIdescBf16N64 : kIdescBf16;
+        // the first stage of an accumulator: the first loaded one, and with N = 64 the
+        // first of each half of K (which writes the other output half)
+        const bool fst = kb == kbeg || (bz != 0 && kb == nkh);
+        bool first[SG_GROUPS] = {fst, fst, fst, fst};
 #pragma unroll
         for (int kk = 0; kk < BK / SG_MMA_K; ++kk) {
 #pragma unroll
@@ -766,7 +787,7 @@ split_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
                 bd = kmajor_desc<BK>(b0 + sb * B_TILE_BYTES + kk * SG_MMA_K * 2);
               }
               if constexpr (CTAS == 2) tc_mma_bf16_pair(tmem + g * 128, ad, bd, kIdescBf16M256, acc);
-              else tc_mma_bf16(tmem + g * 128, ad, bd, kIdescBf16, acc);
+              else tc_mma_bf16(tmem + g * 128 + dcol, ad, bd, idesc, acc);
             }
           }
         }
@@ -833,13 +854,22 @@ split_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
       const int row = mt * SG_BM + r;
       const int Ea = row < d ? ea[(long long)b * Mp + row] : 0;
       const uint32_t lane_base = tmem + ((uint32_t)(q * 32) << 16);
+      // output halves no MMA wrote (N = 64 products with one half of K skipped) are zero
+      bool wr[2] = {true, true};
+      if (bz) {
+        wr[0] = wr[1] = false;
+        if (kbeg == 0) wr[(bz & 2) ? 0 : 1] = true;     // the real half of K was multiplied
+        if (kend == num_k) wr[(bz & 2) ? 1 : 0] = true; // the imaginary half was
+      }
       constexpr int CW = 4;   // complex columns per step
       for (int jc = c0; jc < c0 + SG_BNC / 2; jc += CW) {
         uint32_t re_acc[SG_GROUPS][CW], im_acc[SG_GROUPS][CW];
 #pragma unroll
         for (int g = 0; g < SG_GROUPS; ++g) {
-          tmem_ld4(lane_base + g * 128 + jc, re_acc[g]);
-          tmem_ld4(lane_base + g * 128 + SG_BNC + jc, im_acc[g]);
+          if (wr[0]) tmem_ld4(lane_base + g * 128 + jc, re_acc[g]);
+          else re_acc[g][0] = re_acc[g][1] = re_acc[g][2] = re_acc[g][3] = 0u;
+          if (wr[1]) tmem_ld4(lane_base + g * 128 + SG_BNC + jc, im_acc[g]);
+          else im_acc[g][0] = im_acc[g][1] = im_acc[g][2] = im_acc[g][3] = 0u;
         }
         tmem_wait_ld();
 #pragma unroll
@@ -1111,7 +1141,9 @@ static int launch_split_gemm_L(const SplitGeom& g, int batch, const __nv_bfloat1
   // multiplying zeros: -19% at d = 300, three tiles).
   const int mtiles = g.Mp / SG_BM;
   const bool shape_ok = (mtiles % 2 == 0) ? g.d >= 256 : mtiles >= 7;
-  const bool pair = mtiles >= 2 && (ctl.cta_pairs > 0 || (ctl.cta_pairs < 0 && L >= 5 && shape_ok));
+  // a product with a zero part of B runs N = 64 MMAs on one CTA per tile
+  const bool bstruct = ctl.b_zero == 1 || ctl.b_zero == 2;
+  const bool pair = mtiles >= 2 && !bstruct && (ctl.cta_pairs > 0 || (ctl.cta_pairs < 0 && L >= 5 && shape_ok));
   if constexpr (L % 2 == 0) {
     if (paired_layout(g, ctl)) {
       // pairs = 2: 32-deep stages of 128-byte rows where two stages fit, else 16-deep

@@ -120,6 +120,7 @@ SIGNATURES = {
     "mg_ctx_set_stage_k": (_I, [_P, _I]),
     "mg_ctx_set_digit_pairs": (_I, [_P, _I]),
     "mg_ctx_set_cta_pairs": (_I, [_P, _I]),
+    "mg_ctx_set_structure": (_I, [_P, _I]),
     "mg_ctx_gemm_stats": (_I, [_P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(_D), ctypes.POINTER(_D), _I]),
     "mg_cgemm_split_static": (_I, [_I, _P, _I, _I, _P, _P, _P, _I]),
     "mg_tune_select": (_I, [_I, ctypes.POINTER(mg_tune_entry), _D, _D, ctypes.POINTER(_I)]),
@@ -216,6 +217,10 @@ class Context:
     def set_cta_pairs(self, on):
         """True / False, or None for the library's choice by digit count."""
         _check(load().mg_ctx_set_cta_pairs(self.h, -1 if on is None else (1 if on else 0)), "mg_ctx_set_cta_pairs")
+
+    def set_structure(self, on):
+        """True (default): split products skip the exactly-zero parts of real operators' powers."""
+        _check(load().mg_ctx_set_structure(self.h, 1 if on else 0), "mg_ctx_set_structure")
 
     def set_wait_limit(self, seconds=4.0, stall_test=False):
         _check(load().mg_ctx_set_wait_limit(self.h, float(seconds), 1 if stall_test else 0), "mg_ctx_set_wait_limit")
