@@ -557,23 +557,33 @@ int mg_ctx_set_digit_pairs(mg_ctx* ctx, int on);
  * each SM's shared-memory port, which every MMA reads its operands through (8 KiB
  * per MMA on one CTA, 6 KiB on a pair).  MG_EINVAL for other values. */
 int mg_ctx_set_cta_pairs(mg_ctx* ctx, int on);
-/* Operand structure of the tensor-core product (MG_PREC_SPLIT).  When every operator
- * of a plan (H0 and the H_k, with the commutator operators of the second-order term
- * where mg_plan_set_magnus_order(2) adds them) has an exactly zero imaginary part --
+/* Structure of the tensor-core products (MG_PREC_SPLIT) of real operators.  When every
+ * operator of a plan (H0 and the H_k, with the commutator operators of the second-order
+ * term where mg_plan_set_magnus_order(2) adds them) has an exactly zero imaginary part --
  * the drive operators b + b^dag and the Hamiltonians of the Sec. "Magnus Expansion"
  * workloads in a real basis -- every first-order Hbar_n is real, so the exponent
  * X_n = -i 2^-s (Hbar_n - tau_n I) of Eq. magnus-first-order-term is purely imaginary,
- * its even powers real and its odd powers imaginary.  mg_plan_create (and
- * mg_plan_set_magnus_order) check this on the device.  on = 1 (the default): the
- * products X X, X^2 X and X^3 X^3 of the Taylor polynomial (and the power products
- * of the Paterson-Stockmeyer forms) leave out the digit products of the zero parts:
- * the zero half of the K axis of A is not loaded, and where B has a zero part each
- * half of K multiplies the other one into the output half it feeds (N = 64 MMAs, one
- * CTA per tile): a quarter of the tensor-core work of a general product.  Only exact
- * zeros are left out, so the result is the same as with on = 0, which issues every
- * product in full.  Applies to mg_evolve and mg_evolve_batch (a batch only when all of
- * its plans are real); gemm statistics count such a product's work as 2 d^3 (one real
- * product) instead of 8 d^3.  MG_EINVAL for other values. */
+ * its even powers real and its odd powers imaginary; when the operators are also exactly
+ * symmetric (real Hermitian), every polynomial in X_n, and so every Taylor polynomial,
+ * squaring and U_n, is complex symmetric (U = U^T).  mg_plan_create (and
+ * mg_plan_set_magnus_order) check both on the device.  `on` is a bit mask:
+ *   bit 0: the products X X, X^2 X and X^3 X^3 of the Taylor polynomial (and the power
+ *          products of the Paterson-Stockmeyer forms) leave out the digit products of the
+ *          zero parts: the zero half of the K axis of A is not loaded, and where B has a
+ *          zero part each half of K multiplies the other one into the output half it feeds
+ *          (N = 64 MMAs, one CTA per tile): a quarter of a general product's tensor-core
+ *          work.  Only exact zeros are left out: the result is the same as without.
+ *   bit 1: every product of the exponential (Taylor polynomial and squarings) computes
+ *          only the output tiles on or below the diagonal (128-row tiles, or 256 on CTA
+ *          pairs) and then copies every entry above the diagonal from its transpose: the
+ *          result is exactly symmetric, the same on either tiling, and differs from the
+ *          full product's by that product's own rounding asymmetry.  The tree product of
+ *          the U_n is general.
+ * 3 (the default) sets both, 0 issues every product in full.  Applies to mg_evolve and
+ * mg_evolve_batch (a batch only when all of its plans qualify); gemm statistics count
+ * the algorithmic work of such a product: a quarter of 8 d^3 with two zero parts, and
+ * the d (d + 1) / 2 entries on and below the diagonal of a symmetric result.  MG_EINVAL
+ * outside 0..3. */
 int mg_ctx_set_structure(mg_ctx* ctx, int on);
 int mg_ctx_gemm_stats(mg_ctx* ctx, int64_t* launches, double* ms, double* flops, int reset);
 

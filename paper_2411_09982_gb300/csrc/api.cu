@@ -130,8 +130,9 @@ struct mg_ctx {
   int stage_k = 32;         // K per pipeline stage of the split product (mg_ctx_set_stage_k)
   int digit_pairs = 0;      // paired digit layout of the split product (mg_ctx_set_digit_pairs)
   int cta_pairs = -1;       // split products on CTA pairs (mg_ctx_set_cta_pairs; -1: by digit count)
-  int structure = 1;        // split products skip the exactly-zero parts of real operators' powers
-                            // (mg_ctx_set_structure)
+  int structure = 3;        // split products of real operators: bit 0 skips the exactly-zero parts
+                            // of X's powers, bit 1 the tiles above the diagonal of symmetric
+                            // results (mg_ctx_set_structure)
 };
 
 struct mg_plan {
@@ -168,6 +169,8 @@ struct mg_plan {
   // imaginary part, so every Hbar_n - tau_n I is real and X_n = -i 2^-s (Hbar_n - tau_n I)
   // purely imaginary (checked on the device whenever the operator set is formed)
   bool real_ops = false;
+  // ... and every one is exactly symmetric, so every polynomial in X_n is complex symmetric
+  bool sym_ops = false;
 };
 
 namespace {
@@ -365,7 +368,9 @@ struct Engine {
   // X^j of the Taylor polynomial are real (j even) or imaginary (j odd), and their
   // split products skip the zero parts (SplitCtl::a_zero, b_zero) of the next product
   bool x_imag = false;
+  bool x_sym = false;                 // ... and symmetric: every polynomial in X is symmetric
   int a_zero = 0, b_zero = 0;         // structure of the next product's operands
+  int sym = 0;                        // the next product's result is complex symmetric
   bool allow18() const { return prec == MG_PREC_SPLIT && taylor_mode != MG_TAYLOR_PS; }
   SplitCtl ctl() const {
     SplitCtl c;
@@ -378,6 +383,7 @@ struct Engine {
     c.cta_pairs = ctx->cta_pairs;
     c.a_zero = a_zero;
     c.b_zero = b_zero;
+    c.sym_out = sym;
     return c;
   }
 
@@ -439,11 +445,14 @@ struct Engine {
     int e0 = -1, e1 = -1;
     if (ctx->timing) MG_TRY(timing_begin(&e0));
     int r;
-    // algorithmic work: a zero part of an operand halves the real products the complex one needs
-    const double work = (prec == MG_PREC_SPLIT ? (a_zero ? 0.5 : 1.0) * (b_zero ? 0.5 : 1.0) : 1.0);
+    // algorithmic work: a zero part of an operand halves the real products the complex one
+    // needs; a symmetric result needs its d (d + 1) / 2 entries on and below the diagonal
+    const double work = prec == MG_PREC_SPLIT ? (a_zero ? 0.5 : 1.0) * (b_zero ? 0.5 : 1.0) *
+                                                    (sym ? (d + 1.0) / (2.0 * d) : 1.0)
+                                              : 1.0;
     if (prec == MG_PREC_SPLIT) {
       r = split_gemm(d, L, batch, abuf, bbuf[slot], C, sC, add, ctx->status, ctx->stream, ctl());
-      a_zero = b_zero = 0;
+      a_zero = b_zero = sym = 0;
     } else {
       AddTerms a = add;
       a.item_sq = item_sq;
@@ -464,10 +473,16 @@ struct Engine {
   int timing_begin(int* idx) { return timing_mark(ctx, idx); }
   // operand structure of the next split product, where X is known to be imaginary
   void set_structure(int az, int bz) {
-    if (x_imag && prec == MG_PREC_SPLIT && ctx->structure) {
+    if (x_imag && prec == MG_PREC_SPLIT && (ctx->structure & 1)) {
       a_zero = az;
       b_zero = bz;
     }
+    set_sym();
+  }
+  // the next split product is a polynomial in X (or a product of two): with X = -i S, S real
+  // symmetric, every such matrix is complex symmetric
+  void set_sym() {
+    if (x_sym && prec == MG_PREC_SPLIT && (ctx->structure & 2)) sym = 1;
   }
 };
 
@@ -532,6 +547,7 @@ int taylor_poly(mg_ctx* ctx, Engine& eng, int batch, double* W, const TaylorChoi
     add4.diag = 0.0;
     MG_TRY(eng.prepA(batch, R0, md));
     MG_TRY(eng.prepB(0, batch, R1, md));
+    eng.set_sym();
     MG_TRY(eng.mul(batch, R0, md, 0, R1, md, W, md, add4));       // A9 (over X)
     {
       const double* qs[2] = {W, P3};
@@ -546,6 +562,7 @@ int taylor_poly(mg_ctx* ctx, Engine& eng, int batch, double* W, const TaylorChoi
     add2.diag = 0.0;
     MG_TRY(eng.prepA(batch, P3, md));
     MG_TRY(eng.prepB(1, batch, W, md));
+    eng.set_sym();
     MG_TRY(eng.mul(batch, P3, md, 1, W, md, R0, md, add2));       // T
     R = R0;
     Rn = R1;
@@ -592,6 +609,7 @@ int taylor_poly(mg_ctx* ctx, Engine& eng, int batch, double* W, const TaylorChoi
     add.stride = md;
     add.diag = coef(i * p);
     MG_TRY(eng.prepA(batch, R, md));
+    eng.set_sym();
     MG_TRY(eng.mul(batch, R, md, 1, P[p], md, Rn, md, add));
     std::swap(R, Rn);
   }
@@ -648,6 +666,7 @@ int expm_chunk(mg_ctx* ctx, Engine& eng, int batch, double* W, const double* tau
     MG_TRY(eng.prepA(batch, R, md));
     MG_TRY(eng.prepB(0, batch, R, md));
     AddTerms none;
+    eng.set_sym();
     MG_TRY(eng.mul(batch, R, md, 0, R, md, Rn, md, none));
     std::swap(R, Rn);
   }
@@ -678,6 +697,7 @@ int expm_chunk_dev(mg_ctx* ctx, Engine& eng, int batch, double* W, const double*
       eng.sq_step = k;
       int r = eng.prepA(batch, R, md);
       if (r == MG_OK) r = eng.prepB(0, batch, R, md);
+      eng.set_sym();
       if (r == MG_OK) r = eng.mul(batch, R, md, 0, R, md, R, md, none);
       eng.item_sq = nullptr;
       eng.sq_step = 0;
@@ -1214,7 +1234,7 @@ int mg_ctx_set_digit_pairs(mg_ctx* ctx, int on) {
 }
 
 int mg_ctx_set_structure(mg_ctx* ctx, int on) {
-  if (!ctx || (on != 0 && on != 1)) return MG_EINVAL;
+  if (!ctx || on < 0 || on > 3) return MG_EINVAL;
   ctx->structure = on;
   return MG_OK;
 }
@@ -1319,20 +1339,20 @@ int mg_split_digits(int d, int bits, int* beta, int* slices) {
   return MG_OK;
 }
 
-// p->real_ops from the operators now entering Hbar_n (H0 and Kx operators); synchronises
-// the context's stream (plan set-up only)
+// p->real_ops and p->sym_ops from the operators now entering Hbar_n (H0 and the Kx
+// operators); synchronises the context's stream (plan set-up only)
 static int detect_real_ops(mg_ctx* ctx, mg_plan* p) {
   double* sc;
   MG_TRY(small_scratch(ctx, 1, &sc));
   int* flag = reinterpret_cast<int*>(sc);
-  const long long md = mat_doubles(p->d);
   MG_CUDA_TRY(cudaMemsetAsync(flag, 0, sizeof(int), ctx->stream));
-  MG_TRY(launch_imag_nonzero(md / 2, p->H0, flag, ctx->stream));
-  if (p->Kx > 0) MG_TRY(launch_imag_nonzero(md / 2 * p->Kx, p->Hk, flag, ctx->stream));
-  int any = 1;
-  MG_CUDA_TRY(cudaMemcpyAsync(&any, flag, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  MG_TRY(launch_operator_structure(p->d, 1, p->H0, flag, ctx->stream));
+  if (p->Kx > 0) MG_TRY(launch_operator_structure(p->d, p->Kx, p->Hk, flag, ctx->stream));
+  int bits = 3;
+  MG_CUDA_TRY(cudaMemcpyAsync(&bits, flag, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
   MG_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
-  p->real_ops = any == 0;
+  p->real_ops = (bits & 1) == 0;
+  p->sym_ops = bits == 0;
   return MG_OK;
 }
 
@@ -1699,6 +1719,7 @@ int mg_evolve(mg_plan* p, int output, const double* in, double* out, int reorth_
   eng.taylor_mode = p->taylor_mode;
   eng.taylor_u = p->taylor_u;
   eng.x_imag = p->real_ops;
+  eng.x_sym = p->sym_ops;
   PropState ps;
   ps.output = output;
   ps.d = d;
@@ -2450,8 +2471,11 @@ int issue_group(mg_ctx* ctx, GroupProgram& G, const double* const* in, double* c
   Engine eng{ctx, dp, G.prec, G.L};
   eng.taylor_mode = G.taylor;
   eng.taylor_u = G.taylor_u;
-  eng.x_imag = !G.plans.empty();
-  for (const mg_plan* q : G.plans) eng.x_imag = eng.x_imag && q->real_ops;
+  eng.x_imag = eng.x_sym = !G.plans.empty();
+  for (const mg_plan* q : G.plans) {
+    eng.x_imag = eng.x_imag && q->real_ops;
+    eng.x_sym = eng.x_sym && q->sym_ops;
+  }
   MG_CUDA_TRY(cudaMemsetAsync(G.job_fail, 0, sizeof(int) * G.jobs.size(), s));
   MG_CUDA_TRY(cudaMemsetAsync(G.overflow, 0, sizeof(int), s));
   for (BatchJob& j : G.jobs) {

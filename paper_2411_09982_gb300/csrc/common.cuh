@@ -90,8 +90,9 @@ int launch_shift_norm(int batch, int d, const double* A, double* dst, double* ta
 // out[0] = max|H - H^dag|, out[1] = max|H| over `count` stacked d x d operators (as double bits)
 int launch_hermitian_defect(int d, int count, const double* H, unsigned long long* out, cudaStream_t s);
 
-// *out |= 1 if any of the n complex entries at M has a nonzero imaginary part
-int launch_imag_nonzero(long long n, const double* M, int* out, cudaStream_t s);
+// *out |= 1 if an entry of the count stacked d x d operators at M has a nonzero imaginary
+// part, |= 2 if a real part differs from its transpose's
+int launch_operator_structure(int d, long long count, const double* M, int* out, cudaStream_t s);
 
 // X_b = (-i) 2^{-sq_b} src_b, sq from a device int array (sq_dev) or the constant sq
 int launch_scale_minus_i(int batch, int d, const double* src, double* dst, const int* sq_dev,
@@ -162,6 +163,11 @@ struct SplitCtl {
   // structured gives a wrong product.  3 (both parts zero) is treated as 0.
   int a_zero = 0;
   int b_zero = 0;
+  // The product is complex symmetric (C = C^T: polynomials in a symmetric matrix and
+  // their products with one another).  Output tiles wholly right of the diagonal are
+  // not computed; split_gemm then copies every entry above the diagonal from its
+  // transpose, so the stored result is exactly symmetric.
+  int sym_out = 0;
 };
 int split_slice_a(int d, int L, int batch, const double* A, long long sA, int in_df32, void* buf, cudaStream_t s,
                   const SplitCtl& ctl = SplitCtl());

@@ -587,20 +587,28 @@ int launch_hermitian_defect(int d, int count, const double* H, unsigned long lon
   return check_launch("hermitian_defect_kernel");
 }
 
-// Whether any of n complex entries has a nonzero imaginary part: *out = 1 if so (out
-// must be preset to 0).  A stack of real operators keeps every Hbar_n of the first-order
-// term real, so the split products of its exponential can skip exactly-zero parts.
-__global__ void imag_nonzero_kernel(long long n, const double* __restrict__ M, int* __restrict__ out) {
-  int any = 0;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
-    any |= M[2 * e + 1] != 0.0;
-  if (__any_sync(0xffffffffu, any) && (threadIdx.x & 31) == 0) atomicOr(out, 1);
+// Structure of a stack of `count` d x d complex operators: *out |= 1 if an entry has a
+// nonzero imaginary part, |= 2 if a real part differs from its transpose's (out preset to
+// 0).  Real operators keep every Hbar_n of the first-order term real; real symmetric ones
+// make every polynomial in X_n = -i 2^-s (Hbar_n - tau_n I) complex symmetric.
+__global__ void operator_structure_kernel(int d, long long count, const double* __restrict__ M,
+                                          int* __restrict__ out) {
+  const long long dd = (long long)d * d, n = count * dd;
+  int bits = 0;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    const long long m = e / dd, r = e % dd;
+    const long long i = r / d, j = r % d;
+    if (M[2 * e + 1] != 0.0) bits |= 1;
+    if (M[2 * e] != M[2 * (m * dd + j * d + i)]) bits |= 2;
+  }
+  for (int o = 16; o > 0; o >>= 1) bits |= __shfl_xor_sync(0xffffffffu, bits, o);
+  if ((threadIdx.x & 31) == 0 && bits) atomicOr(out, bits);
 }
 
-int launch_imag_nonzero(long long n, const double* M, int* out, cudaStream_t s) {
-  if (n <= 0) return MG_OK;
-  imag_nonzero_kernel<<<304, 256, 0, s>>>(n, M, out);
-  return check_launch("imag_nonzero_kernel");
+int launch_operator_structure(int d, long long count, const double* M, int* out, cudaStream_t s) {
+  if (count <= 0) return MG_OK;
+  operator_structure_kernel<<<304, 256, 0, s>>>(d, count, M, out);
+  return check_launch("operator_structure_kernel");
 }
 
 }  // namespace mg

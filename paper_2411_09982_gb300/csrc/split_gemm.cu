@@ -630,6 +630,9 @@ split_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
   const int nt = CTAS == 2 ? blockIdx.y : blockIdx.x, mt = CTAS == 2 ? blockIdx.x : blockIdx.y, b = blockIdx.z;
   // uniform over the CTA (and over a CTA pair, which shares b): no cluster barrier is reached
   if (ctl.item_sq && ctl.item_sq[b] <= ctl.sq_step) return;
+  // a symmetric product computes no tile (of a CTA pair: no pair of tiles) whose columns
+  // all lie right of all its rows; split_gemm mirrors those from below the diagonal
+  if (ctl.sym_out && nt * SG_BNC >= (CTAS == 2 ? ((mt | 1) + 1) : (mt + 1)) * SG_BM) return;
   const uint32_t crank = CTAS == 2 ? cluster_rank() : 0u;
   const bool leader = crank == 0;
   const int num_k = Kp / BK;
@@ -950,6 +953,32 @@ split_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
   }
 }
 
+// C_ij = C_ji for every i < j after a symmetric product: the tiles it skipped (wholly
+// right of the diagonal) and the upper parts of the diagonal tiles, whose entries were
+// computed directly and differ from their transposes by the rounding order of the
+// level->=3 accumulator.  Every source lies on or below the diagonal, in a computed
+// tile, and is never written here, so the result is exactly symmetric and the same for
+// every tiling.  One 32 x 32 block per CTA: grid (ceil(d/32), ceil(d/32), batch), blocks
+// below the diagonal return at once; 256 threads; DF32 storage (float4 per element).
+__global__ void __launch_bounds__(256)
+sym_mirror_kernel(int d, float4* __restrict__ C, long long sC4, const int* __restrict__ item_sq, int sq_step) {
+  const int i0 = blockIdx.y * 32, j0 = blockIdx.x * 32, b = blockIdx.z;
+  if (j0 < i0) return;
+  if (item_sq && item_sq[b] <= sq_step) return;
+  __shared__ float4 t[32][33];
+  float4* Cb = C + b * sC4;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  for (int r = ty; r < 32; r += 8) {   // source rows j0 + r, columns i0 + tx
+    const int si = j0 + r, sj = i0 + tx;
+    if (si < d && sj < d) t[r][tx] = Cb[(long long)si * d + sj];
+  }
+  __syncthreads();
+  for (int r = ty; r < 32; r += 8) {
+    const int di = i0 + r, dj = j0 + tx;
+    if (di < dj && dj < d) Cb[(long long)di * d + dj] = t[tx][r];
+  }
+}
+
 // ---------------------------------------------------------------------------
 // host side: tensor maps, launches, workspace
 // ---------------------------------------------------------------------------
@@ -1131,19 +1160,23 @@ static int launch_split_gemm_LC(const SplitGeom& g, int batch, const __nv_bfloat
   return launch_split_gemm_LB<L, 32, false, CTAS>(g, batch, Ad, ea, Bd, eb, C, sC, epi, status, ctl, s);
 }
 
+// Whether a product runs on CTA pairs.  By default pairs run from 5 digits (measured at 6:
+// +3% at d = 729, +7% at d = 4096, +6% at d = 256; with 2-4 digits 2-4% slower) where the
+// row tiles pair up evenly from d = 256 on, or are 7 or more (an odd count leaves the last
+// pair's second CTA multiplying zeros: -19% at d = 300, three tiles).  A product with a
+// zero part of B runs N = 64 MMAs on one CTA per tile.
+static bool split_uses_pairs(const SplitGeom& g, const SplitCtl& ctl) {
+  const int mtiles = g.Mp / SG_BM;
+  const bool shape_ok = (mtiles % 2 == 0) ? g.d >= 256 : mtiles >= 7;
+  const bool bstruct = ctl.b_zero == 1 || ctl.b_zero == 2;
+  return mtiles >= 2 && !bstruct && (ctl.cta_pairs > 0 || (ctl.cta_pairs < 0 && g.L >= 5 && shape_ok));
+}
+
 template <int L>
 static int launch_split_gemm_L(const SplitGeom& g, int batch, const __nv_bfloat16* Ad, const int* ea,
                                const __nv_bfloat16* Bd, const int* eb, double* C, long long sC,
                                const SplitEpi& epi, int* status, const SplitCtl& ctl, cudaStream_t s) {
-  // By default pairs run from 5 digits (measured at 6: +3% at d = 729, +7% at d = 4096,
-  // +6% at d = 256; with 2-4 digits 2-4% slower) where the row tiles pair up evenly from
-  // d = 256 on, or are 7 or more (an odd count leaves the last pair's second CTA
-  // multiplying zeros: -19% at d = 300, three tiles).
-  const int mtiles = g.Mp / SG_BM;
-  const bool shape_ok = (mtiles % 2 == 0) ? g.d >= 256 : mtiles >= 7;
-  // a product with a zero part of B runs N = 64 MMAs on one CTA per tile
-  const bool bstruct = ctl.b_zero == 1 || ctl.b_zero == 2;
-  const bool pair = mtiles >= 2 && !bstruct && (ctl.cta_pairs > 0 || (ctl.cta_pairs < 0 && L >= 5 && shape_ok));
+  const bool pair = split_uses_pairs(g, ctl);
   if constexpr (L % 2 == 0) {
     if (paired_layout(g, ctl)) {
       // pairs = 2: 32-deep stages of 128-byte rows where two stages fit, else 16-deep
@@ -1249,16 +1282,21 @@ int split_gemm(int d, int L, int batch, const void* abuf, const void* bbuf, doub
   for (int m = 0; m < 3; ++m) { e.add_src[m] = add.src[m]; e.add_coef[m] = df_from_double(add.coef[m]); }
   e.add_stride = add.stride;
   e.diag = df_from_double(add.diag);
+  int r = MG_EINVAL;
   switch (L) {
-    case 2: return launch_split_gemm_L<2>(g, batch, Ad, ea, Bd, eb, C, sC, e, status, ctl, s);
-    case 3: return launch_split_gemm_L<3>(g, batch, Ad, ea, Bd, eb, C, sC, e, status, ctl, s);
-    case 4: return launch_split_gemm_L<4>(g, batch, Ad, ea, Bd, eb, C, sC, e, status, ctl, s);
-    case 5: return launch_split_gemm_L<5>(g, batch, Ad, ea, Bd, eb, C, sC, e, status, ctl, s);
-    case 6: return launch_split_gemm_L<6>(g, batch, Ad, ea, Bd, eb, C, sC, e, status, ctl, s);
-    case 7: return launch_split_gemm_L<7>(g, batch, Ad, ea, Bd, eb, C, sC, e, status, ctl, s);
-    case 8: return launch_split_gemm_L<8>(g, batch, Ad, ea, Bd, eb, C, sC, e, status, ctl, s);
+    case 2: r = launch_split_gemm_L<2>(g, batch, Ad, ea, Bd, eb, C, sC, e, status, ctl, s); break;
+    case 3: r = launch_split_gemm_L<3>(g, batch, Ad, ea, Bd, eb, C, sC, e, status, ctl, s); break;
+    case 4: r = launch_split_gemm_L<4>(g, batch, Ad, ea, Bd, eb, C, sC, e, status, ctl, s); break;
+    case 5: r = launch_split_gemm_L<5>(g, batch, Ad, ea, Bd, eb, C, sC, e, status, ctl, s); break;
+    case 6: r = launch_split_gemm_L<6>(g, batch, Ad, ea, Bd, eb, C, sC, e, status, ctl, s); break;
+    case 7: r = launch_split_gemm_L<7>(g, batch, Ad, ea, Bd, eb, C, sC, e, status, ctl, s); break;
+    case 8: r = launch_split_gemm_L<8>(g, batch, Ad, ea, Bd, eb, C, sC, e, status, ctl, s); break;
   }
-  return MG_EINVAL;
+  if (r != MG_OK || !ctl.sym_out) return r;
+  const int nb = ceil_div(d, 32);
+  sym_mirror_kernel<<<dim3(nb, nb, batch), 256, 0, s>>>(d, reinterpret_cast<float4*>(C), sC / 2, ctl.item_sq,
+                                                        ctl.sq_step);
+  return check_launch("sym_mirror_kernel");
 }
 
 // ---------------------------------------------------------------------------

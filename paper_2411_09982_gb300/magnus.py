@@ -218,9 +218,11 @@ class Context:
         """True / False, or None for the library's choice by digit count."""
         _check(load().mg_ctx_set_cta_pairs(self.h, -1 if on is None else (1 if on else 0)), "mg_ctx_set_cta_pairs")
 
-    def set_structure(self, on):
-        """True (default): split products skip the exactly-zero parts of real operators' powers."""
-        _check(load().mg_ctx_set_structure(self.h, 1 if on else 0), "mg_ctx_set_structure")
+    def set_structure(self, mode):
+        """Split products of real operators: bit 0 skips the exactly-zero parts of X's powers,
+        bit 1 the tiles above the diagonal of symmetric results; True = 3 (default), False = 0."""
+        mode = 3 if mode is True else (0 if mode is False else int(mode))
+        _check(load().mg_ctx_set_structure(self.h, mode), "mg_ctx_set_structure")
 
     def set_wait_limit(self, seconds=4.0, stall_test=False):
         _check(load().mg_ctx_set_wait_limit(self.h, float(seconds), 1 if stall_test else 0), "mg_ctx_set_wait_limit")

@@ -1,13 +1,16 @@
-"""Split products that leave out the exactly-zero parts of real operators' powers.
+"""Split products that use the structure of real operators (mg_ctx_set_structure).
 
 With real operators (H0 and b + b^dag drives in a real basis) every first-order Hbar_n is
 real (Eq. magnus-first-order-term with real coefficients c_{k,n}), so the exponent
 X_n = -i 2^-s (Hbar_n - tau_n I) is purely imaginary, X^2 and X^6 are real and X^3 is
-imaginary.  The products of these powers (mg_ctx_set_structure, on by default) skip the
-zero half of A's K axis and, where B has a zero part, multiply one B plane into one output
-half.  The skipped digit products are exact zeros: every result must equal the full
-product's, in every product configuration (one CTA or CTA pairs, stage depths, digit
-layouts, digit counts), and meet the oracle within the stated 1e-6.
+imaginary (bit 0: the products of these powers skip the zero half of A's K axis and, where
+B has a zero part, multiply one B plane into one output half), and with real symmetric
+operators every polynomial in X is complex symmetric (bit 1: the products of the
+exponential compute the tiles on and below the diagonal and mirror the rest).  The digit
+products bit 0 skips are exact zeros: those results must equal the full products' in every
+product configuration (one CTA or CTA pairs, stage depths, digit layouts, digit counts).
+With bit 1 every U_n is exactly symmetric and every result meets the oracle within the
+stated 1e-6.
 """
 import numpy as np
 import pytest
@@ -33,18 +36,19 @@ def ctx():
     c.close()
 
 
-def _evolve(ctx, wl, structure, L=6, taylor=None, order=1):
+def _evolve(ctx, wl, structure, L=6, taylor=None, order=1, N=None):
     """One mg_evolve of the workload; returns (result, report, counted gemm flops)."""
     ctx.set_structure(structure)
     ctx.enable_gemm_timing(True)
     ctx.gemm_stats(reset=True)
-    samples, w = M.node_samples(wl)
+    N = wl.N if N is None else N
+    samples, w = M.node_samples(wl, N)
     p = M.Plan(ctx, cuda(wl.H0), cuda(wl.Hk), M.MG_PREC_SPLIT, L)
     if order != 1:
         p.set_magnus_order(order)
     if taylor is not None:
         p.set_taylor(taylor)
-    p.set_controls(wl.N, wl.P, wl.t0, wl.dt, w, cuda(samples))
+    p.set_controls(N, wl.P, wl.t0, wl.dt, w, cuda(samples))
     if wl.psi0 is None:
         out = torch.empty((wl.d, wl.d), dtype=torch.complex128, device="cuda")
         rep = p.evolve(M.MG_OUT_PROPAGATOR, None, out)
@@ -86,8 +90,9 @@ def test_structured_products_equal_full_products(ctx, L, stage_k, digit_pairs, c
     ctx.set_digit_pairs(digit_pairs)
     ctx.set_cta_pairs(cta_pairs)
     try:
-        on, rep_on, f_on = _evolve(ctx, wl, True, L)
-        off, rep_off, f_off = _evolve(ctx, wl, False, L)
+        on, rep_on, f_on = _evolve(ctx, wl, 1, L)
+        off, rep_off, f_off = _evolve(ctx, wl, 0, L)
+        sym, rep_sym, f_sym = _evolve(ctx, wl, 3, L)
     finally:
         _restore(ctx)
     assert np.array_equal(on, off), np.abs(on - off).max()
@@ -97,35 +102,67 @@ def test_structured_products_equal_full_products(ctx, L, stage_k, digit_pairs, c
         assert f_on == pytest.approx(f_off - 18.0 * wl.d ** 3 * wl.N, rel=1e-12)
     else:
         assert f_on < f_off
+    assert f_sym < f_on
     # the oracle bound from six digits (this job's ||Hbar_n||_1 ~ 1e3 takes ten squarings,
     # which five digits' 35 bits do not carry to 1e-6)
     if L >= 6:
         ref = oracle.evolve_workload(wl)
-        err = np.abs(on - ref).max()
-        assert err <= 1e-6, err
+        for got in (on, sym):
+            err = np.abs(got - ref).max()
+            assert err <= 1e-6, err
+
+
+_SYM_BY_TILING = {}
+
+
+@pytest.mark.parametrize("cta_pairs", [False, True])
+def test_symmetric_products_give_exactly_symmetric_exponentials(ctx, cta_pairs):
+    """One interval: U_0 = exp(-i Hbar_0) is complex symmetric; with bit 1 every product of
+    its exponential copies the entries above the diagonal from below it, so U_0 = U_0^T
+    exactly, the same on single CTAs and CTA pairs, and it differs from the full
+    products' U_0 by their rounding only."""
+    wl = W.transmon_resonator(**_D300)
+    ctx.set_cta_pairs(cta_pairs)
+    try:
+        sym, _, f_sym = _evolve(ctx, wl, 3, N=1)
+        full, _, f_full = _evolve(ctx, wl, 0, N=1)
+    finally:
+        _restore(ctx)
+    assert np.array_equal(sym, sym.T)
+    _SYM_BY_TILING[cta_pairs] = sym
+    if len(_SYM_BY_TILING) == 2:
+        assert np.array_equal(_SYM_BY_TILING[False], _SYM_BY_TILING[True])
+    assert np.abs(sym - full).max() <= 1e-9, np.abs(sym - full).max()
+    assert f_sym < 0.6 * f_full
+    ref = oracle.evolve_workload(wl, n_intervals=1)
+    assert np.abs(sym - ref).max() <= 1e-8
 
 
 def test_state_workload_and_trace(ctx):
     """The d = 30 workload (state output) and the report agree with and without skipping."""
     wl = W.config(0, N=200)
-    on, rep_on, f_on = _evolve(ctx, wl, True)
-    off, rep_off, f_off = _evolve(ctx, wl, False)
+    on, rep_on, f_on = _evolve(ctx, wl, 1)
+    off, rep_off, f_off = _evolve(ctx, wl, 0)
+    sym, rep_sym, f_sym = _evolve(ctx, wl, 3)
     assert np.array_equal(on, off)
-    assert rep_on["max_squarings"] == rep_off["max_squarings"]
-    assert f_on < f_off
+    assert rep_on["max_squarings"] == rep_off["max_squarings"] == rep_sym["max_squarings"]
+    assert f_sym < f_on < f_off
     ref = oracle.evolve_workload(wl)
     assert np.abs(on - ref).max() <= 1e-6
+    assert np.abs(sym - ref).max() <= 1e-6
 
 
 def test_paterson_stockmeyer_powers(ctx):
     """The Paterson-Stockmeyer forms' powers X^j = X^{j-1} X skip too (MG_TAYLOR_PS)."""
     wl = W.transmon_resonator(nt=4, nr=36, N=10, T=5.0, sigma=2.0, omega0=0.2, unitary=True, name="tr144")
-    on, _, f_on = _evolve(ctx, wl, True, taylor=M.MG_TAYLOR_PS)
-    off, _, f_off = _evolve(ctx, wl, False, taylor=M.MG_TAYLOR_PS)
+    on, _, f_on = _evolve(ctx, wl, 1, taylor=M.MG_TAYLOR_PS)
+    off, _, f_off = _evolve(ctx, wl, 0, taylor=M.MG_TAYLOR_PS)
+    sym, _, f_sym = _evolve(ctx, wl, 3, taylor=M.MG_TAYLOR_PS)
     assert np.array_equal(on, off)
-    assert f_on < f_off
+    assert f_sym < f_on < f_off
     ref = oracle.evolve_workload(wl)
     assert np.abs(on - ref).max() <= 1e-6
+    assert np.abs(sym - ref).max() <= 1e-6
 
 
 def test_complex_operators_take_full_products(ctx):
@@ -137,8 +174,8 @@ def test_complex_operators_take_full_products(ctx):
     low = np.tril(Hk[0], -1)
     Hk[0] = 1j * (low - low.T)
     wl = W.Workload("tr120y", base.H0, Hk, base.drive, base.t0, base.T, base.N, base.P, None)
-    on, _, f_on = _evolve(ctx, wl, True)
-    off, _, f_off = _evolve(ctx, wl, False)
+    on, _, f_on = _evolve(ctx, wl, 3)
+    off, _, f_off = _evolve(ctx, wl, 0)
     assert f_on == f_off
     assert np.array_equal(on, off)
     ref = oracle.evolve_workload(wl)
@@ -148,8 +185,8 @@ def test_complex_operators_take_full_products(ctx):
 def test_second_order_term_takes_full_products(ctx):
     """The second-order term adds -(i/2)[H_j, H_k] (imaginary for real operators): full products."""
     wl = W.transmon_resonator(nt=3, nr=12, N=20, T=10.0, sigma=3.0, omega0=0.1, name="tr36")
-    on, _, f_on = _evolve(ctx, wl, True, order=2)
-    off, _, f_off = _evolve(ctx, wl, False, order=2)
+    on, _, f_on = _evolve(ctx, wl, 3, order=2)
+    off, _, f_off = _evolve(ctx, wl, 0, order=2)
     assert f_on == f_off
     assert np.array_equal(on, off)
 
@@ -161,7 +198,7 @@ def test_batch_of_real_plans(ctx):
     jobs = [W.random_instance(rng, name=f"j{i}", N_range=(10, 30), d_range=(40, 200)) for i in range(5)]
     jobs[1].psi0 = None
     results = {}
-    for structure in (True, False):
+    for structure in (1, 0, 3):
         ctx.set_structure(structure)
         plans, outs, ins, kinds = [], [], [], []
         for wl in jobs:
@@ -183,15 +220,16 @@ def test_batch_of_real_plans(ctx):
         results[structure] = [o.cpu().numpy() for o in outs]
         for p in plans:
             p.close()
-    ctx.set_structure(True)
-    for wl, a, b in zip(jobs, results[True], results[False]):
+    ctx.set_structure(3)
+    for wl, a, b, c in zip(jobs, results[1], results[0], results[3]):
         assert np.array_equal(a, b), wl.name
         ref = oracle.evolve_workload(wl)
         assert np.abs(a - ref).max() <= 1e-6, wl.name
+        assert np.abs(c - ref).max() <= 1e-6, wl.name
 
 
 def test_structure_option_rejects_other_values(ctx):
-    for bad in (-1, 2):
+    for bad in (-1, 4):
         with pytest.raises(M.MagnusError) as e:
             M._check(M.load().mg_ctx_set_structure(ctx.h, bad), "mg_ctx_set_structure")
         assert e.value.code == M.MG_EINVAL
