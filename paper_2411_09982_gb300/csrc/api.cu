@@ -406,6 +406,26 @@ struct Engine {
     return split_slice_b(d, L, batch, B, sB, in_df, bbuf[slot], ctx->stream, ctl());
   }
   int prepA(int batch, const double* A, long long sA) { return prepA(batch, A, sA, df() ? 1 : 0); }
+  // Digits of an operand that is a polynomial in X: as A (slot < 0: not as B), as B into
+  // `slot`, or both in one pass.  With X symmetric (x_sym) the matrix is symmetric and is
+  // sliced by rows for both operands; part (1: its real part is zero, 2: its imaginary
+  // part is; 0: general) leaves unwritten what the products of zero-part skipping never
+  // read (the zero half of A's K axis; the zero plane of B, or both -Im and Im planes of
+  // a real B).  Otherwise the general slicers.
+  int prep_poly(bool as_a, int slot, int batch, const double* M, int part) {
+    if (prec != MG_PREC_SPLIT) return MG_OK;
+    if (!(x_sym && (ctx->structure & 2))) {
+      if (as_a) MG_TRY(prepA(batch, M, mat_doubles_(), 1));
+      if (slot >= 0) MG_TRY(prepB(slot, batch, M, mat_doubles_(), 1));
+      return MG_OK;
+    }
+    const int p = (x_imag && (ctx->structure & 1)) ? part : 0;
+    const int askip = p;                                  // bit 0: real half, bit 1: imaginary half
+    const int bskip = p == 1 ? 2 : (p == 2 ? 1 | 4 : 0);  // bit q: plane q (-Im, Re, Im)
+    return split_slice_sym(d, L, batch, M, mat_doubles_(), 1, as_a ? abuf : nullptr, askip,
+                           slot >= 0 ? bbuf[slot] : nullptr, bskip, ctx->stream, ctl());
+  }
+  long long mat_doubles_() const { return 2LL * d * d; }
   int prepB(int slot, int batch, const double* B, long long sB) { return prepB(slot, batch, B, sB, df() ? 1 : 0); }
   // elementwise steps in the engine's storage format
   int lincomb(int batch, double* dst, int n, const double* const* src, const double* coef, double diag) {
@@ -519,16 +539,14 @@ int taylor_poly(mg_ctx* ctx, Engine& eng, int batch, double* W, const TaylorChoi
   if (tc.p == 0) {
     // degree 18 in five products: A2, A3, A6, A9 = B1 B5 + B4, T = B2 + (B3 + A9) A9
     AddTerms none;
-    MG_TRY(eng.prepA(batch, X, md));
-    MG_TRY(eng.prepB(0, batch, X, md));
     // with X imaginary: A2 and A6 real, A3 imaginary
+    MG_TRY(eng.prep_poly(true, 0, batch, X, 1));
     eng.set_structure(1, 1);
     MG_TRY(eng.mul(batch, X, md, 0, X, md, P2, md, none));        // A2
-    MG_TRY(eng.prepA(batch, P2, md));
+    MG_TRY(eng.prep_poly(true, -1, batch, P2, 2));
     eng.set_structure(2, 1);
     MG_TRY(eng.mul(batch, P2, md, 0, X, md, P3, md, none));       // A3
-    MG_TRY(eng.prepA(batch, P3, md));
-    MG_TRY(eng.prepB(1, batch, P3, md));
+    MG_TRY(eng.prep_poly(true, 1, batch, P3, 1));
     eng.set_structure(1, 1);
     MG_TRY(eng.mul(batch, P3, md, 1, P3, md, Y, md, none));       // A6
     // B1 -> R0, B5 -> R1, B4 -> P2, B3 -> P3, B2 -> Y (in place over A2, A3, A6)
@@ -545,8 +563,8 @@ int taylor_poly(mg_ctx* ctx, Engine& eng, int batch, double* W, const TaylorChoi
     add4.coef[0] = 1.0;
     add4.stride = md;
     add4.diag = 0.0;
-    MG_TRY(eng.prepA(batch, R0, md));
-    MG_TRY(eng.prepB(0, batch, R1, md));
+    MG_TRY(eng.prep_poly(true, -1, batch, R0, 0));
+    MG_TRY(eng.prep_poly(false, 0, batch, R1, 0));
     eng.set_sym();
     MG_TRY(eng.mul(batch, R0, md, 0, R1, md, W, md, add4));       // A9 (over X)
     {
@@ -560,8 +578,8 @@ int taylor_poly(mg_ctx* ctx, Engine& eng, int batch, double* W, const TaylorChoi
     add2.coef[0] = 1.0;
     add2.stride = md;
     add2.diag = 0.0;
-    MG_TRY(eng.prepA(batch, P3, md));
-    MG_TRY(eng.prepB(1, batch, W, md));
+    MG_TRY(eng.prep_poly(true, -1, batch, P3, 0));
+    MG_TRY(eng.prep_poly(false, 1, batch, W, 0));
     eng.set_sym();
     MG_TRY(eng.mul(batch, P3, md, 1, W, md, R0, md, add2));       // T
     R = R0;
@@ -579,9 +597,9 @@ int taylor_poly(mg_ctx* ctx, Engine& eng, int batch, double* W, const TaylorChoi
   const double* P[5] = {nullptr, X, nullptr, nullptr, nullptr};
   double* pow_buf[5] = {nullptr, nullptr, P2, P3, nullptr};
   pow_buf[p] = Y;
-  MG_TRY(eng.prepB(0, batch, X, md));
+  MG_TRY(eng.prep_poly(false, 0, batch, X, 1));
   for (int j = 2; j <= p; ++j) {
-    MG_TRY(eng.prepA(batch, P[j - 1], md));
+    MG_TRY(eng.prep_poly(true, -1, batch, P[j - 1], (j - 1) % 2 == 1 ? 1 : 2));
     AddTerms none;
     eng.set_structure((j - 1) % 2 == 1 ? 1 : 2, 1);   // X^{j-1} imaginary for odd j - 1, else real
     MG_TRY(eng.mul(batch, P[j - 1], md, 0, X, md, pow_buf[j], md, none));
@@ -601,14 +619,14 @@ int taylor_poly(mg_ctx* ctx, Engine& eng, int batch, double* W, const TaylorChoi
     MG_TRY(eng.lincomb(batch, R, ns, src, cf, diag));
     i_next = top - 1;
   }
-  if (i_next >= 0) MG_TRY(eng.prepB(1, batch, P[p], md));
+  if (i_next >= 0) MG_TRY(eng.prep_poly(false, 1, batch, P[p], 0));   // full products: every plane
   for (int i = i_next; i >= 0; --i) {
     AddTerms add;
     add.n = 0;
     for (int j = 1; j < p; ++j) { add.src[add.n] = P[j]; add.coef[add.n] = coef(i * p + j); ++add.n; }
     add.stride = md;
     add.diag = coef(i * p);
-    MG_TRY(eng.prepA(batch, R, md));
+    MG_TRY(eng.prep_poly(true, -1, batch, R, 0));
     eng.set_sym();
     MG_TRY(eng.mul(batch, R, md, 1, P[p], md, Rn, md, add));
     std::swap(R, Rn);
@@ -663,8 +681,7 @@ int expm_chunk(mg_ctx* ctx, Engine& eng, int batch, double* W, const double* tau
   MG_TRY(taylor_poly(ctx, eng, batch, W, tc, &R, &Rn));
   // squarings
   for (int k = 0; k < tc.s; ++k) {
-    MG_TRY(eng.prepA(batch, R, md));
-    MG_TRY(eng.prepB(0, batch, R, md));
+    MG_TRY(eng.prep_poly(true, 0, batch, R, 0));
     AddTerms none;
     eng.set_sym();
     MG_TRY(eng.mul(batch, R, md, 0, R, md, Rn, md, none));
@@ -695,8 +712,7 @@ int expm_chunk_dev(mg_ctx* ctx, Engine& eng, int batch, double* W, const double*
     for (int k = 0; k < S; ++k) {
       eng.item_sq = sq_dev;
       eng.sq_step = k;
-      int r = eng.prepA(batch, R, md);
-      if (r == MG_OK) r = eng.prepB(0, batch, R, md);
+      int r = eng.prep_poly(true, 0, batch, R, 0);
       eng.set_sym();
       if (r == MG_OK) r = eng.mul(batch, R, md, 0, R, md, R, md, none);
       eng.item_sq = nullptr;

@@ -173,6 +173,8 @@ int split_slice_a(int d, int L, int batch, const double* A, long long sA, int in
                   const SplitCtl& ctl = SplitCtl());
 int split_slice_b(int d, int L, int batch, const double* B, long long sB, int in_df32, void* buf, cudaStream_t s,
                   const SplitCtl& ctl = SplitCtl());
+int split_slice_sym(int d, int L, int batch, const double* M, long long sM, int in_df32, void* abuf, int askip,
+                    void* bbuf, int bskip, cudaStream_t s, const SplitCtl& ctl = SplitCtl());
 int split_gemm(int d, int L, int batch, const void* abuf, const void* bbuf, double* C, long long sC,
                const AddTerms& add, int* status, cudaStream_t s, const SplitCtl& ctl = SplitCtl());
 

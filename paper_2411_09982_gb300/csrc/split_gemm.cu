@@ -261,6 +261,87 @@ slice_a_kernel(int d, int Kp, int Mp, int beta, const double* __restrict__ A, lo
   }
 }
 
+// Digits of a complex symmetric matrix M (M = M^T) by rows, as the A operand, the B
+// operand or both: column j of M is its row j, so the column exponent of B equals the
+// row exponent of A and B's plane rows are M's rows (plane 0: -Im, 1: Re, 2: Im).  One
+// warp per row as in slice_a_kernel; one read of M serves both operands, with no column
+// pass.  askip (bit 0: the real half, bit 1: the imaginary half of A's K axis) and bskip
+// (bit p: plane p of B) name parts that are not written because no product reads them:
+// the zero parts of a real or imaginary operand, which the products skip.
+// grid (ceil(Mp/8), batch), block 256.
+template <int L, typename T>
+__global__ void __launch_bounds__(256, 3)
+slice_sym_kernel(int d, int Kp, int Mp, int beta, const double* __restrict__ M, long long sM,
+                 __nv_bfloat16* __restrict__ aout, int* __restrict__ ea, long long a_item_elems, int askip,
+                 __nv_bfloat16* __restrict__ bout, int* __restrict__ eb, long long b_item_elems, int brows,
+                 int bskip, const int* __restrict__ item_sq, int sq_step, int pairs) {
+  using E_ = Elem<T>;
+  const int lane = threadIdx.x & 31;
+  const int row = blockIdx.x * 8 + (threadIdx.x >> 5);
+  const int b = blockIdx.y;
+  if (row >= d) return;   // rows d..Mp (and d..brows) are never read: the tensor maps end at row d
+  if (item_sq && item_sq[b] <= sq_step) return;
+  const int Kh = Kp / 2;
+  const double* a = M + b * sM;
+  const long long r0 = (long long)row * d;
+  int E = -(1 << 29);
+  for (int k = lane; k < d; k += 32) {
+    const auto v = E_::load(a, r0 + k);
+    E = max(E, max(exp_bound(v.re), exp_bound(v.im)));
+  }
+  for (int o2 = 16; o2 > 0; o2 >>= 1) E = max(E, __shfl_xor_sync(0xffffffffu, E, o2));
+  if (E < -(1 << 28)) E = 0;   // all-zero row
+  if (lane == 0) {
+    if (aout) ea[(long long)b * Mp + row] = E;
+    if (bout) eb[(long long)b * brows + row] = E;
+  }
+  __nv_bfloat16* oa = aout ? aout + (long long)b * a_item_elems : nullptr;
+  __nv_bfloat16* ob = bout ? bout + (long long)b * b_item_elems : nullptr;
+  // digit s of an element lies (s >> 1) * S2 + (s & 1) * S1 past digit 0 (both layouts)
+  const long long a_s1 = pairs ? 16 : (long long)Mp * Kp, a_s2 = pairs ? 2LL * Mp * Kp : 2 * a_s1;
+  const long long b_s1 = pairs ? 16 : 3LL * brows * Kh, b_s2 = pairs ? 6LL * brows * Kh : 2 * b_s1;
+  const Pow2Pair f = pow2_pair(beta - 1 - E);
+  for (int k = 4 * lane; k < Kh; k += 128) {
+    df32 re[4], im[4];   // the 4 elements, scaled (zero beyond d)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      re[q] = im[q] = df32{0.f, 0.f};
+      if (k + q < d) {
+        const auto v = E_::load(a, r0 + k + q);
+        re[q] = scaled_pair(v.re, f);
+        im[q] = scaled_pair(v.im, f);
+      }
+    }
+    uint32_t r01[L], r23[L], i01[L], i23[L];
+    digits_pair<L>(re[0], re[1], beta, r01);
+    digits_pair<L>(re[2], re[3], beta, r23);
+    digits_pair<L>(im[0], im[1], beta, i01);
+    digits_pair<L>(im[2], im[3], beta, i23);
+    if (oa) {
+      __nv_bfloat16* pr = oa + a_digit_off(pairs, 0, row, k, Mp, Kp);
+      __nv_bfloat16* pi = oa + a_digit_off(pairs, 0, row, Kh + k, Mp, Kp);
+#pragma unroll
+      for (int s = 0; s < L; ++s) {
+        const long long o = (s >> 1) * a_s2 + (s & 1) * a_s1;
+        if (!(askip & 1)) *reinterpret_cast<uint2*>(pr + o) = make_uint2(r01[s], r23[s]);
+        if (!(askip & 2)) *reinterpret_cast<uint2*>(pi + o) = make_uint2(i01[s], i23[s]);
+      }
+    }
+    if (ob) {
+      __nv_bfloat16* p0 = ob + b_digit_off(pairs, 0, 0, row, k, brows, Kh);
+      const long long plane = pairs ? 2LL * brows * Kh : (long long)brows * Kh;
+#pragma unroll
+      for (int s = 0; s < L; ++s) {
+        const long long o = (s >> 1) * b_s2 + (s & 1) * b_s1;
+        const uint2 wi = make_uint2(i01[s], i23[s]);
+        if (!(bskip & 1)) *reinterpret_cast<uint2*>(p0 + o) = neg4(wi);
+        if (!(bskip & 2)) *reinterpret_cast<uint2*>(p0 + o + plane) = make_uint2(r01[s], r23[s]);
+        if (!(bskip & 4)) *reinterpret_cast<uint2*>(p0 + o + 2 * plane) = wi;
+      }
+    }
+  }
+}
+
 // B digits: for every digit, three planes of K-major rows in the order
 // -Im B, Re B, Im B: row j of a plane holds column j of that part of B along k
 // (Kh = Kp / 2 entries, zero beyond d); rows j >= d up to Np / 2 are zero.  The
@@ -622,17 +703,14 @@ split_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
   uint64_t* never = accfull + 1;   // no thread ever arrives here (the stall test waits on it)
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(never + 1);
   int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
-  int* eb_s = abort_flag + 1;   // column exponents of this tile's 64 columns
-  int* epi_flag = eb_s + SG_BNC;  // epilogue verdict (accumulators ready and no abort)
+  int* eb_s = abort_flag + 1;   // column exponents of this tile's 64 (real mode: 128) columns
+  int* epi_flag = eb_s + 2 * SG_BNC;  // epilogue verdict (accumulators ready and no abort)
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   // a CTA pair lies along x of the grid (clusters of 2 x 1 x 1): row tiles on x there
   const int nt = CTAS == 2 ? blockIdx.y : blockIdx.x, mt = CTAS == 2 ? blockIdx.x : blockIdx.y, b = blockIdx.z;
   // uniform over the CTA (and over a CTA pair, which shares b): no cluster barrier is reached
   if (ctl.item_sq && ctl.item_sq[b] <= ctl.sq_step) return;
-  // a symmetric product computes no tile (of a CTA pair: no pair of tiles) whose columns
-  // all lie right of all its rows; split_gemm mirrors those from below the diagonal
-  if (ctl.sym_out && nt * SG_BNC >= (CTAS == 2 ? ((mt | 1) + 1) : (mt + 1)) * SG_BM) return;
   const uint32_t crank = CTAS == 2 ? cluster_rank() : 0u;
   const bool leader = crank == 0;
   const int num_k = Kp / BK;
@@ -640,8 +718,21 @@ split_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
   // operand structure (uniform over the launch; see SplitCtl): the K stages [kbeg, kend)
   // are loaded and multiplied; bz != 0 (one CTA per tile only) selects N = 64 products
   const int az = ctl.a_zero == 3 ? 0 : ctl.a_zero;
-  const int bz = (CTAS == 1 && ctl.b_zero != 3) ? ctl.b_zero : 0;
+  const int bzr = ctl.b_zero == 3 ? 0 : ctl.b_zero;
+  const int bz = CTAS == 1 ? bzr : 0;
   const int kbeg = (az & 1) ? nkh : 0, kend = (az & 2) ? nkh : num_k;
+  // Real mode (CTA pairs, both operands with a zero part): the one active half of K times
+  // the one B plane it meets is a single real product into one output half (rh: 0 Re C,
+  // 1 Im C).  The pair's M = 256 x N = 128 MMAs then cover 128 output columns of that half:
+  // each CTA loads 64 rows of the plane, tiles are 128 complex columns wide (TNC), and the
+  // epilogue writes them in two passes of 64 with the other half zero.
+  const bool real_mode = CTAS == 2 && az != 0 && bzr != 0;
+  const int rh = (bzr & 2) ? (kbeg == nkh ? 1 : 0) : (kbeg == nkh ? 0 : 1);
+  const int TNC = real_mode ? 2 * SG_BNC : SG_BNC;
+  // a symmetric product computes no tile (of a CTA pair: no pair of tiles) whose columns
+  // all lie right of all its rows; split_gemm then copies the entries above the diagonal
+  if (ctl.sym_out && nt * TNC >= (CTAS == 2 ? ((mt | 1) + 1) : (mt + 1)) * SG_BM)
+    return;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -654,8 +745,8 @@ split_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
-  if (warp == 2 || warp == 3) {
-    const int c = (warp - 2) * 32 + lane, j = nt * SG_BNC + c;
+  if (warp >= 2 && warp < 2 + TNC / 32) {
+    const int c = (warp - 2) * 32 + lane, j = nt * TNC + c;
     eb_s[c] = j < d ? eb[(long long)b * (Np / 2) + j] : 0;
   }
   if (warp == 1) {
@@ -707,13 +798,17 @@ split_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
           // rank 0 expects the bytes of both CTAs; the copies of both signal its barrier
           if (leader) mbar_expect_tx(&full[s], 2 * STAGE_BYTES);
           const uint32_t bar = cluster_addr(&full[s], 0);
+          // the B rows this CTA loads: one plane of the tile's 64 columns each, or in real
+          // mode 64 of the tile's 128 columns of the one plane the active half of K meets
+          // (Re B where Im B = 0; else Im B for the real half of K, -Im B for the imaginary)
+          const int brow = real_mode ? nt * 2 * SG_BNC + SG_BNC * (int)crank : nt * SG_BNC;
+          const int bplane = real_mode ? ((bzr & 2) ? 1 : (imag ? 0 : 2)) : plane0 + (int)crank;
           if constexpr (PAIRS) {
             tma_load_4d_pair(st, &tmA, bar, 0, kb, mt * SG_BM, b * (L / 2));
-            tma_load_5d_pair(st + L * TILE_BYTES, &tmB, bar, 0, kbb, nt * SG_BNC, plane0 + (int)crank,
-                             b * (L / 2));
+            tma_load_5d_pair(st + L * TILE_BYTES, &tmB, bar, 0, kbb, brow, bplane, b * (L / 2));
           } else {
             tma_load_4d_pair(st, &tmA, bar, kb * BK, mt * SG_BM, 0, b);
-            tma_load_5d_pair(st + L * TILE_BYTES, &tmB, bar, kbb * BK, nt * SG_BNC, plane0 + (int)crank, 0, b);
+            tma_load_5d_pair(st + L * TILE_BYTES, &tmB, bar, kbb * BK, brow, bplane, 0, b);
           }
         } else if constexpr (PAIRS) {
           mbar_expect_tx(&full[s], STAGE_BYTES);
@@ -839,10 +934,10 @@ split_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
       // pull this tile's addend rows into L2 while phase 1 drains TMEM (8 x 128-byte
       // lines cover a row's 64 complex double-float values)
       if (epi.add_n > 0) {
-        const int et = threadIdx.x - 2 * 32;
-        for (int idx = et; idx < epi.add_n * SG_BM * 8; idx += SG_EPI_WARPS * 32) {
-          const int m = idx / (SG_BM * 8), rem = idx % (SG_BM * 8), rr = rem / 8, q = rem % 8;
-          const int grow = mt * SG_BM + rr, j = nt * SG_BNC + q * 8;
+        const int et = threadIdx.x - 2 * 32, lines = TNC / 8;
+        for (int idx = et; idx < epi.add_n * SG_BM * lines; idx += SG_EPI_WARPS * 32) {
+          const int m = idx / (SG_BM * lines), rem = idx % (SG_BM * lines), rr = rem / lines, q = rem % lines;
+          const int grow = mt * SG_BM + rr, j = nt * TNC + q * 8;
           if (grow < d && j < d) {
             const double* src = m == 0 ? epi.add_src[0] : (m == 1 ? epi.add_src[1] : epi.add_src[2]);
             const double* p = src + b * epi.add_stride + 4 * ((long long)grow * d + j);
@@ -850,8 +945,6 @@ split_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
           }
         }
       }
-      // phase 1 (thread = row): TMEM -> level combine -> double-float tile in shared memory
-      // (the stage ring is idle once every MMA has completed)
       float4* stile = reinterpret_cast<float4*>(smem);
       const int r = q * 32 + lane;                 // tile-local row
       const int row = mt * SG_BM + r;
@@ -864,73 +957,95 @@ split_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
         if (kbeg == 0) wr[(bz & 2) ? 0 : 1] = true;     // the real half of K was multiplied
         if (kend == num_k) wr[(bz & 2) ? 1 : 0] = true; // the imaginary half was
       }
-      constexpr int CW = 4;   // complex columns per step
-      for (int jc = c0; jc < c0 + SG_BNC / 2; jc += CW) {
-        uint32_t re_acc[SG_GROUPS][CW], im_acc[SG_GROUPS][CW];
-#pragma unroll
-        for (int g = 0; g < SG_GROUPS; ++g) {
-          if (wr[0]) tmem_ld4(lane_base + g * 128 + jc, re_acc[g]);
-          else re_acc[g][0] = re_acc[g][1] = re_acc[g][2] = re_acc[g][3] = 0u;
-          if (wr[1]) tmem_ld4(lane_base + g * 128 + SG_BNC + jc, im_acc[g]);
-          else im_acc[g][0] = im_acc[g][1] = im_acc[g][2] = im_acc[g][3] = 0u;
-        }
-        tmem_wait_ld();
-#pragma unroll
-        for (int jj = 0; jj < CW; ++jj) {
-          const int k = Ea + eb_s[jc + jj] + 2 - 2 * beta;
-          // levels that no digit pair reaches (L < 4) were never written: they hold
-          // whatever an earlier kernel left in TMEM and must not be read as data
-          const df32 re = combine_levels(re_acc[0][jj], L > 1 ? re_acc[1][jj] : 0u, L > 2 ? re_acc[2][jj] : 0u,
-                                         L > 3 ? re_acc[3][jj] : 0u, k);
-          const df32 im = combine_levels(im_acc[0][jj], L > 1 ? im_acc[1][jj] : 0u, L > 2 ? im_acc[2][jj] : 0u,
-                                         L > 3 ? im_acc[3][jj] : 0u, k);
-          stile[r * SG_EPI_PITCH + jc + jj] = make_float4(re.hi, re.lo, im.hi, im.lo);
-        }
-      }
-      tc_fence_before();
-      asm volatile("bar.sync 1, %0;" ::"n"(SG_EPI_WARPS * 32) : "memory");
-      // phase 2 (warp = row, lane = column): addends and coalesced row stores
       const float4* addp[3];
 #pragma unroll
       for (int m = 0; m < 3; ++m)
         addp[m] = epi.add_src[m] ? reinterpret_cast<const float4*>(epi.add_src[m] + b * epi.add_stride) : nullptr;
       float4* Cb = reinterpret_cast<float4*>(C + b * sC);
       const int ew = warp - 2;
-      // The warp's (row, half) items, EPI_GROUP at a time: every addend load of a group
-      // is issued before the first is used, so that a warp keeps several rows of loads
-      // in flight (one row at a time left the addend products latency-bound).
-      constexpr int HALVES = SG_BNC / 32;
-      constexpr int ITEMS = (SG_BM / SG_EPI_WARPS) * HALVES;
-      constexpr int EPI_GROUP = 4;
-      for (int i0 = 0; i0 < ITEMS; i0 += EPI_GROUP) {
-        float4 ad[EPI_GROUP][3];
-        long long offs[EPI_GROUP];
-        bool ok[EPI_GROUP];
+      // one pass per 64 output columns (two in real mode, whose TMEM columns all hold
+      // the one computed half)
+      for (int pass = 0; pass * SG_BNC < TNC; ++pass) {
+        const int cb = pass * SG_BNC;   // first tile column of this pass
+        if (pass > 0) asm volatile("bar.sync 1, %0;" ::"n"(SG_EPI_WARPS * 32) : "memory");   // stile free
+        // phase 1 (thread = row): TMEM -> level combine -> double-float tile in shared memory
+        // (the stage ring is idle once every MMA has completed)
+        constexpr int CW = 4;   // complex columns per step
+        for (int jc = c0; jc < c0 + SG_BNC / 2; jc += CW) {
+          uint32_t re_acc[SG_GROUPS][CW], im_acc[SG_GROUPS][CW];
 #pragma unroll
-        for (int u = 0; u < EPI_GROUP; ++u) {
-          const int it = i0 + u, rr = ew + SG_EPI_WARPS * (it / HALVES), c = (it % HALVES) * 32 + lane;
-          const int grow = mt * SG_BM + rr, j = nt * SG_BNC + c;
-          ok[u] = grow < d && j < d;
-          offs[u] = ok[u] ? (long long)grow * d + j : 0;
-#pragma unroll
-          for (int m = 0; m < 3; ++m)
-            ad[u][m] = (ok[u] && m < epi.add_n) ? addp[m][offs[u]] : make_float4(0.f, 0.f, 0.f, 0.f);
-        }
-#pragma unroll
-        for (int u = 0; u < EPI_GROUP; ++u) {
-          if (!ok[u]) continue;
-          const int it = i0 + u, rr = ew + SG_EPI_WARPS * (it / HALVES), c = (it % HALVES) * 32 + lane;
-          const float4 v = stile[rr * SG_EPI_PITCH + c];
-          df32 re{v.x, v.y}, im{v.z, v.w};
-#pragma unroll
-          for (int m = 0; m < 3; ++m) {
-            if (m < epi.add_n) {
-              re = df_add(re, df_mul(df32{ad[u][m].x, ad[u][m].y}, epi.add_coef[m]));
-              im = df_add(im, df_mul(df32{ad[u][m].z, ad[u][m].w}, epi.add_coef[m]));
+          for (int g = 0; g < SG_GROUPS; ++g) {
+            if (real_mode) {   // the computed half goes to re_acc first (moved below for rh = 1)
+              tmem_ld4(lane_base + g * 128 + cb + jc, re_acc[g]);
+              im_acc[g][0] = im_acc[g][1] = im_acc[g][2] = im_acc[g][3] = 0u;
+            } else {
+              if (wr[0]) tmem_ld4(lane_base + g * 128 + jc, re_acc[g]);
+              else re_acc[g][0] = re_acc[g][1] = re_acc[g][2] = re_acc[g][3] = 0u;
+              if (wr[1]) tmem_ld4(lane_base + g * 128 + SG_BNC + jc, im_acc[g]);
+              else im_acc[g][0] = im_acc[g][1] = im_acc[g][2] = im_acc[g][3] = 0u;
             }
           }
-          if (mt * SG_BM + rr == nt * SG_BNC + c) re = df_add(re, epi.diag);
-          Cb[offs[u]] = make_float4(re.hi, re.lo, im.hi, im.lo);
+          tmem_wait_ld();
+          if (real_mode && rh == 1) {
+#pragma unroll
+            for (int g = 0; g < SG_GROUPS; ++g)
+#pragma unroll
+              for (int jj = 0; jj < CW; ++jj) {
+                im_acc[g][jj] = re_acc[g][jj];
+                re_acc[g][jj] = 0u;
+              }
+          }
+#pragma unroll
+          for (int jj = 0; jj < CW; ++jj) {
+            const int k = Ea + eb_s[cb + jc + jj] + 2 - 2 * beta;
+            // levels that no digit pair reaches (L < 4) were never written: they hold
+            // whatever an earlier kernel left in TMEM and must not be read as data
+            const df32 re = combine_levels(re_acc[0][jj], L > 1 ? re_acc[1][jj] : 0u, L > 2 ? re_acc[2][jj] : 0u,
+                                           L > 3 ? re_acc[3][jj] : 0u, k);
+            const df32 im = combine_levels(im_acc[0][jj], L > 1 ? im_acc[1][jj] : 0u, L > 2 ? im_acc[2][jj] : 0u,
+                                           L > 3 ? im_acc[3][jj] : 0u, k);
+            stile[r * SG_EPI_PITCH + jc + jj] = make_float4(re.hi, re.lo, im.hi, im.lo);
+          }
+        }
+        tc_fence_before();
+        asm volatile("bar.sync 1, %0;" ::"n"(SG_EPI_WARPS * 32) : "memory");
+        // phase 2 (warp = row, lane = column): addends and coalesced row stores
+        // The warp's (row, half) items, EPI_GROUP at a time: every addend load of a group
+        // is issued before the first is used, so that a warp keeps several rows of loads
+        // in flight (one row at a time left the addend products latency-bound).
+        constexpr int HALVES = SG_BNC / 32;
+        constexpr int ITEMS = (SG_BM / SG_EPI_WARPS) * HALVES;
+        constexpr int EPI_GROUP = 4;
+        for (int i0 = 0; i0 < ITEMS; i0 += EPI_GROUP) {
+          float4 ad[EPI_GROUP][3];
+          long long offs[EPI_GROUP];
+          bool ok[EPI_GROUP];
+#pragma unroll
+          for (int u = 0; u < EPI_GROUP; ++u) {
+            const int it = i0 + u, rr = ew + SG_EPI_WARPS * (it / HALVES), c = (it % HALVES) * 32 + lane;
+            const int grow = mt * SG_BM + rr, j = nt * TNC + cb + c;
+            ok[u] = grow < d && j < d;
+            offs[u] = ok[u] ? (long long)grow * d + j : 0;
+#pragma unroll
+            for (int m = 0; m < 3; ++m)
+              ad[u][m] = (ok[u] && m < epi.add_n) ? addp[m][offs[u]] : make_float4(0.f, 0.f, 0.f, 0.f);
+          }
+#pragma unroll
+          for (int u = 0; u < EPI_GROUP; ++u) {
+            if (!ok[u]) continue;
+            const int it = i0 + u, rr = ew + SG_EPI_WARPS * (it / HALVES), c = (it % HALVES) * 32 + lane;
+            const float4 v = stile[rr * SG_EPI_PITCH + c];
+            df32 re{v.x, v.y}, im{v.z, v.w};
+#pragma unroll
+            for (int m = 0; m < 3; ++m) {
+              if (m < epi.add_n) {
+                re = df_add(re, df_mul(df32{ad[u][m].x, ad[u][m].y}, epi.add_coef[m]));
+                im = df_add(im, df_mul(df32{ad[u][m].z, ad[u][m].w}, epi.add_coef[m]));
+              }
+            }
+            if (mt * SG_BM + rr == nt * TNC + cb + c) re = df_add(re, epi.diag);
+            Cb[offs[u]] = make_float4(re.hi, re.lo, im.hi, im.lo);
+          }
         }
       }
     }
@@ -1085,6 +1200,28 @@ static int make_pair_maps(CUtensorMap* ma, CUtensorMap* mb, const SplitGeom& g, 
   return MG_OK;
 }
 
+// Whether a product runs on CTA pairs.  By default pairs run from 5 digits (measured at 6:
+// +3% at d = 729, +7% at d = 4096, +6% at d = 256; with 2-4 digits 2-4% slower) where the
+// row tiles pair up evenly from d = 256 on, or are 7 or more (an odd count leaves the last
+// pair's second CTA multiplying zeros: -19% at d = 300, three tiles).  A product with a
+// zero part of B and a general A runs N = 64 MMAs on one CTA per tile; with zero parts in
+// both it may run in the real mode of a pair.
+static bool split_uses_pairs(const SplitGeom& g, const SplitCtl& ctl) {
+  const int mtiles = g.Mp / SG_BM;
+  const bool shape_ok = (mtiles % 2 == 0) ? g.d >= 256 : mtiles >= 7;
+  const bool bstruct = ctl.b_zero == 1 || ctl.b_zero == 2;
+  const bool astruct = ctl.a_zero == 1 || ctl.a_zero == 2;
+  return mtiles >= 2 && (!bstruct || astruct) && (ctl.cta_pairs > 0 || (ctl.cta_pairs < 0 && g.L >= 5 && shape_ok));
+}
+
+// Complex output columns per tile: 128 in the real mode of CTA pairs (both operands with a
+// zero part: one real product into one output half), else 64.
+static int split_tile_cols(const SplitGeom& g, const SplitCtl& ctl) {
+  const bool real_mode = (ctl.a_zero == 1 || ctl.a_zero == 2) && (ctl.b_zero == 1 || ctl.b_zero == 2) &&
+                         split_uses_pairs(g, ctl);
+  return real_mode ? 2 * SG_BNC : SG_BNC;
+}
+
 // bytes one CTA loads per pipeline stage (a CTA pair splits the B tile)
 template <int L, int BK, int CTAS>
 static constexpr int stage_bytes() {
@@ -1124,7 +1261,7 @@ static int launch_split_gemm_LB(const SplitGeom& g, int batch, const __nv_bfloat
     // pairs of row tiles; with an odd count the last pair's second CTA lies wholly
     // beyond row d (its loads read zeros, its epilogue writes nothing)
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(ceil_div(mtiles, 2) * 2, ceil_div(g.d, SG_BNC), batch);
+    cfg.gridDim = dim3(ceil_div(mtiles, 2) * 2, ceil_div(g.d, split_tile_cols(g, ctl)), batch);
     cfg.blockDim = dim3(SG_THREADS, 1, 1);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
@@ -1158,18 +1295,6 @@ static int launch_split_gemm_LC(const SplitGeom& g, int batch, const __nv_bfloat
     if (ctl.stage_k == 64 && g.Kh() % 64 == 0)
       return launch_split_gemm_LB<L, 64, false, CTAS>(g, batch, Ad, ea, Bd, eb, C, sC, epi, status, ctl, s);
   return launch_split_gemm_LB<L, 32, false, CTAS>(g, batch, Ad, ea, Bd, eb, C, sC, epi, status, ctl, s);
-}
-
-// Whether a product runs on CTA pairs.  By default pairs run from 5 digits (measured at 6:
-// +3% at d = 729, +7% at d = 4096, +6% at d = 256; with 2-4 digits 2-4% slower) where the
-// row tiles pair up evenly from d = 256 on, or are 7 or more (an odd count leaves the last
-// pair's second CTA multiplying zeros: -19% at d = 300, three tiles).  A product with a
-// zero part of B runs N = 64 MMAs on one CTA per tile.
-static bool split_uses_pairs(const SplitGeom& g, const SplitCtl& ctl) {
-  const int mtiles = g.Mp / SG_BM;
-  const bool shape_ok = (mtiles % 2 == 0) ? g.d >= 256 : mtiles >= 7;
-  const bool bstruct = ctl.b_zero == 1 || ctl.b_zero == 2;
-  return mtiles >= 2 && !bstruct && (ctl.cta_pairs > 0 || (ctl.cta_pairs < 0 && g.L >= 5 && shape_ok));
 }
 
 template <int L>
@@ -1215,6 +1340,16 @@ static int launch_slicers_LT(const SplitGeom& g, int batch, const double* A, lon
   return MG_OK;
 }
 
+template <int L, typename T>
+static int launch_slice_sym_LT(const SplitGeom& g, int batch, const double* M, long long sM, __nv_bfloat16* Ad,
+                               int* ea, int askip, __nv_bfloat16* Bd, int* eb, int bskip, cudaStream_t s,
+                               const SplitCtl& ctl) {
+  slice_sym_kernel<L, T><<<dim3(ceil_div(g.d, 8), batch), 256, 0, s>>>(
+      g.d, g.Kp, g.Mp, g.beta, M, sM, Ad, ea, g.a_item_elems(), askip, Bd, eb, g.b_item_elems(), g.Np / 2, bskip,
+      ctl.item_sq, ctl.sq_step, paired_layout(g, ctl));
+  return check_launch("slice_sym_kernel");
+}
+
 template <int L>
 static int launch_slicers_L(const SplitGeom& g, int batch, int in_df32, const double* A, long long sA,
                             __nv_bfloat16* Ad, int* ea, const double* B, long long sB, __nv_bfloat16* Bd, int* eb,
@@ -1239,6 +1374,32 @@ static int launch_slicers(const SplitGeom& g, int batch, int in_df32, const doub
 }
 
 // Public-to-the-library entry points ------------------------------------------
+
+// Digits of a symmetric matrix for the A operand (abuf), the B operand (bbuf) or both
+// (either may be null), in one pass over its rows; askip / bskip as in slice_sym_kernel.
+int split_slice_sym(int d, int L, int batch, const double* M, long long sM, int in_df32, void* abuf, int askip,
+                    void* bbuf, int bskip, cudaStream_t s, const SplitCtl& ctl) {
+  SplitGeom g = split_geom(d, L);
+  __nv_bfloat16* Ad = reinterpret_cast<__nv_bfloat16*>(abuf);
+  int* ea = Ad ? reinterpret_cast<int*>(Ad + g.a_item_elems() * batch) : nullptr;
+  __nv_bfloat16* Bd = reinterpret_cast<__nv_bfloat16*>(bbuf);
+  int* eb = Bd ? reinterpret_cast<int*>(Bd + g.b_item_elems() * batch) : nullptr;
+#define MG_SYM_CASE(LL)                                                                                  \
+  case LL:                                                                                               \
+    return in_df32 ? launch_slice_sym_LT<LL, df32>(g, batch, M, sM, Ad, ea, askip, Bd, eb, bskip, s, ctl) \
+                   : launch_slice_sym_LT<LL, double>(g, batch, M, sM, Ad, ea, askip, Bd, eb, bskip, s, ctl);
+  switch (L) {
+    MG_SYM_CASE(2)
+    MG_SYM_CASE(3)
+    MG_SYM_CASE(4)
+    MG_SYM_CASE(5)
+    MG_SYM_CASE(6)
+    MG_SYM_CASE(7)
+    MG_SYM_CASE(8)
+  }
+#undef MG_SYM_CASE
+  return MG_EINVAL;
+}
 
 size_t split_a_bytes(int d, int L, int batch) {
   SplitGeom g = split_geom(d, L);

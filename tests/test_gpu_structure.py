@@ -76,7 +76,9 @@ _D300 = dict(nt=6, nr=50, N=12, T=6.0, sigma=2.0, omega0=0.2, unitary=True, name
 
 @pytest.mark.parametrize("L,stage_k,digit_pairs,cta_pairs", [
     (6, 32, 0, None),     # the default: one CTA per tile at three row tiles
-    (6, 32, 0, True),     # CTA pairs for the full products (structured ones stay on one CTA)
+    (6, 32, 0, True),     # CTA pairs: the power products in the pairs' real mode
+    (6, 16, 0, True),
+    (6, 32, 2, True),     # paired digit layout on CTA pairs
     (6, 16, 0, False),
     (6, 32, 1, False),    # paired digit layout, 16-deep stages
     (6, 32, 2, False),    # paired digit layout, 32-deep stages of 128-byte rows
@@ -93,9 +95,13 @@ def test_structured_products_equal_full_products(ctx, L, stage_k, digit_pairs, c
         on, rep_on, f_on = _evolve(ctx, wl, 1, L)
         off, rep_off, f_off = _evolve(ctx, wl, 0, L)
         sym, rep_sym, f_sym = _evolve(ctx, wl, 3, L)
+        sym2, _, _ = _evolve(ctx, wl, 2, L)
     finally:
         _restore(ctx)
     assert np.array_equal(on, off), np.abs(on - off).max()
+    # zero-part skipping is exact on symmetric products too, where the operands' zero
+    # halves and planes are not even written
+    assert np.array_equal(sym, sym2), np.abs(sym - sym2).max()
     # three of the degree-18 polynomial's products (X X, X^2 X, X^3 X^3) per interval take
     # 2 d^3 instead of 8 d^3 (degree 18 wherever the digits carry 30 bits or more)
     if L >= 5:
@@ -110,6 +116,23 @@ def test_structured_products_equal_full_products(ctx, L, stage_k, digit_pairs, c
         for got in (on, sym):
             err = np.abs(got - ref).max()
             assert err <= 1e-6, err
+
+
+@pytest.mark.parametrize("nt,nr,N", [(8, 64, 6), (8, 100, 3)])
+def test_default_pairs_real_mode(ctx, nt, nr, N):
+    """d = 512 (four row tiles) and d = 800 (seven): CTA pairs by default, the power
+    products in the real mode (128-column tiles of one output half), ragged edges."""
+    wl = W.transmon_resonator(nt=nt, nr=nr, N=N, T=0.5 * N, sigma=0.5, omega0=0.2, unitary=True, name="trpairs")
+    on, _, f_on = _evolve(ctx, wl, 1)
+    off, _, f_off = _evolve(ctx, wl, 0)
+    sym, _, f_sym = _evolve(ctx, wl, 3)
+    sym2, _, _ = _evolve(ctx, wl, 2)
+    assert np.array_equal(on, off), np.abs(on - off).max()
+    assert np.array_equal(sym, sym2), np.abs(sym - sym2).max()
+    assert f_sym < f_on < f_off
+    ref = oracle.evolve_workload(wl)
+    for got in (on, sym):
+        assert np.abs(got - ref).max() <= 1e-6, np.abs(got - ref).max()
 
 
 _SYM_BY_TILING = {}
