@@ -32,11 +32,13 @@ METRIC = "Magnus intervals/sec at dim 729 vs FP64 err; p50/p99 latency, mixed st
 UNIT = "intervals/s"
 WORKLOAD = "transmon_chain_d729_N2000_P16_K6_propagator"
 SAMPLE_INTERVALS = 128          # oracle sample (cpu_baseline) and accuracy prefix
-# DRAM bytes (read + write) per complex product of the split-product kernel in its current
-# form, keyed by (d, digits): one ncu capture of a 32-product launch divided by 32; the bench
-# scales it to the average timed launch by the products that launch computes.  An entry is
-# valid for the kernel build it was captured from only, and is removed when the kernel changes.
-GEMM_DRAM_BYTES_PER_PRODUCT = {(729, 6): (1.214349e9 + 0.255134e9) / 32}
+# DRAM bytes (read + write) of the split-product launches per flop of algorithmic work they
+# count, keyed by (d, digits): the summed ncu DRAM bytes of every product launch of one pass
+# over 32 intervals (three power products, three symmetric products, the tree) divided by
+# their summed algorithmic work; the bench scales it to the average timed launch by the work
+# that launch counts (the pass has the timed step's mix of products per interval).  An entry
+# is valid for the kernel build it was captured from only, and is removed when it changes.
+GEMM_DRAM_BYTES_PER_FLOP = {(729, 6): 7.720727296e9 / 2.82297207672e11}
 REFERENCE_STEP_INTERVALS = 16   # oracle intervals per step of --impl reference
 # FP64 and TF32 dense matrix-product peaks of GB300 measured by `python bench.py --peaks`
 # (torch.matmul, n = 8192, best of 10, CUDA events); the BF16 peaks come from MEASURED_PEAKS.json
@@ -109,19 +111,6 @@ def dist_info():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return ws, rank, local
 
-
-# dense BF16 tensor rate of one SM per clock (tcgen05 kind::f16); 152 SMs on GB300
-BF16_FLOPS_PER_SM_CLOCK = 8192
-NUM_SMS = 152
-
-
-def digit_mma_frac(achieved_tflops, pairs, clk):
-    """Share of the nominal BF16 tensor rate at the SM clock seen during the run that the
-    digit-pair MMAs occupy (pairs BF16 products per algorithmic flop)."""
-    mhz = (clk or {}).get("sm_mhz")
-    if not pairs or not mhz:
-        return None
-    return achieved_tflops * pairs / (NUM_SMS * BF16_FLOPS_PER_SM_CLOCK * mhz * 1e6 / 1e12)
 
 
 def tune_plan(M, torch, stream, plan, output, tolerance, set_controls):
@@ -338,18 +327,19 @@ def run_ours(args):
         if prec == M.MG_PREC_SPLIT:
             peak = float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops")))
             pairs = slices * (slices + 1) // 2
-            per_prod = GEMM_DRAM_BYTES_PER_PRODUCT.get((wl.d, slices))
-            products_per_launch = per_launch_flops / (8.0 * wl.d ** 3)
+            per_flop = GEMM_DRAM_BYTES_PER_FLOP.get((wl.d, slices)) if not args.no_structure else None
             roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                     "frac": achieved / peak,
-                    "traffic": per_prod * products_per_launch if per_prod else None,
-                    "traffic_note": "bytes per average launch, scaled by products from one ncu capture",
+                    "traffic": per_flop * per_launch_flops if per_flop else None,
+                    "traffic_note": "bytes per average launch: ncu DRAM bytes per counted flop of one "
+                                    "32-interval pass, times the launch's counted work",
                     "kernel": "split_gemm_kernel",
                     "peak_source": f"bf16 dense sustained, {peak_src}",
-                    "digit_mma_frac_of_nominal_at_clock": digit_mma_frac(achieved, pairs, clk),
-                    "note": f"achieved counts 8 d^3 flops per complex product; the tensor pipe issues "
-                            f"{pairs} BF16 digit-pair products per such flop (digit_mma_frac: their share "
-                            f"of 8192 flop/clock/SM x 152 SMs at the run's median SM clock)"}
+                    "note": f"achieved counts algorithmic work: 8 d^3 flops per general complex product, "
+                            f"a quarter of that where both operands have a zero part (powers of X with "
+                            f"real operators), and d (d + 1) / 2 of the d^2 outputs of a symmetric "
+                            f"result; the tensor pipe issues {pairs} BF16 digit-pair products per such "
+                            f"flop"}
         else:
             fp64_peak = FP64_TFLOPS_MEASURED
             roof = {"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
@@ -655,7 +645,6 @@ def run_config(args):
         p64 = FP64_TFLOPS_MEASURED
         return {"bound": "tensor" if pairs else "alu", "achieved": ach, "peak": peak if pairs else p64,
                 "unit": "TFLOP/s", "frac": ach / (peak if pairs else p64), "traffic": None,
-                "digit_mma_frac_of_nominal_at_clock": digit_mma_frac(ach, pairs, clk),
                 "peak_source": f"bf16 dense sustained, {src}" if pairs else
                 "FP64 torch.matmul, measured (bench.py --peaks)"}
 
