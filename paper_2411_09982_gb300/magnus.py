@@ -201,6 +201,9 @@ class Context:
         if workspace_limit is not None:
             _check(lib.mg_ctx_set_workspace_limit(self.h, int(workspace_limit)), "mg_ctx_set_workspace_limit")
 
+    def set_workspace_limit(self, nbytes):
+        _check(load().mg_ctx_set_workspace_limit(self.h, int(nbytes)), "mg_ctx_set_workspace_limit")
+
     def enable_gemm_timing(self, on=True):
         _check(load().mg_ctx_enable_gemm_timing(self.h, 1 if on else 0), "mg_ctx_enable_gemm_timing")
 
