@@ -579,8 +579,11 @@ int mg_ctx_set_cta_pairs(mg_ctx* ctx, int on);
  *          result is exactly symmetric, the same on either tiling, and differs from the
  *          full product's by that product's own rounding asymmetry.  The tree product of
  *          the U_n is general.
- * 3 (the default) sets both, 0 issues every product in full.  Applies to mg_evolve and
- * mg_evolve_batch (a batch only when all of its plans qualify); gemm statistics count
+ * 3 (the default) sets both, 0 issues every product in full.  Applies to mg_evolve,
+ * mg_evolve_batch (a batch only when all of its plans qualify) and the chunk steps of a
+ * server (mg_submit checks each job's operators; a step only when all of its jobs
+ * qualify, so a result in a mix can differ from the same job alone by the rounding
+ * asymmetry of bit 1, within the split tolerance); gemm statistics count
  * the algorithmic work of such a product: a quarter of 8 d^3 with two zero parts, and
  * the d (d + 1) / 2 entries on and below the diagonal of a symmetric result.  MG_EINVAL
  * outside 0..3. */

@@ -2884,6 +2884,8 @@ struct SJob {
   uint64_t id = 0;
   BatchJob b;
   int dp = 0, prec = 0, L = 6, taylor = MG_TAYLOR_AUTO;
+  // its operators are real (X imaginary) / also exactly symmetric (see mg_ctx_set_structure)
+  bool real_ops = false, sym_ops = false;
   double taylor_u = 0.0;
   double* out = nullptr;
   cudaMemcpyKind out_kind = cudaMemcpyDeviceToDevice;
@@ -3123,6 +3125,11 @@ void server_loop(mg_server* srv) {
     Engine eng{ctx, group[0]->dp, group[0]->prec, group[0]->L};
     eng.taylor_mode = group[0]->taylor;
     eng.taylor_u = group[0]->taylor_u;
+    eng.x_imag = eng.x_sym = true;
+    for (SJob* j : group) {
+      eng.x_imag = eng.x_imag && j->real_ops;
+      eng.x_sym = eng.x_sym && j->sym_ops;
+    }
     int rc = MG_OK;
     for (SJob* j : group) cudaStreamWaitEvent(ctx->stream, j->ready, 0);
     const int chunk = chunk_size(ctx, eng.d, eng.prec, eng.L, 1 << 30, 1);
@@ -3497,8 +3504,24 @@ int mg_submit(mg_server* srv, const mg_job* job_in, uint64_t* job_id) {
         r = MG_ECUDA;
       b.init = true;
     }
+    // structure of the padded operators (read back with the upload's synchronisation)
+    int bits = 3;
+    void* flag = nullptr;
+    if (r == MG_OK) {
+      if (cudaMallocFromPoolAsync(&flag, 16, srv->ctx->pool, s) != cudaSuccess) {
+        cudaGetLastError();
+        flag = nullptr;
+        r = MG_ENOMEM;
+      }
+    }
+    if (r == MG_OK && cudaMemsetAsync(flag, 0, sizeof(int), s) != cudaSuccess) r = MG_ECUDA;
+    if (r == MG_OK) r = launch_operator_structure(dp, 1 + K, H, reinterpret_cast<int*>(flag), s);
+    if (r == MG_OK && cudaMemcpyAsync(&bits, flag, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess) r = MG_ECUDA;
+    if (flag) cudaFreeAsync(flag, s);
     cudaFreeAsync(tmp, s);
     if (cudaStreamSynchronize(s) != cudaSuccess && r == MG_OK) r = MG_ECUDA;
+    j->real_ops = r == MG_OK && (bits & 1) == 0;
+    j->sym_ops = r == MG_OK && bits == 0;
     if (r == MG_OK && cudaEventCreateWithFlags(&j->ready, cudaEventDisableTiming) != cudaSuccess) r = MG_ECUDA;
     if (r == MG_OK && cudaEventRecord(j->ready, s) != cudaSuccess) r = MG_ECUDA;
     return r;
