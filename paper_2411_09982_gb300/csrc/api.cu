@@ -406,15 +406,21 @@ struct Engine {
     return split_slice_b(d, L, batch, B, sB, in_df, bbuf[slot], ctx->stream, ctl());
   }
   int prepA(int batch, const double* A, long long sA) { return prepA(batch, A, sA, df() ? 1 : 0); }
+  // Symmetric matrices of the exponential in lower-block storage: with X symmetric and
+  // symmetric products on, every polynomial in X is held as its 32 x 32 blocks on and
+  // below the diagonal (entry (i, j) with j > i read as (j, i)); its products, slicers
+  // and elementwise steps read and write only those blocks, and the phase step writes
+  // the full U_n.
+  bool lower() const { return x_sym && df() && (ctx->structure & 2); }
   // Digits of an operand that is a polynomial in X: as A (slot < 0: not as B), as B into
-  // `slot`, or both in one pass.  With X symmetric (x_sym) the matrix is symmetric and is
-  // sliced by rows for both operands; part (1: its real part is zero, 2: its imaginary
-  // part is; 0: general) leaves unwritten what the products of zero-part skipping never
-  // read (the zero half of A's K axis; the zero plane of B, or both -Im and Im planes of
-  // a real B).  Otherwise the general slicers.
+  // `slot`, or both in one pass.  In lower-block storage its B digits are its A digits
+  // read as columns (one slicer for both); part (1: its real part is zero, 2: its
+  // imaginary part is; 0: general) leaves unwritten what the products of zero-part
+  // skipping never read (the zero half of A's K axis; the zero plane of B, or both -Im
+  // and Im planes of a real B).  Otherwise the general slicers.
   int prep_poly(bool as_a, int slot, int batch, const double* M, int part) {
     if (prec != MG_PREC_SPLIT) return MG_OK;
-    if (!(x_sym && (ctx->structure & 2))) {
+    if (!lower()) {
       if (as_a) MG_TRY(prepA(batch, M, mat_doubles_(), 1));
       if (slot >= 0) MG_TRY(prepB(slot, batch, M, mat_doubles_(), 1));
       return MG_OK;
@@ -422,32 +428,34 @@ struct Engine {
     const int p = (x_imag && (ctx->structure & 1)) ? part : 0;
     const int askip = p;                                  // bit 0: real half, bit 1: imaginary half
     const int bskip = p == 1 ? 2 : (p == 2 ? 1 | 4 : 0);  // bit q: plane q (-Im, Re, Im)
-    return split_slice_sym(d, L, batch, M, mat_doubles_(), 1, as_a ? abuf : nullptr, askip,
+    return split_slice_sym(d, L, batch, M, mat_doubles_(), as_a ? abuf : nullptr, askip,
                            slot >= 0 ? bbuf[slot] : nullptr, bskip, ctx->stream, ctl());
   }
   long long mat_doubles_() const { return 2LL * d * d; }
   int prepB(int slot, int batch, const double* B, long long sB) { return prepB(slot, batch, B, sB, df() ? 1 : 0); }
   // elementwise steps in the engine's storage format
   int lincomb(int batch, double* dst, int n, const double* const* src, const double* coef, double diag) {
-    return df() ? launch_lincomb_df(batch, d, dst, n, src, coef, diag, ctx->stream)
+    return df() ? launch_lincomb_df(batch, d, dst, n, src, coef, diag, ctx->stream, lower() ? 1 : 0)
                 : launch_lincomb(batch, d, dst, n, src, coef, diag, ctx->stream);
   }
   int lincomb_multi(int batch, int nout, double* const* dst, int n, const double* const* src, const double* coef,
                     const double* diag) {
-    return df() ? launch_lincomb_multi_df(batch, d, nout, dst, n, src, coef, diag, ctx->stream)
+    return df() ? launch_lincomb_multi_df(batch, d, nout, dst, n, src, coef, diag, ctx->stream, lower() ? 1 : 0)
                 : launch_lincomb_multi(batch, d, nout, dst, n, src, coef, diag, ctx->stream);
   }
   int identity(int batch, double* dst) {
     return df() ? launch_identity_df(batch, d, dst, ctx->stream) : launch_identity(batch, d, dst, ctx->stream);
   }
+  // U = e^{-i tau} R into full storage
   int phase(int batch, const double* tau, const double* src, double* dst) {
+    if (lower()) return launch_apply_phase_sym_df(batch, d, tau, src, dst, ctx->stream);
     return df() ? launch_apply_phase_df(batch, d, tau, src, dst, ctx->stream)
                 : launch_apply_phase(batch, d, (long long)d * d, tau, src, dst, ctx->stream);
   }
   // X = -i 2^{-sq} W (X in engine storage; may alias W); sq_dev: per-item counts.  W is
   // FP64, or double-float when w_df (the split path's own Hbar builder writes it so)
   int scale_x(int batch, const double* W, double* X, int sq, const int* sq_dev = nullptr, bool w_df = false) {
-    return df() ? launch_scale_minus_i_df(batch, d, W, X, sq, ctx->stream, sq_dev, w_df ? 1 : 0)
+    return df() ? launch_scale_minus_i_df(batch, d, W, X, sq, ctx->stream, sq_dev, w_df ? 1 : 0, lower() ? 1 : 0)
                 : launch_scale_minus_i(batch, d, W, X, sq_dev, sq, ctx->stream);
   }
   int to_fp64(int batch, const double* src, long long ss, double* dst, long long ds) {
@@ -690,6 +698,7 @@ int expm_chunk(mg_ctx* ctx, Engine& eng, int batch, double* W, const double* tau
   // exact trace phase e^{-i tau_b}
   if (sU != md) return MG_EINVAL;
   if (tau) return eng.phase(batch, tau, R, U);
+  if (eng.lower()) MG_TRY(split_sym_fill(d, batch, R, md, s));   // full storage for the caller
   return launch_copy_strided(batch, md, R, md, U, sU, s);
 }
 

@@ -164,17 +164,19 @@ struct SplitCtl {
   int a_zero = 0;
   int b_zero = 0;
   // The product is complex symmetric (C = C^T: polynomials in a symmetric matrix and
-  // their products with one another).  Output tiles wholly right of the diagonal are
-  // not computed; split_gemm then copies every entry above the diagonal from its
-  // transpose, so the stored result is exactly symmetric.
+  // their products with one another) and its operands and addends are held in lower-block
+  // storage (valid 32 x 32 blocks on and below the diagonal; entry (i, j) with j > i read
+  // as (j, i)).  Output tiles wholly right of the diagonal are not computed; the result
+  // is left in the same storage.
   int sym_out = 0;
 };
 int split_slice_a(int d, int L, int batch, const double* A, long long sA, int in_df32, void* buf, cudaStream_t s,
                   const SplitCtl& ctl = SplitCtl());
 int split_slice_b(int d, int L, int batch, const double* B, long long sB, int in_df32, void* buf, cudaStream_t s,
                   const SplitCtl& ctl = SplitCtl());
-int split_slice_sym(int d, int L, int batch, const double* M, long long sM, int in_df32, void* abuf, int askip,
-                    void* bbuf, int bskip, cudaStream_t s, const SplitCtl& ctl = SplitCtl());
+int split_slice_sym(int d, int L, int batch, const double* M, long long sM, void* abuf, int askip, void* bbuf,
+                    int bskip, cudaStream_t s, const SplitCtl& ctl = SplitCtl());
+int split_sym_fill(int d, int batch, double* C, long long sC, cudaStream_t s);
 int split_gemm(int d, int L, int batch, const void* abuf, const void* bbuf, double* C, long long sC,
                const AddTerms& add, int* status, cudaStream_t s, const SplitCtl& ctl = SplitCtl());
 
@@ -267,20 +269,24 @@ int launch_copy_active(int batch, long long md, const double* src, double* dst, 
 int launch_squarings(int n, const double* norm, double theta, int S, int uniform, int* sq, int* overflow,
                      double* flops_acc, double flops_per_square, cudaStream_t s);
 
-// Double-float (DF32) elementwise kernels of the split path; see elementwise.cu.
+// Double-float (DF32) elementwise kernels of the split path; see elementwise.cu.  With
+// lower != 0 they touch only the 32 x 32 blocks on and below the diagonal (the valid
+// part of a symmetric matrix in lower-block storage).
 // X_b = -i 2^{-sq_b} W_b with sq_b from sq_dev (device, per item) or the constant sq;
 // W FP64 (in_df32 = 0) or double-float (in_df32 = 1), X double-float (may alias W)
 int launch_scale_minus_i_df(int batch, int d, const double* src, double* dst_df, int sq, cudaStream_t s,
-                            const int* sq_dev = nullptr, int in_df32 = 0);
+                            const int* sq_dev = nullptr, int in_df32 = 0, int lower = 0);
 // dst[o] = sum_m coef[o * nsrc + m] src[m] + diag[o] I, o < nout <= 5, nsrc <= 4, one pass
 // (a destination may alias a source); FP64 and double-float storage
 int launch_lincomb_multi(int batch, int d, int nout, double* const* dst, int nsrc, const double* const* src,
                          const double* coef, const double* diag, cudaStream_t s);
 int launch_lincomb_multi_df(int batch, int d, int nout, double* const* dst, int nsrc, const double* const* src,
-                            const double* coef, const double* diag, cudaStream_t s);
+                            const double* coef, const double* diag, cudaStream_t s, int lower = 0);
 int launch_lincomb_df(int batch, int d, double* dst, int nsrc, const double* const* src, const double* coef,
-                      double diag, cudaStream_t s);
+                      double diag, cudaStream_t s, int lower = 0);
 int launch_apply_phase_df(int batch, int d, const double* phase, const double* src, double* dst, cudaStream_t s);
+// dst_b = e^{-i phase_b} src_b into full storage from a symmetric src in lower-block storage
+int launch_apply_phase_sym_df(int batch, int d, const double* phase, const double* src, double* dst, cudaStream_t s);
 int launch_identity_df(int batch, int d, double* dst, cudaStream_t s);
 int launch_df_to_fp64(int batch, int d, const double* src, long long ss, double* dst, long long ds, cudaStream_t s);
 int launch_fp64_to_df(int batch, int d, const double* src, long long ss, double* dst, long long ds, cudaStream_t s);

@@ -238,6 +238,14 @@ static dim3 item_grid(int batch, long long per) {
   return dim3((unsigned)std::max<long long>(gx, 1), (unsigned)batch);
 }
 
+// lower-block storage of a symmetric matrix (see split_gemm.cu): with `lower`, the
+// per-element kernels below touch only the 32 x 32 blocks on and below the diagonal
+__device__ __forceinline__ bool outside_lower(int lower, int r, int d) {
+  if (!lower) return false;
+  const int i = r / d, j = r - i * d;
+  return (j >> 5) > (i >> 5);
+}
+
 __global__ void scale_minus_i_df_kernel(int per, const double* __restrict__ src, float4* __restrict__ dst, double f,
                                         const int* __restrict__ sq_dev) {
   const long long base = (long long)blockIdx.y * per;
@@ -252,25 +260,26 @@ __global__ void scale_minus_i_df_kernel(int per, const double* __restrict__ src,
 
 // the same from a double-float W: (-i)(a + i b) 2^{-s} = (b - i a) 2^{-s}, exact on the FP32 pipe
 __global__ void scale_minus_i_dfdf_kernel(int per, const float4* __restrict__ src, float4* __restrict__ dst, int sq,
-                                          const int* __restrict__ sq_dev) {
+                                          const int* __restrict__ sq_dev, int d, int lower) {
   const long long base = (long long)blockIdx.y * per;
   const int s = sq_dev ? sq_dev[blockIdx.y] : sq;
   const int s1 = s / 2, s2 = s - s1;   // two factors keep each in range
   const float f1 = __int_as_float((127 - s1) << 23), f2 = __int_as_float((127 - s2) << 23);
   for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < per; r += gridDim.x * blockDim.x) {
+    if (outside_lower(lower, r, d)) continue;
     const float4 v = src[base + r];
     dst[base + r] = make_float4((v.z * f1) * f2, (v.w * f1) * f2, -(v.x * f1) * f2, -(v.y * f1) * f2);
   }
 }
 
 int launch_scale_minus_i_df(int batch, int d, const double* src, double* dst_df, int sq, cudaStream_t s,
-                            const int* sq_dev, int in_df32) {
+                            const int* sq_dev, int in_df32, int lower) {
   if (batch <= 0) return MG_OK;
   if (batch > 65535) return MG_EUNSUPPORTED;
   const dim3 grid = item_grid(batch, (long long)d * d);
   if (in_df32) {
     scale_minus_i_dfdf_kernel<<<grid, 256, 0, s>>>(d * d, reinterpret_cast<const float4*>(src),
-                                                   reinterpret_cast<float4*>(dst_df), sq, sq_dev);
+                                                   reinterpret_cast<float4*>(dst_df), sq, sq_dev, d, lower);
     return check_launch("scale_minus_i_dfdf_kernel");
   }
   const double f = std::ldexp(1.0, -sq);
@@ -290,10 +299,11 @@ struct LincombDfArgs {
   df32 coef[4];
 };
 
-__global__ void lincomb_df_kernel(int d, int nsrc, LincombDfArgs a, df32 diag, float4* __restrict__ dst) {
+__global__ void lincomb_df_kernel(int d, int nsrc, LincombDfArgs a, df32 diag, float4* __restrict__ dst, int lower) {
   const int per = d * d;
   const long long base = (long long)blockIdx.y * per;
   for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < per; r += gridDim.x * blockDim.x) {
+    if (outside_lower(lower, r, d)) continue;
     const long long e = base + r;
     df32 re{0.f, 0.f}, im{0.f, 0.f};
     for (int m = 0; m < nsrc; ++m) {
@@ -307,7 +317,7 @@ __global__ void lincomb_df_kernel(int d, int nsrc, LincombDfArgs a, df32 diag, f
 }
 
 int launch_lincomb_df(int batch, int d, double* dst, int nsrc, const double* const* src, const double* coef,
-                      double diag, cudaStream_t s) {
+                      double diag, cudaStream_t s, int lower) {
   if (nsrc < 0 || nsrc > 4) return MG_EINVAL;
   if (batch <= 0) return MG_OK;
   if (batch > 65535) return MG_EUNSUPPORTED;
@@ -317,7 +327,7 @@ int launch_lincomb_df(int batch, int d, double* dst, int nsrc, const double* con
     a.coef[m] = df_from_double(coef[m]);
   }
   lincomb_df_kernel<<<item_grid(batch, (long long)d * d), 256, 0, s>>>(d, nsrc, a, df_from_double(diag),
-                                                                       reinterpret_cast<float4*>(dst));
+                                                                       reinterpret_cast<float4*>(dst), lower);
   return check_launch("lincomb_df_kernel");
 }
 
@@ -330,10 +340,11 @@ struct LincombMultiDfArgs {
 };
 
 template <int NSRC>
-__global__ void lincomb_multi_df_kernel(int d, int nout, LincombMultiDfArgs a) {
+__global__ void lincomb_multi_df_kernel(int d, int nout, LincombMultiDfArgs a, int lower) {
   const int per = d * d;
   const long long base = (long long)blockIdx.y * per;
   for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < per; r += gridDim.x * blockDim.x) {
+    if (outside_lower(lower, r, d)) continue;
     const long long e = base + r;
     float4 v[NSRC];
 #pragma unroll
@@ -353,7 +364,7 @@ __global__ void lincomb_multi_df_kernel(int d, int nout, LincombMultiDfArgs a) {
 }
 
 int launch_lincomb_multi_df(int batch, int d, int nout, double* const* dst, int nsrc, const double* const* src,
-                            const double* coef, const double* diag, cudaStream_t s) {
+                            const double* coef, const double* diag, cudaStream_t s, int lower) {
   if (nsrc < 1 || nsrc > 4 || nout < 1 || nout > 5) return MG_EINVAL;
   if (batch <= 0) return MG_OK;
   if (batch > 65535) return MG_EUNSUPPORTED;
@@ -366,10 +377,10 @@ int launch_lincomb_multi_df(int batch, int d, int nout, double* const* dst, int 
   }
   const dim3 grid = item_grid(batch, (long long)d * d);
   switch (nsrc) {
-    case 1: lincomb_multi_df_kernel<1><<<grid, 256, 0, s>>>(d, nout, a); break;
-    case 2: lincomb_multi_df_kernel<2><<<grid, 256, 0, s>>>(d, nout, a); break;
-    case 3: lincomb_multi_df_kernel<3><<<grid, 256, 0, s>>>(d, nout, a); break;
-    default: lincomb_multi_df_kernel<4><<<grid, 256, 0, s>>>(d, nout, a); break;
+    case 1: lincomb_multi_df_kernel<1><<<grid, 256, 0, s>>>(d, nout, a, lower); break;
+    case 2: lincomb_multi_df_kernel<2><<<grid, 256, 0, s>>>(d, nout, a, lower); break;
+    case 3: lincomb_multi_df_kernel<3><<<grid, 256, 0, s>>>(d, nout, a, lower); break;
+    default: lincomb_multi_df_kernel<4><<<grid, 256, 0, s>>>(d, nout, a, lower); break;
   }
   return check_launch("lincomb_multi_df_kernel");
 }
@@ -398,6 +409,59 @@ __global__ void apply_phase_df_kernel(long long per_item, const double* __restri
     const df32 im = df_add(df_mul(y, c), df_mul(x, msn));
     db[e] = make_float4(re.hi, re.lo, im.hi, im.lo);
   }
+}
+
+// The same from a symmetric src in lower-block storage into a full dst: entry (i, j) with
+// j > i is taken from (j, i), also inside the diagonal blocks, so dst is exactly
+// symmetric.  One 32 x 32 block per CTA (its own, or its transposed partner, staged in
+// shared memory): grid (ceil(d/32), ceil(d/32), batch), 256 threads.
+__global__ void apply_phase_sym_df_kernel(int d, const double* __restrict__ phase, const float4* __restrict__ src,
+                                          float4* __restrict__ dst) {
+  __shared__ float4 t[32][33];
+  __shared__ df32 cs_sn[2];
+  const int bj = blockIdx.x, bi = blockIdx.y, b = blockIdx.z;
+  const long long per = (long long)d * d;
+  const float4* sb = src + b * per;
+  float4* db = dst + b * per;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int i0 = bi * 32, j0 = bj * 32;
+  if (threadIdx.x == 0) {
+    double sn, cs;
+    sincos(phase[b], &sn, &cs);
+    cs_sn[0] = df_from_double(cs);
+    cs_sn[1] = df_from_double(sn);
+  }
+  for (int r = ty; r < 32; r += 8) {
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (bj <= bi) {   // t[r][tx] = src[i0 + r][j0 + tx]
+      if (i0 + r < d && j0 + tx < d) v = sb[(long long)(i0 + r) * d + j0 + tx];
+      t[r][tx] = v;
+    } else {          // t[tx][r] = src[j0 + r][i0 + tx]
+      if (j0 + r < d && i0 + tx < d) v = sb[(long long)(j0 + r) * d + i0 + tx];
+      t[tx][r] = v;
+    }
+  }
+  __syncthreads();
+  const df32 c = cs_sn[0], sn = cs_sn[1], msn = df_neg(cs_sn[1]);
+  for (int r = ty; r < 32; r += 8) {
+    const int i = i0 + r, j = j0 + tx;
+    if (i >= d || j >= d) continue;
+    const float4 v = (bi == bj && tx > r) ? t[tx][r] : t[r][tx];
+    const df32 x{v.x, v.y}, y{v.z, v.w};
+    // (c - i s)(x + i y) = (c x + s y) + i (c y - s x)
+    const df32 re = df_add(df_mul(x, c), df_mul(y, sn));
+    const df32 im = df_add(df_mul(y, c), df_mul(x, msn));
+    db[(long long)i * d + j] = make_float4(re.hi, re.lo, im.hi, im.lo);
+  }
+}
+
+int launch_apply_phase_sym_df(int batch, int d, const double* phase, const double* src, double* dst, cudaStream_t s) {
+  if (batch <= 0) return MG_OK;
+  if (batch > 65535) return MG_EUNSUPPORTED;
+  const int nb = (d + 31) / 32;
+  apply_phase_sym_df_kernel<<<dim3(nb, nb, batch), 256, 0, s>>>(d, phase, reinterpret_cast<const float4*>(src),
+                                                                reinterpret_cast<float4*>(dst));
+  return check_launch("apply_phase_sym_df_kernel");
 }
 
 int launch_apply_phase_df(int batch, int d, const double* phase, const double* src, double* dst, cudaStream_t s) {

@@ -261,83 +261,142 @@ slice_a_kernel(int d, int Kp, int Mp, int beta, const double* __restrict__ A, lo
   }
 }
 
-// Digits of a complex symmetric matrix M (M = M^T) by rows, as the A operand, the B
-// operand or both: column j of M is its row j, so the column exponent of B equals the
-// row exponent of A and B's plane rows are M's rows (plane 0: -Im, 1: Re, 2: Im).  One
-// warp per row as in slice_a_kernel; one read of M serves both operands, with no column
-// pass.  askip (bit 0: the real half, bit 1: the imaginary half of A's K axis) and bskip
-// (bit p: plane p of B) name parts that are not written because no product reads them:
-// the zero parts of a real or imaginary operand, which the products skip.
-// grid (ceil(Mp/8), batch), block 256.
-template <int L, typename T>
-__global__ void __launch_bounds__(256, 3)
-slice_sym_kernel(int d, int Kp, int Mp, int beta, const double* __restrict__ M, long long sM,
-                 __nv_bfloat16* __restrict__ aout, int* __restrict__ ea, long long a_item_elems, int askip,
-                 __nv_bfloat16* __restrict__ bout, int* __restrict__ eb, long long b_item_elems, int brows,
-                 int bskip, const int* __restrict__ item_sq, int sq_step, int pairs) {
-  using E_ = Elem<T>;
-  const int lane = threadIdx.x & 31;
-  const int row = blockIdx.x * 8 + (threadIdx.x >> 5);
-  const int b = blockIdx.y;
-  if (row >= d) return;   // rows d..Mp (and d..brows) are never read: the tensor maps end at row d
+// Complex symmetric matrices (M = M^T) of the exponential are held as their lower 32 x 32
+// blocks: block (bi, bj) is valid for bj <= bi, and entry (i, j) with j > i is read as
+// M[j][i] (also inside the diagonal blocks, so every use sees exactly symmetric values).
+// Their digits come from two kernels: the row exponents, then the digits of every 32 x 32
+// block of rows and K, each from its own block or its transposed partner.
+
+// Row exponent bounds E_i (|M_ij| < 2^{E_i} over the whole row i) from the stored lower
+// triangle: entry (i, j), j <= i, bounds row i and row j (its transpose's row).  grid
+// (ceil(d/32), ceil(d/32), batch), blocks above the diagonal return; block 256 (thread =
+// column tx of rows ty, ty + 8, ...).  e1 (stride n1 per item) and e2 (n2; may be null)
+// must be preset below -2^28 (byte 0x80); combined by atomicMax.
+__global__ void __launch_bounds__(256)
+sym_exponent_kernel(int d, const float4* __restrict__ M, long long sM4, int* __restrict__ e1, long long n1,
+                    int* __restrict__ e2, long long n2, const int* __restrict__ item_sq, int sq_step) {
+  const int bj = blockIdx.x, bi = blockIdx.y, b = blockIdx.z;
+  if (bj > bi) return;
   if (item_sq && item_sq[b] <= sq_step) return;
+  __shared__ int rmax[32], cmax[32];
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  if (threadIdx.x < 32) rmax[tx] = cmax[tx] = -(1 << 29);
+  __syncthreads();
+  const float4* Mb = M + b * sM4;
+  const int j = bj * 32 + tx;
+  int cm = -(1 << 29);
+  for (int r = ty; r < 32; r += 8) {
+    const int i = bi * 32 + r;
+    int e = -(1 << 29);
+    if (i < d && j < d && j <= i) {
+      const float4 v = Mb[(long long)i * d + j];
+      e = max(exp_bound(df32{v.x, v.y}), exp_bound(df32{v.z, v.w}));
+    }
+    cm = max(cm, e);
+    // every lane of the warp takes part (no divergent shuffle)
+    for (int o = 16; o > 0; o >>= 1) e = max(e, __shfl_xor_sync(0xffffffffu, e, o));
+    if (tx == 0) rmax[r] = e;   // row r is this warp's alone
+  }
+  atomicMax(&cmax[tx], cm);
+  __syncthreads();
+  if (threadIdx.x < 64) {
+    const int c = threadIdx.x & 31;
+    const int idx = threadIdx.x < 32 ? bi * 32 + c : bj * 32 + c;
+    const int e = threadIdx.x < 32 ? rmax[c] : cmax[c];
+    if (idx < d && e > -(1 << 29)) {
+      atomicMax(e1 + b * n1 + idx, e);
+      if (e2) atomicMax(e2 + b * n2 + idx, e);
+    }
+  }
+}
+
+// Digits of a complex symmetric matrix in lower-block storage for the A operand, the B
+// operand or both: B's column j is its row j, so B's column exponents are the row
+// exponents and B's plane rows are M's rows (plane 0: -Im, 1: Re, 2: Im).  One 32 x 32
+// block of rows i and K positions k per CTA, staged in shared memory from block (i, k)
+// or, right of the diagonal, from the transposed block (k, i); thread = (row, 4 k).
+// ea / eb hold the row exponents (sym_exponent_kernel); askip (bit 0: the real half,
+// bit 1: the imaginary half of A's K axis) and bskip (bit p: plane p of B) name parts
+// that are not written because no product reads them (the zero parts of a real or
+// imaginary operand, which the products skip).  K positions d..Kh are written as zero
+// digits (the tile padding along K).  grid (Kh/32, ceil(d/32), batch), block 256.
+template <int L>
+__global__ void __launch_bounds__(256)
+slice_sym_block_kernel(int d, int Kp, int Mp, int beta, const float4* __restrict__ M, long long sM4,
+                       __nv_bfloat16* __restrict__ aout, const int* __restrict__ ea, long long a_item_elems,
+                       int askip, __nv_bfloat16* __restrict__ bout, const int* __restrict__ eb,
+                       long long b_item_elems, int brows, int bskip, const int* __restrict__ item_sq, int sq_step,
+                       int pairs) {
+  const int bk = blockIdx.x, bi = blockIdx.y, b = blockIdx.z;
+  if (item_sq && item_sq[b] <= sq_step) return;
+  __shared__ float4 t[32][33];
   const int Kh = Kp / 2;
-  const double* a = M + b * sM;
-  const long long r0 = (long long)row * d;
-  int E = -(1 << 29);
-  for (int k = lane; k < d; k += 32) {
-    const auto v = E_::load(a, r0 + k);
-    E = max(E, max(exp_bound(v.re), exp_bound(v.im)));
+  const int i0 = bi * 32, k0 = bk * 32;
+  const float4* Mb = M + b * sM4;
+  {
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    for (int r = ty; r < 32; r += 8) {
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (bk < bi) {   // t[r][tx] = M[i0 + r][k0 + tx]
+        if (i0 + r < d && k0 + tx < d) v = Mb[(long long)(i0 + r) * d + k0 + tx];
+        t[r][tx] = v;
+      } else if (bk > bi) {   // t[tx][r] = M[k0 + r][i0 + tx]
+        if (k0 + r < d && i0 + tx < d) v = Mb[(long long)(k0 + r) * d + i0 + tx];
+        t[tx][r] = v;
+      } else {   // the diagonal block as stored, its upper half replaced below
+        if (i0 + r < d && k0 + tx < d) v = Mb[(long long)(i0 + r) * d + k0 + tx];
+        t[r][tx] = v;
+      }
+    }
   }
-  for (int o2 = 16; o2 > 0; o2 >>= 1) E = max(E, __shfl_xor_sync(0xffffffffu, E, o2));
-  if (E < -(1 << 28)) E = 0;   // all-zero row
-  if (lane == 0) {
-    if (aout) ea[(long long)b * Mp + row] = E;
-    if (bout) eb[(long long)b * brows + row] = E;
-  }
-  __nv_bfloat16* oa = aout ? aout + (long long)b * a_item_elems : nullptr;
-  __nv_bfloat16* ob = bout ? bout + (long long)b * b_item_elems : nullptr;
-  // digit s of an element lies (s >> 1) * S2 + (s & 1) * S1 past digit 0 (both layouts)
-  const long long a_s1 = pairs ? 16 : (long long)Mp * Kp, a_s2 = pairs ? 2LL * Mp * Kp : 2 * a_s1;
-  const long long b_s1 = pairs ? 16 : 3LL * brows * Kh, b_s2 = pairs ? 6LL * brows * Kh : 2 * b_s1;
+  __syncthreads();
+  const int r = threadIdx.x >> 3, g = threadIdx.x & 7;   // row r of the block, K positions 4g..4g+3
+  const int row = i0 + r;
+  if (row >= d) return;
+  const int k = k0 + 4 * g;
+  if (k >= Kh) return;
+  const int E0 = ea ? ea[(long long)b * Mp + row] : eb[(long long)b * brows + row];
+  const int E = E0 < -(1 << 28) ? 0 : E0;   // all-zero row
   const Pow2Pair f = pow2_pair(beta - 1 - E);
-  for (int k = 4 * lane; k < Kh; k += 128) {
-    df32 re[4], im[4];   // the 4 elements, scaled (zero beyond d)
+  df32 re[4], im[4];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      re[q] = im[q] = df32{0.f, 0.f};
-      if (k + q < d) {
-        const auto v = E_::load(a, r0 + k + q);
-        re[q] = scaled_pair(v.re, f);
-        im[q] = scaled_pair(v.im, f);
-      }
+  for (int q = 0; q < 4; ++q) {
+    const int c = 4 * g + q;
+    // inside the diagonal block the entries right of the diagonal come from the left
+    const float4 v = (bk == bi && c > r) ? t[c][r] : t[r][c];
+    re[q] = k + q < d ? scaled_pair(df32{v.x, v.y}, f) : df32{0.f, 0.f};
+    im[q] = k + q < d ? scaled_pair(df32{v.z, v.w}, f) : df32{0.f, 0.f};
+  }
+  uint32_t r01[L], r23[L], i01[L], i23[L];
+  digits_pair<L>(re[0], re[1], beta, r01);
+  digits_pair<L>(re[2], re[3], beta, r23);
+  digits_pair<L>(im[0], im[1], beta, i01);
+  digits_pair<L>(im[2], im[3], beta, i23);
+  // digit s of an element lies (s >> 1) * S2 + (s & 1) * S1 past digit 0 (both layouts)
+  if (aout) {
+    __nv_bfloat16* oa = aout + (long long)b * a_item_elems;
+    const long long s1 = pairs ? 16 : (long long)Mp * Kp, s2 = pairs ? 2LL * Mp * Kp : 2 * s1;
+    __nv_bfloat16* pr = oa + a_digit_off(pairs, 0, row, k, Mp, Kp);
+    __nv_bfloat16* pi = oa + a_digit_off(pairs, 0, row, Kh + k, Mp, Kp);
+#pragma unroll
+    for (int s = 0; s < L; ++s) {
+      const long long o = (s >> 1) * s2 + (s & 1) * s1;
+      if (!(askip & 1)) *reinterpret_cast<uint2*>(pr + o) = make_uint2(r01[s], r23[s]);
+      if (!(askip & 2)) *reinterpret_cast<uint2*>(pi + o) = make_uint2(i01[s], i23[s]);
     }
-    uint32_t r01[L], r23[L], i01[L], i23[L];
-    digits_pair<L>(re[0], re[1], beta, r01);
-    digits_pair<L>(re[2], re[3], beta, r23);
-    digits_pair<L>(im[0], im[1], beta, i01);
-    digits_pair<L>(im[2], im[3], beta, i23);
-    if (oa) {
-      __nv_bfloat16* pr = oa + a_digit_off(pairs, 0, row, k, Mp, Kp);
-      __nv_bfloat16* pi = oa + a_digit_off(pairs, 0, row, Kh + k, Mp, Kp);
+  }
+  if (bout) {
+    __nv_bfloat16* ob = bout + (long long)b * b_item_elems;
+    const long long s1 = pairs ? 16 : 3LL * brows * Kh, s2 = pairs ? 6LL * brows * Kh : 2 * s1;
+    const long long plane = pairs ? 2LL * brows * Kh : (long long)brows * Kh;
+    __nv_bfloat16* p0 = ob + b_digit_off(pairs, 0, 0, row, k, brows, Kh);
 #pragma unroll
-      for (int s = 0; s < L; ++s) {
-        const long long o = (s >> 1) * a_s2 + (s & 1) * a_s1;
-        if (!(askip & 1)) *reinterpret_cast<uint2*>(pr + o) = make_uint2(r01[s], r23[s]);
-        if (!(askip & 2)) *reinterpret_cast<uint2*>(pi + o) = make_uint2(i01[s], i23[s]);
-      }
-    }
-    if (ob) {
-      __nv_bfloat16* p0 = ob + b_digit_off(pairs, 0, 0, row, k, brows, Kh);
-      const long long plane = pairs ? 2LL * brows * Kh : (long long)brows * Kh;
-#pragma unroll
-      for (int s = 0; s < L; ++s) {
-        const long long o = (s >> 1) * b_s2 + (s & 1) * b_s1;
-        const uint2 wi = make_uint2(i01[s], i23[s]);
-        if (!(bskip & 1)) *reinterpret_cast<uint2*>(p0 + o) = neg4(wi);
-        if (!(bskip & 2)) *reinterpret_cast<uint2*>(p0 + o + plane) = make_uint2(r01[s], r23[s]);
-        if (!(bskip & 4)) *reinterpret_cast<uint2*>(p0 + o + 2 * plane) = wi;
-      }
+    for (int s = 0; s < L; ++s) {
+      const long long o = (s >> 1) * s2 + (s & 1) * s1;
+      const uint2 wi = make_uint2(i01[s], i23[s]);
+      if (!(bskip & 1)) *reinterpret_cast<uint2*>(p0 + o) = neg4(wi);
+      if (!(bskip & 2)) *reinterpret_cast<uint2*>(p0 + o + plane) = make_uint2(r01[s], r23[s]);
+      if (!(bskip & 4)) *reinterpret_cast<uint2*>(p0 + o + 2 * plane) = wi;
     }
   }
 }
@@ -1068,13 +1127,13 @@ split_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
   }
 }
 
-// C_ij = C_ji for every i < j after a symmetric product: the tiles it skipped (wholly
-// right of the diagonal) and the upper parts of the diagonal tiles, whose entries were
-// computed directly and differ from their transposes by the rounding order of the
-// level->=3 accumulator.  Every source lies on or below the diagonal, in a computed
-// tile, and is never written here, so the result is exactly symmetric and the same for
-// every tiling.  One 32 x 32 block per CTA: grid (ceil(d/32), ceil(d/32), batch), blocks
-// below the diagonal return at once; 256 threads; DF32 storage (float4 per element).
+// C_ij = C_ji for every i < j of a symmetric matrix in lower-block storage: the blocks
+// right of the diagonal and the upper halves of the diagonal blocks (whose entries, where
+// a product computed them, differ from their transposes by the rounding order of the
+// level->=3 accumulator).  Every source lies on or below the diagonal and is never written
+// here, so the result is exactly symmetric.  One 32 x 32 block per CTA: grid (ceil(d/32),
+// ceil(d/32), batch), blocks below the diagonal return at once; 256 threads; DF32
+// storage (float4 per element).
 __global__ void __launch_bounds__(256)
 sym_mirror_kernel(int d, float4* __restrict__ C, long long sC4, const int* __restrict__ item_sq, int sq_step) {
   const int i0 = blockIdx.y * 32, j0 = blockIdx.x * 32, b = blockIdx.z;
@@ -1345,14 +1404,22 @@ static int launch_slicers_LT(const SplitGeom& g, int batch, const double* A, lon
   return MG_OK;
 }
 
-template <int L, typename T>
-static int launch_slice_sym_LT(const SplitGeom& g, int batch, const double* M, long long sM, __nv_bfloat16* Ad,
-                               int* ea, int askip, __nv_bfloat16* Bd, int* eb, int bskip, cudaStream_t s,
-                               const SplitCtl& ctl) {
-  slice_sym_kernel<L, T><<<dim3(ceil_div(g.d, 8), batch), 256, 0, s>>>(
-      g.d, g.Kp, g.Mp, g.beta, M, sM, Ad, ea, g.a_item_elems(), askip, Bd, eb, g.b_item_elems(), g.Np / 2, bskip,
-      ctl.item_sq, ctl.sq_step, paired_layout(g, ctl));
-  return check_launch("slice_sym_kernel");
+template <int L>
+static int launch_slice_sym_L(const SplitGeom& g, int batch, const double* M, long long sM, __nv_bfloat16* Ad,
+                              int* ea, int askip, __nv_bfloat16* Bd, int* eb, int bskip, cudaStream_t s,
+                              const SplitCtl& ctl) {
+  const int nb = ceil_div(g.d, 32);
+  const float4* M4 = reinterpret_cast<const float4*>(M);
+  if (Ad) MG_CUDA_TRY(cudaMemsetAsync(ea, 0x80, sizeof(int) * (size_t)g.Mp * batch, s));
+  if (Bd) MG_CUDA_TRY(cudaMemsetAsync(eb, 0x80, sizeof(int) * (size_t)(g.Np / 2) * batch, s));
+  sym_exponent_kernel<<<dim3(nb, nb, batch), 256, 0, s>>>(g.d, M4, sM / 2, Ad ? ea : eb, Ad ? g.Mp : g.Np / 2,
+                                                          Ad && Bd ? eb : nullptr, g.Np / 2, ctl.item_sq,
+                                                          ctl.sq_step);
+  MG_TRY(check_launch("sym_exponent_kernel"));
+  slice_sym_block_kernel<L><<<dim3(g.Kh() / 32, nb, batch), 256, 0, s>>>(
+      g.d, g.Kp, g.Mp, g.beta, M4, sM / 2, Ad, ea, g.a_item_elems(), askip, Bd, eb, g.b_item_elems(), g.Np / 2,
+      bskip, ctl.item_sq, ctl.sq_step, paired_layout(g, ctl));
+  return check_launch("slice_sym_block_kernel");
 }
 
 template <int L>
@@ -1380,29 +1447,26 @@ static int launch_slicers(const SplitGeom& g, int batch, int in_df32, const doub
 
 // Public-to-the-library entry points ------------------------------------------
 
-// Digits of a symmetric matrix for the A operand (abuf), the B operand (bbuf) or both
-// (either may be null), in one pass over its rows; askip / bskip as in slice_sym_kernel.
-int split_slice_sym(int d, int L, int batch, const double* M, long long sM, int in_df32, void* abuf, int askip,
-                    void* bbuf, int bskip, cudaStream_t s, const SplitCtl& ctl) {
+// Digits of a complex symmetric matrix in lower-block storage (double-float) for the A
+// operand (abuf), the B operand (bbuf) or both (either may be null); askip / bskip as in
+// slice_sym_block_kernel.
+int split_slice_sym(int d, int L, int batch, const double* M, long long sM, void* abuf, int askip, void* bbuf,
+                    int bskip, cudaStream_t s, const SplitCtl& ctl) {
   SplitGeom g = split_geom(d, L);
+  if (batch > 65535) return MG_EUNSUPPORTED;
   __nv_bfloat16* Ad = reinterpret_cast<__nv_bfloat16*>(abuf);
   int* ea = Ad ? reinterpret_cast<int*>(Ad + g.a_item_elems() * batch) : nullptr;
   __nv_bfloat16* Bd = reinterpret_cast<__nv_bfloat16*>(bbuf);
   int* eb = Bd ? reinterpret_cast<int*>(Bd + g.b_item_elems() * batch) : nullptr;
-#define MG_SYM_CASE(LL)                                                                                  \
-  case LL:                                                                                               \
-    return in_df32 ? launch_slice_sym_LT<LL, df32>(g, batch, M, sM, Ad, ea, askip, Bd, eb, bskip, s, ctl) \
-                   : launch_slice_sym_LT<LL, double>(g, batch, M, sM, Ad, ea, askip, Bd, eb, bskip, s, ctl);
   switch (L) {
-    MG_SYM_CASE(2)
-    MG_SYM_CASE(3)
-    MG_SYM_CASE(4)
-    MG_SYM_CASE(5)
-    MG_SYM_CASE(6)
-    MG_SYM_CASE(7)
-    MG_SYM_CASE(8)
+    case 2: return launch_slice_sym_L<2>(g, batch, M, sM, Ad, ea, askip, Bd, eb, bskip, s, ctl);
+    case 3: return launch_slice_sym_L<3>(g, batch, M, sM, Ad, ea, askip, Bd, eb, bskip, s, ctl);
+    case 4: return launch_slice_sym_L<4>(g, batch, M, sM, Ad, ea, askip, Bd, eb, bskip, s, ctl);
+    case 5: return launch_slice_sym_L<5>(g, batch, M, sM, Ad, ea, askip, Bd, eb, bskip, s, ctl);
+    case 6: return launch_slice_sym_L<6>(g, batch, M, sM, Ad, ea, askip, Bd, eb, bskip, s, ctl);
+    case 7: return launch_slice_sym_L<7>(g, batch, M, sM, Ad, ea, askip, Bd, eb, bskip, s, ctl);
+    case 8: return launch_slice_sym_L<8>(g, batch, M, sM, Ad, ea, askip, Bd, eb, bskip, s, ctl);
   }
-#undef MG_SYM_CASE
   return MG_EINVAL;
 }
 
@@ -1458,10 +1522,17 @@ int split_gemm(int d, int L, int batch, const void* abuf, const void* bbuf, doub
     case 7: r = launch_split_gemm_L<7>(g, batch, Ad, ea, Bd, eb, C, sC, e, status, ctl, s); break;
     case 8: r = launch_split_gemm_L<8>(g, batch, Ad, ea, Bd, eb, C, sC, e, status, ctl, s); break;
   }
-  if (r != MG_OK || !ctl.sym_out) return r;
+  // a symmetric result stays in lower-block storage: its consumers read the lower blocks
+  return r;
+}
+
+// C_ij = C_ji for every i < j of a batch of symmetric matrices in lower-block storage (the
+// full matrix, for a consumer that reads every entry).
+int split_sym_fill(int d, int batch, double* C, long long sC, cudaStream_t s) {
+  if (batch <= 0) return MG_OK;
+  if (batch > 65535) return MG_EUNSUPPORTED;
   const int nb = ceil_div(d, 32);
-  sym_mirror_kernel<<<dim3(nb, nb, batch), 256, 0, s>>>(d, reinterpret_cast<float4*>(C), sC / 2, ctl.item_sq,
-                                                        ctl.sq_step);
+  sym_mirror_kernel<<<dim3(nb, nb, batch), 256, 0, s>>>(d, reinterpret_cast<float4*>(C), sC / 2, nullptr, 0);
   return check_launch("sym_mirror_kernel");
 }
 
