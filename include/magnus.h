@@ -569,16 +569,19 @@ int mg_ctx_set_cta_pairs(mg_ctx* ctx, int on);
  * mg_plan_set_magnus_order) check both on the device.  `on` is a bit mask:
  *   bit 0: the products X X, X^2 X and X^3 X^3 of the Taylor polynomial (and the power
  *          products of the Paterson-Stockmeyer forms) leave out the digit products of the
- *          zero parts: the zero half of the K axis of A is not loaded, and where B has a
- *          zero part each half of K multiplies the other one into the output half it feeds
- *          (N = 64 MMAs, one CTA per tile): a quarter of a general product's tensor-core
- *          work.  Only exact zeros are left out: the result is the same as without.
+ *          zero parts: the zero half of the K axis of A is not loaded, and only the B
+ *          plane that the remaining half meets is multiplied -- one real product into
+ *          one output half (on CTA pairs as M = 256 x N = 128 MMAs over 128 output
+ *          columns of that half; on single CTAs as N = 64 MMAs): a quarter of a general
+ *          product's tensor-core work.  Only exact zeros are left out: the result is the
+ *          same as without.
  *   bit 1: every product of the exponential (Taylor polynomial and squarings) computes
- *          only the output tiles on or below the diagonal (128-row tiles, or 256 on CTA
- *          pairs) and then copies every entry above the diagonal from its transpose: the
- *          result is exactly symmetric, the same on either tiling, and differs from the
- *          full product's by that product's own rounding asymmetry.  The tree product of
- *          the U_n is general.
+ *          only the output tiles on or below the diagonal (128-row tiles on single CTAs,
+ *          256 on CTA pairs), and its symmetric matrices are kept as their 32 x 32 blocks
+ *          on and below the diagonal, entry (i, j) with j > i read as (j, i); each U_n is
+ *          written in full, exactly symmetric, the same on either tiling, and differs from
+ *          the full products' by their own rounding asymmetry.  The tree product of the
+ *          U_n is general.
  * 3 (the default) sets both, 0 issues every product in full.  Applies to mg_evolve,
  * mg_evolve_batch (a batch only when all of its plans qualify) and the chunk steps of a
  * server (mg_submit checks each job's operators; a step only when all of its jobs
