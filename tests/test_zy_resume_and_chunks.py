@@ -12,7 +12,7 @@ without the trace shift.
 * MG_FLAG_NO_TRACE_SHIFT: the exponent keeps its trace, and the phase is carried by
   the polynomial and the squarings instead of an exact factor.
 
-This file is collected last of the GPU suite.
+This file is collected late in the GPU suite, just before the allocation-free product's.
 """
 import numpy as np
 import pytest
